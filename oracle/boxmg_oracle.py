@@ -1,0 +1,545 @@
+"""Plain FP64 CPU oracle of the BoxMG V-cycle for 2D heterogeneous diffusion.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+benchmark's CPU-baseline leg may import this module.  The library's product
+path never calls it, and it shares no code with the CUDA path.
+
+What it computes (Reisner, Olson, Moulton, "Scaling Structured Multigrid to
+500K+ Cores through Coarse-Grid Redistribution"):
+
+* ``assemble_fv5``   -- the standard 5-point cell-centred finite-volume
+  discretisation of Eq. (diffusion) with the homogeneous Dirichlet condition
+  of Eq. (diffusion_bc) (Section 5).  Face coefficients are harmonic means
+  2 k1 k2 / (k1 + k2); a boundary face contributes 2 k to the diagonal.  The
+  operator is scaled by h^2 (square cells), so the right-hand side b is used
+  as given.
+* ``interpolation``  -- operator-induced interpolation P (Section 2): weights
+  from the operator, stored per fine point, computed by collapsing the fine
+  stencil (flux continuity, Dendy's black-box construction).  Coarse point I
+  is fine point 2I (1-based); coarsening by 2 (Section 2).
+* ``galerkin``       -- the variational coarse operator A_{l-1} = P^T A_l P
+  (Section 2), formed literally as a sparse triple product; the result is
+  checked to be a 9-point stencil.
+* ``cholesky`` / ``cholesky_solve`` -- the coarsest-grid direct solve, with
+  the factor computed once in setup (Section 3, Eq. for T_cgsolve).
+* ``relax``          -- multicolour point Gauss-Seidel (Section 2, Section 3
+  Eq. for T_smooth, Section 5): red-black on the 5-point finest level, four
+  colours on 9-point coarse levels.
+* ``residual``, restriction R = P^T, interpolate-and-correct -- Algorithm 1,
+  with the optional r/C term of the interpolation equations in Section 3.
+* ``vcycle`` / ``solve`` -- Algorithm 1, iterated until the relative residual
+  ||b - A x||_2 / ||b||_2 is at most ``tol``.
+* ``assembly_vjp`` / ``adjoint_gradient`` -- the gradient of
+  L = 0.5 ||u - u_obs||^2 with respect to log-coefficients through the adjoint
+  equation A lambda = u - u_obs (A is symmetric), with exact sparse solves.
+
+Readings where the paper is silent (each is also listed in the design notes):
+* interpolation weights: x-edge point w_W = (a_W + a_SW + a_NW) / (C - a_S - a_N)
+  (and the mirror for E); y-edge point w_S = (a_S + a_SW + a_SE) / (C - a_W - a_E)
+  (and the mirror for N); cell-centre point: the fine equation at the point
+  with the four edge neighbours replaced by their interpolants.  Here a_X >= 0
+  are the negated off-diagonal entries of the fine row.
+* colour order: red = (i + j) even (1-based), first; four colours
+  (i mod 2, j mod 2) in the order (1,1), (0,1), (1,0), (0,0).  Pre-smoothing
+  runs the colours forward, post-smoothing in reverse.
+* residual norm: the Euclidean norm; the stop test is applied after each
+  full cycle (and once before the first).
+* sizes: nx and ny of the form 2^m - 1; coarsening stops when the smaller
+  side reaches 3.
+
+Data layout: every grid quantity is a float64 array of shape (ny, nx),
+``a[j, i]`` with i the x index (fast).  A stencil is a dict of nine planes,
+'C' and the eight negated off-diagonals 'W','E','S','N','SW','SE','NW','NE'
+(``st['E'][j, i] = -A[(i, j), (i + 1, j)]``), zero where the neighbour lies
+outside the domain.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+# direction -> (di, dj) offset of the neighbour in (x, y)
+OFFSETS = {
+    "W": (-1, 0), "E": (1, 0), "S": (0, -1), "N": (0, 1),
+    "SW": (-1, -1), "SE": (1, -1), "NW": (-1, 1), "NE": (1, 1),
+}
+DIRS = tuple(OFFSETS)
+
+
+# ---------------------------------------------------------------------------
+# Discretisation (Section 5, Eqs. (diffusion), (diffusion_bc))
+# ---------------------------------------------------------------------------
+
+def harmonic_face(k1: np.ndarray, k2: np.ndarray) -> np.ndarray:
+    """Face coefficient between two square cells: the series conductance of
+    two half cells, 2 k1 k2 / (k1 + k2)."""
+    return 2.0 * k1 * k2 / (k1 + k2)
+
+
+def assemble_fv5(k: np.ndarray) -> dict:
+    """5-point cell-centred FV operator for -div(k grad u) = f, u = 0 on the
+    boundary of the unit square (Section 5), scaled by h^2.
+
+    Interior faces carry the harmonic mean of the two cell coefficients; a
+    boundary face sits half a cell from the cell centre and carries 2 k.  The
+    diagonal C is the sum of the cell's four face coefficients.
+    """
+    k = np.asarray(k, dtype=np.float64)
+    ny, nx = k.shape
+    st = {d: np.zeros((ny, nx)) for d in ("C",) + DIRS}
+    ax = harmonic_face(k[:, :-1], k[:, 1:])          # face between i and i+1
+    ay = harmonic_face(k[:-1, :], k[1:, :])          # face between j and j+1
+    st["E"][:, :-1] = ax
+    st["W"][:, 1:] = ax
+    st["N"][:-1, :] = ay
+    st["S"][1:, :] = ay
+    bw = np.zeros((ny, nx))                          # boundary face coefficients
+    bw[:, 0] += 2.0 * k[:, 0]
+    bw[:, -1] += 2.0 * k[:, -1]
+    bw[0, :] += 2.0 * k[0, :]
+    bw[-1, :] += 2.0 * k[-1, :]
+    st["C"] = st["W"] + st["E"] + st["S"] + st["N"] + bw
+    return st
+
+
+def shifted(xp: np.ndarray, d: str, ny: int, nx: int,
+            rows=slice(None), cols=slice(None)) -> np.ndarray:
+    """Neighbour values x[j + dj, i + di] read from the zero-padded array
+    ``xp`` (one ghost cell on every side), restricted to rows/cols of the
+    unpadded grid."""
+    di, dj = OFFSETS[d]
+    v = xp[1 + dj:1 + dj + ny, 1 + di:1 + di + nx]
+    return v[rows, cols]
+
+
+def apply(st: dict, x: np.ndarray) -> np.ndarray:
+    """y = A x for a stencil in plane form."""
+    ny, nx = x.shape
+    xp = np.pad(x, 1)
+    y = st["C"] * x
+    for d in DIRS:
+        y = y - st[d] * shifted(xp, d, ny, nx)
+    return y
+
+
+def residual(st: dict, x: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """r = b - A x (Algorithm 1)."""
+    return b - apply(st, x)
+
+
+def stencil_to_csr(st: dict) -> sp.csr_matrix:
+    """The matrix of a plane-form stencil; unknown (i, j) has index j*nx + i."""
+    ny, nx = st["C"].shape
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    rows = [idx.ravel()]
+    cols = [idx.ravel()]
+    vals = [st["C"].ravel()]
+    for d, (di, dj) in OFFSETS.items():
+        j0, j1 = max(0, -dj), ny - max(0, dj)
+        i0, i1 = max(0, -di), nx - max(0, di)
+        r = idx[j0:j1, i0:i1]
+        c = idx[j0 + dj:j1 + dj, i0 + di:i1 + di]
+        v = -st[d][j0:j1, i0:i1]
+        rows.append(r.ravel())
+        cols.append(c.ravel())
+        vals.append(v.ravel())
+    a = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(nx * ny, nx * ny))
+    return a.tocsr()
+
+
+def csr_to_stencil(a: sp.spmatrix, nx: int, ny: int) -> dict:
+    """Plane form of a matrix whose pattern is at most 9-point; raises if an
+    entry couples unknowns more than one cell apart."""
+    a = a.tocoo()
+    jr, ir = np.divmod(a.row, nx)
+    jc, ic = np.divmod(a.col, nx)
+    di = ic - ir
+    dj = jc - jr
+    if np.any(np.abs(di) > 1) or np.any(np.abs(dj) > 1):
+        raise ValueError("operator is not a 9-point stencil")
+    st = {d: np.zeros((ny, nx)) for d in ("C",) + DIRS}
+    diag = (di == 0) & (dj == 0)
+    np.add.at(st["C"], (jr[diag], ir[diag]), a.data[diag])
+    for d, (ddi, ddj) in OFFSETS.items():
+        m = (di == ddi) & (dj == ddj)
+        np.add.at(st[d], (jr[m], ir[m]), -a.data[m])
+    return st
+
+
+# ---------------------------------------------------------------------------
+# Operator-induced interpolation (Section 2; weights stored per point as in
+# the interpolation stencil of Section 3)
+# ---------------------------------------------------------------------------
+
+def coarse_size(n: int) -> int:
+    """Standard coarsening by 2: coarse point I is fine point 2I (1-based)."""
+    return (n - 1) // 2
+
+
+def edge_weights(st: dict):
+    """Weights of the two kinds of edge points.
+
+    x-edge points lie on a coarse row between two coarse points (1-based i
+    odd, j even; 0-based rows 1::2, cols 0::2).  Collapsing the fine row in y
+    gives the 1D flux balance (C - a_S - a_N) u = (a_W + a_SW + a_NW) u_W +
+    (a_E + a_SE + a_NE) u_E.  y-edge points (0-based rows 0::2, cols 1::2)
+    are the mirror image.  Returns (xw, xe, ys, yn).
+    """
+    xs = (slice(1, None, 2), slice(0, None, 2))
+    den = st["C"][xs] - st["S"][xs] - st["N"][xs]
+    xw = (st["W"][xs] + st["SW"][xs] + st["NW"][xs]) / den
+    xe = (st["E"][xs] + st["SE"][xs] + st["NE"][xs]) / den
+    ysl = (slice(0, None, 2), slice(1, None, 2))
+    den = st["C"][ysl] - st["W"][ysl] - st["E"][ysl]
+    ys = (st["S"][ysl] + st["SW"][ysl] + st["SE"][ysl]) / den
+    yn = (st["N"][ysl] + st["NW"][ysl] + st["NE"][ysl]) / den
+    return xw, xe, ys, yn
+
+
+def interpolation(st: dict) -> sp.csr_matrix:
+    """Operator-induced interpolation P_l from level l-1 (coarse) to level l.
+
+    Returns a CSR matrix of shape (nx*ny, ncx*ncy).  Rows are fine unknowns,
+    columns interior coarse unknowns; weights towards ghost coarse points
+    (outside the domain, value 0) are dropped.
+    """
+    ny, nx = st["C"].shape
+    ncx, ncy = coarse_size(nx), coarse_size(ny)
+    fidx = np.arange(nx * ny).reshape(ny, nx)
+
+    def cidx(q, p):
+        """Flat coarse index of 0-based coarse (row q, col p); -1 for ghosts."""
+        q = np.asarray(q)
+        p = np.asarray(p)
+        ok = (q >= 0) & (q < ncy) & (p >= 0) & (p < ncx)
+        return np.where(ok, q * ncx + p, -1)
+
+    rows, cols, vals = [], [], []
+
+    def add(frows, ccols, w):
+        frows, ccols, w = np.broadcast_arrays(frows, ccols, w)
+        keep = ccols >= 0
+        rows.append(frows[keep])
+        cols.append(ccols[keep])
+        vals.append(w[keep])
+
+    # coarse points: injection (0-based fine rows 1::2, cols 1::2)
+    q, p = np.meshgrid(np.arange(ncy), np.arange(ncx), indexing="ij")
+    add(fidx[1::2, 1::2], cidx(q, p), np.ones((ncy, ncx)))
+
+    xw, xe, ys, yn = edge_weights(st)
+    # x-edge point (row 2q+1, col 2p): west coarse (q, p-1), east (q, p)
+    q, p = np.meshgrid(np.arange(ncy), np.arange(ncx + 1), indexing="ij")
+    add(fidx[1::2, 0::2], cidx(q, p - 1), xw)
+    add(fidx[1::2, 0::2], cidx(q, p), xe)
+    # y-edge point (row 2q, col 2p+1): south coarse (q-1, p), north (q, p)
+    q, p = np.meshgrid(np.arange(ncy + 1), np.arange(ncx), indexing="ij")
+    add(fidx[0::2, 1::2], cidx(q - 1, p), ys)
+    add(fidx[0::2, 1::2], cidx(q, p), yn)
+
+    # cell-centre point (row 2q, col 2p).  Its W/E neighbours are y-edge
+    # points (q, p-1) and (q, p); its S/N neighbours are x-edge points
+    # (q-1, p) and (q, p).  Edge weights of neighbours outside the grid are
+    # taken as 0; their a-coefficients are 0 anyway (Dirichlet).
+    ysp = np.pad(ys, ((0, 0), (1, 1)))   # ysp[q, p'] = ys[q, p'-1]
+    ynp = np.pad(yn, ((0, 0), (1, 1)))
+    xwp = np.pad(xw, ((1, 1), (0, 0)))   # xwp[q', p] = xw[q'-1, p]
+    xep = np.pad(xe, ((1, 1), (0, 0)))
+    cs = (slice(0, None, 2), slice(0, None, 2))
+    c = st["C"][cs]
+    aw, ae, as_, an = st["W"][cs], st["E"][cs], st["S"][cs], st["N"][cs]
+    q, p = np.meshgrid(np.arange(ncy + 1), np.arange(ncx + 1), indexing="ij")
+    ys_w, ys_e = ysp[:, 0:ncx + 1], ysp[:, 1:ncx + 2]   # W nbr (q,p-1), E nbr (q,p)
+    yn_w, yn_e = ynp[:, 0:ncx + 1], ynp[:, 1:ncx + 2]
+    xw_s, xw_n = xwp[0:ncy + 1, :], xwp[1:ncy + 2, :]   # S nbr (q-1,p), N nbr (q,p)
+    xe_s, xe_n = xep[0:ncy + 1, :], xep[1:ncy + 2, :]
+    w_sw = (st["SW"][cs] + aw * ys_w + as_ * xw_s) / c
+    w_se = (st["SE"][cs] + ae * ys_e + as_ * xe_s) / c
+    w_nw = (st["NW"][cs] + aw * yn_w + an * xw_n) / c
+    w_ne = (st["NE"][cs] + ae * yn_e + an * xe_n) / c
+    f = fidx[0::2, 0::2]
+    add(f, cidx(q - 1, p - 1), w_sw)
+    add(f, cidx(q - 1, p), w_se)
+    add(f, cidx(q, p - 1), w_nw)
+    add(f, cidx(q, p), w_ne)
+
+    pm = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                       shape=(nx * ny, ncx * ncy))
+    return pm.tocsr()
+
+
+def galerkin(st: dict, p: sp.csr_matrix) -> dict:
+    """Variational coarse operator P^T A P (Section 2) as a sparse triple
+    product; returned in plane form (raises unless it is 9-point)."""
+    ny, nx = st["C"].shape
+    a = stencil_to_csr(st)
+    ac = (p.T @ (a @ p)).tocsr()
+    return csr_to_stencil(ac, coarse_size(nx), coarse_size(ny))
+
+
+# ---------------------------------------------------------------------------
+# Coarsest-grid direct solve (Section 3, cost model of the coarse solve:
+# a Cholesky factorisation computed and stored in setup)
+# ---------------------------------------------------------------------------
+
+def cholesky(m: np.ndarray) -> np.ndarray:
+    """Lower-triangular L with L L^T = m (column-by-column Cholesky)."""
+    n = m.shape[0]
+    lo = np.zeros_like(m, dtype=np.float64)
+    for j in range(n):
+        s = m[j, j] - lo[j, :j] @ lo[j, :j]
+        if not s > 0.0:
+            raise ValueError("coarsest operator is not positive definite")
+        lo[j, j] = np.sqrt(s)
+        for i in range(j + 1, n):
+            lo[i, j] = (m[i, j] - lo[i, :j] @ lo[j, :j]) / lo[j, j]
+    return lo
+
+
+def cholesky_solve(lo: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Solve L L^T x = b by forward then backward substitution."""
+    n = lo.shape[0]
+    y = np.zeros(n)
+    for i in range(n):
+        y[i] = (b[i] - lo[i, :i] @ y[:i]) / lo[i, i]
+    x = np.zeros(n)
+    for i in range(n - 1, -1, -1):
+        x[i] = (y[i] - lo[i + 1:, i] @ x[i + 1:]) / lo[i, i]
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Multicolour Gauss-Seidel (Section 2 smoothing; Section 3 T_smooth with n_c
+# colours; Section 5 four-colour Gauss-Seidel)
+# ---------------------------------------------------------------------------
+
+# Each colour is a union of the four parity sub-lattices, named by 0-based
+# (row parity, col parity).  1-based (i mod 2, j mod 2) = (1, 1) is 0-based
+# (even col, even row).
+RB_ORDER = (((0, 0), (1, 1)),            # red: (i + j) even
+            ((0, 1), (1, 0)))            # black
+FOUR_ORDER = (((0, 0),),                 # (i mod 2, j mod 2) = (1, 1)
+              ((0, 1),),                 # (0, 1): i even, j odd  -> col odd, row even
+              ((1, 0),),                 # (1, 0): i odd, j even  -> col even, row odd
+              ((1, 1),))                 # (0, 0)
+
+
+def is_five_point(st: dict) -> bool:
+    return all(not np.any(st[d]) for d in ("SW", "SE", "NW", "NE"))
+
+
+def colour_order(st: dict):
+    """Red-black on a 5-point level (the assembled finest level), four
+    colours on a 9-point level (every Galerkin coarse level)."""
+    return RB_ORDER if is_five_point(st) else FOUR_ORDER
+
+
+def relax(st: dict, x: np.ndarray, b: np.ndarray, nu: int, order,
+          reverse: bool = False) -> None:
+    """``nu`` multicolour Gauss-Seidel sweeps in place.  Within one colour no
+    two points are coupled, so each sub-lattice update reads only values of
+    other colours: x_p <- (b_p + sum_X a_X x_{p+X}) / C_p."""
+    ny, nx = x.shape
+    seq = tuple(reversed(order)) if reverse else tuple(order)
+    for _ in range(nu):
+        for colour in seq:
+            for (pj, pi) in colour:
+                rows = slice(pj, None, 2)
+                cols = slice(pi, None, 2)
+                xp = np.pad(x, 1)
+                s = b[rows, cols].copy()
+                for d in DIRS:
+                    s += st[d][rows, cols] * shifted(xp, d, ny, nx, rows, cols)
+                x[rows, cols] = s / st["C"][rows, cols]
+
+
+# ---------------------------------------------------------------------------
+# Hierarchy and V-cycle (Algorithm 1)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Level:
+    st: dict                       # A_l in plane form
+    p: sp.csr_matrix | None = None  # P_l: level l-1 -> level l (None on level 0)
+
+    @property
+    def shape(self):
+        return self.st["C"].shape
+
+
+@dataclass
+class Hierarchy:
+    levels: list                   # levels[0] coarsest ... levels[L-1] finest
+    chol: np.ndarray               # Cholesky factor of A_0
+    nu1: int = 2
+    nu2: int = 1
+    interp_residual_term: bool = False
+    stats: dict = field(default_factory=dict)
+
+    @property
+    def nlevels(self):
+        return len(self.levels)
+
+
+def valid_size(n: int) -> bool:
+    return n >= 3 and ((n + 1) & n) == 0
+
+
+def level_shapes(nx: int, ny: int):
+    """[(nx, ny) finest, ..., coarsest]: halve (n - 1) / 2 until the smaller
+    side is 3."""
+    if not (valid_size(nx) and valid_size(ny)):
+        raise ValueError("grid sides must be 2^m - 1 >= 3")
+    out = [(nx, ny)]
+    while min(nx, ny) > 3:
+        nx, ny = coarse_size(nx), coarse_size(ny)
+        out.append((nx, ny))
+    return out
+
+
+def setup(k: np.ndarray, nu1: int = 2, nu2: int = 1,
+          interp_residual_term: bool = False) -> Hierarchy:
+    """BoxMG setup: assemble the fine operator, then for each level build P_l
+    from A_l and A_{l-1} = P_l^T A_l P_l; factor A_0 (Section 2)."""
+    ny, nx = k.shape
+    shapes = level_shapes(nx, ny)
+    if not np.all(np.isfinite(k)) or np.any(k <= 0):
+        raise ValueError("coefficients must be finite and positive")
+    st = assemble_fv5(k)
+    fine_to_coarse = [Level(st)]
+    for _ in shapes[1:]:
+        p = interpolation(st)
+        st_c = galerkin(st, p)
+        fine_to_coarse[-1].p = p
+        fine_to_coarse.append(Level(st_c))
+        st = st_c
+    levels = fine_to_coarse[::-1]          # levels[0] coarsest
+    a0 = stencil_to_csr(levels[0].st).toarray()
+    return Hierarchy(levels=levels, chol=cholesky(a0), nu1=nu1, nu2=nu2,
+                     interp_residual_term=interp_residual_term)
+
+
+def vcycle(h: Hierarchy, x: np.ndarray, b: np.ndarray) -> None:
+    """One V(nu1, nu2) cycle of Algorithm 1, updating the finest x in place."""
+    nl = h.nlevels
+    xs = [None] * nl
+    bs = [None] * nl
+    rs = [None] * nl
+    xs[nl - 1], bs[nl - 1] = x, b
+    for l in range(nl - 1, 0, -1):
+        lev = h.levels[l]
+        order = colour_order(lev.st)
+        relax(lev.st, xs[l], bs[l], h.nu1, order)
+        rs[l] = residual(lev.st, xs[l], bs[l])
+        nyc, nxc = h.levels[l - 1].shape
+        bs[l - 1] = (lev.p.T @ rs[l].ravel()).reshape(nyc, nxc)
+        xs[l - 1] = np.zeros((nyc, nxc))
+    xs[0][:] = cholesky_solve(h.chol, bs[0].ravel()).reshape(xs[0].shape)
+    for l in range(1, nl):
+        lev = h.levels[l]
+        corr = (lev.p @ xs[l - 1].ravel()).reshape(xs[l].shape)
+        if h.interp_residual_term:
+            # Section 3 interpolation equations: add r/C at every fine point
+            # that is not a coarse point (injection points get no r/C).
+            rc = rs[l] / lev.st["C"]
+            rc[1::2, 1::2] = 0.0
+            corr = corr + rc
+        xs[l] += corr
+        order = colour_order(lev.st)
+        relax(lev.st, xs[l], bs[l], h.nu2, order, reverse=True)
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    cycles: int
+    rel_resid: float
+    history: list
+    converged: bool
+
+
+def solve(h: Hierarchy, b: np.ndarray, x0: np.ndarray | None = None,
+          tol: float = 1e-10, max_cycles: int = 200) -> SolveResult:
+    """Iterate V-cycles until ||b - A x||_2 / ||b||_2 <= tol (checked before
+    the first cycle and after each one) or ``max_cycles`` cycles ran."""
+    fine = h.levels[-1].st
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    bn = float(np.linalg.norm(b))
+    if bn == 0.0:
+        x[:] = 0.0
+        return SolveResult(x, 0, 0.0, [0.0], True)
+    rel = float(np.linalg.norm(residual(fine, x, b))) / bn
+    hist = [rel]
+    cycles = 0
+    while rel > tol and cycles < max_cycles:
+        vcycle(h, x, b)
+        cycles += 1
+        rel = float(np.linalg.norm(residual(fine, x, b))) / bn
+        hist.append(rel)
+        if not np.isfinite(rel):
+            break
+    return SolveResult(x, cycles, rel, hist, bool(rel <= tol))
+
+
+# ---------------------------------------------------------------------------
+# Adjoint gradient with respect to log-coefficients
+# ---------------------------------------------------------------------------
+
+def assembly_vjp(k: np.ndarray, u: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    """g_c = -d(lam^T A(theta) u)/d theta_c with k = exp(theta).
+
+    A = sum over interior faces f=(p,q) of a_f (e_p - e_q)(e_p - e_q)^T plus
+    sum over boundary faces of 2 k_p e_p e_p^T, so
+    lam^T A u = sum_f a_f (u_p - u_q)(lam_p - lam_q) + sum_bf 2 k_p u_p lam_p.
+    With da/dk1 = 2 k2^2 / (k1 + k2)^2 and dk/dtheta = k:
+    g_c = -k_c [ sum_{faces of c} da_f/dk_c (u_c - u_n)(lam_c - lam_n)
+                 + (number of boundary faces of c) * 2 u_c lam_c ].
+    """
+    k = np.asarray(k, dtype=np.float64)
+    ny, nx = k.shape
+    g = np.zeros((ny, nx))
+    # x faces between (i, j) and (i+1, j)
+    k1, k2 = k[:, :-1], k[:, 1:]
+    prod = (u[:, :-1] - u[:, 1:]) * (lam[:, :-1] - lam[:, 1:])
+    s = (k1 + k2) ** 2
+    g[:, :-1] += 2.0 * k2 * k2 / s * prod
+    g[:, 1:] += 2.0 * k1 * k1 / s * prod
+    # y faces
+    k1, k2 = k[:-1, :], k[1:, :]
+    prod = (u[:-1, :] - u[1:, :]) * (lam[:-1, :] - lam[1:, :])
+    s = (k1 + k2) ** 2
+    g[:-1, :] += 2.0 * k2 * k2 / s * prod
+    g[1:, :] += 2.0 * k1 * k1 / s * prod
+    # boundary faces
+    nb = np.zeros((ny, nx))
+    nb[:, 0] += 1
+    nb[:, -1] += 1
+    nb[0, :] += 1
+    nb[-1, :] += 1
+    g += nb * 2.0 * u * lam
+    return -k * g
+
+
+def direct_solve(k: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Exact (sparse LU) solution of the assembled system, for small grids."""
+    import scipy.sparse.linalg as spla
+    a = stencil_to_csr(assemble_fv5(k)).tocsc()
+    return spla.spsolve(a, b.ravel()).reshape(b.shape)
+
+
+def loss(theta: np.ndarray, b: np.ndarray, u_obs: np.ndarray) -> float:
+    """L = 0.5 ||u(theta) - u_obs||^2 with u the exact solution."""
+    u = direct_solve(np.exp(theta), b)
+    return 0.5 * float(np.sum((u - u_obs) ** 2))
+
+
+def adjoint_gradient(theta: np.ndarray, b: np.ndarray, u_obs: np.ndarray):
+    """dL/dtheta via the adjoint equation A lam = u - u_obs (A symmetric),
+    with exact sparse solves.  Returns (grad, u, lam)."""
+    k = np.exp(theta)
+    u = direct_solve(k, b)
+    lam = direct_solve(k, u - u_obs)
+    return assembly_vjp(k, u, lam), u, lam

@@ -1,0 +1,461 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, exact rational arithmetic done independently, invariants, library
+routines on special cases, brute force on tiny grids, or convergence orders.
+Together they are meant to fail for a dropped term, a wrong sign, a wrong
+index or a transposed operand anywhere in the oracle.
+"""
+from fractions import Fraction as F
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import boxmg_oracle as O
+from paper_1803_02481_gb300 import inputs
+
+
+# ---------------------------------------------------------------------------
+# Assembly (Section 5, Eqs. (diffusion), (diffusion_bc))
+# ---------------------------------------------------------------------------
+
+def test_assembly_constant_k_closed_form():
+    """k = 1: interior row [-1; -1 4 -1; -1]; a boundary face adds 2k, so an
+    edge cell has C = 3 + 2 = 5 and a corner cell C = 2 + 4 = 6; no coupling
+    leaves the domain."""
+    st = O.assemble_fv5(np.ones((5, 6)))
+    assert np.all(st["C"][1:-1, 1:-1] == 4.0)
+    assert st["C"][0, 2] == 5.0 and st["C"][2, 0] == 5.0 and st["C"][-1, 2] == 5.0
+    assert st["C"][0, 0] == 6.0 and st["C"][-1, -1] == 6.0 and st["C"][0, -1] == 6.0
+    for d in ("W", "E", "S", "N"):
+        inner = st[d][1:-1, 1:-1]
+        assert np.all(inner == 1.0)
+    assert np.all(st["W"][:, 0] == 0) and np.all(st["E"][:, -1] == 0)
+    assert np.all(st["S"][0, :] == 0) and np.all(st["N"][-1, :] == 0)
+    for d in ("SW", "SE", "NW", "NE"):
+        assert not np.any(st[d])
+
+
+def _mms_layered_error(n, k1, k2):
+    """u = sin(2 pi x) sin(pi y) / k(x), k = k1 left of x = 1/2, k2 right.
+    u is continuous (zero at x = 1/2), the flux k u_x = 2 pi cos(2 pi x)
+    sin(pi y) is continuous and non-zero there, and -div(k grad u) =
+    5 pi^2 sin(2 pi x) sin(pi y) on both sides."""
+    h = 1.0 / n
+    xc = (np.arange(n) + 0.5) * h
+    x, y = np.meshgrid(xc, xc)
+    k = np.where(x < 0.5, k1, k2)
+    u = np.sin(2 * np.pi * x) * np.sin(np.pi * y) / k
+    f = 5 * np.pi ** 2 * np.sin(2 * np.pi * x) * np.sin(np.pi * y)
+    uh = O.direct_solve(k, h * h * f)
+    return np.abs(uh - u).max() / np.abs(u).max()
+
+
+def test_assembly_second_order_across_interface():
+    """Harmonic-mean faces give O(h^2) across a coefficient jump aligned with
+    cell faces (an arithmetic mean would give O(h))."""
+    errs = [_mms_layered_error(n, 1.0, 100.0) for n in (16, 32, 64)]
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 3.6 < e0 / e1 < 4.4
+    assert errs[-1] < 1e-3
+
+
+def test_assembly_second_order_smooth_k():
+    """u = sin(pi x) sin(pi y), k = exp(x + 2y):
+    f = k (2 pi^2 u - pi cos(pi x) sin(pi y) - 2 pi sin(pi x) cos(pi y))."""
+    def err(n):
+        h = 1.0 / n
+        xc = (np.arange(n) + 0.5) * h
+        x, y = np.meshgrid(xc, xc)
+        k = np.exp(x + 2 * y)
+        u = np.sin(np.pi * x) * np.sin(np.pi * y)
+        f = k * (2 * np.pi ** 2 * u - np.pi * np.cos(np.pi * x) * np.sin(np.pi * y)
+                 - 2 * np.pi * np.sin(np.pi * x) * np.cos(np.pi * y))
+        return np.abs(O.direct_solve(k, h * h * f) - u).max()
+    errs = [err(n) for n in (16, 32, 64)]
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 3.6 < e0 / e1 < 4.4
+
+
+def test_operator_symmetric_positive_definite():
+    rng = np.random.default_rng(11)
+    k = 10.0 ** rng.uniform(-3, 3, size=(9, 12))
+    a = O.stencil_to_csr(O.assemble_fv5(k)).toarray()
+    assert np.array_equal(a, a.T)
+    assert np.linalg.eigvalsh(a).min() > 0
+
+
+# ---------------------------------------------------------------------------
+# Operator-induced interpolation (Section 2)
+# ---------------------------------------------------------------------------
+
+def _hat(n_fine, n_coarse, idx):
+    """1D piecewise-linear hat of coarse node ``idx`` (0-based) evaluated at
+    the fine cell centres of [0, 1].  Coarse node I (1-based) sits at fine
+    cell centre 2I, i.e. x = (2I - 0.5) h; the boundary x = 0, 1 is a node
+    with value 0 (Dirichlet)."""
+    h = 1.0 / n_fine
+    xf = (np.arange(n_fine) + 0.5) * h
+    nodes = np.concatenate([[0.0], (2 * np.arange(1, n_coarse + 1) - 0.5) * h, [1.0]])
+    vals = np.zeros(n_coarse + 2)
+    vals[idx + 1] = 1.0
+    return np.interp(xf, nodes, vals)
+
+
+def test_interpolation_constant_k_is_bilinear():
+    """k = 1: every column of P is the tensor product of 1D hats on the
+    coarse nodes plus the boundary (weights 1, 1/2, 1/4 inside; the fine
+    point between the wall and the first coarse node gets 1/3, a corner
+    1/9)."""
+    nx, ny = 15, 7
+    st = O.assemble_fv5(np.ones((ny, nx)))
+    p = O.interpolation(st).toarray()
+    ncx, ncy = 7, 3
+    for q in range(ncy):
+        for pp in range(ncx):
+            expect = np.outer(_hat(ny, ncy, q), _hat(nx, ncx, pp))
+            np.testing.assert_allclose(p[:, q * ncx + pp].reshape(ny, nx), expect,
+                                       rtol=0, atol=1e-15)
+
+
+def test_interpolation_layered_medium_flux_weights():
+    """k depending on x only: an interior x-edge point between coarse nodes
+    takes the series-conductance (flux-continuous) weights a_w / (a_w + a_e)
+    and a_e / (a_w + a_e); a y-edge point takes 1/2, 1/2; a cell-centre point
+    the product of the two."""
+    rng = np.random.default_rng(3)
+    nx, ny = 15, 15
+    kx = 10.0 ** rng.uniform(-3, 3, size=nx)
+    k = np.repeat(kx[None, :], ny, axis=0)
+    st = O.assemble_fv5(k)
+    p = O.interpolation(st).toarray()
+    ncx = 7
+    face = 2 * kx[:-1] * kx[1:] / (kx[:-1] + kx[1:])   # face between i and i+1
+    j0 = 7                                             # 0-based row 7 = coarse row 3
+    q = 3
+    for i0 in range(2, nx - 2, 2):                     # x-edge points, 0-based even
+        aw, ae = face[i0 - 1], face[i0]
+        # C - a_S - a_N cancels the y couplings: rounding is relative to C
+        tol = 8e-16 * st["C"][j0, i0] / (aw + ae)
+        row = p[j0 * nx + i0].reshape(-1)
+        pw, pe = i0 // 2 - 1, i0 // 2
+        assert abs(row[q * ncx + pw] - aw / (aw + ae)) < tol
+        assert abs(row[q * ncx + pe] - ae / (aw + ae)) < tol
+        # the cell-centre point one row below: product with 1/2 in y
+        rowc = p[(j0 - 1) * nx + i0]
+        assert abs(rowc[q * ncx + pw] - 0.5 * aw / (aw + ae)) < tol
+        assert abs(rowc[(q - 1) * ncx + pe] - 0.5 * ae / (aw + ae)) < tol
+    for i0 in range(1, nx - 1, 2):                     # y-edge points
+        row = p[(j0 - 1) * nx + i0]
+        assert abs(row[q * ncx + i0 // 2] - 0.5) < 1e-14
+        assert abs(row[(q - 1) * ncx + i0 // 2] - 0.5) < 1e-14
+
+
+def test_interpolation_rows_sum_to_one_where_row_sum_zero():
+    """Where A's row sum vanishes (interior), the weights of the interior
+    edge/centre points sum to 1: constants are interpolated exactly."""
+    rng = np.random.default_rng(5)
+    k = 10.0 ** rng.uniform(-2, 2, size=(31, 31))
+    st = O.assemble_fv5(k)
+    p = O.interpolation(st)
+    s = np.asarray(p.sum(axis=1)).reshape(31, 31)
+    np.testing.assert_allclose(s[2:-2, 2:-2], 1.0, atol=1e-14)
+
+
+def test_operator_induced_beats_bilinear_on_contrast():
+    """On a 10^8-contrast block field the two-grid error reduction with
+    operator-induced P is far better than with the constant-k (bilinear) P.
+    A wrong index or swapped weight in P destroys the gap."""
+    rng = np.random.default_rng(2)
+    n = 15
+    k = inputs.block_field(rng, n, n, 4, -4, 4)
+    st = O.assemble_fv5(k)
+
+    def rate(p):
+        a = O.stencil_to_csr(st)
+        lu = spla.splu((p.T @ a @ p).tocsc())
+        x = np.random.default_rng(0).standard_normal((n, n))
+        b = np.zeros((n, n))
+        for _ in range(30):
+            n0 = np.sqrt(x.ravel() @ (a @ x.ravel()))
+            O.relax(st, x, b, 2, O.RB_ORDER)
+            r = -(a @ x.ravel())
+            x += (p @ lu.solve(p.T @ r)).reshape(n, n)
+            O.relax(st, x, b, 1, O.RB_ORDER, reverse=True)
+            n1 = np.sqrt(x.ravel() @ (a @ x.ravel()))
+        return n1 / n0
+
+    good = rate(O.interpolation(st))
+    bilinear = rate(O.interpolation(O.assemble_fv5(np.ones((n, n)))))
+    assert good < 0.25
+    assert bilinear > 0.5
+
+
+# ---------------------------------------------------------------------------
+# Galerkin coarse operator (Section 2)
+# ---------------------------------------------------------------------------
+
+def _conv(s1, s2):
+    out = {}
+    for (a, b), v in s1.items():
+        for (c, d), w in s2.items():
+            out[(a + c, b + d)] = out.get((a + c, b + d), 0) + v * w
+    return out
+
+
+def _galerkin_symbol(alpha, pi):
+    """Interior (infinite-grid) Galerkin stencil of a constant stencil alpha
+    with a symmetric prolongation stencil pi: A_c(D) = (pi * alpha * pi)(2D),
+    computed with exact rationals."""
+    full = _conv(_conv(pi, alpha), pi)
+    return {(dx // 2, dy // 2): v for (dx, dy), v in full.items()
+            if dx % 2 == 0 and dy % 2 == 0 and v != 0}
+
+
+BILINEAR = {(dx, dy): F(2 - abs(dx), 2) * F(2 - abs(dy), 2)
+            for dx in (-1, 0, 1) for dy in (-1, 0, 1)}
+LAPLACE5 = {(0, 0): F(4), (1, 0): F(-1), (-1, 0): F(-1), (0, 1): F(-1), (0, -1): F(-1)}
+
+
+def _oracle_interior(st):
+    ny, nx = st["C"].shape
+    j, i = ny // 2, nx // 2
+    m = {(0, 0): st["C"][j, i]}
+    for d, (di, dj) in O.OFFSETS.items():
+        m[(di, dj)] = -st[d][j, i]
+    return m
+
+
+def test_rap_constant_k_closed_form_two_levels():
+    lev1 = _galerkin_symbol(LAPLACE5, BILINEAR)
+    # the familiar closed form [[-1/4,-1/2,-1/4],[-1/2,3,-1/2],[-1/4,-1/2,-1/4]]
+    assert lev1[(0, 0)] == 3 and lev1[(1, 0)] == F(-1, 2) and lev1[(1, 1)] == F(-1, 4)
+    lev2 = _galerkin_symbol(lev1, BILINEAR)
+    assert lev2[(0, 0)] == F(11, 4) and lev2[(1, 0)] == F(-3, 8) and lev2[(1, 1)] == F(-5, 16)
+    h = O.setup(np.ones((63, 63)))
+    for l, expect in ((h.nlevels - 2, lev1), (h.nlevels - 3, lev2)):
+        got = _oracle_interior(h.levels[l].st)
+        for key, v in expect.items():
+            assert got[key] == float(v), (l, key)
+    # interior P of the level-1 operator is bilinear again
+    p = O.interpolation(h.levels[h.nlevels - 2].st)
+    assert p[15 * 31 + 14, 7 * 15 + 6] == 0.5        # x-edge, row 15 col 14
+    assert p[14 * 31 + 14, 7 * 15 + 6] == 0.25       # centre
+
+
+def test_rap_is_symmetric_nine_point_with_zero_interior_row_sums():
+    rng = np.random.default_rng(7)
+    k = inputs.block_field(rng, 63, 63, 8, -4, 4)
+    h = O.setup(k)
+    for l in range(h.nlevels - 1):
+        st = h.levels[l].st
+        ny, nx = st["C"].shape
+        scale = np.abs(st["C"]).max()
+        # full symmetry of the stored 9-point planes
+        assert np.allclose(st["W"][:, 1:], st["E"][:, :-1], rtol=0, atol=1e-13 * scale)
+        assert np.allclose(st["S"][1:, :], st["N"][:-1, :], rtol=0, atol=1e-13 * scale)
+        assert np.allclose(st["SW"][1:, 1:], st["NE"][:-1, :-1], rtol=0, atol=1e-13 * scale)
+        assert np.allclose(st["NW"][:-1, 1:], st["SE"][1:, :-1], rtol=0, atol=1e-13 * scale)
+        rs = st["C"] - sum(st[d] for d in O.DIRS)
+        if ny > 4:
+            assert np.abs(rs[2:-2, 2:-2]).max() <= 1e-12 * scale
+        assert np.all(rs >= -1e-12 * scale)                 # diagonally dominant rows
+        a = O.stencil_to_csr(st).toarray()
+        assert np.linalg.eigvalsh(a).min() > 0
+
+
+def test_rap_pattern_check_rejects_wider_coupling():
+    import scipy.sparse as sp
+    a = sp.lil_matrix((9, 9))
+    a[0, 0] = 1.0
+    a[0, 2] = 1.0                                         # two cells apart in x
+    with pytest.raises(ValueError):
+        O.csr_to_stencil(a.tocsr(), 3, 3)
+
+
+def test_two_grid_galerkin_orthogonality():
+    """After an exact coarse-grid correction the restricted residual
+    vanishes: P^T (b - A (x + P A_c^{-1} P^T r)) = 0."""
+    rng = np.random.default_rng(9)
+    k = 10.0 ** rng.uniform(-2, 2, size=(31, 31))
+    st = O.assemble_fv5(k)
+    p = O.interpolation(st)
+    ac = O.stencil_to_csr(O.galerkin(st, p)).toarray()
+    a = O.stencil_to_csr(st)
+    b = rng.uniform(-1, 1, 31 * 31)
+    x = rng.uniform(-1, 1, 31 * 31)
+    r = b - a @ x
+    x2 = x + p @ np.linalg.solve(ac, p.T @ r)
+    rr = p.T @ (b - a @ x2)
+    assert np.abs(rr).max() <= 1e-12 * np.abs(p.T @ r).max()
+
+
+# ---------------------------------------------------------------------------
+# Coarsest direct solve
+# ---------------------------------------------------------------------------
+
+def test_cholesky_matches_lapack():
+    rng = np.random.default_rng(4)
+    h = O.setup(inputs.block_field(rng, 31, 31, 4, -4, 4))
+    a0 = O.stencil_to_csr(h.levels[0].st).toarray()
+    np.testing.assert_allclose(h.chol, np.linalg.cholesky(a0), rtol=1e-13, atol=1e-13 * np.abs(a0).max())
+    b = rng.uniform(-1, 1, a0.shape[0])
+    np.testing.assert_allclose(O.cholesky_solve(h.chol, b), np.linalg.solve(a0, b), rtol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# Smoother and V-cycle (Algorithm 1)
+# ---------------------------------------------------------------------------
+
+def _gs_loop(st, x, b, order, reverse=False):
+    """Pointwise Gauss-Seidel visiting colours in order and, inside a colour,
+    the points in reverse lexicographic order (any in-colour order must give
+    the same result because same-coloured points do not couple)."""
+    ny, nx = x.shape
+    seq = list(reversed(order)) if reverse else list(order)
+    for colour in seq:
+        pts = [(j, i) for j in range(ny) for i in range(nx) if (j % 2, i % 2) in colour]
+        for (j, i) in reversed(pts):
+            s = b[j, i]
+            for d, (di, dj) in O.OFFSETS.items():
+                jj, ii = j + dj, i + di
+                if 0 <= jj < ny and 0 <= ii < nx:
+                    s += st[d][j, i] * x[jj, ii]
+            x[j, i] = s / st["C"][j, i]
+
+
+@pytest.mark.parametrize("nine_point", [False, True])
+def test_multicolour_gs_matches_pointwise_loop(nine_point):
+    rng = np.random.default_rng(12)
+    k = 10.0 ** rng.uniform(-2, 2, size=(15, 15))
+    h = O.setup(k)
+    st = h.levels[-2].st if nine_point else h.levels[-1].st
+    order = O.colour_order(st)
+    assert order == (O.FOUR_ORDER if nine_point else O.RB_ORDER)
+    ny, nx = st["C"].shape
+    b = rng.uniform(-1, 1, (ny, nx))
+    x0 = rng.uniform(-1, 1, (ny, nx))
+    for reverse in (False, True):
+        x1 = x0.copy()
+        O.relax(st, x1, b, 1, order, reverse=reverse)
+        x2 = x0.copy()
+        _gs_loop(st, x2, b, order, reverse=reverse)
+        np.testing.assert_allclose(x1, x2, rtol=1e-14, atol=1e-15)
+
+
+def test_gs_is_gauss_seidel_not_jacobi():
+    """The second colour must see the first colour's new values: one red
+    sweep then one black sweep differs from a Jacobi update."""
+    rng = np.random.default_rng(1)
+    st = O.assemble_fv5(np.ones((7, 7)))
+    b = rng.uniform(-1, 1, (7, 7))
+    x = np.zeros((7, 7))
+    O.relax(st, x, b, 1, O.RB_ORDER)
+    red = np.add.outer(np.arange(7), np.arange(7)) % 2 == 0
+    np.testing.assert_allclose(x[red], b[red] / st["C"][red], rtol=1e-15)
+    assert not np.allclose(x[~red], b[~red] / st["C"][~red])
+
+
+@pytest.mark.parametrize("n", [7, 15, 31])
+def test_vcycle_converges_to_direct_solution(n):
+    rng = np.random.default_rng(100 + n)
+    k = 10.0 ** rng.uniform(-2, 2, size=(n, n))
+    b = rng.uniform(-1, 1, (n, n))
+    h = O.setup(k)
+    res = O.solve(h, b, tol=1e-13, max_cycles=400)
+    assert res.converged
+    xd = O.direct_solve(k, b)
+    assert np.abs(res.x - xd).max() <= 1e-10 * np.abs(xd).max()
+
+
+def test_rectangular_grid_solves():
+    rng = np.random.default_rng(21)
+    k = 10.0 ** rng.uniform(-1, 1, size=(15, 63))
+    b = rng.uniform(-1, 1, (15, 63))
+    h = O.setup(k)
+    assert [lv.shape for lv in h.levels] == [(3, 15), (7, 31), (15, 63)]
+    res = O.solve(h, b, tol=1e-12)
+    assert res.converged
+    assert np.abs(res.x - O.direct_solve(k, b)).max() <= 1e-9 * np.abs(res.x).max()
+
+
+def test_poisson_vcycle_rate_is_textbook():
+    """V(2,1) with red-black GS on the 5-point Poisson problem contracts the
+    residual by roughly an order of magnitude per cycle."""
+    pr = inputs.constant_problem(127)
+    h = O.setup(pr["k"])
+    res = O.solve(h, pr["b"], tol=1e-10)
+    assert res.converged and res.cycles <= 13
+    rates = np.array(res.history[2:]) / np.array(res.history[1:-1])
+    assert rates.max() < 0.2
+
+
+def test_residual_term_variant_converges_and_differs():
+    rng = np.random.default_rng(8)
+    k = 10.0 ** rng.uniform(-1, 1, size=(31, 31))
+    b = rng.uniform(-1, 1, (31, 31))
+    r0 = O.solve(O.setup(k), b, tol=1e-11)
+    r1 = O.solve(O.setup(k, interp_residual_term=True), b, tol=1e-11)
+    assert r0.converged and r1.converged
+    assert r0.history[1] != r1.history[1]
+    np.testing.assert_allclose(r0.x, r1.x, rtol=0, atol=1e-9 * np.abs(r0.x).max())
+
+
+def test_zero_rhs_and_bad_input():
+    h = O.setup(np.ones((7, 7)))
+    res = O.solve(h, np.zeros((7, 7)))
+    assert res.cycles == 0 and res.rel_resid == 0.0
+    with pytest.raises(ValueError):
+        O.setup(np.ones((8, 7)))
+    with pytest.raises(ValueError):
+        O.setup(-np.ones((7, 7)))
+    k = np.ones((7, 7))
+    k[3, 3] = np.nan
+    with pytest.raises(ValueError):
+        O.setup(k)
+
+
+# ---------------------------------------------------------------------------
+# Adjoint gradient
+# ---------------------------------------------------------------------------
+
+def test_adjoint_gradient_matches_central_differences():
+    rng = np.random.default_rng(13)
+    n = 8
+    theta = rng.normal(0.0, 1.0, (n, n))
+    b = rng.uniform(-1, 1, (n, n))
+    u_obs = O.direct_solve(np.exp(theta + 0.1 * rng.normal(size=(n, n))), b)
+    g, _, _ = O.adjoint_gradient(theta, b, u_obs)
+    eps = 1e-6
+    fd = np.zeros_like(theta)
+    for j in range(n):
+        for i in range(n):
+            tp = theta.copy()
+            tm = theta.copy()
+            tp[j, i] += eps
+            tm[j, i] -= eps
+            fd[j, i] = (O.loss(tp, b, u_obs) - O.loss(tm, b, u_obs)) / (2 * eps)
+    assert np.abs(fd - g).max() <= 1e-6 * np.abs(g).max()
+
+
+def test_compliance_identity():
+    """For L = b^T u the adjoint is u itself, so dL/dtheta_c =
+    -k_c sum_f da_f/dk_c (u_c - u_n)^2 (- 2 k_c u_c^2 per boundary face): all
+    entries are <= 0; check against central differences."""
+    rng = np.random.default_rng(14)
+    n = 6
+    theta = rng.normal(0.0, 1.0, (n, n))
+    b = rng.uniform(-1, 1, (n, n))
+    u = O.direct_solve(np.exp(theta), b)
+    g = O.assembly_vjp(np.exp(theta), u, u)
+    assert np.all(g <= 0)
+    eps = 1e-6
+    for (j, i) in [(0, 0), (2, 3), (5, 1), (3, 3)]:
+        tp = theta.copy()
+        tm = theta.copy()
+        tp[j, i] += eps
+        tm[j, i] -= eps
+        fd = (b.ravel() @ O.direct_solve(np.exp(tp), b).ravel()
+              - b.ravel() @ O.direct_solve(np.exp(tm), b).ravel()) / (2 * eps)
+        assert abs(fd - g[j, i]) <= 1e-6 * np.abs(g).max()
