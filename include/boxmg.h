@@ -1,0 +1,212 @@
+/*
+ * boxmg.h -- C ABI of the GB300 BoxMG library (2D heterogeneous diffusion).
+ *
+ * Method: Reisner, Olson, Moulton, "Scaling Structured Multigrid to 500K+
+ * Cores through Coarse-Grid Redistribution".  The library implements
+ *   - the 5-point cell-centred finite-volume operator of Eq. (diffusion) with
+ *     the Dirichlet condition of Eq. (diffusion_bc) (Section 5);
+ *   - BoxMG setup (Section 2): operator-induced interpolation P_l, the
+ *     Galerkin coarse operators A_{l-1} = P_l^T A_l P_l, and the Cholesky
+ *     factor of the coarsest operator (Section 3, coarse-solve cost model);
+ *   - the V-cycle of Algorithm 1 with multicolour Gauss-Seidel, residual,
+ *     restriction R = P^T and interpolate-and-correct;
+ *   - the coarse-grid redistribution of Section 2.2 / Algorithm 2 re-read for
+ *     one GPU: every level below a threshold runs inside one persistent
+ *     thread block instead of one kernel launch per operation; a cost model in
+ *     the spirit of Section 3 (Eq. (Vmodel)) with measured parameters picks
+ *     the threshold.
+ *
+ * Conventions (all entry points):
+ *   - Grid arrays passed in or out are dense, row-major, shape (ny, nx):
+ *     element (i, j), 0 <= i < nx (x, fast), 0 <= j < ny, at offset j*nx + i.
+ *   - "_dev" pointers are CUDA device pointers owned by the caller; "_host"
+ *     pointers are host memory owned by the caller.  The library never frees
+ *     caller memory.  Coefficients are copied into the hierarchy, so the
+ *     caller may free or reuse k after bmg_setup returns (stream-ordered).
+ *   - Every call is ordered on the given stream (NULL = legacy default
+ *     stream).  A call that returns data to a host pointer synchronises the
+ *     stream before returning.
+ *   - Return value: BMG_OK (0) or a negative BMG_E* code; no call aborts, and
+ *     no call falls back to the CPU.  bmg_strerror() gives a message.
+ *   - Sizes: nx and ny must be 2^m - 1 with m >= 2.  Levels are halved,
+ *     n -> (n - 1) / 2, until the smaller side is 3; the coarsest level must
+ *     have at most BMG_MAX_COARSEST unknowns.
+ */
+#ifndef BOXMG_H
+#define BOXMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so the header needs no CUDA. */
+typedef struct CUstream_st *bmg_stream_t;
+
+typedef struct bmg_hierarchy bmg_hierarchy; /* opaque, library-owned */
+
+enum {
+  BMG_OK = 0,
+  BMG_EINVAL = -1,   /* bad argument: size, NaN/Inf or non-positive k, level */
+  BMG_ENOMEM = -2,   /* device allocation failed                            */
+  BMG_ECUDA = -3,    /* a CUDA runtime call failed                          */
+  BMG_ENOCONV = -4,  /* max_cycles reached before the tolerance             */
+  BMG_ENAN = -5,     /* the residual norm became NaN or Inf                 */
+  BMG_ETIMEOUT = -6  /* a bounded device-side wait gave up                  */
+};
+
+enum { BMG_FP64 = 0, BMG_FP32_REFINE = 1 };
+
+#define BMG_MAX_COARSEST 1024
+
+typedef struct {
+  int nu1;                  /* pre-smoothing sweeps (Algorithm 1), default 2  */
+  int nu2;                  /* post-smoothing sweeps, default 1               */
+  int precision;            /* BMG_FP64 or BMG_FP32_REFINE                    */
+  int interp_residual_term; /* 1: add r/C at non-coarse points when
+                               interpolating (Section 3, interpolation
+                               equations); 0: x += P x_c (Algorithm 1)       */
+  int coarse_threshold;     /* levels l < threshold run inside the persistent
+                               coarse kernel (1 <= threshold <= L); -1: chosen
+                               by the cost model                              */
+  int max_cycles;           /* cap on V-cycles (or refinement steps), 200    */
+} bmg_options;
+
+typedef struct {
+  int cycles;        /* V-cycles run (FP32_REFINE: refinement steps)          */
+  int threshold;     /* level threshold used by the schedule                  */
+  double rel_resid;  /* final ||b - A x||_2 / ||b||_2, computed in FP64       */
+  double setup_ms;   /* wall time of bmg_setup                                 */
+  double solve_ms;   /* wall time of the last bmg_solve                        */
+} bmg_info;
+
+/* Fill *opt with the defaults above. */
+void bmg_default_options(bmg_options *opt);
+
+/* Message for a BMG_* code (static storage). */
+const char *bmg_strerror(int code);
+
+/* BoxMG setup (Section 2; Section 5 discretisation).
+ * k_dev: cell coefficients k > 0, dense (ny, nx) float64, device.
+ * Assembles the fine 5-point operator (harmonic face means, 2k on Dirichlet
+ * faces, scaled by h^2), builds P_l and A_{l-1} = P_l^T A_l P_l on every
+ * level, factors A_0, and fixes the level schedule.  With precision
+ * BMG_FP32_REFINE the coarse hierarchy (P and RAP) is built in FP32 from an
+ * FP32 copy of the fine operator; the FP64 fine operator is kept for the
+ * outer residual.  On success *out owns all device memory of the hierarchy.
+ * Errors: BMG_EINVAL (sizes, NaN/Inf or k <= 0 found on the device, options),
+ * BMG_ENOMEM, BMG_ECUDA.  *out is NULL on error. */
+int bmg_setup(const double *k_dev, int nx, int ny, const bmg_options *opt,
+              bmg_stream_t stream, bmg_hierarchy **out);
+
+/* Solve A x = b with V-cycles (Algorithm 1) until
+ * ||b - A x||_2 / ||b||_2 <= tol (checked before the first cycle and after
+ * every cycle) or max_cycles cycles ran.
+ * b_dev: dense (ny, nx) float64, device.  x_dev: dense (ny, nx) float64,
+ * device; on entry the initial guess, on exit the solution.  info may be
+ * NULL.  Synchronises the stream (the cycle count and residual return to the
+ * host).  Errors: BMG_ENOCONV (x holds the last iterate), BMG_ENAN,
+ * BMG_ETIMEOUT, BMG_ECUDA, BMG_EINVAL (tol <= 0 or NULL pointers). */
+int bmg_solve(bmg_hierarchy *h, const double *b_dev, double *x_dev, double tol,
+              bmg_info *info, bmg_stream_t stream);
+
+/* End-to-end convenience: copy k and b from pinned (or pageable) host memory,
+ * set up, solve, and copy x back, all on `stream`.  Equivalent to
+ * bmg_setup + bmg_solve + bmg_destroy with device buffers the call allocates
+ * and frees.  x_host holds the initial guess on entry. */
+int bmg_solve_host(const double *k_host, const double *b_host, double *x_host,
+                   int nx, int ny, const bmg_options *opt, double tol,
+                   bmg_info *info, bmg_stream_t stream);
+
+/* Release every device resource of the hierarchy (NULL is allowed). */
+void bmg_destroy(bmg_hierarchy *h);
+
+/* ---- Introspection (parity checks against the CPU oracle) ---------------- */
+
+/* Number of levels L; level L-1 is the finest, level 0 the coarsest. */
+int bmg_num_levels(const bmg_hierarchy *h, int *nlevels);
+
+/* Grid size of a level. */
+int bmg_level_shape(const bmg_hierarchy *h, int level, int *nx, int *ny);
+
+/* A_level as five dense (ny, nx) float64 planes, concatenated, in host
+ * memory: C, W, S, SW, NW, where W(i,j) = -A[(i,j),(i-1,j)],
+ * S(i,j) = -A[(i,j),(i,j-1)], SW(i,j) = -A[(i,j),(i-1,j-1)],
+ * NW(i,j) = -A[(i,j),(i-1,j+1)]; E, N, NE, SE follow by symmetry.  The
+ * finest level has SW = NW = 0.  FP32 hierarchies are widened to float64.
+ * host_out holds 5*nx*ny doubles. */
+int bmg_level_stencil(const bmg_hierarchy *h, int level, double *host_out);
+
+/* Interpolation weights of P_level (coarse level-1 -> level), 1 <= level,
+ * as eight dense (ncy+1, ncx+1) float64 planes in host memory, ncx, ncy the
+ * coarse sizes.  Plane entry (I, J), 0 <= I <= ncx, 0 <= J <= ncy, with
+ * 1-based fine indices:
+ *   0 xw, 1 xe : x-edge point (2I+1, 2J) -> coarse (I, J), (I+1, J)
+ *   2 ys, 3 yn : y-edge point (2I, 2J+1) -> coarse (I, J), (I, J+1)
+ *   4 csw, 5 cse, 6 cnw, 7 cne : centre point (2I+1, 2J+1) -> coarse
+ *                (I, J), (I+1, J), (I, J+1), (I+1, J+1)
+ * Entries that name no fine point (xw at J = 0, ys at I = 0) are 0.
+ * host_out holds 8*(ncx+1)*(ncy+1) doubles. */
+int bmg_level_interp(const bmg_hierarchy *h, int level, double *host_out);
+
+/* Lower-triangular Cholesky factor of the coarsest operator A_0, dense
+ * N0 x N0 row-major float64 in host memory (N0 = nx0 * ny0, unknown index
+ * j*nx0 + i). */
+int bmg_coarse_factor(const bmg_hierarchy *h, double *host_out, int n0_capacity);
+
+/* ---- Single operations on one level (for per-kernel parity and timing) -- */
+/* Each takes dense (ny, nx) float64 device arrays of that level and runs the
+ * same device code as the V-cycle on them.  FP64 hierarchies only. */
+
+/* nu multicolour Gauss-Seidel sweeps on level `level`, in place on x_dev
+ * (Section 3 smoothing; colours forward, or reversed if reverse != 0). */
+int bmg_op_relax(bmg_hierarchy *h, int level, double *x_dev, const double *b_dev,
+                 int nu, int reverse, bmg_stream_t stream);
+
+/* r = b - A_level x (Algorithm 1). */
+int bmg_op_residual(bmg_hierarchy *h, int level, const double *x_dev,
+                    const double *b_dev, double *r_dev, bmg_stream_t stream);
+
+/* bc = P_level^T r  (r on level `level`, bc on level-1; Algorithm 1). */
+int bmg_op_restrict(bmg_hierarchy *h, int level, const double *r_dev,
+                    double *bc_dev, bmg_stream_t stream);
+
+/* x += P_level xc  (xc on level-1, x on level `level`; Algorithm 1). */
+int bmg_op_interp(bmg_hierarchy *h, int level, const double *xc_dev,
+                  double *x_dev, bmg_stream_t stream);
+
+/* ---- Adjoint gradient (extension: differentiation) ---------------------- */
+
+/* dtheta_c = -d(lam^T A(theta) u)/d theta_c for k = exp(theta), the
+ * backward of the Section 5 assembly contracted with the state u and the
+ * adjoint lam (both dense (ny, nx) float64, device):
+ *   dtheta_c = -k_c [ sum_{faces f of c} dA_f/dk_c (u_c - u_n)(lam_c - lam_n)
+ *                     + sum_{boundary faces} 2 u_c lam_c ],
+ *   dA_f/dk_c = 2 k_n^2 / (k_c + k_n)^2.
+ * With lam solving A lam = u - u_obs this is dL/dtheta for
+ * L = 0.5 ||u - u_obs||^2.  Uses the k given to bmg_setup. */
+int bmg_assemble_backward(bmg_hierarchy *h, const double *u_dev,
+                          const double *lam_dev, double *dtheta_dev,
+                          bmg_stream_t stream);
+
+/* ---- Observability ------------------------------------------------------ */
+
+/* Total kernel launches this library has issued in this process. */
+long long bmg_kernel_launches(void);
+
+/* Kernel classes that can be timed live with CUDA events. */
+enum { BMG_PROF_NONE = 0, BMG_PROF_FINE_SMOOTH = 1, BMG_PROF_FINE_RESID = 2,
+       BMG_PROF_FINE_INTERP = 3, BMG_PROF_COARSE = 4 };
+
+/* Start bracketing every launch of kernel class `which` (BMG_PROF_*) with a
+ * pair of CUDA events on its stream (up to 65536 launches); resets the
+ * record.  BMG_PROF_NONE stops recording. */
+int bmg_profile_set(int which);
+
+/* Synchronise the recorded events and return the number of bracketed
+ * launches and their summed device time in milliseconds. */
+int bmg_profile_read(int *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BOXMG_H */

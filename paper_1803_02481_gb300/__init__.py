@@ -1,0 +1,268 @@
+"""GB300 BoxMG: Python binding of the C ABI in include/boxmg.h.
+
+Argument marshalling only: every step of setup and solve runs in the CUDA
+library ``libboxmg.so`` (built in-tree by ``build.py``).  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if the library is not
+built, or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "BMG_OK", "BMG_EINVAL", "BMG_ENOMEM", "BMG_ECUDA", "BMG_ENOCONV", "BMG_ENAN", "BMG_ETIMEOUT",
+    "BMG_FP64", "BMG_FP32_REFINE", "BoxMGError", "Options", "Info", "lib", "library_path",
+    "default_options", "setup", "Hierarchy", "solve_host", "EXPORTED",
+]
+
+BMG_OK, BMG_EINVAL, BMG_ENOMEM, BMG_ECUDA, BMG_ENOCONV, BMG_ENAN, BMG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+BMG_FP64, BMG_FP32_REFINE = 0, 1
+MAX_COARSEST = 1024
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("precision", ctypes.c_int),
+                ("interp_residual_term", ctypes.c_int), ("coarse_threshold", ctypes.c_int),
+                ("max_cycles", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("threshold", ctypes.c_int), ("rel_resid", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BoxMGError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().bmg_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_HP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes); every symbol include/boxmg.h declares
+EXPORTED = {
+    "bmg_default_options": (None, [ctypes.POINTER(Options)]),
+    "bmg_strerror": (ctypes.c_char_p, [_i]),
+    "bmg_setup": (_i, [_vp, _i, _i, ctypes.POINTER(Options), _vp, _HP]),
+    "bmg_solve": (_i, [_vp, _vp, _vp, _d, ctypes.POINTER(Info), _vp]),
+    "bmg_solve_host": (_i, [_vp, _vp, _vp, _i, _i, ctypes.POINTER(Options), _d,
+                            ctypes.POINTER(Info), _vp]),
+    "bmg_destroy": (None, [_vp]),
+    "bmg_num_levels": (_i, [_vp, ctypes.POINTER(_i)]),
+    "bmg_level_shape": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "bmg_level_stencil": (_i, [_vp, _i, _vp]),
+    "bmg_level_interp": (_i, [_vp, _i, _vp]),
+    "bmg_coarse_factor": (_i, [_vp, _vp, _i]),
+    "bmg_op_relax": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp]),
+    "bmg_op_residual": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "bmg_op_restrict": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "bmg_op_interp": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "bmg_assemble_backward": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "bmg_kernel_launches": (ctypes.c_longlong, []),
+    "bmg_profile_set": (_i, [_i]),
+    "bmg_profile_read": (_i, [ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+}
+
+BMG_PROF_NONE, BMG_PROF_FINE_SMOOTH, BMG_PROF_FINE_RESID, BMG_PROF_FINE_INTERP, BMG_PROF_COARSE = 0, 1, 2, 3, 4
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(lib().bmg_kernel_launches())
+
+
+def profile_set(which: int):
+    _check(lib().bmg_profile_set(int(which)), "bmg_profile_set")
+
+
+def profile_read():
+    """(launches, total_ms) of the bracketed kernel class since profile_set."""
+    n, ms = ctypes.c_int(), ctypes.c_double()
+    _check(lib().bmg_profile_read(ctypes.byref(n), ctypes.byref(ms)), "bmg_profile_read")
+    return n.value, ms.value
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; call paper_1803_02481_gb300.build.build()")
+        cdll = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTED.items():
+            fn = getattr(cdll, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = cdll
+    return _LIB
+
+
+def _check(code: int, where: str, ok=(BMG_OK,)):
+    if code not in ok:
+        raise BoxMGError(code, where)
+    return code
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().bmg_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Hierarchy:
+    """A BoxMG hierarchy living on the GPU (wraps ``bmg_hierarchy*``)."""
+
+    def __init__(self, handle: ctypes.c_void_p, nx: int, ny: int, options: Options):
+        self._h = handle
+        self.nx, self.ny = nx, ny
+        self.options = options
+
+    # -- lifetime -----------------------------------------------------------
+    def destroy(self):
+        if self._h:
+            lib().bmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    # -- solve ----------------------------------------------------------------
+    def solve(self, b, x=None, tol=1e-10, stream=None, allow_noconv=False):
+        """Solve A x = b (b, x: (ny, nx) float64 CUDA tensors; x is the initial
+        guess, zero if None, overwritten with the solution).  Returns
+        (x, Info)."""
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        info = Info()
+        ok = (BMG_OK, BMG_ENOCONV) if allow_noconv else (BMG_OK,)
+        _check(lib().bmg_solve(self._h, _dev(b, "b"), _dev(x, "x"), float(tol), ctypes.byref(info),
+                               _stream(stream)), "bmg_solve", ok)
+        return x, info
+
+    # -- introspection ----------------------------------------------------------
+    @property
+    def nlevels(self) -> int:
+        n = ctypes.c_int()
+        _check(lib().bmg_num_levels(self._h, ctypes.byref(n)), "bmg_num_levels")
+        return n.value
+
+    def level_shape(self, level: int):
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        _check(lib().bmg_level_shape(self._h, level, ctypes.byref(nx), ctypes.byref(ny)), "bmg_level_shape")
+        return nx.value, ny.value
+
+    def level_stencil(self, level: int) -> dict:
+        nx, ny = self.level_shape(level)
+        out = np.zeros((5, ny, nx))
+        _check(lib().bmg_level_stencil(self._h, level, out.ctypes.data_as(ctypes.c_void_p)),
+               "bmg_level_stencil")
+        return dict(zip(("C", "W", "S", "SW", "NW"), out))
+
+    def level_interp(self, level: int) -> dict:
+        ncx, ncy = self.level_shape(level - 1)
+        out = np.zeros((8, ncy + 1, ncx + 1))
+        _check(lib().bmg_level_interp(self._h, level, out.ctypes.data_as(ctypes.c_void_p)),
+               "bmg_level_interp")
+        return dict(zip(("XW", "XE", "YS", "YN", "CSW", "CSE", "CNW", "CNE"), out))
+
+    def coarse_factor(self) -> np.ndarray:
+        nx, ny = self.level_shape(0)
+        n0 = nx * ny
+        out = np.zeros((n0, n0))
+        _check(lib().bmg_coarse_factor(self._h, out.ctypes.data_as(ctypes.c_void_p), n0),
+               "bmg_coarse_factor")
+        return out
+
+    # -- single operations --------------------------------------------------------
+    def op_relax(self, level, x, b, nu=1, reverse=False, stream=None):
+        _check(lib().bmg_op_relax(self._h, level, _dev(x, "x"), _dev(b, "b"), int(nu), int(bool(reverse)),
+                                  _stream(stream)), "bmg_op_relax")
+        return x
+
+    def op_residual(self, level, x, b, r, stream=None):
+        _check(lib().bmg_op_residual(self._h, level, _dev(x, "x"), _dev(b, "b"), _dev(r, "r"),
+                                     _stream(stream)), "bmg_op_residual")
+        return r
+
+    def op_restrict(self, level, r, bc, stream=None):
+        _check(lib().bmg_op_restrict(self._h, level, _dev(r, "r"), _dev(bc, "bc"), _stream(stream)),
+               "bmg_op_restrict")
+        return bc
+
+    def op_interp(self, level, xc, x, stream=None):
+        _check(lib().bmg_op_interp(self._h, level, _dev(xc, "xc"), _dev(x, "x"), _stream(stream)),
+               "bmg_op_interp")
+        return x
+
+    def assemble_backward(self, u, lam, dtheta, stream=None):
+        _check(lib().bmg_assemble_backward(self._h, _dev(u, "u"), _dev(lam, "lam"), _dev(dtheta, "dtheta"),
+                                           _stream(stream)), "bmg_assemble_backward")
+        return dtheta
+
+
+def setup(k, options: Options | None = None, stream=None) -> Hierarchy:
+    """BoxMG setup from cell coefficients k ((ny, nx) float64 CUDA tensor)."""
+    if options is None:
+        options = default_options()
+    ny, nx = k.shape
+    h = ctypes.c_void_p()
+    _check(lib().bmg_setup(_dev(k, "k"), nx, ny, ctypes.byref(options), _stream(stream), ctypes.byref(h)),
+           "bmg_setup")
+    return Hierarchy(h, nx, ny, options)
+
+
+def solve_host(k: np.ndarray, b: np.ndarray, x: np.ndarray, options: Options | None = None,
+               tol: float = 1e-10, stream=None, allow_noconv=False) -> Info:
+    """End-to-end solve from host arrays (copies, setup, solve, copy back in
+    one C call).  x holds the initial guess and receives the solution."""
+    for a, n in ((k, "k"), (b, "b"), (x, "x")):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise TypeError(f"{n} must be a C-contiguous float64 numpy array")
+    if options is None:
+        options = default_options()
+    ny, nx = k.shape
+    info = Info()
+    ok = (BMG_OK, BMG_ENOCONV) if allow_noconv else (BMG_OK,)
+    _check(lib().bmg_solve_host(k.ctypes.data_as(_vp), b.ctypes.data_as(_vp), x.ctypes.data_as(_vp), nx, ny,
+                                ctypes.byref(options), float(tol), ctypes.byref(info), _stream(stream)),
+           "bmg_solve_host", ok)
+    return info

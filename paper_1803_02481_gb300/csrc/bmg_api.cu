@@ -1,0 +1,581 @@
+// Host side of the GB300 BoxMG library: the hierarchy (one device arena per
+// setup), the setup sequence of Section 2, the V-cycle launch schedule of
+// Algorithm 1 with the coarse levels below the threshold run by one
+// persistent kernel (the single-GPU reading of Algorithm 2), the solve loops
+// (plain FP64, and FP32 V-cycles inside FP64 iterative refinement), and the
+// extern "C" entry points declared in include/boxmg.h.
+#include "bmg_internal.h"
+#include "bmg_schedule.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+namespace bmg {
+
+namespace {
+
+#define BMG_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return BMG_ECUDA;            \
+  } while (0)
+
+bool valid_side(int n) { return n >= 3 && ((n + 1) & n) == 0; }
+
+double now_ms() {
+  using clk = std::chrono::steady_clock;
+  return std::chrono::duration<double, std::milli>(clk::now().time_since_epoch()).count();
+}
+
+// Carves planes out of one allocation.  First pass (base == nullptr) only
+// counts bytes.
+struct Carver {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* plane(const Geom& g) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) + base_shift<T>() : nullptr;
+    off += g.elems * sizeof(T);
+    return p;
+  }
+  template <typename T>
+  T* raw(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+template <typename T>
+void carve_levels(Carver& cv, const std::vector<Geom>& geo, int first, std::vector<LevelV<T>>& lv,
+                  int finest_index) {
+  // lv[i] corresponds to hierarchy level first + i.
+  const int n = int(geo.size());
+  lv.assign(n, LevelV<T>{});
+  for (int i = 0; i < n; ++i) {
+    const int l = first + i;
+    const Geom& g = geo[i];
+    LevelV<T>& L = lv[i];
+    L.nx = g.nx;
+    L.ny = g.ny;
+    L.pitch = g.pitch;
+    L.C = cv.plane<T>(g);
+    L.iC = cv.plane<T>(g);
+    L.W = cv.plane<T>(g);
+    L.S = cv.plane<T>(g);
+    const bool nine = l != finest_index;
+    L.SW = nine ? cv.plane<T>(g) : nullptr;
+    L.NW = nine ? cv.plane<T>(g) : nullptr;
+    L.x = cv.plane<T>(g);
+    L.b = cv.plane<T>(g);
+    L.r = cv.plane<T>(g);
+    if (l >= 1 && i >= 1) {
+      const Geom& gc = geo[i - 1];
+      for (int k = 0; k < NPW; ++k) L.P[k] = cv.plane<T>(gc);
+      L.cpitch = gc.pitch;
+    } else {
+      for (int k = 0; k < NPW; ++k) L.P[k] = nullptr;
+      L.cpitch = 0;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Setup
+// ---------------------------------------------------------------------------
+
+static int check_derr(Hierarchy* h, cudaStream_t s) {
+  BMG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaStreamSynchronize(s));
+  if (h->sc_host->err & (DEV_BADK | DEV_NOTSPD | DEV_BADDEN)) return BMG_EINVAL;
+  return BMG_OK;
+}
+
+template <typename T>
+static int build_coarse(Hierarchy* h, std::vector<LevelV<T>>& lv, cudaStream_t s) {
+  int* derr = &h->sc->err;
+  const int L = h->L;
+  for (int l = L - 1; l >= 1; --l) {
+    const bool nine = l != L - 1;
+    if (launch_interp_weights<T>(lv[l], nine, derr, s)) return BMG_ECUDA;
+    if (launch_rap<T>(lv[l], nine, lv[l - 1], s)) return BMG_ECUDA;
+  }
+  return BMG_OK;
+}
+
+static void free_hierarchy(Hierarchy* h) {
+  if (!h) return;
+  if (h->arena) cudaFree(h->arena);
+  if (h->sc_host) cudaFreeHost(h->sc_host);
+  delete h;
+}
+
+static int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in,
+                      cudaStream_t s, Hierarchy** out) {
+  *out = nullptr;
+  if (!k || !valid_side(nx) || !valid_side(ny)) return BMG_EINVAL;
+  bmg_options opt;
+  bmg_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.nu1 < 0 || opt.nu2 < 0 || opt.nu1 + opt.nu2 < 1 || opt.max_cycles < 0) return BMG_EINVAL;
+  if (opt.precision != BMG_FP64 && opt.precision != BMG_FP32_REFINE) return BMG_EINVAL;
+  const double t0 = now_ms();
+
+  Hierarchy* h = new (std::nothrow) Hierarchy();
+  if (!h) return BMG_ENOMEM;
+  h->nx = nx;
+  h->ny = ny;
+  h->opt = opt;
+  // level sizes, finest last
+  std::vector<std::pair<int, int>> sz;
+  {
+    int a = nx, b = ny;
+    sz.push_back({a, b});
+    while (std::min(a, b) > 3) {
+      a = (a - 1) / 2;
+      b = (b - 1) / 2;
+      sz.push_back({a, b});
+    }
+  }
+  h->L = int(sz.size());
+  const int L = h->L;
+  h->n0 = sz.back().first * sz.back().second;
+  if (h->n0 > BMG_MAX_COARSEST) {
+    delete h;
+    return BMG_EINVAL;
+  }
+  if (opt.coarse_threshold != -1 && (opt.coarse_threshold < 1 || opt.coarse_threshold > L)) {
+    delete h;
+    return BMG_EINVAL;
+  }
+  const bool fp32 = opt.precision == BMG_FP32_REFINE;
+  for (int l = 0; l < L; ++l) {
+    const auto& q = sz[L - 1 - l];
+    h->geo64.push_back(make_geom<double>(q.first, q.second));
+    h->geo32.push_back(make_geom<float>(q.first, q.second));
+  }
+  h->npartials = 2 * 152;
+
+  // Two passes: size, then carve.
+  std::vector<Geom> g64 = fp32 ? std::vector<Geom>{h->geo64.back()} : h->geo64;
+  Carver cv;
+  for (int pass = 0; pass < 2; ++pass) {
+    cv.off = 0;
+    carve_levels<double>(cv, g64, fp32 ? L - 1 : 0, h->d, L - 1);
+    if (fp32) carve_levels<float>(cv, h->geo32, 0, h->f, L - 1);
+    h->kcopy = cv.raw<double>(size_t(nx) * ny);
+    h->chol = cv.raw<double>(size_t(h->n0) * h->n0);
+    h->chol_idiag = cv.raw<double>(h->n0);
+    h->partials = cv.raw<double>(h->npartials);
+    h->sc = cv.raw<Scalars>(1);
+    h->dlev64 = cv.raw<LevelV<double>>(L);
+    h->dlev32 = cv.raw<LevelV<float>>(L);
+    if (pass == 0) {
+      h->arena_bytes = cv.off;
+      if (cudaMalloc(&h->arena, h->arena_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return BMG_ENOMEM;
+      }
+      cv.base = static_cast<char*>(h->arena);
+    }
+  }
+  if (cudaMallocHost(&h->sc_host, sizeof(Scalars)) != cudaSuccess) {
+    free_hierarchy(h);
+    return BMG_ENOMEM;
+  }
+  int rc = BMG_OK;
+  auto fail = [&](int code) {
+    free_hierarchy(h);
+    return code;
+  };
+  if (cudaMemsetAsync(h->arena, 0, h->arena_bytes, s) != cudaSuccess) return fail(BMG_ECUDA);
+
+  // Assembly (Section 5), then P and RAP level by level (Section 2).
+  int* derr = &h->sc->err;
+  LevelV<double>& fine64 = h->d.back();
+  if (launch_assemble<double>(k, nx, ny, fine64, h->kcopy, derr, s)) return fail(BMG_ECUDA);
+  if (!fp32) {
+    if ((rc = build_coarse<double>(h, h->d, s))) return fail(rc);
+    if (launch_coarse_factor(h, &h->d[0], nullptr, s)) return fail(BMG_ECUDA);
+  } else {
+    if (launch_downcast_fine(fine64, h->f.back(), s)) return fail(BMG_ECUDA);
+    if ((rc = build_coarse<float>(h, h->f, s))) return fail(rc);
+    if (launch_coarse_factor(h, nullptr, &h->f[0], s)) return fail(BMG_ECUDA);
+  }
+  // level views for the persistent kernel
+  if (!fp32) {
+    if (cudaMemcpyAsync(h->dlev64, h->d.data(), sizeof(LevelV<double>) * L,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return fail(BMG_ECUDA);
+  } else {
+    if (cudaMemcpyAsync(h->dlev32, h->f.data(), sizeof(LevelV<float>) * L,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return fail(BMG_ECUDA);
+  }
+  if ((rc = check_derr(h, s))) return fail(rc);
+
+  // Level schedule: which levels leave the full-grid launches.
+  h->threshold = opt.coarse_threshold > 0 ? opt.coarse_threshold : choose_threshold(h);
+  h->setup_ms = now_ms() - t0;
+  *out = h;
+  return BMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle schedule (Algorithm 1)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* dlev, int thr,
+                    cudaStream_t s) {
+  const int L = h->L;
+  const int nu1 = h->opt.nu1, nu2 = h->opt.nu2;
+  const bool rc = h->opt.interp_residual_term != 0;
+  for (int l = L - 1; l >= thr; --l) {
+    const bool nine = l != L - 1;
+    launch_relax<T>(lv[l], nine, nu1, false, s);
+    launch_residual<T>(lv[l], nine, lv[l].x, lv[l].b, lv[l].r, s);
+    launch_restrict<T>(lv[l], lv[l].r, lv[l - 1], true, s);
+  }
+  launch_coarse_cycle<T>(h, dlev, thr, s);
+  for (int l = thr; l < L; ++l) {
+    const bool nine = l != L - 1;
+    launch_interp<T>(lv[l], lv[l - 1].x, rc, s);
+    launch_relax<T>(lv[l], nine, nu2, true, s);
+  }
+}
+
+template void enqueue_vcycle<double>(Hierarchy*, std::vector<LevelV<double>>&,
+                                     const LevelV<double>*, int, cudaStream_t);
+template void enqueue_vcycle<float>(Hierarchy*, std::vector<LevelV<float>>&, const LevelV<float>*,
+                                    int, cudaStream_t);
+
+static int read_scalars(Hierarchy* h, cudaStream_t s) {
+  BMG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaStreamSynchronize(s));
+  return BMG_OK;
+}
+
+static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_info* info,
+                      cudaStream_t s) {
+  if (!h || !b || !x || !(tol > 0.0)) return BMG_EINVAL;
+  const double t0 = now_ms();
+  const int L = h->L;
+  LevelV<double>& F = h->d.back();
+  launch_pack<double>(b, F.b, h->nx, h->ny, F.pitch, s);
+  launch_pack<double>(x, F.x, h->nx, h->ny, F.pitch, s);
+  Scalars init{};
+  init.tol = tol;
+  init.max_cycles = h->opt.max_cycles;
+  *h->sc_host = init;
+  BMG_CUDA(cudaMemcpyAsync(h->sc, h->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
+  launch_fine_norm(h, nullptr, F.b, 0, tol, s);
+  const bool fp32 = h->opt.precision == BMG_FP32_REFINE;
+  int rc = BMG_OK;
+  if (!fp32) {
+    launch_fine_norm(h, F.x, F.b, 1, tol, s);
+    if ((rc = read_scalars(h, s))) return rc;
+    if (h->sc_host->bnorm2 == 0.0) {
+      BMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * size_t(h->nx) * h->ny, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+      if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0};
+      return BMG_OK;
+    }
+    while (h->sc_host->go) {
+      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+      launch_fine_norm(h, F.x, F.b, 1, tol, s);
+      if ((rc = read_scalars(h, s))) return rc;
+    }
+  } else {
+    if ((rc = read_scalars(h, s))) return rc;
+    if (h->sc_host->bnorm2 == 0.0) {
+      BMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * size_t(h->nx) * h->ny, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+      if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0};
+      return BMG_OK;
+    }
+    for (;;) {
+      launch_refine_residual(h, tol, s);
+      if ((rc = read_scalars(h, s))) return rc;
+      if (!h->sc_host->go) break;
+      enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s);
+      launch_refine_update(h, s);
+    }
+  }
+  (void)L;
+  launch_unpack<double>(F.x, x, h->nx, h->ny, F.pitch, s);
+  BMG_CUDA(cudaGetLastError());
+  BMG_CUDA(cudaStreamSynchronize(s));
+  const Scalars& r = *h->sc_host;
+  if (info) *info = bmg_info{r.cycles, h->threshold, r.rel, h->setup_ms, now_ms() - t0};
+  if (r.err & DEV_NAN) return BMG_ENAN;
+  if (r.err & DEV_TIMEOUT) return BMG_ETIMEOUT;
+  if (!(r.rel <= tol)) return BMG_ENOCONV;
+  return BMG_OK;
+}
+
+}  // namespace bmg
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+using bmg::Hierarchy;
+
+static Hierarchy* H(bmg_hierarchy* p) { return reinterpret_cast<Hierarchy*>(p); }
+static const Hierarchy* H(const bmg_hierarchy* p) { return reinterpret_cast<const Hierarchy*>(p); }
+
+extern "C" {
+
+void bmg_default_options(bmg_options* opt) {
+  if (!opt) return;
+  opt->nu1 = 2;
+  opt->nu2 = 1;
+  opt->precision = BMG_FP64;
+  opt->interp_residual_term = 0;
+  opt->coarse_threshold = -1;
+  opt->max_cycles = 200;
+}
+
+const char* bmg_strerror(int code) {
+  switch (code) {
+    case BMG_OK: return "success";
+    case BMG_EINVAL: return "invalid argument (size, coefficient, option or level)";
+    case BMG_ENOMEM: return "device allocation failed";
+    case BMG_ECUDA: return "CUDA runtime error";
+    case BMG_ENOCONV: return "no convergence within max_cycles";
+    case BMG_ENAN: return "residual norm is NaN or Inf";
+    case BMG_ETIMEOUT: return "bounded device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+int bmg_setup(const double* k_dev, int nx, int ny, const bmg_options* opt, bmg_stream_t stream,
+              bmg_hierarchy** out) {
+  if (!out) return BMG_EINVAL;
+  Hierarchy* h = nullptr;
+  const int rc = bmg::setup_impl(k_dev, nx, ny, opt, reinterpret_cast<cudaStream_t>(stream), &h);
+  *out = reinterpret_cast<bmg_hierarchy*>(h);
+  return rc;
+}
+
+int bmg_solve(bmg_hierarchy* h, const double* b_dev, double* x_dev, double tol, bmg_info* info,
+              bmg_stream_t stream) {
+  return bmg::solve_impl(H(h), b_dev, x_dev, tol, info, reinterpret_cast<cudaStream_t>(stream));
+}
+
+void bmg_destroy(bmg_hierarchy* h) { bmg::free_hierarchy(H(h)); }
+
+int bmg_solve_host(const double* k_host, const double* b_host, double* x_host, int nx, int ny,
+                   const bmg_options* opt, double tol, bmg_info* info, bmg_stream_t stream) {
+  if (!k_host || !b_host || !x_host) return BMG_EINVAL;
+  if (!bmg::valid_side(nx) || !bmg::valid_side(ny)) return BMG_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes = sizeof(double) * size_t(nx) * ny;
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, 3 * bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return BMG_ENOMEM;
+  }
+  double *k = buf, *b = buf + size_t(nx) * ny, *x = buf + 2 * size_t(nx) * ny;
+  int rc = BMG_OK;
+  bmg_hierarchy* h = nullptr;
+  if (cudaMemcpyAsync(k, k_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b, b_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(x, x_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    rc = BMG_ECUDA;
+  }
+  if (rc == BMG_OK) rc = bmg_setup(k, nx, ny, opt, stream, &h);
+  double setup_ms = 0.0;
+  if (rc == BMG_OK) {
+    setup_ms = H(h)->setup_ms;
+    rc = bmg_solve(h, b, x, tol, info, stream);
+    if (rc == BMG_OK || rc == BMG_ENOCONV) {
+      if (cudaMemcpyAsync(x_host, x, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        rc = BMG_ECUDA;
+    }
+  }
+  if (info) info->setup_ms = setup_ms;
+  bmg_destroy(h);
+  cudaFree(buf);
+  return rc;
+}
+
+int bmg_num_levels(const bmg_hierarchy* h, int* nlevels) {
+  if (!h || !nlevels) return BMG_EINVAL;
+  *nlevels = H(h)->L;
+  return BMG_OK;
+}
+
+int bmg_level_shape(const bmg_hierarchy* h, int level, int* nx, int* ny) {
+  if (!h || !nx || !ny || level < 0 || level >= H(h)->L) return BMG_EINVAL;
+  *nx = H(h)->geo64[level].nx;
+  *ny = H(h)->geo64[level].ny;
+  return BMG_OK;
+}
+
+}  // extern "C"
+
+namespace bmg {
+
+// Copy the interior of a device plane to a dense host array (as double).
+template <typename T>
+static int plane_to_host(const T* plane, int nx, int ny, int pitch, double* out) {
+  if (!plane) {
+    std::memset(out, 0, sizeof(double) * size_t(nx) * ny);
+    return BMG_OK;
+  }
+  std::vector<T> tmp(size_t(ny + 2) * pitch);
+  BMG_CUDA(cudaMemcpy(tmp.data(), plane, sizeof(T) * tmp.size(), cudaMemcpyDeviceToHost));
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) out[size_t(j) * nx + i] = double(tmp[size_t(j + 1) * pitch + i + 1]);
+  return BMG_OK;
+}
+
+template <typename T>
+static int plane_block_to_host(const T* plane, int nx1, int ny1, int pitch, double* out) {
+  // entries (I, J), 0 <= I < nx1, 0 <= J < ny1 of a coarse-grid plane
+  std::vector<T> tmp(size_t(ny1 + 1) * pitch);
+  BMG_CUDA(cudaMemcpy(tmp.data(), plane, sizeof(T) * tmp.size(), cudaMemcpyDeviceToHost));
+  for (int J = 0; J < ny1; ++J)
+    for (int I = 0; I < nx1; ++I) out[size_t(J) * nx1 + I] = double(tmp[size_t(J) * pitch + I]);
+  return BMG_OK;
+}
+
+template <typename T>
+static int stencil_out(const LevelV<T>& L, double* out) {
+  const size_t n = size_t(L.nx) * L.ny;
+  int rc;
+  if ((rc = plane_to_host<T>(L.C, L.nx, L.ny, L.pitch, out))) return rc;
+  if ((rc = plane_to_host<T>(L.W, L.nx, L.ny, L.pitch, out + n))) return rc;
+  if ((rc = plane_to_host<T>(L.S, L.nx, L.ny, L.pitch, out + 2 * n))) return rc;
+  if ((rc = plane_to_host<T>(L.SW, L.nx, L.ny, L.pitch, out + 3 * n))) return rc;
+  return plane_to_host<T>(L.NW, L.nx, L.ny, L.pitch, out + 4 * n);
+}
+
+template <typename T>
+static int interp_out(const LevelV<T>& L, const LevelV<T>& Lc, double* out) {
+  const int nx1 = Lc.nx + 1, ny1 = Lc.ny + 1;
+  for (int k = 0; k < NPW; ++k) {
+    int rc = plane_block_to_host<T>(L.P[k], nx1, ny1, L.cpitch, out + size_t(k) * nx1 * ny1);
+    if (rc) return rc;
+  }
+  return BMG_OK;
+}
+
+}  // namespace bmg
+
+extern "C" {
+
+int bmg_level_stencil(const bmg_hierarchy* hp, int level, double* host_out) {
+  const Hierarchy* h = H(hp);
+  if (!h || !host_out || level < 0 || level >= h->L) return BMG_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return BMG_ECUDA;
+  if (h->opt.precision == BMG_FP32_REFINE) return bmg::stencil_out<float>(h->f[level], host_out);
+  return bmg::stencil_out<double>(h->d[level], host_out);
+}
+
+int bmg_level_interp(const bmg_hierarchy* hp, int level, double* host_out) {
+  const Hierarchy* h = H(hp);
+  if (!h || !host_out || level < 1 || level >= h->L) return BMG_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return BMG_ECUDA;
+  if (h->opt.precision == BMG_FP32_REFINE)
+    return bmg::interp_out<float>(h->f[level], h->f[level - 1], host_out);
+  return bmg::interp_out<double>(h->d[level], h->d[level - 1], host_out);
+}
+
+int bmg_coarse_factor(const bmg_hierarchy* hp, double* host_out, int n0_capacity) {
+  const Hierarchy* h = H(hp);
+  if (!h || !host_out || n0_capacity < h->n0) return BMG_EINVAL;
+  if (cudaMemcpy(host_out, h->chol, sizeof(double) * size_t(h->n0) * h->n0,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BMG_ECUDA;
+  return BMG_OK;
+}
+
+static int op_check(bmg_hierarchy* hp, int level, int lo) {
+  Hierarchy* h = H(hp);
+  if (!h || level < lo || level >= h->L) return BMG_EINVAL;
+  if (h->opt.precision != BMG_FP64) return BMG_EINVAL;
+  return BMG_OK;
+}
+
+int bmg_op_relax(bmg_hierarchy* hp, int level, double* x, const double* b, int nu, int reverse,
+                 bmg_stream_t stream) {
+  int rc = op_check(hp, level, 0);
+  if (rc) return rc;
+  if (!x || !b || nu < 0) return BMG_EINVAL;
+  Hierarchy* h = H(hp);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto& L = h->d[level];
+  bmg::launch_pack<double>(x, L.x, L.nx, L.ny, L.pitch, s);
+  bmg::launch_pack<double>(b, L.b, L.nx, L.ny, L.pitch, s);
+  bmg::launch_relax<double>(L, level != h->L - 1, nu, reverse != 0, s);
+  bmg::launch_unpack<double>(L.x, x, L.nx, L.ny, L.pitch, s);
+  return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;
+}
+
+int bmg_op_residual(bmg_hierarchy* hp, int level, const double* x, const double* b, double* r,
+                    bmg_stream_t stream) {
+  int rc = op_check(hp, level, 0);
+  if (rc) return rc;
+  if (!x || !b || !r) return BMG_EINVAL;
+  Hierarchy* h = H(hp);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto& L = h->d[level];
+  bmg::launch_pack<double>(x, L.x, L.nx, L.ny, L.pitch, s);
+  bmg::launch_pack<double>(b, L.b, L.nx, L.ny, L.pitch, s);
+  bmg::launch_residual<double>(L, level != h->L - 1, L.x, L.b, L.r, s);
+  bmg::launch_unpack<double>(L.r, r, L.nx, L.ny, L.pitch, s);
+  return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;
+}
+
+int bmg_op_restrict(bmg_hierarchy* hp, int level, const double* r, double* bc,
+                    bmg_stream_t stream) {
+  int rc = op_check(hp, level, 1);
+  if (rc) return rc;
+  if (!r || !bc) return BMG_EINVAL;
+  Hierarchy* h = H(hp);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto& L = h->d[level];
+  auto& Lc = h->d[level - 1];
+  bmg::launch_pack<double>(r, L.r, L.nx, L.ny, L.pitch, s);
+  bmg::launch_restrict<double>(L, L.r, Lc, false, s);
+  bmg::launch_unpack<double>(Lc.b, bc, Lc.nx, Lc.ny, Lc.pitch, s);
+  return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;
+}
+
+int bmg_op_interp(bmg_hierarchy* hp, int level, const double* xc, double* x,
+                  bmg_stream_t stream) {
+  int rc = op_check(hp, level, 1);
+  if (rc) return rc;
+  if (!xc || !x) return BMG_EINVAL;
+  Hierarchy* h = H(hp);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto& L = h->d[level];
+  auto& Lc = h->d[level - 1];
+  bmg::launch_pack<double>(xc, Lc.x, Lc.nx, Lc.ny, Lc.pitch, s);
+  bmg::launch_pack<double>(x, L.x, L.nx, L.ny, L.pitch, s);
+  bmg::launch_interp<double>(L, Lc.x, false, s);
+  bmg::launch_unpack<double>(L.x, x, L.nx, L.ny, L.pitch, s);
+  return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;
+}
+
+int bmg_assemble_backward(bmg_hierarchy* hp, const double* u, const double* lam, double* dtheta,
+                          bmg_stream_t stream) {
+  Hierarchy* h = H(hp);
+  if (!h || !u || !lam || !dtheta) return BMG_EINVAL;
+  bmg::launch_assemble_backward(h->kcopy, u, lam, dtheta, h->nx, h->ny,
+                                reinterpret_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;
+}
+
+}  // extern "C"

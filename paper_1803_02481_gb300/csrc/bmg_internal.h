@@ -1,0 +1,268 @@
+// Internal declarations of the GB300 BoxMG library: device data layout, the
+// per-point stencil arithmetic shared by every kernel, and the host-side
+// launch interface.
+//
+// Data layout in HBM
+// ------------------
+// Every grid quantity of a level lives in a "plane": (ny + 2) rows of `pitch`
+// elements, with a one-cell ghost ring that holds zeros (the Dirichlet
+// condition of Eq. (diffusion_bc) and the zero coarse values outside the
+// domain).  Element (i, j), 0 <= i <= nx + 1, 0 <= j <= ny + 1, 1-based in
+// the interior, is at base[j * pitch + i].  `base` is offset inside the
+// allocation so that every interior row starts (i = 1) on a 128-byte
+// boundary; pitch is a multiple of 128 bytes.
+//
+// Operator of a level (symmetric; the five stored planes give all nine
+// entries, as in BoxMG):
+//   C(i,j)  = A[(i,j),(i,j)]              iC = 1 / C (so no divide in sweeps)
+//   W(i,j)  = -A[(i,j),(i-1,j)]           E(i,j)  = W(i+1,j)
+//   S(i,j)  = -A[(i,j),(i,j-1)]           N(i,j)  = S(i,j+1)
+//   SW(i,j) = -A[(i,j),(i-1,j-1)]         NE(i,j) = SW(i+1,j+1)
+//   NW(i,j) = -A[(i,j),(i-1,j+1)]         SE(i,j) = NW(i+1,j-1)
+// The assembled finest level is 5-point (no SW/NW planes).
+//
+// Interpolation P_l (level l-1 -> l) is stored as eight planes on the coarse
+// grid of level l-1 (index (I, J), 0..nc), one weight per (fine point,
+// coarse neighbour) pair, 1-based fine indices:
+//   XW, XE           x-edge point (2I+1, 2J)   -> coarse (I,J), (I+1,J)
+//   YS, YN           y-edge point (2I, 2J+1)   -> coarse (I,J), (I,J+1)
+//   CSW, CSE, CNW, CNE  centre (2I+1, 2J+1)    -> (I,J),(I+1,J),(I,J+1),(I+1,J+1)
+// Coarse point (I, J) is fine point (2I, 2J) with weight 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/boxmg.h"
+
+namespace bmg {
+
+enum PIdx { XW = 0, XE, YS, YN, CSW, CSE, CNW, CNE, NPW };
+
+// Grid geometry of one plane.
+struct Geom {
+  int nx, ny, pitch;   // pitch in elements
+  size_t elems;        // elements reserved per plane (incl. alignment slack)
+};
+
+template <typename T>
+inline Geom make_geom(int nx, int ny) {
+  const int per128 = int(128 / sizeof(T));
+  Geom g;
+  g.nx = nx;
+  g.ny = ny;
+  g.pitch = ((nx + 2 + per128 - 1) / per128) * per128;
+  g.elems = size_t(ny + 2) * g.pitch + per128;
+  return g;
+}
+
+// Offset of the plane base inside its allocation: interior i = 1 lands on a
+// 128-byte boundary.
+template <typename T>
+constexpr int base_shift() { return int(128 / sizeof(T)) - 1; }
+
+// Device view of one level.  Pointers are plane bases (element (0,0) is the
+// lower-left ghost).  SW/NW are null on a 5-point level.  P holds the
+// interpolation INTO this level from the next coarser one (null on level 0).
+template <typename T>
+struct LevelV {
+  int nx, ny, pitch;
+  T *C, *iC, *W, *S, *SW, *NW;
+  T *x, *b, *r;
+  T *P[NPW];
+  int cpitch;          // pitch of the coarse grid the P planes live on
+};
+
+// ---------------------------------------------------------------------------
+// Per-point arithmetic.  Every kernel (full-grid or persistent) uses these,
+// so a level gives bit-identical results whichever kernel processes it.
+// ---------------------------------------------------------------------------
+
+// Gauss-Seidel update of one point: x = (b + sum_X a_X x_X) * (1/C), the
+// neighbour terms accumulated in the order W, E, S, N, SW, SE, NW, NE.
+template <typename T, bool NINE>
+__device__ __forceinline__ T gs_value(const LevelV<T>& L, const T* __restrict__ x,
+                                      T bval, int o) {
+  const int p = L.pitch;
+  T acc = bval;
+  acc = fma(L.W[o], x[o - 1], acc);
+  acc = fma(L.W[o + 1], x[o + 1], acc);
+  acc = fma(L.S[o], x[o - p], acc);
+  acc = fma(L.S[o + p], x[o + p], acc);
+  if (NINE) {
+    acc = fma(L.SW[o], x[o - p - 1], acc);
+    acc = fma(L.NW[o + 1 - p], x[o + 1 - p], acc);
+    acc = fma(L.NW[o], x[o + p - 1], acc);
+    acc = fma(L.SW[o + 1 + p], x[o + 1 + p], acc);
+  }
+  return acc * L.iC[o];
+}
+
+// Residual of one point: r = b - (C x - sum_X a_X x_X).
+template <typename T, bool NINE>
+__device__ __forceinline__ T resid_value(const LevelV<T>& L, const T* __restrict__ x,
+                                         T bval, int o) {
+  const int p = L.pitch;
+  T y = L.C[o] * x[o];
+  y = fma(-L.W[o], x[o - 1], y);
+  y = fma(-L.W[o + 1], x[o + 1], y);
+  y = fma(-L.S[o], x[o - p], y);
+  y = fma(-L.S[o + p], x[o + p], y);
+  if (NINE) {
+    y = fma(-L.SW[o], x[o - p - 1], y);
+    y = fma(-L.NW[o + 1 - p], x[o + 1 - p], y);
+    y = fma(-L.NW[o], x[o + p - 1], y);
+    y = fma(-L.SW[o + 1 + p], x[o + 1 + p], y);
+  }
+  return bval - y;
+}
+
+// Weight of fine point (2I + rx, 2J + ry) towards coarse point (I, J),
+// rx, ry in {-1, 0, 1}; c = J * cpitch + I.
+template <typename T>
+__device__ __forceinline__ T pweight(T* const* P, int cp, int rx, int ry, int c) {
+  if (rx == 0 && ry == 0) return T(1);
+  if (ry == 0) return rx > 0 ? P[XW][c] : P[XE][c - 1];
+  if (rx == 0) return ry > 0 ? P[YS][c] : P[YN][c - cp];
+  if (rx > 0 && ry > 0) return P[CSW][c];
+  if (rx < 0 && ry > 0) return P[CSE][c - 1];
+  if (rx > 0 && ry < 0) return P[CNW][c - cp];
+  return P[CNE][c - cp - 1];
+}
+
+// Restriction at coarse point (I, J): b_c = sum over the 3x3 fine block of
+// P(p, I) r(p) (R = P^T, Algorithm 1).  f = fine offset of (2I, 2J).
+template <typename T>
+__device__ __forceinline__ T restrict_value(T* const* P, int cp, const T* __restrict__ r,
+                                            int fp, int c, int f) {
+  T acc = r[f];
+  acc = fma(P[XE][c - 1], r[f - 1], acc);
+  acc = fma(P[XW][c], r[f + 1], acc);
+  acc = fma(P[YN][c - cp], r[f - fp], acc);
+  acc = fma(P[YS][c], r[f + fp], acc);
+  acc = fma(P[CNE][c - cp - 1], r[f - fp - 1], acc);
+  acc = fma(P[CNW][c - cp], r[f - fp + 1], acc);
+  acc = fma(P[CSE][c - 1], r[f + fp - 1], acc);
+  acc = fma(P[CSW][c], r[f + fp + 1], acc);
+  return acc;
+}
+
+// Interpolated correction (P x_c)(i, j) at fine point (i, j), 1-based.
+template <typename T>
+__device__ __forceinline__ T interp_value(T* const* P, int cp, const T* __restrict__ xc,
+                                          int i, int j) {
+  const int I = i >> 1, J = j >> 1;
+  const int c = J * cp + I;
+  if (!(i & 1)) {
+    if (!(j & 1)) return xc[c];
+    return fma(P[YS][c], xc[c], P[YN][c] * xc[c + cp]);
+  }
+  if (!(j & 1)) return fma(P[XW][c], xc[c], P[XE][c] * xc[c + 1]);
+  T v = P[CSW][c] * xc[c];
+  v = fma(P[CSE][c], xc[c + 1], v);
+  v = fma(P[CNW][c], xc[c + cp], v);
+  v = fma(P[CNE][c], xc[c + cp + 1], v);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+// Error word written by device code (0 = fine).
+enum DevErr { DEV_OK = 0, DEV_BADK = 1, DEV_NOTSPD = 2, DEV_BADDEN = 4, DEV_NAN = 8,
+              DEV_TIMEOUT = 16 };
+
+struct Scalars {            // device-resident solve state (one cache line)
+  double bnorm2;            // ||b||^2
+  double rnorm2;            // ||r||^2 of the latest residual
+  double scale2;            // FP32_REFINE: ||r||^2 of the previous residual,
+                            // the square of the scale the latest residual was
+                            // divided by before the cast to FP32
+  double rel;               // sqrt(rnorm2 / bnorm2)
+  double tol;               // stop test
+  int cycles;               // cycles / refinement steps run
+  int max_cycles;
+  int go;                   // 1 while the loop should continue
+  int err;                  // DevErr bits
+};
+
+struct Timing;
+
+struct Hierarchy {
+  int nx = 0, ny = 0, L = 0;
+  bmg_options opt{};
+  int threshold = 1;                 // levels l < threshold: persistent kernel
+  std::vector<LevelV<double>> d;     // FP64 levels (all for FP64; finest only
+                                     // for FP32_REFINE)
+  std::vector<LevelV<float>> f;      // FP32 levels (FP32_REFINE)
+  std::vector<Geom> geo64, geo32;
+  double* kcopy = nullptr;           // dense (ny, nx) copy of k
+  double* chol = nullptr;            // N0 x N0 lower factor (row-major)
+  double* chol_idiag = nullptr;      // 1 / L[i][i]
+  int n0 = 0;
+  double* partials = nullptr;        // reduction scratch
+  int npartials = 0;
+  Scalars* sc = nullptr;             // device scalars
+  Scalars* sc_host = nullptr;        // pinned mirror
+  LevelV<double>* dlev64 = nullptr;  // device copies of the level views (for
+  LevelV<float>* dlev32 = nullptr;   // the persistent coarse kernel)
+  double predicted_us[16] = {};      // cost model: V-cycle time per threshold
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  double setup_ms = 0.0;
+};
+
+// Observability: launch counter and optional event bracketing of one kernel
+// class (bmg_profile.cu).
+void count_launch(int n = 1);
+void prof_begin(int which, cudaStream_t s);
+void prof_end(int which, cudaStream_t s);
+
+// Kernel launch wrappers (defined in the .cu files).
+template <typename T>
+int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy,
+                    int* derr, cudaStream_t s);
+template <typename T>
+int launch_interp_weights(const LevelV<T>& fine, bool nine, int* derr, cudaStream_t s);
+template <typename T>
+int launch_rap(const LevelV<T>& fine, bool nine, LevelV<T> coarse, cudaStream_t s);
+int launch_coarse_factor(Hierarchy* h, const LevelV<double>* l0d, const LevelV<float>* l0f,
+                         cudaStream_t s);
+int launch_downcast_fine(const LevelV<double>& d, LevelV<float> f, cudaStream_t s);
+
+template <typename T>
+void launch_pack(const double* src, T* dst, int nx, int ny, int pitch, cudaStream_t s);
+template <typename T>
+void launch_unpack(const T* src, double* dst, int nx, int ny, int pitch, cudaStream_t s);
+
+template <typename T>
+void launch_relax(const LevelV<T>& L, bool nine, int nu, bool reverse, cudaStream_t s);
+template <typename T>
+void launch_residual(const LevelV<T>& L, bool nine, const T* x, const T* b, T* r,
+                     cudaStream_t s);
+template <typename T>
+void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool zero_x,
+                     cudaStream_t s);
+template <typename T>
+void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s);
+template <typename T>
+void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* levels, int threshold,
+                         cudaStream_t s);
+
+// ||b - A x||^2 (or ||b||^2 when x == nullptr) of the finest FP64 level into
+// sc->rnorm2 / sc->bnorm2; then updates rel/go.  `what`: 0 = b norm, 1 =
+// residual norm + convergence flag.
+void launch_fine_norm(Hierarchy* h, const double* x, const double* b, int what,
+                      double tol, cudaStream_t s);
+// FP32_REFINE: r = b - A x in FP64 on the finest level, cast r/scale to FP32
+// into the FP32 fine RHS; zero the FP32 fine x.
+void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s);
+void launch_refine_update(Hierarchy* h, cudaStream_t s);
+
+void launch_assemble_backward(const double* k, const double* u, const double* lam,
+                              double* g, int nx, int ny, cudaStream_t s);
+
+}  // namespace bmg

@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (FP64):
+* coarse stencil entries: |gpu - oracle| <= 1e-12 * max(|a|, C_row), the
+  row diagonal as scale because off-diagonals can be tiny under 10^8
+  contrast; the finest level is assembled with the same operation order as
+  the oracle and must match exactly;
+* interpolation weights (in [0, 1]): 1e-12 absolute;
+* solves: identical V-cycle counts; final relative residuals within 1e-10 of
+  each other (both are below tol = 1e-10) and, tighter, within 1e-6 relative;
+  iterates within 1e-9 of max|x|.
+"""
+import numpy as np
+import pytest
+
+from oracle import boxmg_oracle as O
+from tests.parity_helpers import PROBLEMS, interp_planes, oracle_hierarchy, oracle_solve, problem
+
+torch = pytest.importorskip("torch")
+import paper_1803_02481_gb300 as bm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def gpu_setup(name, **opts):
+    return bm.setup(dev(problem(name)["k"]), bm.default_options(**opts))
+
+
+SETUP_CASES = ["poisson255", "blocks255", "blocks511_c2", "lognormal255", "random63",
+               "rect127x31", "tiny3"]
+
+
+@pytest.mark.parametrize("name", SETUP_CASES)
+def test_setup_stencils_and_interpolation_match_oracle(name):
+    ho = oracle_hierarchy(name)
+    hg = gpu_setup(name)
+    assert hg.nlevels == ho.nlevels
+    L = ho.nlevels
+    for l in range(L):
+        so = ho.levels[l].st
+        sg = hg.level_stencil(l)
+        assert sg["C"].shape == so["C"].shape
+        if l == L - 1:
+            # finest level: same operations in the same order -> bit-identical
+            for d in ("C", "W", "S"):
+                assert np.array_equal(sg[d], so[d]), d
+            assert not sg["SW"].any() and not sg["NW"].any()
+            continue
+        scale = np.maximum(np.abs(so["C"]), 1e-300)
+        for d in ("C", "W", "S", "SW", "NW"):
+            err = np.abs(sg[d] - so[d]) / np.maximum(np.abs(so[d]), scale)
+            assert err.max() <= 1e-12, (l, d, err.max())
+    for l in range(1, L):
+        ny, nx = ho.levels[l].shape
+        planes, valid = interp_planes(ho.levels[l].p, nx, ny)
+        pg = hg.level_interp(l)
+        for k, key in enumerate(("XW", "XE", "YS", "YN", "CSW", "CSE", "CNW", "CNE")):
+            err = np.abs(pg[key] - planes[k])[valid[k]]
+            assert err.max(initial=0.0) <= 1e-12, (l, key, err.max())
+    # coarsest Cholesky factor
+    lg = hg.coarse_factor()
+    assert np.abs(lg - ho.chol).max() <= 1e-12 * np.abs(ho.chol).max()
+    hg.destroy()
+
+
+@pytest.mark.parametrize("name", ["blocks255", "rect127x31"])
+def test_single_operations_match_oracle(name):
+    ho = oracle_hierarchy(name)
+    hg = gpu_setup(name)
+    rng = np.random.default_rng(3)
+    L = ho.nlevels
+    for l in (L - 1, L - 2, 1):
+        st = ho.levels[l].st
+        ny, nx = st["C"].shape
+        x = rng.uniform(-1, 1, (ny, nx))
+        b = rng.uniform(-1, 1, (ny, nx))
+        scale = np.abs(st["C"]).max()
+        # residual
+        r_g = hg.op_residual(l, dev(x), dev(b), torch.zeros((ny, nx), dtype=torch.float64, device="cuda"))
+        r_o = O.residual(st, x, b)
+        assert np.abs(r_g.cpu().numpy() - r_o).max() <= 1e-13 * scale * 4
+        # relaxation, forward and reverse, two sweeps
+        for rev in (False, True):
+            xg = hg.op_relax(l, dev(x), dev(b), nu=2, reverse=rev).cpu().numpy()
+            xo = x.copy()
+            O.relax(st, xo, b, 2, O.colour_order(st), reverse=rev)
+            assert np.abs(xg - xo).max() <= 1e-11 * max(1.0, np.abs(xo).max()), (l, rev)
+        if l >= 1:
+            p = ho.levels[l].p
+            nyc, nxc = ho.levels[l - 1].shape
+            bc_g = hg.op_restrict(l, dev(r_o), torch.zeros((nyc, nxc), dtype=torch.float64, device="cuda"))
+            bc_o = (p.T @ r_o.ravel()).reshape(nyc, nxc)
+            assert np.abs(bc_g.cpu().numpy() - bc_o).max() <= 1e-12 * max(1.0, np.abs(bc_o).max())
+            xc = rng.uniform(-1, 1, (nyc, nxc))
+            xi_g = hg.op_interp(l, dev(xc), dev(x)).cpu().numpy()
+            xi_o = x + (p @ xc.ravel()).reshape(ny, nx)
+            assert np.abs(xi_g - xi_o).max() <= 1e-13 * 4
+    hg.destroy()
+
+
+SOLVE_CASES = ["poisson255", "blocks255", "lognormal255", "random63", "rect127x31", "tiny3"]
+
+
+@pytest.mark.parametrize("name", SOLVE_CASES)
+def test_solve_matches_oracle(name):
+    pr = problem(name)
+    ro = oracle_solve(name)
+    hg = gpu_setup(name)
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+    xg = x.cpu().numpy()
+    assert info.cycles == ro.cycles, (info.cycles, ro.cycles, ro.history[-3:])
+    assert info.rel_resid <= 1e-10 and ro.rel_resid <= 1e-10
+    assert abs(info.rel_resid - ro.rel_resid) <= 1e-6 * ro.rel_resid + 1e-16
+    assert np.abs(xg - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+    # the returned x satisfies the stop test with the oracle's own operator
+    st = oracle_hierarchy(name).levels[-1].st
+    rel = np.linalg.norm(O.residual(st, xg, pr["b"])) / np.linalg.norm(pr["b"])
+    assert rel <= 1.0000001e-10
+    hg.destroy()
+
+
+def test_solve_slow_contrast_case_matches_oracle():
+    """511^2, 64-cell blocks, contrast 10^4: several hundred thousand
+    unknowns, 8 full tiles and ragged tails on every coarse level."""
+    test_solve_matches_oracle("blocks511_c2")
+
+
+@pytest.mark.parametrize("name", ["blocks255", "rect127x31"])
+def test_every_threshold_gives_identical_iterates(name):
+    """The level schedule moves levels between full-grid launches and the
+    persistent kernel; per-point arithmetic is shared, so results are
+    bit-identical for every threshold."""
+    pr = problem(name)
+    L = oracle_hierarchy(name).nlevels
+    ref = None
+    for thr in range(1, L + 1):
+        hg = gpu_setup(name, coarse_threshold=thr)
+        x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+        assert info.threshold == thr
+        xn = x.cpu().numpy()
+        if ref is None:
+            ref = (xn, info.cycles, info.rel_resid)
+        else:
+            assert np.array_equal(xn, ref[0]), thr
+            assert info.cycles == ref[1] and info.rel_resid == ref[2]
+        hg.destroy()
+
+
+def test_interp_residual_term_variant_matches_oracle():
+    name = "random63"
+    pr = problem(name)
+    ho = O.setup(pr["k"], interp_residual_term=True)
+    ro = O.solve(ho, pr["b"], tol=1e-10)
+    hg = gpu_setup(name, interp_residual_term=1)
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+    assert info.cycles == ro.cycles
+    assert np.abs(x.cpu().numpy() - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+    hg.destroy()
+
+
+@pytest.mark.parametrize("name", ["poisson255", "blocks255", "lognormal255"])
+def test_fp32_refinement_reaches_fp64_tolerance(name):
+    pr = problem(name)
+    ro = oracle_solve(name)
+    hg = gpu_setup(name, precision=bm.BMG_FP32_REFINE)
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+    xg = x.cpu().numpy()
+    st = oracle_hierarchy(name).levels[-1].st
+    rel = np.linalg.norm(O.residual(st, xg, pr["b"])) / np.linalg.norm(pr["b"])
+    assert rel <= 1.0000001e-10 and info.rel_resid <= 1e-10
+    # error against the FP64 oracle solution, bounded by what 1e-10 allows
+    err = np.abs(xg - ro.x).max() / np.abs(ro.x).max()
+    assert err <= 1e-7
+    # FP32 coarse hierarchy is the FP32 Galerkin product of the FP32 fine operator
+    so = O.galerkin({k: v.astype(np.float32).astype(np.float64) for k, v in st.items()},
+                    O.interpolation({k: v.astype(np.float32).astype(np.float64) for k, v in st.items()}))
+    sg = hg.level_stencil(hg.nlevels - 2)
+    assert np.abs(sg["C"] - so["C"]).max() <= 1e-5 * np.abs(so["C"]).max()
+    hg.destroy()
+
+
+def test_assembly_backward_matches_oracle():
+    rng = np.random.default_rng(31)
+    n = 127
+    theta = rng.normal(0, 1, (n, n))
+    k = np.exp(theta)
+    u = rng.uniform(-1, 1, (n, n))
+    lam = rng.uniform(-1, 1, (n, n))
+    hg = bm.setup(dev(k))
+    g = hg.assemble_backward(dev(u), dev(lam), torch.zeros((n, n), dtype=torch.float64, device="cuda"))
+    go = O.assembly_vjp(k, u, lam)
+    assert np.abs(g.cpu().numpy() - go).max() <= 1e-13 * np.abs(go).max()
+    hg.destroy()
+
+
+def test_zero_rhs_and_error_codes():
+    k = dev(np.ones((31, 31)))
+    hg = bm.setup(k)
+    x, info = hg.solve(dev(np.zeros((31, 31))), x=dev(np.ones((31, 31))))
+    assert info.cycles == 0 and not x.any()
+    hg.destroy()
+    bad = np.ones((31, 31))
+    bad[4, 5] = np.nan
+    with pytest.raises(bm.BoxMGError) as e:
+        bm.setup(dev(bad))
+    assert e.value.code == bm.BMG_EINVAL
+    bad[4, 5] = -1.0
+    with pytest.raises(bm.BoxMGError) as e:
+        bm.setup(dev(bad))
+    assert e.value.code == bm.BMG_EINVAL
+    with pytest.raises(bm.BoxMGError) as e:
+        bm.setup(dev(np.ones((30, 31))))
+    assert e.value.code == bm.BMG_EINVAL
+    # the cycle cap returns ENOCONV with the last iterate
+    pr = problem("blocks255")
+    hg = bm.setup(dev(pr["k"]), bm.default_options(max_cycles=3))
+    with pytest.raises(bm.BoxMGError) as e:
+        hg.solve(dev(pr["b"]), tol=1e-10)
+    assert e.value.code == bm.BMG_ENOCONV
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10, allow_noconv=True)
+    assert info.cycles == 3 and info.rel_resid > 1e-10
+    ro = O.setup(pr["k"])
+    xo = np.zeros_like(pr["b"])
+    for _ in range(3):
+        O.vcycle(ro, xo, pr["b"])
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-12 * np.abs(xo).max()
+    hg.destroy()
+
+
+def test_solve_host_end_to_end():
+    pr = problem("poisson255")
+    ro = oracle_solve("poisson255")
+    x = np.zeros_like(pr["b"])
+    info = bm.solve_host(np.ascontiguousarray(pr["k"]), np.ascontiguousarray(pr["b"]), x)
+    assert info.cycles == ro.cycles
+    assert np.abs(x - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
