@@ -37,8 +37,18 @@ Readings where the paper is silent (each is also listed in the design notes):
 * interpolation weights: x-edge point w_W = (a_W + a_SW + a_NW) / (C - a_S - a_N)
   (and the mirror for E); y-edge point w_S = (a_S + a_SW + a_SE) / (C - a_W - a_E)
   (and the mirror for N); cell-centre point: the fine equation at the point
-  with the four edge neighbours replaced by their interpolants.  Here a_X >= 0
+  with the four edge neighbours replaced by their interpolants.  Here a_X
   are the negated off-diagonal entries of the fine row.
+* rows that are not M-matrix rows (the paper mentions BoxMG heuristics for
+  non-zero row sums without stating them): before collapsing, a coupling
+  with a_X < 0 (a positive matrix entry) is lumped into the diagonal and a
+  negative row sum sigma = C - sum_X a_X is dropped, i.e. the formulas above
+  are applied to a_X+ = max(a_X, 0) and C_eff = C - sum_X min(a_X, 0) -
+  min(sigma, 0).  On rows with all a_X >= 0 and sigma >= 0 (every row of the
+  assembled operator) C_eff = C exactly and nothing changes.  Galerkin
+  operators of high-contrast fields develop such rows once the coefficient
+  blocks are narrower than a coarse cell; without this the collapse
+  denominators turn negative there.
 * colour order: red = (i + j) even (1-based), first; four colours
   (i mod 2, j mod 2) in the order (1,1), (0,1), (1,0), (0,0).  Pre-smoothing
   runs the colours forward, post-smoothing in reverse.
@@ -179,6 +189,24 @@ def coarse_size(n: int) -> int:
     return (n - 1) // 2
 
 
+def collapse_stencil(st: dict) -> dict:
+    """The stencil the interpolation formulas are applied to: couplings with
+    a_X < 0 lumped into the diagonal and a negative row sum dropped,
+    a_X+ = max(a_X, 0), C_eff = C - sum_X min(a_X, 0) - min(sigma, 0) with
+    sigma = C - sum_X a_X.  Identical to ``st`` on M-matrix rows with
+    sigma >= 0."""
+    total = 0.0
+    for d in DIRS:
+        total = total + st[d]
+    sigma = st["C"] - total
+    neg = 0.0
+    for d in DIRS:
+        neg = neg + np.minimum(st[d], 0.0)
+    out = {d: np.maximum(st[d], 0.0) for d in DIRS}
+    out["C"] = (st["C"] - neg) - np.minimum(sigma, 0.0)
+    return out
+
+
 def edge_weights(st: dict):
     """Weights of the two kinds of edge points.
 
@@ -204,8 +232,10 @@ def interpolation(st: dict) -> sp.csr_matrix:
 
     Returns a CSR matrix of shape (nx*ny, ncx*ncy).  Rows are fine unknowns,
     columns interior coarse unknowns; weights towards ghost coarse points
-    (outside the domain, value 0) are dropped.
+    (outside the domain, value 0) are dropped.  The formulas act on
+    ``collapse_stencil(st)``.
     """
+    st = collapse_stencil(st)
     ny, nx = st["C"].shape
     ncx, ncy = coarse_size(nx), coarse_size(ny)
     fidx = np.arange(nx * ny).reshape(ny, nx)

@@ -459,3 +459,62 @@ def test_compliance_identity():
         fd = (b.ravel() @ O.direct_solve(np.exp(tp), b).ravel()
               - b.ravel() @ O.direct_solve(np.exp(tm), b).ravel()) / (2 * eps)
         assert abs(fd - g[j, i]) <= 1e-6 * np.abs(g).max()
+
+
+# ---------------------------------------------------------------------------
+# Reading for non-M-matrix Galerkin rows (lumping before collapsing)
+# ---------------------------------------------------------------------------
+
+def test_collapse_is_identity_on_m_matrix_rows():
+    rng = np.random.default_rng(41)
+    st = O.assemble_fv5(10.0 ** rng.uniform(-4, 4, size=(15, 15)))
+    cs = O.collapse_stencil(st)
+    for d in ("C",) + O.DIRS:
+        assert np.array_equal(cs[d], st[d]), d
+
+
+def test_lumped_rows_keep_constants_and_bounded_weights():
+    """A 9-point operator whose rows have zero row sum but some positive
+    off-diagonal matrix entries (a_X < 0): lumping keeps the interpolation of
+    constants exact (interior P rows sum to 1) and the weights in [0, 1]."""
+    rng = np.random.default_rng(42)
+    n = 15
+    st = {d: np.zeros((n, n)) for d in ("C",) + O.DIRS}
+    for d in O.DIRS:
+        st[d] = rng.uniform(0.2, 1.0, (n, n))
+    st["SW"] = rng.uniform(-0.3, 0.3, (n, n))          # mixed-sign corners
+    # symmetric partners
+    st["E"][:, :-1] = st["W"][:, 1:]
+    st["N"][:-1, :] = st["S"][1:, :]
+    st["NE"][:-1, :-1] = st["SW"][1:, 1:]
+    st["SE"][1:, :-1] = st["NW"][:-1, 1:]
+    for d, (di, dj) in O.OFFSETS.items():               # no coupling out of the grid
+        if di < 0:
+            st[d][:, 0] = 0
+        if di > 0:
+            st[d][:, -1] = 0
+        if dj < 0:
+            st[d][0, :] = 0
+        if dj > 0:
+            st[d][-1, :] = 0
+    st["C"] = sum(st[d] for d in O.DIRS)               # zero row sums
+    assert (st["SW"] < 0).any()
+    p = O.interpolation(st)
+    assert p.data.min() >= 0.0 and p.data.max() <= 1.0 + 1e-15
+    s = np.asarray(p.sum(axis=1)).reshape(n, n)
+    np.testing.assert_allclose(s[2:-2, 2:-2], 1.0, atol=1e-13)
+
+
+def test_high_contrast_galerkin_levels_stay_interpolable():
+    """Blocks of 10^[-4,4] narrower than a coarse cell make the Galerkin
+    operators lose the M-matrix property; every interpolation weight must
+    still lie in [0, 1] on every level."""
+    pr = inputs.block_problem(255, seed=1, block=16, lo=-4, hi=4)
+    h = O.setup(pr["k"])
+    saw_negative = False
+    for l in range(1, h.nlevels):
+        st = h.levels[l].st
+        saw_negative |= any((st[d] < 0).any() for d in O.DIRS)
+        p = h.levels[l].p
+        assert p.data.min() >= 0.0 and p.data.max() <= 1.0 + 1e-12, l
+    assert saw_negative
