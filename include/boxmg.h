@@ -85,6 +85,11 @@ void bmg_default_options(bmg_options *opt);
 /* Message for a BMG_* code (static storage). */
 const char *bmg_strerror(int code);
 
+/* Details of the last failed call made by this thread (which device check
+ * fired, on which level), or "" (thread-local storage, valid until the next
+ * call). */
+const char *bmg_last_error(void);
+
 /* BoxMG setup (Section 2; Section 5 discretisation).
  * k_dev: cell coefficients k > 0, dense (ny, nx) float64, device.
  * Assembles the fine 5-point operator (harmonic face means, 2k on Dirichlet

@@ -42,7 +42,8 @@ class Info(ctypes.Structure):
 class BoxMGError(RuntimeError):
     def __init__(self, code: int, where: str):
         msg = lib().bmg_strerror(code).decode()
-        super().__init__(f"{where}: {msg} (code {code})")
+        detail = lib().bmg_last_error().decode()
+        super().__init__(f"{where}: {msg} (code {code})" + (f" [{detail}]" if detail else ""))
         self.code = code
 
 
@@ -55,6 +56,7 @@ _HP = ctypes.POINTER(ctypes.c_void_p)
 EXPORTED = {
     "bmg_default_options": (None, [ctypes.POINTER(Options)]),
     "bmg_strerror": (ctypes.c_char_p, [_i]),
+    "bmg_last_error": (ctypes.c_char_p, []),
     "bmg_setup": (_i, [_vp, _i, _i, ctypes.POINTER(Options), _vp, _HP]),
     "bmg_solve": (_i, [_vp, _vp, _vp, _d, ctypes.POINTER(Info), _vp]),
     "bmg_solve_host": (_i, [_vp, _vp, _vp, _i, _i, ctypes.POINTER(Options), _d,

@@ -9,10 +9,21 @@
 
 #include <chrono>
 #include <cmath>
+#include <cstdarg>
+#include <cstdio>
 #include <cstring>
 #include <new>
 
 namespace bmg {
+
+static thread_local char g_last_error[256] = "";
+
+void set_last_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+}
 
 namespace {
 
@@ -91,9 +102,27 @@ void carve_levels(Carver& cv, const std::vector<Geom>& geo, int first, std::vect
 // ---------------------------------------------------------------------------
 
 static int check_derr(Hierarchy* h, cudaStream_t s) {
-  BMG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
-  BMG_CUDA(cudaStreamSynchronize(s));
-  if (h->sc_host->err & (DEV_BADK | DEV_NOTSPD | DEV_BADDEN)) return BMG_EINVAL;
+  if (cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_last_error("setup: %s", cudaGetErrorString(cudaGetLastError()));
+    return BMG_ECUDA;
+  }
+  const int e = h->sc_host->err;
+  if (e & DEV_BADK) {
+    set_last_error("setup: a coefficient k is not finite and positive");
+    return BMG_EINVAL;
+  }
+  if (e & DEV_BADDEN) {
+    char lv[96] = "";
+    for (int l = 0; l < 20; ++l)
+      if (e & (1 << (8 + l))) std::snprintf(lv + std::strlen(lv), sizeof(lv) - std::strlen(lv), " %d", l);
+    set_last_error("setup: interpolation denominator <= 0 building P on level(s)%s", lv);
+    return BMG_EINVAL;
+  }
+  if (e & DEV_NOTSPD) {
+    set_last_error("setup: coarsest operator is not positive definite");
+    return BMG_EINVAL;
+  }
   return BMG_OK;
 }
 
@@ -103,7 +132,7 @@ static int build_coarse(Hierarchy* h, std::vector<LevelV<T>>& lv, cudaStream_t s
   const int L = h->L;
   for (int l = L - 1; l >= 1; --l) {
     const bool nine = l != L - 1;
-    if (launch_interp_weights<T>(lv[l], nine, derr, s)) return BMG_ECUDA;
+    if (launch_interp_weights<T>(lv[l], nine, derr, l, s)) return BMG_ECUDA;
     if (launch_rap<T>(lv[l], nine, lv[l - 1], s)) return BMG_ECUDA;
   }
   return BMG_OK;
@@ -119,6 +148,7 @@ static void free_hierarchy(Hierarchy* h) {
 static int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in,
                       cudaStream_t s, Hierarchy** out) {
   *out = nullptr;
+  g_last_error[0] = 0;
   if (!k || !valid_side(nx) || !valid_side(ny)) return BMG_EINVAL;
   bmg_options opt;
   bmg_default_options(&opt);
@@ -343,6 +373,8 @@ void bmg_default_options(bmg_options* opt) {
   opt->coarse_threshold = -1;
   opt->max_cycles = 200;
 }
+
+const char* bmg_last_error(void) { return bmg::g_last_error; }
 
 const char* bmg_strerror(int code) {
   switch (code) {

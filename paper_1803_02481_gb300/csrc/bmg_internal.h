@@ -172,8 +172,13 @@ __device__ __forceinline__ T interp_value(T* const* P, int cp, const T* __restri
 // ---------------------------------------------------------------------------
 
 // Error word written by device code (0 = fine).
+// Bits 8.. of the error word name the levels whose interpolation met a
+// non-positive denominator (bit 8 + l for P_l).
 enum DevErr { DEV_OK = 0, DEV_BADK = 1, DEV_NOTSPD = 2, DEV_BADDEN = 4, DEV_NAN = 8,
               DEV_TIMEOUT = 16 };
+
+// Thread-local detail message of the last failure (bmg_last_error).
+void set_last_error(const char* fmt, ...);
 
 struct Scalars {            // device-resident solve state (one cache line)
   double bnorm2;            // ||b||^2
@@ -226,7 +231,7 @@ template <typename T>
 int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy,
                     int* derr, cudaStream_t s);
 template <typename T>
-int launch_interp_weights(const LevelV<T>& fine, bool nine, int* derr, cudaStream_t s);
+int launch_interp_weights(const LevelV<T>& fine, bool nine, int* derr, int level, cudaStream_t s);
 template <typename T>
 int launch_rap(const LevelV<T>& fine, bool nine, LevelV<T> coarse, cudaStream_t s);
 int launch_coarse_factor(Hierarchy* h, const LevelV<double>* l0d, const LevelV<float>* l0f,

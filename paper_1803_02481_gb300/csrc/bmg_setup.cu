@@ -54,7 +54,12 @@ __global__ void k_assemble(const double* __restrict__ k, int nx, int ny, LevelV<
   L.S[o] = T(as);
 }
 
-// Fine stencil entries (negated off-diagonals) at plane offset o.
+// Fine stencil row at plane offset o, as the interpolation formulas use it:
+// negated off-diagonals a_X with a_X < 0 (positive matrix entries) lumped into
+// the diagonal and a negative row sum sigma dropped,
+//   a_X+ = max(a_X, 0),  C_eff = C - sum_X min(a_X, 0) - min(sigma, 0).
+// On M-matrix rows with sigma >= 0 (the whole assembled level) this is the
+// plain row.  Sums run in the order W, E, S, N, SW, SE, NW, NE.
 template <typename T, bool NINE>
 struct St {
   T c, w, e, s, n, sw, se, nw, ne;
@@ -73,25 +78,41 @@ struct St {
     } else {
       sw = se = nw = ne = T(0);
     }
+    const T total = ((((((((T(0) + w) + e) + s) + n) + sw) + se) + nw) + ne);
+    const T sigma = c - total;
+    const T z = T(0);
+    const T neg = ((((((((z + fmin(w, z)) + fmin(e, z)) + fmin(s, z)) + fmin(n, z)) + fmin(sw, z)) +
+                     fmin(se, z)) + fmin(nw, z)) + fmin(ne, z));
+    c = (c - neg) - fmin(sigma, z);
+    w = fmax(w, z);
+    e = fmax(e, z);
+    s = fmax(s, z);
+    n = fmax(n, z);
+    sw = fmax(sw, z);
+    se = fmax(se, z);
+    nw = fmax(nw, z);
+    ne = fmax(ne, z);
   }
 };
 
 // x-edge point: collapse the fine row in y (flux balance along x).
 template <typename T, bool NINE>
-__device__ __forceinline__ void xedge(const LevelV<T>& L, int o, T& ww, T& we, int* derr) {
+__device__ __forceinline__ void xedge(const LevelV<T>& L, int o, T& ww, T& we, int* derr,
+                                      int lbit) {
   St<T, NINE> a(L, o);
   const T den = (a.c - a.s) - a.n;
-  if (!(den > T(0))) atomicOr(derr, DEV_BADDEN);
+  if (!(den > T(0))) atomicOr(derr, DEV_BADDEN | lbit);
   ww = ((a.w + a.sw) + a.nw) / den;
   we = ((a.e + a.se) + a.ne) / den;
 }
 
 // y-edge point: collapse the fine row in x.
 template <typename T, bool NINE>
-__device__ __forceinline__ void yedge(const LevelV<T>& L, int o, T& ws, T& wn, int* derr) {
+__device__ __forceinline__ void yedge(const LevelV<T>& L, int o, T& ws, T& wn, int* derr,
+                                      int lbit) {
   St<T, NINE> a(L, o);
   const T den = (a.c - a.w) - a.e;
-  if (!(den > T(0))) atomicOr(derr, DEV_BADDEN);
+  if (!(den > T(0))) atomicOr(derr, DEV_BADDEN | lbit);
   ws = ((a.s + a.sw) + a.se) / den;
   wn = ((a.n + a.nw) + a.ne) / den;
 }
@@ -102,7 +123,8 @@ __device__ __forceinline__ void yedge(const LevelV<T>& L, int o, T& ws, T& wn, i
 // edge neighbours are recomputed here with the same code, so the stored
 // edge weights and the ones used for the centre agree bit for bit.
 template <typename T, bool NINE>
-__global__ void k_interp_weights(LevelV<T> F, int ncx, int ncy, int* derr) {
+__global__ void k_interp_weights(LevelV<T> F, int ncx, int ncy, int* derr, int level) {
+  const int lbit = 1 << (8 + level);
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y;
   if (I > ncx || J > ncy) return;
@@ -110,11 +132,11 @@ __global__ void k_interp_weights(LevelV<T> F, int ncx, int ncy, int* derr) {
   const int c = J * cp + I;
   T xw0 = 0, xe0 = 0, xw1 = 0, xe1 = 0, ys0 = 0, yn0 = 0, ys1 = 0, yn1 = 0;
   // x-edge (2I+1, 2J) and (2I+1, 2J+2)
-  if (J >= 1) xedge<T, NINE>(F, (2 * J) * p + 2 * I + 1, xw0, xe0, derr);
-  if (J + 1 <= ncy) xedge<T, NINE>(F, (2 * J + 2) * p + 2 * I + 1, xw1, xe1, derr);
+  if (J >= 1) xedge<T, NINE>(F, (2 * J) * p + 2 * I + 1, xw0, xe0, derr, lbit);
+  if (J + 1 <= ncy) xedge<T, NINE>(F, (2 * J + 2) * p + 2 * I + 1, xw1, xe1, derr, lbit);
   // y-edge (2I, 2J+1) and (2I+2, 2J+1)
-  if (I >= 1) yedge<T, NINE>(F, (2 * J + 1) * p + 2 * I, ys0, yn0, derr);
-  if (I + 1 <= ncx) yedge<T, NINE>(F, (2 * J + 1) * p + 2 * I + 2, ys1, yn1, derr);
+  if (I >= 1) yedge<T, NINE>(F, (2 * J + 1) * p + 2 * I, ys0, yn0, derr, lbit);
+  if (I + 1 <= ncx) yedge<T, NINE>(F, (2 * J + 1) * p + 2 * I + 2, ys1, yn1, derr, lbit);
   if (J >= 1) {
     F.P[XW][c] = xw0;
     F.P[XE][c] = xe0;
@@ -315,13 +337,13 @@ int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy,
 }
 
 template <typename T>
-int launch_interp_weights(const LevelV<T>& fine, bool nine, int* derr, cudaStream_t s) {
+int launch_interp_weights(const LevelV<T>& fine, bool nine, int* derr, int level, cudaStream_t s) {
   const int ncx = (fine.nx - 1) / 2, ncy = (fine.ny - 1) / 2;
   dim3 grid(cdiv(ncx + 1, 128), ncy + 1);
   if (nine)
-    k_interp_weights<T, true><<<grid, 128, 0, s>>>(fine, ncx, ncy, derr);
+    k_interp_weights<T, true><<<grid, 128, 0, s>>>(fine, ncx, ncy, derr, level);
   else
-    k_interp_weights<T, false><<<grid, 128, 0, s>>>(fine, ncx, ncy, derr);
+    k_interp_weights<T, false><<<grid, 128, 0, s>>>(fine, ncx, ncy, derr, level);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : BMG_ECUDA;
 }
@@ -374,8 +396,8 @@ void launch_assemble_backward(const double* k, const double* u, const double* la
 
 template int launch_assemble<double>(const double*, int, int, LevelV<double>, double*, int*,
                                      cudaStream_t);
-template int launch_interp_weights<double>(const LevelV<double>&, bool, int*, cudaStream_t);
-template int launch_interp_weights<float>(const LevelV<float>&, bool, int*, cudaStream_t);
+template int launch_interp_weights<double>(const LevelV<double>&, bool, int*, int, cudaStream_t);
+template int launch_interp_weights<float>(const LevelV<float>&, bool, int*, int, cudaStream_t);
 template int launch_rap<double>(const LevelV<double>&, bool, LevelV<double>, cudaStream_t);
 template int launch_rap<float>(const LevelV<float>&, bool, LevelV<float>, cudaStream_t);
 template void launch_pack<double>(const double*, double*, int, int, int, cudaStream_t);

@@ -70,3 +70,20 @@ def interp_planes(p, nxf, nyf):
         planes[k][ok] = np.asarray(csr[f, c]).ravel()
         valid[k] = ok
     return planes, valid
+
+
+def nine_from_five(planes):
+    """The library's symmetric 5-plane export (C, W, S, SW, NW) as the
+    oracle's 9-plane stencil: E(i,j) = W(i+1,j), N(i,j) = S(i,j+1),
+    NE(i,j) = SW(i+1,j+1), SE(i,j) = NW(i+1,j-1)."""
+    st = {d: np.array(planes[d], dtype=np.float64) for d in ("C", "W", "S", "SW", "NW")}
+    ny, nx = st["C"].shape
+    st["E"] = np.zeros((ny, nx))
+    st["E"][:, :-1] = st["W"][:, 1:]
+    st["N"] = np.zeros((ny, nx))
+    st["N"][:-1, :] = st["S"][1:, :]
+    st["NE"] = np.zeros((ny, nx))
+    st["NE"][:-1, :-1] = st["SW"][1:, 1:]
+    st["SE"] = np.zeros((ny, nx))
+    st["SE"][1:, :-1] = st["NW"][:-1, 1:]
+    return st
