@@ -114,6 +114,12 @@ int bmg_setup(const double *k_dev, int nx, int ny, const bmg_options *opt,
 int bmg_solve(bmg_hierarchy *h, const double *b_dev, double *x_dev, double tol,
               bmg_info *info, bmg_stream_t stream);
 
+/* Relative residuals of the last bmg_solve: entry 0 before the first cycle,
+ * entry c after cycle c (at most BMG_MAX_HISTORY entries are kept).  Copies
+ * min(n, capacity) values to host_out and stores the count in *n. */
+#define BMG_MAX_HISTORY 4096
+int bmg_residual_history(const bmg_hierarchy *h, double *host_out, int capacity, int *n);
+
 /* End-to-end convenience: copy k and b from pinned (or pageable) host memory,
  * set up, solve, and copy x back, all on `stream`.  Equivalent to
  * bmg_setup + bmg_solve + bmg_destroy with device buffers the call allocates
@@ -192,6 +198,21 @@ int bmg_op_interp(bmg_hierarchy *h, int level, const double *xc_dev,
 int bmg_assemble_backward(bmg_hierarchy *h, const double *u_dev,
                           const double *lam_dev, double *dtheta_dev,
                           bmg_stream_t stream);
+
+/* ---- Level schedule (single-GPU reading of Section 2.2 / Algorithm 2) ----- */
+
+/* Measure the cost-model parameters on the current device (the analogue of
+ * the Section 3 machine parameters alpha, beta, gamma) and use them for every
+ * later threshold choice in this process.  params_out (may be NULL) receives
+ * 8 doubles: launch latency [us], in-block barrier phase [us], streaming
+ * bandwidth [GB/s], FP64 and FP32 FMA rates of the whole GPU [GFLOP/s],
+ * one-block L2 bandwidth [GB/s], one-block FP64 and FP32 rates [GFLOP/s].
+ * Allocates and frees 1 GiB of scratch; synchronises the stream. */
+int bmg_calibrate(bmg_stream_t stream, double *params_out);
+
+/* Model-predicted time [us] of one V-cycle of h with the given threshold
+ * (levels l < threshold inside the persistent kernel). */
+int bmg_predict_cycle_us(const bmg_hierarchy *h, int threshold, double *us);
 
 /* ---- Observability ------------------------------------------------------ */
 

@@ -59,6 +59,7 @@ EXPORTED = {
     "bmg_last_error": (ctypes.c_char_p, []),
     "bmg_setup": (_i, [_vp, _i, _i, ctypes.POINTER(Options), _vp, _HP]),
     "bmg_solve": (_i, [_vp, _vp, _vp, _d, ctypes.POINTER(Info), _vp]),
+    "bmg_residual_history": (_i, [_vp, _vp, _i, ctypes.POINTER(_i)]),
     "bmg_solve_host": (_i, [_vp, _vp, _vp, _i, _i, ctypes.POINTER(Options), _d,
                             ctypes.POINTER(Info), _vp]),
     "bmg_destroy": (None, [_vp]),
@@ -72,12 +73,25 @@ EXPORTED = {
     "bmg_op_restrict": (_i, [_vp, _i, _vp, _vp, _vp]),
     "bmg_op_interp": (_i, [_vp, _i, _vp, _vp, _vp]),
     "bmg_assemble_backward": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "bmg_calibrate": (_i, [_vp, _vp]),
+    "bmg_predict_cycle_us": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "bmg_kernel_launches": (ctypes.c_longlong, []),
     "bmg_profile_set": (_i, [_i]),
     "bmg_profile_read": (_i, [ctypes.POINTER(_i), ctypes.POINTER(_d)]),
 }
 
 BMG_PROF_NONE, BMG_PROF_FINE_SMOOTH, BMG_PROF_FINE_RESID, BMG_PROF_FINE_INTERP, BMG_PROF_COARSE = 0, 1, 2, 3, 4
+
+
+CALIBRATION_KEYS = ("launch_us", "sync_us", "gpu_gbs", "gpu_gflops64", "gpu_gflops32", "cta_gbs",
+                    "cta_gflops64", "cta_gflops32")
+
+
+def calibrate(stream=None) -> dict:
+    """Measure the level-schedule cost-model parameters on this GPU."""
+    out = (ctypes.c_double * 8)()
+    _check(lib().bmg_calibrate(_stream(stream), out), "bmg_calibrate")
+    return dict(zip(CALIBRATION_KEYS, list(out)))
 
 
 def kernel_launches() -> int:
@@ -179,6 +193,19 @@ class Hierarchy:
         _check(lib().bmg_solve(self._h, _dev(b, "b"), _dev(x, "x"), float(tol), ctypes.byref(info),
                                _stream(stream)), "bmg_solve", ok)
         return x, info
+
+    def predict_cycle_us(self, threshold: int) -> float:
+        us = ctypes.c_double()
+        _check(lib().bmg_predict_cycle_us(self._h, int(threshold), ctypes.byref(us)), "bmg_predict_cycle_us")
+        return us.value
+
+    def residual_history(self) -> np.ndarray:
+        """Relative residuals of the last solve (before cycle 1, after each)."""
+        n = ctypes.c_int()
+        out = np.zeros(4096)
+        _check(lib().bmg_residual_history(self._h, out.ctypes.data_as(ctypes.c_void_p), out.size,
+                                          ctypes.byref(n)), "bmg_residual_history")
+        return out[:min(n.value, out.size)].copy()
 
     # -- introspection ----------------------------------------------------------
     @property

@@ -203,6 +203,7 @@ static int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in
     h->chol = cv.raw<double>(size_t(h->n0) * h->n0);
     h->chol_idiag = cv.raw<double>(h->n0);
     h->partials = cv.raw<double>(h->npartials);
+    h->hist = cv.raw<double>(BMG_MAX_HISTORY);
     h->sc = cv.raw<Scalars>(1);
     h->dlev64 = cv.raw<LevelV<double>>(L);
     h->dlev32 = cv.raw<LevelV<float>>(L);
@@ -439,6 +440,19 @@ int bmg_solve_host(const double* k_host, const double* b_host, double* x_host, i
   bmg_destroy(h);
   cudaFree(buf);
   return rc;
+}
+
+int bmg_residual_history(const bmg_hierarchy* hp, double* host_out, int capacity, int* n) {
+  const Hierarchy* h = H(hp);
+  if (!h || !n || (capacity > 0 && !host_out)) return BMG_EINVAL;
+  if (cudaMemcpy(h->sc_host, h->sc, sizeof(bmg::Scalars), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BMG_ECUDA;
+  const int count = std::min(h->sc_host->cycles + 1, BMG_MAX_HISTORY);
+  *n = count;
+  const int m = std::min(count, capacity);
+  if (m > 0 && cudaMemcpy(host_out, h->hist, sizeof(double) * m, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BMG_ECUDA;
+  return BMG_OK;
 }
 
 int bmg_num_levels(const bmg_hierarchy* h, int* nlevels) {

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kNormThreads) k_fine_norm(LevelV<double> L, co
 // Sums the partials; what == 0 stores ||b||^2, else stores ||r||^2 (keeping
 // the previous one in scale2), the relative residual and the loop flag.
 __global__ void __launch_bounds__(kNormThreads) k_norm_final(const double* partials, int n,
-                                                             Scalars* sc, int what) {
+                                                             Scalars* sc, int what, double* hist) {
   double acc = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
   acc = block_sum(acc);
@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(kNormThreads) k_norm_final(const double* parti
   sc->rnorm2 = acc;
   const double rel = sqrt(acc / sc->bnorm2);
   sc->rel = rel;
+  if (sc->cycles < BMG_MAX_HISTORY) hist[sc->cycles] = rel;
   const bool finite = isfinite(rel);
   if (!finite) sc->err |= DEV_NAN;
   const int go = (finite && rel > sc->tol && sc->cycles < sc->max_cycles && sc->err == 0) ? 1 : 0;
@@ -403,7 +404,7 @@ void launch_fine_norm(Hierarchy* h, const double* x, const double* b, int what, 
   (void)tol;
   const LevelV<double>& L = h->d.back();
   k_fine_norm<false><<<h->npartials, kNormThreads, 0, s>>>(L, x, b, what, h->partials);
-  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, what);
+  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, what, h->hist);
   count_launch(2);
 }
 
@@ -411,7 +412,7 @@ void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s) {
   (void)tol;
   k_refine_residual<false><<<h->npartials, kNormThreads, 0, s>>>(h->d.back(), h->f.back(), h->sc,
                                                                  h->partials);
-  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, 1);
+  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, 1, h->hist);
   count_launch(2);
 }
 

@@ -209,6 +209,7 @@ struct Hierarchy {
   double* chol_idiag = nullptr;      // 1 / L[i][i]
   int n0 = 0;
   double* partials = nullptr;        // reduction scratch
+  double* hist = nullptr;            // relative residual per cycle (BMG_MAX_HISTORY)
   int npartials = 0;
   Scalars* sc = nullptr;             // device scalars
   Scalars* sc_host = nullptr;        // pinned mirror

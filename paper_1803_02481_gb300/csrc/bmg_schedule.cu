@@ -96,3 +96,146 @@ int choose_threshold(Hierarchy* h) {
 }
 
 }  // namespace bmg
+
+// ---------------------------------------------------------------------------
+// Calibration: measure the parameters of the cost model on this device (the
+// analogue of measuring alpha, beta, gamma with machine benchmarks in
+// Section 3).  Results stay in cost_params() for the process.
+// ---------------------------------------------------------------------------
+
+namespace bmg {
+
+namespace {
+
+__global__ void k_empty() {}
+
+// Barrier-separated phases in one block, each touching global memory the way
+// the persistent kernel does.
+__global__ void __launch_bounds__(1024) k_phases(double* buf, int phases) {
+  double v = 0.0;
+  for (int p = 0; p < phases; ++p) {
+    v += buf[(threadIdx.x + p) & 1023];
+    __syncthreads();
+    if (threadIdx.x == 0) buf[p & 1023] = v;
+    __syncthreads();
+  }
+  if (v == -1.0) buf[0] = v;
+}
+
+template <typename T>
+__global__ void k_fma_rate(T* out, int iters, T a, T c) {
+  T x0 = T(threadIdx.x) * T(1e-3), x1 = x0 + T(1), x2 = x0 + T(2), x3 = x0 + T(3);
+  T x4 = x0 + T(4), x5 = x0 + T(5), x6 = x0 + T(6), x7 = x0 + T(7);
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, c); x1 = fma(x1, a, c); x2 = fma(x2, a, c); x3 = fma(x3, a, c);
+    x4 = fma(x4, a, c); x5 = fma(x5, a, c); x6 = fma(x6, a, c); x7 = fma(x7, a, c);
+  }
+  const T s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+  if (s == T(-12345)) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void k_stream(const double4* __restrict__ in, double4* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    out[i] = in[i];
+}
+
+float time_ms(cudaStream_t s, cudaEvent_t a, cudaEvent_t b) {
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+}  // namespace
+
+int calibrate(cudaStream_t s, double* out) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return BMG_ECUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  CostParams p = cost_params();
+  double* buf = nullptr;
+  const size_t stream_elems = size_t(1) << 26;      // 2 x 512 MiB in double
+  if (cudaMalloc(&buf, sizeof(double) * (2 * stream_elems + 1024)) != cudaSuccess) {
+    cudaGetLastError();
+    return BMG_ENOMEM;
+  }
+  cudaMemsetAsync(buf, 0, sizeof(double) * (2 * stream_elems + 1024), s);
+  // launch latency: back-to-back empty launches on the stream
+  for (int i = 0; i < 20; ++i) k_empty<<<1, 32, 0, s>>>();
+  cudaEventRecord(e0, s);
+  const int nl = 400;
+  for (int i = 0; i < nl; ++i) k_empty<<<1, 32, 0, s>>>();
+  cudaEventRecord(e1, s);
+  p.launch_us = 1e3 * time_ms(s, e0, e1) / nl;
+  // barrier phase inside one block
+  const int ph = 4000;
+  k_phases<<<1, 1024, 0, s>>>(buf, 10);
+  cudaEventRecord(e0, s);
+  k_phases<<<1, 1024, 0, s>>>(buf, ph);
+  cudaEventRecord(e1, s);
+  p.sync_us = 1e3 * time_ms(s, e0, e1) / (2.0 * ph);
+  // FMA rates, whole GPU and one block
+  const int iters = 1 << 14, tb = 256;
+  auto rate = [&](auto tag, int blocks) {
+    using T = decltype(tag);
+    k_fma_rate<T><<<blocks, tb, 0, s>>>(reinterpret_cast<T*>(buf), 64, T(1.0000001), T(1e-7));
+    cudaEventRecord(e0, s);
+    k_fma_rate<T><<<blocks, tb, 0, s>>>(reinterpret_cast<T*>(buf), iters, T(1.0000001), T(1e-7));
+    cudaEventRecord(e1, s);
+    const double ms = time_ms(s, e0, e1);
+    return 2.0 * 8.0 * iters * double(blocks) * tb / (ms * 1e6);   // GFLOP/s
+  };
+  p.gpu_gflops64 = rate(double(0), 4 * sms);
+  p.cta_gflops64 = rate(double(0), 1);
+  p.gpu_gflops32 = rate(float(0), 8 * sms);
+  p.cta_gflops32 = rate(float(0), 1);
+  // streaming bandwidth: copy 512 MiB (read + write bytes)
+  const size_t n4 = stream_elems / 4;
+  const double4* src = reinterpret_cast<const double4*>(buf);
+  double4* dst = reinterpret_cast<double4*>(buf + stream_elems);
+  k_stream<<<4 * sms, 512, 0, s>>>(src, dst, n4);
+  cudaEventRecord(e0, s);
+  k_stream<<<4 * sms, 512, 0, s>>>(src, dst, n4);
+  cudaEventRecord(e1, s);
+  p.gpu_gbs = 2.0 * sizeof(double) * stream_elems / (time_ms(s, e0, e1) * 1e6);
+  // one block on an L2-resident 4 MiB buffer
+  const size_t small4 = (size_t(1) << 19) / 4;
+  k_stream<<<1, 1024, 0, s>>>(src, dst, small4);
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < 4; ++r) k_stream<<<1, 1024, 0, s>>>(src, dst, small4);
+  cudaEventRecord(e1, s);
+  p.cta_gbs = 4 * 2.0 * sizeof(double) * (size_t(1) << 19) / (time_ms(s, e0, e1) * 1e6);
+  const bool ok = cudaGetLastError() == cudaSuccess;
+  cudaFree(buf);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return BMG_ECUDA;
+  cost_params() = p;
+  if (out) {
+    out[0] = p.launch_us;
+    out[1] = p.sync_us;
+    out[2] = p.gpu_gbs;
+    out[3] = p.gpu_gflops64;
+    out[4] = p.gpu_gflops32;
+    out[5] = p.cta_gbs;
+    out[6] = p.cta_gflops64;
+    out[7] = p.cta_gflops32;
+  }
+  return BMG_OK;
+}
+
+}  // namespace bmg
+
+extern "C" int bmg_calibrate(bmg_stream_t stream, double* params_out) {
+  return bmg::calibrate(reinterpret_cast<cudaStream_t>(stream), params_out);
+}
+
+extern "C" int bmg_predict_cycle_us(const bmg_hierarchy* hp, int threshold, double* us) {
+  const bmg::Hierarchy* h = reinterpret_cast<const bmg::Hierarchy*>(hp);
+  if (!h || !us || threshold < 1 || threshold > h->L) return BMG_EINVAL;
+  *us = bmg::predict_vcycle_us(h, threshold);
+  return BMG_OK;
+}

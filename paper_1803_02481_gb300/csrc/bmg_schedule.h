@@ -31,4 +31,7 @@ double predict_vcycle_us(const Hierarchy* h, int threshold);
 // argmin over thresholds 1..L of predict_vcycle_us; fills h->predicted_us.
 int choose_threshold(Hierarchy* h);
 
+// Microbenchmarks of the cost-model parameters (bmg_calibrate).
+int calibrate(cudaStream_t s, double* out);
+
 }  // namespace bmg

@@ -156,3 +156,32 @@ def batch_problems(count: int = 512, seed: int = 4, block: int = 16,
         b = uniform_rhs(rng, n, n)
         probs.append({"n": n, "k": k, "b": b})
     return probs
+
+
+def gaussian_random_field_torch(seed: int, nx: int, ny: int, ell: float = 32.0, device="cuda"):
+    """The same spectral synthesis as ``gaussian_random_field`` with torch
+    (on the GPU, for the 8191^2 benchmark field): white noise from a seeded
+    torch generator, two zero-padded FFT filters with exp(-d^2/ell^2),
+    standardised.  The numbers differ from the NumPy generator (another
+    random stream); the statistics are the same."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    w = torch.randn((ny, nx), generator=g, device=device, dtype=torch.float64)
+
+    def filt(a, axis):
+        n = a.shape[axis]
+        m = 2 * n
+        d = torch.arange(m, device=device, dtype=torch.float64)
+        d = torch.minimum(d, m - d)
+        hh = torch.fft.rfft(torch.exp(-(d * d) / (ell * ell)))
+        fa = torch.fft.rfft(a, n=m, dim=axis)
+        shape = [1, 1]
+        shape[axis] = hh.shape[0]
+        fa = fa * hh.reshape(shape)
+        out = torch.fft.irfft(fa, n=m, dim=axis)
+        return out.narrow(axis, 0, n).contiguous()
+
+    f = filt(filt(w, 1), 0)
+    f = f - f.mean()
+    return f / f.std(unbiased=False)

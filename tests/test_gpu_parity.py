@@ -7,8 +7,10 @@ Tolerances (FP64):
   the oracle and must match exactly;
 * interpolation weights (in [0, 1]): 1e-12 absolute;
 * solves: identical V-cycle counts; final relative residuals within 1e-10 of
-  each other (both are below tol = 1e-10) and, tighter, within 1e-6 relative;
-  iterates within 1e-9 of max|x|.
+  each other (both are below tol = 1e-10) and, tighter, within 1e-13: the
+  relative residual of an iterate is evaluated in FP64 with rounding of order
+  eps * ||(|A| |x|)|| / ||b||, a few hundred ulp here, and the GPU (FMA)
+  and the oracle (no FMA) round differently; iterates within 1e-9 of max|x|.
 """
 import numpy as np
 import pytest
@@ -145,7 +147,8 @@ def test_solve_matches_oracle(name):
     xg = x.cpu().numpy()
     assert info.cycles == ro.cycles, (info.cycles, ro.cycles, ro.history[-3:])
     assert info.rel_resid <= 1e-10 and ro.rel_resid <= 1e-10
-    assert abs(info.rel_resid - ro.rel_resid) <= 1e-6 * ro.rel_resid + 1e-16
+    assert abs(info.rel_resid - ro.rel_resid) <= 1e-10
+    assert abs(info.rel_resid - ro.rel_resid) <= 1e-13
     assert np.abs(xg - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
     # the returned x satisfies the stop test with the oracle's own operator
     st = oracle_hierarchy(name).levels[-1].st
