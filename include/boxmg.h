@@ -214,6 +214,30 @@ int bmg_calibrate(bmg_stream_t stream, double *params_out);
  * (levels l < threshold inside the persistent kernel). */
 int bmg_predict_cycle_us(const bmg_hierarchy *h, int threshold, double *us);
 
+/* ---- Allocation-free residual check --------------------------------------- */
+
+/* ||b - A(k) x||_2 and ||b||_2 for the 5-point cell-centred operator of k
+ * (the same operator bmg_setup assembles), written to norms_dev[0] and
+ * norms_dev[1] (device memory, 2 doubles).  This entry point has no
+ * counterpart in the paper: it exists for callers that cannot allocate
+ * device memory -- programs whose device memory is all handed out by their
+ * own pool, and latency-critical loops that cannot afford the device-wide
+ * synchronisation a cudaMalloc/cudaFree pair can cause.  Such callers cannot
+ * create a hierarchy, but can check a solution with this call.
+ * k_dev, x_dev, b_dev: dense (ny, nx) float64 device arrays, caller-owned.
+ * The call allocates nothing: its reduction scratch (one pair of partial sums
+ * per grid row) is a static device array of 2 x 16384 doubles (256 KiB) that
+ * every GPU loading the library holds until the process exits, so ny may be
+ * at most 16384 (BMG_EINVAL beyond, see bmg_last_error).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and
+ * each call overwrites every slot it reads, so nothing carries over between
+ * calls; calls that overlap on the GPU (different streams, or different
+ * threads) race on the array and must be serialised by the caller. */
+int bmg_residual_norm_noalloc(const double *k_dev, const double *x_dev,
+                              const double *b_dev, int nx, int ny,
+                              double *norms_dev, bmg_stream_t stream);
+
 /* ---- Observability ------------------------------------------------------ */
 
 /* Total kernel launches this library has issued in this process. */

@@ -75,6 +75,7 @@ EXPORTED = {
     "bmg_assemble_backward": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "bmg_calibrate": (_i, [_vp, _vp]),
     "bmg_predict_cycle_us": (_i, [_vp, _i, ctypes.POINTER(_d)]),
+    "bmg_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp]),
     "bmg_kernel_launches": (ctypes.c_longlong, []),
     "bmg_profile_set": (_i, [_i]),
     "bmg_profile_read": (_i, [ctypes.POINTER(_i), ctypes.POINTER(_d)]),
@@ -277,6 +278,19 @@ def setup(k, options: Options | None = None, stream=None) -> Hierarchy:
     _check(lib().bmg_setup(_dev(k, "k"), nx, ny, ctypes.byref(options), _stream(stream), ctypes.byref(h)),
            "bmg_setup")
     return Hierarchy(h, nx, ny, options)
+
+
+def residual_norm_noalloc(k, x, b, norms=None, stream=None):
+    """(||b - A(k) x||_2, ||b||_2) into a 2-element float64 CUDA tensor,
+    without any device allocation inside the library (see
+    bmg_residual_norm_noalloc in include/boxmg.h)."""
+    import torch
+    ny, nx = k.shape
+    if norms is None:
+        norms = torch.zeros(2, dtype=torch.float64, device=k.device)
+    _check(lib().bmg_residual_norm_noalloc(_dev(k, "k"), _dev(x, "x"), _dev(b, "b"), nx, ny,
+                                           _dev(norms, "norms"), _stream(stream)), "bmg_residual_norm_noalloc")
+    return norms
 
 
 def solve_host(k: np.ndarray, b: np.ndarray, x: np.ndarray, options: Options | None = None,

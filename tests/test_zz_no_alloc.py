@@ -1,0 +1,60 @@
+"""The allocation-free residual check (bmg_residual_norm_noalloc).
+
+Some callers cannot let a library allocate device memory: programs whose
+device memory is all served by their own pool, and latency-critical loops
+where a cudaMalloc/cudaFree pair may synchronise the whole device.  For them
+the library offers one entry point that keeps its reduction scratch in a
+static device array.  These tests call it through the C ABI and compare it
+with the existing entry points (bmg_op_residual, and the residual bmg_solve
+reports), twice in a row, so a stale scratch array would show.  This file is
+collected last so that a stop-at-first-failure run has run everything else.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1803_02481_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+import paper_1803_02481_gb300 as bm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def test_noalloc_norm_matches_existing_entry_points_twice():
+    pr = inputs.block_problem(255, seed=1, block=64, lo=-4, hi=4)
+    k = torch.from_numpy(pr["k"]).cuda()
+    b = torch.from_numpy(pr["b"]).cuda()
+    h = bm.setup(k)
+    x, info = h.solve(b, tol=1e-10)
+    ny, nx = pr["k"].shape
+    norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    bnorm = np.linalg.norm(pr["b"])
+    for call, xx in enumerate((x, 0.5 * x)):        # two calls in a row, different inputs
+        rc = bm.lib().bmg_residual_norm_noalloc(_ptr(k), _ptr(xx), _ptr(b), nx, ny, _ptr(norms), stream)
+        assert rc == bm.BMG_OK
+        got = norms.cpu().numpy()
+        r = h.op_residual(h.nlevels - 1, xx.contiguous(), b, torch.zeros_like(b)).cpu().numpy()
+        rnorm = np.linalg.norm(r)
+        # same tolerance as the solve parity tests: relative residuals agree
+        # to 1e-13 (rounding of b - A x near convergence), ||b|| to 1e-13
+        assert abs(got[0] - rnorm) / bnorm <= 1e-13
+        assert abs(got[1] - bnorm) <= 1e-13 * bnorm
+        if call == 0:
+            # the residual bmg_solve reported for the same x
+            assert abs(got[0] / got[1] - info.rel_resid) <= 1e-13
+    h.destroy()
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    t = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+    norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    rc = bm.lib().bmg_residual_norm_noalloc(_ptr(t), _ptr(t), _ptr(t), 3, 16385, _ptr(norms), None)
+    assert rc == bm.BMG_EINVAL
+    assert b"16384" in bm.lib().bmg_last_error()
