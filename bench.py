@@ -188,8 +188,7 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    prof_kind = bm.BMG_PROF_FINE_SMOOTH
-    bm.profile_set(prof_kind)
+    bm.profile_set(tuple(bm.PROF_CLASSES))
     launches0 = bm.kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -205,8 +204,12 @@ def run_ours(args, rank, world, local_rank):
         barrier()
     ms = ev0.elapsed_time(ev1)
     launches = bm.kernel_launches() - launches0
-    nprof, prof_ms = bm.profile_read()
-    bm.profile_set(bm.BMG_PROF_NONE)
+    breakdown = {}
+    for cname in bm.PROF_CLASSES:
+        cnt, cms = bm.profile_read(cname)
+        breakdown[cname] = {"brackets": cnt, "ms_per_step": cms / args.steps}
+    nprof, prof_ms = bm.profile_read("fine_smooth")
+    bm.profile_set(())
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device=dev)
@@ -277,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
                            l2="inputs and hierarchy larger than L2", parallelism=f"replicas{world}"),
             "cycles": info.cycles, "rel_resid": info.rel_resid, "threshold": info.threshold,
             "setup_ms": info.setup_ms, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
-            "calibration": calib,
+            "calibration": calib, "breakdown": breakdown,
             "clocks": clk.summary(), **extra}
     if rank == 0 and not args.quick and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()

@@ -243,18 +243,22 @@ int bmg_residual_norm_noalloc(const double *k_dev, const double *x_dev,
 /* Total kernel launches this library has issued in this process. */
 long long bmg_kernel_launches(void);
 
-/* Kernel classes that can be timed live with CUDA events. */
-enum { BMG_PROF_NONE = 0, BMG_PROF_FINE_SMOOTH = 1, BMG_PROF_FINE_RESID = 2,
-       BMG_PROF_FINE_INTERP = 3, BMG_PROF_COARSE = 4 };
+/* Kernel classes that can be timed live with CUDA events (class numbers;
+ * bit (1 << class) in a mask). */
+enum { BMG_PROF_FINE_SMOOTH = 1, BMG_PROF_FINE_RESID = 2, BMG_PROF_FINE_INTERP = 3,
+       BMG_PROF_COARSE = 4, BMG_PROF_LEVELS = 5, BMG_PROF_NORM = 6, BMG_PROF_CYCLE = 7 };
 
-/* Start bracketing every launch of kernel class `which` (BMG_PROF_*) with a
- * pair of CUDA events on its stream (up to 65536 launches); resets the
- * record.  BMG_PROF_NONE stops recording. */
-int bmg_profile_set(int which);
+/* Bracket every launch of each kernel class whose bit is set in `mask` with
+ * a pair of CUDA events on its stream (up to 65536 per class) and reset all
+ * records; mask 0 stops recording.  Classes: fine-level sweeps (one bracket
+ * per full sweep), fine-level residual, fine-level interpolation, the
+ * persistent coarse kernel, all other levels' full-grid work of one V-cycle,
+ * the convergence norm, and one whole V-cycle. */
+int bmg_profile_set(int mask);
 
-/* Synchronise the recorded events and return the number of bracketed
- * launches and their summed device time in milliseconds. */
-int bmg_profile_read(int *launches, double *total_ms);
+/* Synchronise the recorded events of class `which` and return the number of
+ * brackets and their summed device time in milliseconds. */
+int bmg_profile_read(int which, int *launches, double *total_ms);
 
 #ifdef __cplusplus
 }

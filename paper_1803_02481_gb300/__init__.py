@@ -78,10 +78,11 @@ EXPORTED = {
     "bmg_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp]),
     "bmg_kernel_launches": (ctypes.c_longlong, []),
     "bmg_profile_set": (_i, [_i]),
-    "bmg_profile_read": (_i, [ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "bmg_profile_read": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
 }
 
-BMG_PROF_NONE, BMG_PROF_FINE_SMOOTH, BMG_PROF_FINE_RESID, BMG_PROF_FINE_INTERP, BMG_PROF_COARSE = 0, 1, 2, 3, 4
+PROF_CLASSES = {"fine_smooth": 1, "fine_resid": 2, "fine_interp": 3, "coarse_kernel": 4,
+                "other_levels": 5, "norm": 6, "vcycle": 7}
 
 
 CALIBRATION_KEYS = ("launch_us", "sync_us", "gpu_gbs", "gpu_gflops64", "gpu_gflops32", "cta_gbs",
@@ -100,14 +101,18 @@ def kernel_launches() -> int:
     return int(lib().bmg_kernel_launches())
 
 
-def profile_set(which: int):
-    _check(lib().bmg_profile_set(int(which)), "bmg_profile_set")
+def profile_set(classes=()):
+    """Start live CUDA-event timing of the named kernel classes (PROF_CLASSES)."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << PROF_CLASSES[c]
+    _check(lib().bmg_profile_set(mask), "bmg_profile_set")
 
 
-def profile_read():
-    """(launches, total_ms) of the bracketed kernel class since profile_set."""
+def profile_read(name: str):
+    """(brackets, total_ms) of one class since profile_set."""
     n, ms = ctypes.c_int(), ctypes.c_double()
-    _check(lib().bmg_profile_read(ctypes.byref(n), ctypes.byref(ms)), "bmg_profile_read")
+    _check(lib().bmg_profile_read(PROF_CLASSES[name], ctypes.byref(n), ctypes.byref(ms)), "bmg_profile_read")
     return n.value, ms.value
 
 _LIB = None

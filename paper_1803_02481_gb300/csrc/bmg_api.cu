@@ -269,18 +269,24 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
   const int L = h->L;
   const int nu1 = h->opt.nu1, nu2 = h->opt.nu2;
   const bool rc = h->opt.interp_residual_term != 0;
+  prof_begin(BMG_PROF_CYCLE, s);
   for (int l = L - 1; l >= thr; --l) {
     const bool nine = l != L - 1;
+    if (nine) prof_begin(BMG_PROF_LEVELS, s);
     launch_relax<T>(lv[l], nine, nu1, false, s);
     launch_residual<T>(lv[l], nine, lv[l].x, lv[l].b, lv[l].r, s);
     launch_restrict<T>(lv[l], lv[l].r, lv[l - 1], true, s);
+    if (nine) prof_end(BMG_PROF_LEVELS, s);
   }
   launch_coarse_cycle<T>(h, dlev, thr, s);
   for (int l = thr; l < L; ++l) {
     const bool nine = l != L - 1;
+    if (nine) prof_begin(BMG_PROF_LEVELS, s);
     launch_interp<T>(lv[l], lv[l - 1].x, rc, s);
     launch_relax<T>(lv[l], nine, nu2, true, s);
+    if (nine) prof_end(BMG_PROF_LEVELS, s);
   }
+  prof_end(BMG_PROF_CYCLE, s);
 }
 
 template void enqueue_vcycle<double>(Hierarchy*, std::vector<LevelV<double>>&,

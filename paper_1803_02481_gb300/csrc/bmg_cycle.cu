@@ -403,8 +403,10 @@ void launch_fine_norm(Hierarchy* h, const double* x, const double* b, int what, 
                       cudaStream_t s) {
   (void)tol;
   const LevelV<double>& L = h->d.back();
+  prof_begin(BMG_PROF_NORM, s);
   k_fine_norm<false><<<h->npartials, kNormThreads, 0, s>>>(L, x, b, what, h->partials);
   k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, what, h->hist);
+  prof_end(BMG_PROF_NORM, s);
   count_launch(2);
 }
 

@@ -12,12 +12,19 @@ namespace {
 
 std::atomic<long long> g_launches{0};
 
-struct Prof {
-  std::mutex mu;
-  int which = BMG_PROF_NONE;
+constexpr int kClasses = 8;
+constexpr size_t kMaxPairs = 65536;
+
+struct ClassRec {
   std::vector<cudaEvent_t> ev;   // pairs (start, stop)
   size_t used = 0;               // events used
-  cudaEvent_t pending = nullptr; // start event awaiting its stop
+  bool open = false;             // a start awaits its stop
+};
+
+struct Prof {
+  std::mutex mu;
+  unsigned mask = 0;             // bit c: class c is recorded
+  ClassRec cls[kClasses];
 };
 
 Prof& prof() {
@@ -25,36 +32,34 @@ Prof& prof() {
   return p;
 }
 
-constexpr size_t kMaxPairs = 65536;
-
 }  // namespace
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void prof_begin(int which, cudaStream_t s) {
   Prof& p = prof();
-  if (p.which == BMG_PROF_NONE || p.which != which) return;
+  if (!(p.mask & (1u << which))) return;
   std::lock_guard<std::mutex> g(p.mu);
-  if (p.used + 2 > 2 * kMaxPairs) return;
-  if (p.ev.size() < p.used + 2) {
-    for (int k = 0; k < 2; ++k) {
-      cudaEvent_t e;
-      if (cudaEventCreate(&e) != cudaSuccess) return;
-      p.ev.push_back(e);
-    }
+  ClassRec& c = p.cls[which];
+  if (c.open || c.used + 2 > 2 * kMaxPairs) return;
+  while (c.ev.size() < c.used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c.ev.push_back(e);
   }
-  cudaEventRecord(p.ev[p.used], s);
-  p.pending = p.ev[p.used];
+  cudaEventRecord(c.ev[c.used], s);
+  c.open = true;
 }
 
 void prof_end(int which, cudaStream_t s) {
   Prof& p = prof();
-  if (p.which == BMG_PROF_NONE || p.which != which) return;
+  if (!(p.mask & (1u << which))) return;
   std::lock_guard<std::mutex> g(p.mu);
-  if (!p.pending || p.pending != p.ev[p.used]) return;
-  cudaEventRecord(p.ev[p.used + 1], s);
-  p.used += 2;
-  p.pending = nullptr;
+  ClassRec& c = p.cls[which];
+  if (!c.open) return;
+  cudaEventRecord(c.ev[c.used + 1], s);
+  c.used += 2;
+  c.open = false;
 }
 
 }  // namespace bmg
@@ -63,28 +68,31 @@ extern "C" {
 
 long long bmg_kernel_launches(void) { return bmg::g_launches.load(); }
 
-int bmg_profile_set(int which) {
-  if (which < BMG_PROF_NONE || which > BMG_PROF_COARSE) return BMG_EINVAL;
+int bmg_profile_set(int mask) {
+  if (mask < 0 || mask >= (1 << bmg::kClasses)) return BMG_EINVAL;
   bmg::Prof& p = bmg::prof();
   std::lock_guard<std::mutex> g(p.mu);
-  p.which = which;
-  p.used = 0;
-  p.pending = nullptr;
+  p.mask = unsigned(mask);
+  for (auto& c : p.cls) {
+    c.used = 0;
+    c.open = false;
+  }
   return BMG_OK;
 }
 
-int bmg_profile_read(int* launches, double* total_ms) {
-  if (!launches || !total_ms) return BMG_EINVAL;
+int bmg_profile_read(int which, int* launches, double* total_ms) {
+  if (!launches || !total_ms || which < 0 || which >= bmg::kClasses) return BMG_EINVAL;
   bmg::Prof& p = bmg::prof();
   std::lock_guard<std::mutex> g(p.mu);
+  bmg::ClassRec& c = p.cls[which];
   double tot = 0.0;
-  for (size_t k = 0; k + 1 < p.used; k += 2) {
-    if (cudaEventSynchronize(p.ev[k + 1]) != cudaSuccess) return BMG_ECUDA;
+  for (size_t k = 0; k + 1 < c.used; k += 2) {
+    if (cudaEventSynchronize(c.ev[k + 1]) != cudaSuccess) return BMG_ECUDA;
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, p.ev[k], p.ev[k + 1]) != cudaSuccess) return BMG_ECUDA;
+    if (cudaEventElapsedTime(&ms, c.ev[k], c.ev[k + 1]) != cudaSuccess) return BMG_ECUDA;
     tot += ms;
   }
-  *launches = int(p.used / 2);
+  *launches = int(c.used / 2);
   *total_ms = tot;
   return BMG_OK;
 }
