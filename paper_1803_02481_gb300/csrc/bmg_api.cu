@@ -7,8 +7,10 @@
 #include "bmg_internal.h"
 #include "bmg_schedule.h"
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <utility>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -82,6 +84,7 @@ void carve_levels(Carver& cv, const std::vector<Geom>& geo, int first, std::vect
     L.SW = nine ? cv.plane<T>(g) : nullptr;
     L.NW = nine ? cv.plane<T>(g) : nullptr;
     L.x = cv.plane<T>(g);
+    L.x2 = cv.plane<T>(g);
     L.b = cv.plane<T>(g);
     L.r = cv.plane<T>(g);
     if (l >= 1 && i >= 1) {
@@ -190,7 +193,7 @@ static int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in
     h->geo64.push_back(make_geom<double>(q.first, q.second));
     h->geo32.push_back(make_geom<float>(q.first, q.second));
   }
-  h->npartials = 2 * 152;
+  h->npartials = 4 * 152;
 
   // Two passes: size, then carve.
   std::vector<Geom> g64 = fp32 ? std::vector<Geom>{h->geo64.back()} : h->geo64;
@@ -269,11 +272,23 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
   const int L = h->L;
   const int nu1 = h->opt.nu1, nu2 = h->opt.nu2;
   const bool rc = h->opt.interp_residual_term != 0;
+  // Sweeps write the other iterate buffer; with nu1 + nu2 odd the
+  // interpolation also writes out of place, so every level's iterate is back
+  // in lv[l].x when the cycle ends and every cycle issues the same launches.
+  const bool interp_oop = ((nu1 + nu2) & 1) != 0;
+  auto sweep = [&](int l, bool reverse) {
+    LevelV<T>& V = lv[l];
+    const bool nine = l != L - 1;
+    if (!nine) prof_begin(BMG_PROF_FINE_SMOOTH, s);
+    launch_sweep<T>(V, nine, reverse, V.x, V.x2, s);
+    if (!nine) prof_end(BMG_PROF_FINE_SMOOTH, s);
+    std::swap(V.x, V.x2);
+  };
   prof_begin(BMG_PROF_CYCLE, s);
   for (int l = L - 1; l >= thr; --l) {
     const bool nine = l != L - 1;
     if (nine) prof_begin(BMG_PROF_LEVELS, s);
-    launch_relax<T>(lv[l], nine, nu1, false, s);
+    for (int k = 0; k < nu1; ++k) sweep(l, false);
     launch_residual<T>(lv[l], nine, lv[l].x, lv[l].b, lv[l].r, s);
     launch_restrict<T>(lv[l], lv[l].r, lv[l - 1], true, s);
     if (nine) prof_end(BMG_PROF_LEVELS, s);
@@ -282,8 +297,13 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
   for (int l = thr; l < L; ++l) {
     const bool nine = l != L - 1;
     if (nine) prof_begin(BMG_PROF_LEVELS, s);
-    launch_interp<T>(lv[l], lv[l - 1].x, rc, s);
-    launch_relax<T>(lv[l], nine, nu2, true, s);
+    if (interp_oop) {
+      launch_interp<T>(lv[l], lv[l - 1].x, rc, s, lv[l].x2);
+      std::swap(lv[l].x, lv[l].x2);
+    } else {
+      launch_interp<T>(lv[l], lv[l - 1].x, rc, s);
+    }
+    for (int k = 0; k < nu2; ++k) sweep(l, true);
     if (nine) prof_end(BMG_PROF_LEVELS, s);
   }
   prof_end(BMG_PROF_CYCLE, s);
@@ -570,7 +590,10 @@ int bmg_op_relax(bmg_hierarchy* hp, int level, double* x, const double* b, int n
   auto& L = h->d[level];
   bmg::launch_pack<double>(x, L.x, L.nx, L.ny, L.pitch, s);
   bmg::launch_pack<double>(b, L.b, L.nx, L.ny, L.pitch, s);
-  bmg::launch_relax<double>(L, level != h->L - 1, nu, reverse != 0, s);
+  for (int k = 0; k < nu; ++k) {
+    bmg::launch_sweep<double>(L, level != h->L - 1, reverse != 0, L.x, L.x2, s);
+    std::swap(L.x, L.x2);
+  }
   bmg::launch_unpack<double>(L.x, x, L.nx, L.ny, L.pitch, s);
   return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;
 }

@@ -24,23 +24,6 @@ __host__ __device__ constexpr unsigned rb_mask(int c) { return c == 0 ? 0x9u : 0
 __host__ __device__ constexpr unsigned four_mask(int c) { return 1u << c; }
 
 template <typename T, bool NINE>
-__global__ void k_relax_colour(LevelV<T> L, unsigned mask) {
-  const int ii = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jj = blockIdx.y;
-#pragma unroll
-  for (int pj = 0; pj < 2; ++pj) {
-#pragma unroll
-    for (int pi = 0; pi < 2; ++pi) {
-      if (!(mask & (1u << (2 * pj + pi)))) continue;
-      const int i = 1 + pi + 2 * ii, j = 1 + pj + 2 * jj;
-      if (i > L.nx || j > L.ny) continue;
-      const int o = j * L.pitch + i;
-      L.x[o] = gs_value<T, NINE>(L, L.x, L.b[o], o);
-    }
-  }
-}
-
-template <typename T, bool NINE>
 __global__ void k_residual(LevelV<T> L, const T* __restrict__ x, const T* __restrict__ b,
                            T* __restrict__ r) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
@@ -62,7 +45,7 @@ __global__ void k_restrict(LevelV<T> F, const T* __restrict__ r, LevelV<T> Cc, i
 }
 
 template <typename T>
-__global__ void k_interp(LevelV<T> F, const T* __restrict__ xc, int add_rc) {
+__global__ void k_interp(LevelV<T> F, const T* __restrict__ xc, int add_rc, T* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y + 1;
   if (i > F.nx) return;
@@ -71,7 +54,7 @@ __global__ void k_interp(LevelV<T> F, const T* __restrict__ xc, int add_rc) {
   // Section 3 interpolation equations: + r/C at points that are not coarse
   // points (r is the residual computed after pre-smoothing).
   if (add_rc && ((i | j) & 1)) corr = fma(F.r[o], F.iC[o], corr);
-  F.x[o] = F.x[o] + corr;
+  out[o] = F.x[o] + corr;
 }
 
 // ---------------------------------------------------------------------------
@@ -333,24 +316,6 @@ __global__ void k_refine_update(LevelV<double> L, LevelV<float> F, const Scalars
 // ---------------------------------------------------------------------------
 
 template <typename T>
-void launch_relax(const LevelV<T>& L, bool nine, int nu, bool reverse, cudaStream_t s) {
-  const dim3 grid(cdiv((L.nx + 1) / 2, kTB), (L.ny + 1) / 2);
-  const int nc = nine ? 4 : 2;
-  for (int sw = 0; sw < nu; ++sw) {
-    if (!nine) prof_begin(BMG_PROF_FINE_SMOOTH, s);
-    for (int k = 0; k < nc; ++k) {
-      const int c = reverse ? nc - 1 - k : k;
-      if (nine)
-        k_relax_colour<T, true><<<grid, kTB, 0, s>>>(L, four_mask(c));
-      else
-        k_relax_colour<T, false><<<grid, kTB, 0, s>>>(L, rb_mask(c));
-    }
-    if (!nine) prof_end(BMG_PROF_FINE_SMOOTH, s);
-  }
-  count_launch(nu * nc);
-}
-
-template <typename T>
 void launch_residual(const LevelV<T>& L, bool nine, const T* x, const T* b, T* r,
                      cudaStream_t s) {
   const dim3 grid(cdiv(L.nx, kTB), L.ny);
@@ -372,11 +337,11 @@ void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool z
 }
 
 template <typename T>
-void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s) {
+void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s, T* out) {
   const dim3 grid(cdiv(fine.nx, kTB), fine.ny);
   const bool finest = fine.SW == nullptr;
   if (finest) prof_begin(BMG_PROF_FINE_INTERP, s);
-  k_interp<T><<<grid, kTB, 0, s>>>(fine, xc, add_r_over_c ? 1 : 0);
+  k_interp<T><<<grid, kTB, 0, s>>>(fine, xc, add_r_over_c ? 1 : 0, out ? out : fine.x);
   if (finest) prof_end(BMG_PROF_FINE_INTERP, s);
   count_launch();
 }
@@ -424,8 +389,6 @@ void launch_refine_update(Hierarchy* h, cudaStream_t s) {
   count_launch();
 }
 
-template void launch_relax<double>(const LevelV<double>&, bool, int, bool, cudaStream_t);
-template void launch_relax<float>(const LevelV<float>&, bool, int, bool, cudaStream_t);
 template void launch_residual<double>(const LevelV<double>&, bool, const double*, const double*,
                                       double*, cudaStream_t);
 template void launch_residual<float>(const LevelV<float>&, bool, const float*, const float*,
@@ -434,8 +397,9 @@ template void launch_restrict<double>(const LevelV<double>&, const double*, Leve
                                       cudaStream_t);
 template void launch_restrict<float>(const LevelV<float>&, const float*, LevelV<float>, bool,
                                      cudaStream_t);
-template void launch_interp<double>(const LevelV<double>&, const double*, bool, cudaStream_t);
-template void launch_interp<float>(const LevelV<float>&, const float*, bool, cudaStream_t);
+template void launch_interp<double>(const LevelV<double>&, const double*, bool, cudaStream_t,
+                                    double*);
+template void launch_interp<float>(const LevelV<float>&, const float*, bool, cudaStream_t, float*);
 template void launch_coarse_cycle<double>(Hierarchy*, const LevelV<double>*, int, cudaStream_t);
 template void launch_coarse_cycle<float>(Hierarchy*, const LevelV<float>*, int, cudaStream_t);
 

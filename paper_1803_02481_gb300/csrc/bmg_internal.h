@@ -71,6 +71,7 @@ struct LevelV {
   int nx, ny, pitch;
   T *C, *iC, *W, *S, *SW, *NW;
   T *x, *b, *r;
+  T *x2;               // second iterate buffer (sweeps write out of place)
   T *P[NPW];
   int cpitch;          // pitch of the coarse grid the P planes live on
 };
@@ -82,22 +83,60 @@ struct LevelV {
 
 // Gauss-Seidel update of one point: x = (b + sum_X a_X x_X) * (1/C), the
 // neighbour terms accumulated in the order W, E, S, N, SW, SE, NW, NE.
+// The coefficients of the point are loaded first (GsCoef), then applied to
+// the iterate through an accessor `xa(dx, dy)`; the same arithmetic serves
+// iterates in global memory and in shared-memory tiles, so every kernel
+// produces the same bits.
+template <typename T, bool NINE>
+struct GsCoef {
+  T b, ic, w, e, s, n, sw, se, nw, ne;
+};
+
+template <typename T, bool NINE>
+__device__ __forceinline__ GsCoef<T, NINE> gs_load(const LevelV<T>& L, int o, T bval) {
+  const int p = L.pitch;
+  GsCoef<T, NINE> c;
+  c.b = bval;
+  c.ic = __ldg(L.iC + o);
+  c.w = __ldg(L.W + o);
+  c.e = __ldg(L.W + o + 1);
+  c.s = __ldg(L.S + o);
+  c.n = __ldg(L.S + o + p);
+  if (NINE) {
+    c.sw = __ldg(L.SW + o);
+    c.se = __ldg(L.NW + o + 1 - p);
+    c.nw = __ldg(L.NW + o);
+    c.ne = __ldg(L.SW + o + 1 + p);
+  }
+  return c;
+}
+
+template <typename T, bool NINE, class XA>
+__device__ __forceinline__ T gs_apply(const GsCoef<T, NINE>& c, XA xa) {
+  T acc = c.b;
+  acc = fma(c.w, xa(-1, 0), acc);
+  acc = fma(c.e, xa(1, 0), acc);
+  acc = fma(c.s, xa(0, -1), acc);
+  acc = fma(c.n, xa(0, 1), acc);
+  if (NINE) {
+    acc = fma(c.sw, xa(-1, -1), acc);
+    acc = fma(c.se, xa(1, -1), acc);
+    acc = fma(c.nw, xa(-1, 1), acc);
+    acc = fma(c.ne, xa(1, 1), acc);
+  }
+  return acc * c.ic;
+}
+
+template <typename T, bool NINE, class XA>
+__device__ __forceinline__ T gs_update(const LevelV<T>& L, XA xa, T bval, int o) {
+  return gs_apply<T, NINE>(gs_load<T, NINE>(L, o, bval), xa);
+}
+
 template <typename T, bool NINE>
 __device__ __forceinline__ T gs_value(const LevelV<T>& L, const T* __restrict__ x,
                                       T bval, int o) {
   const int p = L.pitch;
-  T acc = bval;
-  acc = fma(L.W[o], x[o - 1], acc);
-  acc = fma(L.W[o + 1], x[o + 1], acc);
-  acc = fma(L.S[o], x[o - p], acc);
-  acc = fma(L.S[o + p], x[o + p], acc);
-  if (NINE) {
-    acc = fma(L.SW[o], x[o - p - 1], acc);
-    acc = fma(L.NW[o + 1 - p], x[o + 1 - p], acc);
-    acc = fma(L.NW[o], x[o + p - 1], acc);
-    acc = fma(L.SW[o + 1 + p], x[o + 1 + p], acc);
-  }
-  return acc * L.iC[o];
+  return gs_update<T, NINE>(L, [&](int dx, int dy) { return x[o + dx + dy * p]; }, bval, o);
 }
 
 // Residual of one point: r = b - (C x - sum_X a_X x_X).
@@ -245,15 +284,19 @@ template <typename T>
 void launch_unpack(const T* src, double* dst, int nx, int ny, int pitch, cudaStream_t s);
 
 template <typename T>
-void launch_relax(const LevelV<T>& L, bool nine, int nu, bool reverse, cudaStream_t s);
-template <typename T>
 void launch_residual(const LevelV<T>& L, bool nine, const T* x, const T* b, T* r,
                      cudaStream_t s);
 template <typename T>
 void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool zero_x,
                      cudaStream_t s);
 template <typename T>
-void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s);
+void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s,
+                   T* out = nullptr);
+// One multicolour Gauss-Seidel sweep of a level as a single kernel: reads
+// the iterate from xin and writes the swept iterate to xout (xin != xout).
+template <typename T>
+void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* xout,
+                  cudaStream_t s);
 template <typename T>
 void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* levels, int threshold,
                          cudaStream_t s);
