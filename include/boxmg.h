@@ -69,6 +69,9 @@ typedef struct {
                                coarse kernel (1 <= threshold <= L); -1: chosen
                                by the cost model                              */
   int max_cycles;           /* cap on V-cycles (or refinement steps), 200    */
+  int log_coefficients;     /* 1: the coefficient array holds theta = log k and
+                               the assembly uses k = exp(theta) (adjoint
+                               gradients with respect to theta); 0: holds k */
 } bmg_options;
 
 typedef struct {
@@ -91,7 +94,8 @@ const char *bmg_strerror(int code);
 const char *bmg_last_error(void);
 
 /* BoxMG setup (Section 2; Section 5 discretisation).
- * k_dev: cell coefficients k > 0, dense (ny, nx) float64, device.
+ * k_dev: cell coefficients k > 0 (or theta = log k when
+ * opt->log_coefficients), dense (ny, nx) float64, device.
  * Assembles the fine 5-point operator (harmonic face means, 2k on Dirichlet
  * faces, scaled by h^2), builds P_l and A_{l-1} = P_l^T A_l P_l on every
  * level, factors A_0, and fixes the level schedule.  With precision
@@ -119,6 +123,9 @@ int bmg_solve(bmg_hierarchy *h, const double *b_dev, double *x_dev, double tol,
  * min(n, capacity) values to host_out and stores the count in *n. */
 #define BMG_MAX_HISTORY 4096
 int bmg_residual_history(const bmg_hierarchy *h, double *host_out, int capacity, int *n);
+
+/* Change the cycle cap of later bmg_solve calls on h (>= 0). */
+int bmg_set_max_cycles(bmg_hierarchy *h, int max_cycles);
 
 /* End-to-end convenience: copy k and b from pinned (or pageable) host memory,
  * set up, solve, and copy x back, all on `stream`.  Equivalent to

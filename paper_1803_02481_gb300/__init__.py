@@ -28,7 +28,7 @@ MAX_COARSEST = 1024
 class Options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("precision", ctypes.c_int),
                 ("interp_residual_term", ctypes.c_int), ("coarse_threshold", ctypes.c_int),
-                ("max_cycles", ctypes.c_int)]
+                ("max_cycles", ctypes.c_int), ("log_coefficients", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -60,6 +60,7 @@ EXPORTED = {
     "bmg_setup": (_i, [_vp, _i, _i, ctypes.POINTER(Options), _vp, _HP]),
     "bmg_solve": (_i, [_vp, _vp, _vp, _d, ctypes.POINTER(Info), _vp]),
     "bmg_residual_history": (_i, [_vp, _vp, _i, ctypes.POINTER(_i)]),
+    "bmg_set_max_cycles": (_i, [_vp, _i]),
     "bmg_solve_host": (_i, [_vp, _vp, _vp, _i, _i, ctypes.POINTER(Options), _d,
                             ctypes.POINTER(Info), _vp]),
     "bmg_destroy": (None, [_vp]),
@@ -199,6 +200,10 @@ class Hierarchy:
         _check(lib().bmg_solve(self._h, _dev(b, "b"), _dev(x, "x"), float(tol), ctypes.byref(info),
                                _stream(stream)), "bmg_solve", ok)
         return x, info
+
+    def set_max_cycles(self, max_cycles: int):
+        _check(lib().bmg_set_max_cycles(self._h, int(max_cycles)), "bmg_set_max_cycles")
+        self.options.max_cycles = int(max_cycles)
 
     def predict_cycle_us(self, threshold: int) -> float:
         us = ctypes.c_double()

@@ -234,7 +234,8 @@ static int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in
   // Assembly (Section 5), then P and RAP level by level (Section 2).
   int* derr = &h->sc->err;
   LevelV<double>& fine64 = h->d.back();
-  if (launch_assemble<double>(k, nx, ny, fine64, h->kcopy, derr, s)) return fail(BMG_ECUDA);
+  if (launch_assemble<double>(k, nx, ny, fine64, h->kcopy, derr, opt.log_coefficients != 0, s))
+    return fail(BMG_ECUDA);
   if (!fp32) {
     if ((rc = build_coarse<double>(h, h->d, s))) return fail(rc);
     if (launch_coarse_factor(h, &h->d[0], nullptr, s)) return fail(BMG_ECUDA);
@@ -399,6 +400,7 @@ void bmg_default_options(bmg_options* opt) {
   opt->interp_residual_term = 0;
   opt->coarse_threshold = -1;
   opt->max_cycles = 200;
+  opt->log_coefficients = 0;
 }
 
 const char* bmg_last_error(void) { return bmg::g_last_error; }
@@ -466,6 +468,13 @@ int bmg_solve_host(const double* k_host, const double* b_host, double* x_host, i
   bmg_destroy(h);
   cudaFree(buf);
   return rc;
+}
+
+int bmg_set_max_cycles(bmg_hierarchy* hp, int max_cycles) {
+  Hierarchy* h = H(hp);
+  if (!h || max_cycles < 0) return BMG_EINVAL;
+  h->opt.max_cycles = max_cycles;
+  return BMG_OK;
 }
 
 int bmg_residual_history(const bmg_hierarchy* hp, double* host_out, int capacity, int* n) {

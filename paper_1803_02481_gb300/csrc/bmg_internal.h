@@ -269,7 +269,7 @@ void prof_end(int which, cudaStream_t s);
 // Kernel launch wrappers (defined in the .cu files).
 template <typename T>
 int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy,
-                    int* derr, cudaStream_t s);
+                    int* derr, bool log_k, cudaStream_t s);
 template <typename T>
 int launch_interp_weights(const LevelV<T>& fine, bool nine, int* derr, int level, cudaStream_t s);
 template <typename T>

@@ -23,23 +23,28 @@ __device__ __forceinline__ double harmonic(double k1, double k2) {
 
 // One thread per cell.  Writes C, 1/C, W, S of the finest level and a dense
 // copy of k; flags k that is not finite and positive.
+// k of cell q: the input itself, or exp(input) for log-coefficients.
+__device__ __forceinline__ double cell_k(const double* __restrict__ k, size_t q, bool log_k) {
+  return log_k ? exp(k[q]) : k[q];
+}
+
 template <typename T>
 __global__ void k_assemble(const double* __restrict__ k, int nx, int ny, LevelV<T> L,
-                           double* __restrict__ kcopy, int* derr) {
+                           double* __restrict__ kcopy, int* derr, bool log_k) {
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = blockIdx.y;
   if (i0 >= nx) return;
   const size_t q = size_t(j0) * nx + i0;
-  const double kc = k[q];
+  const double kc = cell_k(k, q, log_k);
   if (!(kc > 0.0) || !(kc < INFINITY)) {
     atomicOr(derr, DEV_BADK);
     return;
   }
   kcopy[q] = kc;
-  const double aw = i0 > 0 ? harmonic(k[q - 1], kc) : 0.0;
-  const double ae = i0 < nx - 1 ? harmonic(kc, k[q + 1]) : 0.0;
-  const double as = j0 > 0 ? harmonic(k[q - nx], kc) : 0.0;
-  const double an = j0 < ny - 1 ? harmonic(kc, k[q + nx]) : 0.0;
+  const double aw = i0 > 0 ? harmonic(cell_k(k, q - 1, log_k), kc) : 0.0;
+  const double ae = i0 < nx - 1 ? harmonic(kc, cell_k(k, q + 1, log_k)) : 0.0;
+  const double as = j0 > 0 ? harmonic(cell_k(k, q - nx, log_k), kc) : 0.0;
+  const double an = j0 < ny - 1 ? harmonic(kc, cell_k(k, q + nx, log_k)) : 0.0;
   // boundary faces, in the order west, east, south, north
   double bw = 0.0;
   if (i0 == 0) bw = bw + 2.0 * kc;
@@ -330,8 +335,8 @@ __global__ void k_assemble_backward(const double* __restrict__ k, const double* 
 
 template <typename T>
 int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy, int* derr,
-                    cudaStream_t s) {
-  k_assemble<T><<<dim3(cdiv(nx, kTB), ny), kTB, 0, s>>>(k, nx, ny, L, kcopy, derr);
+                    bool log_k, cudaStream_t s) {
+  k_assemble<T><<<dim3(cdiv(nx, kTB), ny), kTB, 0, s>>>(k, nx, ny, L, kcopy, derr, log_k);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : BMG_ECUDA;
 }
@@ -395,7 +400,7 @@ void launch_assemble_backward(const double* k, const double* u, const double* la
 }
 
 template int launch_assemble<double>(const double*, int, int, LevelV<double>, double*, int*,
-                                     cudaStream_t);
+                                     bool, cudaStream_t);
 template int launch_interp_weights<double>(const LevelV<double>&, bool, int*, int, cudaStream_t);
 template int launch_interp_weights<float>(const LevelV<float>&, bool, int*, int, cudaStream_t);
 template int launch_rap<double>(const LevelV<double>&, bool, LevelV<double>, cudaStream_t);
