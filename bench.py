@@ -223,6 +223,7 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if not args.quick:
         extra["fp64_vs_fp32_refine"] = lognormal_leg(bm, torch, dev, stream, args)
+        extra["batched"] = batch_leg(bm, torch, dev, stream)
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.quick:
@@ -323,6 +324,58 @@ def lognormal_leg(bm, torch, dev, stream, args, n=8191):
     out["speedup_fp32_refine_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["fp32_refine"]["ms_per_solve"]
     d = (xs["fp32_refine"] - xs["fp64"]).abs().max() / xs["fp64"].abs().max()
     out["max_rel_diff_fp32_refine_vs_fp64"] = float(d)
+    return out
+
+
+def batch_leg(bm, torch, dev, stream, count=512):
+    """512 independent problems (sides 63..1023, weights 8:4:2:1:1, 16-cell
+    blocks 10^U(-3,3), seed 4) solved to 1e-8: one graph launch of the batched
+    FP32+refinement solver, against the same problems solved one by one
+    (FP32+refinement and plain FP64)."""
+    probs = inputs.batch_problems(count=count, seed=4)
+    ks = [torch.from_numpy(p["k"]).to(dev) for p in probs]
+    bs = [torch.from_numpy(p["b"]).to(dev) for p in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    unknowns = sum(p["n"] ** 2 for p in probs)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch = bm.Batch(ks, bm.default_options(max_cycles=3000), stream=stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    batch.solve(bs, xs, tol=1e-8, stream=stream)
+    reps = 2
+    ev0.record(stream)
+    for _ in range(reps):
+        for x in xs:
+            x.zero_()
+        infos = batch.solve(bs, xs, tol=1e-8, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = ev0.elapsed_time(ev1) / reps
+    batch.destroy()
+    out = {"workload": f"{count} problems, sides 63..1023 (8:4:2:1:1), 16-cell blocks 10^U(-3,3), seed 4, tol 1e-8",
+           "unknowns": unknowns, "batch_setup_s": setup_s,
+           "batched_fp32_refine": {"value": unknowns / (ms_batch / 1e3), "unit": UNIT, "ms_per_solve": ms_batch,
+                                   "max_refinement_steps": max(i.cycles for i in infos),
+                                   "max_rel_resid": max(i.rel_resid for i in infos)}}
+    for name, prec in (("sequential_fp32_refine", bm.BMG_FP32_REFINE), ("sequential_fp64", bm.BMG_FP64)):
+        opts = bm.default_options(precision=prec, max_cycles=3000)
+        hs = [bm.setup(k, opts, stream=stream) for k in ks]
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for h, b, x in zip(hs, bs, xs):
+            h.solve(b, x, tol=1e-8, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        for h in hs:
+            h.destroy()
+        ms = ev0.elapsed_time(ev1)
+        out[name] = {"value": unknowns / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms}
+    out["speedup_batched_vs_sequential_fp64"] = out["sequential_fp64"]["ms_per_solve"] / ms_batch
     return out
 
 

@@ -221,6 +221,40 @@ int bmg_calibrate(bmg_stream_t stream, double *params_out);
  * (levels l < threshold inside the persistent kernel). */
 int bmg_predict_cycle_us(const bmg_hierarchy *h, int threshold, double *us);
 
+/* ---- Batched solves (many independent problems) -------------------------- */
+
+typedef struct bmg_batch bmg_batch; /* opaque, library-owned */
+
+/* Set up nprob independent square problems at once: problem p has side n[p]
+ * (2^m - 1) and coefficients k_dev[p] (dense n[p] x n[p] float64, device).
+ * k_dev and n are host arrays.  Each problem is solved with FP32 V-cycles
+ * (Algorithm 1) inside FP64 iterative refinement (opt->precision is ignored);
+ * levels of side <= 31 run in the persistent coarse kernel, one thread block
+ * per problem.  Setup also picks the tile shape of the batched sweeps for
+ * every level side by timing the candidates on this batch (cached per
+ * process, and in the file named by the environment variable BMG_TUNE_CACHE
+ * if set) and records the refinement loop as one CUDA graph.  Errors as
+ * bmg_setup, naming the failing problem in bmg_last_error. */
+int bmg_batch_setup(int nprob, const double *const *k_dev, const int *n,
+                    const bmg_options *opt, bmg_stream_t stream, bmg_batch **out);
+
+/* Solve every problem to ||b - A x||_2 / ||b||_2 <= tol with ONE launch of
+ * the refinement-loop graph: every V-cycle operation is one launch over all
+ * problems that have a level of that side, problems that have converged
+ * drop out, and the loop ends when none is left.  b_dev[p], x_dev[p]: host
+ * arrays of device pointers to dense n[p] x n[p] float64 arrays (x: initial
+ * guess in, solution out).  per_prob (may be NULL) receives nprob bmg_info
+ * (cycles = refinement steps of that problem).  Returns BMG_OK, or
+ * BMG_ENOCONV / BMG_ENAN if any problem ended that way. */
+int bmg_batch_solve(bmg_batch *b, const double *const *b_dev, double *const *x_dev,
+                    double tol, bmg_info *per_prob, bmg_stream_t stream);
+
+/* Number of problems of a batch. */
+int bmg_batch_size(const bmg_batch *b, int *nprob);
+
+/* Release a batch (NULL is allowed). */
+void bmg_batch_destroy(bmg_batch *b);
+
 /* ---- Allocation-free residual check --------------------------------------- */
 
 /* ||b - A(k) x||_2 and ||b||_2 for the 5-point cell-centred operator of k

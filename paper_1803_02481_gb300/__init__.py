@@ -74,6 +74,10 @@ EXPORTED = {
     "bmg_op_restrict": (_i, [_vp, _i, _vp, _vp, _vp]),
     "bmg_op_interp": (_i, [_vp, _i, _vp, _vp, _vp]),
     "bmg_assemble_backward": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "bmg_batch_setup": (_i, [_i, _vp, _vp, ctypes.POINTER(Options), _vp, _HP]),
+    "bmg_batch_solve": (_i, [_vp, _vp, _vp, _d, _vp, _vp]),
+    "bmg_batch_size": (_i, [_vp, ctypes.POINTER(_i)]),
+    "bmg_batch_destroy": (None, [_vp]),
     "bmg_calibrate": (_i, [_vp, _vp]),
     "bmg_predict_cycle_us": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "bmg_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp]),
@@ -288,6 +292,44 @@ def setup(k, options: Options | None = None, stream=None) -> Hierarchy:
     _check(lib().bmg_setup(_dev(k, "k"), nx, ny, ctypes.byref(options), _stream(stream), ctypes.byref(h)),
            "bmg_setup")
     return Hierarchy(h, nx, ny, options)
+
+
+class Batch:
+    """Many independent square problems solved together (wraps ``bmg_batch*``)."""
+
+    def __init__(self, ks, options: Options | None = None, stream=None):
+        if options is None:
+            options = default_options()
+        self.n = [int(k.shape[0]) for k in ks]
+        self._ks = ks
+        kp = (ctypes.c_void_p * len(ks))(*[_dev(k, "k").value for k in ks])
+        ns = (ctypes.c_int * len(ks))(*self.n)
+        h = ctypes.c_void_p()
+        _check(lib().bmg_batch_setup(len(ks), kp, ns, ctypes.byref(options), _stream(stream), ctypes.byref(h)),
+               "bmg_batch_setup")
+        self._h = h
+
+    def solve(self, bs, xs, tol=1e-8, stream=None, allow_noconv=False):
+        """Solve all problems in place (xs: initial guesses, overwritten).
+        Returns the per-problem Info list."""
+        m = len(self.n)
+        bp = (ctypes.c_void_p * m)(*[_dev(b, "b").value for b in bs])
+        xp = (ctypes.c_void_p * m)(*[_dev(x, "x").value for x in xs])
+        infos = (Info * m)()
+        ok = (BMG_OK, BMG_ENOCONV) if allow_noconv else (BMG_OK,)
+        _check(lib().bmg_batch_solve(self._h, bp, xp, float(tol), infos, _stream(stream)), "bmg_batch_solve", ok)
+        return list(infos)
+
+    def destroy(self):
+        if self._h:
+            lib().bmg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def residual_norm_noalloc(k, x, b, norms=None, stream=None):

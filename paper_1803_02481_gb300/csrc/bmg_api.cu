@@ -141,15 +141,15 @@ static int build_coarse(Hierarchy* h, std::vector<LevelV<T>>& lv, cudaStream_t s
   return BMG_OK;
 }
 
-static void free_hierarchy(Hierarchy* h) {
+void free_hierarchy(Hierarchy* h) {
   if (!h) return;
   if (h->arena) cudaFree(h->arena);
   if (h->sc_host) cudaFreeHost(h->sc_host);
   delete h;
 }
 
-static int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in,
-                      cudaStream_t s, Hierarchy** out) {
+int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaStream_t s,
+               Hierarchy** out) {
   *out = nullptr;
   g_last_error[0] = 0;
   if (!k || !valid_side(nx) || !valid_side(ny)) return BMG_EINVAL;

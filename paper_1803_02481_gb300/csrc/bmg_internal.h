@@ -266,6 +266,11 @@ void count_launch(int n = 1);
 void prof_begin(int which, cudaStream_t s);
 void prof_end(int which, cudaStream_t s);
 
+// Hierarchy lifetime (bmg_api.cu).
+int setup_impl(const double* k, int nx, int ny, const bmg_options* opt, cudaStream_t s,
+               Hierarchy** out);
+void free_hierarchy(Hierarchy* h);
+
 // Kernel launch wrappers (defined in the .cu files).
 template <typename T>
 int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy,

@@ -134,7 +134,7 @@ __global__ void k_fma_rate(T* out, int iters, T a, T c) {
   if (s == T(-12345)) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-__global__ void k_stream(const double4* __restrict__ in, double4* __restrict__ out, size_t n) {
+__global__ void k_stream(const double2* __restrict__ in, double2* __restrict__ out, size_t n) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
     out[i] = in[i];
 }
@@ -193,19 +193,19 @@ int calibrate(cudaStream_t s, double* out) {
   p.gpu_gflops32 = rate(float(0), 8 * sms);
   p.cta_gflops32 = rate(float(0), 1);
   // streaming bandwidth: copy 512 MiB (read + write bytes)
-  const size_t n4 = stream_elems / 4;
-  const double4* src = reinterpret_cast<const double4*>(buf);
-  double4* dst = reinterpret_cast<double4*>(buf + stream_elems);
-  k_stream<<<4 * sms, 512, 0, s>>>(src, dst, n4);
+  const size_t n2 = stream_elems / 2;
+  const double2* src = reinterpret_cast<const double2*>(buf);
+  double2* dst = reinterpret_cast<double2*>(buf + stream_elems);
+  k_stream<<<4 * sms, 512, 0, s>>>(src, dst, n2);
   cudaEventRecord(e0, s);
-  k_stream<<<4 * sms, 512, 0, s>>>(src, dst, n4);
+  k_stream<<<4 * sms, 512, 0, s>>>(src, dst, n2);
   cudaEventRecord(e1, s);
   p.gpu_gbs = 2.0 * sizeof(double) * stream_elems / (time_ms(s, e0, e1) * 1e6);
   // one block on an L2-resident 4 MiB buffer
-  const size_t small4 = (size_t(1) << 19) / 4;
-  k_stream<<<1, 1024, 0, s>>>(src, dst, small4);
+  const size_t small2 = (size_t(1) << 19) / 2;
+  k_stream<<<1, 1024, 0, s>>>(src, dst, small2);
   cudaEventRecord(e0, s);
-  for (int r = 0; r < 4; ++r) k_stream<<<1, 1024, 0, s>>>(src, dst, small4);
+  for (int r = 0; r < 4; ++r) k_stream<<<1, 1024, 0, s>>>(src, dst, small2);
   cudaEventRecord(e1, s);
   p.cta_gbs = 4 * 2.0 * sizeof(double) * (size_t(1) << 19) / (time_ms(s, e0, e1) * 1e6);
   const bool ok = cudaGetLastError() == cudaSuccess;

@@ -1,0 +1,103 @@
+// Tile body of the one-kernel multicolour Gauss-Seidel sweep, shared by the
+// single-problem and the batched kernels.
+//
+// A thread block owns a TX x TY tile.  It loads the old iterate on the tile
+// plus a halo of NC cells into shared memory, then relaxes the colours in
+// order: colour k (0-based) is updated on the tile grown by NC-1-k cells, so
+// the last colour's neighbours of earlier colours are all available without
+// reading another block's new values.  The points a block relaxes outside its
+// tile are recomputed by the neighbouring block from the same old values, so
+// every block sees exactly what an in-place sweep would see.  The new iterate
+// goes to a second buffer (old and new never alias); only the tile is
+// written.  Per-point arithmetic is gs_load/gs_apply.
+#pragma once
+
+#include "bmg_internal.h"
+
+namespace bmg {
+
+// Sub-lattice masks of the colours in sweep order (bit 2*pj + pi: 0-based
+// row parity pj, column parity pi), 4 bits per colour.
+__host__ __device__ constexpr unsigned rb_order(bool reverse) { return reverse ? 0x96u : 0x69u; }
+__host__ __device__ constexpr unsigned four_order(bool reverse) {
+  return reverse ? 0x1248u : 0x8421u;
+}
+
+template <typename T, bool NINE, int TX, int TY, int NT>
+__device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restrict__ xin,
+                                           T* __restrict__ xout, unsigned order, int bx, int by) {
+  constexpr int NC = NINE ? 4 : 2;
+  constexpr int H = NC;
+  constexpr int SX = TX + 2 * H, SY = TY + 2 * H;
+  __shared__ T xs[SY * SX];
+  const int nx = L.nx, ny = L.ny, p = L.pitch;
+  // domain coordinates of shared-memory cell (0, 0)
+  const int ib = bx * TX + 1 - H;
+  const int jb = by * TY + 1 - H;
+
+  for (int e = threadIdx.x; e < SX * SY; e += NT) {
+    const int r = e / SX, c = e - r * SX;
+    const int i = ib + c, j = jb + r;
+    T v = T(0);
+    if (i >= 0 && i <= nx + 1 && j >= 0 && j <= ny + 1) v = xin[j * p + i];
+    xs[e] = v;
+  }
+  __syncthreads();
+
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const unsigned mask = (order >> (4 * k)) & 0xFu;
+    const int ring = NC - 1 - k;
+    const int r0 = H - ring, r1 = H + TY + ring;   // region rows [r0, r1)
+    const int c0 = H - ring, c1 = H + TX + ring;
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl) {
+      if (!(mask & (1u << sl))) continue;
+      const int pj = sl >> 1, pi = sl & 1;
+      // first region row/col whose 0-based domain index has the right parity
+      const int rf = r0 + ((pj + 1 - jb - r0) & 1);
+      const int cf = c0 + ((pi + 1 - ib - c0) & 1);
+      const int nr = (r1 - rf + 1) >> 1, ncol = (c1 - cf + 1) >> 1;
+      const int npts = nr * ncol;
+      // U points per thread per step: all their coefficient loads are issued
+      // before any update, so the loads overlap instead of serialising (a
+      // win for the 9-point stencil; for 5 points the extra registers cost
+      // more occupancy than the overlap gains, measured).
+      constexpr int U = NINE ? 3 : 1;
+      for (int t0 = threadIdx.x; t0 < npts; t0 += NT * U) {
+        GsCoef<T, NINE> cf_[U];
+        int sp[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int t = t0 + u * NT;
+          const int rr = t / ncol;
+          const int r = rf + 2 * rr, c = cf + 2 * (t - rr * ncol);
+          const int i = ib + c, j = jb + r;
+          ok[u] = t < npts && i >= 1 && i <= nx && j >= 1 && j <= ny;
+          sp[u] = r * SX + c;
+          if (ok[u]) {
+            const int o = j * p + i;
+            cf_[u] = gs_load<T, NINE>(L, o, __ldg(L.b + o));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (!ok[u]) continue;
+          T* xp = xs + sp[u];
+          *xp = gs_apply<T, NINE>(cf_[u], [&](int dx, int dy) { return xp[dx + dy * SX]; });
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  for (int e = threadIdx.x; e < TX * TY; e += NT) {
+    const int r = e / TX, c = e - r * TX;
+    const int i = ib + H + c, j = jb + H + r;
+    if (i <= nx && j <= ny) xout[j * p + i] = xs[(r + H) * SX + c + H];
+  }
+}
+
+
+}  // namespace bmg
