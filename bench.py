@@ -188,7 +188,6 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    bm.profile_set(tuple(bm.PROF_CLASSES))
     launches0 = bm.kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -204,10 +203,20 @@ def run_ours(args, rank, world, local_rank):
         barrier()
     ms = ev0.elapsed_time(ev1)
     launches = bm.kernel_launches() - launches0
-    breakdown = {}
+    # One more step with every kernel class bracketed by CUDA events on the
+    # solve stream (this runs the stream-launched path; the timed steps above
+    # run the solve loop as one CUDA graph): per-class breakdown and the
+    # per-launch duration of the fine-level sweep for the roofline.
+    bm.profile_set(tuple(bm.PROF_CLASSES))
+    ev0.record(stream)
+    step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_profiled = ev0.elapsed_time(ev1)
+    breakdown = {"ms_step_stream_launched": ms_profiled}
     for cname in bm.PROF_CLASSES:
         cnt, cms = bm.profile_read(cname)
-        breakdown[cname] = {"brackets": cnt, "ms_per_step": cms / args.steps}
+        breakdown[cname] = {"brackets": cnt, "ms_per_step": cms}
     nprof, prof_ms = bm.profile_read("fine_smooth")
     bm.profile_set(())
     if world > 1:
@@ -224,6 +233,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.quick:
         extra["fp64_vs_fp32_refine"] = lognormal_leg(bm, torch, dev, stream, args)
         extra["batched"] = batch_leg(bm, torch, dev, stream)
+        extra["threshold_sweep"] = threshold_sweep(bm, torch, k, b, stream)
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.quick:
@@ -258,8 +268,9 @@ def run_ours(args, rank, world, local_rank):
     f_hbm = gbs / peaks["hbm_gbs"]
     alu_peak = calib["gpu_gflops64"] if args.precision == "fp64" else calib["gpu_gflops32"]
     f_alu = gfl / alu_peak
-    common = {"kernel": "fine-level red-black Gauss-Seidel sweep (k_relax_colour, 2 launches per sweep)",
+    common = {"kernel": "fine-level red-black Gauss-Seidel sweep (k_sweep, one launch per sweep)",
               "per_launch_ms": sweep_ms, "launches_timed": nprof,
+              "timing": "CUDA events around every fine sweep of one full profiled step on the solve stream",
               "algorithmic_bytes_per_unknown": per_unit_b, "algorithmic_flops_per_unknown": per_unit_f,
               "units_per_launch": n_fine,
               "hbm": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": f_hbm,
@@ -325,6 +336,43 @@ def lognormal_leg(bm, torch, dev, stream, args, n=8191):
     d = (xs["fp32_refine"] - xs["fp64"]).abs().max() / xs["fp64"].abs().max()
     out["max_rel_diff_fp32_refine_vs_fp64"] = float(d)
     return out
+
+
+def threshold_sweep(bm, torch, k, b, stream, cycles=20):
+    """Measured time of one V-cycle for every schedule threshold (levels below
+    it run inside the persistent coarse kernel) next to the cost model's
+    prediction, on the bench workload (the single-GPU analogue of comparing
+    modelled and measured redistribution paths)."""
+    h0 = bm.setup(k, bm.default_options(), stream=stream)
+    nl = h0.nlevels
+    chosen = None
+    h0.destroy()
+    rows = []
+    x = torch.zeros_like(b)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for thr in range(1, nl + 1):
+        h = bm.setup(k, bm.default_options(coarse_threshold=thr, max_cycles=cycles), stream=stream)
+        pred = h.predict_cycle_us(thr)
+        x.zero_()
+        h.solve(b, x, tol=1e-30, stream=stream, allow_noconv=True)
+        x.zero_()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        h.solve(b, x, tol=1e-30, stream=stream, allow_noconv=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        rows.append({"threshold": thr, "measured_us_per_cycle": 1e3 * ms / cycles, "predicted_us_per_cycle": pred})
+        h.destroy()
+    hc = bm.setup(k, bm.default_options(), stream=stream)
+    x.zero_()
+    _, info = hc.solve(b, x, tol=1e-30, stream=stream, allow_noconv=True)
+    chosen = info.threshold
+    hc.destroy()
+    best = min(rows, key=lambda r: r["measured_us_per_cycle"])["threshold"]
+    return {"levels": nl, "model_choice": chosen, "measured_best": best, "rows": rows,
+            "note": "per cycle including the convergence norm and one host read of the stop flag"}
 
 
 def batch_leg(bm, torch, dev, stream, count=512):

@@ -13,6 +13,7 @@
 #include <utility>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -143,6 +144,8 @@ static int build_coarse(Hierarchy* h, std::vector<LevelV<T>>& lv, cudaStream_t s
 
 void free_hierarchy(Hierarchy* h) {
   if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
   if (h->arena) cudaFree(h->arena);
   if (h->sc_host) cudaFreeHost(h->sc_host);
   delete h;
@@ -321,6 +324,79 @@ static int read_scalars(Hierarchy* h, cudaStream_t s) {
   return BMG_OK;
 }
 
+// Record the solve loop of h as one graph (see Hierarchy::graph).  Recording
+// runs on a private stream (the caller's may be the legacy default stream,
+// which cannot capture) and executes nothing.
+static int build_solve_graph(Hierarchy* h) {
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return BMG_ECUDA;
+  const bool fp32 = h->opt.precision == BMG_FP32_REFINE;
+  LevelV<double>& F = h->d.back();
+  int rc = BMG_ECUDA;
+  do {
+    if (cudaGraphCreate(&h->graph, 0) != cudaSuccess) break;
+    if (cudaGraphConditionalHandleCreate(&h->cond, h->graph, 0, cudaGraphCondAssignDefault) !=
+        cudaSuccess)
+      break;
+    if (cudaStreamBeginCaptureToGraph(s, h->graph, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      break;
+    if (fp32)
+      launch_refine_residual(h, 0.0, s, true);
+    else
+      launch_fine_norm(h, F.x, F.b, 1, 0.0, s, true);
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps) != cudaSuccess)
+      break;
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h->cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, h->graph, deps, nullptr, ndeps, &cp) != cudaSuccess) break;
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies) != cudaSuccess)
+      break;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(s, &g) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess)
+      break;
+    if (fp32) {
+      enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s);
+      launch_refine_update(h, s);
+      launch_refine_residual(h, 0.0, s, true);
+    } else {
+      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+      launch_fine_norm(h, F.x, F.b, 1, 0.0, s, true);
+    }
+    if (cudaStreamEndCapture(s, &g) != cudaSuccess) break;
+    if (cudaGraphInstantiate(&h->gexec, h->graph, 0) != cudaSuccess) break;
+    rc = BMG_OK;
+  } while (0);
+  cudaStreamDestroy(s);
+  if (rc != BMG_OK) {
+    cudaGetLastError();
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return rc;
+}
+
+static bool graphs_disabled() {
+  static const bool off = [] {
+    const char* e = std::getenv("BMG_NO_GRAPH");
+    return e && e[0] && e[0] != '0';
+  }();
+  return off;
+}
+
 static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_info* info,
                       cudaStream_t s) {
   if (!h || !b || !x || !(tol > 0.0)) return BMG_EINVAL;
@@ -337,6 +413,28 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
   launch_fine_norm(h, nullptr, F.b, 0, tol, s);
   const bool fp32 = h->opt.precision == BMG_FP32_REFINE;
   int rc = BMG_OK;
+  // Graph path: the whole loop in one launch (not while kernel classes are
+  // being timed with events, which need the stream path).
+  if (!prof_active() && !graphs_disabled()) {
+    if (h->graph_state == 0) h->graph_state = build_solve_graph(h) == BMG_OK ? 1 : -1;
+    if (h->graph_state == 1) {
+      BMG_CUDA(cudaGraphLaunch(h->gexec, s));
+      launch_unpack<double>(F.x, x, h->nx, h->ny, F.pitch, s);
+      if ((rc = read_scalars(h, s))) return rc;
+      const Scalars& r = *h->sc_host;
+      if (r.bnorm2 == 0.0) {
+        BMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * size_t(h->nx) * h->ny, s));
+        BMG_CUDA(cudaStreamSynchronize(s));
+        if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0};
+        return BMG_OK;
+      }
+      if (info) *info = bmg_info{r.cycles, h->threshold, r.rel, h->setup_ms, now_ms() - t0};
+      if (r.err & DEV_NAN) return BMG_ENAN;
+      if (r.err & DEV_TIMEOUT) return BMG_ETIMEOUT;
+      if (!(r.rel <= tol)) return BMG_ENOCONV;
+      return BMG_OK;
+    }
+  }
   if (!fp32) {
     launch_fine_norm(h, F.x, F.b, 1, tol, s);
     if ((rc = read_scalars(h, s))) return rc;

@@ -37,17 +37,32 @@ __global__ void k_restrict(LevelV<T> F, const T* __restrict__ r, LevelV<T> Cc, i
   if (zero_x) Cc.x[c] = T(0);
 }
 
+// One thread per coarse cell (I, J), 0 <= I <= ncx, 0 <= J <= ncy: the four
+// fine points (2I+1..2I+2, 2J+1..2J+2) -- a cell centre, a y-edge, an x-edge
+// and a coarse point -- so every thread does the same work (no divergence on
+// the point type) and the weight planes are read contiguously.
 template <typename T>
 __global__ void k_interp(LevelV<T> F, const T* __restrict__ xc, int add_rc, T* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  const int j = blockIdx.y + 1;
-  if (i > F.nx) return;
-  const int o = j * F.pitch + i;
-  T corr = interp_value<T>(F.P, F.cpitch, xc, i, j);
-  // Section 3 interpolation equations: + r/C at points that are not coarse
-  // points (r is the residual computed after pre-smoothing).
-  if (add_rc && ((i | j) & 1)) corr = fma(F.r[o], F.iC[o], corr);
-  out[o] = F.x[o] + corr;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y;
+  const int ncx = (F.nx - 1) >> 1;
+  if (I > ncx) return;
+#pragma unroll
+  for (int dj = 1; dj <= 2; ++dj) {
+    const int j = 2 * J + dj;
+    if (j > F.ny) continue;
+#pragma unroll
+    for (int di = 1; di <= 2; ++di) {
+      const int i = 2 * I + di;
+      if (i > F.nx) continue;
+      const int o = j * F.pitch + i;
+      T corr = interp_value<T>(F.P, F.cpitch, xc, i, j);
+      // Section 3 interpolation equations: + r/C at points that are not
+      // coarse points (r is the residual computed after pre-smoothing).
+      if (add_rc && ((i | j) & 1)) corr = fma(F.r[o], F.iC[o], corr);
+      out[o] = F.x[o] + corr;
+    }
+  }
 }
 
 template <typename T>
@@ -98,7 +113,9 @@ __global__ void __launch_bounds__(kNormThreads) k_fine_norm(LevelV<double> L, co
 // Sums the partials; what == 0 stores ||b||^2, else stores ||r||^2 (keeping
 // the previous one in scale2), the relative residual and the loop flag.
 __global__ void __launch_bounds__(kNormThreads) k_norm_final(const double* partials, int n,
-                                                             Scalars* sc, int what, double* hist) {
+                                                             Scalars* sc, int what, double* hist,
+                                                             cudaGraphConditionalHandle cond,
+                                                             int use_cond) {
   double acc = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
   acc = block_sum(acc);
@@ -118,6 +135,8 @@ __global__ void __launch_bounds__(kNormThreads) k_norm_final(const double* parti
   const int go = (finite && rel > sc->tol && sc->cycles < sc->max_cycles && sc->err == 0) ? 1 : 0;
   sc->go = go;
   sc->cycles += go;
+  // inside the solve graph this drives the WHILE node
+  if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
 }
 
 // FP32_REFINE: r = b - A x in FP64 on the finest level (partials of ||r||^2)
@@ -182,7 +201,8 @@ void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool z
 
 template <typename T>
 void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s, T* out) {
-  const dim3 grid(cdiv(fine.nx, kTB), fine.ny);
+  const int ncx = (fine.nx - 1) / 2, ncy = (fine.ny - 1) / 2;
+  const dim3 grid(cdiv(ncx + 1, kTB), ncy + 1);
   const bool finest = fine.SW == nullptr;
   if (finest) prof_begin(BMG_PROF_FINE_INTERP, s);
   k_interp<T><<<grid, kTB, 0, s>>>(fine, xc, add_r_over_c ? 1 : 0, out ? out : fine.x);
@@ -209,21 +229,23 @@ void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* dev_levels, int thr, cud
 }
 
 void launch_fine_norm(Hierarchy* h, const double* x, const double* b, int what, double tol,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool in_graph) {
   (void)tol;
   const LevelV<double>& L = h->d.back();
   prof_begin(BMG_PROF_NORM, s);
   k_fine_norm<false><<<h->npartials, kNormThreads, 0, s>>>(L, x, b, what, h->partials);
-  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, what, h->hist);
+  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, what, h->hist, h->cond,
+                                          in_graph ? 1 : 0);
   prof_end(BMG_PROF_NORM, s);
   count_launch(2);
 }
 
-void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s) {
+void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s, bool in_graph) {
   (void)tol;
   k_refine_residual<false><<<h->npartials, kNormThreads, 0, s>>>(h->d.back(), h->f.back(), h->sc,
                                                                  h->partials);
-  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, 1, h->hist);
+  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, 1, h->hist, h->cond,
+                                          in_graph ? 1 : 0);
   count_launch(2);
 }
 

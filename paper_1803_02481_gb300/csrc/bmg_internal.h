@@ -255,6 +255,12 @@ struct Hierarchy {
   LevelV<double>* dlev64 = nullptr;  // device copies of the level views (for
   LevelV<float>* dlev32 = nullptr;   // the persistent coarse kernel)
   double predicted_us[16] = {};      // cost model: V-cycle time per threshold
+  // The solve loop as one CUDA graph: [first residual + stop test] then
+  // WHILE(go) { V-cycle; (refinement update;) residual + stop test }.
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  int graph_state = 0;               // 0 not built, 1 ready, -1 unavailable
   void* arena = nullptr;
   size_t arena_bytes = 0;
   double setup_ms = 0.0;
@@ -263,6 +269,7 @@ struct Hierarchy {
 // Observability: launch counter and optional event bracketing of one kernel
 // class (bmg_profile.cu).
 void count_launch(int n = 1);
+bool prof_active();
 void prof_begin(int which, cudaStream_t s);
 void prof_end(int which, cudaStream_t s);
 
@@ -310,10 +317,10 @@ void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* levels, int threshold,
 // sc->rnorm2 / sc->bnorm2; then updates rel/go.  `what`: 0 = b norm, 1 =
 // residual norm + convergence flag.
 void launch_fine_norm(Hierarchy* h, const double* x, const double* b, int what,
-                      double tol, cudaStream_t s);
+                      double tol, cudaStream_t s, bool in_graph = false);
 // FP32_REFINE: r = b - A x in FP64 on the finest level, cast r/scale to FP32
 // into the FP32 fine RHS; zero the FP32 fine x.
-void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s);
+void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s, bool in_graph = false);
 void launch_refine_update(Hierarchy* h, cudaStream_t s);
 
 void launch_assemble_backward(const double* k, const double* u, const double* lam,

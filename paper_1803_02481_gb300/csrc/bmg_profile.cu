@@ -36,6 +36,8 @@ Prof& prof() {
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+bool prof_active() { return prof().mask != 0; }
+
 void prof_begin(int which, cudaStream_t s) {
   Prof& p = prof();
   if (!(p.mask & (1u << which))) return;

@@ -272,3 +272,22 @@ def test_solve_host_end_to_end():
     info = bm.solve_host(np.ascontiguousarray(pr["k"]), np.ascontiguousarray(pr["b"]), x)
     assert info.cycles == ro.cycles
     assert np.abs(x - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_graph_and_stream_paths_agree(precision):
+    """The solve loop recorded as one CUDA graph (default) and launched op by
+    op on the stream (used while kernel classes are being timed) run the
+    same kernels in the same order: identical results."""
+    pr = problem("blocks255")
+    prec = bm.BMG_FP64 if precision == "fp64" else bm.BMG_FP32_REFINE
+    hg = gpu_setup("blocks255", precision=prec)
+    x1, i1 = hg.solve(dev(pr["b"]), tol=1e-10)
+    bm.profile_set(("norm",))
+    try:
+        x2, i2 = hg.solve(dev(pr["b"]), tol=1e-10)
+    finally:
+        bm.profile_set(())
+    assert i1.cycles == i2.cycles and i1.rel_resid == i2.rel_resid
+    assert torch.equal(x1, x2)
+    hg.destroy()
