@@ -162,10 +162,28 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     calib = bm.calibrate(stream)
-    pr = inputs.block_problem(args.n, seed=1, block=64, lo=-4, hi=4)
+    tol = TOL
+    workload = dict(WORKLOAD)
+    if args.workload == "lognormal":
+        # the log-normal field of the mixed-precision comparison (generated on
+        # the GPU), solved to 1e-10
+        n = args.n if args.n != N_SIDE else 8191
+        args.n = n
+        g = inputs.gaussian_random_field_torch(2, n, n, 32.0, device=dev)
+        k = torch.exp(2.0 * g)
+        del g
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(102)
+        b = torch.rand((n, n), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+        pr = None
+        tol = 1e-10
+        workload = {"workload": f"log-normal k = exp(2 g), GRF correlation 32 cells, {n}x{n}, tol 1e-10",
+                    "nx": n, "ny": n, "seed": 2, "cycle": "V(2,1)", "tol": tol}
+    else:
+        pr = inputs.block_problem(args.n, seed=1, block=64, lo=-4, hi=4)
+        k = torch.from_numpy(pr["k"]).to(dev)
+        b = torch.from_numpy(pr["b"]).to(dev)
     n_fine = args.n * args.n
-    k = torch.from_numpy(pr["k"]).to(dev)
-    b = torch.from_numpy(pr["b"]).to(dev)
     x = torch.zeros_like(b)
     opts = bm.default_options(precision=bm.BMG_FP64 if args.precision == "fp64" else bm.BMG_FP32_REFINE,
                               max_cycles=args.max_cycles)
@@ -175,7 +193,7 @@ def run_ours(args, rank, world, local_rank):
     def step():
         x.zero_()
         h = bm.setup(k, opts, stream=stream)
-        _, info = h.solve(b, x, tol=TOL, stream=stream, allow_noconv=args.profile)
+        _, info = h.solve(b, x, tol=tol, stream=stream, allow_noconv=args.profile)
         h.destroy()
         return info
 
@@ -237,8 +255,8 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.quick:
-        kh = torch.from_numpy(pr["k"]).pin_memory()
-        bh = torch.from_numpy(pr["b"]).pin_memory()
+        kh = (torch.from_numpy(pr["k"]) if pr is not None else k.cpu()).pin_memory()
+        bh = (torch.from_numpy(pr["b"]) if pr is not None else b.cpu()).pin_memory()
         xh = torch.zeros_like(bh).pin_memory()
         kn, bn, xn = kh.numpy(), bh.numpy(), xh.numpy()
         reps = max(1, args.steps // 2)
@@ -288,7 +306,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": dict(WORKLOAD, nx=args.n, ny=args.n, precision=args.precision,
+            "config": dict(workload, nx=args.n, ny=args.n, precision=args.precision,
                            l2="inputs and hierarchy larger than L2", parallelism=f"replicas{world}"),
             "cycles": info.cycles, "rel_resid": info.rel_resid, "threshold": info.threshold,
             "setup_ms": info.setup_ms, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
@@ -434,6 +452,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default="blocks", choices=["blocks", "lognormal"],
+                    help="blocks: the 4095^2 block field (default); lognormal: the 8191^2 log-normal field")
     ap.add_argument("--threshold", type=int, default=None)
     ap.add_argument("--max-cycles", type=int, default=4000)
     ap.add_argument("--n", type=int, default=N_SIDE, help="grid side (smaller cases for profiling)")

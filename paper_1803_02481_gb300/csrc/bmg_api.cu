@@ -162,6 +162,7 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   if (opt.nu1 < 0 || opt.nu2 < 0 || opt.nu1 + opt.nu2 < 1 || opt.max_cycles < 0) return BMG_EINVAL;
   if (opt.precision != BMG_FP64 && opt.precision != BMG_FP32_REFINE) return BMG_EINVAL;
   const double t0 = now_ms();
+  prepare_sweep_kernels();
 
   Hierarchy* h = new (std::nothrow) Hierarchy();
   if (!h) return BMG_ENOMEM;

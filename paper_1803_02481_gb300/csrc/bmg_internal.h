@@ -304,6 +304,7 @@ void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool z
 template <typename T>
 void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s,
                    T* out = nullptr);
+void prepare_sweep_kernels();
 // One multicolour Gauss-Seidel sweep of a level as a single kernel: reads
 // the iterate from xin and writes the swept iterate to xout (xin != xout).
 template <typename T>

@@ -23,7 +23,7 @@ __host__ __device__ constexpr unsigned four_order(bool reverse) {
   return reverse ? 0x1248u : 0x8421u;
 }
 
-template <typename T, bool NINE, int TX, int TY, int NT>
+template <typename T, bool NINE, int TX, int TY, int NT, int UB = (NINE ? 3 : 1)>
 __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restrict__ xin,
                                            T* __restrict__ xout, unsigned order, int bx, int by) {
   constexpr int NC = NINE ? 4 : 2;
@@ -63,7 +63,7 @@ __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restri
       // before any update, so the loads overlap instead of serialising (a
       // win for the 9-point stencil; for 5 points the extra registers cost
       // more occupancy than the overlap gains, measured).
-      constexpr int U = NINE ? 3 : 1;
+      constexpr int U = UB;
       for (int t0 = threadIdx.x; t0 < npts; t0 += NT * U) {
         GsCoef<T, NINE> cf_[U];
         int sp[U];

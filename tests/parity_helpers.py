@@ -20,6 +20,7 @@ PROBLEMS = {
     "random63": lambda: {"k": 10.0 ** np.random.default_rng(7).uniform(-2, 2, (63, 63)),
                          "b": np.random.default_rng(8).uniform(-1, 1, (63, 63))},
     "rect127x31": lambda: inputs.block_problem(seed=5, block=8, lo=-3, hi=3, nx=127, ny=31),
+    "wide2047x127": lambda: inputs.block_problem(seed=6, block=64, lo=-2, hi=2, nx=2047, ny=127),
     "tiny3": lambda: {"k": np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0], [7.0, 8.0, 9.0]]),
                       "b": np.array([[1.0, -1.0, 0.5], [0.25, 2.0, -3.0], [1.0, 1.0, 1.0]])},
 }

@@ -100,7 +100,7 @@ def test_setup_hierarchy_matches_oracle_end_to_end(name):
     hg.destroy()
 
 
-@pytest.mark.parametrize("name", ["blocks255", "rect127x31"])
+@pytest.mark.parametrize("name", ["blocks255", "rect127x31", "wide2047x127"])
 def test_single_operations_match_oracle(name):
     ho = oracle_hierarchy(name)
     hg = gpu_setup(name)
@@ -135,7 +135,8 @@ def test_single_operations_match_oracle(name):
     hg.destroy()
 
 
-SOLVE_CASES = ["poisson255", "blocks255", "lognormal255", "random63", "rect127x31", "tiny3"]
+SOLVE_CASES = ["poisson255", "blocks255", "lognormal255", "random63", "rect127x31", "tiny3",
+               "wide2047x127"]
 
 
 @pytest.mark.parametrize("name", SOLVE_CASES)
