@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kNT) k_brefine_resid(const LevelV<double>* __r
   if (what == 1 && !sc[p].go) return;
   const LevelV<double> L = f64[z];
   const LevelV<float> F = f32[z];
-  const double inv = what ? 1.0 / sqrt(sc[p].rnorm2) : 0.0;
+  const double inv = what ? sc[p].inv : 0.0;
   double acc = 0.0;
   for (int j = blockIdx.x + 1; j <= L.ny; j += gridDim.x) {
     for (int i = threadIdx.x + 1; i <= L.nx; i += blockDim.x) {
@@ -186,12 +186,15 @@ __global__ void __launch_bounds__(kNT) k_bnorm_final(const double* __restrict__ 
   if (what == 0) {
     s->bnorm2 = acc;
     s->rnorm2 = acc;
+    s->inv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
     s->go = acc > 0.0 ? 1 : 0;     // a zero right-hand side needs no cycle
     s->rel = 0.0;
     return;
   }
   s->scale2 = s->rnorm2;
+  s->scale = sqrt(s->scale2);
   s->rnorm2 = acc;
+  s->inv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
   const double rel = sqrt(acc / s->bnorm2);
   s->rel = rel;
   const bool finite = isfinite(rel);
@@ -225,7 +228,7 @@ __global__ void k_bupdate(const LevelV<double>* __restrict__ f64,
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y + 1;
   if (i > L.nx) return;
-  const double s = sqrt(sc[p].scale2);
+  const double s = sc[p].scale;
   const int o = j * L.pitch + i;
   L.x[o] = fma(s, double(e[j * f32[z].pitch + i]), L.x[o]);
 }

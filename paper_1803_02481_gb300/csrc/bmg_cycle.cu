@@ -123,10 +123,13 @@ __global__ void __launch_bounds__(kNormThreads) k_norm_final(const double* parti
   if (what == 0) {
     sc->bnorm2 = acc;
     sc->rnorm2 = acc;
+    sc->inv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
     return;
   }
   sc->scale2 = sc->rnorm2;
+  sc->scale = sqrt(sc->scale2);
   sc->rnorm2 = acc;
+  sc->inv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
   const double rel = sqrt(acc / sc->bnorm2);
   sc->rel = rel;
   if (sc->cycles < BMG_MAX_HISTORY) hist[sc->cycles] = rel;
@@ -146,7 +149,7 @@ template <bool NINE>
 __global__ void __launch_bounds__(kNormThreads) k_refine_residual(LevelV<double> L, LevelV<float> F,
                                                                   const Scalars* sc,
                                                                   double* partials) {
-  const double inv = 1.0 / sqrt(sc->rnorm2);
+  const double inv = sc->inv;
   double acc = 0.0;
   for (int j = blockIdx.x + 1; j <= L.ny; j += gridDim.x) {
     for (int i = threadIdx.x + 1; i <= L.nx; i += blockDim.x) {
@@ -167,7 +170,7 @@ __global__ void k_refine_update(LevelV<double> L, LevelV<float> F, const Scalars
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y + 1;
   if (i > L.nx) return;
-  const double s = sqrt(sc->scale2);
+  const double s = sc->scale;
   const int o = j * L.pitch + i;
   L.x[o] = fma(s, double(F.x[j * F.pitch + i]), L.x[o]);
 }

@@ -139,23 +139,24 @@ __device__ __forceinline__ T gs_value(const LevelV<T>& L, const T* __restrict__ 
   return gs_update<T, NINE>(L, [&](int dx, int dy) { return x[o + dx + dy * p]; }, bval, o);
 }
 
-// Residual of one point: r = b - (C x - sum_X a_X x_X).
+// Residual of one point: r = b - (C x - sum_X a_X x_X), accumulated as
+// b - C x first, then + a_X x_X (one FMA per stencil entry).
 template <typename T, bool NINE>
 __device__ __forceinline__ T resid_value(const LevelV<T>& L, const T* __restrict__ x,
                                          T bval, int o) {
   const int p = L.pitch;
-  T y = L.C[o] * x[o];
-  y = fma(-L.W[o], x[o - 1], y);
-  y = fma(-L.W[o + 1], x[o + 1], y);
-  y = fma(-L.S[o], x[o - p], y);
-  y = fma(-L.S[o + p], x[o + p], y);
+  T r = fma(-L.C[o], x[o], bval);
+  r = fma(L.W[o], x[o - 1], r);
+  r = fma(L.W[o + 1], x[o + 1], r);
+  r = fma(L.S[o], x[o - p], r);
+  r = fma(L.S[o + p], x[o + p], r);
   if (NINE) {
-    y = fma(-L.SW[o], x[o - p - 1], y);
-    y = fma(-L.NW[o + 1 - p], x[o + 1 - p], y);
-    y = fma(-L.NW[o], x[o + p - 1], y);
-    y = fma(-L.SW[o + 1 + p], x[o + 1 + p], y);
+    r = fma(L.SW[o], x[o - p - 1], r);
+    r = fma(L.NW[o + 1 - p], x[o + 1 - p], r);
+    r = fma(L.NW[o], x[o + p - 1], r);
+    r = fma(L.SW[o + 1 + p], x[o + 1 + p], r);
   }
-  return bval - y;
+  return r;
 }
 
 // Weight of fine point (2I + rx, 2J + ry) towards coarse point (I, J),
@@ -219,7 +220,7 @@ enum DevErr { DEV_OK = 0, DEV_BADK = 1, DEV_NOTSPD = 2, DEV_BADDEN = 4, DEV_NAN 
 // Thread-local detail message of the last failure (bmg_last_error).
 void set_last_error(const char* fmt, ...);
 
-struct Scalars {            // device-resident solve state (one cache line)
+struct Scalars {            // device-resident solve state
   double bnorm2;            // ||b||^2
   double rnorm2;            // ||r||^2 of the latest residual
   double scale2;            // FP32_REFINE: ||r||^2 of the previous residual,
@@ -227,6 +228,8 @@ struct Scalars {            // device-resident solve state (one cache line)
                             // divided by before the cast to FP32
   double rel;               // sqrt(rnorm2 / bnorm2)
   double tol;               // stop test
+  double scale;             // sqrt(scale2), set with scale2 (one thread)
+  double inv;               // 1 / sqrt(rnorm2) (0 when rnorm2 == 0), set with rnorm2
   int cycles;               // cycles / refinement steps run
   int max_cycles;
   int go;                   // 1 while the loop should continue

@@ -21,30 +21,48 @@ __device__ __forceinline__ double harmonic(double k1, double k2) {
   return 2.0 * k1 * k2 / (k1 + k2);
 }
 
-// One thread per cell.  Writes C, 1/C, W, S of the finest level and a dense
-// copy of k; flags k that is not finite and positive.
 // k of cell q: the input itself, or exp(input) for log-coefficients.
 __device__ __forceinline__ double cell_k(const double* __restrict__ k, size_t q, bool log_k) {
   return log_k ? exp(k[q]) : k[q];
 }
 
+// Assembly tile: kAX x kAY cells per block, one thread per cell.
+constexpr int kAX = 32, kAY = 8;
+
+// Writes C, 1/C, W, S of the finest level and a dense copy of k; flags k that
+// is not finite and positive.  Each thread forms the west and south faces of
+// its cell (each interior face once); the east and north faces come from the
+// neighbours through shared memory, the tile's last column and row forming
+// the faces beyond it.  The east face of cell q is harmonic(k_q, k_q+1), the
+// same call as the west face of cell q+1, so C is what forming all four
+// faces per cell would give.
 template <typename T>
-__global__ void k_assemble(const double* __restrict__ k, int nx, int ny, LevelV<T> L,
-                           double* __restrict__ kcopy, int* derr, bool log_k) {
-  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = blockIdx.y;
-  if (i0 >= nx) return;
+__global__ void __launch_bounds__(kAX * kAY) k_assemble(const double* __restrict__ k, int nx,
+                                                        int ny, LevelV<T> L,
+                                                        double* __restrict__ kcopy, int* derr,
+                                                        bool log_k) {
+  __shared__ double fw[kAY][kAX + 1];   // west faces, column kAX = east of the tile
+  __shared__ double fs[kAY + 1][kAX];   // south faces, row kAY = north of the tile
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * kAX + tx;
+  const int j0 = blockIdx.y * kAY + ty;
+  const bool in = i0 < nx && j0 < ny;
   const size_t q = size_t(j0) * nx + i0;
-  const double kc = cell_k(k, q, log_k);
-  if (!(kc > 0.0) || !(kc < INFINITY)) {
-    atomicOr(derr, DEV_BADK);
-    return;
+  double kc = 1.0;
+  if (in) {
+    kc = cell_k(k, q, log_k);
+    if (!(kc > 0.0) || !(kc < INFINITY)) atomicOr(derr, DEV_BADK);
+    kcopy[q] = kc;
+    fw[ty][tx] = i0 > 0 ? harmonic(cell_k(k, q - 1, log_k), kc) : 0.0;
+    fs[ty][tx] = j0 > 0 ? harmonic(cell_k(k, q - nx, log_k), kc) : 0.0;
+    if (tx == kAX - 1) fw[ty][kAX] = i0 < nx - 1 ? harmonic(kc, cell_k(k, q + 1, log_k)) : 0.0;
+    if (ty == kAY - 1) fs[kAY][tx] = j0 < ny - 1 ? harmonic(kc, cell_k(k, q + nx, log_k)) : 0.0;
   }
-  kcopy[q] = kc;
-  const double aw = i0 > 0 ? harmonic(cell_k(k, q - 1, log_k), kc) : 0.0;
-  const double ae = i0 < nx - 1 ? harmonic(kc, cell_k(k, q + 1, log_k)) : 0.0;
-  const double as = j0 > 0 ? harmonic(cell_k(k, q - nx, log_k), kc) : 0.0;
-  const double an = j0 < ny - 1 ? harmonic(kc, cell_k(k, q + nx, log_k)) : 0.0;
+  __syncthreads();
+  if (!in) return;
+  const double aw = fw[ty][tx], as = fs[ty][tx];
+  const double ae = i0 < nx - 1 ? fw[ty][tx + 1] : 0.0;
+  const double an = j0 < ny - 1 ? fs[ty + 1][tx] : 0.0;
   // boundary faces, in the order west, east, south, north
   double bw = 0.0;
   if (i0 == 0) bw = bw + 2.0 * kc;
@@ -336,7 +354,8 @@ __global__ void k_assemble_backward(const double* __restrict__ k, const double* 
 template <typename T>
 int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy, int* derr,
                     bool log_k, cudaStream_t s) {
-  k_assemble<T><<<dim3(cdiv(nx, kTB), ny), kTB, 0, s>>>(k, nx, ny, L, kcopy, derr, log_k);
+  k_assemble<T><<<dim3(cdiv(nx, kAX), cdiv(ny, kAY)), dim3(kAX, kAY), 0, s>>>(k, nx, ny, L, kcopy,
+                                                                            derr, log_k);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : BMG_ECUDA;
 }
