@@ -167,7 +167,7 @@ def run_ours(args, rank, world, local_rank):
     if args.workload == "lognormal":
         # the log-normal field of the mixed-precision comparison (generated on
         # the GPU), solved to 1e-10
-        n = args.n if args.n != N_SIDE else 8191
+        n = args.n if args.n is not None else 8191
         args.n = n
         g = inputs.gaussian_random_field_torch(2, n, n, 32.0, device=dev)
         k = torch.exp(2.0 * g)
@@ -180,6 +180,8 @@ def run_ours(args, rank, world, local_rank):
         workload = {"workload": f"log-normal k = exp(2 g), GRF correlation 32 cells, {n}x{n}, tol 1e-10",
                     "nx": n, "ny": n, "seed": 2, "cycle": "V(2,1)", "tol": tol}
     else:
+        if args.n is None:
+            args.n = N_SIDE
         pr = inputs.block_problem(args.n, seed=1, block=64, lo=-4, hi=4)
         k = torch.from_numpy(pr["k"]).to(dev)
         b = torch.from_numpy(pr["b"]).to(dev)
@@ -456,7 +458,8 @@ def main():
                     help="blocks: the 4095^2 block field (default); lognormal: the 8191^2 log-normal field")
     ap.add_argument("--threshold", type=int, default=None)
     ap.add_argument("--max-cycles", type=int, default=4000)
-    ap.add_argument("--n", type=int, default=N_SIDE, help="grid side (smaller cases for profiling)")
+    ap.add_argument("--n", type=int, default=None,
+                    help="grid side (default 4095 block field, 8191 log-normal field)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: allow stopping at --max-cycles, skip the extra legs")
     ap.add_argument("--quick", action="store_true", help="skip the e2e, fp32 and CPU legs")

@@ -148,6 +148,8 @@ void free_hierarchy(Hierarchy* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->arena) cudaFree(h->arena);
   if (h->sc_host) cudaFreeHost(h->sc_host);
+  delete h->maps64;
+  delete h->maps32;
   delete h;
 }
 
@@ -260,6 +262,21 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   }
   if ((rc = check_derr(h, s))) return fail(rc);
 
+  // TMA descriptors of the finest level (the level the fine sweeps read)
+  if (!fp32) {
+    h->maps64 = new SweepMaps<double>;
+    if (!make_sweep_maps<double>(h->d.back(), derr, h->maps64)) {
+      delete h->maps64;
+      h->maps64 = nullptr;
+    }
+  } else {
+    h->maps32 = new SweepMaps<float>;
+    if (!make_sweep_maps<float>(h->f.back(), derr, h->maps32)) {
+      delete h->maps32;
+      h->maps32 = nullptr;
+    }
+  }
+
   // Level schedule: which levels leave the full-grid launches.
   h->threshold = opt.coarse_threshold > 0 ? opt.coarse_threshold : choose_threshold(h);
   h->setup_ms = now_ms() - t0;
@@ -272,6 +289,17 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
 // ---------------------------------------------------------------------------
 
 template <typename T>
+const SweepMaps<T>* fine_sweep_maps(const Hierarchy* h);
+template <>
+const SweepMaps<double>* fine_sweep_maps<double>(const Hierarchy* h) {
+  return h->maps64;
+}
+template <>
+const SweepMaps<float>* fine_sweep_maps<float>(const Hierarchy* h) {
+  return h->maps32;
+}
+
+template <typename T>
 void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* dlev, int thr,
                     cudaStream_t s) {
   const int L = h->L;
@@ -281,11 +309,12 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
   // interpolation also writes out of place, so every level's iterate is back
   // in lv[l].x when the cycle ends and every cycle issues the same launches.
   const bool interp_oop = ((nu1 + nu2) & 1) != 0;
+  const SweepMaps<T>* fine_maps = fine_sweep_maps<T>(h);
   auto sweep = [&](int l, bool reverse) {
     LevelV<T>& V = lv[l];
     const bool nine = l != L - 1;
     if (!nine) prof_begin(BMG_PROF_FINE_SMOOTH, s);
-    launch_sweep<T>(V, nine, reverse, V.x, V.x2, s);
+    launch_sweep<T>(V, nine, reverse, V.x, V.x2, s, nine ? nullptr : fine_maps);
     if (!nine) prof_end(BMG_PROF_FINE_SMOOTH, s);
     std::swap(V.x, V.x2);
   };
@@ -698,11 +727,14 @@ int bmg_op_relax(bmg_hierarchy* hp, int level, double* x, const double* b, int n
   auto& L = h->d[level];
   bmg::launch_pack<double>(x, L.x, L.nx, L.ny, L.pitch, s);
   bmg::launch_pack<double>(b, L.b, L.nx, L.ny, L.pitch, s);
+  const bool fine = level == h->L - 1;
   for (int k = 0; k < nu; ++k) {
-    bmg::launch_sweep<double>(L, level != h->L - 1, reverse != 0, L.x, L.x2, s);
+    bmg::launch_sweep<double>(L, !fine, reverse != 0, L.x, L.x2, s, fine ? h->maps64 : nullptr);
     std::swap(L.x, L.x2);
   }
   bmg::launch_unpack<double>(L.x, x, L.nx, L.ny, L.pitch, s);
+  // keep the level's buffer roles as the recorded solve graph expects them
+  if (nu & 1) std::swap(L.x, L.x2);
   return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;
 }
 

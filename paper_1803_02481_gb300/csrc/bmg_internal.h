@@ -30,6 +30,7 @@
 // Coarse point (I, J) is fine point (2I, 2J) with weight 1.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -53,7 +54,11 @@ inline Geom make_geom(int nx, int ny) {
   Geom g;
   g.nx = nx;
   g.ny = ny;
-  g.pitch = ((nx + 2 + per128 - 1) / per128) * per128;
+  // pitch >= nx + 1 + 128 / sizeof(T): counted from the 128-byte aligned
+  // start of a row's storage (i = 1 - base_shift), the row's pitch elements
+  // reach the east ghost column i = nx + 1 (the extent a plane's TMA
+  // descriptor gives a row)
+  g.pitch = ((nx + 1 + per128 + per128 - 1) / per128) * per128;
   g.elems = size_t(ny + 2) * g.pitch + per128;
   return g;
 }
@@ -236,6 +241,16 @@ struct Scalars {            // device-resident solve state
   int err;                  // DevErr bits
 };
 
+// 2-D TMA descriptors of the planes the TMA-staged sweep reads, for one
+// 5-point level (built at setup; see make_sweep_maps).
+template <typename T>
+struct SweepMaps {
+  CUtensorMap x, x2, ic, w, s, b;
+  const T* xp;      // plane the map `x` describes
+  const T* x2p;     // plane the map `x2` describes
+  int* err;         // device error word (DEV_TIMEOUT)
+};
+
 struct Timing;
 
 struct Hierarchy {
@@ -267,6 +282,10 @@ struct Hierarchy {
   void* arena = nullptr;
   size_t arena_bytes = 0;
   double setup_ms = 0.0;
+  // TMA descriptors of the finest level (null when the level is swept by
+  // the tiled kernel)
+  SweepMaps<double>* maps64 = nullptr;
+  SweepMaps<float>* maps32 = nullptr;
 };
 
 // Observability: launch counter and optional event bracketing of one kernel
@@ -308,11 +327,16 @@ template <typename T>
 void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s,
                    T* out = nullptr);
 void prepare_sweep_kernels();
+// TMA descriptors of a 5-point level for the TMA-staged sweep; false (and no
+// descriptors) when the level is swept by the tiled kernel instead.
+template <typename T>
+bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m);
 // One multicolour Gauss-Seidel sweep of a level as a single kernel: reads
 // the iterate from xin and writes the swept iterate to xout (xin != xout).
+// `maps` (finest level only, may be null) selects the TMA-staged kernel.
 template <typename T>
 void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* xout,
-                  cudaStream_t s);
+                  cudaStream_t s, const SweepMaps<T>* maps = nullptr);
 template <typename T>
 void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* levels, int threshold,
                          cudaStream_t s);

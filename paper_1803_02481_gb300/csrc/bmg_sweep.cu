@@ -2,9 +2,11 @@
 // Algorithm 1; red-black on 5-point levels, four colours on 9-point levels,
 // Section 5).  The tile body is in bmg_sweep_tile.cuh.
 #include <cstdlib>
+#include <cstring>
 
 #include "bmg_sweep_stream.cuh"
 #include "bmg_sweep_tile.cuh"
+#include "bmg_sweep_tma.cuh"
 
 namespace bmg {
 
@@ -24,22 +26,166 @@ __global__ void __launch_bounds__(NT) k_sweep(LevelV<T> L, const T* __restrict__
 // block (36 KB of shared memory in FP64: six blocks per SM).
 constexpr int kStreamNT = 64, kStreamR = 32;
 
+// TMA-staged kernel shapes (tile TX x TY, NT threads, MINB blocks per SM),
+// one table per precision.  Entry 0 is the default, measured fastest on the
+// fine level: FP64 64 x 16 tiles, 512 threads, two blocks per SM (FP64 is
+// ALU-bound: more warps hide the FP64 latency); FP32 128 x 16 tiles, 256
+// threads, two blocks per SM (memory-bound: four stages per SM in flight).
+// BMG_TMA_CFG selects another entry, for measurements.
+struct TmaCfg {
+  int tx, ty, nt, minb;
+};
+constexpr TmaCfg kTma64[] = {{64, 16, 512, 2}, {128, 16, 256, 1}, {128, 16, 512, 1},
+                             {128, 16, 1024, 1}, {64, 16, 256, 2}};
+constexpr TmaCfg kTma32[] = {{128, 16, 256, 2}, {128, 32, 256, 1}, {128, 32, 512, 1},
+                             {128, 16, 512, 2}, {128, 8, 256, 3}};
+constexpr int kNumTmaCfg = 5;
+
+static int tma_cfg_index() {
+  static const int v = [] {
+    const char* e = std::getenv("BMG_TMA_CFG");
+    const int k = e ? std::atoi(e) : 0;
+    return k >= 0 && k < kNumTmaCfg ? k : 0;
+  }();
+  return v;
+}
+template <typename T>
+static TmaCfg tma_cfg() {
+  return sizeof(T) == 8 ? kTma64[tma_cfg_index()] : kTma32[tma_cfg_index()];
+}
+
 // Kernel for large 5-point levels: 0 = streaming strips, 1 = tiled (one
-// point per thread step, the default: measured fastest), 2 = tiled with two
-// points' loads issued together.  BMG_RB_KERNEL overrides the default, for
-// measurements.
+// point per thread step), 2 = tiled with two points' loads issued together,
+// 3 = persistent TMA-staged tiles (the default).  BMG_RB_KERNEL overrides the
+// default, for measurements.
 static int rb_kernel_choice() {
   static const int v = [] {
     const char* e = std::getenv("BMG_RB_KERNEL");
-    return e ? std::atoi(e) : 1;
+    return e ? std::atoi(e) : 3;
   }();
   return v;
 }
 static bool stream_rb_enabled() { return rb_kernel_choice() == 0; }
 
+static int sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  return n;
+}
+
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link
+// against libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                        &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    cudaGetLastError();
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Descriptor of one plane (base = element (0, 0)) as a 2-D tensor of
+// (ny + 2) rows of `pitch` elements, starting base_shift elements before the
+// plane base (the 128-byte aligned start of its allocation), staged in boxes
+// of the TMA tile shape.
+template <typename T>
+static bool encode_plane(CUtensorMap* m, const T* base, int pitch, int ny) {
+  const TmaCfg c = tma_cfg<T>();
+  const int ha = int(16 / sizeof(T));
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || !base) return false;
+  void* start = const_cast<T*>(base - base_shift<T>());
+  const cuuint64_t dims[2] = {cuuint64_t(pitch), cuuint64_t(ny + 2)};
+  const cuuint64_t strides[1] = {cuuint64_t(pitch) * sizeof(T)};
+  const cuuint32_t box[2] = {cuuint32_t(c.tx + 2 * ha), cuuint32_t(c.ty + 4)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt =
+      sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(m, dt, 2, start, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T>
+bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m) {
+  if (rb_kernel_choice() != 3 || L.nx < 1024 || L.SW) return false;
+  std::memset(static_cast<void*>(m), 0, sizeof(*m));
+  const bool ok = encode_plane<T>(&m->x, L.x, L.pitch, L.ny) &&
+                  encode_plane<T>(&m->x2, L.x2, L.pitch, L.ny) &&
+                  encode_plane<T>(&m->ic, L.iC, L.pitch, L.ny) &&
+                  encode_plane<T>(&m->w, L.W, L.pitch, L.ny) &&
+                  encode_plane<T>(&m->s, L.S, L.pitch, L.ny) &&
+                  encode_plane<T>(&m->b, L.b, L.pitch, L.ny);
+  m->xp = L.x;
+  m->x2p = L.x2;
+  m->err = err;
+  return ok;
+}
+
+template <typename T, int TX, int TY, int NT, int MINB>
+static void launch_tma_shape(const LevelV<T>& L, const SweepMaps<T>& m, const CUtensorMap& mx,
+                             bool reverse, T* xout, cudaStream_t s) {
+  using G = TmaTile<T, TX, TY>;
+  const int ntiles = ((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
+  const int cap = sm_count() * MINB;
+  k_sweep_rb_tma<T, TX, TY, NT, MINB><<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(
+      mx, m.ic, m.w, m.s, m.b, L, xout, rb_order(reverse), m.err);
+}
+
+template <typename T, int TX, int TY, int NT, int MINB>
+static void allow_tma_smem() {
+  cudaFuncSetAttribute(k_sweep_rb_tma<T, TX, TY, NT, MINB>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(TmaTile<T, TX, TY>::SMEM));
+}
+
+// Instantiates BODY(T, TX, TY, NT, MINB) for entry K of T's shape table.
+#define BMG_TMA_DISPATCH(T, K, BODY)                                  \
+  do {                                                                 \
+    if constexpr (sizeof(T) == 8) {                                    \
+      switch (K) {                                                     \
+        case 1: BODY(T, 128, 16, 256, 1); break;                       \
+        case 2: BODY(T, 128, 16, 512, 1); break;                       \
+        case 3: BODY(T, 128, 16, 1024, 1); break;                      \
+        case 4: BODY(T, 64, 16, 256, 2); break;                        \
+        default: BODY(T, 64, 16, 512, 2); break;                       \
+      }                                                                \
+    } else {                                                           \
+      switch (K) {                                                     \
+        case 1: BODY(T, 128, 32, 256, 1); break;                       \
+        case 2: BODY(T, 128, 32, 512, 1); break;                       \
+        case 3: BODY(T, 128, 16, 512, 2); break;                       \
+        case 4: BODY(T, 128, 8, 256, 3); break;                        \
+        default: BODY(T, 128, 16, 256, 2); break;                      \
+      }                                                                \
+    }                                                                  \
+  } while (0)
+
+template <typename T>
+static void launch_sweep_tma(const LevelV<T>& L, const SweepMaps<T>& m, bool reverse,
+                             const T* xin, T* xout, cudaStream_t s) {
+  const CUtensorMap& mx = xin == m.xp ? m.x : m.x2;
+#define BMG_TMA_LAUNCH(TT, TX, TY, NT, MB) launch_tma_shape<TT, TX, TY, NT, MB>(L, m, mx, reverse, xout, s)
+  BMG_TMA_DISPATCH(T, tma_cfg_index(), BMG_TMA_LAUNCH);
+#undef BMG_TMA_LAUNCH
+}
+
 template <typename T>
 void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* xout,
-                  cudaStream_t s) {
+                  cudaStream_t s, const SweepMaps<T>* maps) {
   // Large tiles keep the redundant halo work small (4% red-black, 12% four
   // colours); levels narrower than 1024 use small tiles so that they still
   // spread over all SMs.
@@ -59,6 +205,8 @@ void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* 
       constexpr int TX = 32, TY = 16;
       k_sweep<T, false, TX, TY, 128><<<dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), 128, 0, s>>>(
           L, xin, xout, rb_order(reverse));
+    } else if (maps && (xin == maps->xp || xin == maps->x2p)) {
+      launch_sweep_tma<T>(L, *maps, reverse, xin, xout, s);
     } else if (stream_rb_enabled()) {
       constexpr int NT = kStreamNT, R = kStreamR;
       using S = StreamRB<T, NT, R>;
@@ -90,14 +238,22 @@ void prepare_sweep_kernels() {
     cudaFuncSetAttribute(k_sweep_rb_stream<float, kStreamNT, kStreamR>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(S32::Row) * S32::NSLOT));
+#define BMG_TMA_ALLOW(TT, TX, TY, NT, MB) allow_tma_smem<TT, TX, TY, NT, MB>()
+    BMG_TMA_DISPATCH(double, tma_cfg_index(), BMG_TMA_ALLOW);
+    BMG_TMA_DISPATCH(float, tma_cfg_index(), BMG_TMA_ALLOW);
+#undef BMG_TMA_ALLOW
+    sm_count();
+    encode_tiled();
     return true;
   }();
   (void)done;
 }
 
 template void launch_sweep<double>(const LevelV<double>&, bool, bool, const double*, double*,
-                                   cudaStream_t);
+                                   cudaStream_t, const SweepMaps<double>*);
 template void launch_sweep<float>(const LevelV<float>&, bool, bool, const float*, float*,
-                                  cudaStream_t);
+                                  cudaStream_t, const SweepMaps<float>*);
+template bool make_sweep_maps<double>(const LevelV<double>&, int*, SweepMaps<double>*);
+template bool make_sweep_maps<float>(const LevelV<float>&, int*, SweepMaps<float>*);
 
 }  // namespace bmg

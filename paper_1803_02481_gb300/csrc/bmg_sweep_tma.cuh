@@ -1,0 +1,231 @@
+// Persistent, TMA-staged red-black Gauss-Seidel sweep of a large 5-point
+// level (smoothing of Algorithm 1).
+//
+// One thread block per SM walks the level's TX x TY tiles.  For each tile,
+// one thread issues five 2-D bulk tensor copies (cp.async.bulk.tensor) of the
+// tile plus a halo: the old iterate and the planes 1/C, W, S and b.  They land
+// in one of two shared-memory stages and complete on that stage's mbarrier.
+// While the block relaxes tile t out of one stage, the copies of its next
+// tile fill the other, so HBM traffic and arithmetic overlap inside the block.
+//
+// The relaxation itself is the redundant-halo scheme of the tiled kernel: the
+// first colour is updated on the tile grown by one cell, the second on the
+// tile, so no block reads another block's new values.  The new iterate goes
+// to a second buffer.  Per-point arithmetic is gs_apply, as in every other
+// kernel, so the result is bit-identical to theirs.
+//
+// Staged box: rows j0-2 .. j0+TY+1 and columns i0-HA .. i0+TX+HA-1 of each
+// plane, (i0, j0) the tile's first interior point.  HA = 16 / sizeof(T) keeps
+// the box's first column on a 16-byte boundary (interior rows start on a
+// 128-byte boundary); only two halo columns are used.  Rows and columns
+// outside the plane read as zero, the Dirichlet ghost value.
+//
+// Every wait on an mbarrier gives up after one second: the block then sets
+// DEV_TIMEOUT in the error word, waits (again bounded) for its copies in
+// flight and returns.
+#pragma once
+
+#include <cuda.h>
+
+#include "bmg_internal.h"
+
+namespace bmg {
+
+namespace tma_detail {
+
+__device__ __forceinline__ unsigned saddr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Waits for the phase of `bar` with the given parity to complete; false
+// after about one second.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > 1000000000ull) return false;
+  }
+  return true;
+}
+
+// 2-D tiled bulk tensor copy global -> shared, completing on `bar`.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+
+}  // namespace tma_detail
+
+// Shape of the staged tile.
+template <typename T, int TX, int TY>
+struct TmaTile {
+  static constexpr int HA = int(16 / sizeof(T));   // halo columns staged on each side
+  static constexpr int BW = TX + 2 * HA;           // box width (elements)
+  static constexpr int BH = TY + 4;                // box height: two halo rows each side
+  static constexpr int PLANE = BW * BH;            // elements of one staged plane
+  static constexpr int NPL = 5;                    // x, 1/C, W, S, b
+  static constexpr unsigned STAGE_BYTES = unsigned(NPL * PLANE * sizeof(T));
+  static constexpr size_t SMEM = 2 * size_t(STAGE_BYTES);
+  static_assert(TX % 4 == 0 && TY % 2 == 0, "tile sides keep colours and TMA alignment");
+  static_assert(BW <= 256 && BH <= 256, "TMA box sides are at most 256 elements");
+  static_assert((BW * sizeof(T)) % 16 == 0, "TMA box rows are multiples of 16 bytes");
+  static_assert((PLANE * sizeof(T)) % 128 == 0, "staged planes start 128-byte aligned");
+};
+
+template <typename T, int TX, int TY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_sweep_rb_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mic,
+                   const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap ms,
+                   const __grid_constant__ CUtensorMap mb, LevelV<T> L, T* __restrict__ xout,
+                   unsigned order, int* __restrict__ err) {
+  using namespace tma_detail;
+  using G = TmaTile<T, TX, TY>;
+  constexpr int BW = G::BW, HA = G::HA, PL = G::PLANE;
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int nx = L.nx, ny = L.ny, p = L.pitch;
+  const int ntx = (nx + TX - 1) / TX;
+  const int ntiles = ntx * ((ny + TY - 1) / TY);
+  const int tid = threadIdx.x;
+  T* const stage0 = reinterpret_cast<T*>(tma_smem);
+  T* const stage1 = reinterpret_cast<T*>(tma_smem + G::STAGE_BYTES);
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // Thread 0: stage the box of tile t into stage s.
+  auto issue = [&](int s, int t) {
+    const int bx = t % ntx, by = t / ntx;
+    const int X = bx * TX + 1 - HA + base_shift<T>();   // tensor column of the box start
+    const int Y = by * TY - 1;                          // tensor row (= j) of the box start
+    T* d = s ? stage1 : stage0;
+    uint64_t* b = &bar[s];
+    mbar_expect_tx(b, G::STAGE_BYTES);
+    tma_load_2d(d + 0 * PL, &mx, X, Y, b);
+    tma_load_2d(d + 1 * PL, &mic, X, Y, b);
+    tma_load_2d(d + 2 * PL, &mw, X, Y, b);
+    tma_load_2d(d + 3 * PL, &ms, X, Y, b);
+    tma_load_2d(d + 4 * PL, &mb, X, Y, b);
+  };
+
+  int t = blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(0, t);
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int s = it & 1;
+    const int tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) issue(s ^ 1, tn);
+    const bool ok = mbar_wait_bounded(&bar[s], unsigned(it >> 1) & 1u);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) {
+        atomicOr(err, DEV_TIMEOUT);
+        // the block's shared memory must outlive its copies in flight
+        mbar_wait_bounded(&bar[s], unsigned(it >> 1) & 1u);
+        if (tn < ntiles) mbar_wait_bounded(&bar[s ^ 1], unsigned((it + 1) >> 1) & 1u);
+      }
+      __syncthreads();
+      return;
+    }
+
+    T* const sx = s ? stage1 : stage0;
+    const T* const sic = sx + 1 * PL;
+    const T* const sw = sx + 2 * PL;
+    const T* const ss = sx + 3 * PL;
+    const T* const sb = sx + 4 * PL;
+    const int bx = t % ntx, by = t / ntx;
+    const int i0 = bx * TX + 1, j0 = by * TY + 1;
+    // Shared cell (r, c) holds domain point (i0 + c - HA, j0 + r - 2).  With
+    // TX, TY and HA even, the 0-based domain parities of (r, c) are (r, c) & 1.
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const unsigned mask = (order >> (4 * k)) & 0xFu;
+      const int ring = 1 - k;
+      const int r0 = 2 - ring, r1 = 2 + TY + ring;
+      const int c0 = HA - ring, c1 = HA + TX + ring;
+#pragma unroll
+      for (int sl = 0; sl < 4; ++sl) {
+        if (!(mask & (1u << sl))) continue;
+        const int pj = sl >> 1, pi = sl & 1;
+        const int rf = r0 + ((pj - r0) & 1);
+        const int cf = c0 + ((pi - c0) & 1);
+        const int nr = (r1 - rf + 1) >> 1, ncol = (c1 - cf + 1) >> 1;
+        const int npts = nr * ncol;
+        for (int q = tid; q < npts; q += NT) {
+          const int rr = q / ncol;
+          const int r = rf + 2 * rr, c = cf + 2 * (q - rr * ncol);
+          const int i = i0 + c - HA, j = j0 + r - 2;
+          if (i < 1 || i > nx || j < 1 || j > ny) continue;
+          const int o = r * BW + c;
+          GsCoef<T, false> cf_;
+          cf_.b = sb[o];
+          cf_.ic = sic[o];
+          cf_.w = sw[o];
+          cf_.e = sw[o + 1];
+          cf_.s = ss[o];
+          cf_.n = ss[o + BW];
+          T* xp = sx + o;
+          *xp = gs_apply<T, false>(cf_, [&](int dx, int dy) { return xp[dx + dy * BW]; });
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < TX * TY; e += NT) {
+      const int r = e / TX, c = e - r * TX;
+      const int i = i0 + c, j = j0 + r;
+      if (i <= nx && j <= ny) xout[j * p + i] = sx[(r + 2) * BW + c + HA];
+    }
+    // this stage is refilled by the copies issued in the next iteration
+    fence_proxy_async();
+    __syncthreads();
+  }
+}
+
+}  // namespace bmg

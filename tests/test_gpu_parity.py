@@ -197,7 +197,7 @@ def test_interp_residual_term_variant_matches_oracle():
     hg.destroy()
 
 
-@pytest.mark.parametrize("name", ["poisson255", "blocks255", "lognormal255"])
+@pytest.mark.parametrize("name", ["poisson255", "blocks255", "lognormal255", "wide2047x127"])
 def test_fp32_refinement_reaches_fp64_tolerance(name):
     pr = problem(name)
     ro = oracle_solve(name)
