@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 namespace bmg {
 
@@ -148,8 +149,8 @@ void free_hierarchy(Hierarchy* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->arena) cudaFree(h->arena);
   if (h->sc_host) cudaFreeHost(h->sc_host);
-  delete h->maps64;
-  delete h->maps32;
+  for (auto* m : h->maps64) delete m;
+  for (auto* m : h->maps32) delete m;
   delete h;
 }
 
@@ -262,19 +263,22 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   }
   if ((rc = check_derr(h, s))) return fail(rc);
 
-  // TMA descriptors of the finest level (the level the fine sweeps read)
+  // TMA descriptors of every level swept by the TMA-staged kernel
+  auto make_maps = [&](auto& lv, auto& maps) {
+    using M = std::remove_pointer_t<typename std::remove_reference_t<decltype(maps)>::value_type>;
+    maps.assign(lv.size(), nullptr);
+    for (size_t l = 0; l < lv.size(); ++l) {
+      M* m = new M;
+      if (make_sweep_maps(lv[l], derr, m))
+        maps[l] = m;
+      else
+        delete m;
+    }
+  };
   if (!fp32) {
-    h->maps64 = new SweepMaps<double>;
-    if (!make_sweep_maps<double>(h->d.back(), derr, h->maps64)) {
-      delete h->maps64;
-      h->maps64 = nullptr;
-    }
+    make_maps(h->d, h->maps64);
   } else {
-    h->maps32 = new SweepMaps<float>;
-    if (!make_sweep_maps<float>(h->f.back(), derr, h->maps32)) {
-      delete h->maps32;
-      h->maps32 = nullptr;
-    }
+    make_maps(h->f, h->maps32);
   }
 
   // Level schedule: which levels leave the full-grid launches.
@@ -288,15 +292,16 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
 // V-cycle schedule (Algorithm 1)
 // ---------------------------------------------------------------------------
 
+// TMA descriptors of level l of the FP64 (d) or FP32 (f) hierarchy, or null.
 template <typename T>
-const SweepMaps<T>* fine_sweep_maps(const Hierarchy* h);
+const SweepMaps<T>* level_maps(const Hierarchy* h, int l);
 template <>
-const SweepMaps<double>* fine_sweep_maps<double>(const Hierarchy* h) {
-  return h->maps64;
+const SweepMaps<double>* level_maps<double>(const Hierarchy* h, int l) {
+  return l >= 0 && l < int(h->maps64.size()) ? h->maps64[l] : nullptr;
 }
 template <>
-const SweepMaps<float>* fine_sweep_maps<float>(const Hierarchy* h) {
-  return h->maps32;
+const SweepMaps<float>* level_maps<float>(const Hierarchy* h, int l) {
+  return l >= 0 && l < int(h->maps32.size()) ? h->maps32[l] : nullptr;
 }
 
 template <typename T>
@@ -309,12 +314,11 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
   // interpolation also writes out of place, so every level's iterate is back
   // in lv[l].x when the cycle ends and every cycle issues the same launches.
   const bool interp_oop = ((nu1 + nu2) & 1) != 0;
-  const SweepMaps<T>* fine_maps = fine_sweep_maps<T>(h);
   auto sweep = [&](int l, bool reverse) {
     LevelV<T>& V = lv[l];
     const bool nine = l != L - 1;
     if (!nine) prof_begin(BMG_PROF_FINE_SMOOTH, s);
-    launch_sweep<T>(V, nine, reverse, V.x, V.x2, s, nine ? nullptr : fine_maps);
+    launch_sweep<T>(V, nine, reverse, V.x, V.x2, s, level_maps<T>(h, l));
     if (!nine) prof_end(BMG_PROF_FINE_SMOOTH, s);
     std::swap(V.x, V.x2);
   };
@@ -729,7 +733,8 @@ int bmg_op_relax(bmg_hierarchy* hp, int level, double* x, const double* b, int n
   bmg::launch_pack<double>(b, L.b, L.nx, L.ny, L.pitch, s);
   const bool fine = level == h->L - 1;
   for (int k = 0; k < nu; ++k) {
-    bmg::launch_sweep<double>(L, !fine, reverse != 0, L.x, L.x2, s, fine ? h->maps64 : nullptr);
+    bmg::launch_sweep<double>(L, !fine, reverse != 0, L.x, L.x2, s,
+                              bmg::level_maps<double>(h, level));
     std::swap(L.x, L.x2);
   }
   bmg::launch_unpack<double>(L.x, x, L.nx, L.ny, L.pitch, s);

@@ -242,13 +242,14 @@ struct Scalars {            // device-resident solve state
 };
 
 // 2-D TMA descriptors of the planes the TMA-staged sweep reads, for one
-// 5-point level (built at setup; see make_sweep_maps).
+// level (built at setup; see make_sweep_maps).
 template <typename T>
 struct SweepMaps {
-  CUtensorMap x, x2, ic, w, s, b;
+  CUtensorMap x, x2, ic, w, s, b, sw, nw;   // sw, nw: 9-point levels only
   const T* xp;      // plane the map `x` describes
   const T* x2p;     // plane the map `x2` describes
   int* err;         // device error word (DEV_TIMEOUT)
+  bool nine;        // 9-point level (four colours, seven staged planes)
 };
 
 struct Timing;
@@ -282,10 +283,11 @@ struct Hierarchy {
   void* arena = nullptr;
   size_t arena_bytes = 0;
   double setup_ms = 0.0;
-  // TMA descriptors of the finest level (null when the level is swept by
-  // the tiled kernel)
-  SweepMaps<double>* maps64 = nullptr;
-  SweepMaps<float>* maps32 = nullptr;
+  // TMA descriptors per level of d / f (null where a level is swept by the
+  // tiled kernel)
+  std::vector<SweepMaps<double>*> maps64;
+  std::vector<SweepMaps<float>*> maps32;
+
 };
 
 // Observability: launch counter and optional event bracketing of one kernel
@@ -327,13 +329,15 @@ template <typename T>
 void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s,
                    T* out = nullptr);
 void prepare_sweep_kernels();
-// TMA descriptors of a 5-point level for the TMA-staged sweep; false (and no
+// TMA descriptors of a level for the TMA-staged sweep; false (and no
 // descriptors) when the level is swept by the tiled kernel instead.
 template <typename T>
 bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m);
+
 // One multicolour Gauss-Seidel sweep of a level as a single kernel: reads
 // the iterate from xin and writes the swept iterate to xout (xin != xout).
-// `maps` (finest level only, may be null) selects the TMA-staged kernel.
+// `maps` (the level's descriptors, may be null) selects the TMA-staged
+// kernel.
 template <typename T>
 void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* xout,
                   cudaStream_t s, const SweepMaps<T>* maps = nullptr);

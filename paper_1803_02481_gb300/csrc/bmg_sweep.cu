@@ -26,32 +26,53 @@ __global__ void __launch_bounds__(NT) k_sweep(LevelV<T> L, const T* __restrict__
 // block (36 KB of shared memory in FP64: six blocks per SM).
 constexpr int kStreamNT = 64, kStreamR = 32;
 
-// TMA-staged kernel shapes (tile TX x TY, NT threads, MINB blocks per SM),
-// one table per precision.  Entry 0 is the default, measured fastest on the
-// fine level: FP64 64 x 16 tiles, 512 threads, two blocks per SM (FP64 is
-// ALU-bound: more warps hide the FP64 latency); FP32 128 x 16 tiles, 256
-// threads, two blocks per SM (memory-bound: four stages per SM in flight).
-// BMG_TMA_CFG selects another entry, for measurements.
+// TMA-staged kernel shapes: tile TX x TY, NT threads, MINB blocks per SM.
+// 5-point levels (measured fastest on the finest level): FP64 64 x 16 tiles,
+// 608 threads, two blocks per SM (FP64 is ALU-bound: more warps hide the
+// FP64 latency, and 608 threads give every thread one point in each colour
+// phase, 594 red points on the grown tile); FP32 128 x 16 tiles, 256
+// threads, two blocks per SM (memory-bound: four stages per SM in flight).  9-point levels: a table per
+// precision.  Entry 0 of each table is the default; BMG_TMA_CFG (5-point)
+// and BMG_TMA9_CFG (9-point) select other entries, for measurements.
 struct TmaCfg {
   int tx, ty, nt, minb;
 };
-constexpr TmaCfg kTma64[] = {{64, 16, 512, 2}, {128, 16, 256, 1}, {128, 16, 512, 1},
-                             {128, 16, 1024, 1}, {64, 16, 256, 2}};
-constexpr TmaCfg kTma32[] = {{128, 16, 256, 2}, {128, 32, 256, 1}, {128, 32, 512, 1},
-                             {128, 16, 512, 2}, {128, 8, 256, 3}};
-constexpr int kNumTmaCfg = 5;
+constexpr TmaCfg kRb64[] = {{64, 16, 608, 2}, {64, 16, 512, 2}};
+constexpr TmaCfg kRb32[] = {{128, 16, 256, 2}, {64, 16, 256, 3}};
+constexpr int kNumRbCfg = 2;
+constexpr TmaCfg kNine64[] = {{32, 16, 256, 2}, {32, 32, 512, 1}, {32, 32, 1024, 1},
+                              {64, 16, 512, 1}, {16, 16, 256, 3}};
+constexpr TmaCfg kNine32[] = {{64, 16, 256, 2}, {32, 32, 256, 2}, {64, 32, 512, 1},
+                              {32, 16, 256, 3}, {128, 16, 256, 1}};
+constexpr int kNumNineCfg = 5;
 
-static int tma_cfg_index() {
+static int env_int(const char* name, int dflt) {
+  const char* e = std::getenv(name);
+  return e && e[0] ? std::atoi(e) : dflt;
+}
+static int nine_cfg_index() {
   static const int v = [] {
-    const char* e = std::getenv("BMG_TMA_CFG");
-    const int k = e ? std::atoi(e) : 0;
-    return k >= 0 && k < kNumTmaCfg ? k : 0;
+    const int k = env_int("BMG_TMA9_CFG", 0);
+    return k >= 0 && k < kNumNineCfg ? k : 0;
+  }();
+  return v;
+}
+// 9-point levels narrower than this use the tiled kernel (BMG_TMA9_MIN).
+static int nine_tma_min_side() {
+  static const int v = env_int("BMG_TMA9_MIN", 0);
+  return v;
+}
+static int rb_cfg_index() {
+  static const int v = [] {
+    const int k = env_int("BMG_TMA_CFG", 0);
+    return k >= 0 && k < kNumRbCfg ? k : 0;
   }();
   return v;
 }
 template <typename T>
-static TmaCfg tma_cfg() {
-  return sizeof(T) == 8 ? kTma64[tma_cfg_index()] : kTma32[tma_cfg_index()];
+static TmaCfg tma_cfg(bool nine) {
+  if (!nine) return sizeof(T) == 8 ? kRb64[rb_cfg_index()] : kRb32[rb_cfg_index()];
+  return sizeof(T) == 8 ? kNine64[nine_cfg_index()] : kNine32[nine_cfg_index()];
 }
 
 // Kernel for large 5-point levels: 0 = streaming strips, 1 = tiled (one
@@ -59,10 +80,7 @@ static TmaCfg tma_cfg() {
 // 3 = persistent TMA-staged tiles (the default).  BMG_RB_KERNEL overrides the
 // default, for measurements.
 static int rb_kernel_choice() {
-  static const int v = [] {
-    const char* e = std::getenv("BMG_RB_KERNEL");
-    return e ? std::atoi(e) : 3;
-  }();
+  static const int v = env_int("BMG_RB_KERNEL", 3);
   return v;
 }
 static bool stream_rb_enabled() { return rb_kernel_choice() == 0; }
@@ -100,17 +118,15 @@ static EncodeTiledFn encode_tiled() {
 // Descriptor of one plane (base = element (0, 0)) as a 2-D tensor of
 // (ny + 2) rows of `pitch` elements, starting base_shift elements before the
 // plane base (the 128-byte aligned start of its allocation), staged in boxes
-// of the TMA tile shape.
+// of bw x bh elements.
 template <typename T>
-static bool encode_plane(CUtensorMap* m, const T* base, int pitch, int ny) {
-  const TmaCfg c = tma_cfg<T>();
-  const int ha = int(16 / sizeof(T));
+static bool encode_plane(CUtensorMap* m, const T* base, int pitch, int ny, int bw, int bh) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn || !base) return false;
   void* start = const_cast<T*>(base - base_shift<T>());
   const cuuint64_t dims[2] = {cuuint64_t(pitch), cuuint64_t(ny + 2)};
   const cuuint64_t strides[1] = {cuuint64_t(pitch) * sizeof(T)};
-  const cuuint32_t box[2] = {cuuint32_t(c.tx + 2 * ha), cuuint32_t(c.ty + 4)};
+  const cuuint32_t box[2] = {cuuint32_t(bw), cuuint32_t(bh)};
   const cuuint32_t estr[2] = {1, 1};
   const CUtensorMapDataType dt =
       sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -119,57 +135,88 @@ static bool encode_plane(CUtensorMap* m, const T* base, int pitch, int ny) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Descriptors of the planes of L for boxes of a c.tx x c.ty tile and nph
+// colour phases.
 template <typename T>
-bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m) {
-  if (rb_kernel_choice() != 3 || L.nx < 1024 || L.SW) return false;
+static bool encode_level(const LevelV<T>& L, const TmaCfg& c, int nph, int* err,
+                         SweepMaps<T>* m) {
+  const bool nine = L.SW != nullptr;
   std::memset(static_cast<void*>(m), 0, sizeof(*m));
-  const bool ok = encode_plane<T>(&m->x, L.x, L.pitch, L.ny) &&
-                  encode_plane<T>(&m->x2, L.x2, L.pitch, L.ny) &&
-                  encode_plane<T>(&m->ic, L.iC, L.pitch, L.ny) &&
-                  encode_plane<T>(&m->w, L.W, L.pitch, L.ny) &&
-                  encode_plane<T>(&m->s, L.S, L.pitch, L.ny) &&
-                  encode_plane<T>(&m->b, L.b, L.pitch, L.ny);
+  const int align = int(16 / sizeof(T));
+  const int ha = nph > align ? nph : align;
+  const int bw = c.tx + 2 * ha, bh = c.ty + 2 * nph;
+  auto enc = [&](CUtensorMap* mm, const T* base) {
+    return encode_plane<T>(mm, base, L.pitch, L.ny, bw, bh);
+  };
+  bool ok = enc(&m->x, L.x) && enc(&m->x2, L.x2) && enc(&m->ic, L.iC) && enc(&m->w, L.W) &&
+            enc(&m->s, L.S) && enc(&m->b, L.b);
+  if (nine) ok = ok && enc(&m->sw, L.SW) && enc(&m->nw, L.NW);
   m->xp = L.x;
   m->x2p = L.x2;
   m->err = err;
+  m->nine = nine;
   return ok;
 }
 
-template <typename T, int TX, int TY, int NT, int MINB>
+template <typename T>
+bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m) {
+  const bool nine = L.SW != nullptr;
+  if (!nine && (rb_kernel_choice() != 3 || L.nx < 1024)) return false;
+  if (nine && L.nx < nine_tma_min_side()) return false;
+  return encode_level<T>(L, tma_cfg<T>(nine), nine ? 4 : 2, err, m);
+}
+
+
+// `order`: 4 bits per colour phase (sub-lattice masks, see rb_order).
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB>
 static void launch_tma_shape(const LevelV<T>& L, const SweepMaps<T>& m, const CUtensorMap& mx,
-                             bool reverse, T* xout, cudaStream_t s) {
-  using G = TmaTile<T, TX, TY>;
+                             unsigned order, T* xout, cudaStream_t s) {
+  using G = TmaTile<T, NINE, TX, TY>;
   const int ntiles = ((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
   const int cap = sm_count() * MINB;
-  k_sweep_rb_tma<T, TX, TY, NT, MINB><<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(
-      mx, m.ic, m.w, m.s, m.b, L, xout, rb_order(reverse), m.err);
+  // 5-point levels have no SW/NW planes: their maps are passed unused
+  const CUtensorMap& msw = NINE ? m.sw : m.b;
+  const CUtensorMap& mnw = NINE ? m.nw : m.b;
+  k_sweep_tma<T, NINE, TX, TY, NT, MINB><<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(
+      mx, m.ic, m.w, m.s, m.b, msw, mnw, L, xout, order, m.err);
 }
 
-template <typename T, int TX, int TY, int NT, int MINB>
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB>
 static void allow_tma_smem() {
-  cudaFuncSetAttribute(k_sweep_rb_tma<T, TX, TY, NT, MINB>,
+  cudaFuncSetAttribute(k_sweep_tma<T, NINE, TX, TY, NT, MINB>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       int(TmaTile<T, TX, TY>::SMEM));
+                       int(TmaTile<T, NINE, TX, TY>::SMEM));
 }
 
-// Instantiates BODY(T, TX, TY, NT, MINB) for entry K of T's shape table.
-#define BMG_TMA_DISPATCH(T, K, BODY)                                  \
+// Instantiates BODY(T, NINE, TX, TY, NT, MINB) for entry K of T's 5-point
+// or 9-point table (the shapes of kRb64/kRb32, kNine64/kNine32).
+#define BMG_TMA_DISPATCH(T, NINE, K, BODY)                             \
   do {                                                                 \
-    if constexpr (sizeof(T) == 8) {                                    \
+    if constexpr (!(NINE) && sizeof(T) == 8) {                         \
+      if (K == 1)                                                      \
+        BODY(T, false, 64, 16, 512, 2);                                \
+      else                                                             \
+        BODY(T, false, 64, 16, 608, 2);                                \
+    } else if constexpr (!(NINE)) {                                    \
+      if (K == 1)                                                      \
+        BODY(T, false, 64, 16, 256, 3);                                \
+      else                                                             \
+        BODY(T, false, 128, 16, 256, 2);                               \
+    } else if constexpr (sizeof(T) == 8) {                             \
       switch (K) {                                                     \
-        case 1: BODY(T, 128, 16, 256, 1); break;                       \
-        case 2: BODY(T, 128, 16, 512, 1); break;                       \
-        case 3: BODY(T, 128, 16, 1024, 1); break;                      \
-        case 4: BODY(T, 64, 16, 256, 2); break;                        \
-        default: BODY(T, 64, 16, 512, 2); break;                       \
+        case 1: BODY(T, true, 32, 32, 512, 1); break;                  \
+        case 2: BODY(T, true, 32, 32, 1024, 1); break;                 \
+        case 3: BODY(T, true, 64, 16, 512, 1); break;                  \
+        case 4: BODY(T, true, 16, 16, 256, 3); break;                  \
+        default: BODY(T, true, 32, 16, 256, 2); break;                 \
       }                                                                \
     } else {                                                           \
       switch (K) {                                                     \
-        case 1: BODY(T, 128, 32, 256, 1); break;                       \
-        case 2: BODY(T, 128, 32, 512, 1); break;                       \
-        case 3: BODY(T, 128, 16, 512, 2); break;                       \
-        case 4: BODY(T, 128, 8, 256, 3); break;                        \
-        default: BODY(T, 128, 16, 256, 2); break;                      \
+        case 1: BODY(T, true, 32, 32, 256, 2); break;                  \
+        case 2: BODY(T, true, 64, 32, 512, 1); break;                  \
+        case 3: BODY(T, true, 32, 16, 256, 3); break;                  \
+        case 4: BODY(T, true, 128, 16, 256, 1); break;                 \
+        default: BODY(T, true, 64, 16, 256, 2); break;                 \
       }                                                                \
     }                                                                  \
   } while (0)
@@ -178,10 +225,16 @@ template <typename T>
 static void launch_sweep_tma(const LevelV<T>& L, const SweepMaps<T>& m, bool reverse,
                              const T* xin, T* xout, cudaStream_t s) {
   const CUtensorMap& mx = xin == m.xp ? m.x : m.x2;
-#define BMG_TMA_LAUNCH(TT, TX, TY, NT, MB) launch_tma_shape<TT, TX, TY, NT, MB>(L, m, mx, reverse, xout, s)
-  BMG_TMA_DISPATCH(T, tma_cfg_index(), BMG_TMA_LAUNCH);
+  const unsigned order = m.nine ? four_order(reverse) : rb_order(reverse);
+#define BMG_TMA_LAUNCH(TT, NN, TX, TY, NT, MB) \
+  launch_tma_shape<TT, NN, TX, TY, NT, MB>(L, m, mx, order, xout, s)
+  if (m.nine)
+    BMG_TMA_DISPATCH(T, true, nine_cfg_index(), BMG_TMA_LAUNCH);
+  else
+    BMG_TMA_DISPATCH(T, false, rb_cfg_index(), BMG_TMA_LAUNCH);
 #undef BMG_TMA_LAUNCH
 }
+
 
 template <typename T>
 void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* xout,
@@ -190,7 +243,10 @@ void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* 
   // colours); levels narrower than 1024 use small tiles so that they still
   // spread over all SMs.
   const bool small = L.nx < 1024;
-  if (nine) {
+  const bool tma = maps && maps->nine == nine && (xin == maps->xp || xin == maps->x2p);
+  if (tma) {
+    launch_sweep_tma<T>(L, *maps, reverse, xin, xout, s);
+  } else if (nine) {
     if (small) {
       constexpr int TX = 32, TY = 16;
       k_sweep<T, true, TX, TY, 128><<<dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), 128, 0, s>>>(
@@ -205,8 +261,6 @@ void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* 
       constexpr int TX = 32, TY = 16;
       k_sweep<T, false, TX, TY, 128><<<dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), 128, 0, s>>>(
           L, xin, xout, rb_order(reverse));
-    } else if (maps && (xin == maps->xp || xin == maps->x2p)) {
-      launch_sweep_tma<T>(L, *maps, reverse, xin, xout, s);
     } else if (stream_rb_enabled()) {
       constexpr int NT = kStreamNT, R = kStreamR;
       using S = StreamRB<T, NT, R>;
@@ -238,9 +292,11 @@ void prepare_sweep_kernels() {
     cudaFuncSetAttribute(k_sweep_rb_stream<float, kStreamNT, kStreamR>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(S32::Row) * S32::NSLOT));
-#define BMG_TMA_ALLOW(TT, TX, TY, NT, MB) allow_tma_smem<TT, TX, TY, NT, MB>()
-    BMG_TMA_DISPATCH(double, tma_cfg_index(), BMG_TMA_ALLOW);
-    BMG_TMA_DISPATCH(float, tma_cfg_index(), BMG_TMA_ALLOW);
+#define BMG_TMA_ALLOW(TT, NN, TX, TY, NT, MB) allow_tma_smem<TT, NN, TX, TY, NT, MB>()
+    BMG_TMA_DISPATCH(double, false, rb_cfg_index(), BMG_TMA_ALLOW);
+    BMG_TMA_DISPATCH(float, false, rb_cfg_index(), BMG_TMA_ALLOW);
+    BMG_TMA_DISPATCH(double, true, nine_cfg_index(), BMG_TMA_ALLOW);
+    BMG_TMA_DISPATCH(float, true, nine_cfg_index(), BMG_TMA_ALLOW);
 #undef BMG_TMA_ALLOW
     sm_count();
     encode_tiled();

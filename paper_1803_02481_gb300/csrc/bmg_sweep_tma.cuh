@@ -1,23 +1,24 @@
-// Persistent, TMA-staged red-black Gauss-Seidel sweep of a large 5-point
-// level (smoothing of Algorithm 1).
+// Persistent, TMA-staged multicolour Gauss-Seidel sweep (smoothing of
+// Algorithm 1): red-black on 5-point levels, four colours on 9-point levels.
 //
-// One thread block per SM walks the level's TX x TY tiles.  For each tile,
-// one thread issues five 2-D bulk tensor copies (cp.async.bulk.tensor) of the
-// tile plus a halo: the old iterate and the planes 1/C, W, S and b.  They land
-// in one of two shared-memory stages and complete on that stage's mbarrier.
+// Persistent blocks (one or a few per SM) walk the level's TX x TY tiles.
+// For each tile, one thread issues 2-D bulk tensor copies
+// (cp.async.bulk.tensor) of the tile plus a halo: the old iterate and the
+// planes 1/C, W, S, b (and SW, NW on 9-point levels).  They land in one of
+// two shared-memory stages and complete on that stage's mbarrier.
 // While the block relaxes tile t out of one stage, the copies of its next
 // tile fill the other, so HBM traffic and arithmetic overlap inside the block.
 //
-// The relaxation itself is the redundant-halo scheme of the tiled kernel: the
-// first colour is updated on the tile grown by one cell, the second on the
-// tile, so no block reads another block's new values.  The new iterate goes
-// to a second buffer.  Per-point arithmetic is gs_apply, as in every other
+// The relaxation itself is the redundant-halo scheme of the tiled kernel:
+// colour phase k of NPH (2 red-black, 4 four-colour) is updated on the tile
+// grown by NPH - 1 - k cells, so no block reads another block's new values.  The new iterate goes to a
+// second buffer.  Per-point arithmetic is gs_apply, as in every other
 // kernel, so the result is bit-identical to theirs.
 //
-// Staged box: rows j0-2 .. j0+TY+1 and columns i0-HA .. i0+TX+HA-1 of each
-// plane, (i0, j0) the tile's first interior point.  HA = 16 / sizeof(T) keeps
-// the box's first column on a 16-byte boundary (interior rows start on a
-// 128-byte boundary); only two halo columns are used.  Rows and columns
+// Staged box: rows j0-NPH .. j0+TY+NPH-1 and columns i0-HA .. i0+TX+HA-1
+// of each plane, (i0, j0) the tile's first interior point.  HA >= NPH columns
+// make 16 bytes a whole number of times, which keeps the box's first column
+// on a 16-byte boundary (interior rows start on a 128-byte boundary).  Rows and columns
 // outside the plane read as zero, the Dirichlet ghost value.
 //
 // Every wait on an mbarrier gives up after one second: the block then sets
@@ -101,31 +102,40 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 
 }  // namespace tma_detail
 
-// Shape of the staged tile.
-template <typename T, int TX, int TY>
+// Shape of the staged tile.  NPH colour phases (2 on 5-point levels, 4 on
+// 9-point levels) need NPH halo rows and at least NPH halo columns; HA
+// columns are staged so that the box start stays 16-byte aligned.
+template <typename T, bool NINE, int TX, int TY>
 struct TmaTile {
-  static constexpr int HA = int(16 / sizeof(T));   // halo columns staged on each side
-  static constexpr int BW = TX + 2 * HA;           // box width (elements)
-  static constexpr int BH = TY + 4;                // box height: two halo rows each side
-  static constexpr int PLANE = BW * BH;            // elements of one staged plane
-  static constexpr int NPL = 5;                    // x, 1/C, W, S, b
+  static constexpr int NPH = NINE ? 4 : 2;                  // colour phases
+  static constexpr int ALIGN = int(16 / sizeof(T));        // elements per 16 bytes
+  static constexpr int HA = NPH > ALIGN ? NPH : ALIGN;      // halo columns staged on each side
+  static constexpr int BW = TX + 2 * HA;                    // box width (elements)
+  static constexpr int BH = TY + 2 * NPH;                   // box height
+  static constexpr int PLANE = BW * BH;                     // elements of one staged plane
+  static constexpr int NPL = NINE ? 7 : 5;                  // x, 1/C, W, S, b (, SW, NW)
   static constexpr unsigned STAGE_BYTES = unsigned(NPL * PLANE * sizeof(T));
   static constexpr size_t SMEM = 2 * size_t(STAGE_BYTES);
   static_assert(TX % 4 == 0 && TY % 2 == 0, "tile sides keep colours and TMA alignment");
+  static_assert(HA % ALIGN == 0 && HA % 2 == 0, "box start aligned, colour parity kept");
   static_assert(BW <= 256 && BH <= 256, "TMA box sides are at most 256 elements");
   static_assert((BW * sizeof(T)) % 16 == 0, "TMA box rows are multiples of 16 bytes");
   static_assert((PLANE * sizeof(T)) % 128 == 0, "staged planes start 128-byte aligned");
 };
 
-template <typename T, int TX, int TY, int NT, int MINB>
+// Planes a TMA sweep stages, in their order in a stage.
+enum TmaPlane { TP_X = 0, TP_IC, TP_W, TP_S, TP_B, TP_SW, TP_NW };
+
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
-    k_sweep_rb_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mic,
-                   const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap ms,
-                   const __grid_constant__ CUtensorMap mb, LevelV<T> L, T* __restrict__ xout,
-                   unsigned order, int* __restrict__ err) {
+    k_sweep_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mic,
+                const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap ms,
+                const __grid_constant__ CUtensorMap mb, const __grid_constant__ CUtensorMap msw,
+                const __grid_constant__ CUtensorMap mnw, LevelV<T> L, T* __restrict__ xout,
+                unsigned order, int* __restrict__ err) {
   using namespace tma_detail;
-  using G = TmaTile<T, TX, TY>;
-  constexpr int BW = G::BW, HA = G::HA, PL = G::PLANE;
+  using G = TmaTile<T, NINE, TX, TY>;
+  constexpr int BW = G::BW, HA = G::HA, PL = G::PLANE, NPH = G::NPH;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[2];
   const int nx = L.nx, ny = L.ny, p = L.pitch;
@@ -146,15 +156,19 @@ __global__ void __launch_bounds__(NT, MINB)
   auto issue = [&](int s, int t) {
     const int bx = t % ntx, by = t / ntx;
     const int X = bx * TX + 1 - HA + base_shift<T>();   // tensor column of the box start
-    const int Y = by * TY - 1;                          // tensor row (= j) of the box start
+    const int Y = by * TY + 1 - NPH;                    // tensor row (= j) of the box start
     T* d = s ? stage1 : stage0;
     uint64_t* b = &bar[s];
     mbar_expect_tx(b, G::STAGE_BYTES);
-    tma_load_2d(d + 0 * PL, &mx, X, Y, b);
-    tma_load_2d(d + 1 * PL, &mic, X, Y, b);
-    tma_load_2d(d + 2 * PL, &mw, X, Y, b);
-    tma_load_2d(d + 3 * PL, &ms, X, Y, b);
-    tma_load_2d(d + 4 * PL, &mb, X, Y, b);
+    tma_load_2d(d + TP_X * PL, &mx, X, Y, b);
+    tma_load_2d(d + TP_IC * PL, &mic, X, Y, b);
+    tma_load_2d(d + TP_W * PL, &mw, X, Y, b);
+    tma_load_2d(d + TP_S * PL, &ms, X, Y, b);
+    tma_load_2d(d + TP_B * PL, &mb, X, Y, b);
+    if (NINE) {
+      tma_load_2d(d + TP_SW * PL, &msw, X, Y, b);
+      tma_load_2d(d + TP_NW * PL, &mnw, X, Y, b);
+    }
   };
 
   int t = blockIdx.x;
@@ -176,19 +190,22 @@ __global__ void __launch_bounds__(NT, MINB)
     }
 
     T* const sx = s ? stage1 : stage0;
-    const T* const sic = sx + 1 * PL;
-    const T* const sw = sx + 2 * PL;
-    const T* const ss = sx + 3 * PL;
-    const T* const sb = sx + 4 * PL;
+    const T* const sic = sx + TP_IC * PL;
+    const T* const sw = sx + TP_W * PL;
+    const T* const ss = sx + TP_S * PL;
+    const T* const sb = sx + TP_B * PL;
+    const T* const ssw = sx + TP_SW * PL;
+    const T* const snw = sx + TP_NW * PL;
     const int bx = t % ntx, by = t / ntx;
     const int i0 = bx * TX + 1, j0 = by * TY + 1;
-    // Shared cell (r, c) holds domain point (i0 + c - HA, j0 + r - 2).  With
-    // TX, TY and HA even, the 0-based domain parities of (r, c) are (r, c) & 1.
+    // Shared cell (r, c) holds domain point (i0 + c - HA, j0 + r - NPH).  With
+    // TX, TY, HA and NPH even, the 0-based domain parities of (r, c) are
+    // (r & 1, c & 1).  Phase k is relaxed on the tile grown by NPH - 1 - k.
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < NPH; ++k) {
       const unsigned mask = (order >> (4 * k)) & 0xFu;
-      const int ring = 1 - k;
-      const int r0 = 2 - ring, r1 = 2 + TY + ring;
+      const int ring = NPH - 1 - k;
+      const int r0 = NPH - ring, r1 = NPH + TY + ring;
       const int c0 = HA - ring, c1 = HA + TX + ring;
 #pragma unroll
       for (int sl = 0; sl < 4; ++sl) {
@@ -198,21 +215,38 @@ __global__ void __launch_bounds__(NT, MINB)
         const int cf = c0 + ((pi - c0) & 1);
         const int nr = (r1 - rf + 1) >> 1, ncol = (c1 - cf + 1) >> 1;
         const int npts = nr * ncol;
+        // point q = rr * ncol + cc of the sub-lattice; q advances by NT, so
+        // (rr, cc) advance by (NT / ncol, NT % ncol) with one carry
+        const int drr = NT / ncol, dcc = NT - drr * ncol;
+        int rr = tid / ncol, cc = tid - rr * ncol;
         for (int q = tid; q < npts; q += NT) {
-          const int rr = q / ncol;
-          const int r = rf + 2 * rr, c = cf + 2 * (q - rr * ncol);
-          const int i = i0 + c - HA, j = j0 + r - 2;
-          if (i < 1 || i > nx || j < 1 || j > ny) continue;
+          const int r = rf + 2 * rr, c = cf + 2 * cc;
+          rr += drr;
+          cc += dcc;
+          if (cc >= ncol) {
+            cc -= ncol;
+            ++rr;
+          }
+          // domain point (i, j) = (i0 + c - HA, j0 + r - NPH) inside 1..nx, 1..ny
+          if (unsigned(i0 + c - HA - 1) >= unsigned(nx) ||
+              unsigned(j0 + r - NPH - 1) >= unsigned(ny))
+            continue;
           const int o = r * BW + c;
-          GsCoef<T, false> cf_;
+          GsCoef<T, NINE> cf_;
           cf_.b = sb[o];
           cf_.ic = sic[o];
           cf_.w = sw[o];
           cf_.e = sw[o + 1];
           cf_.s = ss[o];
           cf_.n = ss[o + BW];
+          if (NINE) {
+            cf_.sw = ssw[o];
+            cf_.se = snw[o + 1 - BW];
+            cf_.nw = snw[o];
+            cf_.ne = ssw[o + 1 + BW];
+          }
           T* xp = sx + o;
-          *xp = gs_apply<T, false>(cf_, [&](int dx, int dy) { return xp[dx + dy * BW]; });
+          *xp = gs_apply<T, NINE>(cf_, [&](int dx, int dy) { return xp[dx + dy * BW]; });
         }
       }
       __syncthreads();
@@ -220,7 +254,7 @@ __global__ void __launch_bounds__(NT, MINB)
     for (int e = tid; e < TX * TY; e += NT) {
       const int r = e / TX, c = e - r * TX;
       const int i = i0 + c, j = j0 + r;
-      if (i <= nx && j <= ny) xout[j * p + i] = sx[(r + 2) * BW + c + HA];
+      if (i <= nx && j <= ny) xout[j * p + i] = sx[(r + NPH) * BW + c + HA];
     }
     // this stage is refilled by the copies issued in the next iteration
     fence_proxy_async();
