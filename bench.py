@@ -45,6 +45,25 @@ WORKLOAD = {"workload": "diffusion 4095x4095, 64x64-cell blocks k=10^U(-4,4), se
             "tol_note": "1e-10 is below the FP64 floor of this field (residual stagnates at 6.0e-10)"}
 
 
+# DRAM bytes (read + write) per fine unknown of one fine-level sweep launch,
+# from the ncu capture summarised in profiles/k_sweep_tma_fine_ncu.md; set
+# to None whenever the kernel changes until it is captured again.
+SWEEP_DRAM_BYTES_PER_UNKNOWN = {
+    "fp64": (169.331456e6 + 18.557440e6) / 4190209,    # 2047^2 block field
+    "fp32": (338.771456e6 + 52.550912e6) / 16769025,   # 4095^2 log-normal field
+}
+
+
+def alu_peak_gflops(torch, dev, precision, clocks):
+    """Peak FMA rate derived from unit counts and the SM clock: FP64 2 FMA
+    per clock per SM on GB300, FP32 128; 2 flops per FMA."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    per_sm = 2 if precision == "fp64" else 128
+    return (sms * per_sm * 2 * mhz / 1e3,
+            f"derived: {sms} SMs x {per_sm} FMA/clk x 2 flops x {mhz:g} MHz")
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -262,13 +281,13 @@ def run_ours(args, rank, world, local_rank):
         xh = torch.zeros_like(bh).pin_memory()
         kn, bn, xn = kh.numpy(), bh.numpy(), xh.numpy()
         reps = max(1, args.steps // 2)
-        bm.solve_host(kn, bn, xn, opts, TOL, stream=stream)
+        bm.solve_host(kn, bn, xn, opts, tol, stream=stream)
         tot = 0.0
         for _ in range(reps):
             xn[...] = 0.0
             torch.cuda.synchronize()
             ev0.record(stream)
-            bm.solve_host(kn, bn, xn, opts, TOL, stream=stream)
+            bm.solve_host(kn, bn, xn, opts, tol, stream=stream)
             ev1.record(stream)
             torch.cuda.synchronize()
             tot += ev0.elapsed_time(ev1)
@@ -278,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
 
     peaks, peak_kind = load_peaks()
     # fine-level smoothing: one bracket = one full red-black sweep over the
-    # 4095^2 level.  Algorithmic bytes per fine unknown: 1/C, W, S, b and x
+    # fine level.  Algorithmic bytes per fine unknown: 1/C, W, S, b and x
     # read, x written = 6 words (48 B FP64); flops: 4 FMA + 1 MUL = 9.
     word = 8.0 if args.precision == "fp64" else 4.0
     per_unit_b, per_unit_f = 6 * word, 9.0
@@ -286,23 +305,30 @@ def run_ours(args, rank, world, local_rank):
     gbs = per_unit_b * n_fine / (sweep_ms / 1e3) / 1e9
     gfl = per_unit_f * n_fine / (sweep_ms / 1e3) / 1e9
     f_hbm = gbs / peaks["hbm_gbs"]
-    alu_peak = calib["gpu_gflops64"] if args.precision == "fp64" else calib["gpu_gflops32"]
+    alu_peak, alu_src = alu_peak_gflops(torch, dev, args.precision, clk.summary())
     f_alu = gfl / alu_peak
-    common = {"kernel": "fine-level red-black Gauss-Seidel sweep (k_sweep, one launch per sweep)",
+    kname = "k_sweep_tma<%s, 5-point>" % ("double" if args.precision == "fp64" else "float")
+    # DRAM bytes per launch from the ncu capture of this kernel (a smaller
+    # grid of the same kind, scaled by the units one launch processes)
+    traffic_per_unit = SWEEP_DRAM_BYTES_PER_UNKNOWN.get(args.precision)
+    traffic = traffic_per_unit * n_fine if traffic_per_unit else None
+    common = {"kernel": kname + ": fine-level red-black Gauss-Seidel sweep, TMA-staged, one launch per sweep",
               "per_launch_ms": sweep_ms, "launches_timed": nprof,
               "timing": "CUDA events around every fine sweep of one full profiled step on the solve stream",
               "algorithmic_bytes_per_unknown": per_unit_b, "algorithmic_flops_per_unknown": per_unit_f,
               "units_per_launch": n_fine,
+              "traffic_source": "profiles/k_sweep_tma_fine_ncu.md (dram bytes per unknown x units)",
               "hbm": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": f_hbm,
                       "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
               "alu": {"achieved_gflops": gfl, "peak_gflops": alu_peak, "frac": f_alu,
-                      "peak_source": "bmg_calibrate: FMA chains on all SMs, this run"}}
+                      "peak_source": alu_src,
+                      "measured_gflops": calib["gpu_gflops64" if args.precision == "fp64" else "gpu_gflops32"]}}
     if f_alu > f_hbm:
         roofline = {"bound": "alu", "achieved": gfl, "peak": alu_peak, "unit": "GFLOP/s", "frac": f_alu,
-                    "traffic": None, **common}
+                    "traffic": traffic, **common}
     else:
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
-                    "traffic": None, **common}
+                    "traffic": traffic, **common}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
