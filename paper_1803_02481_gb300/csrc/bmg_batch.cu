@@ -154,6 +154,9 @@ __global__ void __launch_bounds__(kNT) k_brefine_resid(const LevelV<double>* __r
   const LevelV<double> L = f64[z];
   const LevelV<float> F = f32[z];
   const double inv = what ? sc[p].inv : 0.0;
+  // FP32 scaling of the right-hand side, as in the single-problem kernel
+  const bool fp32_scale = inv > 1e-28 && inv < 1e28;
+  const float inv32 = float(inv);
   double acc = 0.0;
   for (int j = blockIdx.x + 1; j <= L.ny; j += gridDim.x) {
     for (int i = threadIdx.x + 1; i <= L.nx; i += blockDim.x) {
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kNT) k_brefine_resid(const LevelV<double>* __r
         const double r = resid_value<double, false>(L, L.x, L.b[o], o);
         acc = fma(r, r, acc);
         const int of = j * F.pitch + i;
-        F.b[of] = float(r * inv);
+        F.b[of] = fp32_scale ? float(r) * inv32 : float(r * inv);
         F.x[of] = 0.0f;
       }
     }

@@ -26,25 +26,31 @@ __global__ void __launch_bounds__(NT) k_sweep(LevelV<T> L, const T* __restrict__
 // block (36 KB of shared memory in FP64: six blocks per SM).
 constexpr int kStreamNT = 64, kStreamR = 32;
 
-// TMA-staged kernel shapes: tile TX x TY, NT threads, MINB blocks per SM.
-// 5-point levels (measured fastest on the finest level): FP64 64 x 16 tiles,
-// 608 threads, two blocks per SM (FP64 is ALU-bound: more warps hide the
-// FP64 latency, and 608 threads give every thread one point in each colour
-// phase, 594 red points on the grown tile); FP32 128 x 16 tiles, 256
-// threads, two blocks per SM (memory-bound: four stages per SM in flight).  9-point levels: a table per
-// precision.  Entry 0 of each table is the default; BMG_TMA_CFG (5-point)
-// and BMG_TMA9_CFG (9-point) select other entries, for measurements.
+// TMA-staged kernel shapes: tile TX x TY, NT threads, MINB blocks per SM,
+// NSTAGE shared-memory stages per block.  Entry 0 of each table is the
+// default, the fastest measured on the GB300:
+//  * 5-point levels (the finest level): FP64 64 x 16 tiles, 608 threads, two
+//    blocks per SM, two stages (FP64 is ALU-bound: more warps hide the FP64
+//    latency, and 608 threads give every thread one point in each colour
+//    phase, 594 red points on the grown tile); FP32 128 x 16 tiles, 256
+//    threads, two blocks per SM, two stages (memory-bound: four stages per
+//    SM in flight).
+//  * 9-point levels (2047^2 and 4095^2 levels): one stage per block and four
+//    blocks per SM (FP64 32 x 16 tiles, FP32 64 x 16): with four colour
+//    phases per tile, more resident warps beat a second stage.
+// BMG_TMA_CFG (5-point) and BMG_TMA9_CFG (9-point) select other entries, for
+// measurements.
 struct TmaCfg {
-  int tx, ty, nt, minb;
+  int tx, ty, nt, minb, nstage;
 };
-constexpr TmaCfg kRb64[] = {{64, 16, 608, 2}, {64, 16, 512, 2}};
-constexpr TmaCfg kRb32[] = {{128, 16, 256, 2}, {64, 16, 256, 3}};
-constexpr int kNumRbCfg = 2;
-constexpr TmaCfg kNine64[] = {{32, 16, 256, 2}, {32, 32, 512, 1}, {32, 32, 1024, 1},
-                              {64, 16, 512, 1}, {16, 16, 256, 3}};
-constexpr TmaCfg kNine32[] = {{64, 16, 256, 2}, {32, 32, 256, 2}, {64, 32, 512, 1},
-                              {32, 16, 256, 3}, {128, 16, 256, 1}};
-constexpr int kNumNineCfg = 5;
+constexpr TmaCfg kRb64[] = {{64, 16, 608, 2, 2}, {64, 16, 512, 2, 2}, {64, 16, 512, 4, 1}};
+constexpr TmaCfg kRb32[] = {{128, 16, 256, 2, 2}, {64, 16, 256, 3, 2}, {128, 16, 256, 4, 1}};
+constexpr int kNumRbCfg = 3;
+constexpr TmaCfg kNine64[] = {{32, 16, 256, 4, 1}, {32, 32, 512, 1, 2}, {32, 16, 256, 2, 2},
+                              {64, 16, 512, 1, 2}, {32, 16, 224, 2, 2}, {32, 32, 512, 2, 1}};
+constexpr TmaCfg kNine32[] = {{64, 16, 256, 4, 1}, {32, 32, 256, 2, 2}, {64, 16, 256, 2, 2},
+                              {32, 16, 256, 3, 2}, {128, 16, 256, 1, 2}, {32, 32, 256, 4, 1}};
+constexpr int kNumNineCfg = 6;
 
 static int env_int(const char* name, int dflt) {
   const char* e = std::getenv(name);
@@ -167,56 +173,80 @@ bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m) {
 }
 
 
+// Blocks of a TMA sweep shape resident per SM (at most MINB), measured once;
+// first called from prepare_sweep_kernels, after the shared-memory opt-in and
+// before any graph capture.
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE>
+static int tma_resident() {
+  static const int r = [] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE>, NT,
+            TmaTile<T, NINE, TX, TY, NSTAGE>::SMEM) != cudaSuccess ||
+        n < 1)
+      n = 1;
+    cudaGetLastError();
+    return n < MINB ? n : MINB;
+  }();
+  return r;
+}
+
 // `order`: 4 bits per colour phase (sub-lattice masks, see rb_order).
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB>
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE>
 static void launch_tma_shape(const LevelV<T>& L, const SweepMaps<T>& m, const CUtensorMap& mx,
                              unsigned order, T* xout, cudaStream_t s) {
-  using G = TmaTile<T, NINE, TX, TY>;
+  using G = TmaTile<T, NINE, TX, TY, NSTAGE>;
   const int ntiles = ((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
-  const int cap = sm_count() * MINB;
+  // persistent blocks: no more than fit on the GPU at once
+  const int cap = sm_count() * tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE>();
   // 5-point levels have no SW/NW planes: their maps are passed unused
   const CUtensorMap& msw = NINE ? m.sw : m.b;
   const CUtensorMap& mnw = NINE ? m.nw : m.b;
-  k_sweep_tma<T, NINE, TX, TY, NT, MINB><<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(
+  k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE><<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(
       mx, m.ic, m.w, m.s, m.b, msw, mnw, L, xout, order, m.err);
 }
 
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB>
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE>
 static void allow_tma_smem() {
-  cudaFuncSetAttribute(k_sweep_tma<T, NINE, TX, TY, NT, MINB>,
+  cudaFuncSetAttribute(k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       int(TmaTile<T, NINE, TX, TY>::SMEM));
+                       int(TmaTile<T, NINE, TX, TY, NSTAGE>::SMEM));
+  tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE>();
 }
 
-// Instantiates BODY(T, NINE, TX, TY, NT, MINB) for entry K of T's 5-point
-// or 9-point table (the shapes of kRb64/kRb32, kNine64/kNine32).
+// Instantiates BODY(T, NINE, TX, TY, NT, MINB, NSTAGE) for entry K of T's
+// 5-point or 9-point table (the shapes of kRb64/kRb32, kNine64/kNine32).
 #define BMG_TMA_DISPATCH(T, NINE, K, BODY)                             \
   do {                                                                 \
     if constexpr (!(NINE) && sizeof(T) == 8) {                         \
-      if (K == 1)                                                      \
-        BODY(T, false, 64, 16, 512, 2);                                \
-      else                                                             \
-        BODY(T, false, 64, 16, 608, 2);                                \
+      switch (K) {                                                     \
+        case 1: BODY(T, false, 64, 16, 512, 2, 2); break;              \
+        case 2: BODY(T, false, 64, 16, 512, 4, 1); break;              \
+        default: BODY(T, false, 64, 16, 608, 2, 2); break;             \
+      }                                                                \
     } else if constexpr (!(NINE)) {                                    \
-      if (K == 1)                                                      \
-        BODY(T, false, 64, 16, 256, 3);                                \
-      else                                                             \
-        BODY(T, false, 128, 16, 256, 2);                               \
+      switch (K) {                                                     \
+        case 1: BODY(T, false, 64, 16, 256, 3, 2); break;              \
+        case 2: BODY(T, false, 128, 16, 256, 4, 1); break;             \
+        default: BODY(T, false, 128, 16, 256, 2, 2); break;            \
+      }                                                                \
     } else if constexpr (sizeof(T) == 8) {                             \
       switch (K) {                                                     \
-        case 1: BODY(T, true, 32, 32, 512, 1); break;                  \
-        case 2: BODY(T, true, 32, 32, 1024, 1); break;                 \
-        case 3: BODY(T, true, 64, 16, 512, 1); break;                  \
-        case 4: BODY(T, true, 16, 16, 256, 3); break;                  \
-        default: BODY(T, true, 32, 16, 256, 2); break;                 \
+        case 1: BODY(T, true, 32, 32, 512, 1, 2); break;               \
+        case 2: BODY(T, true, 32, 16, 256, 2, 2); break;               \
+        case 3: BODY(T, true, 64, 16, 512, 1, 2); break;               \
+        case 4: BODY(T, true, 32, 16, 224, 2, 2); break;               \
+        case 5: BODY(T, true, 32, 32, 512, 2, 1); break;               \
+        default: BODY(T, true, 32, 16, 256, 4, 1); break;              \
       }                                                                \
     } else {                                                           \
       switch (K) {                                                     \
-        case 1: BODY(T, true, 32, 32, 256, 2); break;                  \
-        case 2: BODY(T, true, 64, 32, 512, 1); break;                  \
-        case 3: BODY(T, true, 32, 16, 256, 3); break;                  \
-        case 4: BODY(T, true, 128, 16, 256, 1); break;                 \
-        default: BODY(T, true, 64, 16, 256, 2); break;                 \
+        case 1: BODY(T, true, 32, 32, 256, 2, 2); break;               \
+        case 2: BODY(T, true, 64, 16, 256, 2, 2); break;               \
+        case 3: BODY(T, true, 32, 16, 256, 3, 2); break;               \
+        case 4: BODY(T, true, 128, 16, 256, 1, 2); break;              \
+        case 5: BODY(T, true, 32, 32, 256, 4, 1); break;               \
+        default: BODY(T, true, 64, 16, 256, 4, 1); break;              \
       }                                                                \
     }                                                                  \
   } while (0)
@@ -226,8 +256,8 @@ static void launch_sweep_tma(const LevelV<T>& L, const SweepMaps<T>& m, bool rev
                              const T* xin, T* xout, cudaStream_t s) {
   const CUtensorMap& mx = xin == m.xp ? m.x : m.x2;
   const unsigned order = m.nine ? four_order(reverse) : rb_order(reverse);
-#define BMG_TMA_LAUNCH(TT, NN, TX, TY, NT, MB) \
-  launch_tma_shape<TT, NN, TX, TY, NT, MB>(L, m, mx, order, xout, s)
+#define BMG_TMA_LAUNCH(TT, NN, TX, TY, NT, MB, NS) \
+  launch_tma_shape<TT, NN, TX, TY, NT, MB, NS>(L, m, mx, order, xout, s)
   if (m.nine)
     BMG_TMA_DISPATCH(T, true, nine_cfg_index(), BMG_TMA_LAUNCH);
   else
@@ -292,7 +322,7 @@ void prepare_sweep_kernels() {
     cudaFuncSetAttribute(k_sweep_rb_stream<float, kStreamNT, kStreamR>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(S32::Row) * S32::NSLOT));
-#define BMG_TMA_ALLOW(TT, NN, TX, TY, NT, MB) allow_tma_smem<TT, NN, TX, TY, NT, MB>()
+#define BMG_TMA_ALLOW(TT, NN, TX, TY, NT, MB, NS) allow_tma_smem<TT, NN, TX, TY, NT, MB, NS>()
     BMG_TMA_DISPATCH(double, false, rb_cfg_index(), BMG_TMA_ALLOW);
     BMG_TMA_DISPATCH(float, false, rb_cfg_index(), BMG_TMA_ALLOW);
     BMG_TMA_DISPATCH(double, true, nine_cfg_index(), BMG_TMA_ALLOW);

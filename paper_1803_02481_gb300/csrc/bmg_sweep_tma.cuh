@@ -1,13 +1,13 @@
 // Persistent, TMA-staged multicolour Gauss-Seidel sweep (smoothing of
 // Algorithm 1): red-black on 5-point levels, four colours on 9-point levels.
 //
-// Persistent blocks (one or a few per SM) walk the level's TX x TY tiles.
-// For each tile, one thread issues 2-D bulk tensor copies
-// (cp.async.bulk.tensor) of the tile plus a halo: the old iterate and the
-// planes 1/C, W, S, b (and SW, NW on 9-point levels).  They land in one of
-// two shared-memory stages and complete on that stage's mbarrier.
-// While the block relaxes tile t out of one stage, the copies of its next
-// tile fill the other, so HBM traffic and arithmetic overlap inside the block.
+// Persistent blocks (a few per SM) walk the level's TX x TY tiles.  For each
+// tile, one thread issues 2-D bulk tensor copies (cp.async.bulk.tensor) of
+// the tile plus a halo: the old iterate and the planes 1/C, W, S, b (and SW,
+// NW on 9-point levels).  They land in a shared-memory stage and complete on
+// that stage's mbarrier.  With two stages, the block relaxes tile t out of
+// one while the copies of its next tile fill the other; with one stage,
+// the other blocks on the SM do their arithmetic while a block waits.
 //
 // The relaxation itself is the redundant-halo scheme of the tiled kernel:
 // colour phase k of NPH (2 red-black, 4 four-colour) is updated on the tile
@@ -105,7 +105,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // Shape of the staged tile.  NPH colour phases (2 on 5-point levels, 4 on
 // 9-point levels) need NPH halo rows and at least NPH halo columns; HA
 // columns are staged so that the box start stays 16-byte aligned.
-template <typename T, bool NINE, int TX, int TY>
+template <typename T, bool NINE, int TX, int TY, int NSTAGE = 2>
 struct TmaTile {
   static constexpr int NPH = NINE ? 4 : 2;                  // colour phases
   static constexpr int ALIGN = int(16 / sizeof(T));        // elements per 16 bytes
@@ -115,7 +115,8 @@ struct TmaTile {
   static constexpr int PLANE = BW * BH;                     // elements of one staged plane
   static constexpr int NPL = NINE ? 7 : 5;                  // x, 1/C, W, S, b (, SW, NW)
   static constexpr unsigned STAGE_BYTES = unsigned(NPL * PLANE * sizeof(T));
-  static constexpr size_t SMEM = 2 * size_t(STAGE_BYTES);
+  static constexpr size_t SMEM = NSTAGE * size_t(STAGE_BYTES);
+  static_assert(NSTAGE == 1 || NSTAGE == 2, "one or two stages");
   static_assert(TX % 4 == 0 && TY % 2 == 0, "tile sides keep colours and TMA alignment");
   static_assert(HA % ALIGN == 0 && HA % 2 == 0, "box start aligned, colour parity kept");
   static_assert(BW <= 256 && BH <= 256, "TMA box sides are at most 256 elements");
@@ -126,7 +127,7 @@ struct TmaTile {
 // Planes a TMA sweep stages, in their order in a stage.
 enum TmaPlane { TP_X = 0, TP_IC, TP_W, TP_S, TP_B, TP_SW, TP_NW };
 
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB>
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE>
 __global__ void __launch_bounds__(NT, MINB)
     k_sweep_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mic,
                 const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap ms,
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(NT, MINB)
                 const __grid_constant__ CUtensorMap mnw, LevelV<T> L, T* __restrict__ xout,
                 unsigned order, int* __restrict__ err) {
   using namespace tma_detail;
-  using G = TmaTile<T, NINE, TX, TY>;
+  using G = TmaTile<T, NINE, TX, TY, NSTAGE>;
   constexpr int BW = G::BW, HA = G::HA, PL = G::PLANE, NPH = G::NPH;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -143,7 +144,8 @@ __global__ void __launch_bounds__(NT, MINB)
   const int ntiles = ntx * ((ny + TY - 1) / TY);
   const int tid = threadIdx.x;
   T* const stage0 = reinterpret_cast<T*>(tma_smem);
-  T* const stage1 = reinterpret_cast<T*>(tma_smem + G::STAGE_BYTES);
+  // with one stage, both names denote it (stage1 is never selected)
+  T* const stage1 = reinterpret_cast<T*>(tma_smem + (NSTAGE == 2 ? G::STAGE_BYTES : 0));
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -171,19 +173,24 @@ __global__ void __launch_bounds__(NT, MINB)
     }
   };
 
+  // Two stages: the copies of the next tile are issued before the current
+  // one is relaxed.  One stage: after it (more blocks per SM then overlap
+  // one block's copies with another's arithmetic).  Stage s serves
+  // iterations it with it % NSTAGE == s; its mbarrier phase is it / NSTAGE.
   int t = blockIdx.x;
   if (tid == 0 && t < ntiles) issue(0, t);
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
-    const int s = it & 1;
+    const int s = NSTAGE == 2 ? (it & 1) : 0;
+    const unsigned parity = unsigned(it / NSTAGE) & 1u;
     const int tn = t + gridDim.x;
-    if (tid == 0 && tn < ntiles) issue(s ^ 1, tn);
-    const bool ok = mbar_wait_bounded(&bar[s], unsigned(it >> 1) & 1u);
+    if (NSTAGE == 2 && tid == 0 && tn < ntiles) issue(s ^ 1, tn);
+    const bool ok = mbar_wait_bounded(&bar[s], parity);
     if (!__syncthreads_and(ok)) {
       if (tid == 0) {
         atomicOr(err, DEV_TIMEOUT);
         // the block's shared memory must outlive its copies in flight
-        mbar_wait_bounded(&bar[s], unsigned(it >> 1) & 1u);
-        if (tn < ntiles) mbar_wait_bounded(&bar[s ^ 1], unsigned((it + 1) >> 1) & 1u);
+        mbar_wait_bounded(&bar[s], parity);
+        if (NSTAGE == 2 && tn < ntiles) mbar_wait_bounded(&bar[s ^ 1], unsigned((it + 1) >> 1) & 1u);
       }
       __syncthreads();
       return;
@@ -256,9 +263,10 @@ __global__ void __launch_bounds__(NT, MINB)
       const int i = i0 + c, j = j0 + r;
       if (i <= nx && j <= ny) xout[j * p + i] = sx[(r + NPH) * BW + c + HA];
     }
-    // this stage is refilled by the copies issued in the next iteration
+    // this stage is refilled by the copies issued next
     fence_proxy_async();
     __syncthreads();
+    if (NSTAGE == 1 && tid == 0 && tn < ntiles) issue(0, tn);
   }
 }
 
