@@ -279,6 +279,18 @@ int bmg_residual_norm_noalloc(const double *k_dev, const double *x_dev,
                               const double *b_dev, int nx, int ny,
                               double *norms_dev, bmg_stream_t stream);
 
+/* Failure-detection self-test (no counterpart in the paper).  The TMA-staged
+ * sweeps wait for their bulk copies on mbarriers; every such wait gives up
+ * after about one second, records DEV_TIMEOUT in the solve's device error
+ * word and lets the kernel return, so a solve ends with BMG_ETIMEOUT instead
+ * of hanging the GPU.  This call runs that same bounded wait, in one thread
+ * of a one-block kernel, on a barrier phase that expects bytes no copy ever
+ * delivers.  Returns BMG_ETIMEOUT after about one second (the expected
+ * result), BMG_OK if the wait completed (it cannot), BMG_ENOMEM/BMG_ECUDA on
+ * a CUDA error.  Allocates and frees 4 bytes of device memory; synchronises
+ * `stream`. */
+int bmg_selftest_bounded_wait(bmg_stream_t stream);
+
 /* ---- Observability ------------------------------------------------------ */
 
 /* Total kernel launches this library has issued in this process. */

@@ -81,6 +81,7 @@ EXPORTED = {
     "bmg_calibrate": (_i, [_vp, _vp]),
     "bmg_predict_cycle_us": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "bmg_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp]),
+    "bmg_selftest_bounded_wait": (_i, [_vp]),
     "bmg_kernel_launches": (ctypes.c_longlong, []),
     "bmg_profile_set": (_i, [_i]),
     "bmg_profile_read": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
@@ -104,6 +105,12 @@ def calibrate(stream=None) -> dict:
 def kernel_launches() -> int:
     """Kernels the library has launched in this process."""
     return int(lib().bmg_kernel_launches())
+
+
+def selftest_bounded_wait(stream=None) -> int:
+    """Run the sweeps' bounded mbarrier wait on a phase nothing completes;
+    returns the status code (BMG_ETIMEOUT is the expected result)."""
+    return int(lib().bmg_selftest_bounded_wait(_stream(stream)))
 
 
 def profile_set(classes=()):

@@ -705,6 +705,10 @@ int bmg_level_interp(const bmg_hierarchy* hp, int level, double* host_out) {
   return bmg::interp_out<double>(h->d[level], h->d[level - 1], host_out);
 }
 
+int bmg_selftest_bounded_wait(bmg_stream_t stream) {
+  return bmg::selftest_bounded_wait(reinterpret_cast<cudaStream_t>(stream));
+}
+
 int bmg_coarse_factor(const bmg_hierarchy* hp, double* host_out, int n0_capacity) {
   const Hierarchy* h = H(hp);
   if (!h || !host_out || n0_capacity < h->n0) return BMG_EINVAL;

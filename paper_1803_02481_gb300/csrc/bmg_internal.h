@@ -329,6 +329,9 @@ template <typename T>
 void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s,
                    T* out = nullptr);
 void prepare_sweep_kernels();
+// Runs the TMA sweeps' bounded mbarrier wait on a phase nothing completes
+// (bmg_selftest_bounded_wait).
+int selftest_bounded_wait(cudaStream_t s);
 // TMA descriptors of a level for the TMA-staged sweep; false (and no
 // descriptors) when the level is swept by the tiled kernel instead.
 template <typename T>

@@ -335,6 +335,34 @@ void prepare_sweep_kernels() {
   (void)done;
 }
 
+// Failure-detection self-test: one thread waits, with the bounded wait of
+// the TMA sweeps, on an mbarrier phase that expects 16 bytes no copy ever
+// delivers, and records DEV_TIMEOUT when the wait gives up.
+__global__ void k_selftest_wait(int* __restrict__ err) {
+  using namespace tma_detail;
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  mbar_expect_tx(&bar, 16);
+  if (!mbar_wait_bounded(&bar, 0)) atomicOr(err, DEV_TIMEOUT);
+}
+
+int selftest_bounded_wait(cudaStream_t s) {
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return BMG_ENOMEM;
+  int h = 0, rc = BMG_ECUDA;
+  if (cudaMemsetAsync(d, 0, sizeof(int), s) == cudaSuccess) {
+    k_selftest_wait<<<1, 32, 0, s>>>(d);
+    count_launch();
+    if (cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess)
+      rc = (h & DEV_TIMEOUT) ? BMG_ETIMEOUT : BMG_OK;
+  }
+  cudaFree(d);
+  return rc;
+}
+
 template void launch_sweep<double>(const LevelV<double>&, bool, bool, const double*, double*,
                                    cudaStream_t, const SweepMaps<double>*);
 template void launch_sweep<float>(const LevelV<float>&, bool, bool, const float*, float*,

@@ -80,12 +80,13 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Waits for the phase of `bar` with the given parity to complete; false
-// after about one second.
+// after about one second (and, should the global timer not advance, after
+// 2^32 polls).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer_ns() - t0 > 1000000000ull) return false;
+  for (uint64_t n = 1; !mbar_try_wait(bar, parity); ++n) {
+    if (globaltimer_ns() - t0 > 1000000000ull || n > (1ull << 32)) return false;
   }
   return true;
 }
