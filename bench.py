@@ -54,6 +54,18 @@ SWEEP_DRAM_BYTES_PER_UNKNOWN = {
 }
 
 
+def aggregate(torch, ms, units, world, device):
+    """Whole-job timing across ranks: the slowest rank's time (MAX over
+    ranks) and the units all ranks processed divided by it.  Each rank runs
+    its own replica of the workload (no collective on the data path)."""
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units * world / (ms / 1e3)
+
+
 def alu_peak_gflops(torch, dev, precision, clocks):
     """Peak FMA rate derived from unit counts and the SM clock: FP64 2 FMA
     per clock per SM on GB300, FP32 128; 2 flops per FMA."""
@@ -268,18 +280,14 @@ def run_ours(args, rank, world, local_rank):
         breakdown[cname] = {"brackets": cnt, "ms_per_step": cms}
     nprof, prof_ms = bm.profile_read("fine_smooth")
     bm.profile_set(())
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n_fine * args.steps * world / (ms / 1e3)
+    ms, value = aggregate(torch, ms, n_fine * args.steps, world, dev)
     info = infos[-1]
 
     # FP64 vs FP32 + refinement on the log-normal 8191^2 field (its own
-    # workload: smooth k = exp(2 g), correlation 32 cells), solved to 1e-10
+    # workload: smooth k = exp(2 g), correlation 32 cells), solved to 1e-10;
+    # these legs run on rank 0 only
     extra = {}
-    if not args.quick:
+    if not args.quick and rank == 0:
         extra["fp64_vs_fp32_refine"] = lognormal_leg(bm, torch, dev, stream, args)
         extra["batched"] = batch_leg(bm, torch, dev, stream)
         extra["threshold_sweep"] = threshold_sweep(bm, torch, k, b, stream)
@@ -293,6 +301,7 @@ def run_ours(args, rank, world, local_rank):
         reps = max(1, args.steps // 2)
         bm.solve_host(kn, bn, xn, opts, tol, stream=stream)
         tot = 0.0
+        barrier()
         for _ in range(reps):
             xn[...] = 0.0
             torch.cuda.synchronize()
@@ -301,7 +310,9 @@ def run_ours(args, rank, world, local_rank):
             ev1.record(stream)
             torch.cuda.synchronize()
             tot += ev0.elapsed_time(ev1)
-        e2e = {"value": n_fine * world / (tot / reps / 1e3), "unit": UNIT,
+        barrier()
+        tot, e2e_value = aggregate(torch, tot, n_fine * reps, world, dev)
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 3 * 8 * n_fine, "d2h_bytes_per_step": 8 * n_fine,
                "ms_per_step": tot / reps}
 
