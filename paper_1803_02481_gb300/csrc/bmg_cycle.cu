@@ -184,13 +184,25 @@ __global__ void __launch_bounds__(kNormThreads) k_refine_residual(LevelV<double>
 }
 
 // x += ||r_prev|| * e  (e the FP32 correction).
+// One thread per pair of points (i, i+1), i odd: interior rows start on
+// 128-byte boundaries, so the pair is one 16-byte FP64 and one 8-byte FP32
+// access; a last unpaired point (i = nx, nx odd) is done alone.
 __global__ void k_refine_update(LevelV<double> L, LevelV<float> F, const Scalars* sc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + 1;
   const int j = blockIdx.y + 1;
   if (i > L.nx) return;
   const double s = sc->scale;
-  const int o = j * L.pitch + i;
-  L.x[o] = fma(s, double(F.x[j * F.pitch + i]), L.x[o]);
+  double* x = L.x + j * L.pitch + i;
+  const float* e = F.x + j * F.pitch + i;
+  if (i < L.nx) {
+    double2 xv = *reinterpret_cast<const double2*>(x);
+    const float2 ev = *reinterpret_cast<const float2*>(e);
+    xv.x = fma(s, double(ev.x), xv.x);
+    xv.y = fma(s, double(ev.y), xv.y);
+    *reinterpret_cast<double2*>(x) = xv;
+  } else {
+    x[0] = fma(s, double(e[0]), x[0]);
+  }
 }
 
 }  // namespace
@@ -272,7 +284,7 @@ void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s, bool in_gr
 
 void launch_refine_update(Hierarchy* h, cudaStream_t s) {
   const LevelV<double>& L = h->d.back();
-  k_refine_update<<<dim3(cdiv(L.nx, kTB), L.ny), kTB, 0, s>>>(L, h->f.back(), h->sc);
+  k_refine_update<<<dim3(cdiv((L.nx + 1) / 2, kTB), L.ny), kTB, 0, s>>>(L, h->f.back(), h->sc);
   count_launch();
 }
 

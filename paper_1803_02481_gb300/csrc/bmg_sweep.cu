@@ -48,8 +48,8 @@ constexpr TmaCfg kRb32[] = {{128, 16, 256, 2, 2}, {64, 16, 256, 3, 2}, {128, 16,
 constexpr int kNumRbCfg = 3;
 constexpr TmaCfg kNine64[] = {{32, 16, 256, 4, 1}, {32, 32, 512, 1, 2}, {32, 16, 256, 2, 2},
                               {64, 16, 512, 1, 2}, {32, 16, 224, 2, 2}, {32, 32, 512, 2, 1}};
-constexpr TmaCfg kNine32[] = {{64, 16, 256, 4, 1}, {32, 32, 256, 2, 2}, {64, 16, 256, 2, 2},
-                              {32, 16, 256, 3, 2}, {128, 16, 256, 1, 2}, {32, 32, 256, 4, 1}};
+constexpr TmaCfg kNine32[] = {{64, 16, 256, 4, 1}, {64, 32, 256, 2, 1}, {64, 16, 256, 2, 2},
+                              {32, 16, 256, 3, 2}, {128, 16, 256, 2, 1}, {32, 32, 256, 4, 1}};
 constexpr int kNumNineCfg = 6;
 
 static int env_int(const char* name, int dflt) {
@@ -241,10 +241,10 @@ static void allow_tma_smem() {
       }                                                                \
     } else {                                                           \
       switch (K) {                                                     \
-        case 1: BODY(T, true, 32, 32, 256, 2, 2); break;               \
+        case 1: BODY(T, true, 64, 32, 256, 2, 1); break;               \
         case 2: BODY(T, true, 64, 16, 256, 2, 2); break;               \
         case 3: BODY(T, true, 32, 16, 256, 3, 2); break;               \
-        case 4: BODY(T, true, 128, 16, 256, 1, 2); break;              \
+        case 4: BODY(T, true, 128, 16, 256, 2, 1); break;              \
         case 5: BODY(T, true, 32, 32, 256, 4, 1); break;               \
         default: BODY(T, true, 64, 16, 256, 4, 1); break;              \
       }                                                                \
