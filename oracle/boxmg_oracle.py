@@ -29,6 +29,9 @@ What it computes (Reisner, Olson, Moulton, "Scaling Structured Multigrid to
   with the optional r/C term of the interpolation equations in Section 3.
 * ``vcycle`` / ``solve`` -- Algorithm 1, iterated until the relative residual
   ||b - A x||_2 / ||b||_2 is at most ``tol``.
+* ``pcg``            -- conjugate gradients preconditioned by one symmetric
+  V(nu, nu) cycle (the V-cycle used as a preconditioner rather than as the
+  iteration; the paper solves with V-cycles alone).
 * ``assembly_vjp`` / ``adjoint_gradient`` -- the gradient of
   L = 0.5 ||u - u_obs||^2 with respect to log-coefficients through the adjoint
   equation A lambda = u - u_obs (A is symmetric), with exact sparse solves.
@@ -512,6 +515,71 @@ def solve(h: Hierarchy, b: np.ndarray, x0: np.ndarray | None = None,
         if not np.isfinite(rel):
             break
     return SolveResult(x, cycles, rel, hist, bool(rel <= tol))
+
+
+# ---------------------------------------------------------------------------
+# Conjugate gradients preconditioned by one symmetric V-cycle
+# ---------------------------------------------------------------------------
+
+def vcycle_precond(h: Hierarchy, r: np.ndarray) -> np.ndarray:
+    """z = M^{-1} r: one V(nu, nu) cycle of Algorithm 1 on A z = r from z = 0.
+    With nu1 = nu2, forward colours before the coarse correction and the
+    reverse order after it, R = P^T and an exact coarsest solve, M^{-1} is a
+    symmetric linear operator."""
+    z = np.zeros_like(r)
+    vcycle(h, z, r)
+    return z
+
+
+def pcg(h: Hierarchy, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1e-10,
+        max_iter: int = 500, precond=None) -> SolveResult:
+    """Preconditioned conjugate gradients on A x = b (A the finest operator of
+    h), in the textbook order:
+        r = b - A x, z = M^{-1} r, p = z, rz = r.z; then per iteration
+        q = A p, alpha = rz / p.q, x += alpha p, r -= alpha q, stop test,
+        z = M^{-1} r, rz' = r.z, beta = rz' / rz, p = z + beta p.
+    The stop test ||r||_2 / ||b||_2 <= tol uses the updated r and is applied
+    before the first iteration and after each one.  ``precond`` maps r to z;
+    the default is one symmetric V-cycle (h.nu1 == h.nu2 required), None
+    for it, or ``"identity"`` for plain conjugate gradients."""
+    fine = h.levels[-1].st
+    if precond is None:
+        if h.nu1 != h.nu2 or h.interp_residual_term:
+            raise ValueError("the V-cycle preconditioner needs nu1 == nu2 and no r/C term")
+        precond = lambda r: vcycle_precond(h, r)  # noqa: E731
+    elif precond == "identity":
+        precond = lambda r: r.copy()  # noqa: E731
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    bn = float(np.linalg.norm(b))
+    if bn == 0.0:
+        x[:] = 0.0
+        return SolveResult(x, 0, 0.0, [0.0], True)
+    r = residual(fine, x, b)
+    rel = float(np.linalg.norm(r)) / bn
+    hist = [rel]
+    it = 0
+    if rel <= tol:
+        return SolveResult(x, 0, rel, hist, True)
+    z = precond(r)
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    while it < max_iter:
+        q = apply(fine, p)
+        pq = float(np.sum(p * q))
+        alpha = rz / pq
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        rel = float(np.linalg.norm(r)) / bn
+        hist.append(rel)
+        if rel <= tol or not np.isfinite(rel):
+            break
+        z = precond(r)
+        rz_new = float(np.sum(r * z))
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    return SolveResult(x, it, rel, hist, bool(rel <= tol))
 
 
 # ---------------------------------------------------------------------------

@@ -518,3 +518,82 @@ def test_high_contrast_galerkin_levels_stay_interpolable():
         p = h.levels[l].p
         assert p.data.min() >= 0.0 and p.data.max() <= 1.0 + 1e-12, l
     assert saw_negative
+
+
+# ---------------------------------------------------------------------------
+# Conjugate gradients preconditioned by one symmetric V-cycle
+# ---------------------------------------------------------------------------
+
+def _one_d_operator(n):
+    """The 1-D cell-centred Dirichlet operator of unit coefficient: 2 on the
+    diagonal, 3 at both ends (a boundary face carries 2k), -1 off it."""
+    t = np.diag(np.full(n, 2.0)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)
+    t[0, 0] = t[-1, -1] = 3.0
+    return t
+
+
+def test_cg_converges_in_as_many_steps_as_distinct_eigenvalues():
+    # For k = 1 the 5-point operator is the Kronecker sum T (+) T, whose
+    # eigenvectors are v_i (x) v_j with eigenvalues mu_i + mu_j.  Conjugate
+    # gradients from x = 0 on a right-hand side with components along three
+    # eigenvectors of three distinct eigenvalues is exact after three steps.
+    n = 15
+    mu, v = np.linalg.eigh(_one_d_operator(n))
+    pairs = [(0, 0), (2, 5), (7, 11)]
+    assert len({round(mu[i] + mu[j], 9) for i, j in pairs}) == 3
+    b = sum((c * np.outer(v[:, j], v[:, i])) for c, (i, j) in zip((1.0, -0.5, 2.0), pairs))
+    h = O.setup(np.ones((n, n)), nu1=1, nu2=1)
+    r = O.pcg(h, b, tol=1e-13, max_iter=10, precond="identity")
+    assert r.cycles == 3
+    assert r.history[2] > 1e-3 and r.history[3] < 1e-12
+    assert np.abs(O.apply(h.levels[-1].st, r.x) - b).max() < 1e-12 * np.abs(b).max()
+
+
+def _block_field(n, seed):
+    return inputs.block_problem(seed=seed, block=4, lo=-3, hi=3, nx=n, ny=n)
+
+
+def test_symmetric_vcycle_preconditioner_is_symmetric_positive_definite():
+    pr = _block_field(31, 11)
+    rng = np.random.default_rng(12)
+    u, w = rng.normal(size=(31, 31)), rng.normal(size=(31, 31))
+    h = O.setup(pr["k"], nu1=1, nu2=1)
+    mu, mw = O.vcycle_precond(h, u), O.vcycle_precond(h, w)
+    scale = np.linalg.norm(u) * np.linalg.norm(mw)
+    assert abs(np.sum(mu * w) - np.sum(u * mw)) <= 1e-13 * scale
+    assert np.sum(mu * u) > 0 and np.sum(mw * w) > 0
+    # V(2,1) is not symmetric: the same check fails by many orders of magnitude
+    h21 = O.setup(pr["k"], nu1=2, nu2=1)
+    z = np.zeros_like(u)
+    O.vcycle(h21, z, u)
+    z2 = np.zeros_like(w)
+    O.vcycle(h21, z2, w)
+    assert abs(np.sum(z * w) - np.sum(u * z2)) > 1e-6 * np.linalg.norm(u) * np.linalg.norm(z2)
+
+
+@pytest.mark.parametrize("n", [15, 31])
+def test_pcg_converges_to_direct_solution(n):
+    pr = _block_field(n, 13)
+    h = O.setup(pr["k"], nu1=1, nu2=1)
+    r = O.pcg(h, pr["b"], tol=1e-12)
+    xd = O.direct_solve(pr["k"], pr["b"])
+    assert r.converged
+    assert np.abs(r.x - xd).max() <= 1e-9 * np.abs(xd).max()
+    # the updated residual tracks the true one
+    rel_true = np.linalg.norm(O.residual(h.levels[-1].st, r.x, pr["b"])) / np.linalg.norm(pr["b"])
+    assert rel_true <= 1e-11
+
+
+def test_pcg_needs_fewer_iterations_than_vcycles_on_contrast():
+    pr = inputs.block_problem(seed=1, block=8, lo=-4, hi=4, nx=63, ny=63)
+    h = O.setup(pr["k"], nu1=1, nu2=1)
+    rp = O.pcg(h, pr["b"], tol=1e-10)
+    rv = O.solve(O.setup(pr["k"], nu1=1, nu2=1), pr["b"], tol=1e-10, max_cycles=2000)
+    assert rp.converged and rv.converged
+    assert rp.cycles < rv.cycles / 2
+
+
+def test_pcg_rejects_unsymmetric_cycle():
+    h = O.setup(np.ones((7, 7)), nu1=2, nu2=1)
+    with pytest.raises(ValueError):
+        O.pcg(h, np.ones((7, 7)))
