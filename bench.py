@@ -49,8 +49,8 @@ WORKLOAD = {"workload": "diffusion 4095x4095, 64x64-cell blocks k=10^U(-4,4), se
 # from the ncu capture summarised in profiles/k_sweep_tma_fine_ncu.md; set
 # to None whenever the kernel changes until it is captured again.
 SWEEP_DRAM_BYTES_PER_UNKNOWN = {
-    "fp64": (169.331456e6 + 18.557440e6) / 4190209,    # 2047^2 block field
-    "fp32": (338.771456e6 + 52.550912e6) / 16769025,   # 4095^2 log-normal field
+    "fp64": (169.342720e6 + 18.732288e6) / 4190209,    # 2047^2 block field
+    "fp32": (338.814976e6 + 52.656128e6) / 16769025,   # 4095^2 log-normal field
 }
 
 
@@ -291,6 +291,7 @@ def run_ours(args, rank, world, local_rank):
         extra["fp64_vs_fp32_refine"] = lognormal_leg(bm, torch, dev, stream, args)
         extra["batched"] = batch_leg(bm, torch, dev, stream)
         extra["threshold_sweep"] = threshold_sweep(bm, torch, k, b, stream)
+        extra["pcg"] = pcg_leg(bm, torch, k, b, stream, tol, ms / args.steps, info.cycles)
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.quick:
@@ -440,6 +441,36 @@ def threshold_sweep(bm, torch, k, b, stream, cycles=20):
     best = min(rows, key=lambda r: r["measured_us_per_cycle"])["threshold"]
     return {"levels": nl, "model_choice": chosen, "measured_best": best, "rows": rows,
             "note": "per cycle including the convergence norm and one host read of the stop flag"}
+
+
+def pcg_leg(bm, torch, k, b, stream, tol, vcycle_ms, vcycle_cycles, max_iter=2000):
+    """Conjugate gradients preconditioned by one symmetric V(1,1) cycle on the
+    bench workload, to the bench tolerance, setup + solve timed like a bench
+    step, against the plain V(2,1) iteration of the headline."""
+    opts = bm.default_options(nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG, max_cycles=max_iter)
+    x = torch.zeros_like(b)
+
+    def step():
+        x.zero_()
+        h = bm.setup(k, opts, stream=stream)
+        _, info = h.solve(b, x, tol=tol, stream=stream)
+        h.destroy()
+        return info
+
+    step()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    info = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    n = b.numel()
+    return {"solver": "CG preconditioned by one symmetric V(1,1) cycle", "tol": tol,
+            "value": n / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms, "iterations": info.cycles,
+            "rel_resid": info.rel_resid, "vcycle_v21_ms_per_solve": vcycle_ms,
+            "vcycle_v21_cycles": vcycle_cycles, "speedup_vs_vcycle": vcycle_ms / ms}
 
 
 def batch_leg(bm, torch, dev, stream, count=512):

@@ -56,6 +56,13 @@ enum {
 
 enum { BMG_FP64 = 0, BMG_FP32_REFINE = 1 };
 
+/* Solvers: the V-cycle iteration of Algorithm 1, or conjugate gradients
+ * preconditioned by one symmetric V(nu, nu) cycle (an extension: the paper
+ * iterates V-cycles).  BMG_SOLVER_PCG needs precision BMG_FP64, nu1 == nu2
+ * >= 1 and interp_residual_term == 0, which make the cycle a symmetric
+ * positive definite preconditioner. */
+enum { BMG_SOLVER_VCYCLE = 0, BMG_SOLVER_PCG = 1 };
+
 #define BMG_MAX_COARSEST 1024
 
 typedef struct {
@@ -72,6 +79,7 @@ typedef struct {
   int log_coefficients;     /* 1: the coefficient array holds theta = log k and
                                the assembly uses k = exp(theta) (adjoint
                                gradients with respect to theta); 0: holds k */
+  int solver;               /* BMG_SOLVER_VCYCLE (default) or BMG_SOLVER_PCG  */
 } bmg_options;
 
 typedef struct {
@@ -109,7 +117,12 @@ int bmg_setup(const double *k_dev, int nx, int ny, const bmg_options *opt,
 
 /* Solve A x = b with V-cycles (Algorithm 1) until
  * ||b - A x||_2 / ||b||_2 <= tol (checked before the first cycle and after
- * every cycle) or max_cycles cycles ran.
+ * every cycle) or max_cycles cycles ran.  With solver BMG_SOLVER_PCG: with
+ * preconditioned conjugate gradients (r = b - A x, z = M^{-1} r, p = z; per
+ * iteration q = A p, alpha = r.z / p.q, x += alpha p, r -= alpha q, stop
+ * test on the updated r, z = M^{-1} r, beta = r.z' / r.z, p = z + beta p;
+ * M^{-1} is one V(nu, nu) cycle from zero), max_cycles capping the
+ * iterations and info->cycles counting them.
  * b_dev: dense (ny, nx) float64, device.  x_dev: dense (ny, nx) float64,
  * device; on entry the initial guess, on exit the solution.  info may be
  * NULL.  Synchronises the stream (the cycle count and residual return to the
@@ -299,14 +312,17 @@ long long bmg_kernel_launches(void);
 /* Kernel classes that can be timed live with CUDA events (class numbers;
  * bit (1 << class) in a mask). */
 enum { BMG_PROF_FINE_SMOOTH = 1, BMG_PROF_FINE_RESID = 2, BMG_PROF_FINE_INTERP = 3,
-       BMG_PROF_COARSE = 4, BMG_PROF_LEVELS = 5, BMG_PROF_NORM = 6, BMG_PROF_CYCLE = 7 };
+       BMG_PROF_COARSE = 4, BMG_PROF_LEVELS = 5, BMG_PROF_NORM = 6, BMG_PROF_CYCLE = 7,
+       BMG_PROF_KRYLOV = 8 };
 
 /* Bracket every launch of each kernel class whose bit is set in `mask` with
  * a pair of CUDA events on its stream (up to 65536 per class) and reset all
  * records; mask 0 stops recording.  Classes: fine-level sweeps (one bracket
  * per full sweep), fine-level residual, fine-level interpolation, the
  * persistent coarse kernel, all other levels' full-grid work of one V-cycle,
- * the convergence norm, and one whole V-cycle. */
+ * the convergence norm, one whole V-cycle, and the conjugate-gradient vector
+ * kernels of BMG_SOLVER_PCG (A p with p.q, the x/r update with r.r, r.z with
+ * the scalars, and p = z + beta p; one bracket per iteration). */
 int bmg_profile_set(int mask);
 
 /* Synchronise the recorded events of class `which` and return the number of

@@ -22,13 +22,15 @@ __all__ = [
 
 BMG_OK, BMG_EINVAL, BMG_ENOMEM, BMG_ECUDA, BMG_ENOCONV, BMG_ENAN, BMG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 BMG_FP64, BMG_FP32_REFINE = 0, 1
+BMG_SOLVER_VCYCLE, BMG_SOLVER_PCG = 0, 1
 MAX_COARSEST = 1024
 
 
 class Options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("precision", ctypes.c_int),
                 ("interp_residual_term", ctypes.c_int), ("coarse_threshold", ctypes.c_int),
-                ("max_cycles", ctypes.c_int), ("log_coefficients", ctypes.c_int)]
+                ("max_cycles", ctypes.c_int), ("log_coefficients", ctypes.c_int),
+                ("solver", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -88,7 +90,7 @@ EXPORTED = {
 }
 
 PROF_CLASSES = {"fine_smooth": 1, "fine_resid": 2, "fine_interp": 3, "coarse_kernel": 4,
-                "other_levels": 5, "norm": 6, "vcycle": 7}
+                "other_levels": 5, "norm": 6, "vcycle": 7, "krylov": 8}
 
 
 CALIBRATION_KEYS = ("launch_us", "sync_us", "gpu_gbs", "gpu_gflops64", "gpu_gflops32", "cta_gbs",

@@ -164,6 +164,13 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   if (opt_in) opt = *opt_in;
   if (opt.nu1 < 0 || opt.nu2 < 0 || opt.nu1 + opt.nu2 < 1 || opt.max_cycles < 0) return BMG_EINVAL;
   if (opt.precision != BMG_FP64 && opt.precision != BMG_FP32_REFINE) return BMG_EINVAL;
+  if (opt.solver != BMG_SOLVER_VCYCLE && opt.solver != BMG_SOLVER_PCG) return BMG_EINVAL;
+  if (opt.solver == BMG_SOLVER_PCG &&
+      (opt.precision != BMG_FP64 || opt.nu1 != opt.nu2 || opt.interp_residual_term)) {
+    set_last_error("BMG_SOLVER_PCG needs precision BMG_FP64, nu1 == nu2 and "
+                   "interp_residual_term == 0 (a symmetric V-cycle)");
+    return BMG_EINVAL;
+  }
   const double t0 = now_ms();
   prepare_sweep_kernels();
 
@@ -217,6 +224,13 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
     h->sc = cv.raw<Scalars>(1);
     h->dlev64 = cv.raw<LevelV<double>>(L);
     h->dlev32 = cv.raw<LevelV<float>>(L);
+    if (opt.solver == BMG_SOLVER_PCG) {
+      const Geom& gf = h->geo64.back();
+      h->pcg_x = cv.plane<double>(gf);
+      h->pcg_b = cv.plane<double>(gf);
+      h->pcg_p = cv.plane<double>(gf);
+      h->pcg_q = cv.plane<double>(gf);
+    }
     if (pass == 0) {
       h->arena_bytes = cv.off;
       if (cudaMalloc(&h->arena, h->arena_bytes) != cudaSuccess) {
@@ -365,7 +379,39 @@ static int build_solve_graph(Hierarchy* h) {
   cudaStream_t s = nullptr;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return BMG_ECUDA;
   const bool fp32 = h->opt.precision == BMG_FP32_REFINE;
+  const bool pcg = h->opt.solver == BMG_SOLVER_PCG;
   LevelV<double>& F = h->d.back();
+  // [prologue: first residual and stop test] WHILE(go) { body }
+  auto prologue = [&] {
+    if (pcg) {
+      launch_pcg_init(h, s, true);
+      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+      launch_pcg_rz(h, true, s);
+      launch_pcg_p(h, s);
+    } else if (fp32) {
+      launch_refine_residual(h, 0.0, s, true);
+    } else {
+      launch_fine_norm(h, F.x, F.b, 1, 0.0, s, true);
+    }
+  };
+  auto body = [&] {
+    if (pcg) {
+      // after the stop test the rest of the body only prepares the next
+      // direction (x no longer changes), so a last pass is harmless
+      launch_pcg_ap(h, s);
+      launch_pcg_xr(h, s, true);
+      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+      launch_pcg_rz(h, false, s);
+      launch_pcg_p(h, s);
+    } else if (fp32) {
+      enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s);
+      launch_refine_update(h, s);
+      launch_refine_residual(h, 0.0, s, true);
+    } else {
+      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+      launch_fine_norm(h, F.x, F.b, 1, 0.0, s, true);
+    }
+  };
   int rc = BMG_ECUDA;
   do {
     if (cudaGraphCreate(&h->graph, 0) != cudaSuccess) break;
@@ -375,10 +421,7 @@ static int build_solve_graph(Hierarchy* h) {
     if (cudaStreamBeginCaptureToGraph(s, h->graph, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed) != cudaSuccess)
       break;
-    if (fp32)
-      launch_refine_residual(h, 0.0, s, true);
-    else
-      launch_fine_norm(h, F.x, F.b, 1, 0.0, s, true);
+    prologue();
     cudaStreamCaptureStatus st;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -398,18 +441,11 @@ static int build_solve_graph(Hierarchy* h) {
       break;
     cudaGraph_t g = nullptr;
     if (cudaStreamEndCapture(s, &g) != cudaSuccess) break;
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
-        cudaSuccess)
+    cudaGraph_t gbody = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(s, gbody, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
       break;
-    if (fp32) {
-      enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s);
-      launch_refine_update(h, s);
-      launch_refine_residual(h, 0.0, s, true);
-    } else {
-      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
-      launch_fine_norm(h, F.x, F.b, 1, 0.0, s, true);
-    }
+    body();
     if (cudaStreamEndCapture(s, &g) != cudaSuccess) break;
     if (cudaGraphInstantiate(&h->gexec, h->graph, 0) != cudaSuccess) break;
     rc = BMG_OK;
@@ -437,14 +473,21 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
   const double t0 = now_ms();
   const int L = h->L;
   LevelV<double>& F = h->d.back();
-  launch_pack<double>(b, F.b, h->nx, h->ny, F.pitch, s);
-  launch_pack<double>(x, F.x, h->nx, h->ny, F.pitch, s);
+  const bool pcg = h->opt.solver == BMG_SOLVER_PCG;
+  // the iterate and right-hand side: the fine level's x and b planes, or the
+  // conjugate-gradient planes (whose b and x planes then hold r and z)
+  double* xk = pcg ? h->pcg_x : F.x;
+  double* bk = pcg ? h->pcg_b : F.b;
+  launch_pack<double>(b, bk, h->nx, h->ny, F.pitch, s);
+  launch_pack<double>(x, xk, h->nx, h->ny, F.pitch, s);
+  if (pcg)
+    BMG_CUDA(cudaMemsetAsync(h->pcg_p, 0, sizeof(double) * size_t(h->ny + 2) * F.pitch, s));
   Scalars init{};
   init.tol = tol;
   init.max_cycles = h->opt.max_cycles;
   *h->sc_host = init;
   BMG_CUDA(cudaMemcpyAsync(h->sc, h->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
-  launch_fine_norm(h, nullptr, F.b, 0, tol, s);
+  launch_fine_norm(h, nullptr, bk, 0, tol, s);
   const bool fp32 = h->opt.precision == BMG_FP32_REFINE;
   int rc = BMG_OK;
   // Graph path: the whole loop in one launch (not while kernel classes are
@@ -453,7 +496,7 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
     if (h->graph_state == 0) h->graph_state = build_solve_graph(h) == BMG_OK ? 1 : -1;
     if (h->graph_state == 1) {
       BMG_CUDA(cudaGraphLaunch(h->gexec, s));
-      launch_unpack<double>(F.x, x, h->nx, h->ny, F.pitch, s);
+      launch_unpack<double>(xk, x, h->nx, h->ny, F.pitch, s);
       if ((rc = read_scalars(h, s))) return rc;
       const Scalars& r = *h->sc_host;
       if (r.bnorm2 == 0.0) {
@@ -469,7 +512,30 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
       return BMG_OK;
     }
   }
-  if (!fp32) {
+  if (pcg) {
+    launch_pcg_init(h, s, false);
+    if ((rc = read_scalars(h, s))) return rc;
+    if (h->sc_host->bnorm2 == 0.0) {
+      BMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * size_t(h->nx) * h->ny, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+      if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0};
+      return BMG_OK;
+    }
+    if (h->sc_host->go) {
+      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+      launch_pcg_rz(h, true, s);
+      launch_pcg_p(h, s);
+      for (;;) {
+        launch_pcg_ap(h, s);
+        launch_pcg_xr(h, s, false);
+        if ((rc = read_scalars(h, s))) return rc;
+        if (!h->sc_host->go) break;
+        enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+        launch_pcg_rz(h, false, s);
+        launch_pcg_p(h, s);
+      }
+    }
+  } else if (!fp32) {
     launch_fine_norm(h, F.x, F.b, 1, tol, s);
     if ((rc = read_scalars(h, s))) return rc;
     if (h->sc_host->bnorm2 == 0.0) {
@@ -500,7 +566,7 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
     }
   }
   (void)L;
-  launch_unpack<double>(F.x, x, h->nx, h->ny, F.pitch, s);
+  launch_unpack<double>(xk, x, h->nx, h->ny, F.pitch, s);
   BMG_CUDA(cudaGetLastError());
   BMG_CUDA(cudaStreamSynchronize(s));
   const Scalars& r = *h->sc_host;
@@ -533,6 +599,7 @@ void bmg_default_options(bmg_options* opt) {
   opt->coarse_threshold = -1;
   opt->max_cycles = 200;
   opt->log_coefficients = 0;
+  opt->solver = BMG_SOLVER_VCYCLE;
 }
 
 const char* bmg_last_error(void) { return bmg::g_last_error; }

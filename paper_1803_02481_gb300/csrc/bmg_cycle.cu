@@ -282,6 +282,12 @@ void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s, bool in_gr
   count_launch(2);
 }
 
+void launch_norm_final(Hierarchy* h, cudaStream_t s, bool in_graph) {
+  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, 1, h->hist, h->cond,
+                                          in_graph ? 1 : 0);
+  count_launch();
+}
+
 void launch_refine_update(Hierarchy* h, cudaStream_t s) {
   const LevelV<double>& L = h->d.back();
   k_refine_update<<<dim3(cdiv((L.nx + 1) / 2, kTB), L.ny), kTB, 0, s>>>(L, h->f.back(), h->sc);

@@ -235,6 +235,8 @@ struct Scalars {            // device-resident solve state
   double tol;               // stop test
   double scale;             // sqrt(scale2), set with scale2 (one thread)
   double inv;               // 1 / sqrt(rnorm2) (0 when rnorm2 == 0), set with rnorm2
+  double rz;                // BMG_SOLVER_PCG: r.z of the current iteration
+  double alpha, beta;       // BMG_SOLVER_PCG: step and direction coefficients
   int cycles;               // cycles / refinement steps run
   int max_cycles;
   int go;                   // 1 while the loop should continue
@@ -287,6 +289,10 @@ struct Hierarchy {
   // tiled kernel)
   std::vector<SweepMaps<double>*> maps64;
   std::vector<SweepMaps<float>*> maps32;
+  // BMG_SOLVER_PCG planes on the finest level (FP64): iterate, right-hand
+  // side, search direction and A p.  The fine level's b plane holds the
+  // residual r (the V-cycle's right-hand side) and its x plane z.
+  double *pcg_x = nullptr, *pcg_b = nullptr, *pcg_p = nullptr, *pcg_q = nullptr;
 
 };
 
@@ -357,6 +363,25 @@ void launch_fine_norm(Hierarchy* h, const double* x, const double* b, int what,
 // into the FP32 fine RHS; zero the FP32 fine x.
 void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s, bool in_graph = false);
 void launch_refine_update(Hierarchy* h, cudaStream_t s);
+// Sums h->partials (npartials squared-residual partials) into the stop test:
+// rnorm2, rel, history, go, cycles; in a graph it also sets the WHILE
+// condition.
+void launch_norm_final(Hierarchy* h, cudaStream_t s, bool in_graph);
+
+// Preconditioned conjugate gradients (bmg_pcg.cu).  init: r = b - A x, z = 0,
+// ||r||^2 and the stop test; ap: q = A p, p.q, alpha; xr: x += alpha p,
+// r -= alpha q, z = 0, ||r||^2 and the stop test; rz: r.z and beta (first:
+// beta = 0); p: p = z + beta p.
+void launch_pcg_init(Hierarchy* h, cudaStream_t s, bool in_graph);
+void launch_pcg_ap(Hierarchy* h, cudaStream_t s);
+void launch_pcg_xr(Hierarchy* h, cudaStream_t s, bool in_graph);
+void launch_pcg_rz(Hierarchy* h, bool first, cudaStream_t s);
+void launch_pcg_p(Hierarchy* h, cudaStream_t s);
+
+// One V-cycle of the FP64 (d) or FP32 (f) hierarchy (bmg_api.cu).
+template <typename T>
+void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* dlev, int thr,
+                    cudaStream_t s);
 
 void launch_assemble_backward(const double* k, const double* u, const double* lam,
                               double* g, int nx, int ny, cudaStream_t s);

@@ -12,7 +12,7 @@ namespace {
 
 std::atomic<long long> g_launches{0};
 
-constexpr int kClasses = 8;
+constexpr int kClasses = 9;
 constexpr size_t kMaxPairs = 65536;
 
 struct ClassRec {

@@ -12,6 +12,8 @@ Tolerances (FP64):
   eps * ||(|A| |x|)|| / ||b||, a few hundred ulp here, and the GPU (FMA)
   and the oracle (no FMA) round differently; iterates within 1e-9 of max|x|.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -275,14 +277,17 @@ def test_solve_host_end_to_end():
     assert np.abs(x - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine", "pcg"])
 def test_graph_and_stream_paths_agree(precision):
     """The solve loop recorded as one CUDA graph (default) and launched op by
     op on the stream (used while kernel classes are being timed) run the
     same kernels in the same order: identical results."""
     pr = problem("blocks255")
-    prec = bm.BMG_FP64 if precision == "fp64" else bm.BMG_FP32_REFINE
-    hg = gpu_setup("blocks255", precision=prec)
+    if precision == "pcg":
+        hg = gpu_setup("blocks255", nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG)
+    else:
+        prec = bm.BMG_FP64 if precision == "fp64" else bm.BMG_FP32_REFINE
+        hg = gpu_setup("blocks255", precision=prec)
     x1, i1 = hg.solve(dev(pr["b"]), tol=1e-10)
     bm.profile_set(("norm",))
     try:
@@ -292,3 +297,48 @@ def test_graph_and_stream_paths_agree(precision):
     assert i1.cycles == i2.cycles and i1.rel_resid == i2.rel_resid
     assert torch.equal(x1, x2)
     hg.destroy()
+
+
+# ---------------------------------------------------------------------------
+# Conjugate gradients preconditioned by one symmetric V(1,1) cycle
+# ---------------------------------------------------------------------------
+
+PCG_CASES = ["poisson255", "blocks255", "blocks511_c2", "lognormal255", "random63", "rect127x31",
+             "wide2047x127", "tiny3"]
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_pcg(name, tol=1e-10):
+    pr = problem(name)
+    return O.pcg(O.setup(pr["k"], nu1=1, nu2=1), pr["b"], tol=tol, max_iter=400)
+
+
+@pytest.mark.parametrize("name", PCG_CASES)
+def test_pcg_matches_oracle(name):
+    pr = problem(name)
+    ro = oracle_pcg(name)
+    hg = gpu_setup(name, nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG, max_cycles=400)
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+    xg = x.cpu().numpy()
+    hist = hg.residual_history()
+    hg.destroy()
+    assert ro.converged and info.cycles == ro.cycles, (info.cycles, ro.cycles)
+    # the recurrences agree to rounding: dot products summed in another order
+    h_o = np.array(ro.history)
+    assert np.all(np.abs(hist - h_o) <= 1e-7 * h_o + 1e-14)
+    assert info.rel_resid <= 1e-10
+    assert np.abs(xg - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+    # the true residual of the returned x (the stop test uses the updated one)
+    st = oracle_hierarchy(name).levels[-1].st
+    rel = np.linalg.norm(O.residual(st, xg, pr["b"])) / np.linalg.norm(pr["b"])
+    assert rel <= 2e-10
+
+
+def test_pcg_needs_a_symmetric_fp64_cycle():
+    k = dev(problem("blocks255")["k"])
+    for opts in (dict(solver=bm.BMG_SOLVER_PCG),                       # V(2,1)
+                 dict(solver=bm.BMG_SOLVER_PCG, nu1=1, nu2=1, precision=bm.BMG_FP32_REFINE),
+                 dict(solver=bm.BMG_SOLVER_PCG, nu1=1, nu2=1, interp_residual_term=1)):
+        with pytest.raises(bm.BoxMGError) as e:
+            bm.setup(k, bm.default_options(**opts))
+        assert e.value.code == bm.BMG_EINVAL
