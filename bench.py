@@ -370,7 +370,9 @@ def run_ours(args, rank, world, local_rank):
 
 def lognormal_leg(bm, torch, dev, stream, args, n=8191):
     """FP64 V-cycles against FP32 V-cycles inside FP64 refinement, both to
-    1e-10 on the 8191^2 log-normal field (setup + solve timed)."""
+    1e-10 on the 8191^2 log-normal field (setup + solve timed); beside them
+    the r/C interpolation variant and CG preconditioned by a symmetric
+    V(1,1) cycle, both FP64."""
     g = inputs.gaussian_random_field_torch(2, n, n, 32.0, device=dev)
     k = torch.exp(2.0 * g)
     gen = torch.Generator(device=dev)
@@ -381,8 +383,15 @@ def lognormal_leg(bm, torch, dev, stream, args, n=8191):
     xs = {}
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    for name, prec in (("fp64", bm.BMG_FP64), ("fp32_refine", bm.BMG_FP32_REFINE)):
-        opts = bm.default_options(precision=prec, max_cycles=500)
+    variants = (("fp64", dict(precision=bm.BMG_FP64)),
+                ("fp32_refine", dict(precision=bm.BMG_FP32_REFINE)),
+                # the Section 3 interpolation with the r/C term, FP64
+                ("fp64_interp_rc", dict(precision=bm.BMG_FP64, interp_residual_term=1)),
+                # CG preconditioned by one symmetric V(1,1) cycle, FP64
+                ("fp64_pcg_v11", dict(precision=bm.BMG_FP64, nu1=1, nu2=1,
+                                      solver=bm.BMG_SOLVER_PCG)))
+    for name, kw in variants:
+        opts = bm.default_options(max_cycles=500, **kw)
         x = torch.zeros_like(b)
         times = []
         for rep in range(3):
