@@ -91,28 +91,36 @@ def harmonic_face(k1: np.ndarray, k2: np.ndarray) -> np.ndarray:
     return 2.0 * k1 * k2 / (k1 + k2)
 
 
-def assemble_fv5(k: np.ndarray) -> dict:
-    """5-point cell-centred FV operator for -div(k grad u) = f, u = 0 on the
-    boundary of the unit square (Section 5), scaled by h^2.
+def assemble_fv5(k: np.ndarray, r: float = 1.0, aspect: float = 1.0) -> dict:
+    """5-point cell-centred FV operator for -div(D grad u) = f, u = 0 on the
+    boundary of the unit square (Section 5, Eqs. (diffusion),
+    (diffusion_bc)), in integrated form (for square cells: scaled by h^2).
 
-    Interior faces carry the harmonic mean of the two cell coefficients; a
-    boundary face sits half a cell from the cell centre and carries 2 k.  The
-    diagonal C is the sum of the cell's four face coefficients.
+    D = diag(k / r, k r) per cell (Section 5 uses a constant D with r ~ 16;
+    r = 1 is isotropic diffusion with coefficient k), on cells of aspect
+    hy / hx = ``aspect`` (nx x ny cells of the unit square: aspect nx / ny).
+    Interior x faces carry the harmonic mean of the two cells' k / r times
+    hy / hx, y faces that of k r times hx / hy; a boundary face sits half a
+    cell from the cell centre and carries 2 (k / r) hy / hx or 2 k r hx / hy.
+    The diagonal C is the sum of the cell's four face coefficients.  With
+    r = aspect = 1 every factor is an exact 1.
     """
     k = np.asarray(k, dtype=np.float64)
     ny, nx = k.shape
+    inv_r, inv_a = 1.0 / r, 1.0 / aspect
+    kx, ky = k * inv_r, k * r
     st = {d: np.zeros((ny, nx)) for d in ("C",) + DIRS}
-    ax = harmonic_face(k[:, :-1], k[:, 1:])          # face between i and i+1
-    ay = harmonic_face(k[:-1, :], k[1:, :])          # face between j and j+1
+    ax = harmonic_face(kx[:, :-1], kx[:, 1:]) * aspect     # face between i and i+1
+    ay = harmonic_face(ky[:-1, :], ky[1:, :]) * inv_a      # face between j and j+1
     st["E"][:, :-1] = ax
     st["W"][:, 1:] = ax
     st["N"][:-1, :] = ay
     st["S"][1:, :] = ay
     bw = np.zeros((ny, nx))                          # boundary face coefficients
-    bw[:, 0] += 2.0 * k[:, 0]
-    bw[:, -1] += 2.0 * k[:, -1]
-    bw[0, :] += 2.0 * k[0, :]
-    bw[-1, :] += 2.0 * k[-1, :]
+    bw[:, 0] += 2.0 * kx[:, 0] * aspect
+    bw[:, -1] += 2.0 * kx[:, -1] * aspect
+    bw[0, :] += 2.0 * ky[0, :] * inv_a
+    bw[-1, :] += 2.0 * ky[-1, :] * inv_a
     st["C"] = st["W"] + st["E"] + st["S"] + st["N"] + bw
     return st
 
@@ -434,14 +442,17 @@ def level_shapes(nx: int, ny: int):
 
 
 def setup(k: np.ndarray, nu1: int = 2, nu2: int = 1,
-          interp_residual_term: bool = False) -> Hierarchy:
-    """BoxMG setup: assemble the fine operator, then for each level build P_l
-    from A_l and A_{l-1} = P_l^T A_l P_l; factor A_0 (Section 2)."""
+          interp_residual_term: bool = False, r: float = 1.0, aspect: float = 1.0) -> Hierarchy:
+    """BoxMG setup: assemble the fine operator (``r``, ``aspect`` as in
+    assemble_fv5), then for each level build P_l from A_l and
+    A_{l-1} = P_l^T A_l P_l; factor A_0 (Section 2)."""
     ny, nx = k.shape
     shapes = level_shapes(nx, ny)
     if not np.all(np.isfinite(k)) or np.any(k <= 0):
         raise ValueError("coefficients must be finite and positive")
-    st = assemble_fv5(k)
+    if not (np.isfinite(r) and r > 0 and np.isfinite(aspect) and aspect > 0):
+        raise ValueError("r and the cell aspect must be finite and positive")
+    st = assemble_fv5(k, r, aspect)
     fine_to_coarse = [Level(st)]
     for _ in shapes[1:]:
         p = interpolation(st)

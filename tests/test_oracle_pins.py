@@ -597,3 +597,67 @@ def test_pcg_rejects_unsymmetric_cycle():
     h = O.setup(np.ones((7, 7)), nu1=2, nu2=1)
     with pytest.raises(ValueError):
         O.pcg(h, np.ones((7, 7)))
+
+
+# ---------------------------------------------------------------------------
+# The paper's workload: D = diag(1/r, r) on stretched cells (Section 5)
+# ---------------------------------------------------------------------------
+
+def test_anisotropic_stretched_assembly_closed_form():
+    # k = 1, r = 4, cells of aspect hy/hx = 2 on a 5 x 3 grid: x faces carry
+    # (1/4) * 2 = 1/2, y faces 4 * (1/2) = 2; boundary faces twice that.
+    st = O.assemble_fv5(np.ones((3, 5)), r=4.0, aspect=2.0)
+    half, two = F(1, 2), F(2)
+    for j in range(3):
+        for i in range(5):
+            w = half if i > 0 else 0
+            e = half if i < 4 else 0
+            s = two if j > 0 else 0
+            n = two if j < 2 else 0
+            bnd = (2 * half) * ((i == 0) + (i == 4)) + (2 * two) * ((j == 0) + (j == 2))
+            assert st["W"][j, i] == w and st["E"][j, i] == e
+            assert st["S"][j, i] == s and st["N"][j, i] == n
+            assert st["C"][j, i] == w + e + s + n + bnd
+
+
+def test_compensating_anisotropy_gives_an_isotropic_discrete_operator():
+    # Section 5: with r equal to the cell aspect the couplings in x and y are
+    # equal (the grid stretching is compensated), here with r = aspect = 16
+    st = O.assemble_fv5(np.ones((7, 15)), r=16.0, aspect=16.0)
+    assert np.all(st["W"][:, 1:] == 1.0) and np.all(st["S"][1:, :] == 1.0)
+    iso = O.assemble_fv5(np.ones((7, 15)))
+    for d in ("C", "W", "E", "S", "N"):
+        assert np.array_equal(st[d], iso[d])
+
+
+def test_anisotropic_stretched_assembly_is_second_order():
+    # u = sin(pi x) sin(pi y) on the unit square, D = diag(1/r, r) with
+    # r = 3, nx = 2 ny cells (aspect 2); b = f(x_c) hx hy, f = (1/r + r) pi^2 u
+    r = 3.0
+    errs = []
+    for ny in (8, 16, 32):
+        nx = 2 * ny
+        hx, hy = 1.0 / nx, 1.0 / ny
+        xc = (np.arange(nx) + 0.5) * hx
+        yc = (np.arange(ny) + 0.5) * hy
+        u = np.outer(np.sin(np.pi * yc), np.sin(np.pi * xc))
+        b = (1.0 / r + r) * np.pi ** 2 * u * hx * hy
+        st = O.assemble_fv5(np.ones((ny, nx)), r=r, aspect=nx / ny)
+        uh = spla.spsolve(O.stencil_to_csr(st).tocsc(), b.ravel()).reshape(ny, nx)
+        errs.append(np.abs(uh - u).max())
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.7
+
+
+def test_paper_workload_vcycle_converges_like_poisson():
+    # 255 x 15 cells of the unit square (aspect 17) with r = 17: the
+    # compensating anisotropy keeps point-smoothed V(2,1) cycles fast
+    rng = np.random.default_rng(21)
+    b = rng.uniform(-1, 1, (15, 255))
+    h = O.setup(np.ones((15, 255)), r=17.0, aspect=17.0)
+    res = O.solve(h, b, tol=1e-10, max_cycles=100)
+    assert res.converged and res.cycles <= 20
+    # without the compensation (isotropic D on the same stretched cells) the
+    # point smoother stalls
+    h_iso = O.setup(np.ones((15, 255)), aspect=17.0)
+    res_iso = O.solve(h_iso, b, tol=1e-10, max_cycles=100)
+    assert res_iso.cycles > 3 * res.cycles
