@@ -80,6 +80,10 @@ typedef struct {
                                the assembly uses k = exp(theta) (adjoint
                                gradients with respect to theta); 0: holds k */
   int solver;               /* BMG_SOLVER_VCYCLE (default) or BMG_SOLVER_PCG  */
+  double aniso_r;           /* diffusion tensor D = diag(k / r, k r) per cell
+                               (Section 5 uses r ~ 16); 1: isotropic (default) */
+  double cell_aspect;       /* cell aspect hy / hx (nx x ny cells of the unit
+                               square: nx / ny); 1: square cells (default)    */
 } bmg_options;
 
 typedef struct {
@@ -105,7 +109,10 @@ const char *bmg_last_error(void);
  * k_dev: cell coefficients k > 0 (or theta = log k when
  * opt->log_coefficients), dense (ny, nx) float64, device.
  * Assembles the fine 5-point operator (harmonic face means, 2k on Dirichlet
- * faces, scaled by h^2), builds P_l and A_{l-1} = P_l^T A_l P_l on every
+ * faces, scaled by h^2; with opt->aniso_r and opt->cell_aspect, x faces carry
+ * the harmonic mean of k / r times hy / hx and y faces that of k r times
+ * hx / hy, boundary faces 2 (k / r) hy / hx and 2 k r hx / hy), builds P_l
+ * and A_{l-1} = P_l^T A_l P_l on every
  * level, factors A_0, and fixes the level schedule.  With precision
  * BMG_FP32_REFINE the coarse hierarchy (P and RAP) is built in FP32 from an
  * FP32 copy of the fine operator; the FP64 fine operator is kept for the
@@ -214,7 +221,8 @@ int bmg_op_interp(bmg_hierarchy *h, int level, const double *xc_dev,
  *                     + sum_{boundary faces} 2 u_c lam_c ],
  *   dA_f/dk_c = 2 k_n^2 / (k_c + k_n)^2.
  * With lam solving A lam = u - u_obs this is dL/dtheta for
- * L = 0.5 ||u - u_obs||^2.  Uses the k given to bmg_setup. */
+ * L = 0.5 ||u - u_obs||^2.  Uses the k given to bmg_setup.  Isotropic square
+ * cells only (aniso_r = cell_aspect = 1, else BMG_EINVAL). */
 int bmg_assemble_backward(bmg_hierarchy *h, const double *u_dev,
                           const double *lam_dev, double *dtheta_dev,
                           bmg_stream_t stream);
@@ -271,7 +279,8 @@ void bmg_batch_destroy(bmg_batch *b);
 /* ---- Allocation-free residual check --------------------------------------- */
 
 /* ||b - A(k) x||_2 and ||b||_2 for the 5-point cell-centred operator of k
- * (the same operator bmg_setup assembles), written to norms_dev[0] and
+ * (the operator bmg_setup assembles with aniso_r = cell_aspect = 1), written
+ * to norms_dev[0] and
  * norms_dev[1] (device memory, 2 doubles).  This entry point has no
  * counterpart in the paper: it exists for callers that cannot allocate
  * device memory -- programs whose device memory is all handed out by their

@@ -30,7 +30,8 @@ class Options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("precision", ctypes.c_int),
                 ("interp_residual_term", ctypes.c_int), ("coarse_threshold", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("log_coefficients", ctypes.c_int),
-                ("solver", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("aniso_r", ctypes.c_double),
+                ("cell_aspect", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -161,8 +162,11 @@ def _check(code: int, where: str, ok=(BMG_OK,)):
 def default_options(**kw) -> Options:
     o = Options()
     lib().bmg_default_options(ctypes.byref(o))
+    types = dict(Options._fields_)
     for k, v in kw.items():
-        setattr(o, k, int(v))
+        if k not in types:
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, float(v) if types[k] is ctypes.c_double else int(v))
     return o
 
 

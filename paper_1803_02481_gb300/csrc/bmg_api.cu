@@ -165,6 +165,11 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   if (opt.nu1 < 0 || opt.nu2 < 0 || opt.nu1 + opt.nu2 < 1 || opt.max_cycles < 0) return BMG_EINVAL;
   if (opt.precision != BMG_FP64 && opt.precision != BMG_FP32_REFINE) return BMG_EINVAL;
   if (opt.solver != BMG_SOLVER_VCYCLE && opt.solver != BMG_SOLVER_PCG) return BMG_EINVAL;
+  if (!(opt.aniso_r > 0.0 && opt.aniso_r < INFINITY && opt.cell_aspect > 0.0 &&
+        opt.cell_aspect < INFINITY)) {
+    set_last_error("aniso_r and cell_aspect must be finite and positive");
+    return BMG_EINVAL;
+  }
   if (opt.solver == BMG_SOLVER_PCG &&
       (opt.precision != BMG_FP64 || opt.nu1 != opt.nu2 || opt.interp_residual_term)) {
     set_last_error("BMG_SOLVER_PCG needs precision BMG_FP64, nu1 == nu2 and "
@@ -255,7 +260,8 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   // Assembly (Section 5), then P and RAP level by level (Section 2).
   int* derr = &h->sc->err;
   LevelV<double>& fine64 = h->d.back();
-  if (launch_assemble<double>(k, nx, ny, fine64, h->kcopy, derr, opt.log_coefficients != 0, s))
+  if (launch_assemble<double>(k, nx, ny, fine64, h->kcopy, derr, opt.log_coefficients != 0,
+                              opt.aniso_r, opt.cell_aspect, s))
     return fail(BMG_ECUDA);
   if (!fp32) {
     if ((rc = build_coarse<double>(h, h->d, s))) return fail(rc);
@@ -600,6 +606,8 @@ void bmg_default_options(bmg_options* opt) {
   opt->max_cycles = 200;
   opt->log_coefficients = 0;
   opt->solver = BMG_SOLVER_VCYCLE;
+  opt->aniso_r = 1.0;
+  opt->cell_aspect = 1.0;
 }
 
 const char* bmg_last_error(void) { return bmg::g_last_error; }
@@ -864,6 +872,7 @@ int bmg_assemble_backward(bmg_hierarchy* hp, const double* u, const double* lam,
                           bmg_stream_t stream) {
   Hierarchy* h = H(hp);
   if (!h || !u || !lam || !dtheta) return BMG_EINVAL;
+  if (h->opt.aniso_r != 1.0 || h->opt.cell_aspect != 1.0) return BMG_EINVAL;
   bmg::launch_assemble_backward(h->kcopy, u, lam, dtheta, h->nx, h->ny,
                                 reinterpret_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;

@@ -29,18 +29,26 @@ __device__ __forceinline__ double cell_k(const double* __restrict__ k, size_t q,
 // Assembly tile: kAX x kAY cells per block, one thread per cell.
 constexpr int kAX = 32, kAY = 8;
 
+// Face and cell factors of the assembly: D = diag(k / r, k r) on cells of
+// aspect hy / hx.  x faces carry harmonic(k_1 / r, k_2 / r) * hy / hx, y
+// faces harmonic(k_1 r, k_2 r) * hx / hy; boundary faces (2 k / r) hy / hx
+// and (2 k r) hx / hy.  1 / r and hx / hy come from the host; with
+// r = aspect = 1 every factor is an exact 1.
+struct AssemblyScale {
+  double inv_r, r, aspect, inv_aspect;
+};
+
 // Writes C, 1/C, W, S of the finest level and a dense copy of k; flags k that
 // is not finite and positive.  Each thread forms the west and south faces of
 // its cell (each interior face once); the east and north faces come from the
 // neighbours through shared memory, the tile's last column and row forming
-// the faces beyond it.  The east face of cell q is harmonic(k_q, k_q+1), the
-// same call as the west face of cell q+1, so C is what forming all four
-// faces per cell would give.
+// the faces beyond it.  The east face of cell q is the same call as the west
+// face of cell q+1, so C is what forming all four faces per cell would give.
 template <typename T>
 __global__ void __launch_bounds__(kAX * kAY) k_assemble(const double* __restrict__ k, int nx,
                                                         int ny, LevelV<T> L,
                                                         double* __restrict__ kcopy, int* derr,
-                                                        bool log_k) {
+                                                        bool log_k, AssemblyScale f) {
   __shared__ double fw[kAY][kAX + 1];   // west faces, column kAX = east of the tile
   __shared__ double fs[kAY + 1][kAX];   // south faces, row kAY = north of the tile
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -49,26 +57,32 @@ __global__ void __launch_bounds__(kAX * kAY) k_assemble(const double* __restrict
   const bool in = i0 < nx && j0 < ny;
   const size_t q = size_t(j0) * nx + i0;
   double kc = 1.0;
+  auto kx = [&](size_t c) { return cell_k(k, c, log_k) * f.inv_r; };
+  auto ky = [&](size_t c) { return cell_k(k, c, log_k) * f.r; };
   if (in) {
     kc = cell_k(k, q, log_k);
     if (!(kc > 0.0) || !(kc < INFINITY)) atomicOr(derr, DEV_BADK);
     kcopy[q] = kc;
-    fw[ty][tx] = i0 > 0 ? harmonic(cell_k(k, q - 1, log_k), kc) : 0.0;
-    fs[ty][tx] = j0 > 0 ? harmonic(cell_k(k, q - nx, log_k), kc) : 0.0;
-    if (tx == kAX - 1) fw[ty][kAX] = i0 < nx - 1 ? harmonic(kc, cell_k(k, q + 1, log_k)) : 0.0;
-    if (ty == kAY - 1) fs[kAY][tx] = j0 < ny - 1 ? harmonic(kc, cell_k(k, q + nx, log_k)) : 0.0;
+    const double kxc = kc * f.inv_r, kyc = kc * f.r;
+    fw[ty][tx] = i0 > 0 ? harmonic(kx(q - 1), kxc) * f.aspect : 0.0;
+    fs[ty][tx] = j0 > 0 ? harmonic(ky(q - nx), kyc) * f.inv_aspect : 0.0;
+    if (tx == kAX - 1)
+      fw[ty][kAX] = i0 < nx - 1 ? harmonic(kxc, kx(q + 1)) * f.aspect : 0.0;
+    if (ty == kAY - 1)
+      fs[kAY][tx] = j0 < ny - 1 ? harmonic(kyc, ky(q + nx)) * f.inv_aspect : 0.0;
   }
   __syncthreads();
   if (!in) return;
+  const double kxc = kc * f.inv_r, kyc = kc * f.r;
   const double aw = fw[ty][tx], as = fs[ty][tx];
   const double ae = i0 < nx - 1 ? fw[ty][tx + 1] : 0.0;
   const double an = j0 < ny - 1 ? fs[ty + 1][tx] : 0.0;
   // boundary faces, in the order west, east, south, north
   double bw = 0.0;
-  if (i0 == 0) bw = bw + 2.0 * kc;
-  if (i0 == nx - 1) bw = bw + 2.0 * kc;
-  if (j0 == 0) bw = bw + 2.0 * kc;
-  if (j0 == ny - 1) bw = bw + 2.0 * kc;
+  if (i0 == 0) bw = bw + 2.0 * kxc * f.aspect;
+  if (i0 == nx - 1) bw = bw + 2.0 * kxc * f.aspect;
+  if (j0 == 0) bw = bw + 2.0 * kyc * f.inv_aspect;
+  if (j0 == ny - 1) bw = bw + 2.0 * kyc * f.inv_aspect;
   const double c = (((aw + ae) + as) + an) + bw;
   const int o = (j0 + 1) * L.pitch + (i0 + 1);
   L.C[o] = T(c);
@@ -353,9 +367,10 @@ __global__ void k_assemble_backward(const double* __restrict__ k, const double* 
 
 template <typename T>
 int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy, int* derr,
-                    bool log_k, cudaStream_t s) {
+                    bool log_k, double r, double aspect, cudaStream_t s) {
+  const AssemblyScale f{1.0 / r, r, aspect, 1.0 / aspect};
   k_assemble<T><<<dim3(cdiv(nx, kAX), cdiv(ny, kAY)), dim3(kAX, kAY), 0, s>>>(k, nx, ny, L, kcopy,
-                                                                            derr, log_k);
+                                                                            derr, log_k, f);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? 0 : BMG_ECUDA;
 }
@@ -419,7 +434,7 @@ void launch_assemble_backward(const double* k, const double* u, const double* la
 }
 
 template int launch_assemble<double>(const double*, int, int, LevelV<double>, double*, int*,
-                                     bool, cudaStream_t);
+                                     bool, double, double, cudaStream_t);
 template int launch_interp_weights<double>(const LevelV<double>&, bool, int*, int, cudaStream_t);
 template int launch_interp_weights<float>(const LevelV<float>&, bool, int*, int, cudaStream_t);
 template int launch_rap<double>(const LevelV<double>&, bool, LevelV<double>, cudaStream_t);

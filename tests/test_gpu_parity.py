@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 from oracle import boxmg_oracle as O
+from paper_1803_02481_gb300 import inputs
 from tests.parity_helpers import (PROBLEMS, interp_planes, nine_from_five, oracle_hierarchy,
                                   oracle_solve, problem)
 
@@ -342,3 +343,61 @@ def test_pcg_needs_a_symmetric_fp64_cycle():
         with pytest.raises(bm.BoxMGError) as e:
             bm.setup(k, bm.default_options(**opts))
         assert e.value.code == bm.BMG_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# The paper's workload: D = diag(k/r, k r) on stretched cells (Section 5)
+# ---------------------------------------------------------------------------
+
+ANISO_CASES = {
+    # nx x ny cells of the unit square (cell aspect nx / ny), r = 16
+    "paper1023x63": lambda: {"k": np.ones((63, 1023)),
+                             "b": np.random.default_rng(41).uniform(-1, 1, (63, 1023)),
+                             "r": 16.0, "aspect": 1023 / 63},
+    # the same with a block field k (10^[-1, 1], 8-cell blocks) and r = 4
+    "blocks511x31": lambda: dict(inputs.block_problem(seed=42, block=8, lo=-1, hi=1, nx=511, ny=31),
+                                 r=4.0, aspect=511 / 31),
+    # uncompensated: isotropic k on stretched cells, V(2,1) slow but correct
+    "stretched255x63": lambda: {"k": np.ones((63, 255)),
+                                "b": np.random.default_rng(43).uniform(-1, 1, (63, 255)),
+                                "r": 1.0, "aspect": 255 / 63},
+}
+
+
+@functools.lru_cache(maxsize=None)
+def aniso_case(name):
+    return ANISO_CASES[name]()
+
+
+@pytest.mark.parametrize("name", list(ANISO_CASES))
+def test_anisotropic_stretched_workload_matches_oracle(name):
+    pr = aniso_case(name)
+    ho = O.setup(pr["k"], r=pr["r"], aspect=pr["aspect"])
+    hg = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=pr["r"], cell_aspect=pr["aspect"],
+                                                   max_cycles=400))
+    L = ho.nlevels
+    sg = hg.level_stencil(L - 1)
+    so = ho.levels[L - 1].st
+    for d in ("C", "W", "S"):
+        assert np.array_equal(sg[d], so[d]), d
+    for l in range(L - 1):
+        assert rel_stencil_err(hg.level_stencil(l), ho.levels[l].st) <= 1e-12 * (L - 1 - l), l
+    ro = O.solve(ho, pr["b"], tol=1e-10, max_cycles=400)
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+    hg.destroy()
+    assert ro.converged and info.cycles == ro.cycles, (info.cycles, ro.cycles)
+    assert abs(info.rel_resid - ro.rel_resid) <= 1e-13
+    assert np.abs(x.cpu().numpy() - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+
+
+def test_anisotropic_options_are_checked():
+    k = dev(np.ones((31, 63)))
+    for opts in (dict(aniso_r=0.0), dict(cell_aspect=-1.0), dict(aniso_r=float("inf"))):
+        with pytest.raises(bm.BoxMGError) as e:
+            bm.setup(k, bm.default_options(**opts))
+        assert e.value.code == bm.BMG_EINVAL
+    h = bm.setup(k, bm.default_options(aniso_r=4.0))
+    u = dev(np.ones((31, 63)))
+    with pytest.raises(bm.BoxMGError):
+        h.assemble_backward(u, u, torch.zeros_like(u))
+    h.destroy()
