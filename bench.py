@@ -292,6 +292,7 @@ def run_ours(args, rank, world, local_rank):
         extra["batched"] = batch_leg(bm, torch, dev, stream)
         extra["threshold_sweep"] = threshold_sweep(bm, torch, k, b, stream)
         extra["pcg"] = pcg_leg(bm, torch, k, b, stream, tol, ms / args.steps, info.cycles)
+        extra["paper_workload"] = paper_workload_leg(bm, torch, dev, stream)
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.quick:
@@ -412,6 +413,45 @@ def lognormal_leg(bm, torch, dev, stream, args, n=8191):
     out["speedup_fp32_refine_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["fp32_refine"]["ms_per_solve"]
     d = (xs["fp32_refine"] - xs["fp64"]).abs().max() / xs["fp64"].abs().max()
     out["max_rel_diff_fp32_refine_vs_fp64"] = float(d)
+    return out
+
+
+def paper_workload_leg(bm, torch, dev, stream, nx=16383, ny=1023, r=16.0):
+    """The paper's own problem class (Section 5): D = diag(1/r, r), r = 16, on
+    nx x ny cells of the unit square (cell aspect nx/ny = 16, the compensated
+    anisotropy), constant k = 1, b uniform[-1, 1] (seed 7), to 1e-10: FP64
+    V(2,1), FP32 V-cycles inside FP64 refinement, and CG preconditioned by a
+    symmetric V(1,1) cycle (setup + solve timed)."""
+    k = torch.ones((ny, nx), dtype=torch.float64, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    b = torch.rand((ny, nx), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+    out = {"workload": f"D = diag(1/{r:g}, {r:g}), {nx}x{ny} cells of the unit square "
+                       f"(aspect {nx / ny:.3f}), k = 1, tol 1e-10"}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    base = dict(aniso_r=r, cell_aspect=nx / ny, max_cycles=500)
+    for name, kw in (("fp64", dict(precision=bm.BMG_FP64)),
+                     ("fp32_refine", dict(precision=bm.BMG_FP32_REFINE)),
+                     ("fp64_pcg_v11", dict(precision=bm.BMG_FP64, nu1=1, nu2=1,
+                                           solver=bm.BMG_SOLVER_PCG))):
+        opts = bm.default_options(**base, **kw)
+        x = torch.zeros_like(b)
+        times = []
+        for rep in range(3):
+            x.zero_()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            h = bm.setup(k, opts, stream=stream)
+            _, info = h.solve(b, x, tol=1e-10, stream=stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            h.destroy()
+            if rep:
+                times.append(ev0.elapsed_time(ev1))
+        ms = sum(times) / len(times)
+        out[name] = {"value": nx * ny / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms,
+                     "cycles": info.cycles, "rel_resid": info.rel_resid}
     return out
 
 
