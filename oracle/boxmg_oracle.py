@@ -57,8 +57,9 @@ Readings where the paper is silent (each is also listed in the design notes):
   runs the colours forward, post-smoothing in reverse.
 * residual norm: the Euclidean norm; the stop test is applied after each
   full cycle (and once before the first).
-* sizes: nx and ny of the form 2^m - 1; coarsening stops when the smaller
-  side reaches 3.
+* sizes: any nx, ny >= 2; a side of n points coarsens to floor(n / 2)
+  (coarse point I is fine point 2I), and coarsening stops once the smaller
+  side is at most 3.  2^m - 1 sides keep every level of that form.
 
 Data layout: every grid quantity is a float64 array of shape (ny, nx),
 ``a[j, i]`` with i the x index (fast).  A stencil is a dict of nine planes,
@@ -196,8 +197,11 @@ def csr_to_stencil(a: sp.spmatrix, nx: int, ny: int) -> dict:
 # ---------------------------------------------------------------------------
 
 def coarse_size(n: int) -> int:
-    """Standard coarsening by 2: coarse point I is fine point 2I (1-based)."""
-    return (n - 1) // 2
+    """Standard coarsening by 2: coarse point I is fine point 2I (1-based),
+    so a side of n fine points has floor(n / 2) coarse points ((n - 1) / 2
+    for the 2^m - 1 sides; for an even n the last fine point is a coarse
+    point)."""
+    return n // 2
 
 
 def collapse_stencil(st: dict) -> dict:
@@ -272,12 +276,15 @@ def interpolation(st: dict) -> sp.csr_matrix:
     add(fidx[1::2, 1::2], cidx(q, p), np.ones((ncy, ncx)))
 
     xw, xe, ys, yn = edge_weights(st)
+    # fine points of odd 1-based index along x and y: (n + 1) // 2 of them
+    # (ncx + 1 for the 2^m - 1 sides, ncx for an even side)
+    nex, ney = (nx + 1) // 2, (ny + 1) // 2
     # x-edge point (row 2q+1, col 2p): west coarse (q, p-1), east (q, p)
-    q, p = np.meshgrid(np.arange(ncy), np.arange(ncx + 1), indexing="ij")
+    q, p = np.meshgrid(np.arange(ncy), np.arange(nex), indexing="ij")
     add(fidx[1::2, 0::2], cidx(q, p - 1), xw)
     add(fidx[1::2, 0::2], cidx(q, p), xe)
     # y-edge point (row 2q, col 2p+1): south coarse (q-1, p), north (q, p)
-    q, p = np.meshgrid(np.arange(ncy + 1), np.arange(ncx), indexing="ij")
+    q, p = np.meshgrid(np.arange(ney), np.arange(ncx), indexing="ij")
     add(fidx[0::2, 1::2], cidx(q - 1, p), ys)
     add(fidx[0::2, 1::2], cidx(q, p), yn)
 
@@ -292,11 +299,11 @@ def interpolation(st: dict) -> sp.csr_matrix:
     cs = (slice(0, None, 2), slice(0, None, 2))
     c = st["C"][cs]
     aw, ae, as_, an = st["W"][cs], st["E"][cs], st["S"][cs], st["N"][cs]
-    q, p = np.meshgrid(np.arange(ncy + 1), np.arange(ncx + 1), indexing="ij")
-    ys_w, ys_e = ysp[:, 0:ncx + 1], ysp[:, 1:ncx + 2]   # W nbr (q,p-1), E nbr (q,p)
-    yn_w, yn_e = ynp[:, 0:ncx + 1], ynp[:, 1:ncx + 2]
-    xw_s, xw_n = xwp[0:ncy + 1, :], xwp[1:ncy + 2, :]   # S nbr (q-1,p), N nbr (q,p)
-    xe_s, xe_n = xep[0:ncy + 1, :], xep[1:ncy + 2, :]
+    q, p = np.meshgrid(np.arange(ney), np.arange(nex), indexing="ij")
+    ys_w, ys_e = ysp[:, 0:nex], ysp[:, 1:nex + 1]       # W nbr (q,p-1), E nbr (q,p)
+    yn_w, yn_e = ynp[:, 0:nex], ynp[:, 1:nex + 1]
+    xw_s, xw_n = xwp[0:ney, :], xwp[1:ney + 1, :]       # S nbr (q-1,p), N nbr (q,p)
+    xe_s, xe_n = xep[0:ney, :], xep[1:ney + 1, :]
     w_sw = (st["SW"][cs] + aw * ys_w + as_ * xw_s) / c
     w_se = (st["SE"][cs] + ae * ys_e + as_ * xe_s) / c
     w_nw = (st["NW"][cs] + aw * yn_w + an * xw_n) / c
@@ -426,14 +433,15 @@ class Hierarchy:
 
 
 def valid_size(n: int) -> bool:
-    return n >= 3 and ((n + 1) & n) == 0
+    return n >= 2
 
 
 def level_shapes(nx: int, ny: int):
-    """[(nx, ny) finest, ..., coarsest]: halve (n - 1) / 2 until the smaller
-    side is 3."""
+    """[(nx, ny) finest, ..., coarsest]: coarsen both sides (n -> floor(n/2))
+    while the smaller side exceeds 3 (2^m - 1 sides end at 3; other sides at
+    2 or 3)."""
     if not (valid_size(nx) and valid_size(ny)):
-        raise ValueError("grid sides must be 2^m - 1 >= 3")
+        raise ValueError("grid sides must be at least 2")
     out = [(nx, ny)]
     while min(nx, ny) > 3:
         nx, ny = coarse_size(nx), coarse_size(ny)

@@ -103,20 +103,39 @@ def _hat(n_fine, n_coarse, idx):
     return np.interp(xf, nodes, vals)
 
 
-def test_interpolation_constant_k_is_bilinear():
+@pytest.mark.parametrize("nx, ny", [(15, 7), (16, 8), (14, 9), (6, 5)])
+def test_interpolation_constant_k_is_bilinear(nx, ny):
     """k = 1: every column of P is the tensor product of 1D hats on the
     coarse nodes plus the boundary (weights 1, 1/2, 1/4 inside; the fine
     point between the wall and the first coarse node gets 1/3, a corner
-    1/9)."""
-    nx, ny = 15, 7
+    1/9).  On an even side the last fine point is itself a coarse node next
+    to the wall; the edge points on that last fine line collapse the wall's
+    Dirichlet face into their denominator (flux balance), so they (and the
+    centre points beside them, which use their weights) are left out of
+    the hat comparison and the edge points are checked against that closed
+    form instead: k = 1 gives 1/4, and 1/5 next to a corner."""
     st = O.assemble_fv5(np.ones((ny, nx)))
     p = O.interpolation(st).toarray()
-    ncx, ncy = 7, 3
+    ncx, ncy = nx // 2, ny // 2
+    keep = np.ones((ny, nx), dtype=bool)      # the centre points next to that
+    if nx % 2 == 0:                            # line use its edge weights too
+        keep[:, -2:] = False
+    if ny % 2 == 0:
+        keep[-2:, :] = False
     for q in range(ncy):
         for pp in range(ncx):
             expect = np.outer(_hat(ny, ncy, q), _hat(nx, ncx, pp))
-            np.testing.assert_allclose(p[:, q * ncx + pp].reshape(ny, nx), expect,
-                                       rtol=0, atol=1e-15)
+            got = p[:, q * ncx + pp].reshape(ny, nx)
+            np.testing.assert_allclose(got[keep], expect[keep], rtol=0, atol=1e-15)
+    if nx % 2 == 0:
+        # y-edge points (row j odd, 1-based) on the last column: weight to
+        # the coarse node above and below; denominators 4 (5 at a wall row)
+        col = p.reshape(ny, nx, ncy * ncx)[:, -1, :]
+        for j in range(1, ny + 1, 2):
+            den = 4.0 + (j == 1) + (j == ny)
+            for qq in (j // 2 - 1, j // 2):          # coarse rows below / above (0-based)
+                if 0 <= qq < ncy:
+                    assert abs(col[j - 1, qq * ncx + ncx - 1] - 1.0 / den) <= 1e-15
 
 
 def test_interpolation_layered_medium_flux_weights():
@@ -407,7 +426,7 @@ def test_zero_rhs_and_bad_input():
     res = O.solve(h, np.zeros((7, 7)))
     assert res.cycles == 0 and res.rel_resid == 0.0
     with pytest.raises(ValueError):
-        O.setup(np.ones((8, 7)))
+        O.setup(np.ones((1, 7)))          # a side needs at least 2 cells
     with pytest.raises(ValueError):
         O.setup(-np.ones((7, 7)))
     k = np.ones((7, 7))
@@ -661,3 +680,43 @@ def test_paper_workload_vcycle_converges_like_poisson():
     h_iso = O.setup(np.ones((15, 255)), aspect=17.0)
     res_iso = O.solve(h_iso, b, tol=1e-10, max_cycles=100)
     assert res_iso.cycles > 3 * res.cycles
+
+
+
+# ---------------------------------------------------------------------------
+# General grid sizes (sides other than 2^m - 1)
+# ---------------------------------------------------------------------------
+
+def test_level_shapes_for_general_sides():
+    assert O.level_shapes(16, 8) == [(16, 8), (8, 4), (4, 2)]
+    assert O.level_shapes(100, 60) == [(100, 60), (50, 30), (25, 15), (12, 7), (6, 3)]
+    assert O.level_shapes(255, 15) == [(255, 15), (127, 7), (63, 3)]
+    assert O.level_shapes(3, 40) == [(3, 40)]
+
+
+@pytest.mark.parametrize("nx, ny", [(20, 13), (32, 32), (10, 6), (4, 4), (37, 18)])
+def test_vcycle_converges_to_direct_solution_general_sides(nx, ny):
+    rng = np.random.default_rng(nx * 100 + ny)
+    k = 10.0 ** rng.uniform(-2, 2, size=(ny, nx))
+    b = rng.uniform(-1, 1, (ny, nx))
+    h = O.setup(k)
+    for lv in h.levels[:-1]:
+        st = lv.st
+        scale = np.abs(st["C"]).max()
+        assert np.allclose(st["W"][:, 1:], st["E"][:, :-1], rtol=0, atol=1e-13 * scale)
+        assert np.allclose(st["SW"][1:, 1:], st["NE"][:-1, :-1], rtol=0, atol=1e-13 * scale)
+        assert np.linalg.eigvalsh(O.stencil_to_csr(st).toarray()).min() > 0
+    res = O.solve(h, b, tol=1e-13, max_cycles=400)
+    assert res.converged
+    xd = O.direct_solve(k, b)
+    assert np.abs(res.x - xd).max() <= 1e-10 * np.abs(xd).max()
+
+
+def test_poisson_rate_on_even_sides_is_grid_independent():
+    rates = []
+    for n in (32, 64, 128):
+        rng = np.random.default_rng(n)
+        h = O.setup(np.ones((n, n)))
+        res = O.solve(h, rng.uniform(-1, 1, (n, n)), tol=1e-10, max_cycles=100)
+        rates.append((res.history[-1] / res.history[0]) ** (1.0 / res.cycles))
+    assert max(rates) < 0.3 and max(rates) - min(rates) < 0.05
