@@ -28,9 +28,12 @@
  *     stream before returning.
  *   - Return value: BMG_OK (0) or a negative BMG_E* code; no call aborts, and
  *     no call falls back to the CPU.  bmg_strerror() gives a message.
- *   - Sizes: nx and ny must be 2^m - 1 with m >= 2.  Levels are halved,
- *     n -> (n - 1) / 2, until the smaller side is 3; the coarsest level must
- *     have at most BMG_MAX_COARSEST unknowns.
+ *   - Sizes: nx, ny >= 2.  Coarse point I is fine point 2I (1-based), so a
+ *     side of n points coarsens to floor(n / 2) ((n - 1) / 2 for the 2^m - 1
+ *     sides, which keep every level of that form; on an even side the last
+ *     fine point is a coarse point).  Levels are coarsened while the smaller
+ *     side exceeds 3; the coarsest level must have at most BMG_MAX_COARSEST
+ *     unknowns.  Batched problems (bmg_batch_*) keep sides 2^m - 1.
  */
 #ifndef BOXMG_H
 #define BOXMG_H

@@ -37,7 +37,8 @@ namespace {
     if (e_ != cudaSuccess) return BMG_ECUDA;            \
   } while (0)
 
-bool valid_side(int n) { return n >= 3 && ((n + 1) & n) == 0; }
+// Grid sides: any n >= 2 (a side of n points coarsens to floor(n / 2)).
+bool valid_side(int n) { return n >= 2; }
 
 double now_ms() {
   using clk = std::chrono::steady_clock;
@@ -190,8 +191,8 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
     int a = nx, b = ny;
     sz.push_back({a, b});
     while (std::min(a, b) > 3) {
-      a = (a - 1) / 2;
-      b = (b - 1) / 2;
+      a = a / 2;   // coarse point I is fine point 2I
+      b = b / 2;
       sz.push_back({a, b});
     }
   }

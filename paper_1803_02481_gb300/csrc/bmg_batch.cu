@@ -577,7 +577,8 @@ extern "C" int bmg_batch_setup(int nprob, const double* const* k_dev, const int*
   };
   // individual hierarchies (threshold: levels of side <= 31 in the coarse kernel)
   for (int p = 0; p < nprob; ++p) {
-    if (!k_dev[p]) return fail(BMG_EINVAL);
+    // batched problems: square, sides 2^m - 1 (the level classes below rely on it)
+    if (!k_dev[p] || n[p] < 3 || ((n[p] + 1) & n[p]) != 0) return fail(BMG_EINVAL);
     int levels_small = 0;
     for (int m = n[p]; m >= 3; m = (m - 1) / 2)
       if (m <= kCoarseSide) ++levels_small;

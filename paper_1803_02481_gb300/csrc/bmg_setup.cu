@@ -154,11 +154,14 @@ __device__ __forceinline__ void yedge(const LevelV<T>& L, int o, T& ws, T& wn, i
   wn = ((a.n + a.nw) + a.ne) / den;
 }
 
-// One thread per coarse-grid index (I, J), 0 <= I <= ncx, 0 <= J <= ncy.
-// Computes the weights of the x-edge point (2I+1, 2J), the y-edge point
-// (2I, 2J+1) and the centre point (2I+1, 2J+1).  The centre point's four
-// edge neighbours are recomputed here with the same code, so the stored
-// edge weights and the ones used for the centre agree bit for bit.
+// One thread per coarse-grid index (I, J), 0 <= I <= ncx, 0 <= J <= ncy
+// (ncx = floor(nx / 2)).  Computes the weights of the x-edge point
+// (2I+1, 2J), the y-edge point (2I, 2J+1) and the centre point (2I+1, 2J+1)
+// where those fine points exist: on an even side the last fine point is a
+// coarse point, so column 2I+1 (or row 2J+1) may lie beyond the grid; its
+// weights stay zero and nothing is read there.  The centre point's four edge
+// neighbours are recomputed here with the same code, so the stored edge
+// weights and the ones used for the centre agree bit for bit.
 template <typename T, bool NINE>
 __global__ void k_interp_weights(LevelV<T> F, int ncx, int ncy, int* derr, int level) {
   const int lbit = 1 << (8 + level);
@@ -167,21 +170,26 @@ __global__ void k_interp_weights(LevelV<T> F, int ncx, int ncy, int* derr, int l
   if (I > ncx || J > ncy) return;
   const int p = F.pitch, cp = F.cpitch;
   const int c = J * cp + I;
+  const bool col_odd = 2 * I + 1 <= F.nx;   // fine column 2I+1 exists
+  const bool row_odd = 2 * J + 1 <= F.ny;   // fine row 2J+1 exists
   T xw0 = 0, xe0 = 0, xw1 = 0, xe1 = 0, ys0 = 0, yn0 = 0, ys1 = 0, yn1 = 0;
   // x-edge (2I+1, 2J) and (2I+1, 2J+2)
-  if (J >= 1) xedge<T, NINE>(F, (2 * J) * p + 2 * I + 1, xw0, xe0, derr, lbit);
-  if (J + 1 <= ncy) xedge<T, NINE>(F, (2 * J + 2) * p + 2 * I + 1, xw1, xe1, derr, lbit);
+  if (col_odd && J >= 1) xedge<T, NINE>(F, (2 * J) * p + 2 * I + 1, xw0, xe0, derr, lbit);
+  if (col_odd && J + 1 <= ncy)
+    xedge<T, NINE>(F, (2 * J + 2) * p + 2 * I + 1, xw1, xe1, derr, lbit);
   // y-edge (2I, 2J+1) and (2I+2, 2J+1)
-  if (I >= 1) yedge<T, NINE>(F, (2 * J + 1) * p + 2 * I, ys0, yn0, derr, lbit);
-  if (I + 1 <= ncx) yedge<T, NINE>(F, (2 * J + 1) * p + 2 * I + 2, ys1, yn1, derr, lbit);
-  if (J >= 1) {
+  if (row_odd && I >= 1) yedge<T, NINE>(F, (2 * J + 1) * p + 2 * I, ys0, yn0, derr, lbit);
+  if (row_odd && I + 1 <= ncx)
+    yedge<T, NINE>(F, (2 * J + 1) * p + 2 * I + 2, ys1, yn1, derr, lbit);
+  if (col_odd && J >= 1) {
     F.P[XW][c] = xw0;
     F.P[XE][c] = xe0;
   }
-  if (I >= 1) {
+  if (row_odd && I >= 1) {
     F.P[YS][c] = ys0;
     F.P[YN][c] = yn0;
   }
+  if (!(col_odd && row_odd)) return;
   // centre (2I+1, 2J+1): the fine equation with the edge neighbours replaced
   // by their interpolants.
   St<T, NINE> a(F, (2 * J + 1) * p + 2 * I + 1);
@@ -218,6 +226,8 @@ __device__ __forceinline__ T rap_entry(const LevelV<T>& F, int I, int J) {
   for (int py = -1; py <= 1; ++py) {
 #pragma unroll
     for (int px = -1; px <= 1; ++px) {
+      // fine points beyond an even side do not exist (their weights are 0)
+      if (2 * I + px > F.nx || 2 * J + py > F.ny) continue;
       const int o = (2 * J + py) * p + (2 * I + px);
       T inner = T(0);
 #pragma unroll
@@ -377,7 +387,7 @@ int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy,
 
 template <typename T>
 int launch_interp_weights(const LevelV<T>& fine, bool nine, int* derr, int level, cudaStream_t s) {
-  const int ncx = (fine.nx - 1) / 2, ncy = (fine.ny - 1) / 2;
+  const int ncx = fine.nx / 2, ncy = fine.ny / 2;
   dim3 grid(cdiv(ncx + 1, 128), ncy + 1);
   if (nine)
     k_interp_weights<T, true><<<grid, 128, 0, s>>>(fine, ncx, ncy, derr, level);

@@ -52,7 +52,7 @@ def interp_planes(p, nxf, nyf):
     Returns (planes, valid) with planes[k][J, I] for 0 <= I <= ncx,
     0 <= J <= ncy; valid marks entries whose fine point exists and whose
     coarse target is interior."""
-    ncx, ncy = (nxf - 1) // 2, (nyf - 1) // 2
+    ncx, ncy = nxf // 2, nyf // 2
     J, I = np.meshgrid(np.arange(ncy + 1), np.arange(ncx + 1), indexing="ij")
     # (fine dx, fine dy, coarse dI, coarse dJ) per plane, fine point
     # (2I + fx, 2J + fy) and coarse target (I + cx, J + cy), 1-based

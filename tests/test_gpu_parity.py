@@ -401,3 +401,59 @@ def test_anisotropic_options_are_checked():
     with pytest.raises(bm.BoxMGError):
         h.assemble_backward(u, u, torch.zeros_like(u))
     h.destroy()
+
+
+# ---------------------------------------------------------------------------
+# General grid sides (other than 2^m - 1)
+# ---------------------------------------------------------------------------
+
+GENERAL_CASES = {
+    "even100x60": lambda: dict(inputs.block_problem(seed=51, block=8, lo=-2, hi=2, nx=100, ny=60),
+                               r=1.0, aspect=1.0),
+    "mixed131x46": lambda: dict(inputs.block_problem(seed=52, block=16, lo=-3, hi=3, nx=131, ny=46),
+                                r=1.0, aspect=1.0),
+    "pow2_256x256": lambda: dict(inputs.block_problem(seed=53, block=32, lo=-2, hi=2, nx=256, ny=256),
+                                 r=1.0, aspect=1.0),
+    # the paper's local problem: 568 x 71 cells (8:1) with compensating r = 8
+    "paper568x71": lambda: {"k": np.ones((71, 568)),
+                            "b": np.random.default_rng(54).uniform(-1, 1, (71, 568)),
+                            "r": 8.0, "aspect": 8.0},
+    # wide enough for the TMA-staged sweeps on the finest and first coarse level
+    "even2100x40": lambda: dict(inputs.block_problem(seed=55, block=32, lo=-1, hi=1, nx=2100, ny=40),
+                                r=1.0, aspect=1.0),
+    "tiny2x5": lambda: {"k": np.array([[1.0, 2.0], [3.0, 4.0], [5.0, 6.0], [7.0, 8.0], [9.0, 1.0]]),
+                        "b": np.arange(10.0).reshape(5, 2) - 4.5, "r": 1.0, "aspect": 1.0},
+}
+
+
+@functools.lru_cache(maxsize=None)
+def general_case(name):
+    return GENERAL_CASES[name]()
+
+
+@pytest.mark.parametrize("name", list(GENERAL_CASES))
+def test_general_sides_match_oracle(name):
+    pr = general_case(name)
+    ho = O.setup(pr["k"], r=pr["r"], aspect=pr["aspect"])
+    hg = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=pr["r"], cell_aspect=pr["aspect"],
+                                                   max_cycles=400))
+    L = ho.nlevels
+    assert hg.nlevels == L
+    for l in range(L):
+        assert hg.level_shape(l) == ho.levels[l].shape[::-1], l
+    sg = hg.level_stencil(L - 1)
+    so = ho.levels[L - 1].st
+    for d in ("C", "W", "S"):
+        assert np.array_equal(sg[d], so[d]), d
+    # each setup step on the GPU's own input
+    for l in range(L - 1, 0, -1):
+        st_g = nine_from_five(hg.level_stencil(l))
+        assert p_err(hg, l, st_g) <= 1e-12, l
+        coarse_o = O.galerkin(st_g, O.interpolation(st_g))
+        assert rel_stencil_err(hg.level_stencil(l - 1), coarse_o) <= 1e-12, l
+    ro = O.solve(ho, pr["b"], tol=1e-10, max_cycles=400)
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+    hg.destroy()
+    assert ro.converged and info.cycles == ro.cycles, (info.cycles, ro.cycles)
+    assert abs(info.rel_resid - ro.rel_resid) <= 1e-13
+    assert np.abs(x.cpu().numpy() - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
