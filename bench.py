@@ -293,6 +293,8 @@ def run_ours(args, rank, world, local_rank):
         extra["threshold_sweep"] = threshold_sweep(bm, torch, k, b, stream)
         extra["pcg"] = pcg_leg(bm, torch, k, b, stream, tol, ms / args.steps, info.cycles)
         extra["paper_workload"] = paper_workload_leg(bm, torch, dev, stream)
+        # the paper's global grid as it is (9088 x 568, aspect 16), r = 16
+        extra["paper_workload_9088x568"] = paper_workload_leg(bm, torch, dev, stream, nx=9088, ny=568)
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.quick:

@@ -250,8 +250,11 @@ def test_zero_rhs_and_error_codes():
     with pytest.raises(bm.BoxMGError) as e:
         bm.setup(dev(bad))
     assert e.value.code == bm.BMG_EINVAL
-    with pytest.raises(bm.BoxMGError) as e:
-        bm.setup(dev(np.ones((30, 31))))
+    with pytest.raises(bm.BoxMGError) as e:          # a side needs at least 2 cells
+        bm.setup(dev(np.ones((1, 31))))
+    assert e.value.code == bm.BMG_EINVAL
+    with pytest.raises(bm.BoxMGError) as e:          # coarsest level above 1024 unknowns
+        bm.setup(dev(np.ones((3, 400))))
     assert e.value.code == bm.BMG_EINVAL
     # the cycle cap returns ENOCONV with the last iterate
     pr = problem("blocks255")
