@@ -92,7 +92,21 @@ def harmonic_face(k1: np.ndarray, k2: np.ndarray) -> np.ndarray:
     return 2.0 * k1 * k2 / (k1 + k2)
 
 
-def assemble_fv5(k: np.ndarray, r: float = 1.0, aspect: float = 1.0) -> dict:
+def boundary_face(dirichlet: np.ndarray, k_normal: np.ndarray, beta) -> np.ndarray:
+    """Coefficient of a boundary face.  ``dirichlet`` is the Dirichlet face
+    coefficient (the wall half a cell from the centre: 2 k_n times the face
+    length over the cell width) and ``beta`` selects the condition on that
+    side: None for u = 0 (Dirichlet, the value as given), or beta >= 0 for
+    the Robin condition k du/dn + alpha u = 0 with beta = alpha times the
+    cell width normal to the wall: eliminating the wall value gives the
+    series conductance dirichlet * beta / (2 k_n + beta); beta = 0 is the
+    Neumann condition (no flux)."""
+    if beta is None:
+        return dirichlet
+    return dirichlet * (beta / (2.0 * k_normal + beta))
+
+
+def assemble_fv5(k: np.ndarray, r: float = 1.0, aspect: float = 1.0, bc=None) -> dict:
     """5-point cell-centred FV operator for -div(D grad u) = f, u = 0 on the
     boundary of the unit square (Section 5, Eqs. (diffusion),
     (diffusion_bc)), in integrated form (for square cells: scaled by h^2).
@@ -104,8 +118,16 @@ def assemble_fv5(k: np.ndarray, r: float = 1.0, aspect: float = 1.0) -> dict:
     hy / hx, y faces that of k r times hx / hy; a boundary face sits half a
     cell from the cell centre and carries 2 (k / r) hy / hx or 2 k r hx / hy.
     The diagonal C is the sum of the cell's four face coefficients.  With
-    r = aspect = 1 every factor is an exact 1.
+    r = aspect = 1 every factor is an exact 1.  ``bc`` = (west, east, south,
+    north), each None (u = 0, the default) or a Robin/Neumann beta (see
+    boundary_face); not all four may be Neumann (the operator would be
+    singular).
     """
+    bc = (None, None, None, None) if bc is None else tuple(bc)
+    if len(bc) != 4 or any(b is not None and not (np.isfinite(b) and b >= 0) for b in bc):
+        raise ValueError("bc: four entries, each None or a finite beta >= 0")
+    if all(b is not None and b == 0 for b in bc):
+        raise ValueError("Neumann on every side: the operator is singular")
     k = np.asarray(k, dtype=np.float64)
     ny, nx = k.shape
     inv_r, inv_a = 1.0 / r, 1.0 / aspect
@@ -118,10 +140,10 @@ def assemble_fv5(k: np.ndarray, r: float = 1.0, aspect: float = 1.0) -> dict:
     st["N"][:-1, :] = ay
     st["S"][1:, :] = ay
     bw = np.zeros((ny, nx))                          # boundary face coefficients
-    bw[:, 0] += 2.0 * kx[:, 0] * aspect
-    bw[:, -1] += 2.0 * kx[:, -1] * aspect
-    bw[0, :] += 2.0 * ky[0, :] * inv_a
-    bw[-1, :] += 2.0 * ky[-1, :] * inv_a
+    bw[:, 0] += boundary_face(2.0 * kx[:, 0] * aspect, kx[:, 0], bc[0])
+    bw[:, -1] += boundary_face(2.0 * kx[:, -1] * aspect, kx[:, -1], bc[1])
+    bw[0, :] += boundary_face(2.0 * ky[0, :] * inv_a, ky[0, :], bc[2])
+    bw[-1, :] += boundary_face(2.0 * ky[-1, :] * inv_a, ky[-1, :], bc[3])
     st["C"] = st["W"] + st["E"] + st["S"] + st["N"] + bw
     return st
 
@@ -450,9 +472,10 @@ def level_shapes(nx: int, ny: int):
 
 
 def setup(k: np.ndarray, nu1: int = 2, nu2: int = 1,
-          interp_residual_term: bool = False, r: float = 1.0, aspect: float = 1.0) -> Hierarchy:
-    """BoxMG setup: assemble the fine operator (``r``, ``aspect`` as in
-    assemble_fv5), then for each level build P_l from A_l and
+          interp_residual_term: bool = False, r: float = 1.0, aspect: float = 1.0,
+          bc=None) -> Hierarchy:
+    """BoxMG setup: assemble the fine operator (``r``, ``aspect``, ``bc`` as
+    in assemble_fv5), then for each level build P_l from A_l and
     A_{l-1} = P_l^T A_l P_l; factor A_0 (Section 2)."""
     ny, nx = k.shape
     shapes = level_shapes(nx, ny)
@@ -460,7 +483,7 @@ def setup(k: np.ndarray, nu1: int = 2, nu2: int = 1,
         raise ValueError("coefficients must be finite and positive")
     if not (np.isfinite(r) and r > 0 and np.isfinite(aspect) and aspect > 0):
         raise ValueError("r and the cell aspect must be finite and positive")
-    st = assemble_fv5(k, r, aspect)
+    st = assemble_fv5(k, r, aspect, bc)
     fine_to_coarse = [Level(st)]
     for _ in shapes[1:]:
         p = interpolation(st)

@@ -720,3 +720,69 @@ def test_poisson_rate_on_even_sides_is_grid_independent():
         res = O.solve(h, rng.uniform(-1, 1, (n, n)), tol=1e-10, max_cycles=100)
         rates.append((res.history[-1] / res.history[0]) ** (1.0 / res.cycles))
     assert max(rates) < 0.3 and max(rates) - min(rates) < 0.05
+
+
+# ---------------------------------------------------------------------------
+# Neumann and Robin boundaries
+# ---------------------------------------------------------------------------
+
+def _mms_error(u_exact, f, bc, n):
+    h = 1.0 / n
+    xc = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(xc, xc)
+    st = O.assemble_fv5(np.ones((n, n)), bc=bc)
+    b = f(X, Y) * h * h
+    uh = spla.spsolve(O.stencil_to_csr(st).tocsc(), b.ravel()).reshape(n, n)
+    return np.abs(uh - u_exact(X, Y)).max()
+
+
+def test_neumann_sides_are_second_order():
+    # u = cos(pi x) sin(pi y): no flux through x = 0, 1; u = 0 at y = 0, 1
+    u = lambda x, y: np.cos(np.pi * x) * np.sin(np.pi * y)  # noqa: E731
+    f = lambda x, y: 2 * np.pi ** 2 * u(x, y)  # noqa: E731
+    e = [_mms_error(u, f, (0.0, 0.0, None, None), n) for n in (16, 32, 64)]
+    assert e[0] / e[1] > 3.7 and e[1] / e[2] > 3.8
+
+
+def test_robin_sides_are_second_order():
+    # u = g(x) sin(pi y), g = 1 + x - x^2, meets k du/dn + alpha u = 0 with
+    # alpha = 1 at x = 0 and x = 1 (k = 1); beta = alpha * h
+    g = lambda x: 1 + x - x * x  # noqa: E731
+    u = lambda x, y: g(x) * np.sin(np.pi * y)  # noqa: E731
+    f = lambda x, y: (2 + np.pi ** 2 * g(x)) * np.sin(np.pi * y)  # noqa: E731
+    e = []
+    for n in (16, 32, 64):
+        e.append(_mms_error(u, f, (1.0 / n, 1.0 / n, None, None), n))
+    assert e[0] / e[1] > 3.7 and e[1] / e[2] > 3.8
+
+
+def test_boundary_face_limits_and_closed_form():
+    k = np.ones((3, 4))
+    d = O.assemble_fv5(k)
+    n = O.assemble_fv5(k, bc=(0.0, None, None, None))
+    big = O.assemble_fv5(k, bc=(1e300, None, None, None))
+    # Neumann removes the wall face (2 k) from the west column's diagonal
+    assert np.array_equal(n["C"][:, 0], d["C"][:, 0] - 2.0)
+    assert np.array_equal(n["C"][:, 1:], d["C"][:, 1:])
+    # beta -> infinity is the Dirichlet face
+    assert np.allclose(big["C"], d["C"], rtol=1e-15, atol=0)
+    # beta = 2 with k = 1: 2 * 2 / (2 + 2) = 1
+    rb = O.assemble_fv5(k, bc=(None, 2.0, None, None))
+    assert np.array_equal(rb["C"][:, -1], d["C"][:, -1] - 1.0)
+    with pytest.raises(ValueError):
+        O.assemble_fv5(k, bc=(0.0, 0.0, 0.0, 0.0))
+    with pytest.raises(ValueError):
+        O.assemble_fv5(k, bc=(-1.0, None, None, None))
+
+
+@pytest.mark.parametrize("bc", [(0.0, 0.0, None, 0.5), (None, 0.0, 0.0, 0.0), (0.1, 2.0, 0.0, None)])
+def test_vcycle_with_mixed_boundaries_converges_to_direct_solution(bc):
+    rng = np.random.default_rng(61)
+    k = 10.0 ** rng.uniform(-2, 2, size=(31, 31))
+    b = rng.uniform(-1, 1, (31, 31))
+    h = O.setup(k, bc=bc)
+    res = O.solve(h, b, tol=1e-13, max_cycles=400)
+    a = O.stencil_to_csr(O.assemble_fv5(k, bc=bc)).tocsc()
+    xd = spla.spsolve(a, b.ravel()).reshape(31, 31)
+    assert res.converged
+    assert np.abs(res.x - xd).max() <= 1e-9 * np.abs(xd).max()
