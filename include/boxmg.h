@@ -87,6 +87,12 @@ typedef struct {
                                (Section 5 uses r ~ 16); 1: isotropic (default) */
   double cell_aspect;       /* cell aspect hy / hx (nx x ny cells of the unit
                                square: nx / ny); 1: square cells (default)    */
+  double bc_beta[4];        /* boundary condition of the west, east, south and
+                               north wall: < 0 (default -1): u = 0; >= 0: the
+                               Robin condition k du/dn + alpha u = 0 with
+                               beta = alpha times the cell width normal to
+                               that wall (0: Neumann, no flux).  Not all four
+                               may be Neumann (the operator would be singular) */
 } bmg_options;
 
 typedef struct {
@@ -114,7 +120,9 @@ const char *bmg_last_error(void);
  * Assembles the fine 5-point operator (harmonic face means, 2k on Dirichlet
  * faces, scaled by h^2; with opt->aniso_r and opt->cell_aspect, x faces carry
  * the harmonic mean of k / r times hy / hx and y faces that of k r times
- * hx / hy, boundary faces 2 (k / r) hy / hx and 2 k r hx / hy), builds P_l
+ * hx / hy, boundary faces 2 (k / r) hy / hx and 2 k r hx / hy, times
+ * beta / (2 k_n + beta) on a wall with Robin coefficient beta, k_n = k / r
+ * or k r the coefficient normal to it), builds P_l
  * and A_{l-1} = P_l^T A_l P_l on every
  * level, factors A_0, and fixes the level schedule.  With precision
  * BMG_FP32_REFINE the coarse hierarchy (P and RAP) is built in FP32 from an
@@ -225,7 +233,8 @@ int bmg_op_interp(bmg_hierarchy *h, int level, const double *xc_dev,
  *   dA_f/dk_c = 2 k_n^2 / (k_c + k_n)^2.
  * With lam solving A lam = u - u_obs this is dL/dtheta for
  * L = 0.5 ||u - u_obs||^2.  Uses the k given to bmg_setup.  Isotropic square
- * cells only (aniso_r = cell_aspect = 1, else BMG_EINVAL). */
+ * cells with u = 0 on every wall only (aniso_r = cell_aspect = 1, all
+ * bc_beta < 0; else BMG_EINVAL). */
 int bmg_assemble_backward(bmg_hierarchy *h, const double *u_dev,
                           const double *lam_dev, double *dtheta_dev,
                           bmg_stream_t stream);
@@ -282,7 +291,8 @@ void bmg_batch_destroy(bmg_batch *b);
 /* ---- Allocation-free residual check --------------------------------------- */
 
 /* ||b - A(k) x||_2 and ||b||_2 for the 5-point cell-centred operator of k
- * (the operator bmg_setup assembles with aniso_r = cell_aspect = 1), written
+ * (the operator bmg_setup assembles with aniso_r = cell_aspect = 1 and u = 0
+ * on every wall), written
  * to norms_dev[0] and
  * norms_dev[1] (device memory, 2 doubles).  This entry point has no
  * counterpart in the paper: it exists for callers that cannot allocate

@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
                 ("interp_residual_term", ctypes.c_int), ("coarse_threshold", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("log_coefficients", ctypes.c_int),
                 ("solver", ctypes.c_int), ("aniso_r", ctypes.c_double),
-                ("cell_aspect", ctypes.c_double)]
+                ("cell_aspect", ctypes.c_double), ("bc_beta", ctypes.c_double * 4)]
 
 
 class Info(ctypes.Structure):
@@ -166,7 +166,13 @@ def default_options(**kw) -> Options:
     for k, v in kw.items():
         if k not in types:
             raise TypeError(f"unknown option {k!r}")
-        setattr(o, k, float(v) if types[k] is ctypes.c_double else int(v))
+        t = types[k]
+        if t is ctypes.c_double:
+            setattr(o, k, float(v))
+        elif t is ctypes.c_int:
+            setattr(o, k, int(v))
+        else:   # bc_beta: west, east, south, north; None for u = 0
+            setattr(o, k, t(*[-1.0 if b is None else float(b) for b in v]))
     return o
 
 

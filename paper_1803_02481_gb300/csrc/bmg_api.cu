@@ -171,6 +171,20 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
     set_last_error("aniso_r and cell_aspect must be finite and positive");
     return BMG_EINVAL;
   }
+  {
+    int neumann = 0;
+    for (double b : opt.bc_beta) {
+      if (!(b < INFINITY) || b != b) {
+        set_last_error("bc_beta entries must be finite");
+        return BMG_EINVAL;
+      }
+      neumann += b == 0.0;
+    }
+    if (neumann == 4) {
+      set_last_error("Neumann on every wall: the operator is singular");
+      return BMG_EINVAL;
+    }
+  }
   if (opt.solver == BMG_SOLVER_PCG &&
       (opt.precision != BMG_FP64 || opt.nu1 != opt.nu2 || opt.interp_residual_term)) {
     set_last_error("BMG_SOLVER_PCG needs precision BMG_FP64, nu1 == nu2 and "
@@ -262,7 +276,7 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   int* derr = &h->sc->err;
   LevelV<double>& fine64 = h->d.back();
   if (launch_assemble<double>(k, nx, ny, fine64, h->kcopy, derr, opt.log_coefficients != 0,
-                              opt.aniso_r, opt.cell_aspect, s))
+                              opt.aniso_r, opt.cell_aspect, opt.bc_beta, s))
     return fail(BMG_ECUDA);
   if (!fp32) {
     if ((rc = build_coarse<double>(h, h->d, s))) return fail(rc);
@@ -609,6 +623,7 @@ void bmg_default_options(bmg_options* opt) {
   opt->solver = BMG_SOLVER_VCYCLE;
   opt->aniso_r = 1.0;
   opt->cell_aspect = 1.0;
+  for (double& b : opt->bc_beta) b = -1.0;
 }
 
 const char* bmg_last_error(void) { return bmg::g_last_error; }
@@ -874,6 +889,8 @@ int bmg_assemble_backward(bmg_hierarchy* hp, const double* u, const double* lam,
   Hierarchy* h = H(hp);
   if (!h || !u || !lam || !dtheta) return BMG_EINVAL;
   if (h->opt.aniso_r != 1.0 || h->opt.cell_aspect != 1.0) return BMG_EINVAL;
+  for (double b : h->opt.bc_beta)
+    if (b >= 0.0) return BMG_EINVAL;
   bmg::launch_assemble_backward(h->kcopy, u, lam, dtheta, h->nx, h->ny,
                                 reinterpret_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;

@@ -311,7 +311,8 @@ void free_hierarchy(Hierarchy* h);
 // Kernel launch wrappers (defined in the .cu files).
 template <typename T>
 int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy,
-                    int* derr, bool log_k, double r, double aspect, cudaStream_t s);
+                    int* derr, bool log_k, double r, double aspect, const double* bc_beta,
+                    cudaStream_t s);
 template <typename T>
 int launch_interp_weights(const LevelV<T>& fine, bool nine, int* derr, int level, cudaStream_t s);
 template <typename T>

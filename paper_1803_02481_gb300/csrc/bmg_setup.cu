@@ -36,7 +36,16 @@ constexpr int kAX = 32, kAY = 8;
 // r = aspect = 1 every factor is an exact 1.
 struct AssemblyScale {
   double inv_r, r, aspect, inv_aspect;
+  double beta[4];   // west, east, south, north: < 0 Dirichlet, else Robin beta
 };
+
+// A boundary face: the Dirichlet coefficient d (wall half a cell away), or
+// for a Robin wall (k du/dn + alpha u = 0, beta = alpha times the cell width
+// normal to the wall) the series conductance d * beta / (2 k_n + beta);
+// beta = 0 is Neumann.
+__device__ __forceinline__ double boundary_face(double d, double kn, double beta) {
+  return beta < 0.0 ? d : d * (beta / (2.0 * kn + beta));
+}
 
 // Writes C, 1/C, W, S of the finest level and a dense copy of k; flags k that
 // is not finite and positive.  Each thread forms the west and south faces of
@@ -79,10 +88,10 @@ __global__ void __launch_bounds__(kAX * kAY) k_assemble(const double* __restrict
   const double an = j0 < ny - 1 ? fs[ty + 1][tx] : 0.0;
   // boundary faces, in the order west, east, south, north
   double bw = 0.0;
-  if (i0 == 0) bw = bw + 2.0 * kxc * f.aspect;
-  if (i0 == nx - 1) bw = bw + 2.0 * kxc * f.aspect;
-  if (j0 == 0) bw = bw + 2.0 * kyc * f.inv_aspect;
-  if (j0 == ny - 1) bw = bw + 2.0 * kyc * f.inv_aspect;
+  if (i0 == 0) bw = bw + boundary_face(2.0 * kxc * f.aspect, kxc, f.beta[0]);
+  if (i0 == nx - 1) bw = bw + boundary_face(2.0 * kxc * f.aspect, kxc, f.beta[1]);
+  if (j0 == 0) bw = bw + boundary_face(2.0 * kyc * f.inv_aspect, kyc, f.beta[2]);
+  if (j0 == ny - 1) bw = bw + boundary_face(2.0 * kyc * f.inv_aspect, kyc, f.beta[3]);
   const double c = (((aw + ae) + as) + an) + bw;
   const int o = (j0 + 1) * L.pitch + (i0 + 1);
   L.C[o] = T(c);
@@ -377,8 +386,9 @@ __global__ void k_assemble_backward(const double* __restrict__ k, const double* 
 
 template <typename T>
 int launch_assemble(const double* k, int nx, int ny, LevelV<T> L, double* kcopy, int* derr,
-                    bool log_k, double r, double aspect, cudaStream_t s) {
-  const AssemblyScale f{1.0 / r, r, aspect, 1.0 / aspect};
+                    bool log_k, double r, double aspect, const double* bc_beta, cudaStream_t s) {
+  const AssemblyScale f{1.0 / r, r, aspect, 1.0 / aspect,
+                        {bc_beta[0], bc_beta[1], bc_beta[2], bc_beta[3]}};
   k_assemble<T><<<dim3(cdiv(nx, kAX), cdiv(ny, kAY)), dim3(kAX, kAY), 0, s>>>(k, nx, ny, L, kcopy,
                                                                             derr, log_k, f);
   count_launch();
@@ -444,7 +454,7 @@ void launch_assemble_backward(const double* k, const double* u, const double* la
 }
 
 template int launch_assemble<double>(const double*, int, int, LevelV<double>, double*, int*,
-                                     bool, double, double, cudaStream_t);
+                                     bool, double, double, const double*, cudaStream_t);
 template int launch_interp_weights<double>(const LevelV<double>&, bool, int*, int, cudaStream_t);
 template int launch_interp_weights<float>(const LevelV<float>&, bool, int*, int, cudaStream_t);
 template int launch_rap<double>(const LevelV<double>&, bool, LevelV<double>, cudaStream_t);

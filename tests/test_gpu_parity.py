@@ -460,3 +460,44 @@ def test_general_sides_match_oracle(name):
     assert ro.converged and info.cycles == ro.cycles, (info.cycles, ro.cycles)
     assert abs(info.rel_resid - ro.rel_resid) <= 1e-13
     assert np.abs(x.cpu().numpy() - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+
+
+# ---------------------------------------------------------------------------
+# Neumann and Robin walls
+# ---------------------------------------------------------------------------
+
+BC_CASES = {
+    "blocks127x63_nnd_robin": (lambda: inputs.block_problem(seed=71, block=8, lo=-2, hi=2, nx=127, ny=63),
+                               (0.0, 0.0, None, 0.5)),
+    "even100x60_one_dirichlet": (lambda: inputs.block_problem(seed=72, block=8, lo=-1, hi=1, nx=100,
+                                                              ny=60),
+                                 (None, 0.0, 0.0, 0.0)),
+    "lognormal255_robin": (lambda: problem("lognormal255"), (0.1, 2.0, 0.0, None)),
+}
+
+
+@pytest.mark.parametrize("name", list(BC_CASES))
+def test_neumann_robin_walls_match_oracle(name):
+    make, bc = BC_CASES[name]
+    pr = make()
+    ho = O.setup(pr["k"], bc=bc)
+    hg = bm.setup(dev(pr["k"]), bm.default_options(bc_beta=bc, max_cycles=400))
+    L = ho.nlevels
+    sg = hg.level_stencil(L - 1)
+    so = ho.levels[L - 1].st
+    for d in ("C", "W", "S"):
+        assert np.array_equal(sg[d], so[d]), d
+    for l in range(L - 1):
+        assert rel_stencil_err(hg.level_stencil(l), ho.levels[l].st) <= 1e-12 * (L - 1 - l), l
+    ro = O.solve(ho, pr["b"], tol=1e-10, max_cycles=400)
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+    hg.destroy()
+    assert ro.converged and info.cycles == ro.cycles, (info.cycles, ro.cycles)
+    assert abs(info.rel_resid - ro.rel_resid) <= 1e-13
+    assert np.abs(x.cpu().numpy() - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+
+
+def test_all_neumann_walls_are_rejected():
+    with pytest.raises(bm.BoxMGError) as e:
+        bm.setup(dev(np.ones((31, 31))), bm.default_options(bc_beta=(0.0, 0.0, 0.0, 0.0)))
+    assert e.value.code == bm.BMG_EINVAL
