@@ -25,6 +25,12 @@ What it computes (Reisner, Olson, Moulton, "Scaling Structured Multigrid to
 * ``relax``          -- multicolour point Gauss-Seidel (Section 2, Section 3
   Eq. for T_smooth, Section 5): red-black on the 5-point finest level, four
   colours on 9-point coarse levels.
+* ``relax_lines``    -- zebra line Gauss-Seidel, alternating x- and y-lines
+  (Section 2 names alternating line smoothing as the smoother anisotropy
+  calls for; Section 7 leaves line smoothers to future work): every line of
+  one colour is solved exactly, its tridiagonal system built from the
+  couplings along the line and a right-hand side holding the current values
+  of the neighbouring lines.
 * ``residual``, restriction R = P^T, interpolate-and-correct -- Algorithm 1,
   with the optional r/C term of the interpolation equations in Section 3.
 * ``vcycle`` / ``solve`` -- Algorithm 1, iterated until the relative residual
@@ -55,6 +61,12 @@ Readings where the paper is silent (each is also listed in the design notes):
 * colour order: red = (i + j) even (1-based), first; four colours
   (i mod 2, j mod 2) in the order (1,1), (0,1), (1,0), (0,0).  Pre-smoothing
   runs the colours forward, post-smoothing in reverse.
+* line smoothing: zebra order, the odd lines (1-based) first; a line's
+  system is solved exactly (a banded solve).  "x-lines" are the rows (lines
+  along x, implicit in the W/E couplings), "y-lines" the columns.  The
+  alternating smoother runs x-lines then y-lines; post-smoothing runs the
+  reverse (y-lines then x-lines, each with the colours reversed), so the
+  V-cycle stays symmetric.  The smoother is used on every level.
 * residual norm: the Euclidean norm; the stop test is applied after each
   full cycle (and once before the first).
 * sizes: any nx, ny >= 2; a side of n points coarsens to floor(n / 2)
@@ -427,6 +439,70 @@ def relax(st: dict, x: np.ndarray, b: np.ndarray, nu: int, order,
 
 
 # ---------------------------------------------------------------------------
+# Zebra line Gauss-Seidel (Section 2: alternating line smoothing for
+# anisotropic problems)
+# ---------------------------------------------------------------------------
+
+# The couplings that stay implicit in a line's system, per line direction.
+LINE_DIRS = {"x": ("W", "E"), "y": ("S", "N")}
+SMOOTHERS = ("point", "x", "y", "xy")
+
+
+def line_colour(st: dict, x: np.ndarray, b: np.ndarray, direction: str,
+                colour: int) -> None:
+    """Solve every line of one colour exactly, in place.  ``colour`` 0 is
+    the odd lines (1-based), 0-based rows (x-lines) or columns (y-lines)
+    0, 2, 4, ...  Lines of one colour do not couple (the stencil reaches
+    one line over), so they are solved together as one banded system with
+    no coupling across the seams between lines."""
+    import scipy.linalg
+    if direction == "y":
+        stt = {"C": st["C"].T, "W": st["S"].T, "E": st["N"].T, "S": st["W"].T,
+               "N": st["E"].T, "SW": st["SW"].T, "NE": st["NE"].T,
+               "SE": st["NW"].T, "NW": st["SE"].T}
+        xt = x.T.copy()
+        line_colour(stt, xt, b.T, "x", colour)
+        x[:] = xt.T
+        return
+    ny, nx = x.shape
+    rows = slice(colour, None, 2)
+    xp = np.pad(x, 1)
+    rhs = b[rows, :].copy()
+    for d in DIRS:
+        if d in LINE_DIRS["x"]:
+            continue
+        rhs += st[d][rows, :] * shifted(xp, d, ny, nx, rows, slice(None))
+    n = rhs.size
+    ab = np.zeros((3, n))
+    ab[0, 1:] = -st["E"][rows, :].ravel()[:-1]   # A[k, k+1]; zero at a row's end
+    ab[1] = st["C"][rows, :].ravel()
+    ab[2, :-1] = -st["W"][rows, :].ravel()[1:]   # A[k+1, k]; zero at a row's start
+    x[rows, :] = scipy.linalg.solve_banded((1, 1), ab, rhs.ravel()).reshape(rhs.shape)
+
+
+def relax_lines(st: dict, x: np.ndarray, b: np.ndarray, nu: int, smoother: str,
+                reverse: bool = False) -> None:
+    """``nu`` line Gauss-Seidel sweeps in place: ``smoother`` "x", "y" or
+    "xy" (x-lines then y-lines).  Forward: each direction's colours 0 then
+    1; reverse: the whole sequence backwards."""
+    seq = [(d, c) for d in smoother for c in (0, 1)]
+    if reverse:
+        seq = seq[::-1]
+    for _ in range(nu):
+        for d, c in seq:
+            line_colour(st, x, b, d, c)
+
+
+def smooth(h, st: dict, x: np.ndarray, b: np.ndarray, nu: int, reverse: bool) -> None:
+    """The hierarchy's smoother: multicolour point Gauss-Seidel or line
+    Gauss-Seidel."""
+    if h.smoother == "point":
+        relax(st, x, b, nu, colour_order(st), reverse=reverse)
+    else:
+        relax_lines(st, x, b, nu, h.smoother, reverse=reverse)
+
+
+# ---------------------------------------------------------------------------
 # Hierarchy and V-cycle (Algorithm 1)
 # ---------------------------------------------------------------------------
 
@@ -447,6 +523,7 @@ class Hierarchy:
     nu1: int = 2
     nu2: int = 1
     interp_residual_term: bool = False
+    smoother: str = "point"        # "point", "x", "y" or "xy" (see smooth)
     stats: dict = field(default_factory=dict)
 
     @property
@@ -473,10 +550,13 @@ def level_shapes(nx: int, ny: int):
 
 def setup(k: np.ndarray, nu1: int = 2, nu2: int = 1,
           interp_residual_term: bool = False, r: float = 1.0, aspect: float = 1.0,
-          bc=None) -> Hierarchy:
+          bc=None, smoother: str = "point") -> Hierarchy:
     """BoxMG setup: assemble the fine operator (``r``, ``aspect``, ``bc`` as
     in assemble_fv5), then for each level build P_l from A_l and
-    A_{l-1} = P_l^T A_l P_l; factor A_0 (Section 2)."""
+    A_{l-1} = P_l^T A_l P_l; factor A_0 (Section 2).  ``smoother`` picks
+    point or line Gauss-Seidel (see smooth)."""
+    if smoother not in SMOOTHERS:
+        raise ValueError(f"smoother must be one of {SMOOTHERS}")
     ny, nx = k.shape
     shapes = level_shapes(nx, ny)
     if not np.all(np.isfinite(k)) or np.any(k <= 0):
@@ -494,7 +574,7 @@ def setup(k: np.ndarray, nu1: int = 2, nu2: int = 1,
     levels = fine_to_coarse[::-1]          # levels[0] coarsest
     a0 = stencil_to_csr(levels[0].st).toarray()
     return Hierarchy(levels=levels, chol=cholesky(a0), nu1=nu1, nu2=nu2,
-                     interp_residual_term=interp_residual_term)
+                     interp_residual_term=interp_residual_term, smoother=smoother)
 
 
 def vcycle(h: Hierarchy, x: np.ndarray, b: np.ndarray) -> None:
@@ -506,8 +586,7 @@ def vcycle(h: Hierarchy, x: np.ndarray, b: np.ndarray) -> None:
     xs[nl - 1], bs[nl - 1] = x, b
     for l in range(nl - 1, 0, -1):
         lev = h.levels[l]
-        order = colour_order(lev.st)
-        relax(lev.st, xs[l], bs[l], h.nu1, order)
+        smooth(h, lev.st, xs[l], bs[l], h.nu1, reverse=False)
         rs[l] = residual(lev.st, xs[l], bs[l])
         nyc, nxc = h.levels[l - 1].shape
         bs[l - 1] = (lev.p.T @ rs[l].ravel()).reshape(nyc, nxc)
@@ -523,8 +602,7 @@ def vcycle(h: Hierarchy, x: np.ndarray, b: np.ndarray) -> None:
             rc[1::2, 1::2] = 0.0
             corr = corr + rc
         xs[l] += corr
-        order = colour_order(lev.st)
-        relax(lev.st, xs[l], bs[l], h.nu2, order, reverse=True)
+        smooth(h, lev.st, xs[l], bs[l], h.nu2, reverse=True)
 
 
 @dataclass

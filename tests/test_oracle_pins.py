@@ -786,3 +786,153 @@ def test_vcycle_with_mixed_boundaries_converges_to_direct_solution(bc):
     xd = spla.spsolve(a, b.ravel()).reshape(31, 31)
     assert res.converged
     assert np.abs(res.x - xd).max() <= 1e-9 * np.abs(xd).max()
+
+
+# ---------------------------------------------------------------------------
+# Zebra line Gauss-Seidel (Section 2: alternating line smoothing for
+# anisotropic problems)
+# ---------------------------------------------------------------------------
+
+def _line_sets(nx, ny, direction, colour):
+    """Unknown indices (j * nx + i) of the lines of one colour."""
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    return (idx[colour::2, :] if direction == "x" else idx[:, colour::2]).ravel()
+
+
+def _dense_block_gs(st, x, b, smoother, reverse):
+    """Block Gauss-Seidel with the lines of one colour as one block, by dense
+    linear algebra: x_I = A_II^{-1} (b_I - A_I,rest x_rest)."""
+    ny, nx = x.shape
+    a = O.stencil_to_csr(st).toarray()
+    seq = [(d, c) for d in smoother for c in (0, 1)]
+    if reverse:
+        seq = seq[::-1]
+    xv, bv = x.ravel().copy(), b.ravel()
+    for d, c in seq:
+        idx = _line_sets(nx, ny, d, c)
+        rest = np.setdiff1d(np.arange(nx * ny), idx)
+        rhs = bv[idx] - a[np.ix_(idx, rest)] @ xv[rest]
+        xv[idx] = np.linalg.solve(a[np.ix_(idx, idx)], rhs)
+    return xv.reshape(ny, nx)
+
+
+@pytest.mark.parametrize("smoother", ["x", "y", "xy"])
+@pytest.mark.parametrize("nine_point", [False, True])
+def test_line_relaxation_is_dense_block_gauss_seidel(smoother, nine_point):
+    """One line sweep equals block Gauss-Seidel by dense solves, on a 5-point
+    fine operator and on a 9-point Galerkin level of a rectangular grid, in
+    both directions of traversal."""
+    rng = np.random.default_rng(40)
+    k = 10.0 ** rng.uniform(-2, 2, size=(13, 18))
+    h = O.setup(k, r=3.0, aspect=0.5)
+    st = h.levels[-2].st if nine_point else h.levels[-1].st
+    assert O.is_five_point(st) != nine_point
+    ny, nx = st["C"].shape
+    b = rng.uniform(-1, 1, (ny, nx))
+    x0 = rng.uniform(-1, 1, (ny, nx))
+    for reverse in (False, True):
+        x1 = x0.copy()
+        O.relax_lines(st, x1, b, 1, smoother, reverse=reverse)
+        x2 = _dense_block_gs(st, x0, b, smoother, reverse)
+        np.testing.assert_allclose(x1, x2, rtol=1e-12, atol=1e-13 * np.abs(x2).max())
+
+
+@pytest.mark.parametrize("direction", ["x", "y"])
+def test_line_relaxation_zeroes_the_residual_of_the_last_colour(direction):
+    """After a zebra sweep the equations of every line of the colour solved
+    last hold exactly; those of the first colour do not."""
+    rng = np.random.default_rng(41)
+    k = 10.0 ** rng.uniform(-3, 3, size=(16, 11))
+    st = O.setup(k).levels[-2].st
+    ny, nx = st["C"].shape
+    b = rng.uniform(-1, 1, (ny, nx))
+    x = rng.uniform(-1, 1, (ny, nx))
+    O.relax_lines(st, x, b, 1, direction)
+    r = O.residual(st, x, b)
+    last = (slice(1, None, 2), slice(None)) if direction == "x" else (slice(None), slice(1, None, 2))
+    first = (slice(0, None, 2), slice(None)) if direction == "x" else (slice(None), slice(0, None, 2))
+    assert np.abs(r[last]).max() <= 1e-13 * np.abs(b).max() * 10
+    assert np.abs(r[first]).max() > 1e-3
+
+
+def test_line_relaxation_solves_decoupled_lines_exactly():
+    """With no coupling between rows one x-line sweep is an exact solve (a
+    set of independent 1D problems); a y-line sweep of the transposed
+    problem likewise."""
+    rng = np.random.default_rng(42)
+    ny, nx = 6, 9
+    a = rng.uniform(0.5, 2.0, (ny, nx + 1))
+    st = {d: np.zeros((ny, nx)) for d in ("C",) + O.DIRS}
+    st["W"][:, 1:] = a[:, 1:nx]
+    st["E"][:, :-1] = a[:, 1:nx]
+    st["C"] = st["W"] + st["E"] + a[:, :nx] * 0.5 + 0.1
+    b = rng.uniform(-1, 1, (ny, nx))
+    xd = spla.spsolve(O.stencil_to_csr(st).tocsc(), b.ravel()).reshape(ny, nx)
+    x = rng.uniform(-1, 1, (ny, nx))
+    O.relax_lines(st, x, b, 1, "x")
+    np.testing.assert_allclose(x, xd, rtol=1e-13, atol=1e-14)
+    stt = {"C": st["C"].T, "S": st["W"].T, "N": st["E"].T, "W": st["S"].T, "E": st["N"].T,
+           "SW": st["SW"].T, "NE": st["NE"].T, "SE": st["NW"].T, "NW": st["SE"].T}
+    xt = rng.uniform(-1, 1, (nx, ny))
+    O.relax_lines(stt, xt, b.T.copy(), 1, "y")
+    np.testing.assert_allclose(xt, xd.T, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("r", [0.01, 100.0])
+def test_line_smoothing_in_the_strong_direction_restores_convergence(r):
+    """D = diag(1/r, r) on square cells: with r = 0.01 the x couplings are
+    10^4 times the y couplings.  Point Gauss-Seidel with full coarsening
+    stalls; lines along the strong direction (and alternating lines) give
+    the textbook rate; lines across it stall like points."""
+    rng = np.random.default_rng(43)
+    n = 63
+    b = rng.uniform(-1, 1, (n, n))
+    k = np.ones((n, n))
+    strong, weak = ("x", "y") if r < 1 else ("y", "x")
+    cycles = {}
+    for sm in O.SMOOTHERS:
+        res = O.solve(O.setup(k, nu1=1, nu2=1, r=r, smoother=sm), b, tol=1e-10, max_cycles=60)
+        cycles[sm] = res.cycles if res.converged else None
+    assert cycles[strong] is not None and cycles[strong] <= 8
+    assert cycles["xy"] is not None and cycles["xy"] <= 8
+    assert cycles["point"] is None and cycles[weak] is None
+
+
+def test_line_smoothed_preconditioner_is_symmetric_and_pcg_converges():
+    """With nu1 = nu2 the post-smoothing runs the pre-smoothing's lines in
+    reverse, so the V-cycle is a symmetric preconditioner; PCG with it
+    reaches the direct solution."""
+    pr = _block_field(31, 14)
+    rng = np.random.default_rng(44)
+    u, w = rng.normal(size=(31, 31)), rng.normal(size=(31, 31))
+    h = O.setup(pr["k"], nu1=1, nu2=1, r=4.0, smoother="xy")
+    mu, mw = O.vcycle_precond(h, u), O.vcycle_precond(h, w)
+    scale = np.linalg.norm(u) * np.linalg.norm(mw)
+    assert abs(np.sum(mu * w) - np.sum(u * mw)) <= 1e-13 * scale
+    assert np.sum(mu * u) > 0
+    res = O.pcg(h, pr["b"], tol=1e-12)
+    xd = spla.spsolve(O.stencil_to_csr(O.assemble_fv5(pr["k"], r=4.0)).tocsc(),
+                      pr["b"].ravel()).reshape(31, 31)
+    assert res.converged
+    assert np.abs(res.x - xd).max() <= 1e-9 * np.abs(xd).max()
+
+
+def test_line_smoothed_vcycle_on_general_sides_and_robin_walls():
+    """Line smoothing on even sides with Robin and Neumann walls reaches the
+    direct solution."""
+    rng = np.random.default_rng(45)
+    nx, ny = 20, 14
+    k = 10.0 ** rng.uniform(-1, 1, (ny, nx))
+    b = rng.uniform(-1, 1, (ny, nx))
+    bc = (0.0, 2.0, None, 0.5)
+    h = O.setup(k, r=0.2, aspect=2.0, bc=bc, smoother="xy")
+    res = O.solve(h, b, tol=1e-12)
+    xd = spla.spsolve(O.stencil_to_csr(O.assemble_fv5(k, 0.2, 2.0, bc)).tocsc(),
+                      b.ravel()).reshape(ny, nx)
+    assert res.converged
+    assert np.abs(res.x - xd).max() <= 1e-9 * np.abs(xd).max()
+
+
+def test_bad_smoother_rejected():
+    with pytest.raises(ValueError):
+        O.setup(np.ones((7, 7)), smoother="z")
