@@ -295,6 +295,7 @@ def run_ours(args, rank, world, local_rank):
         extra["paper_workload"] = paper_workload_leg(bm, torch, dev, stream)
         # the paper's global grid as it is (9088 x 568, aspect 16), r = 16
         extra["paper_workload_9088x568"] = paper_workload_leg(bm, torch, dev, stream, nx=9088, ny=568)
+        extra["line_smoother"] = line_smoother_leg(bm, torch, dev, stream, load_peaks()[0])
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.quick:
@@ -454,6 +455,85 @@ def paper_workload_leg(bm, torch, dev, stream, nx=16383, ny=1023, r=16.0):
         ms = sum(times) / len(times)
         out[name] = {"value": nx * ny / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms,
                      "cycles": info.cycles, "rel_resid": info.rel_resid}
+    return out
+
+
+# Algorithmic bytes per fine unknown of one zebra line sweep in one direction
+# (both colours), FP64 5-point: right-hand sides (b, the two off-line
+# couplings, the two neighbouring lines' x, write the scratch: 48), block
+# substitution (scratch read and write, three factors: 40), final update
+# (scratch, two spikes, write x: 32).
+LINE_BYTES_PER_UNKNOWN_DIR = 120.0
+
+
+def line_smoother_leg(bm, torch, dev, stream, peaks, n=4095, r=100.0):
+    """Zebra line smoothing where point smoothing stalls: D = diag(1/r, r),
+    r = 100, on n x n square cells (y couplings 10^4 times the x couplings),
+    k = 1, b uniform[-1, 1] (seed 9), to 1e-10.  Point V(2,1) (capped at 60
+    cycles), y-line and alternating-line V(2,1) in FP64, alternating lines in
+    FP32 refinement, and PCG with the alternating-line V(1,1) cycle
+    (setup + solve timed); then the fine-level line sweep alone, timed with
+    CUDA events, against its algorithmic bytes."""
+    k = torch.ones((n, n), dtype=torch.float64, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(9)
+    b = torch.rand((n, n), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+    out = {"workload": f"D = diag(1/{r:g}, {r:g}), {n}x{n} square cells, k = 1, tol 1e-10"}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    variants = (("fp64_point", dict(max_cycles=60)),
+                ("fp64_yline", dict(smoother=bm.BMG_SMOOTH_YLINE)),
+                ("fp64_altline", dict(smoother=bm.BMG_SMOOTH_ALTLINE)),
+                ("fp32_refine_altline", dict(smoother=bm.BMG_SMOOTH_ALTLINE,
+                                             precision=bm.BMG_FP32_REFINE)),
+                ("fp64_pcg_altline_v11", dict(smoother=bm.BMG_SMOOTH_ALTLINE, nu1=1, nu2=1,
+                                              solver=bm.BMG_SOLVER_PCG)))
+    for name, kw in variants:
+        opts = bm.default_options(aniso_r=r, **dict(dict(max_cycles=200), **kw))
+        x = torch.zeros_like(b)
+        times = []
+        info = None
+        for rep in range(3):
+            x.zero_()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            h = bm.setup(k, opts, stream=stream)
+            try:
+                _, info = h.solve(b, x, tol=1e-10, stream=stream)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+            except bm.BoxMGError as e:
+                if e.code != bm.BMG_ENOCONV:
+                    raise
+                torch.cuda.synchronize()
+                out[name] = {"converged": False, "cycles": opts.max_cycles,
+                             "rel_resid": h.residual_history()[-1]}
+                h.destroy()
+                break
+            h.destroy()
+            if rep:
+                times.append(ev0.elapsed_time(ev1))
+        if name in out:
+            continue
+        ms = sum(times) / len(times)
+        out[name] = {"value": n * n / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms,
+                     "cycles": info.cycles, "rel_resid": info.rel_resid}
+    # the fine-level sweep alone (FP64, alternating: both directions)
+    h = bm.setup(k, bm.default_options(aniso_r=r, smoother=bm.BMG_SMOOTH_ALTLINE), stream=stream)
+    x = torch.zeros_like(b)
+    h.solve(b, x, tol=1e-10, stream=stream)
+    bm.profile_set(("fine_smooth",))
+    x.zero_()
+    _, info = h.solve(b, x, tol=1e-10, stream=stream)
+    torch.cuda.synchronize()
+    cnt, sms = bm.profile_read("fine_smooth")
+    bm.profile_set(())
+    h.destroy()
+    per = sms / max(cnt, 1)
+    gbs = 2 * LINE_BYTES_PER_UNKNOWN_DIR * n * n / (per * 1e-3) / 1e9
+    out["fine_altline_sweep"] = {"ms_per_sweep": per, "sweeps": cnt,
+                                 "algorithmic_bytes_per_unknown": 2 * LINE_BYTES_PER_UNKNOWN_DIR,
+                                 "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]}
     return out
 
 

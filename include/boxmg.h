@@ -66,6 +66,15 @@ enum { BMG_FP64 = 0, BMG_FP32_REFINE = 1 };
  * positive definite preconditioner. */
 enum { BMG_SOLVER_VCYCLE = 0, BMG_SOLVER_PCG = 1 };
 
+/* Smoothers: multicolour point Gauss-Seidel (red-black on the 5-point finest
+ * level, four colours on the 9-point levels; the paper's smoother), or zebra
+ * line Gauss-Seidel along x (every row solved exactly, odd rows first), along
+ * y (the columns), or alternating (x-lines then y-lines) -- Section 2's
+ * alternating line smoothing for anisotropic problems.  Line smoothers run on
+ * every level; post-smoothing takes the steps in reverse order, so with
+ * nu1 == nu2 the cycle stays symmetric. */
+enum { BMG_SMOOTH_POINT = 0, BMG_SMOOTH_XLINE = 1, BMG_SMOOTH_YLINE = 2, BMG_SMOOTH_ALTLINE = 3 };
+
 #define BMG_MAX_COARSEST 1024
 
 typedef struct {
@@ -93,6 +102,9 @@ typedef struct {
                                beta = alpha times the cell width normal to
                                that wall (0: Neumann, no flux).  Not all four
                                may be Neumann (the operator would be singular) */
+  int smoother;             /* BMG_SMOOTH_* (default BMG_SMOOTH_POINT); line
+                               smoothers are not available to the batched
+                               solver                                         */
 } bmg_options;
 
 typedef struct {

@@ -23,6 +23,7 @@ __all__ = [
 BMG_OK, BMG_EINVAL, BMG_ENOMEM, BMG_ECUDA, BMG_ENOCONV, BMG_ENAN, BMG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 BMG_FP64, BMG_FP32_REFINE = 0, 1
 BMG_SOLVER_VCYCLE, BMG_SOLVER_PCG = 0, 1
+BMG_SMOOTH_POINT, BMG_SMOOTH_XLINE, BMG_SMOOTH_YLINE, BMG_SMOOTH_ALTLINE = 0, 1, 2, 3
 MAX_COARSEST = 1024
 
 
@@ -31,7 +32,8 @@ class Options(ctypes.Structure):
                 ("interp_residual_term", ctypes.c_int), ("coarse_threshold", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("log_coefficients", ctypes.c_int),
                 ("solver", ctypes.c_int), ("aniso_r", ctypes.c_double),
-                ("cell_aspect", ctypes.c_double), ("bc_beta", ctypes.c_double * 4)]
+                ("cell_aspect", ctypes.c_double), ("bc_beta", ctypes.c_double * 4),
+                ("smoother", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -68,7 +68,9 @@ struct Carver {
 
 template <typename T>
 void carve_levels(Carver& cv, const std::vector<Geom>& geo, int first, std::vector<LevelV<T>>& lv,
-                  int finest_index) {
+                  int finest_index, int smoother) {
+  const bool xl = smoother == BMG_SMOOTH_XLINE || smoother == BMG_SMOOTH_ALTLINE;
+  const bool yl = smoother == BMG_SMOOTH_YLINE || smoother == BMG_SMOOTH_ALTLINE;
   // lv[i] corresponds to hierarchy level first + i.
   const int n = int(geo.size());
   lv.assign(n, LevelV<T>{});
@@ -90,6 +92,8 @@ void carve_levels(Carver& cv, const std::vector<Geom>& geo, int first, std::vect
     L.x2 = cv.plane<T>(g);
     L.b = cv.plane<T>(g);
     L.r = cv.plane<T>(g);
+    for (int d = 0; d < 2; ++d)
+      for (int k = 0; k < NLF; ++k) L.LF[d][k] = (d == 0 ? xl : yl) ? cv.plane<T>(g) : nullptr;
     if (l >= 1 && i >= 1) {
       const Geom& gc = geo[i - 1];
       for (int k = 0; k < NPW; ++k) L.P[k] = cv.plane<T>(gc);
@@ -129,6 +133,10 @@ static int check_derr(Hierarchy* h, cudaStream_t s) {
     set_last_error("setup: coarsest operator is not positive definite");
     return BMG_EINVAL;
   }
+  if (e & DEV_BADLINE) {
+    set_last_error("setup: a line system of the line smoother has a non-positive pivot");
+    return BMG_EINVAL;
+  }
   return BMG_OK;
 }
 
@@ -141,6 +149,10 @@ static int build_coarse(Hierarchy* h, std::vector<LevelV<T>>& lv, cudaStream_t s
     if (launch_interp_weights<T>(lv[l], nine, derr, l, s)) return BMG_ECUDA;
     if (launch_rap<T>(lv[l], nine, lv[l - 1], s)) return BMG_ECUDA;
   }
+  // line factors of every level the smoother visits (all but the coarsest)
+  if (h->opt.smoother != BMG_SMOOTH_POINT)
+    for (int l = L - 1; l >= 1; --l)
+      if (launch_line_factor<T>(lv[l], h->opt.smoother, derr, s)) return BMG_ECUDA;
   return BMG_OK;
 }
 
@@ -166,6 +178,10 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   if (opt.nu1 < 0 || opt.nu2 < 0 || opt.nu1 + opt.nu2 < 1 || opt.max_cycles < 0) return BMG_EINVAL;
   if (opt.precision != BMG_FP64 && opt.precision != BMG_FP32_REFINE) return BMG_EINVAL;
   if (opt.solver != BMG_SOLVER_VCYCLE && opt.solver != BMG_SOLVER_PCG) return BMG_EINVAL;
+  if (opt.smoother < BMG_SMOOTH_POINT || opt.smoother > BMG_SMOOTH_ALTLINE) {
+    set_last_error("smoother must be one of BMG_SMOOTH_*");
+    return BMG_EINVAL;
+  }
   if (!(opt.aniso_r > 0.0 && opt.aniso_r < INFINITY && opt.cell_aspect > 0.0 &&
         opt.cell_aspect < INFINITY)) {
     set_last_error("aniso_r and cell_aspect must be finite and positive");
@@ -234,8 +250,9 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   Carver cv;
   for (int pass = 0; pass < 2; ++pass) {
     cv.off = 0;
-    carve_levels<double>(cv, g64, fp32 ? L - 1 : 0, h->d, L - 1);
-    if (fp32) carve_levels<float>(cv, h->geo32, 0, h->f, L - 1);
+    carve_levels<double>(cv, g64, fp32 ? L - 1 : 0, h->d, L - 1,
+                         fp32 ? BMG_SMOOTH_POINT : opt.smoother);
+    if (fp32) carve_levels<float>(cv, h->geo32, 0, h->f, L - 1, opt.smoother);
     h->kcopy = cv.raw<double>(size_t(nx) * ny);
     h->chol = cv.raw<double>(size_t(h->n0) * h->n0);
     h->chol_idiag = cv.raw<double>(h->n0);
@@ -353,7 +370,10 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
     LevelV<T>& V = lv[l];
     const bool nine = l != L - 1;
     if (!nine) prof_begin(BMG_PROF_FINE_SMOOTH, s);
-    launch_sweep<T>(V, nine, reverse, V.x, V.x2, s, level_maps<T>(h, l));
+    if (h->opt.smoother != BMG_SMOOTH_POINT)
+      launch_line_sweep<T>(V, nine, h->opt.smoother, reverse, V.x, V.x2, s);
+    else
+      launch_sweep<T>(V, nine, reverse, V.x, V.x2, s, level_maps<T>(h, l));
     if (!nine) prof_end(BMG_PROF_FINE_SMOOTH, s);
     std::swap(V.x, V.x2);
   };
@@ -619,6 +639,7 @@ void bmg_default_options(bmg_options* opt) {
   opt->interp_residual_term = 0;
   opt->coarse_threshold = -1;
   opt->max_cycles = 200;
+  opt->smoother = BMG_SMOOTH_POINT;
   opt->log_coefficients = 0;
   opt->solver = BMG_SOLVER_VCYCLE;
   opt->aniso_r = 1.0;
@@ -828,8 +849,11 @@ int bmg_op_relax(bmg_hierarchy* hp, int level, double* x, const double* b, int n
   bmg::launch_pack<double>(b, L.b, L.nx, L.ny, L.pitch, s);
   const bool fine = level == h->L - 1;
   for (int k = 0; k < nu; ++k) {
-    bmg::launch_sweep<double>(L, !fine, reverse != 0, L.x, L.x2, s,
-                              bmg::level_maps<double>(h, level));
+    if (h->opt.smoother != BMG_SMOOTH_POINT)
+      bmg::launch_line_sweep<double>(L, !fine, h->opt.smoother, reverse != 0, L.x, L.x2, s);
+    else
+      bmg::launch_sweep<double>(L, !fine, reverse != 0, L.x, L.x2, s,
+                                bmg::level_maps<double>(h, level));
     std::swap(L.x, L.x2);
   }
   bmg::launch_unpack<double>(L.x, x, L.nx, L.ny, L.pitch, s);

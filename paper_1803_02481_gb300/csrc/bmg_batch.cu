@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(1024) k_bcoarse(const BCoarse* __restrict__ pc
   a.nu1 = nu1;
   a.nu2 = nu2;
   a.add_rc = 0;
+  a.smoother = BMG_SMOOTH_POINT;
   a.top_nine = q.top_nine;
   a.chol = q.chol;
   a.idiag = q.idiag;
@@ -567,6 +568,10 @@ extern "C" int bmg_batch_setup(int nprob, const double* const* k_dev, const int*
   bmg_options opt;
   bmg_default_options(&opt);
   if (opt_in) opt = *opt_in;
+  if (opt.smoother != BMG_SMOOTH_POINT) {
+    set_last_error("batch setup: only the point smoother is batched");
+    return BMG_EINVAL;
+  }
   opt.precision = BMG_FP32_REFINE;
   Batch* b = new Batch();
   b->nprob = nprob;

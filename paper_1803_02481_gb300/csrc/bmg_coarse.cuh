@@ -7,7 +7,7 @@
 // kernel and the batched kernel (one block per problem).
 #pragma once
 
-#include "bmg_internal.h"
+#include "bmg_line.cuh"
 
 namespace bmg {
 
@@ -24,6 +24,7 @@ struct CoarseArgs {
   const LevelV<T>* lev;      // device array of level views
   int thr;                   // levels 0 .. thr-1 run here
   int nu1, nu2, add_rc;
+  int smoother;              // BMG_SMOOTH_*
   int top_nine;              // is level thr-1 9-point (else red-black)
   const double* chol;        // N0 x N0 lower factor
   const double* idiag;       // 1 / L[i][i]
@@ -50,8 +51,14 @@ __device__ void blk_colour(const LevelV<T>& L, unsigned mask) {
   __syncthreads();
 }
 
-template <typename T, bool NINE>
-__device__ void blk_relax(const LevelV<T>& L, int nu, bool reverse) {
+// LINE: the line smoother of a.smoother (compiled into its own kernel, so the
+// point-smoother kernel keeps its registers).
+template <typename T, bool NINE, bool LINE>
+__device__ void blk_relax(const LevelV<T>& L, int nu, bool reverse, int smoother) {
+  if constexpr (LINE) {
+    blk_line_relax<T, NINE>(L, nu, reverse, smoother);
+    return;
+  }
   const int nc = NINE ? 4 : 2;
   for (int s = 0; s < nu; ++s) {
     for (int k = 0; k < nc; ++k) {
@@ -140,16 +147,16 @@ __device__ void blk_coarse_solve(const LevelV<T>& L0, const double* __restrict__
   __syncthreads();
 }
 
-template <typename T>
+template <typename T, bool LINE = false>
 __device__ void coarse_cycle_body(const CoarseArgs<T>& a) {
   for (int l = a.thr - 1; l >= 1; --l) {
     const LevelV<T> L = a.lev[l];
     const bool nine = (l < a.thr - 1) || a.top_nine;
     if (nine) {
-      blk_relax<T, true>(L, a.nu1, false);
+      blk_relax<T, true, LINE>(L, a.nu1, false, a.smoother);
       blk_residual<T, true>(L);
     } else {
-      blk_relax<T, false>(L, a.nu1, false);
+      blk_relax<T, false, LINE>(L, a.nu1, false, a.smoother);
       blk_residual<T, false>(L);
     }
     blk_restrict<T>(L, a.lev[l - 1]);
@@ -160,9 +167,9 @@ __device__ void coarse_cycle_body(const CoarseArgs<T>& a) {
     const bool nine = (l < a.thr - 1) || a.top_nine;
     blk_interp<T>(L, a.lev[l - 1].x, a.add_rc);
     if (nine)
-      blk_relax<T, true>(L, a.nu2, true);
+      blk_relax<T, true, LINE>(L, a.nu2, true, a.smoother);
     else
-      blk_relax<T, false>(L, a.nu2, true);
+      blk_relax<T, false, LINE>(L, a.nu2, true, a.smoother);
   }
 }
 

@@ -70,6 +70,13 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
   coarse_cycle_body<T>(a);
 }
 
+// The same with line smoothing; fewer threads leave each more registers for
+// a block's substitution.
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_coarse_cycle_line(CoarseArgs<T> a) {
+  coarse_cycle_body<T, true>(a);
+}
+
 // ---------------------------------------------------------------------------
 // Norms and the stop test.  Fixed grid, fixed per-thread order and a fixed
 // reduction tree, so the result is deterministic.
@@ -251,12 +258,16 @@ void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* dev_levels, int thr, cud
   a.nu1 = h->opt.nu1;
   a.nu2 = h->opt.nu2;
   a.add_rc = h->opt.interp_residual_term;
+  a.smoother = h->opt.smoother;
   a.top_nine = (thr < h->L) ? 1 : 0;
   a.chol = h->chol;
   a.idiag = h->chol_idiag;
   a.n0 = h->n0;
   prof_begin(BMG_PROF_COARSE, s);
-  k_coarse_cycle<T><<<1, 1024, 0, s>>>(a);
+  if (a.smoother != BMG_SMOOTH_POINT)
+    k_coarse_cycle_line<T><<<1, 512, 0, s>>>(a);
+  else
+    k_coarse_cycle<T><<<1, 1024, 0, s>>>(a);
   prof_end(BMG_PROF_COARSE, s);
   count_launch();
 }

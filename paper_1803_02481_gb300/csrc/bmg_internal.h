@@ -68,15 +68,26 @@ inline Geom make_geom(int nx, int ny) {
 template <typename T>
 constexpr int base_shift() { return int(128 / sizeof(T)) - 1; }
 
+// Line smoothing (bmg_line.cuh): points per block of a line (kLineM - 1
+// interior points and one separator), and the planes of precomputed factors
+// per line direction: block LU forward multiplier, reciprocal pivot and
+// back-substitution coefficient (at separators: those of the Schur system),
+// and the two spikes.
+constexpr int kLineM = 16;
+enum { LF_MU = 0, LF_IU, LF_CA, LF_V, LF_W, NLF };
+
 // Device view of one level.  Pointers are plane bases (element (0,0) is the
 // lower-left ghost).  SW/NW are null on a 5-point level.  P holds the
 // interpolation INTO this level from the next coarser one (null on level 0).
+// LF[d] holds the line factors of direction d (0: x-lines, 1: y-lines), null
+// unless the smoother uses that direction.
 template <typename T>
 struct LevelV {
   int nx, ny, pitch;
   T *C, *iC, *W, *S, *SW, *NW;
   T *x, *b, *r;
   T *x2;               // second iterate buffer (sweeps write out of place)
+  T *LF[2][NLF];
   T *P[NPW];
   int cpitch;          // pitch of the coarse grid the P planes live on
 };
@@ -220,7 +231,7 @@ __device__ __forceinline__ T interp_value(T* const* P, int cp, const T* __restri
 // Bits 8.. of the error word name the levels whose interpolation met a
 // non-positive denominator (bit 8 + l for P_l).
 enum DevErr { DEV_OK = 0, DEV_BADK = 1, DEV_NOTSPD = 2, DEV_BADDEN = 4, DEV_NAN = 8,
-              DEV_TIMEOUT = 16 };
+              DEV_TIMEOUT = 16, DEV_BADLINE = 32 };
 
 // Thread-local detail message of the last failure (bmg_last_error).
 void set_last_error(const char* fmt, ...);
@@ -354,6 +365,17 @@ void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* 
 template <typename T>
 void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* levels, int threshold,
                          cudaStream_t s);
+
+// Line smoothing (bmg_line.cu).  factor: the block LU factors, spikes and
+// Schur factors of every line of the directions `smoother` uses (setup; a
+// non-positive pivot sets DEV_BADLINE).  sweep: one line Gauss-Seidel sweep
+// (every step of line_steps), reading the iterate from xin and leaving the
+// swept iterate in xout (xin == xout allowed); uses L.r as scratch.
+template <typename T>
+int launch_line_factor(const LevelV<T>& L, int smoother, int* derr, cudaStream_t s);
+template <typename T>
+void launch_line_sweep(const LevelV<T>& L, bool nine, int smoother, bool reverse, const T* xin,
+                       T* xout, cudaStream_t s);
 
 // ||b - A x||^2 (or ||b||^2 when x == nullptr) of the finest FP64 level into
 // sc->rnorm2 / sc->bnorm2; then updates rel/go.  `what`: 0 = b norm, 1 =

@@ -501,3 +501,173 @@ def test_all_neumann_walls_are_rejected():
     with pytest.raises(bm.BoxMGError) as e:
         bm.setup(dev(np.ones((31, 31))), bm.default_options(bc_beta=(0.0, 0.0, 0.0, 0.0)))
     assert e.value.code == bm.BMG_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# Zebra line Gauss-Seidel smoothers (x-lines, y-lines, alternating)
+# ---------------------------------------------------------------------------
+
+SMOOTHER_CODES = {"x": bm.BMG_SMOOTH_XLINE, "y": bm.BMG_SMOOTH_YLINE, "xy": bm.BMG_SMOOTH_ALTLINE}
+
+LINE_RELAX_CASES = {
+    # 2^m - 1 sides: 255-point lines, 15 full blocks and a ragged 16th
+    "blocks255": lambda: dict(problem("blocks255"), r=1.0, aspect=1.0),
+    # sides that are multiples of 16 (a separator ends every line) down to 16
+    "pow2_256x256": lambda: dict(general_case("pow2_256x256")),
+    # even, ragged sides on stretched anisotropic cells
+    "even100x60_r4": lambda: dict(inputs.block_problem(seed=81, block=8, lo=-2, hi=2, nx=100, ny=60),
+                                  r=4.0, aspect=0.5),
+}
+
+
+@pytest.mark.parametrize("smoother", list(SMOOTHER_CODES))
+@pytest.mark.parametrize("name", list(LINE_RELAX_CASES))
+def test_line_relaxation_matches_oracle(name, smoother):
+    """Two line sweeps forward and two reversed, on the 5-point finest level
+    and on 9-point levels with and without separators, against the oracle's
+    banded solves.  Each line is solved exactly by both sides (different
+    elimination orders), so the iterates agree to rounding: 1e-11 of max|x|."""
+    pr = LINE_RELAX_CASES[name]()
+    ho = O.setup(pr["k"], r=pr["r"], aspect=pr["aspect"], smoother=smoother)
+    hg = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=pr["r"], cell_aspect=pr["aspect"],
+                                                   smoother=SMOOTHER_CODES[smoother]))
+    rng = np.random.default_rng(82)
+    L = ho.nlevels
+    for l in sorted({L - 1, L - 2, L - 3, 1}):
+        st = nine_from_five(hg.level_stencil(l)) if l < L - 1 else ho.levels[l].st
+        ny, nx = st["C"].shape
+        x = rng.uniform(-1, 1, (ny, nx))
+        b = rng.uniform(-1, 1, (ny, nx))
+        for rev in (False, True):
+            xg = hg.op_relax(l, dev(x), dev(b), nu=2, reverse=rev).cpu().numpy()
+            xo = x.copy()
+            O.relax_lines(st, xo, b, 2, smoother, reverse=rev)
+            assert np.abs(xg - xo).max() <= 1e-11 * max(1.0, np.abs(xo).max()), (l, rev)
+    hg.destroy()
+
+
+LINE_SOLVE_CASES = {
+    # D = diag(1/r, r) on square cells: r = 0.01 couples x 10^4 times more
+    # strongly than y, r = 100 the reverse; point smoothing stalls on both
+    "strong_x127": (lambda: {"k": np.ones((127, 127)),
+                             "b": np.random.default_rng(83).uniform(-1, 1, (127, 127)),
+                             "r": 0.01, "aspect": 1.0}, "x"),
+    "strong_y127_alt": (lambda: {"k": np.ones((127, 127)),
+                                 "b": np.random.default_rng(84).uniform(-1, 1, (127, 127)),
+                                 "r": 100.0, "aspect": 1.0}, "xy"),
+    "strong_y127": (lambda: {"k": np.ones((127, 127)),
+                             "b": np.random.default_rng(84).uniform(-1, 1, (127, 127)),
+                             "r": 100.0, "aspect": 1.0}, "y"),
+    # a heterogeneous block field with anisotropy, alternating lines
+    "blocks255_r8_alt": (lambda: dict(problem("blocks255"), r=8.0, aspect=1.0), "xy"),
+    # the paper's workload (compensated anisotropy on 16:1 cells), long lines
+    "paper1023x63_alt": (lambda: dict(aniso_case("paper1023x63")), "xy"),
+    # general sides, lines ending on separators
+    "pow2_256_alt": (lambda: dict(general_case("pow2_256x256")), "xy"),
+}
+
+
+@pytest.mark.parametrize("name", list(LINE_SOLVE_CASES))
+def test_line_smoothed_solve_matches_oracle(name):
+    """Identical cycle counts and iterates within 1e-9 of max|x|.  The final
+    relative residuals differ by at most ||A (x_gpu - x_oracle)|| / ||b||
+    (triangle inequality) plus the rounding of their evaluation, and by at
+    most 1e-11: unlike the point smoother, the two sides eliminate each
+    line in a different order (blocks and separators against a banded LU),
+    so the iterates carry rounding differences of order eps times the line
+    systems' condition, which a 10^4-contrast field amplifies in the
+    residual of a slowly converging solve (a CPU run of the oracle with the
+    block/separator elimination moves the final residual of blocks255 with
+    r = 8 by 5e-13)."""
+    make, smoother = LINE_SOLVE_CASES[name]
+    pr = make()
+    ho = O.setup(pr["k"], r=pr["r"], aspect=pr["aspect"], smoother=smoother)
+    hg = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=pr["r"], cell_aspect=pr["aspect"],
+                                                   smoother=SMOOTHER_CODES[smoother],
+                                                   max_cycles=200))
+    ro = O.solve(ho, pr["b"], tol=1e-10, max_cycles=200)
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+    hg.destroy()
+    xg = x.cpu().numpy()
+    assert ro.converged and info.cycles == ro.cycles, (info.cycles, ro.cycles)
+    assert info.rel_resid <= 1e-10
+    st = ho.levels[-1].st
+    dres = np.linalg.norm(O.apply(st, xg - ro.x)) / np.linalg.norm(pr["b"])
+    assert abs(info.rel_resid - ro.rel_resid) <= dres + 1e-13
+    assert abs(info.rel_resid - ro.rel_resid) <= 1e-11
+    assert np.abs(xg - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+
+
+def test_line_smoothing_restores_convergence_on_the_gpu():
+    """Strong x coupling on square cells: point smoothing does not reach
+    1e-10 in 100 cycles, x-line smoothing needs a handful."""
+    pr = LINE_SOLVE_CASES["strong_x127"][0]()
+    hp = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=pr["r"], max_cycles=100))
+    with pytest.raises(bm.BoxMGError) as e:
+        hp.solve(dev(pr["b"]), tol=1e-10)
+    assert e.value.code == bm.BMG_ENOCONV
+    hp.destroy()
+    hl = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=pr["r"], smoother=bm.BMG_SMOOTH_XLINE))
+    _, info = hl.solve(dev(pr["b"]), tol=1e-10)
+    hl.destroy()
+    assert info.cycles <= 8
+
+
+@pytest.mark.parametrize("name", ["blocks255_r8_alt", "paper1023x63_alt"])
+def test_line_smoother_every_threshold_gives_identical_iterates(name):
+    """The persistent coarse kernel smooths its levels with the same per-line
+    arithmetic as the full-grid kernels: bit-identical for every threshold."""
+    make, smoother = LINE_SOLVE_CASES[name]
+    pr = make()
+    ref = None
+    hg0 = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=pr["r"], cell_aspect=pr["aspect"],
+                                                    smoother=SMOOTHER_CODES[smoother]))
+    L = hg0.nlevels
+    hg0.destroy()
+    for thr in range(1, L + 1):
+        hg = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=pr["r"], cell_aspect=pr["aspect"],
+                                                       smoother=SMOOTHER_CODES[smoother],
+                                                       coarse_threshold=thr))
+        x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+        hg.destroy()
+        assert info.threshold == thr
+        xn = x.cpu().numpy()
+        if ref is None:
+            ref = (xn, info.cycles, info.rel_resid)
+        else:
+            assert np.array_equal(xn, ref[0]), thr
+            assert info.cycles == ref[1] and info.rel_resid == ref[2]
+
+
+def test_line_smoothed_pcg_and_fp32_refinement():
+    """PCG with the symmetric alternating-line V(1,1) cycle matches the
+    oracle's PCG; FP32 refinement with line smoothing reaches the FP64
+    tolerance."""
+    pr = dict(problem("blocks255"), r=8.0, aspect=1.0)
+    ho = O.setup(pr["k"], nu1=1, nu2=1, r=8.0, smoother="xy")
+    ro = O.pcg(ho, pr["b"], tol=1e-10)
+    hg = bm.setup(dev(pr["k"]), bm.default_options(nu1=1, nu2=1, aniso_r=8.0,
+                                                   smoother=bm.BMG_SMOOTH_ALTLINE,
+                                                   solver=bm.BMG_SOLVER_PCG))
+    x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+    hg.destroy()
+    assert ro.converged and info.cycles == ro.cycles, (info.cycles, ro.cycles)
+    assert np.abs(x.cpu().numpy() - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+    hf = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=8.0, smoother=bm.BMG_SMOOTH_ALTLINE,
+                                                   precision=bm.BMG_FP32_REFINE))
+    xf, infof = hf.solve(dev(pr["b"]), tol=1e-10)
+    hf.destroy()
+    st = O.assemble_fv5(pr["k"], r=8.0)
+    rel = np.linalg.norm(O.residual(st, xf.cpu().numpy(), pr["b"])) / np.linalg.norm(pr["b"])
+    assert infof.rel_resid <= 1e-10 and rel <= 1.0000001e-10
+
+
+def test_smoother_option_is_checked():
+    k = dev(np.ones((31, 31)))
+    for bad in (-1, 4):
+        with pytest.raises(bm.BoxMGError) as e:
+            bm.setup(k, bm.default_options(smoother=bad))
+        assert e.value.code == bm.BMG_EINVAL
+    with pytest.raises(bm.BoxMGError) as e:
+        bm.Batch([dev(np.ones((31, 31)))], bm.default_options(smoother=bm.BMG_SMOOTH_ALTLINE))
+    assert e.value.code == bm.BMG_EINVAL
