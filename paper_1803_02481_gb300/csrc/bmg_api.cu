@@ -92,8 +92,21 @@ void carve_levels(Carver& cv, const std::vector<Geom>& geo, int first, std::vect
     L.x2 = cv.plane<T>(g);
     L.b = cv.plane<T>(g);
     L.r = cv.plane<T>(g);
-    for (int d = 0; d < 2; ++d)
-      for (int k = 0; k < NLF; ++k) L.LF[d][k] = (d == 0 ? xl : yl) ? cv.plane<T>(g) : nullptr;
+    // colour-compacted planes of the y-lines: (ny + 2) rows of ycp columns
+    // per colour, ycp >= the columns of a colour, a multiple of 32
+    L.ycp = ((g.nx + 1) / 2 + 31) / 32 * 32;
+    L.yhalf = (g.ny + 2) * L.ycp;
+    L.ys = yl ? cv.raw<T>(2 * size_t(L.yhalf)) : nullptr;
+    for (int d = 0; d < 2; ++d) {
+      const bool use = d == 0 ? xl : yl;
+      for (int k = 0; k < NLF; ++k)
+        L.LF[d][k] = !use ? nullptr : d == 0 ? cv.plane<T>(g) : cv.raw<T>(2 * size_t(L.yhalf));
+      const int n = d == 0 ? g.nx : g.ny, nl = d == 0 ? g.ny : g.nx;
+      const int nsep = n / kLineM;
+      L.spp[d] = use && nsep > 0 ? (nsep + 3) / 4 * 4 : 0;
+      for (int k = 0; k < NSP; ++k)
+        L.SP[d][k] = L.spp[d] ? cv.raw<T>(size_t(nl + 1) * L.spp[d]) : nullptr;
+    }
     if (l >= 1 && i >= 1) {
       const Geom& gc = geo[i - 1];
       for (int k = 0; k < NPW; ++k) L.P[k] = cv.plane<T>(gc);

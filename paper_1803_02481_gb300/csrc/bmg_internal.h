@@ -75,6 +75,12 @@ constexpr int base_shift() { return int(128 / sizeof(T)) - 1; }
 // and the two spikes.
 constexpr int kLineM = 16;
 enum { LF_MU = 0, LF_IU, LF_CA, LF_V, LF_W, NLF };
+// Per-separator arrays of a line direction, compact: separator t (0-based)
+// of line q at q * spp + t.  Setup: the Schur system's forward multiplier,
+// reciprocal pivot, back-substitution coefficient and the coupling a_{s+1}
+// to the point after the separator.  Per sweep: d_s + a_s g_{s-1} (then the
+// forward values) and g_{s+1}, written by the block solves.
+enum { SP_MU = 0, SP_IU, SP_CA, SP_AN, SP_RL, SP_GF, NSP };
 
 // Device view of one level.  Pointers are plane bases (element (0,0) is the
 // lower-left ghost).  SW/NW are null on a 5-point level.  P holds the
@@ -87,7 +93,12 @@ struct LevelV {
   T *C, *iC, *W, *S, *SW, *NW;
   T *x, *b, *r;
   T *x2;               // second iterate buffer (sweeps write out of place)
-  T *LF[2][NLF];
+  T *LF[2][NLF];       // x-lines: plane layout; y-lines: colour-compacted
+  T *SP[2][NSP];
+  int spp[2];          // separators per line, rounded up (0: no separators)
+  T *ys;               // y-line scratch, colour-compacted
+  int ycp, yhalf;      // colour-compacted layout: column c + 2 j + 1 of
+                       // colour c at c * yhalf + row * ycp + j
   T *P[NPW];
   int cpitch;          // pitch of the coarse grid the P planes live on
 };

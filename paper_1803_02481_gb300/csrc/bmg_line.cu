@@ -14,8 +14,8 @@ inline int cdiv(long a, long b) { return int((a + b - 1) / b); }
 
 constexpr int kPT = 256;        // threads of the point-parallel kernels
 constexpr int kBT = 128;        // threads of the block-parallel kernels
-constexpr int kSepWarps = 4;    // lines per block of the separator kernel
-constexpr int kSepChunk = 256;  // separators staged per pass
+constexpr int kSepChunk = 256;  // separators per line staged per pass
+constexpr int kSepLines = 8;    // lines per thread block of the separator kernel
 
 // Point-parallel index space of one colour: the fast grid axis runs along
 // the contiguous direction of the plane (the points of a row for x-lines,
@@ -36,9 +36,9 @@ template <typename T, int DIR, bool NINE>
 __global__ void __launch_bounds__(kPT) k_line_rhs(LevelV<T> L, int colour,
                                                   const T* __restrict__ xs) {
   const LineGeo g = line_geo<DIR>(L);
+  T* G = line_scratch<DIR>(L);
   for_colour_points<DIR>(g, colour, [&](int q, int k) {
-    const int o = q * g.ls + k * g.es;
-    L.r[o] = line_rhs<T, DIR, NINE>(L, xs, o);
+    G[line_fbase<DIR>(L, q) + k * g.fes] = line_rhs<T, DIR, NINE>(L, xs, q * g.ls + k * g.es);
   });
 }
 
@@ -57,61 +57,177 @@ __global__ void __launch_bounds__(kBT) k_line_blocks(LevelV<T> L, int colour) {
   }
 }
 
-// One warp per line.  The lanes compute the Schur right-hand sides (and the
-// products y * (1/u)) of a chunk of separators in parallel into shared
-// memory; lane 0 runs the substitution chain through the chunk.  The
-// arithmetic is that of line_sep_serial.
-template <typename T, int DIR>
-__global__ void __launch_bounds__(kSepWarps * 32) k_line_seps(LevelV<T> L, int colour,
-                                                              T* __restrict__ xo) {
-  __shared__ T sa[kSepWarps][kSepChunk], sb[kSepWarps][kSepChunk];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const LineGeo g = line_geo<DIR>(L);
-  const int li = blockIdx.x * kSepWarps + warp;
-  if (li >= line_count(g.nl, colour)) return;
-  const int nsep = g.n / kLineM;
-  const T* __restrict__ mu = L.LF[DIR][LF_MU];
-  const T* __restrict__ iu = L.LF[DIR][LF_IU];
-  const T* __restrict__ ca = L.LF[DIR][LF_CA];
+// x-lines: one thread block per segment of kXSeg blocks of a row.  The
+// segment's right-hand sides and factors are loaded with contiguous accesses
+// into shared memory (one word of padding per block of kLineM points, so the
+// threads' block-strided reads hit distinct banks), each thread substitutes
+// its block there, and the solutions go back with contiguous stores.
+constexpr int kXSeg = 128;
+constexpr int kXPts = kXSeg * kLineM;
+constexpr int kXPad = kXSeg * (kLineM + 1);
+
+template <typename T>
+size_t xblocks_smem() { return 4 * size_t(kXPad) * sizeof(T); }
+
+template <typename T>
+__global__ void __launch_bounds__(kXSeg) k_line_blocks_x(LevelV<T> L, int colour) {
+  extern __shared__ __align__(16) unsigned char xsm_raw[];
+  T* sd = reinterpret_cast<T*>(xsm_raw);
+  T* sm = sd + kXPad;
+  T* si = sm + kXPad;
+  T* sc = si + kXPad;
+  const LineGeo g = line_geo<0>(L);
+  const int q = 2 * blockIdx.y + colour + 1;
+  const int k_base = blockIdx.x * kXPts + 1;      // first point of the segment
+  const int o_base = q * g.ls + k_base;
+  const T* __restrict__ mu = L.LF[0][LF_MU];
+  const T* __restrict__ iu = L.LF[0][LF_IU];
+  const T* __restrict__ ca = L.LF[0][LF_CA];
   T* G = L.r;
-  T* a = sa[warp];
-  T* c = sb[warp];
-  const int base = (2 * li + colour + 1) * g.ls, step = kLineM * g.es;
+  const int npts = min(kXPts, g.n - k_base + 1);
+  for (int i = threadIdx.x; i < npts; i += kXSeg) {
+    const int p = i + i / kLineM, o = o_base + i;
+    sd[p] = G[o];
+    sm[p] = mu[o];
+    si[p] = iu[o];
+    sc[p] = ca[o];
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  const int bb = blockIdx.x * kXSeg + j;
+  const int k0 = bb * kLineM + 1;
+  const int len = min(kLineM - 1, g.n - k0 + 1);
+  if (len > 0) {
+    const int pb = j * (kLineM + 1);
+    T gfirst, glast;
+    block_subst<T>(
+        len,
+        [&](int e, T& d, T& m, T& iv, T& c) {
+          d = sd[pb + e];
+          m = sm[pb + e];
+          iv = si[pb + e];
+          c = sc[pb + e];
+        },
+        [&](int e, T v) { sd[pb + e] = v; }, gfirst, glast);
+    if (k0 + len <= g.n && len == kLineM - 1) {
+      const int os = q * g.ls + k0 + len;
+      L.SP[0][SP_RL][q * L.spp[0] + bb] = fma(L.W[os], glast, sd[pb + len]);
+    }
+    if (bb > 0) L.SP[0][SP_GF][q * L.spp[0] + bb - 1] = gfirst;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npts; i += kXSeg)
+    if ((i + 1) % kLineM != 0) G[o_base + i] = sd[i + i / kLineM];
+}
+
+// One line per lane: kSepLines lanes of warp 0 run the separator chains of
+// kSepLines lines of the colour at once (an FP64 warp instruction costs the
+// same pipe slot however few lanes are active), after all kSepThreads
+// threads have staged a chunk of kSepChunk separators of those lines in
+// shared memory, transposed to [separator][line] with one word of padding
+// per row (the loads run along each line's compact slots; each chain step
+// reads consecutive words).  Forward: stage the Schur right-hand sides
+// (d_s + a_s g_{s-1}) + a_{s+1} g_{s+1} and the multipliers, run
+// y = mu y + rhs, write y back over d_s + a_s g_{s-1}; backward: stage
+// y * (1/u) and the coefficients, run x = ca x + y / u, write x to the
+// separators.  The arithmetic is that of line_sep_serial.
+constexpr int kSepThreads = 128;
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(kSepThreads) k_line_seps(LevelV<T> L, int colour,
+                                                           T* __restrict__ xo) {
+  __shared__ T sa[kSepChunk][kSepLines + 1], sb[kSepChunk][kSepLines + 1];
+  const int tid = threadIdx.x;
+  const LineGeo g = line_geo<DIR>(L);
+  const int nlc = line_count(g.nl, colour);
+  const int li0 = blockIdx.x * kSepLines;
+  const int nsep = g.n / kLineM, spp = L.spp[DIR];
+  const T* __restrict__ mu = L.SP[DIR][SP_MU];
+  const T* __restrict__ iu = L.SP[DIR][SP_IU];
+  const T* __restrict__ ca = L.SP[DIR][SP_CA];
+  const T* __restrict__ an = L.SP[DIR][SP_AN];
+  const T* __restrict__ gf = L.SP[DIR][SP_GF];
+  T* rl = L.SP[DIR][SP_RL];
+  const int nl_here = min(kSepLines, nlc - li0);
+  const bool chain = tid < nl_here;       // one lane per line
+  auto slot = [&](int l, int t) { return (2 * (li0 + l) + colour + 1) * spp + t; };
   T y = T(0);
   for (int c0 = 0; c0 < nsep; c0 += kSepChunk) {
     const int cn = min(kSepChunk, nsep - c0);
-    for (int t = lane; t < cn; t += 32) {
-      const int os = base + (c0 + t + 1) * step;
-      a[t] = line_sep_rhs<T, DIR>(L, g.es, os);
-      c[t] = mu[os];
+#pragma unroll 4
+    for (int idx = tid; idx < nl_here * cn; idx += kSepThreads) {
+      const int l = idx / cn, t = idx - l * cn;
+      const int r = slot(l, c0 + t);
+      sa[t][l] = fma(an[r], gf[r], rl[r]);
+      sb[t][l] = mu[r];
     }
-    __syncwarp();
-    if (lane == 0)
-      for (int t = 0; t < cn; ++t) {
-        y = fma(c[t], y, a[t]);
-        a[t] = y;
+    __syncthreads();
+    if (chain) {
+      int t = 0;
+      for (; t + 8 <= cn; t += 8) {
+        T m[8], r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          m[u] = sb[t + u][tid];
+          r[u] = sa[t + u][tid];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          y = fma(m[u], y, r[u]);
+          sa[t + u][tid] = y;
+        }
       }
-    __syncwarp();
-    for (int t = lane; t < cn; t += 32) G[base + (c0 + t + 1) * step] = a[t];
-    __syncwarp();
+      for (; t < cn; ++t) {
+        y = fma(sb[t][tid], y, sa[t][tid]);
+        sa[t][tid] = y;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int idx = tid; idx < nl_here * cn; idx += kSepThreads) {
+      const int l = idx / cn, t = idx - l * cn;
+      rl[slot(l, c0 + t)] = sa[t][l];
+    }
+    __syncthreads();
   }
   T xn = T(0);
   for (int c1 = nsep; c1 > 0; c1 -= kSepChunk) {
     const int c0 = max(0, c1 - kSepChunk), cn = c1 - c0;
-    for (int t = lane; t < cn; t += 32) {
-      const int os = base + (c0 + t + 1) * step;
-      a[t] = G[os] * iu[os];
-      c[t] = ca[os];
+#pragma unroll 4
+    for (int idx = tid; idx < nl_here * cn; idx += kSepThreads) {
+      const int l = idx / cn, t = idx - l * cn;
+      const int r = slot(l, c0 + t);
+      sa[t][l] = rl[r] * iu[r];
+      sb[t][l] = ca[r];
     }
-    __syncwarp();
-    if (lane == 0)
-      for (int t = cn - 1; t >= 0; --t) {
-        xn = fma(c[t], xn, a[t]);
-        a[t] = xn;
+    __syncthreads();
+    if (chain) {
+      int t = cn - 1;
+      for (; t >= 7; t -= 8) {
+        T c[8], a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          c[u] = sb[t - u][tid];
+          a[u] = sa[t - u][tid];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          xn = fma(c[u], xn, a[u]);
+          sa[t - u][tid] = xn;
+        }
       }
-    __syncwarp();
-    for (int t = lane; t < cn; t += 32) xo[base + (c0 + t + 1) * step] = a[t];
-    __syncwarp();
+      for (; t >= 0; --t) {
+        xn = fma(sb[t][tid], xn, sa[t][tid]);
+        sa[t][tid] = xn;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int idx = tid; idx < nl_here * cn; idx += kSepThreads) {
+      const int l = idx / cn, t = idx - l * cn;
+      xo[(2 * (li0 + l) + colour + 1) * g.ls + (c0 + t + 1) * kLineM * g.es] = sa[t][l];
+    }
+    __syncthreads();
   }
 }
 
@@ -146,6 +262,7 @@ __global__ void __launch_bounds__(kBT) k_line_factor_blocks(LevelV<T> L, int* de
   if (len <= 0) return;
   const T* A = line_coupling<DIR>(L);
   const int o0 = q * g.ls + k0 * g.es;
+  const int f0 = line_fbase<DIR>(L, q) + k0 * g.fes;
   double iu[kLineM - 1], ca[kLineM - 1], mu[kLineM - 1];
   double up = 1.0;
   bool bad = false;
@@ -178,15 +295,15 @@ __global__ void __launch_bounds__(kBT) k_line_factor_blocks(LevelV<T> L, int* de
 #pragma unroll
   for (int e = kLineM - 2; e >= 0; --e) {
     if (e < len) {
-      const int o = o0 + e * g.es;
+      const int f = f0 + e * g.fes;
       const double cae = e == len - 1 ? 0.0 : ca[e];
       vn = yv[e] * iu[e] + cae * vn;
       wn = (e == len - 1 ? a_next * iu[e] : 0.0) + cae * wn;
-      L.LF[DIR][LF_MU][o] = T(mu[e]);
-      L.LF[DIR][LF_IU][o] = T(iu[e]);
-      L.LF[DIR][LF_CA][o] = T(cae);
-      L.LF[DIR][LF_V][o] = T(vn);
-      L.LF[DIR][LF_W][o] = T(wn);
+      L.LF[DIR][LF_MU][f] = T(mu[e]);
+      L.LF[DIR][LF_IU][f] = T(iu[e]);
+      L.LF[DIR][LF_CA][f] = T(cae);
+      L.LF[DIR][LF_V][f] = T(vn);
+      L.LF[DIR][LF_W][f] = T(wn);
     }
   }
   if (bad) atomicOr(derr, DEV_BADLINE);
@@ -210,18 +327,19 @@ __global__ void __launch_bounds__(kBT) k_line_factor_seps(LevelV<T> L, int* derr
   bool bad = false;
   for (int t = 0; t < nsep; ++t) {
     const int os = q * g.ls + (t + 1) * kLineM * g.es;
+    const int fs = line_fbase<DIR>(L, q) + (t + 1) * kLineM * g.fes;
     const double as = double(A[os]), an = double(A[os + g.es]);
-    const double d = double(L.C[os]) - as * double(W[os - g.es]) - an * double(V[os + g.es]);
-    const double lo = as * double(V[os - g.es]);   // coupling to the previous separator
-    const double hi = an * double(W[os + g.es]);   // coupling to the next separator
+    const double d = double(L.C[os]) - as * double(W[fs - g.fes]) - an * double(V[fs + g.fes]);
+    const double lo = as * double(V[fs - g.fes]);   // coupling to the previous separator
+    const double hi = an * double(W[fs + g.fes]);   // coupling to the next separator
     const double m = t ? lo / up : 0.0;
     const double u = d - m * uprev_coupling;
     if (!(u > 0.0) || !(u < INFINITY)) bad = true;
-    L.LF[DIR][LF_MU][os] = T(m);
-    L.LF[DIR][LF_IU][os] = T(1.0 / u);
-    L.LF[DIR][LF_CA][os] = T(hi / u);
-    L.LF[DIR][LF_V][os] = T(0);
-    L.LF[DIR][LF_W][os] = T(0);
+    const int c = q * L.spp[DIR] + t;
+    L.SP[DIR][SP_MU][c] = T(m);
+    L.SP[DIR][SP_IU][c] = T(1.0 / u);
+    L.SP[DIR][SP_CA][c] = T(hi / u);
+    L.SP[DIR][SP_AN][c] = A[os + g.es];
     up = u;
     uprev_coupling = hi;
   }
@@ -240,12 +358,14 @@ void line_step(const LevelV<T>& L, int colour, const T* xs, T* xo, cudaStream_t 
     const int fast = DIR == 0 ? g.n : nlc, slow = DIR == 0 ? nlc : g.n;
     k_line_rhs<T, DIR, NINE><<<dim3(cdiv(fast, kPT), grid_y(slow)), kPT, 0, s>>>(L, colour, xs);
   }
-  {
-    const int fast = DIR == 0 ? nb : nlc, slow = DIR == 0 ? nlc : nb;
+  if (DIR == 0) {
+    k_line_blocks_x<T><<<dim3(cdiv(g.n, kXPts), nlc), kXSeg, xblocks_smem<T>(), s>>>(L, colour);
+  } else {
+    const int fast = nlc, slow = nb;
     k_line_blocks<T, DIR><<<dim3(cdiv(fast, kBT), grid_y(slow)), kBT, 0, s>>>(L, colour);
   }
   if (g.n >= kLineM)
-    k_line_seps<T, DIR><<<cdiv(nlc, kSepWarps), kSepWarps * 32, 0, s>>>(L, colour, xo);
+    k_line_seps<T, DIR><<<cdiv(nlc, kSepLines), kSepThreads, 0, s>>>(L, colour, xo);
   {
     const int fast = DIR == 0 ? g.n : nlc, slow = DIR == 0 ? nlc : g.n;
     k_line_final<T, DIR><<<dim3(cdiv(fast, kPT), grid_y(slow)), kPT, 0, s>>>(L, colour, xo);
@@ -257,6 +377,13 @@ void line_step(const LevelV<T>& L, int colour, const T* xs, T* xo, cudaStream_t 
 
 template <typename T>
 int launch_line_factor(const LevelV<T>& L, int smoother, int* derr, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_line_blocks_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(xblocks_smem<T>())) != cudaSuccess)
+      return BMG_ECUDA;
+    attr = true;
+  }
   auto one = [&](auto dir_tag) {
     constexpr int DIR = decltype(dir_tag)::value;
     const LineGeo g = line_geo<DIR>(L);

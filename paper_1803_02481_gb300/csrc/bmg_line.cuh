@@ -29,14 +29,31 @@ namespace bmg {
 // Geometry of the lines of one direction: DIR 0 = x-lines (the rows, points
 // along x, implicit in the W couplings), DIR 1 = y-lines (the columns,
 // implicit in the S couplings).  Point k (1-based, 0 and n + 1 are ghosts) of
-// line q (1-based) sits at plane offset q * ls + k * es.
+// line q (1-based) sits at plane offset q * ls + k * es (b, x and the
+// couplings), and its factors and scratch at fbase(q) + k * fes: the plane
+// layout for x-lines, and for y-lines the colour-compacted layout, where the
+// columns of one colour are side by side (so a step along the lines of a
+// colour reads contiguous words).
 struct LineGeo {
-  int n, nl, es, ls;
+  int n, nl, es, ls, fes;
 };
 
 template <int DIR, typename T>
 __host__ __device__ __forceinline__ LineGeo line_geo(const LevelV<T>& L) {
-  return DIR == 0 ? LineGeo{L.nx, L.ny, 1, L.pitch} : LineGeo{L.ny, L.nx, L.pitch, 1};
+  return DIR == 0 ? LineGeo{L.nx, L.ny, 1, L.pitch, 1}
+                  : LineGeo{L.ny, L.nx, L.pitch, 1, L.ycp};
+}
+
+template <int DIR, typename T>
+__host__ __device__ __forceinline__ int line_fbase(const LevelV<T>& L, int q) {
+  return DIR == 0 ? q * L.pitch : ((q - 1) & 1) * L.yhalf + ((q - 1) >> 1);
+}
+
+// The scratch of a direction: the r plane for x-lines, the compact plane
+// for y-lines.
+template <int DIR, typename T>
+__device__ __forceinline__ T* line_scratch(const LevelV<T>& L) {
+  return DIR == 0 ? L.r : L.ys;
 }
 
 // Number of lines of colour c (0: odd lines q = 1, 3, ...; 1: even lines).
@@ -70,12 +87,46 @@ __device__ __forceinline__ T line_rhs(const LevelV<T>& L, const T* __restrict__ 
   return d;
 }
 
-// Step 1 for block bb of line q: G holds d on entry and g on exit.  The
-// forward multiplier of a block's first point and the back-substitution
-// coefficient of its last point are stored as 0, so every point takes the
-// same two fused multiply-adds.  The forward values stay in registers, or
-// (INMEM, for the register-bound persistent kernel) in G itself; the values
-// are the same either way.
+// Forward and back substitution of one block of len points: ld(e, d, mu,
+// iu, ca) fetches point e's right-hand side and factors (all fetched before
+// the first substitution), st(e, g) stores its solution; returns the
+// solutions of the first and last point.
+template <typename T, class LD, class ST>
+__device__ __forceinline__ void block_subst(int len, LD ld, ST st, T& gfirst, T& glast) {
+  T dv[kLineM - 1], mv[kLineM - 1], iv[kLineM - 1], cv[kLineM - 1];
+#pragma unroll
+  for (int e = 0; e < kLineM - 1; ++e)
+    if (e < len) ld(e, dv[e], mv[e], iv[e], cv[e]);
+  T prev = T(0);
+#pragma unroll
+  for (int e = 0; e < kLineM - 1; ++e) {
+    if (e < len) {
+      prev = fma(mv[e], prev, dv[e]);
+      dv[e] = prev;
+    }
+  }
+  T next = T(0);
+  glast = T(0);
+#pragma unroll
+  for (int e = kLineM - 2; e >= 0; --e) {
+    if (e < len) {
+      next = fma(cv[e], next, dv[e] * iv[e]);
+      if (e == len - 1) glast = next;
+      st(e, next);
+    }
+  }
+  gfirst = next;
+}
+
+// Step 1 for block bb of line q: the scratch G holds d on entry and g on
+// exit.  The forward multiplier of a block's first point and the
+// back-substitution coefficient of its last point are stored as 0, so every
+// point takes the same two fused multiply-adds.  The full-grid variant loads
+// the block's four inputs into registers first (all loads in flight at
+// once), then also hands the separators their block values: d_s + a_s g_{s-1}
+// of the separator after the block and g_{s+1} of the one before it (SP_RL,
+// SP_GF).  The INMEM variant (the register-bound persistent kernel) keeps
+// the forward values in G itself; the values are the same either way.
 template <typename T, int DIR, bool INMEM = false>
 __device__ __forceinline__ void line_block_solve(const LevelV<T>& L, int q, int bb) {
   const LineGeo g = line_geo<DIR>(L);
@@ -85,91 +136,86 @@ __device__ __forceinline__ void line_block_solve(const LevelV<T>& L, int q, int 
   const T* __restrict__ mu = L.LF[DIR][LF_MU];
   const T* __restrict__ iu = L.LF[DIR][LF_IU];
   const T* __restrict__ ca = L.LF[DIR][LF_CA];
-  T* G = L.r;
-  const int o0 = q * g.ls + k0 * g.es;
-  if constexpr (INMEM) {
+  T* G = line_scratch<DIR>(L);
+  const int f0 = line_fbase<DIR>(L, q) + k0 * g.fes;
+  if constexpr (!INMEM) {
+    T gfirst, glast;
+    block_subst<T>(
+        len,
+        [&](int e, T& d, T& m, T& i, T& c) {
+          const int f = f0 + e * g.fes;
+          d = G[f];
+          m = mu[f];
+          i = iu[f];
+          c = ca[f];
+        },
+        [&](int e, T v) { G[f0 + e * g.fes] = v; }, gfirst, glast);
+    // the separators on either side (their compact slots)
+    if (k0 + len <= g.n && len == kLineM - 1) {
+      const int os = q * g.ls + (k0 + len) * g.es;
+      L.SP[DIR][SP_RL][q * L.spp[DIR] + bb] =
+          fma(line_coupling<DIR>(L)[os], glast, G[f0 + len * g.fes]);
+    }
+    if (bb > 0) L.SP[DIR][SP_GF][q * L.spp[DIR] + bb - 1] = gfirst;
+  } else {
     T prev = T(0);
     for (int e = 0; e < len; ++e) {
-      const int o = o0 + e * g.es;
-      prev = fma(mu[o], prev, G[o]);
-      G[o] = prev;
+      const int f = f0 + e * g.fes;
+      prev = fma(mu[f], prev, G[f]);
+      G[f] = prev;
     }
     T next = T(0);
     for (int e = len - 1; e >= 0; --e) {
-      const int o = o0 + e * g.es;
-      next = fma(ca[o], next, G[o] * iu[o]);
-      G[o] = next;
-    }
-  } else {
-    T y[kLineM - 1];
-    T prev = T(0);
-#pragma unroll
-    for (int e = 0; e < kLineM - 1; ++e) {
-      if (e < len) {
-        const int o = o0 + e * g.es;
-        prev = fma(mu[o], prev, G[o]);
-        y[e] = prev;
-      }
-    }
-    T next = T(0);
-#pragma unroll
-    for (int e = kLineM - 2; e >= 0; --e) {
-      if (e < len) {
-        const int o = o0 + e * g.es;
-        next = fma(ca[o], next, y[e] * iu[o]);
-        G[o] = next;
-      }
+      const int f = f0 + e * g.fes;
+      next = fma(ca[f], next, G[f] * iu[f]);
+      G[f] = next;
     }
   }
 }
 
-// Right-hand side of the Schur system at the separator at offset os:
-// d_s + a_s g_{s-1} + a_{s+1} g_{s+1} (a_{n+1} = 0 and the ghost of G is 0).
-template <typename T, int DIR>
-__device__ __forceinline__ T line_sep_rhs(const LevelV<T>& L, int es, int os) {
-  const T* A = line_coupling<DIR>(L);
-  const T* G = L.r;
-  const T r = fma(A[os], G[os - es], G[os]);
-  return fma(A[os + es], G[os + es], r);
-}
-
-// Step 2 for line q by one thread: forward substitution (y overwrites d_s in
-// G), then back substitution writing the separator values into xo.
+// Step 2 for line q by one thread: the Schur right-hand side of separator s
+// is (d_s + a_s g_{s-1}) + a_{s+1} g_{s+1} (a_{n+1} = 0 and the ghost of G is
+// 0); forward substitution (y overwrites d_s in G), then back substitution
+// writing the separator values into xo.  The Schur factors are the compact
+// per-separator arrays.
 template <typename T, int DIR>
 __device__ void line_sep_serial(const LevelV<T>& L, int q, T* __restrict__ xo) {
   const LineGeo g = line_geo<DIR>(L);
   const int nsep = g.n / kLineM;
-  const T* __restrict__ mu = L.LF[DIR][LF_MU];
-  const T* __restrict__ iu = L.LF[DIR][LF_IU];
-  const T* __restrict__ ca = L.LF[DIR][LF_CA];
-  T* G = L.r;
-  const int base = q * g.ls, step = kLineM * g.es;
+  const T* __restrict__ mu = L.SP[DIR][SP_MU] + q * L.spp[DIR];
+  const T* __restrict__ iu = L.SP[DIR][SP_IU] + q * L.spp[DIR];
+  const T* __restrict__ ca = L.SP[DIR][SP_CA] + q * L.spp[DIR];
+  const T* A = line_coupling<DIR>(L);
+  T* G = line_scratch<DIR>(L);
+  const int base = q * g.ls, fb = line_fbase<DIR>(L, q);
   T y = T(0);
   for (int t = 0; t < nsep; ++t) {
-    const int os = base + (t + 1) * step;
-    y = fma(mu[os], y, line_sep_rhs<T, DIR>(L, g.es, os));
-    G[os] = y;
+    const int ks = (t + 1) * kLineM;
+    const int os = base + ks * g.es, fs = fb + ks * g.fes;
+    const T r = fma(A[os], G[fs - g.fes], G[fs]);
+    y = fma(mu[t], y, fma(A[os + g.es], G[fs + g.fes], r));
+    G[fs] = y;
   }
   T xn = T(0);
   for (int t = nsep - 1; t >= 0; --t) {
-    const int os = base + (t + 1) * step;
-    xn = fma(ca[os], xn, G[os] * iu[os]);
-    xo[os] = xn;
+    const int ks = (t + 1) * kLineM;
+    xn = fma(ca[t], xn, G[fb + ks * g.fes] * iu[t]);
+    xo[base + ks * g.es] = xn;
   }
 }
 
-// Step 3 at interior point k of line q (plane offset o): the block's g plus
-// the spikes times the separator values on either side (line position 0 or
-// n + 1 where the block has no separator there: a ghost, whose value is 0).
+// Step 3 at interior point k of line q: the block's g plus the spikes times
+// the separator values on either side (line position 0 or n + 1 where the
+// block has no separator there: a ghost, whose value is 0).
 template <typename T, int DIR>
 __device__ __forceinline__ void line_final(const LevelV<T>& L, const LineGeo& g, int q, int k,
                                            T* __restrict__ xo) {
   const int kl = (k / kLineM) * kLineM;
   const int kr = min(kl + kLineM, g.n + 1);
-  const int o = q * g.ls + k * g.es;
-  const T v = L.LF[DIR][LF_V][o], w = L.LF[DIR][LF_W][o];
+  const int f = line_fbase<DIR>(L, q) + k * g.fes;
+  const T v = L.LF[DIR][LF_V][f], w = L.LF[DIR][LF_W][f];
   const T xl = xo[q * g.ls + kl * g.es], xr = xo[q * g.ls + kr * g.es];
-  xo[o] = fma(w, xr, fma(v, xl, L.r[o]));
+  xo[q * g.ls + k * g.es] = fma(w, xr, fma(v, xl, line_scratch<DIR>(L)[f]));
 }
 
 // One colour of one direction by a whole thread block (the persistent coarse
@@ -179,10 +225,10 @@ template <typename T, int DIR, bool NINE>
 __device__ void blk_line_colour(const LevelV<T>& L, int colour) {
   const LineGeo g = line_geo<DIR>(L);
   const int nlc = line_count(g.nl, colour);
+  T* G = line_scratch<DIR>(L);
   for (int t = threadIdx.x; t < nlc * g.n; t += blockDim.x) {
     const int q = 2 * (t / g.n) + colour + 1, k = t % g.n + 1;
-    const int o = q * g.ls + k * g.es;
-    L.r[o] = line_rhs<T, DIR, NINE>(L, L.x, o);
+    G[line_fbase<DIR>(L, q) + k * g.fes] = line_rhs<T, DIR, NINE>(L, L.x, q * g.ls + k * g.es);
   }
   __syncthreads();
   const int nb = g.n / kLineM + 1;
