@@ -104,6 +104,8 @@ void carve_levels(Carver& cv, const std::vector<Geom>& geo, int first, std::vect
       const int n = d == 0 ? g.nx : g.ny, nl = d == 0 ? g.ny : g.nx;
       const int nsep = n / kLineM;
       L.spp[d] = use && nsep > 0 ? (nsep + 3) / 4 * 4 : 0;
+      L.sgl[d] = std::max(16, (nsep + 255) / 256);   // at most 256 groups per line
+      // (16 = the separator kernel's register group: lines up to 65551 points)
       for (int k = 0; k < NSP; ++k)
         L.SP[d][k] = L.spp[d] ? cv.raw<T>(size_t(nl + 1) * L.spp[d]) : nullptr;
     }

@@ -77,10 +77,13 @@ constexpr int kLineM = 16;
 enum { LF_MU = 0, LF_IU, LF_CA, LF_V, LF_W, NLF };
 // Per-separator arrays of a line direction, compact: separator t (0-based)
 // of line q at q * spp + t.  Setup: the Schur system's forward multiplier,
-// reciprocal pivot, back-substitution coefficient and the coupling a_{s+1}
-// to the point after the separator.  Per sweep: d_s + a_s g_{s-1} (then the
-// forward values) and g_{s+1}, written by the block solves.
-enum { SP_MU = 0, SP_IU, SP_CA, SP_AN, SP_RL, SP_GF, NSP };
+// reciprocal pivot, back-substitution coefficient, the coupling a_{s+1} to
+// the point after the separator, and the products of the multipliers from
+// the start of t's group to t (P) and of the coefficients from t to the end
+// of its group (Q; groups of sgl separators, see bmg_line.cuh).  Per sweep:
+// d_s + a_s g_{s-1} (then the substitutions' partial values) and g_{s+1},
+// written by the block solves.
+enum { SP_MU = 0, SP_IU, SP_CA, SP_AN, SP_P, SP_Q, SP_RL, SP_GF, NSP };
 
 // Device view of one level.  Pointers are plane bases (element (0,0) is the
 // lower-left ghost).  SW/NW are null on a 5-point level.  P holds the
@@ -96,6 +99,7 @@ struct LevelV {
   T *LF[2][NLF];       // x-lines: plane layout; y-lines: colour-compacted
   T *SP[2][NSP];
   int spp[2];          // separators per line, rounded up (0: no separators)
+  int sgl[2];          // separators per group of the Schur substitutions
   T *ys;               // y-line scratch, colour-compacted
   int ycp, yhalf;      // colour-compacted layout: column c + 2 j + 1 of
                        // colour c at c * yhalf + row * ycp + j

@@ -14,8 +14,6 @@ inline int cdiv(long a, long b) { return int((a + b - 1) / b); }
 
 constexpr int kPT = 256;        // threads of the point-parallel kernels
 constexpr int kBT = 128;        // threads of the block-parallel kernels
-constexpr int kSepChunk = 256;  // separators per line staged per pass
-constexpr int kSepLines = 8;    // lines per thread block of the separator kernel
 
 // Point-parallel index space of one colour: the fast grid axis runs along
 // the contiguous direction of the plane (the points of a row for x-lines,
@@ -120,114 +118,127 @@ __global__ void __launch_bounds__(kXSeg) k_line_blocks_x(LevelV<T> L, int colour
     if ((i + 1) % kLineM != 0) G[o_base + i] = sd[i + i / kLineM];
 }
 
-// One line per lane: kSepLines lanes of warp 0 run the separator chains of
-// kSepLines lines of the colour at once (an FP64 warp instruction costs the
-// same pipe slot however few lanes are active), after all kSepThreads
-// threads have staged a chunk of kSepChunk separators of those lines in
-// shared memory, transposed to [separator][line] with one word of padding
-// per row (the loads run along each line's compact slots; each chain step
-// reads consecutive words).  Forward: stage the Schur right-hand sides
-// (d_s + a_s g_{s-1}) + a_{s+1} g_{s+1} and the multipliers, run
-// y = mu y + rhs, write y back over d_s + a_s g_{s-1}; backward: stage
-// y * (1/u) and the coefficients, run x = ca x + y / u, write x to the
-// separators.  The arithmetic is that of line_sep_serial.
-constexpr int kSepThreads = 128;
+// The separators' two-level substitution (line_sep_serial states the
+// operations): one thread per group of a line, several lines per thread
+// block; each thread substitutes its group from a zero carry, one thread
+// per line runs the carries through the groups in shared memory, and each
+// thread then fixes up its group.  The right-hand sides come from the
+// compact slots the block solves filled.
+constexpr int kSepThreads = 256;
+constexpr int kSepGroup = 16;   // separators per group held in registers
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(kSepThreads) k_line_seps(LevelV<T> L, int colour,
+__global__ void __launch_bounds__(kSepThreads) k_line_seps(LevelV<T> L, int colour, int ngroups,
                                                            T* __restrict__ xo) {
-  __shared__ T sa[kSepChunk][kSepLines + 1], sb[kSepChunk][kSepLines + 1];
+  __shared__ T s_end[kSepThreads], s_pq[kSepThreads], s_c[kSepThreads];
   const int tid = threadIdx.x;
   const LineGeo g = line_geo<DIR>(L);
-  const int nlc = line_count(g.nl, colour);
-  const int li0 = blockIdx.x * kSepLines;
-  const int nsep = g.n / kLineM, spp = L.spp[DIR];
-  const T* __restrict__ mu = L.SP[DIR][SP_MU];
-  const T* __restrict__ iu = L.SP[DIR][SP_IU];
-  const T* __restrict__ ca = L.SP[DIR][SP_CA];
-  const T* __restrict__ an = L.SP[DIR][SP_AN];
-  const T* __restrict__ gf = L.SP[DIR][SP_GF];
-  T* rl = L.SP[DIR][SP_RL];
-  const int nl_here = min(kSepLines, nlc - li0);
-  const bool chain = tid < nl_here;       // one lane per line
-  auto slot = [&](int l, int t) { return (2 * (li0 + l) + colour + 1) * spp + t; };
-  T y = T(0);
-  for (int c0 = 0; c0 < nsep; c0 += kSepChunk) {
-    const int cn = min(kSepChunk, nsep - c0);
-#pragma unroll 4
-    for (int idx = tid; idx < nl_here * cn; idx += kSepThreads) {
-      const int l = idx / cn, t = idx - l * cn;
-      const int r = slot(l, c0 + t);
-      sa[t][l] = fma(an[r], gf[r], rl[r]);
-      sb[t][l] = mu[r];
-    }
-    __syncthreads();
-    if (chain) {
-      int t = 0;
-      for (; t + 8 <= cn; t += 8) {
-        T m[8], r[8];
+  const int lpb = kSepThreads / ngroups;               // lines per block
+  const int l = tid / ngroups, gi = tid - l * ngroups;
+  const int li = blockIdx.x * lpb + l;
+  const bool act = l < lpb && li < line_count(g.nl, colour);
+  const int nsep = g.n / kLineM, gl = L.sgl[DIR];
+  const int t0 = gi * gl, t1 = min(t0 + gl, nsep);
+  const int q = 2 * li + colour + 1;
+  const int sp = q * L.spp[DIR];
+  const T* __restrict__ mu = L.SP[DIR][SP_MU] + sp;
+  const T* __restrict__ iu = L.SP[DIR][SP_IU] + sp;
+  const T* __restrict__ ca = L.SP[DIR][SP_CA] + sp;
+  const T* __restrict__ an = L.SP[DIR][SP_AN] + sp;
+  const T* __restrict__ P = L.SP[DIR][SP_P] + sp;
+  const T* __restrict__ Q = L.SP[DIR][SP_Q] + sp;
+  const T* __restrict__ gf = L.SP[DIR][SP_GF] + sp;
+  T* h = L.SP[DIR][SP_RL] + sp;
+  // forward partial substitution of the group (groups of kSepGroup: every
+  // load of a phase is issued before its substitution starts)
+  constexpr int GL = kSepGroup;
+  const bool regs = gl == GL;
+  const int len = t1 - t0;
+  T hv[GL];
+  T yh = T(0);
+  if (act) {
+    if (regs) {
+      T mv[GL], rv[GL];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          m[u] = sb[t + u][tid];
-          r[u] = sa[t + u][tid];
+      for (int u = 0; u < GL; ++u)
+        if (u < len) {
+          mv[u] = mu[t0 + u];
+          rv[u] = fma(an[t0 + u], gf[t0 + u], h[t0 + u]);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          y = fma(m[u], y, r[u]);
-          sa[t + u][tid] = y;
+      for (int u = 0; u < GL; ++u)
+        if (u < len) {
+          yh = fma(mv[u], yh, rv[u]);
+          hv[u] = yh;
         }
-      }
-      for (; t < cn; ++t) {
-        y = fma(sb[t][tid], y, sa[t][tid]);
-        sa[t][tid] = y;
+    } else {
+      for (int t = t0; t < t1; ++t) {
+        yh = fma(mu[t], yh, fma(an[t], gf[t], h[t]));
+        h[t] = yh;
       }
     }
-    __syncthreads();
-#pragma unroll 4
-    for (int idx = tid; idx < nl_here * cn; idx += kSepThreads) {
-      const int l = idx / cn, t = idx - l * cn;
-      rl[slot(l, c0 + t)] = sa[t][l];
-    }
-    __syncthreads();
+    s_end[tid] = yh;
+    s_pq[tid] = P[t1 - 1];
   }
-  T xn = T(0);
-  for (int c1 = nsep; c1 > 0; c1 -= kSepChunk) {
-    const int c0 = max(0, c1 - kSepChunk), cn = c1 - c0;
-#pragma unroll 4
-    for (int idx = tid; idx < nl_here * cn; idx += kSepThreads) {
-      const int l = idx / cn, t = idx - l * cn;
-      const int r = slot(l, c0 + t);
-      sa[t][l] = rl[r] * iu[r];
-      sb[t][l] = ca[r];
+  __syncthreads();
+  if (act && gi == 0) {
+    T c = T(0);
+    for (int k = 0; k < ngroups; ++k) {
+      const int j = l * ngroups + k;
+      const T cg = c;
+      s_c[j] = cg;
+      c = fma(s_pq[j], cg, s_end[j]);
     }
-    __syncthreads();
-    if (chain) {
-      int t = cn - 1;
-      for (; t >= 7; t -= 8) {
-        T c[8], a[8];
+  }
+  __syncthreads();
+  // fix-up, scaling and backward partial substitution of the group
+  if (act) {
+    const T cg = s_c[tid];
+    T xh = T(0);
+    if (regs) {
+      T pv[GL], iv[GL], cv[GL];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          c[u] = sb[t - u][tid];
-          a[u] = sa[t - u][tid];
+      for (int u = 0; u < GL; ++u)
+        if (u < len) {
+          pv[u] = P[t0 + u];
+          iv[u] = iu[t0 + u];
+          cv[u] = ca[t0 + u];
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          xn = fma(c[u], xn, a[u]);
-          sa[t - u][tid] = xn;
+      for (int u = GL - 1; u >= 0; --u)
+        if (u < len) {
+          xh = fma(cv[u], xh, fma(pv[u], cg, hv[u]) * iv[u]);
+          hv[u] = xh;
         }
-      }
-      for (; t >= 0; --t) {
-        xn = fma(sb[t][tid], xn, sa[t][tid]);
-        sa[t][tid] = xn;
+    } else {
+      for (int t = t1 - 1; t >= t0; --t) {
+        xh = fma(ca[t], xh, fma(P[t], cg, h[t]) * iu[t]);
+        h[t] = xh;
       }
     }
-    __syncthreads();
-#pragma unroll 4
-    for (int idx = tid; idx < nl_here * cn; idx += kSepThreads) {
-      const int l = idx / cn, t = idx - l * cn;
-      xo[(2 * (li0 + l) + colour + 1) * g.ls + (c0 + t + 1) * kLineM * g.es] = sa[t][l];
+    s_end[tid] = xh;
+    s_pq[tid] = Q[t0];
+  }
+  __syncthreads();
+  if (act && gi == 0) {
+    T e = T(0);
+    for (int k = ngroups - 1; k >= 0; --k) {
+      const int j = l * ngroups + k;
+      s_c[j] = e;
+      e = fma(s_pq[j], e, s_end[j]);
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (act) {
+    const T e = s_c[tid];
+    const int base = q * g.ls;
+    if (regs) {
+#pragma unroll
+      for (int u = 0; u < GL; ++u)
+        if (u < len) xo[base + (t0 + u + 1) * kLineM * g.es] = fma(Q[t0 + u], e, hv[u]);
+    } else {
+      for (int t = t0; t < t1; ++t) xo[base + (t + 1) * kLineM * g.es] = fma(Q[t], e, h[t]);
+    }
   }
 }
 
@@ -343,6 +354,22 @@ __global__ void __launch_bounds__(kBT) k_line_factor_seps(LevelV<T> L, int* derr
     up = u;
     uprev_coupling = hi;
   }
+  // products of the stored multipliers over each group: P from the group's
+  // start to t, Q from t to the group's end
+  const int gl = L.sgl[DIR];
+  T* mu = L.SP[DIR][SP_MU] + q * L.spp[DIR];
+  T* ca = L.SP[DIR][SP_CA] + q * L.spp[DIR];
+  T* P = L.SP[DIR][SP_P] + q * L.spp[DIR];
+  T* Q = L.SP[DIR][SP_Q] + q * L.spp[DIR];
+  double pr = 1.0;
+  for (int t = 0; t < nsep; ++t) {
+    pr = (t % gl == 0 ? 1.0 : pr) * double(mu[t]);
+    P[t] = T(pr);
+  }
+  for (int t = nsep - 1; t >= 0; --t) {
+    pr = (t == nsep - 1 || (t + 1) % gl == 0 ? 1.0 : pr) * double(ca[t]);
+    Q[t] = T(pr);
+  }
   if (bad) atomicOr(derr, DEV_BADLINE);
 }
 
@@ -364,8 +391,11 @@ void line_step(const LevelV<T>& L, int colour, const T* xs, T* xo, cudaStream_t 
     const int fast = nlc, slow = nb;
     k_line_blocks<T, DIR><<<dim3(cdiv(fast, kBT), grid_y(slow)), kBT, 0, s>>>(L, colour);
   }
-  if (g.n >= kLineM)
-    k_line_seps<T, DIR><<<cdiv(nlc, kSepLines), kSepThreads, 0, s>>>(L, colour, xo);
+  if (g.n >= kLineM) {
+    const int nsep = g.n / kLineM, ngroups = cdiv(nsep, L.sgl[DIR]);
+    const int lpb = kSepThreads / ngroups;
+    k_line_seps<T, DIR><<<cdiv(nlc, lpb), kSepThreads, 0, s>>>(L, colour, ngroups, xo);
+  }
   {
     const int fast = DIR == 0 ? g.n : nlc, slow = DIR == 0 ? nlc : g.n;
     k_line_final<T, DIR><<<dim3(cdiv(fast, kPT), grid_y(slow)), kPT, 0, s>>>(L, colour, xo);

@@ -173,34 +173,64 @@ __device__ __forceinline__ void line_block_solve(const LevelV<T>& L, int q, int 
   }
 }
 
-// Step 2 for line q by one thread: the Schur right-hand side of separator s
-// is (d_s + a_s g_{s-1}) + a_{s+1} g_{s+1} (a_{n+1} = 0 and the ghost of G is
-// 0); forward substitution (y overwrites d_s in G), then back substitution
-// writing the separator values into xo.  The Schur factors are the compact
-// per-separator arrays.
+// Step 2, the Schur system on the separators of a line, tridiagonal with
+// precomputed LU factors: forward y_t = mu_t y_{t-1} + rhs_t, back
+// x_t = ca_t x_{t+1} + y_t / u_t.  A chain of FP64 fused multiply-adds is
+// latency-bound, so each substitution runs in two levels: the separators
+// form groups of sgl; every group substitutes from a zero carry (yh, xh);
+// the carries between groups follow serially (one step per group, using the
+// products P and Q of the group's multipliers); a fix-up adds each group's
+// carry times P or Q.  Every implementation (one thread per line here, one
+// thread per group in the full-grid kernel) performs these same operations:
+//   rhs_t = (d_s + a_s g_{s-1}) + a_{s+1} g_{s+1}  (a_{n+1} = 0, ghost G = 0)
+//   yh_t  = fma(mu_t, yh_{t-1}, rhs_t),  yh = 0 before a group
+//   c_0 = 0,  c_{g+1} = fma(P_end(g), c_g, yh_end(g))
+//   a_t   = fma(P_t, c_g, yh_t) * iu_t
+//   xh_t  = fma(ca_t, xh_{t+1}, a_t),    xh = 0 after a group
+//   e_{G-1} = 0,  e_{g-1} = fma(Q_start(g), e_g, xh_start(g))
+//   x_t   = fma(Q_t, e_g, xh_t).
 template <typename T, int DIR>
 __device__ void line_sep_serial(const LevelV<T>& L, int q, T* __restrict__ xo) {
   const LineGeo g = line_geo<DIR>(L);
   const int nsep = g.n / kLineM;
-  const T* __restrict__ mu = L.SP[DIR][SP_MU] + q * L.spp[DIR];
-  const T* __restrict__ iu = L.SP[DIR][SP_IU] + q * L.spp[DIR];
-  const T* __restrict__ ca = L.SP[DIR][SP_CA] + q * L.spp[DIR];
+  if (nsep == 0) return;
+  const int sp = q * L.spp[DIR];
+  const T* __restrict__ mu = L.SP[DIR][SP_MU] + sp;
+  const T* __restrict__ iu = L.SP[DIR][SP_IU] + sp;
+  const T* __restrict__ ca = L.SP[DIR][SP_CA] + sp;
+  const T* __restrict__ P = L.SP[DIR][SP_P] + sp;
+  const T* __restrict__ Q = L.SP[DIR][SP_Q] + sp;
+  T* h = L.SP[DIR][SP_RL] + sp;         // partial values
   const T* A = line_coupling<DIR>(L);
-  T* G = line_scratch<DIR>(L);
-  const int base = q * g.ls, fb = line_fbase<DIR>(L, q);
-  T y = T(0);
-  for (int t = 0; t < nsep; ++t) {
-    const int ks = (t + 1) * kLineM;
-    const int os = base + ks * g.es, fs = fb + ks * g.fes;
-    const T r = fma(A[os], G[fs - g.fes], G[fs]);
-    y = fma(mu[t], y, fma(A[os + g.es], G[fs + g.fes], r));
-    G[fs] = y;
+  const T* G = line_scratch<DIR>(L);
+  const int base = q * g.ls, fb = line_fbase<DIR>(L, q), gl = L.sgl[DIR];
+  // forward, group by group, then each group's carry, fix-up and backward
+  // partial substitution
+  T c = T(0);
+  for (int t0 = 0; t0 < nsep; t0 += gl) {
+    const int t1 = min(t0 + gl, nsep);
+    T yh = T(0);
+    for (int t = t0; t < t1; ++t) {
+      const int ks = (t + 1) * kLineM;
+      const int os = base + ks * g.es, fs = fb + ks * g.fes;
+      const T r = fma(A[os], G[fs - g.fes], G[fs]);
+      yh = fma(mu[t], yh, fma(A[os + g.es], G[fs + g.fes], r));
+      h[t] = yh;
+    }
+    const T cg = c;
+    c = fma(P[t1 - 1], cg, yh);
+    T xh = T(0);
+    for (int t = t1 - 1; t >= t0; --t) {
+      xh = fma(ca[t], xh, fma(P[t], cg, h[t]) * iu[t]);
+      h[t] = xh;
+    }
   }
-  T xn = T(0);
-  for (int t = nsep - 1; t >= 0; --t) {
-    const int ks = (t + 1) * kLineM;
-    xn = fma(ca[t], xn, G[fb + ks * g.fes] * iu[t]);
-    xo[base + ks * g.es] = xn;
+  // backward carries and fix-up, last group first
+  T e = T(0);
+  for (int t0 = (nsep - 1) / gl * gl; t0 >= 0; t0 -= gl) {
+    const int t1 = min(t0 + gl, nsep);
+    for (int t = t0; t < t1; ++t) xo[base + (t + 1) * kLineM * g.es] = fma(Q[t], e, h[t]);
+    e = fma(Q[t0], e, h[t0]);
   }
 }
 
