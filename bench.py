@@ -656,6 +656,23 @@ def batch_leg(bm, torch, dev, stream, count=512):
     return out
 
 
+def run_leg(name):
+    """One of the extra legs alone, on cuda:0 (profiling and single-feature
+    measurements)."""
+    import torch
+    import paper_1803_02481_gb300 as bm
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    if name == "line_smoother":
+        out = line_smoother_leg(bm, torch, dev, stream, load_peaks()[0])
+    elif name == "paper_workload":
+        out = paper_workload_leg(bm, torch, dev, stream)
+    else:
+        out = paper_workload_leg(bm, torch, dev, stream, nx=9088, ny=568)
+    print(json.dumps({"leg": name, **out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -673,7 +690,13 @@ def main():
                     help="profiling run: allow stopping at --max-cycles, skip the extra legs")
     ap.add_argument("--quick", action="store_true", help="skip the e2e, fp32 and CPU legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--only", default=None,
+                    choices=["line_smoother", "paper_workload", "paper_workload_9088x568"],
+                    help="run one measurement leg alone and print its JSON (no headline line)")
     args = ap.parse_args()
+    if args.only is not None:
+        run_leg(args.only)
+        return
     if args.profile:
         args.quick = True
     rank = int(os.environ.get("RANK", "0"))
