@@ -17,7 +17,8 @@ from . import build as _build
 __all__ = [
     "BMG_OK", "BMG_EINVAL", "BMG_ENOMEM", "BMG_ECUDA", "BMG_ENOCONV", "BMG_ENAN", "BMG_ETIMEOUT",
     "BMG_FP64", "BMG_FP32_REFINE", "BoxMGError", "Options", "Info", "lib", "library_path",
-    "default_options", "setup", "Hierarchy", "solve_host", "EXPORTED",
+    "default_options", "setup", "Hierarchy", "solve_host", "EXPORTED", "EXPORTED3", "setup3",
+    "Hierarchy3", "STENCIL3_OFFSETS",
 ]
 
 BMG_OK, BMG_EINVAL, BMG_ENOMEM, BMG_ECUDA, BMG_ENOCONV, BMG_ENAN, BMG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
@@ -92,6 +93,17 @@ EXPORTED = {
     "bmg_profile_read": (_i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
 }
 
+# every symbol include/boxmg3d.h declares
+EXPORTED3 = {
+    "bmg3_setup": (_i, [_vp, _i, _i, _i, ctypes.POINTER(Options), _vp, _HP]),
+    "bmg3_solve": (_i, [_vp, _vp, _vp, _d, ctypes.POINTER(Info), _vp]),
+    "bmg3_destroy": (None, [_vp]),
+    "bmg3_num_levels": (_i, [_vp, ctypes.POINTER(_i)]),
+    "bmg3_level_shape": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "bmg3_level_stencil": (_i, [_vp, _i, _vp]),
+    "bmg3_level_interp": (_i, [_vp, _i, _vp]),
+}
+
 PROF_CLASSES = {"fine_smooth": 1, "fine_resid": 2, "fine_interp": 3, "coarse_kernel": 4,
                 "other_levels": 5, "norm": 6, "vcycle": 7, "krylov": 8}
 
@@ -147,7 +159,7 @@ def lib() -> ctypes.CDLL:
         if not os.path.exists(path):
             raise RuntimeError(f"{path} is not built; call paper_1803_02481_gb300.build.build()")
         cdll = ctypes.CDLL(path)
-        for name, (res, args) in EXPORTED.items():
+        for name, (res, args) in {**EXPORTED, **EXPORTED3}.items():
             fn = getattr(cdll, name)
             fn.restype = res
             fn.argtypes = args
@@ -313,6 +325,77 @@ def setup(k, options: Options | None = None, stream=None) -> Hierarchy:
     _check(lib().bmg_setup(_dev(k, "k"), nx, ny, ctypes.byref(options), _stream(stream), ctypes.byref(h)),
            "bmg_setup")
     return Hierarchy(h, nx, ny, options)
+
+
+class Hierarchy3:
+    """A 3D BoxMG hierarchy (wraps ``bmg3_*``, include/boxmg3d.h)."""
+
+    def __init__(self, h, nx, ny, nz):
+        self._h, self.nx, self.ny, self.nz = h, nx, ny, nz
+
+    def solve(self, b, x=None, tol=1e-10, stream=None, allow_noconv=False):
+        """Solve A x = b (b, x: (nz, ny, nx) float64 CUDA tensors; x is the
+        initial guess, zero if None, overwritten).  Returns (x, Info)."""
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        info = Info()
+        ok = (BMG_OK, BMG_ENOCONV) if allow_noconv else (BMG_OK,)
+        _check(lib().bmg3_solve(self._h, _dev(b, "b"), _dev(x, "x"), float(tol), ctypes.byref(info),
+                                _stream(stream)), "bmg3_solve", ok)
+        return x, info
+
+    @property
+    def nlevels(self) -> int:
+        n = ctypes.c_int()
+        _check(lib().bmg3_num_levels(self._h, ctypes.byref(n)), "bmg3_num_levels")
+        return n.value
+
+    def level_shape(self, level: int):
+        nx, ny, nz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().bmg3_level_shape(self._h, level, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nz)),
+               "bmg3_level_shape")
+        return nx.value, ny.value, nz.value
+
+    def level_stencil(self, level: int) -> np.ndarray:
+        """(14, nz, ny, nx): C, then the negated couplings of the 13 negative
+        offsets in the order STENCIL3_OFFSETS."""
+        nx, ny, nz = self.level_shape(level)
+        out = np.zeros((14, nz, ny, nx))
+        _check(lib().bmg3_level_stencil(self._h, level, out.ctypes.data_as(ctypes.c_void_p)),
+               "bmg3_level_stencil")
+        return out
+
+    def level_interp(self, level: int) -> np.ndarray:
+        """(8, nz, ny, nx): weights of each point of level `level` to its
+        parents, plane 4 cz + 2 cy + cx."""
+        nx, ny, nz = self.level_shape(level)
+        out = np.zeros((8, nz, ny, nx))
+        _check(lib().bmg3_level_interp(self._h, level, out.ctypes.data_as(ctypes.c_void_p)),
+               "bmg3_level_interp")
+        return out
+
+    def destroy(self):
+        if self._h:
+            lib().bmg3_destroy(self._h)
+            self._h = None
+
+
+# (di, dj, dk) of the 13 stored couplings of a 3D level, in storage order
+STENCIL3_OFFSETS = ([(di, dj, -1) for dj in (-1, 0, 1) for di in (-1, 0, 1)]
+                    + [(di, -1, 0) for di in (-1, 0, 1)] + [(-1, 0, 0)])
+
+
+def setup3(k, options: Options | None = None, stream=None) -> Hierarchy3:
+    """3D BoxMG setup from cell coefficients k ((nz, ny, nx) float64 CUDA
+    tensor)."""
+    if options is None:
+        options = default_options()
+    nz, ny, nx = k.shape
+    h = ctypes.c_void_p()
+    _check(lib().bmg3_setup(_dev(k, "k"), nx, ny, nz, ctypes.byref(options), _stream(stream),
+                            ctypes.byref(h)), "bmg3_setup")
+    return Hierarchy3(h, nx, ny, nz)
 
 
 class Batch:

@@ -1,0 +1,832 @@
+// 3D BoxMG V-cycle (include/boxmg3d.h): assembly, operator-induced
+// interpolation, Galerkin coarse operators, multicolour Gauss-Seidel,
+// residual, restriction, interpolation, dense coarsest solve, and the solve
+// loop as one CUDA graph per cycle.
+//
+// Layout: every grid quantity is a plane of (nz + 2) x (ny + 2) rows of px
+// doubles with a one-cell zero ghost layer; point (i, j, k) (1-based) at
+// (k * (ny + 2) + j) * px + i, px >= nx + 2 a multiple of 16 (128-byte rows).
+// An operator is symmetric: its diagonal C, 1/C, and the negated
+// off-diagonals a_d = -A[p, p + d] for the 13 "negative" offsets d (dk = -1;
+// or dk = 0, dj = -1; or (-1, 0, 0)); the coupling to +d is a_{-d} of the
+// neighbour at p + d.  Couplings to points outside the grid are 0.
+// Interpolation into a level: 8 planes on that level's grid, the weight of
+// each fine point to its parent corners (plane 4 cz + 2 cy + cx; per
+// direction a fine point at odd 1-based i has parents (i-1)/2 (c = 0) and
+// (i+1)/2 (c = 1), at even i the single parent i/2 (c = 0)).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "bmg_internal.h"
+#include "boxmg3d.h"
+
+namespace bmg3 {
+
+using bmg::count_launch;
+using bmg::set_last_error;
+
+constexpr int NA = 13;    // stored couplings per point
+constexpr int NPW3 = 8;   // interpolation weight planes
+constexpr int kT = 128;   // threads along x
+constexpr int kNormBlocks = 4 * 152;
+constexpr int kNormThreads = 256;
+
+struct Lev3 {
+  int nx, ny, nz, px, py;
+  double *C, *iC, *A[NA];
+  double *x, *b, *r;
+  double *P[NPW3];
+};
+
+__host__ __device__ __forceinline__ int off3(const Lev3& L, int di, int dj, int dk) {
+  return (dk * L.py + dj) * L.px + di;
+}
+__host__ __device__ __forceinline__ int idx3(const Lev3& L, int i, int j, int k) {
+  return (k * L.py + j) * L.px + i;
+}
+__host__ __device__ __forceinline__ bool is_neg(int di, int dj, int dk) {
+  return dk < 0 || (dk == 0 && (dj < 0 || (dj == 0 && di < 0)));
+}
+// storage index of a negative offset
+__host__ __device__ __forceinline__ int neg_index(int di, int dj, int dk) {
+  if (dk == -1) return (dj + 1) * 3 + (di + 1);
+  if (dj == -1) return 9 + (di + 1);
+  return 12;
+}
+// a_d at point o (negated off-diagonal to o + d)
+__device__ __forceinline__ double coupling(const Lev3& L, int o, int di, int dj, int dk) {
+  if (is_neg(di, dj, dk)) return L.A[neg_index(di, dj, dk)][o];
+  return L.A[neg_index(-di, -dj, -dk)][o + off3(L, di, dj, dk)];
+}
+
+enum { E3_BADK = 1, E3_BADDEN = 2, E3_NOTSPD = 4 };
+
+// ---------------------------------------------------------------------------
+// Assembly: harmonic faces, 2k on boundary faces; the diagonal summed in the
+// order x faces (east, west, west wall, east wall), then y, then z.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double hmean(double lo, double hi) { return 2.0 * lo * hi / (lo + hi); }
+
+__global__ void k3_assemble(const double* __restrict__ k, Lev3 L, int* err) {
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x, j0 = blockIdx.y, k0 = blockIdx.z;
+  if (i0 >= L.nx) return;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const size_t sxy = size_t(nx) * ny;
+  const size_t q = size_t(k0) * sxy + size_t(j0) * nx + i0;
+  const double kc = k[q];
+  if (!(kc > 0.0) || !(kc < INFINITY)) atomicOr(err, E3_BADK);
+  const double aE = i0 < nx - 1 ? hmean(kc, k[q + 1]) : 0.0;
+  const double aW = i0 > 0 ? hmean(k[q - 1], kc) : 0.0;
+  const double aN = j0 < ny - 1 ? hmean(kc, k[q + nx]) : 0.0;
+  const double aS = j0 > 0 ? hmean(k[q - nx], kc) : 0.0;
+  const double aU = k0 < nz - 1 ? hmean(kc, k[q + sxy]) : 0.0;
+  const double aD = k0 > 0 ? hmean(k[q - sxy], kc) : 0.0;
+  double c = 0.0;
+  c = __dadd_rn(c, aE);
+  c = __dadd_rn(c, aW);
+  c = __dadd_rn(c, i0 == 0 ? 2.0 * kc : 0.0);
+  c = __dadd_rn(c, i0 == nx - 1 ? 2.0 * kc : 0.0);
+  c = __dadd_rn(c, aN);
+  c = __dadd_rn(c, aS);
+  c = __dadd_rn(c, j0 == 0 ? 2.0 * kc : 0.0);
+  c = __dadd_rn(c, j0 == ny - 1 ? 2.0 * kc : 0.0);
+  c = __dadd_rn(c, aU);
+  c = __dadd_rn(c, aD);
+  c = __dadd_rn(c, k0 == 0 ? 2.0 * kc : 0.0);
+  c = __dadd_rn(c, k0 == nz - 1 ? 2.0 * kc : 0.0);
+  const int o = idx3(L, i0 + 1, j0 + 1, k0 + 1);
+  L.C[o] = c;
+  L.iC[o] = 1.0 / c;
+  L.A[neg_index(-1, 0, 0)][o] = aW;
+  L.A[neg_index(0, -1, 0)][o] = aS;
+  L.A[neg_index(0, 0, -1)][o] = aD;
+}
+
+// ---------------------------------------------------------------------------
+// Interpolation weights of the fine level F, one pass per number of
+// directions in which a point lies between coarse points (0: coarse points,
+// 1: edge, 2: face, 3: cell centre points; each pass reads the weights of
+// the passes before it).  Operation order as the oracle's: couplings in
+// offset order (dk, dj, di) ascending, products and sums unfused.
+// ---------------------------------------------------------------------------
+
+__global__ void k3_interp_weights(Lev3 F, int pass, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
+  if (i > F.nx) return;
+  const int fr[3] = {i & 1, j & 1, k & 1};    // 1: between coarse points in that direction
+  const int nb = fr[0] + fr[1] + fr[2];
+  if (nb != pass) return;
+  const int o = idx3(F, i, j, k);
+  if (nb == 0) {
+    F.P[0][o] = 1.0;
+    return;
+  }
+  // couplings with the lumping of non-M-matrix rows
+  double a[27];
+  const double C = F.C[o];
+  double sum = 0.0, neg = 0.0;
+  for (int dk = -1; dk <= 1; ++dk)
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        const int t = (dk + 1) * 9 + (dj + 1) * 3 + (di + 1);
+        if (t == 13) {
+          a[t] = 0.0;
+          continue;
+        }
+        const double v = coupling(F, o, di, dj, dk);
+        sum = __dadd_rn(sum, v);
+        neg = __dadd_rn(neg, fmin(v, 0.0));
+        a[t] = fmax(v, 0.0);
+      }
+  const double sigma = __dsub_rn(C, sum);
+  const double ceff = __dsub_rn(__dsub_rn(C, neg), fmin(sigma, 0.0));
+  // collapse the directions the point is coarse-aligned in
+  double coll[27];
+  for (int t = 0; t < 27; ++t) coll[t] = 0.0;
+  double den = ceff;
+  for (int dk = -1; dk <= 1; ++dk)
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        const int t = (dk + 1) * 9 + (dj + 1) * 3 + (di + 1);
+        if (t == 13) continue;
+        const int pi = fr[0] ? di : 0, pj = fr[1] ? dj : 0, pk = fr[2] ? dk : 0;
+        const int tp = (pk + 1) * 9 + (pj + 1) * 3 + (pi + 1);
+        if (tp == 13)
+          den = __dsub_rn(den, a[t]);
+        else
+          coll[tp] = __dadd_rn(coll[tp], a[t]);
+      }
+  if (!(den > 0.0)) {
+    atomicOr(err, E3_BADDEN);
+    return;
+  }
+  // weight to each parent: sum over collapsed neighbours of coll times the
+  // neighbour's weight to the same coarse point
+  for (int m = 0; m < NPW3; ++m) {
+    const int mc[3] = {m & 1, (m >> 1) & 1, (m >> 2) & 1};
+    if ((mc[0] && !fr[0]) || (mc[1] && !fr[1]) || (mc[2] && !fr[2])) continue;
+    double w = 0.0;
+    for (int dk = -1; dk <= 1; ++dk)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          const int t = (dk + 1) * 9 + (dj + 1) * 3 + (di + 1);
+          if (t == 13 || coll[t] == 0.0) continue;
+          const int dd[3] = {di, dj, dk};
+          int gslot = 0;
+          bool ok = true;
+          for (int s = 0; s < 3; ++s) {
+            if (!fr[s]) continue;                      // dd[s] == 0 here
+            if (dd[s] == -1) ok = ok && mc[s] == 0;    // neighbour at the lower parent
+            else if (dd[s] == 1) ok = ok && mc[s] == 1;
+            else gslot |= mc[s] << s;                  // still between: same parent
+          }
+          if (!ok) continue;
+          const double wn = F.P[gslot][o + off3(F, di, dj, dk)];
+          w = __dadd_rn(w, __dmul_rn(coll[t], wn));
+        }
+    F.P[m][o] = w / den;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin product: one thread per coarse point computes its 14 stored
+// entries from the definition A_c(I, I + d) = sum_f sum_g P(f, I) A(f, g)
+// P(g, I + d) over fine f in the support of I and g in that of I + d.
+// ---------------------------------------------------------------------------
+
+// slot of fine point 2 I + e (e in -1..1 per direction) for parent I
+__device__ __forceinline__ int support_slot(int ex, int ey, int ez) {
+  return (ex == -1 ? 1 : 0) | ((ey == -1 ? 1 : 0) << 1) | ((ez == -1 ? 1 : 0) << 2);
+}
+
+__global__ void k3_rap(Lev3 F, Lev3 Cc, int* err) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x + 1, J = blockIdx.y + 1, K = blockIdx.z + 1;
+  if (I > Cc.nx) return;
+  const int oc = idx3(Cc, I, J, K);
+  for (int e = 0; e < 14; ++e) {
+    int di = 0, dj = 0, dk = 0;
+    if (e > 0) {
+      const int m = e - 1;
+      if (m < 9) {
+        dk = -1;
+        dj = m / 3 - 1;
+        di = m % 3 - 1;
+      } else if (m < 12) {
+        dj = -1;
+        di = m - 10;
+      } else {
+        di = -1;
+      }
+    }
+    const int I2 = I + di, J2 = J + dj, K2 = K + dk;
+    double val = 0.0;
+    if (I2 >= 1 && J2 >= 1 && K2 >= 1 && I2 <= Cc.nx && J2 <= Cc.ny && K2 <= Cc.nz) {
+      for (int ez = -1; ez <= 1; ++ez)
+        for (int ey = -1; ey <= 1; ++ey)
+          for (int ex = -1; ex <= 1; ++ex) {
+            const int fi = 2 * I + ex, fj = 2 * J + ey, fk = 2 * K + ez;
+            if (fi > F.nx || fj > F.ny || fk > F.nz) continue;
+            const int of = idx3(F, fi, fj, fk);
+            const double wf = F.P[support_slot(ex, ey, ez)][of];
+            if (wf == 0.0) continue;
+            double s = 0.0;
+            for (int hz = -1; hz <= 1; ++hz)
+              for (int hy = -1; hy <= 1; ++hy)
+                for (int hx = -1; hx <= 1; ++hx) {
+                  const int gx = ex + hx - 2 * di, gy = ey + hy - 2 * dj, gz = ez + hz - 2 * dk;
+                  if (gx < -1 || gx > 1 || gy < -1 || gy > 1 || gz < -1 || gz > 1) continue;
+                  const int gi = fi + hx, gj = fj + hy, gk = fk + hz;
+                  if (gi < 1 || gj < 1 || gk < 1 || gi > F.nx || gj > F.ny || gk > F.nz) continue;
+                  const int og = idx3(F, gi, gj, gk);
+                  const double wg = F.P[support_slot(gx, gy, gz)][og];
+                  if (wg == 0.0) continue;
+                  const double afg =
+                      (hx | hy | hz) == 0 ? F.C[of] : -coupling(F, of, hx, hy, hz);
+                  s = fma(afg, wg, s);
+                }
+            val = fma(wf, s, val);
+          }
+    }
+    if (e == 0) {
+      if (!(val > 0.0) || !(val < INFINITY)) atomicOr(err, E3_NOTSPD);
+      Cc.C[oc] = val;
+      Cc.iC[oc] = 1.0 / val;
+    } else {
+      Cc.A[e - 1][oc] = -val;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Smoothing, residual, restriction, interpolation
+// ---------------------------------------------------------------------------
+
+template <bool SEVEN>
+__device__ __forceinline__ double nb_sum(const Lev3& L, const double* __restrict__ x, int o) {
+  double s = 0.0;
+  if (SEVEN) {
+    const int sx = 1, sy = L.px, sz = L.py * L.px;
+    s = fma(L.A[12][o], x[o - sx], s);
+    s = fma(L.A[12][o + sx], x[o + sx], s);
+    s = fma(L.A[10][o], x[o - sy], s);
+    s = fma(L.A[10][o + sy], x[o + sy], s);
+    s = fma(L.A[4][o], x[o - sz], s);
+    s = fma(L.A[4][o + sz], x[o + sz], s);
+  } else {
+#pragma unroll
+    for (int dk = -1; dk <= 1; ++dk)
+#pragma unroll
+      for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+        for (int di = -1; di <= 1; ++di) {
+          if (di == 0 && dj == 0 && dk == 0) continue;
+          const int d = off3(L, di, dj, dk);
+          s = fma(coupling(L, o, di, dj, dk), x[o + d], s);
+        }
+  }
+  return s;
+}
+
+// One colour of a sweep, in place.  SEVEN: red-black, colour (i + j + k)
+// parity (0-based); else colour 4 (k mod 2) + 2 (j mod 2) + (i mod 2).
+template <bool SEVEN>
+__global__ void k3_gs(Lev3 L, int colour) {
+  const int ih = blockIdx.x * blockDim.x + threadIdx.x;
+  int i0, j0, k0;
+  if (SEVEN) {
+    j0 = blockIdx.y;
+    k0 = blockIdx.z;
+    i0 = 2 * ih + ((j0 + k0 + colour) & 1);
+  } else {
+    j0 = 2 * blockIdx.y + ((colour >> 1) & 1);
+    k0 = 2 * blockIdx.z + (colour >> 2);
+    i0 = 2 * ih + (colour & 1);
+  }
+  if (i0 >= L.nx || j0 >= L.ny || k0 >= L.nz) return;
+  const int o = idx3(L, i0 + 1, j0 + 1, k0 + 1);
+  L.x[o] = (L.b[o] + nb_sum<SEVEN>(L, L.x, o)) * L.iC[o];
+}
+
+template <bool SEVEN>
+__global__ void k3_residual(Lev3 L) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
+  if (i > L.nx) return;
+  const int o = idx3(L, i, j, k);
+  L.r[o] = fma(-L.C[o], L.x[o], L.b[o]) + nb_sum<SEVEN>(L, L.x, o);
+}
+
+// b_c(I) = sum over the fine support of I of P(f, I) r(f); x_c = 0.
+__global__ void k3_restrict(Lev3 F, Lev3 Cc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x + 1, J = blockIdx.y + 1, K = blockIdx.z + 1;
+  if (I > Cc.nx) return;
+  double s = 0.0;
+  for (int ez = -1; ez <= 1; ++ez)
+    for (int ey = -1; ey <= 1; ++ey)
+      for (int ex = -1; ex <= 1; ++ex) {
+        const int fi = 2 * I + ex, fj = 2 * J + ey, fk = 2 * K + ez;
+        if (fi > F.nx || fj > F.ny || fk > F.nz) continue;
+        const int of = idx3(F, fi, fj, fk);
+        s = fma(F.P[support_slot(ex, ey, ez)][of], F.r[of], s);
+      }
+  const int oc = idx3(Cc, I, J, K);
+  Cc.b[oc] = s;
+  Cc.x[oc] = 0.0;
+}
+
+// x(f) += sum over f's parents of P(f, I) x_c(I).
+__global__ void k3_interp(Lev3 F, Lev3 Cc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
+  if (i > F.nx) return;
+  const int o = idx3(F, i, j, k);
+  double s = 0.0;
+  for (int m = 0; m < NPW3; ++m) {
+    const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
+    if ((cx && !(i & 1)) || (cy && !(j & 1)) || (cz && !(k & 1))) continue;
+    const int I = (i & 1) ? (i - 1) / 2 + cx : i / 2;
+    const int J = (j & 1) ? (j - 1) / 2 + cy : j / 2;
+    const int K = (k & 1) ? (k - 1) / 2 + cz : k / 2;
+    s = fma(F.P[m][o], Cc.x[idx3(Cc, I, J, K)], s);
+  }
+  F.x[o] += s;
+}
+
+// ---------------------------------------------------------------------------
+// Norms (fixed grid, fixed order: deterministic) and the stop test
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[kNormThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  v = lane < kNormThreads / 32 ? red[lane] : 0.0;
+  if (w == 0)
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// what 0: ||b||^2; 1: ||b - A x||^2 (7-point finest level)
+__global__ void k3_norm(Lev3 L, int what, double* __restrict__ partials) {
+  double acc = 0.0;
+  const int n = L.nx * L.ny * L.nz;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int i = t % L.nx + 1, rest = t / L.nx, j = rest % L.ny + 1, k = rest / L.ny + 1;
+    const int o = idx3(L, i, j, k);
+    double v = L.b[o];
+    if (what) v = fma(-L.C[o], L.x[o], v) + nb_sum<true>(L, L.x, o);
+    acc = fma(v, v, acc);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+struct Scal3 {
+  double bnorm2, rnorm2;
+  int err;                  // E3_* bits set by setup kernels
+};
+
+__global__ void k3_norm_final(const double* __restrict__ partials, int n, Scal3* sc, int what) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    if (what)
+      sc->rnorm2 = acc;
+    else
+      sc->bnorm2 = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: dense matrix and Cholesky factor (one block), solve
+// ---------------------------------------------------------------------------
+
+__global__ void k3_coarse_factor(Lev3 L0, double* __restrict__ lo, double* __restrict__ idiag,
+                                 int* err) {
+  const int nx = L0.nx, ny = L0.ny, n = nx * L0.ny * L0.nz;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) lo[e] = 0.0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int i = r % nx + 1, j = (r / nx) % ny + 1, k = r / (nx * ny) + 1;
+    const int o = idx3(L0, i, j, k);
+    lo[size_t(r) * n + r] = L0.C[o];
+    for (int dk = -1; dk <= 1; ++dk)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          if ((di | dj | dk) == 0) continue;
+          const int i2 = i + di, j2 = j + dj, k2 = k + dk;
+          if (i2 < 1 || j2 < 1 || k2 < 1 || i2 > nx || j2 > ny || k2 > L0.nz) continue;
+          const int c = ((k2 - 1) * ny + (j2 - 1)) * nx + (i2 - 1);
+          lo[size_t(r) * n + c] = -coupling(L0, o, di, dj, dk);
+        }
+  }
+  __syncthreads();
+  // right-looking Cholesky, lower triangle, row-major
+  for (int c = 0; c < n; ++c) {
+    __shared__ double piv;
+    if (threadIdx.x == 0) {
+      const double d = lo[size_t(c) * n + c];
+      if (!(d > 0.0)) atomicOr(err, E3_NOTSPD);
+      piv = sqrt(fmax(d, 1e-300));
+      lo[size_t(c) * n + c] = piv;
+      idiag[c] = 1.0 / piv;
+    }
+    __syncthreads();
+    for (int r = c + 1 + threadIdx.x; r < n; r += blockDim.x) lo[size_t(r) * n + c] /= piv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < (n - c - 1) * (n - c - 1); e += blockDim.x) {
+      const int r = c + 1 + e / (n - c - 1), q = c + 1 + e % (n - c - 1);
+      if (q <= r) lo[size_t(r) * n + q] -= lo[size_t(r) * n + c] * lo[size_t(q) * n + c];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k3_coarse_solve(Lev3 L0, const double* __restrict__ lo,
+                                const double* __restrict__ idiag) {
+  __shared__ double v[BMG_MAX_COARSEST];
+  const int nx = L0.nx, ny = L0.ny, n = nx * ny * L0.nz;
+  for (int r = threadIdx.x; r < n; r += blockDim.x)
+    v[r] = L0.b[idx3(L0, r % nx + 1, (r / nx) % ny + 1, r / (nx * ny) + 1)];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const double y = v[j] * idiag[j];
+    __syncthreads();
+    if (threadIdx.x == 0) v[j] = y;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) v[i] = fma(-lo[size_t(i) * n + j], y, v[i]);
+    __syncthreads();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const double xj = v[j] * idiag[j];
+    __syncthreads();
+    if (threadIdx.x == 0) v[j] = xj;
+    for (int i = threadIdx.x; i < j; i += blockDim.x) v[i] = fma(-lo[size_t(j) * n + i], xj, v[i]);
+    __syncthreads();
+  }
+  for (int r = threadIdx.x; r < n; r += blockDim.x)
+    L0.x[idx3(L0, r % nx + 1, (r / nx) % ny + 1, r / (nx * ny) + 1)] = v[r];
+}
+
+// dense (nz, ny, nx) <-> plane interior
+__global__ void k3_pack(const double* __restrict__ src, double* __restrict__ dst, Lev3 L) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= L.nx) return;
+  dst[idx3(L, i + 1, j + 1, k + 1)] = src[(size_t(k) * L.ny + j) * L.nx + i];
+}
+__global__ void k3_unpack(const double* __restrict__ src, double* __restrict__ dst, Lev3 L) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= L.nx) return;
+  dst[(size_t(k) * L.ny + j) * L.nx + i] = src[idx3(L, i + 1, j + 1, k + 1)];
+}
+
+inline int cdiv(long a, long b) { return int((a + b - 1) / b); }
+inline dim3 grid_pts(const Lev3& L) { return dim3(cdiv(L.nx, kT), L.ny, L.nz); }
+
+}  // namespace bmg3
+
+using namespace bmg3;
+
+struct bmg3_hierarchy {
+  int L = 0;
+  bmg_options opt{};
+  std::vector<Lev3> lv;           // lv[0] coarsest ... lv[L-1] finest
+  void* arena = nullptr;
+  double *chol = nullptr, *chol_idiag = nullptr, *partials = nullptr;
+  Scal3* sc = nullptr;
+  Scal3* sc_host = nullptr;
+  int* err = nullptr;
+  int n0 = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t gstream = nullptr;   // stream the graph was built for
+  double setup_ms = 0.0;
+};
+
+namespace {
+
+double now_ms() {
+  using clk = std::chrono::steady_clock;
+  return std::chrono::duration<double, std::milli>(clk::now().time_since_epoch()).count();
+}
+
+void free3(bmg3_hierarchy* h) {
+  if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->arena) cudaFree(h->arena);
+  if (h->sc_host) cudaFreeHost(h->sc_host);
+  delete h;
+}
+
+// One V(nu1, nu2) cycle (Algorithm 1), then ||b - A x||^2 of the finest level.
+void enqueue_cycle(bmg3_hierarchy* h, cudaStream_t s) {
+  const int L = h->L;
+  auto sweep = [&](int l, int nu, bool reverse) {
+    const Lev3& V = h->lv[l];
+    const bool seven = l == L - 1;
+    const int nc = seven ? 2 : 8;
+    for (int it = 0; it < nu; ++it) {
+      if (seven) bmg::prof_begin(BMG_PROF_FINE_SMOOTH, s);
+      for (int c0 = 0; c0 < nc; ++c0) {
+        const int c = reverse ? nc - 1 - c0 : c0;
+        if (seven)
+          k3_gs<true><<<dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), kT, 0, s>>>(V, c);
+        else
+          k3_gs<false><<<dim3(cdiv((V.nx + 1) / 2, kT), (V.ny + 1) / 2, (V.nz + 1) / 2), kT, 0, s>>>(V, c);
+        count_launch();
+      }
+      if (seven) bmg::prof_end(BMG_PROF_FINE_SMOOTH, s);
+    }
+  };
+  for (int l = L - 1; l >= 1; --l) {
+    const Lev3& V = h->lv[l];
+    sweep(l, h->opt.nu1, false);
+    if (l == L - 1)
+      k3_residual<true><<<grid_pts(V), kT, 0, s>>>(V);
+    else
+      k3_residual<false><<<grid_pts(V), kT, 0, s>>>(V);
+    k3_restrict<<<grid_pts(h->lv[l - 1]), kT, 0, s>>>(V, h->lv[l - 1]);
+    count_launch(2);
+  }
+  k3_coarse_solve<<<1, 256, 0, s>>>(h->lv[0], h->chol, h->chol_idiag);
+  count_launch();
+  for (int l = 1; l < L; ++l) {
+    k3_interp<<<grid_pts(h->lv[l]), kT, 0, s>>>(h->lv[l], h->lv[l - 1]);
+    count_launch();
+    sweep(l, h->opt.nu2, true);
+  }
+  k3_norm<<<kNormBlocks, kNormThreads, 0, s>>>(h->lv[L - 1], 1, h->partials);
+  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+  cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
+  count_launch(2);
+}
+
+int check_err(bmg3_hierarchy* h, cudaStream_t s) {
+  if (cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return BMG_ECUDA;
+  const int e = h->sc_host->err;
+  if (e & E3_BADK) {
+    set_last_error("3D setup: a coefficient k is not finite and positive");
+    return BMG_EINVAL;
+  }
+  if (e & E3_BADDEN) {
+    set_last_error("3D setup: an interpolation denominator is not positive");
+    return BMG_EINVAL;
+  }
+  if (e & E3_NOTSPD) {
+    set_last_error("3D setup: a coarse operator is not positive definite");
+    return BMG_EINVAL;
+  }
+  return BMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_in,
+               bmg_stream_t stream, bmg3_hierarchy** out) {
+  if (!out) return BMG_EINVAL;
+  *out = nullptr;
+  if (!k || nx < 2 || ny < 2 || nz < 2) return BMG_EINVAL;
+  bmg_options opt;
+  bmg_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.nu1 < 0 || opt.nu2 < 0 || opt.nu1 + opt.nu2 < 1 || opt.max_cycles < 0 ||
+      opt.precision != BMG_FP64 || opt.smoother != BMG_SMOOTH_POINT ||
+      opt.solver != BMG_SOLVER_VCYCLE || opt.interp_residual_term || opt.aniso_r != 1.0 ||
+      opt.cell_aspect != 1.0 || opt.bc_beta[0] >= 0.0 || opt.bc_beta[1] >= 0.0 ||
+      opt.bc_beta[2] >= 0.0 || opt.bc_beta[3] >= 0.0 || opt.log_coefficients) {
+    set_last_error("3D setup: options other than nu1, nu2 and max_cycles must be the defaults");
+    return BMG_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const double t0 = now_ms();
+  std::vector<int> sx{nx}, sy{ny}, sz{nz};
+  while (std::min({sx.back(), sy.back(), sz.back()}) > 3) {
+    sx.push_back(sx.back() / 2);
+    sy.push_back(sy.back() / 2);
+    sz.push_back(sz.back() / 2);
+  }
+  bmg3_hierarchy* h = new (std::nothrow) bmg3_hierarchy();
+  if (!h) return BMG_ENOMEM;
+  h->opt = opt;
+  h->L = int(sx.size());
+  const int L = h->L;
+  h->n0 = sx.back() * sy.back() * sz.back();
+  if (h->n0 > BMG_MAX_COARSEST) {
+    set_last_error("3D setup: the coarsest level would hold %d unknowns (at most %d)", h->n0,
+                   BMG_MAX_COARSEST);
+    delete h;
+    return BMG_EINVAL;
+  }
+  h->lv.assign(L, Lev3{});
+  // sizes, then one zeroed arena
+  size_t total = 0;
+  auto reserve = [&](size_t bytes) {
+    const size_t o = total;
+    total += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  std::vector<size_t> offs;
+  for (int l = 0; l < L; ++l) {
+    Lev3& V = h->lv[l];
+    const int src = L - 1 - l;
+    V.nx = sx[src];
+    V.ny = sy[src];
+    V.nz = sz[src];
+    V.px = (V.nx + 2 + 15) / 16 * 16;
+    V.py = V.ny + 2;
+    const size_t pb = size_t(V.nz + 2) * V.py * V.px * sizeof(double);
+    const int nplanes = 2 + NA + 3 + (l >= 1 ? NPW3 : 0);
+    for (int p = 0; p < nplanes; ++p) offs.push_back(reserve(pb));
+  }
+  const size_t o_chol = reserve(sizeof(double) * size_t(h->n0) * h->n0);
+  const size_t o_idiag = reserve(sizeof(double) * h->n0);
+  const size_t o_part = reserve(sizeof(double) * kNormBlocks);
+  const size_t o_sc = reserve(sizeof(Scal3));
+  if (cudaMalloc(&h->arena, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return BMG_ENOMEM;
+  }
+  if (cudaMallocHost(&h->sc_host, sizeof(Scal3)) != cudaSuccess) {
+    free3(h);
+    return BMG_ENOMEM;
+  }
+  char* base = static_cast<char*>(h->arena);
+  size_t pi = 0;
+  for (int l = 0; l < L; ++l) {
+    Lev3& V = h->lv[l];
+    auto next = [&]() { return reinterpret_cast<double*>(base + offs[pi++]); };
+    V.C = next();
+    V.iC = next();
+    for (int m = 0; m < NA; ++m) V.A[m] = next();
+    V.x = next();
+    V.b = next();
+    V.r = next();
+    for (int m = 0; m < NPW3; ++m) V.P[m] = l >= 1 ? next() : nullptr;
+  }
+  h->chol = reinterpret_cast<double*>(base + o_chol);
+  h->chol_idiag = reinterpret_cast<double*>(base + o_idiag);
+  h->partials = reinterpret_cast<double*>(base + o_part);
+  h->sc = reinterpret_cast<Scal3*>(base + o_sc);
+  h->err = &h->sc->err;
+  if (cudaMemsetAsync(h->arena, 0, total, s) != cudaSuccess) {
+    free3(h);
+    return BMG_ECUDA;
+  }
+  const Lev3& F = h->lv[L - 1];
+  k3_assemble<<<dim3(cdiv(F.nx, kT), F.ny, F.nz), kT, 0, s>>>(k, F, h->err);
+  count_launch();
+  for (int l = L - 1; l >= 1; --l) {
+    const Lev3& V = h->lv[l];
+    for (int pass = 0; pass <= 3; ++pass) {
+      k3_interp_weights<<<grid_pts(V), kT, 0, s>>>(V, pass, h->err);
+      count_launch();
+    }
+    k3_rap<<<grid_pts(h->lv[l - 1]), kT, 0, s>>>(V, h->lv[l - 1], h->err);
+    count_launch();
+  }
+  k3_coarse_factor<<<1, 512, 0, s>>>(h->lv[0], h->chol, h->chol_idiag, h->err);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) {
+    free3(h);
+    return BMG_ECUDA;
+  }
+  int rc = check_err(h, s);
+  if (rc) {
+    free3(h);
+    return rc;
+  }
+  h->setup_ms = now_ms() - t0;
+  *out = h;
+  return BMG_OK;
+}
+
+int bmg3_solve(bmg3_hierarchy* h, const double* b, double* x, double tol, bmg_info* info,
+               bmg_stream_t stream) {
+  if (!h || !b || !x || !(tol >= 0.0)) return BMG_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const double t0 = now_ms();
+  const Lev3& F = h->lv[h->L - 1];
+  const dim3 g = dim3(cdiv(F.nx, kT), F.ny, F.nz);
+  k3_pack<<<g, kT, 0, s>>>(b, F.b, F);
+  k3_pack<<<g, kT, 0, s>>>(x, F.x, F);
+  k3_norm<<<kNormBlocks, kNormThreads, 0, s>>>(F, 0, h->partials);
+  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 0);
+  k3_norm<<<kNormBlocks, kNormThreads, 0, s>>>(F, 1, h->partials);
+  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+  count_launch(6);
+  if (cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return BMG_ECUDA;
+  const double bn2 = h->sc_host->bnorm2;
+  int cycles = 0;
+  double rel = bn2 > 0.0 ? std::sqrt(h->sc_host->rnorm2 / bn2) : 0.0;
+  int rc = BMG_OK;
+  if (bn2 == 0.0) {
+    cudaMemsetAsync(x, 0, sizeof(double) * size_t(F.nx) * F.ny * F.nz, s);
+  } else {
+    // one cycle as a graph, recorded on a private stream (stream launches
+    // while kernel classes are being timed)
+    const bool use_graph = !bmg::prof_active();
+    if (use_graph && !h->gexec) {
+      cudaStream_t cs;
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return BMG_ECUDA;
+      bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) enqueue_cycle(h, cs);
+      ok = cudaStreamEndCapture(cs, &h->graph) == cudaSuccess && ok;
+      ok = ok && cudaGraphInstantiate(&h->gexec, h->graph, 0) == cudaSuccess;
+      cudaStreamDestroy(cs);
+      if (!ok) {
+        cudaGetLastError();
+        return BMG_ECUDA;
+      }
+    }
+    while (rel > tol && cycles < h->opt.max_cycles) {
+      if (use_graph) {
+        if (cudaGraphLaunch(h->gexec, s) != cudaSuccess) return BMG_ECUDA;
+      } else {
+        enqueue_cycle(h, s);
+      }
+      if (cudaStreamSynchronize(s) != cudaSuccess) return BMG_ECUDA;
+      ++cycles;
+      rel = std::sqrt(h->sc_host->rnorm2 / bn2);
+      if (!std::isfinite(rel)) {
+        rc = BMG_ENAN;
+        break;
+      }
+    }
+    if (!rc && rel > tol) rc = BMG_ENOCONV;
+    k3_unpack<<<g, kT, 0, s>>>(F.x, x, F);
+    count_launch();
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return BMG_ECUDA;
+  if (info) {
+    info->cycles = cycles;
+    info->threshold = 0;
+    info->rel_resid = rel;
+    info->setup_ms = h->setup_ms;
+    info->solve_ms = now_ms() - t0;
+  }
+  return rc;
+}
+
+void bmg3_destroy(bmg3_hierarchy* h) { free3(h); }
+
+int bmg3_num_levels(const bmg3_hierarchy* h, int* n) {
+  if (!h || !n) return BMG_EINVAL;
+  *n = h->L;
+  return BMG_OK;
+}
+
+int bmg3_level_shape(const bmg3_hierarchy* h, int level, int* nx, int* ny, int* nz) {
+  if (!h || level < 0 || level >= h->L || !nx || !ny || !nz) return BMG_EINVAL;
+  *nx = h->lv[level].nx;
+  *ny = h->lv[level].ny;
+  *nz = h->lv[level].nz;
+  return BMG_OK;
+}
+
+static int copy_planes(const Lev3& V, double* const* planes, int np, double* out) {
+  const size_t pb = size_t(V.nz + 2) * V.py * V.px;
+  std::vector<double> buf(pb);
+  const size_t n = size_t(V.nx) * V.ny * V.nz;
+  for (int p = 0; p < np; ++p) {
+    if (cudaMemcpy(buf.data(), planes[p], pb * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return BMG_ECUDA;
+    for (int k = 0; k < V.nz; ++k)
+      for (int j = 0; j < V.ny; ++j)
+        for (int i = 0; i < V.nx; ++i)
+          out[p * n + (size_t(k) * V.ny + j) * V.nx + i] = buf[idx3(V, i + 1, j + 1, k + 1)];
+  }
+  return BMG_OK;
+}
+
+int bmg3_level_stencil(const bmg3_hierarchy* h, int level, double* host_out) {
+  if (!h || level < 0 || level >= h->L || !host_out) return BMG_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return BMG_ECUDA;
+  const Lev3& V = h->lv[level];
+  double* planes[1 + NA];
+  planes[0] = V.C;
+  for (int m = 0; m < NA; ++m) planes[1 + m] = V.A[m];
+  return copy_planes(V, planes, 1 + NA, host_out);
+}
+
+int bmg3_level_interp(const bmg3_hierarchy* h, int level, double* host_out) {
+  if (!h || level < 1 || level >= h->L || !host_out) return BMG_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return BMG_ECUDA;
+  const Lev3& V = h->lv[level];
+  return copy_planes(V, V.P, NPW3, host_out);
+}
+
+}  // extern "C"

@@ -11,16 +11,20 @@ import paper_1803_02481_gb300 as bm
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def header_functions():
-    text = open(os.path.join(ROOT, "include", "boxmg.h")).read()
+def header_functions(header="boxmg.h", prefix="bmg_"):
+    text = open(os.path.join(ROOT, "include", header)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return set(re.findall(r"^\s*(?:int|void|long long|const char\s*\*)\s*\*?\s*(bmg_\w+)\s*\(", text, flags=re.M))
+    pat = r"^\s*(?:int|void|long long|const char\s*\*)\s*\*?\s*(" + prefix + r"\w+)\s*\("
+    return set(re.findall(pat, text, flags=re.M))
 
 
 def test_header_and_binding_agree():
     names = header_functions()
     assert len(names) >= 15
     assert names == set(bm.EXPORTED), names ^ set(bm.EXPORTED)
+    names3 = header_functions("boxmg3d.h", "bmg3_")
+    assert len(names3) >= 7
+    assert names3 == set(bm.EXPORTED3), names3 ^ set(bm.EXPORTED3)
 
 
 def test_library_exports_every_declared_symbol():
@@ -28,7 +32,7 @@ def test_library_exports_every_declared_symbol():
         from paper_1803_02481_gb300 import build
         build.build()
     cdll = ctypes.CDLL(bm.library_path())
-    for name in header_functions():
+    for name in header_functions() | header_functions("boxmg3d.h", "bmg3_"):
         assert hasattr(cdll, name), name
 
 
@@ -41,5 +45,8 @@ def test_host_only_calls_work_without_gpu():
     h = ctypes.c_void_p()
     rc = lib.bmg_setup(None, 8, 7, ctypes.byref(o), None, ctypes.byref(h))
     assert rc == bm.BMG_EINVAL and not h.value
+    rc = lib.bmg3_setup(None, 8, 7, 6, ctypes.byref(o), None, ctypes.byref(h))
+    assert rc == bm.BMG_EINVAL and not h.value
+    assert lib.bmg3_num_levels(None, ctypes.byref(ctypes.c_int())) == bm.BMG_EINVAL
     n = ctypes.c_int()
     assert lib.bmg_num_levels(None, ctypes.byref(n)) == bm.BMG_EINVAL
