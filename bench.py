@@ -296,6 +296,7 @@ def run_ours(args, rank, world, local_rank):
         # the paper's global grid as it is (9088 x 568, aspect 16), r = 16
         extra["paper_workload_9088x568"] = paper_workload_leg(bm, torch, dev, stream, nx=9088, ny=568)
         extra["line_smoother"] = line_smoother_leg(bm, torch, dev, stream, load_peaks()[0])
+        extra["three_d"] = three_d_leg(bm, torch, dev, stream, load_peaks()[0])
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.quick:
@@ -537,6 +538,66 @@ def line_smoother_leg(bm, torch, dev, stream, peaks, n=4095, r=100.0):
     return out
 
 
+# Fine-level 7-point red-black sweep of the 3D solver, per fine unknown:
+# 1/C, the three stored couplings (W, S, down; the other three are the
+# neighbours' entries of the same planes), b, x read, x write; 6 FMA + 1 MUL.
+SWEEP3D_BYTES_PER_UNKNOWN = 56.0
+SWEEP3D_FLOPS_PER_UNKNOWN = 13.0
+
+
+def three_d_leg(bm, torch, dev, stream, peaks, n=255, block=16):
+    """3D BoxMG on an n^3 block field: k = 10^U(-2, 2) constant on block^3
+    cells (torch generator seed 11 on the device), b uniform[-1, 1] (seed 12),
+    FP64 V(2,1) to 1e-10 (setup + solve timed), then the fine-level sweep
+    alone with CUDA events."""
+    nb = -(-n // block)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    kb = 10.0 ** (torch.rand((nb, nb, nb), generator=gen, device=dev, dtype=torch.float64) * 4 - 2)
+    k = kb.repeat_interleave(block, 0).repeat_interleave(block, 1).repeat_interleave(block, 2)
+    k = k[:n, :n, :n].contiguous()
+    gen.manual_seed(12)
+    b = torch.rand((n, n, n), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+    out = {"workload": f"3D block field 10^U(-2,2) on {block}^3-cell blocks, {n}^3 cells, tol 1e-10"}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    x = torch.zeros_like(b)
+    times, setups = [], []
+    for rep in range(3):
+        x.zero_()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        h = bm.setup3(k, stream=stream)
+        _, info = h.solve(b, x, tol=1e-10, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            times.append(ev0.elapsed_time(ev1))
+            setups.append(info.setup_ms)
+        if rep < 2:
+            h.destroy()
+    ms = sum(times) / len(times)
+    out["fp64"] = {"value": n ** 3 / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms,
+                   "setup_ms": sum(setups) / len(setups), "cycles": info.cycles,
+                   "rel_resid": info.rel_resid, "levels": h.nlevels}
+    # the fine-level sweep alone (stream-launched solve with CUDA events)
+    bm.profile_set(("fine_smooth",))
+    x.zero_()
+    h.solve(b, x, tol=1e-10, stream=stream)
+    torch.cuda.synchronize()
+    cnt, sms = bm.profile_read("fine_smooth")
+    bm.profile_set(())
+    h.destroy()
+    per = sms / max(cnt, 1)
+    gbs = SWEEP3D_BYTES_PER_UNKNOWN * n ** 3 / (per * 1e-3) / 1e9
+    gfl = SWEEP3D_FLOPS_PER_UNKNOWN * n ** 3 / (per * 1e-3) / 1e9
+    alu = alu_peak_gflops(torch, dev, "fp64", None)[0]
+    out["fine_sweep"] = {"kernel": "k3_gs<7-point>: red-black sweep, two launches", "ms_per_sweep": per,
+                         "sweeps": cnt, "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peaks["hbm_gbs"],
+                         "achieved_gflops": gfl, "frac_of_fp64_peak": gfl / alu}
+    return out
+
+
 def threshold_sweep(bm, torch, k, b, stream, cycles=20):
     """Measured time of one V-cycle for every schedule threshold (levels below
     it run inside the persistent coarse kernel) next to the cost model's
@@ -666,6 +727,8 @@ def run_leg(name):
     stream = torch.cuda.current_stream()
     if name == "line_smoother":
         out = line_smoother_leg(bm, torch, dev, stream, load_peaks()[0])
+    elif name == "three_d":
+        out = three_d_leg(bm, torch, dev, stream, load_peaks()[0])
     elif name == "paper_workload":
         out = paper_workload_leg(bm, torch, dev, stream)
     else:
@@ -691,7 +754,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the e2e, fp32 and CPU legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--only", default=None,
-                    choices=["line_smoother", "paper_workload", "paper_workload_9088x568"],
+                    choices=["line_smoother", "three_d", "paper_workload", "paper_workload_9088x568"],
                     help="run one measurement leg alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.only is not None:
