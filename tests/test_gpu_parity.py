@@ -564,6 +564,12 @@ LINE_SOLVE_CASES = {
     "paper1023x63_alt": (lambda: dict(aniso_case("paper1023x63")), "xy"),
     # general sides, lines ending on separators
     "pow2_256_alt": (lambda: dict(general_case("pow2_256x256")), "xy"),
+    # Neumann and Robin walls on even sides, stretched anisotropic cells
+    "robin100x60_alt": (lambda: dict(inputs.block_problem(seed=85, block=8, lo=-1, hi=1, nx=100, ny=60),
+                                     r=0.2, aspect=2.0, bc=(0.0, 2.0, None, 0.5)), "xy"),
+    # the r/C interpolation variant with x-lines
+    "rc_blocks127_x": (lambda: dict(inputs.block_problem(seed=86, block=8, lo=-2, hi=2, nx=127, ny=127),
+                                    r=0.05, aspect=1.0, rc=True), "x"),
 }
 
 
@@ -581,10 +587,15 @@ def test_line_smoothed_solve_matches_oracle(name):
     r = 8 by 5e-13)."""
     make, smoother = LINE_SOLVE_CASES[name]
     pr = make()
-    ho = O.setup(pr["k"], r=pr["r"], aspect=pr["aspect"], smoother=smoother)
+    bc = pr.get("bc")
+    rc = bool(pr.get("rc", False))
+    ho = O.setup(pr["k"], r=pr["r"], aspect=pr["aspect"], smoother=smoother, bc=bc,
+                 interp_residual_term=rc)
+    extra = {} if bc is None else {"bc_beta": bc}
     hg = bm.setup(dev(pr["k"]), bm.default_options(aniso_r=pr["r"], cell_aspect=pr["aspect"],
                                                    smoother=SMOOTHER_CODES[smoother],
-                                                   max_cycles=200))
+                                                   interp_residual_term=int(rc), max_cycles=200,
+                                                   **extra))
     ro = O.solve(ho, pr["b"], tol=1e-10, max_cycles=200)
     x, info = hg.solve(dev(pr["b"]), tol=1e-10)
     hg.destroy()
