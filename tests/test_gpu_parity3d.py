@@ -43,6 +43,8 @@ CASES = {
     "general12x9x7": lambda: (block_k((12, 9, 7), 26, block=3), 27),
     "general40x24x20": lambda: (block_k((40, 24, 20), 28, block=5), 29),
     "tiny4": lambda: (block_k((4, 4, 4), 30, block=2), 31),
+    # a longer general grid (odd and even sides, four levels)
+    "general45x20x70": lambda: (block_k((45, 20, 70), 34, block=6), 35),
     "single3": lambda: (block_k((3, 3, 3), 32, block=1), 33),
 }
 
@@ -176,3 +178,4 @@ def test_3d_zero_rhs_and_error_codes():
         h.solve(dev(b), tol=1e-14)
     assert e.value.code == bm.BMG_ENOCONV
     h.destroy()
+
