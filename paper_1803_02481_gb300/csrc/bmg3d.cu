@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <new>
 #include <vector>
 
@@ -313,6 +314,27 @@ __global__ void k3_gs(Lev3 L, int colour) {
   L.x[o] = (L.b[o] + nb_sum<SEVEN>(L, L.x, o)) * L.iC[o];
 }
 
+// Two colours of an eight-colour sweep in one launch: colours 2m and 2m + 1
+// (the same parities of j and k, (cj, ck) = (m & 1, m >> 1)) differ only in the
+// parity of i, so a point of one has neighbours of the other only within its
+// own x-row; every other neighbour is of colours 2m + 2 .. 7 (forward) or
+// 0 .. 2m - 1 (reverse), untouched by this launch.  One thread block per row:
+// the first colour of the row, a barrier, the second.  Each point update is
+// that of k3_gs<false>, so a sweep gives the same bits as eight launches.
+__global__ void __launch_bounds__(kT) k3_gs27_pair(Lev3 L, int m, int reverse) {
+  const int j0 = 2 * blockIdx.x + (m & 1), k0 = 2 * blockIdx.y + (m >> 1);   // 0-based
+  if (j0 >= L.ny || k0 >= L.nz) return;
+  const int base = idx3(L, 0, j0 + 1, k0 + 1);
+  for (int h = 0; h < 2; ++h) {
+    const int ci = reverse ? 1 - h : h;
+    for (int i0 = 2 * threadIdx.x + ci; i0 < L.nx; i0 += 2 * kT) {
+      const int o = base + i0 + 1;
+      L.x[o] = (L.b[o] + nb_sum<false>(L, L.x, o)) * L.iC[o];
+    }
+    __syncthreads();
+  }
+}
+
 template <bool SEVEN>
 __global__ void k3_residual(Lev3 L) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
@@ -339,10 +361,11 @@ __global__ void k3_restrict(Lev3 F, Lev3 Cc) {
   Cc.x[oc] = 0.0;
 }
 
-// x(f) += sum over f's parents of P(f, I) x_c(I).
-__global__ void k3_interp(Lev3 F, Lev3 Cc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
-  if (i > F.nx) return;
+// x(f) += sum over f's parents of P(f, I) x_c(I).  A point has 1, 2, 4 or 8
+// parents by the parities of i, j, k; each thread takes one point of each
+// parity of i in turn (j and k are fixed per block), so the lanes of a warp
+// always follow the same parents.
+__device__ __forceinline__ void interp_point(const Lev3& F, const Lev3& Cc, int i, int j, int k) {
   const int o = idx3(F, i, j, k);
   double s = 0.0;
   for (int m = 0; m < NPW3; ++m) {
@@ -354,6 +377,12 @@ __global__ void k3_interp(Lev3 F, Lev3 Cc) {
     s = fma(F.P[m][o], Cc.x[idx3(Cc, I, J, K)], s);
   }
   F.x[o] += s;
+}
+
+__global__ void k3_interp(Lev3 F, Lev3 Cc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y + 1, k = blockIdx.z + 1;
+  if (2 * t + 1 <= F.nx) interp_point(F, Cc, 2 * t + 1, j, k);
+  if (2 * t + 2 <= F.nx) interp_point(F, Cc, 2 * t + 2, j, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -503,6 +532,8 @@ struct bmg3_hierarchy {
   Scal3* sc_host = nullptr;
   int* err = nullptr;
   int n0 = 0;
+  int gs27_pairs = 1;             // 27-point sweeps as four colour-pair launches (1) or
+                                  // eight colour launches (0; environment BMG3_GS27_PAIRS)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t gstream = nullptr;   // stream the graph was built for
@@ -534,6 +565,15 @@ void enqueue_cycle(bmg3_hierarchy* h, cudaStream_t s) {
     const int nc = seven ? 2 : 8;
     for (int it = 0; it < nu; ++it) {
       if (seven) bmg::prof_begin(BMG_PROF_FINE_SMOOTH, s);
+      if (!seven && h->gs27_pairs) {
+        for (int p0 = 0; p0 < 4; ++p0) {
+          const int m = reverse ? 3 - p0 : p0;
+          k3_gs27_pair<<<dim3((V.ny + 1 - (m & 1)) / 2, (V.nz + 1 - (m >> 1)) / 2), kT, 0, s>>>(
+              V, m, reverse ? 1 : 0);
+          count_launch();
+        }
+        continue;
+      }
       for (int c0 = 0; c0 < nc; ++c0) {
         const int c = reverse ? nc - 1 - c0 : c0;
         if (seven)
@@ -558,7 +598,8 @@ void enqueue_cycle(bmg3_hierarchy* h, cudaStream_t s) {
   k3_coarse_solve<<<1, 256, 0, s>>>(h->lv[0], h->chol, h->chol_idiag);
   count_launch();
   for (int l = 1; l < L; ++l) {
-    k3_interp<<<grid_pts(h->lv[l]), kT, 0, s>>>(h->lv[l], h->lv[l - 1]);
+    k3_interp<<<dim3(cdiv((h->lv[l].nx + 1) / 2, kT), h->lv[l].ny, h->lv[l].nz), kT, 0, s>>>(
+        h->lv[l], h->lv[l - 1]);
     count_launch();
     sweep(l, h->opt.nu2, true);
   }
@@ -619,6 +660,7 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
   bmg3_hierarchy* h = new (std::nothrow) bmg3_hierarchy();
   if (!h) return BMG_ENOMEM;
   h->opt = opt;
+  if (const char* e = std::getenv("BMG3_GS27_PAIRS")) h->gs27_pairs = std::atoi(e) != 0;
   h->L = int(sx.size());
   const int L = h->L;
   h->n0 = sx.back() * sy.back() * sz.back();

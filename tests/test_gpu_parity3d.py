@@ -179,3 +179,21 @@ def test_3d_zero_rhs_and_error_codes():
     assert e.value.code == bm.BMG_ENOCONV
     h.destroy()
 
+
+
+@pytest.mark.parametrize("name", ["blocks31_c4", "general45x20x70", "general12x9x7"])
+@pytest.mark.parametrize("nu", [(2, 1), (1, 1)])
+def test_3d_paired_colour_sweeps_are_bit_identical(name, nu, monkeypatch):
+    """The 27-point sweeps as four colour-pair launches (one thread block per
+    x-row, the two colours of a row separated by a barrier) give the same
+    bits as eight colour launches, forward and reversed."""
+    k, b = case(name)
+    out = []
+    for pairs in ("0", "1"):
+        monkeypatch.setenv("BMG3_GS27_PAIRS", pairs)
+        h = bm.setup3(dev(k), bm.default_options(nu1=nu[0], nu2=nu[1], max_cycles=400))
+        x, info = h.solve(dev(b), tol=1e-10)
+        h.destroy()
+        out.append((x.cpu().numpy(), info.cycles, info.rel_resid))
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    assert np.array_equal(out[0][0], out[1][0])
