@@ -50,6 +50,7 @@ WORKLOAD = {"workload": "diffusion 4095x4095, 64x64-cell blocks k=10^U(-4,4), se
 # to None whenever the kernel changes until it is captured again.
 SWEEP_DRAM_BYTES_PER_UNKNOWN = {
     "fp64": (169.342720e6 + 18.732288e6) / 4190209,    # 2047^2 block field
+    "fp64_prescaled": (203.350528e6 + 22.938880e6) / 4190209,   # 2047^2 block field
     "fp32": (338.814976e6 + 52.656128e6) / 16769025,   # 4095^2 log-normal field
 }
 
@@ -233,10 +234,13 @@ def run_ours(args, rank, world, local_rank):
     if args.threshold is not None:
         opts.coarse_threshold = args.threshold
 
+    state = {}
+
     def step():
         x.zero_()
         h = bm.setup(k, opts, stream=stream)
         _, info = h.solve(b, x, tol=tol, stream=stream, allow_noconv=args.profile)
+        state["prescaled"] = h.level_prescaled(h.nlevels - 1)
         h.destroy()
         return info
 
@@ -325,26 +329,31 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_kind = load_peaks()
     # fine-level smoothing: one bracket = one full red-black sweep over the
     # fine level.  Algorithmic bytes per fine unknown: 1/C, W, S, b and x
-    # read, x written = 6 words (48 B FP64); flops: 4 FMA + 1 MUL = 9.
+    # read, x written = 6 words (48 B FP64); flops: 4 FMA + 1 MUL = 9.  The
+    # prescaled FP64 level: b/C, W/C, E/C, S/C, N/C and x read, x written =
+    # 7 words (56 B); flops: 4 FMA = 8.
     word = 8.0 if args.precision == "fp64" else 4.0
-    per_unit_b, per_unit_f = 6 * word, 9.0
+    prescaled = bool(state.get("prescaled"))
+    per_unit_b, per_unit_f = (7 * word, 8.0) if prescaled else (6 * word, 9.0)
     sweep_ms = prof_ms / max(1, nprof)
     gbs = per_unit_b * n_fine / (sweep_ms / 1e3) / 1e9
     gfl = per_unit_f * n_fine / (sweep_ms / 1e3) / 1e9
     f_hbm = gbs / peaks["hbm_gbs"]
     alu_peak, alu_src = alu_peak_gflops(torch, dev, args.precision, clk.summary())
     f_alu = gfl / alu_peak
-    kname = "k_sweep_tma<%s, 5-point>" % ("double" if args.precision == "fp64" else "float")
+    kname = "k_sweep_tma<%s, 5-point%s>" % ("double" if args.precision == "fp64" else "float",
+                                             ", prescaled" if prescaled else "")
     # DRAM bytes per launch from the ncu capture of this kernel (a smaller
     # grid of the same kind, scaled by the units one launch processes)
-    traffic_per_unit = SWEEP_DRAM_BYTES_PER_UNKNOWN.get(args.precision)
+    traffic_per_unit = SWEEP_DRAM_BYTES_PER_UNKNOWN.get(args.precision + ("_prescaled" if prescaled else ""))
     traffic = traffic_per_unit * n_fine if traffic_per_unit else None
     common = {"kernel": kname + ": fine-level red-black Gauss-Seidel sweep, TMA-staged, one launch per sweep",
               "per_launch_ms": sweep_ms, "launches_timed": nprof,
               "timing": "CUDA events around every fine sweep of one full profiled step on the solve stream",
               "algorithmic_bytes_per_unknown": per_unit_b, "algorithmic_flops_per_unknown": per_unit_f,
               "units_per_launch": n_fine,
-              "traffic_source": "profiles/k_sweep_tma_fine_ncu.md (dram bytes per unknown x units)",
+              "traffic_source": ("profiles/k_sweep_tma_fine_prescaled_ncu.md" if prescaled
+                                 else "profiles/k_sweep_tma_fine_ncu.md") + " (dram bytes per unknown x units)",
               "hbm": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": f_hbm,
                       "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
               "alu": {"achieved_gflops": gfl, "peak_gflops": alu_peak, "frac": f_alu,

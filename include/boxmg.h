@@ -188,6 +188,12 @@ int bmg_num_levels(const bmg_hierarchy *h, int *nlevels);
 
 /* Grid size of a level. */
 int bmg_level_shape(const bmg_hierarchy *h, int level, int *nx, int *ny);
+/* *out = 1 when the red-black sweep of level `level` runs on the prescaled
+ * operator (the 5-point FP64 finest level swept by the TMA-staged kernel:
+ * b/C and the couplings divided by C stored beside the operator, four fused
+ * multiply-adds per point update; the same Gauss-Seidel step with different
+ * rounding), else 0. */
+int bmg_level_prescaled(const bmg_hierarchy *h, int level, int *out);
 
 /* A_level as five dense (ny, nx) float64 planes, concatenated, in host
  * memory: C, W, S, SW, NW, where W(i,j) = -A[(i,j),(i-1,j)],

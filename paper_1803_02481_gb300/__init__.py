@@ -72,6 +72,7 @@ EXPORTED = {
     "bmg_destroy": (None, [_vp]),
     "bmg_num_levels": (_i, [_vp, ctypes.POINTER(_i)]),
     "bmg_level_shape": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "bmg_level_prescaled": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "bmg_level_stencil": (_i, [_vp, _i, _vp]),
     "bmg_level_interp": (_i, [_vp, _i, _vp]),
     "bmg_coarse_factor": (_i, [_vp, _vp, _i]),
@@ -261,6 +262,11 @@ class Hierarchy:
         n = ctypes.c_int()
         _check(lib().bmg_num_levels(self._h, ctypes.byref(n)), "bmg_num_levels")
         return n.value
+
+    def level_prescaled(self, level: int) -> bool:
+        out = ctypes.c_int()
+        _check(lib().bmg_level_prescaled(self._h, level, ctypes.byref(out)), "bmg_level_prescaled")
+        return bool(out.value)
 
     def level_shape(self, level: int):
         nx, ny = ctypes.c_int(), ctypes.c_int()

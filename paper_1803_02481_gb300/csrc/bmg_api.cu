@@ -68,7 +68,7 @@ struct Carver {
 
 template <typename T>
 void carve_levels(Carver& cv, const std::vector<Geom>& geo, int first, std::vector<LevelV<T>>& lv,
-                  int finest_index, int smoother) {
+                  int finest_index, int smoother, bool prescale = false) {
   const bool xl = smoother == BMG_SMOOTH_XLINE || smoother == BMG_SMOOTH_ALTLINE;
   const bool yl = smoother == BMG_SMOOTH_YLINE || smoother == BMG_SMOOTH_ALTLINE;
   // lv[i] corresponds to hierarchy level first + i.
@@ -92,6 +92,7 @@ void carve_levels(Carver& cv, const std::vector<Geom>& geo, int first, std::vect
     L.x2 = cv.plane<T>(g);
     L.b = cv.plane<T>(g);
     L.r = cv.plane<T>(g);
+    for (int k = 0; k < 5; ++k) L.PR[k] = prescale && l == finest_index ? cv.plane<T>(g) : nullptr;
     // colour-compacted planes of the y-lines: (ny + 2) rows of ycp columns
     // per colour, ycp >= the columns of a colour, a multiple of 32
     L.ycp = ((g.nx + 1) / 2 + 31) / 32 * 32;
@@ -266,7 +267,8 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   for (int pass = 0; pass < 2; ++pass) {
     cv.off = 0;
     carve_levels<double>(cv, g64, fp32 ? L - 1 : 0, h->d, L - 1,
-                         fp32 ? BMG_SMOOTH_POINT : opt.smoother);
+                         fp32 ? BMG_SMOOTH_POINT : opt.smoother,
+                         !fp32 && opt.smoother == BMG_SMOOTH_POINT && prescale_enabled(nx));
     if (fp32) carve_levels<float>(cv, h->geo32, 0, h->f, L - 1, opt.smoother);
     h->kcopy = cv.raw<double>(size_t(nx) * ny);
     h->chol = cv.raw<double>(size_t(h->n0) * h->n0);
@@ -310,6 +312,7 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
   if (launch_assemble<double>(k, nx, ny, fine64, h->kcopy, derr, opt.log_coefficients != 0,
                               opt.aniso_r, opt.cell_aspect, opt.bc_beta, s))
     return fail(BMG_ECUDA);
+  if (fine64.PR[PR_B]) launch_prescale_coeffs<double>(fine64, s);
   if (!fp32) {
     if ((rc = build_coarse<double>(h, h->d, s))) return fail(rc);
     if (launch_coarse_factor(h, &h->d[0], nullptr, s)) return fail(BMG_ECUDA);
@@ -535,6 +538,8 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
   double* xk = pcg ? h->pcg_x : F.x;
   double* bk = pcg ? h->pcg_b : F.b;
   launch_pack<double>(b, bk, h->nx, h->ny, F.pitch, s);
+  // the V-cycle solver's fine right-hand side is fixed for the whole solve
+  if (!pcg && F.PR[PR_B] && h->opt.precision == BMG_FP64) launch_prescale_b<double>(F, s);
   launch_pack<double>(x, xk, h->nx, h->ny, F.pitch, s);
   if (pcg)
     BMG_CUDA(cudaMemsetAsync(h->pcg_p, 0, sizeof(double) * size_t(h->ny + 2) * F.pitch, s));
@@ -755,6 +760,14 @@ int bmg_num_levels(const bmg_hierarchy* h, int* nlevels) {
   return BMG_OK;
 }
 
+int bmg_level_prescaled(const bmg_hierarchy* hp, int level, int* out) {
+  const Hierarchy* h = H(hp);
+  if (!h || !out || level < 0 || level >= h->L) return BMG_EINVAL;
+  const int first = h->L - int(h->d.size());      // h->d holds levels first .. L-1
+  *out = level >= first && h->d[level - first].PR[bmg::PR_B] != nullptr ? 1 : 0;
+  return BMG_OK;
+}
+
 int bmg_level_shape(const bmg_hierarchy* h, int level, int* nx, int* ny) {
   if (!h || !nx || !ny || level < 0 || level >= H(h)->L) return BMG_EINVAL;
   *nx = H(h)->geo64[level].nx;
@@ -862,6 +875,7 @@ int bmg_op_relax(bmg_hierarchy* hp, int level, double* x, const double* b, int n
   auto& L = h->d[level];
   bmg::launch_pack<double>(x, L.x, L.nx, L.ny, L.pitch, s);
   bmg::launch_pack<double>(b, L.b, L.nx, L.ny, L.pitch, s);
+  if (L.PR[bmg::PR_B]) bmg::launch_prescale_b<double>(L, s);
   const bool fine = level == h->L - 1;
   for (int k = 0; k < nu; ++k) {
     if (h->opt.smoother != BMG_SMOOTH_POINT)

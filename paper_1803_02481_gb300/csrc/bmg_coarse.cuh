@@ -44,7 +44,10 @@ __device__ void blk_colour(const LevelV<T>& L, unsigned mask) {
         const int i = 1 + pi + 2 * ii, j = 1 + pj + 2 * jj;
         if (i > L.nx || j > L.ny) continue;
         const int o = j * L.pitch + i;
-        L.x[o] = gs_value<T, NINE>(L, L.x, L.b[o], o);
+        if (!NINE && sizeof(T) == 8 && L.PR[PR_B])
+          L.x[o] = gs_pre_value<T>(L, L.x, o);     // prescaled finest level (FP64 only)
+        else
+          L.x[o] = gs_value<T, NINE>(L, L.x, L.b[o], o);
       }
     }
   }

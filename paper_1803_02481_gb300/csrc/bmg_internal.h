@@ -96,6 +96,8 @@ struct LevelV {
   T *C, *iC, *W, *S, *SW, *NW;
   T *x, *b, *r;
   T *x2;               // second iterate buffer (sweeps write out of place)
+  T *PR[5];            // prescaled 5-point finest level (else null): b/C, W/C, E/C,
+                       // S/C, N/C, E and N the couplings to i + 1 and j + 1
   T *LF[2][NLF];       // x-lines: plane layout; y-lines: colour-compacted
   T *SP[2][NSP];
   int spp[2];          // separators per line, rounded up (0: no separators)
@@ -156,6 +158,28 @@ __device__ __forceinline__ T gs_apply(const GsCoef<T, NINE>& c, XA xa) {
     acc = fma(c.ne, xa(1, 1), acc);
   }
   return acc * c.ic;
+}
+
+// Gauss-Seidel update of a point of a prescaled level: the same neighbour
+// order with every coefficient already divided by C, so no final product:
+// x = b/C + (W/C) x_W + (E/C) x_E + (S/C) x_S + (N/C) x_N.
+enum { PR_B = 0, PR_W, PR_E, PR_S, PR_N };
+
+template <typename T, class XA>
+__device__ __forceinline__ T gs_pre_apply(T pb, T pw, T pe, T ps, T pn, XA xa) {
+  T acc = pb;
+  acc = fma(pw, xa(-1, 0), acc);
+  acc = fma(pe, xa(1, 0), acc);
+  acc = fma(ps, xa(0, -1), acc);
+  acc = fma(pn, xa(0, 1), acc);
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T gs_pre_value(const LevelV<T>& L, const T* __restrict__ x, int o) {
+  const int p = L.pitch;
+  return gs_pre_apply<T>(L.PR[PR_B][o], L.PR[PR_W][o], L.PR[PR_E][o], L.PR[PR_S][o],
+                         L.PR[PR_N][o], [&](int dx, int dy) { return x[o + dx + dy * p]; });
 }
 
 template <typename T, bool NINE, class XA>
@@ -274,6 +298,8 @@ struct Scalars {            // device-resident solve state
 template <typename T>
 struct SweepMaps {
   CUtensorMap x, x2, ic, w, s, b, sw, nw;   // sw, nw: 9-point levels only
+  CUtensorMap pb, pw, pe, ps, pn;           // prescaled planes (pre)
+  bool pre;         // prescaled 5-point level: the sweep stages x and PR
   const T* xp;      // plane the map `x` describes
   const T* x2p;     // plane the map `x2` describes
   int* err;         // device error word (DEV_TIMEOUT)
@@ -380,6 +406,15 @@ void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* 
 template <typename T>
 void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* levels, int threshold,
                          cudaStream_t s);
+
+// Prescaled finest level (bmg_sweep.cu): whether the finest FP64 level of a
+// hierarchy is prescaled; the coefficient planes W/C, E/C, S/C, N/C (setup)
+// and b/C (whenever the level's b changes).
+bool prescale_enabled(int nx);
+template <typename T>
+void launch_prescale_coeffs(const LevelV<T>& L, cudaStream_t s);
+template <typename T>
+void launch_prescale_b(const LevelV<T>& L, cudaStream_t s);
 
 // Line smoothing (bmg_line.cu).  factor: the block LU factors, spikes and
 // Schur factors of every line of the directions `smoother` uses (setup; a

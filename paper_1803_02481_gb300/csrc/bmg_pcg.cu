@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(LevelV<double> L,
   const double s = for_points(L, [&](int o, double acc) {
     const double r = resid_value<double, false>(L, x, b[o], o);
     L.b[o] = r;
+    if (L.PR[PR_B]) L.PR[PR_B][o] = r * L.iC[o];   // prescaled level: b/C too
     L.x[o] = 0.0;
     return fma(r, r, acc);
   });
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_xr(LevelV<double> L, double* _
     x[o] = fma(a, p[o], x[o]);
     const double r = fma(-a, q[o], L.b[o]);
     L.b[o] = r;
+    if (L.PR[PR_B]) L.PR[PR_B][o] = r * L.iC[o];
     L.x[o] = 0.0;
     return fma(r, r, acc);
   });

@@ -164,25 +164,87 @@ static bool encode_level(const LevelV<T>& L, const TmaCfg& c, int nph, int* err,
   return ok;
 }
 
+// Prescaled finest level: the TMA red-black sweep stages b/C and the four
+// couplings divided by C in place of 1/C, W, S, b and takes four fused
+// multiply-adds per point instead of four and a product (environment
+// BMG_RB_PRESCALE=0 turns it off).  Only levels the TMA sweep handles.
+static int pre_cfg_index() {
+  static const int v = [] {
+    const int k = env_int("BMG_TMA_PRE_CFG", 0);
+    return k >= 0 && k < 4 ? k : 0;
+  }();
+  return v;
+}
+
+bool prescale_enabled(int nx) {
+  static const bool on = env_int("BMG_RB_PRESCALE", 1) != 0;
+  return on && rb_kernel_choice() == 3 && nx >= 1024;
+}
+
+template <typename T>
+__global__ void k_prescale_coeffs(LevelV<T> L) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1;
+  if (i > L.nx) return;
+  const int o = j * L.pitch + i;
+  const T ic = L.iC[o];
+  L.PR[PR_W][o] = L.W[o] * ic;
+  L.PR[PR_E][o] = L.W[o + 1] * ic;
+  L.PR[PR_S][o] = L.S[o] * ic;
+  L.PR[PR_N][o] = L.S[o + L.pitch] * ic;
+}
+
+template <typename T>
+__global__ void k_prescale_b(LevelV<T> L) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1;
+  if (i > L.nx) return;
+  const int o = j * L.pitch + i;
+  L.PR[PR_B][o] = L.b[o] * L.iC[o];
+}
+
+template <typename T>
+void launch_prescale_coeffs(const LevelV<T>& L, cudaStream_t s) {
+  k_prescale_coeffs<T><<<dim3(cdiv(L.nx, 256), L.ny), 256, 0, s>>>(L);
+  count_launch();
+}
+
+template <typename T>
+void launch_prescale_b(const LevelV<T>& L, cudaStream_t s) {
+  k_prescale_b<T><<<dim3(cdiv(L.nx, 256), L.ny), 256, 0, s>>>(L);
+  count_launch();
+}
+
 template <typename T>
 bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m) {
   const bool nine = L.SW != nullptr;
   if (!nine && (rb_kernel_choice() != 3 || L.nx < 1024)) return false;
   if (nine && L.nx < nine_tma_min_side()) return false;
-  return encode_level<T>(L, tma_cfg<T>(nine), nine ? 4 : 2, err, m);
+  if (!encode_level<T>(L, tma_cfg<T>(nine), nine ? 4 : 2, err, m)) return false;
+  if (!nine && L.PR[PR_B]) {
+    // the prescaled shapes stage boxes of 64 + 4 columns and 16 + 4 or 8 + 4 rows
+    const int bh = pre_cfg_index() == 2 ? 12 : 20;
+    auto enc = [&](CUtensorMap* mm, const T* base) {
+      return encode_plane<T>(mm, base, L.pitch, L.ny, 68, bh);
+    };
+    if (!(enc(&m->x, L.x) && enc(&m->x2, L.x2) && enc(&m->pb, L.PR[PR_B]) &&
+          enc(&m->pw, L.PR[PR_W]) && enc(&m->pe, L.PR[PR_E]) && enc(&m->ps, L.PR[PR_S]) &&
+          enc(&m->pn, L.PR[PR_N])))
+      return false;
+    m->pre = true;
+  }
+  return true;
 }
 
 
 // Blocks of a TMA sweep shape resident per SM (at most MINB), measured once;
 // first called from prepare_sweep_kernels, after the shared-memory opt-in and
 // before any graph capture.
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE>
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false>
 static int tma_resident() {
   static const int r = [] {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE>, NT,
-            TmaTile<T, NINE, TX, TY, NSTAGE>::SMEM) != cudaSuccess ||
+            &n, k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE>, NT,
+            TmaTile<T, NINE, TX, TY, NSTAGE, PRE>::SMEM) != cudaSuccess ||
         n < 1)
       n = 1;
     cudaGetLastError();
@@ -206,13 +268,35 @@ static void launch_tma_shape(const LevelV<T>& L, const SweepMaps<T>& m, const CU
       mx, m.ic, m.w, m.s, m.b, msw, mnw, L, xout, order, m.err);
 }
 
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE>
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false>
 static void allow_tma_smem() {
-  cudaFuncSetAttribute(k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE>,
+  cudaFuncSetAttribute(k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       int(TmaTile<T, NINE, TX, TY, NSTAGE>::SMEM));
-  tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE>();
+                       int(TmaTile<T, NINE, TX, TY, NSTAGE, PRE>::SMEM));
+  tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE>();
 }
+
+// The prescaled red-black sweep (FP64, 5-point): x, b/C, W/C, S/C, E/C, N/C.
+template <int TX, int TY, int NT, int MINB, int NSTAGE>
+static void launch_tma_pre(const LevelV<double>& L, const SweepMaps<double>& m,
+                           const CUtensorMap& mx, unsigned order, double* xout, cudaStream_t s) {
+  using G = TmaTile<double, false, TX, TY, NSTAGE, true>;
+  const int ntiles = ((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
+  const int cap = sm_count() * tma_resident<double, false, TX, TY, NT, MINB, NSTAGE, true>();
+  k_sweep_tma<double, false, TX, TY, NT, MINB, NSTAGE, true>
+      <<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(mx, m.pb, m.pw, m.ps, m.pe, m.pn, m.pn, L,
+                                                        xout, order, m.err);
+}
+
+#define BMG_TMA_PRE_DISPATCH(K, BODY)      \
+  do {                                     \
+    switch (K) {                           \
+      case 1: BODY(64, 16, 512, 1, 2); break; \
+      case 2: BODY(64, 8, 512, 2, 2); break;  \
+      case 3: BODY(64, 16, 608, 2, 1); break; \
+      default: BODY(64, 16, 512, 3, 1); break; \
+    }                                      \
+  } while (0)
 
 // Instantiates BODY(T, NINE, TX, TY, NT, MINB, NSTAGE) for entry K of T's
 // 5-point or 9-point table (the shapes of kRb64/kRb32, kNine64/kNine32).
@@ -256,6 +340,14 @@ static void launch_sweep_tma(const LevelV<T>& L, const SweepMaps<T>& m, bool rev
                              const T* xin, T* xout, cudaStream_t s) {
   const CUtensorMap& mx = xin == m.xp ? m.x : m.x2;
   const unsigned order = m.nine ? four_order(reverse) : rb_order(reverse);
+  if constexpr (sizeof(T) == 8) {
+    if (m.pre) {
+#define BMG_TMA_PRE_LAUNCH(TX, TY, NT, MB, NS) launch_tma_pre<TX, TY, NT, MB, NS>(L, m, mx, order, xout, s)
+      BMG_TMA_PRE_DISPATCH(pre_cfg_index(), BMG_TMA_PRE_LAUNCH);
+#undef BMG_TMA_PRE_LAUNCH
+      return;
+    }
+  }
 #define BMG_TMA_LAUNCH(TT, NN, TX, TY, NT, MB, NS) \
   launch_tma_shape<TT, NN, TX, TY, NT, MB, NS>(L, m, mx, order, xout, s)
   if (m.nine)
@@ -328,6 +420,9 @@ void prepare_sweep_kernels() {
     BMG_TMA_DISPATCH(double, true, nine_cfg_index(), BMG_TMA_ALLOW);
     BMG_TMA_DISPATCH(float, true, nine_cfg_index(), BMG_TMA_ALLOW);
 #undef BMG_TMA_ALLOW
+#define BMG_TMA_PRE_ALLOW(TX, TY, NT, MB, NS) allow_tma_smem<double, false, TX, TY, NT, MB, NS, true>()
+    BMG_TMA_PRE_DISPATCH(pre_cfg_index(), BMG_TMA_PRE_ALLOW);
+#undef BMG_TMA_PRE_ALLOW
     sm_count();
     encode_tiled();
     return true;
@@ -368,6 +463,8 @@ template void launch_sweep<double>(const LevelV<double>&, bool, bool, const doub
 template void launch_sweep<float>(const LevelV<float>&, bool, bool, const float*, float*,
                                   cudaStream_t, const SweepMaps<float>*);
 template bool make_sweep_maps<double>(const LevelV<double>&, int*, SweepMaps<double>*);
+template void launch_prescale_coeffs<double>(const LevelV<double>&, cudaStream_t);
+template void launch_prescale_b<double>(const LevelV<double>&, cudaStream_t);
 template bool make_sweep_maps<float>(const LevelV<float>&, int*, SweepMaps<float>*);
 
 }  // namespace bmg

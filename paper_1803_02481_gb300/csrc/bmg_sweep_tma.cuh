@@ -106,7 +106,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // Shape of the staged tile.  NPH colour phases (2 on 5-point levels, 4 on
 // 9-point levels) need NPH halo rows and at least NPH halo columns; HA
 // columns are staged so that the box start stays 16-byte aligned.
-template <typename T, bool NINE, int TX, int TY, int NSTAGE = 2>
+template <typename T, bool NINE, int TX, int TY, int NSTAGE = 2, bool PRE = false>
 struct TmaTile {
   static constexpr int NPH = NINE ? 4 : 2;                  // colour phases
   static constexpr int ALIGN = int(16 / sizeof(T));        // elements per 16 bytes
@@ -114,7 +114,8 @@ struct TmaTile {
   static constexpr int BW = TX + 2 * HA;                    // box width (elements)
   static constexpr int BH = TY + 2 * NPH;                   // box height
   static constexpr int PLANE = BW * BH;                     // elements of one staged plane
-  static constexpr int NPL = NINE ? 7 : 5;                  // x, 1/C, W, S, b (, SW, NW)
+  // x, 1/C, W, S, b (, SW, NW); prescaled: x, b/C, W/C, S/C, E/C, N/C
+  static constexpr int NPL = PRE ? 6 : (NINE ? 7 : 5);
   static constexpr unsigned STAGE_BYTES = unsigned(NPL * PLANE * sizeof(T));
   static constexpr size_t SMEM = NSTAGE * size_t(STAGE_BYTES);
   static_assert(NSTAGE == 1 || NSTAGE == 2, "one or two stages");
@@ -125,10 +126,13 @@ struct TmaTile {
   static_assert((PLANE * sizeof(T)) % 128 == 0, "staged planes start 128-byte aligned");
 };
 
-// Planes a TMA sweep stages, in their order in a stage.
+// Planes a TMA sweep stages, in their order in a stage (a prescaled level:
+// x, b/C, W/C, S/C, E/C, N/C in the slots of x, 1/C, W, S, b, SW).
 enum TmaPlane { TP_X = 0, TP_IC, TP_W, TP_S, TP_B, TP_SW, TP_NW };
 
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE>
+// PRE: the level is prescaled (5-point only); the seven map parameters then
+// carry x, b/C, W/C, S/C, E/C, N/C and an unused one.
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_sweep_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mic,
                 const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap ms,
@@ -136,7 +140,8 @@ __global__ void __launch_bounds__(NT, MINB)
                 const __grid_constant__ CUtensorMap mnw, LevelV<T> L, T* __restrict__ xout,
                 unsigned order, int* __restrict__ err) {
   using namespace tma_detail;
-  using G = TmaTile<T, NINE, TX, TY, NSTAGE>;
+  static_assert(!(PRE && NINE), "prescaled levels are 5-point");
+  using G = TmaTile<T, NINE, TX, TY, NSTAGE, PRE>;
   constexpr int BW = G::BW, HA = G::HA, PL = G::PLANE, NPH = G::NPH;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -168,6 +173,7 @@ __global__ void __launch_bounds__(NT, MINB)
     tma_load_2d(d + TP_W * PL, &mw, X, Y, b);
     tma_load_2d(d + TP_S * PL, &ms, X, Y, b);
     tma_load_2d(d + TP_B * PL, &mb, X, Y, b);
+    if (PRE) tma_load_2d(d + TP_SW * PL, &msw, X, Y, b);
     if (NINE) {
       tma_load_2d(d + TP_SW * PL, &msw, X, Y, b);
       tma_load_2d(d + TP_NW * PL, &mnw, X, Y, b);
@@ -240,6 +246,12 @@ __global__ void __launch_bounds__(NT, MINB)
               unsigned(j0 + r - NPH - 1) >= unsigned(ny))
             continue;
           const int o = r * BW + c;
+          if (PRE) {
+            T* xp = sx + o;
+            *xp = gs_pre_apply<T>(sic[o], sw[o], sb[o], ss[o], ssw[o],
+                                  [&](int dx, int dy) { return xp[dx + dy * BW]; });
+            continue;
+          }
           GsCoef<T, NINE> cf_;
           cf_.b = sb[o];
           cf_.ic = sic[o];

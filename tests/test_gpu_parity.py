@@ -188,6 +188,31 @@ def test_every_threshold_gives_identical_iterates(name):
         hg.destroy()
 
 
+def test_prescaled_fine_level_identical_in_every_kernel():
+    """A fine level wide enough for the TMA sweep runs on the prescaled
+    operator; the persistent kernel applies the same prescaled update when
+    the threshold hands it the finest level, so the iterates stay
+    bit-identical across thresholds; FP32 refinement is never prescaled."""
+    name = "wide2047x127"
+    pr = problem(name)
+    L = oracle_hierarchy(name).nlevels
+    ref = None
+    for thr in (1, L - 1, L):
+        hg = gpu_setup(name, coarse_threshold=thr)
+        assert hg.level_prescaled(L - 1) and not hg.level_prescaled(L - 2)
+        x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+        hg.destroy()
+        xn = x.cpu().numpy()
+        if ref is None:
+            ref = (xn, info.cycles, info.rel_resid)
+        else:
+            assert np.array_equal(xn, ref[0]), thr
+            assert info.cycles == ref[1] and info.rel_resid == ref[2]
+    hf = gpu_setup(name, precision=bm.BMG_FP32_REFINE)
+    assert not hf.level_prescaled(L - 1)
+    hf.destroy()
+
+
 def test_interp_residual_term_variant_matches_oracle():
     name = "random63"
     pr = problem(name)
