@@ -168,10 +168,13 @@ static bool encode_level(const LevelV<T>& L, const TmaCfg& c, int nph, int* err,
 // couplings divided by C in place of 1/C, W, S, b and takes four fused
 // multiply-adds per point instead of four and a product (environment
 // BMG_RB_PRESCALE=0 turns it off).  Only levels the TMA sweep handles.
+// Tile sides of the prescaled shapes (BMG_TMA_PRE_DISPATCH order).
+constexpr int kPreTile[6][2] = {{32, 16}, {64, 16}, {64, 12}, {32, 16}, {32, 8}, {32, 16}};
+
 static int pre_cfg_index() {
   static const int v = [] {
     const int k = env_int("BMG_TMA_PRE_CFG", 0);
-    return k >= 0 && k < 4 ? k : 0;
+    return k >= 0 && k < 6 ? k : 0;
   }();
   return v;
 }
@@ -220,10 +223,10 @@ bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m) {
   if (nine && L.nx < nine_tma_min_side()) return false;
   if (!encode_level<T>(L, tma_cfg<T>(nine), nine ? 4 : 2, err, m)) return false;
   if (!nine && L.PR[PR_B]) {
-    // the prescaled shapes stage boxes of 64 + 4 columns and 16 + 4 or 8 + 4 rows
-    const int bh = pre_cfg_index() == 2 ? 12 : 20;
+    // the prescaled shapes stage boxes of (TX + 4) x (TY + 4)
+    const int bw = kPreTile[pre_cfg_index()][0] + 4, bh = kPreTile[pre_cfg_index()][1] + 4;
     auto enc = [&](CUtensorMap* mm, const T* base) {
-      return encode_plane<T>(mm, base, L.pitch, L.ny, 68, bh);
+      return encode_plane<T>(mm, base, L.pitch, L.ny, bw, bh);
     };
     if (!(enc(&m->x, L.x) && enc(&m->x2, L.x2) && enc(&m->pb, L.PR[PR_B]) &&
           enc(&m->pw, L.PR[PR_W]) && enc(&m->pe, L.PR[PR_E]) && enc(&m->ps, L.PR[PR_S]) &&
@@ -291,10 +294,12 @@ static void launch_tma_pre(const LevelV<double>& L, const SweepMaps<double>& m,
 #define BMG_TMA_PRE_DISPATCH(K, BODY)      \
   do {                                     \
     switch (K) {                           \
-      case 1: BODY(64, 16, 512, 1, 2); break; \
-      case 2: BODY(64, 8, 512, 2, 2); break;  \
-      case 3: BODY(64, 16, 608, 2, 1); break; \
-      default: BODY(64, 16, 512, 3, 1); break; \
+      case 1: BODY(64, 16, 512, 3, 1); break; \
+      case 2: BODY(64, 12, 512, 2, 2); break; \
+      case 3: BODY(32, 16, 384, 3, 2); break; \
+      case 4: BODY(32, 8, 128, 5, 2); break;  \
+      case 5: BODY(32, 16, 128, 3, 2); break; \
+      default: BODY(32, 16, 256, 3, 2); break; \
     }                                      \
   } while (0)
 
