@@ -117,9 +117,8 @@ __global__ void k3_assemble(const double* __restrict__ k, Lev3 L, int* err) {
 // offset order (dk, dj, di) ascending, products and sums unfused.
 // ---------------------------------------------------------------------------
 
-__global__ void k3_interp_weights(Lev3 F, int pass, int* err) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
-  if (i > F.nx) return;
+// The weights of fine point (i, j, k) if it belongs to the pass.
+__device__ void weights_point(const Lev3& F, int i, int j, int k, int pass, int* err) {
   const int fr[3] = {i & 1, j & 1, k & 1};    // 1: between coarse points in that direction
   const int nb = fr[0] + fr[1] + fr[2];
   if (nb != pass) return;
@@ -195,6 +194,14 @@ __global__ void k3_interp_weights(Lev3 F, int pass, int* err) {
   }
 }
 
+// One thread per pair of points i = 2t + 1, 2t + 2 of a row (j and k fixed
+// per block): the points of one pass then fill whole warps.
+__global__ void k3_interp_weights(Lev3 F, int pass, int* err) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y + 1, k = blockIdx.z + 1;
+  if (2 * t + 1 <= F.nx) weights_point(F, 2 * t + 1, j, k, pass, err);
+  if (2 * t + 2 <= F.nx) weights_point(F, 2 * t + 2, j, k, pass, err);
+}
+
 // ---------------------------------------------------------------------------
 // Galerkin product: one thread per coarse point computes its 14 stored
 // entries from the definition A_c(I, I + d) = sum_f sum_g P(f, I) A(f, g)
@@ -228,20 +235,26 @@ __global__ void k3_rap(Lev3 F, Lev3 Cc, int* err) {
     const int I2 = I + di, J2 = J + dj, K2 = K + dk;
     double val = 0.0;
     if (I2 >= 1 && J2 >= 1 && K2 >= 1 && I2 <= Cc.nx && J2 <= Cc.ny && K2 <= Cc.nz) {
+      // per direction only the pairs (e, h) with g = e + h - 2d in -1..1 can
+      // contribute (fine g in the support of I + d); the loops visit exactly
+      // those, in the order of the full 3 x 3 x 3 x 3 x 3 x 3 enumeration
+      auto lo = [](int e, int d) { return max(-1, -1 - e + 2 * d); };
+      auto hi = [](int e, int d) { return min(1, 1 - e + 2 * d); };
       for (int ez = -1; ez <= 1; ++ez)
         for (int ey = -1; ey <= 1; ++ey)
           for (int ex = -1; ex <= 1; ++ex) {
+            if (lo(ex, di) > hi(ex, di) || lo(ey, dj) > hi(ey, dj) || lo(ez, dk) > hi(ez, dk))
+              continue;
             const int fi = 2 * I + ex, fj = 2 * J + ey, fk = 2 * K + ez;
             if (fi > F.nx || fj > F.ny || fk > F.nz) continue;
             const int of = idx3(F, fi, fj, fk);
             const double wf = F.P[support_slot(ex, ey, ez)][of];
             if (wf == 0.0) continue;
             double s = 0.0;
-            for (int hz = -1; hz <= 1; ++hz)
-              for (int hy = -1; hy <= 1; ++hy)
-                for (int hx = -1; hx <= 1; ++hx) {
+            for (int hz = lo(ez, dk); hz <= hi(ez, dk); ++hz)
+              for (int hy = lo(ey, dj); hy <= hi(ey, dj); ++hy)
+                for (int hx = lo(ex, di); hx <= hi(ex, di); ++hx) {
                   const int gx = ex + hx - 2 * di, gy = ey + hy - 2 * dj, gz = ez + hz - 2 * dk;
-                  if (gx < -1 || gx > 1 || gy < -1 || gy > 1 || gz < -1 || gz > 1) continue;
                   const int gi = fi + hx, gj = fj + hy, gk = fk + hz;
                   if (gi < 1 || gj < 1 || gk < 1 || gi > F.nx || gj > F.ny || gk > F.nz) continue;
                   const int og = idx3(F, gi, gj, gk);
@@ -732,7 +745,7 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
   for (int l = L - 1; l >= 1; --l) {
     const Lev3& V = h->lv[l];
     for (int pass = 0; pass <= 3; ++pass) {
-      k3_interp_weights<<<grid_pts(V), kT, 0, s>>>(V, pass, h->err);
+      k3_interp_weights<<<dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), kT, 0, s>>>(V, pass, h->err);
       count_launch();
     }
     k3_rap<<<grid_pts(h->lv[l - 1]), kT, 0, s>>>(V, h->lv[l - 1], h->err);
