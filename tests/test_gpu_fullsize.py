@@ -221,3 +221,48 @@ def test_3d_solve_at_255_satisfies_the_stop_test():
     rel = float(np.linalg.norm(r) / np.linalg.norm(b))
     assert info.rel_resid <= 1e-10 and rel <= 1.2e-10, (rel, info.rel_resid)
     assert abs(rel - info.rel_resid) <= 0.2e-10, (rel, info.rel_resid)
+
+
+def test_3d_setup_sampled_against_oracle_windows():
+    """3D at the benchmark size (255^3 block field): interpolation weights
+    and Galerkin entries of the GPU hierarchy against the 3D oracle on 17^3
+    windows of the GPU's own finest level (interior points: two fine cells,
+    or two coarse cells, from a window face that is not a wall)."""
+    from oracle import boxmg3d_oracle as O3
+    from tests.test_gpu_parity3d import interp_to_csr, stencil_to_csr
+    n, block, nw = 255, 16, 17
+    rng = np.random.default_rng(95)
+    nb = -(-n // block)
+    kb = 10.0 ** rng.uniform(-2, 2, (nb, nb, nb))
+    k = np.repeat(np.repeat(np.repeat(kb, block, 0), block, 1), block, 2)[:n, :n, :n]
+    h = bm.setup3(dev(k))
+    L = h.nlevels
+    sten = h.level_stencil(L - 1)
+    interp = h.level_interp(L - 1)
+    coarse = h.level_stencil(L - 2)
+    h.destroy()
+    nc, cw = n // 2, nw // 2
+    for o in [(0, 0, 0), (96, 32, 160), (238, 238, 238), (0, 120, 64)]:   # 0-based, even
+        sl = np.s_[:, o[2]:o[2] + nw, o[1]:o[1] + nw, o[0]:o[0] + nw]
+        a_w = stencil_to_csr(sten[sl], (nw, nw, nw))
+        p_o = O3.interpolation(a_w, (nw, nw, nw))
+        p_g = interp_to_csr(np.ascontiguousarray(interp[sl]), (nw, nw, nw))
+
+        lo = [0 if oo == 0 else 2 for oo in o]
+        hi = [nw if oo + nw == n else nw - 2 for oo in o]
+        kk, jj, ii = np.meshgrid(np.arange(lo[2], hi[2]), np.arange(lo[1], hi[1]),
+                                 np.arange(lo[0], hi[0]), indexing="ij")
+        rows = ((kk * nw + jj) * nw + ii).ravel()
+        assert abs(p_g[rows] - p_o[rows]).max() <= 1e-12, o
+        ac_o = O3.galerkin(a_w, p_o, (cw, cw, cw))
+        co = tuple(oo // 2 for oo in o)
+        cs = np.s_[:, co[2]:co[2] + cw, co[1]:co[1] + cw, co[0]:co[0] + cw]
+        ac_g = stencil_to_csr(np.ascontiguousarray(coarse[cs]), (cw, cw, cw))
+        clo = [0 if oo == 0 else 2 for oo in o]
+        chi = [cw if oo + nw == n else cw - 2 for oo in o]
+        kk, jj, ii = np.meshgrid(np.arange(clo[2], chi[2]), np.arange(clo[1], chi[1]),
+                                 np.arange(clo[0], chi[0]), indexing="ij")
+        crow = ((kk * cw + jj) * cw + ii).ravel()
+        diag = np.abs(ac_o.diagonal())[crow]
+        err = abs(ac_g[crow] - ac_o[crow]).max(axis=1).toarray().ravel()
+        assert (err / diag).max() <= 1e-12, o
