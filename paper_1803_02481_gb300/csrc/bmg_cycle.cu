@@ -37,29 +37,58 @@ __global__ void k_restrict(LevelV<T> F, const T* __restrict__ r, LevelV<T> Cc, i
   if (zero_x) Cc.x[c] = T(0);
 }
 
+// Two adjacent values of T as one aligned vector access.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+
 // One thread per coarse cell (I, J), 0 <= I <= ncx, 0 <= J <= ncy: the four
 // fine points (2I+1..2I+2, 2J+1..2J+2) -- a cell centre, a y-edge, an x-edge
 // and a coarse point -- so every thread does the same work (no divergence on
-// the point type) and the weight planes are read contiguously.
+// the point type) and the weight planes are read contiguously.  The points
+// (2I+1, j) and (2I+2, j) of a row are one vector load and store: element 1
+// of every row starts a 128-byte line and the pitch is a multiple of it, so
+// the pair starts on a multiple of 2 * sizeof(T) bytes.  A pair that would
+// reach the ghost column nx + 1 is done point by point.
 template <typename T>
 __global__ void k_interp(LevelV<T> F, const T* __restrict__ xc, int add_rc, T* __restrict__ out) {
+  using V = typename Pair<T>::type;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y;
   const int ncx = (F.nx - 1) >> 1;
   if (I > ncx) return;
+  const int i = 2 * I + 1;
 #pragma unroll
   for (int dj = 1; dj <= 2; ++dj) {
     const int j = 2 * J + dj;
     if (j > F.ny) continue;
-#pragma unroll
-    for (int di = 1; di <= 2; ++di) {
-      const int i = 2 * I + di;
-      if (i > F.nx) continue;
-      const int o = j * F.pitch + i;
-      T corr = interp_value<T>(F.P, F.cpitch, xc, i, j);
+    const int o = j * F.pitch + i;
+    if (i + 1 <= F.nx) {
+      T c0 = interp_value<T>(F.P, F.cpitch, xc, i, j);
+      T c1 = interp_value<T>(F.P, F.cpitch, xc, i + 1, j);
       // Section 3 interpolation equations: + r/C at points that are not
-      // coarse points (r is the residual computed after pre-smoothing).
-      if (add_rc && ((i | j) & 1)) corr = fma(F.r[o], F.iC[o], corr);
+      // coarse points (r is the residual computed after pre-smoothing); i
+      // is odd, so (i, j) never is one and (i + 1, j) is one for even j.
+      if (add_rc) {
+        const V rv = *reinterpret_cast<const V*>(F.r + o);
+        const V cv = *reinterpret_cast<const V*>(F.iC + o);
+        c0 = fma(rv.x, cv.x, c0);
+        if (j & 1) c1 = fma(rv.y, cv.y, c1);
+      }
+      V xv = *reinterpret_cast<const V*>(F.x + o);
+      xv.x += c0;
+      xv.y += c1;
+      *reinterpret_cast<V*>(out + o) = xv;
+    } else if (i <= F.nx) {
+      T corr = interp_value<T>(F.P, F.cpitch, xc, i, j);
+      if (add_rc) corr = fma(F.r[o], F.iC[o], corr);
       out[o] = F.x[o] + corr;
     }
   }

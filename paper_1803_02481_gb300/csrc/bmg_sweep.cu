@@ -36,8 +36,10 @@ constexpr int kStreamNT = 64, kStreamR = 32;
 //    threads, two blocks per SM, two stages (memory-bound: four stages per
 //    SM in flight).
 //  * 9-point levels (2047^2 and 4095^2 levels): one stage per block and four
-//    blocks per SM (FP64 32 x 16 tiles, FP32 64 x 16): with four colour
-//    phases per tile, more resident warps beat a second stage.
+//    blocks per SM (FP64 40 x 16 tiles, FP32 64 x 16): with four colour
+//    phases per tile, more resident warps beat a second stage.  40 x 16 is
+//    the widest FP64 tile of which four blocks fit an SM; wider tiles cut the
+//    redundant halo work but lose the fourth block.
 // BMG_TMA_CFG (5-point) and BMG_TMA9_CFG (9-point) select other entries, for
 // measurements.
 struct TmaCfg {
@@ -46,10 +48,10 @@ struct TmaCfg {
 constexpr TmaCfg kRb64[] = {{64, 16, 608, 2, 2}, {64, 16, 512, 2, 2}, {64, 16, 512, 4, 1}};
 constexpr TmaCfg kRb32[] = {{128, 16, 256, 2, 2}, {64, 16, 256, 3, 2}, {128, 16, 256, 4, 1}};
 constexpr int kNumRbCfg = 3;
-constexpr TmaCfg kNine64[] = {{32, 16, 256, 4, 1}, {32, 32, 512, 1, 2}, {32, 16, 256, 2, 2},
-                              {64, 16, 512, 1, 2}, {32, 16, 224, 2, 2}, {32, 32, 512, 2, 1}};
-constexpr TmaCfg kNine32[] = {{64, 16, 256, 4, 1}, {64, 32, 256, 2, 1}, {64, 16, 256, 2, 2},
-                              {32, 16, 256, 3, 2}, {128, 16, 256, 2, 1}, {32, 32, 256, 4, 1}};
+constexpr TmaCfg kNine64[] = {{40, 16, 256, 4, 1}, {32, 16, 256, 4, 1}, {36, 16, 256, 4, 1},
+                              {36, 16, 192, 4, 1}, {28, 20, 192, 4, 1}, {40, 16, 192, 4, 1}};
+constexpr TmaCfg kNine32[] = {{64, 16, 256, 4, 1}, {64, 16, 256, 5, 1}, {80, 16, 256, 4, 1},
+                              {128, 8, 256, 4, 1}, {64, 32, 256, 2, 1}, {32, 32, 256, 4, 1}};
 constexpr int kNumNineCfg = 6;
 
 static int env_int(const char* name, int dflt) {
@@ -150,7 +152,7 @@ static bool encode_level(const LevelV<T>& L, const TmaCfg& c, int nph, int* err,
   std::memset(static_cast<void*>(m), 0, sizeof(*m));
   const int align = int(16 / sizeof(T));
   const int ha = nph > align ? nph : align;
-  const int bw = c.tx + 2 * ha, bh = c.ty + 2 * nph;
+  const int bw = c.tx + 2 * ha, bh = c.ty + 2 * kTmaHaloRows;
   auto enc = [&](CUtensorMap* mm, const T* base) {
     return encode_plane<T>(mm, base, L.pitch, L.ny, bw, bh);
   };
@@ -321,19 +323,19 @@ static void launch_tma_pre(const LevelV<double>& L, const SweepMaps<double>& m,
       }                                                                \
     } else if constexpr (sizeof(T) == 8) {                             \
       switch (K) {                                                     \
-        case 1: BODY(T, true, 32, 32, 512, 1, 2); break;               \
-        case 2: BODY(T, true, 32, 16, 256, 2, 2); break;               \
-        case 3: BODY(T, true, 64, 16, 512, 1, 2); break;               \
-        case 4: BODY(T, true, 32, 16, 224, 2, 2); break;               \
-        case 5: BODY(T, true, 32, 32, 512, 2, 1); break;               \
-        default: BODY(T, true, 32, 16, 256, 4, 1); break;              \
+        case 1: BODY(T, true, 32, 16, 256, 4, 1); break;               \
+        case 2: BODY(T, true, 36, 16, 256, 4, 1); break;               \
+        case 3: BODY(T, true, 36, 16, 192, 4, 1); break;               \
+        case 4: BODY(T, true, 28, 20, 192, 4, 1); break;               \
+        case 5: BODY(T, true, 40, 16, 192, 4, 1); break;               \
+        default: BODY(T, true, 40, 16, 256, 4, 1); break;              \
       }                                                                \
     } else {                                                           \
       switch (K) {                                                     \
-        case 1: BODY(T, true, 64, 32, 256, 2, 1); break;               \
-        case 2: BODY(T, true, 64, 16, 256, 2, 2); break;               \
-        case 3: BODY(T, true, 32, 16, 256, 3, 2); break;               \
-        case 4: BODY(T, true, 128, 16, 256, 2, 1); break;              \
+        case 1: BODY(T, true, 64, 16, 256, 5, 1); break;               \
+        case 2: BODY(T, true, 80, 16, 256, 4, 1); break;               \
+        case 3: BODY(T, true, 128, 8, 256, 4, 1); break;               \
+        case 4: BODY(T, true, 64, 32, 256, 2, 1); break;               \
         case 5: BODY(T, true, 32, 32, 256, 4, 1); break;               \
         default: BODY(T, true, 64, 16, 256, 4, 1); break;              \
       }                                                                \

@@ -9,15 +9,26 @@
 // one while the copies of its next tile fill the other; with one stage,
 // the other blocks on the SM do their arithmetic while a block waits.
 //
-// The relaxation itself is the redundant-halo scheme of the tiled kernel:
-// colour phase k of NPH (2 red-black, 4 four-colour) is updated on the tile
-// grown by NPH - 1 - k cells, so no block reads another block's new values.  The new iterate goes to a
-// second buffer.  Per-point arithmetic is gs_apply, as in every other
-// kernel, so the result is bit-identical to theirs.
+// The relaxation itself is a redundant-halo scheme: colour phase k is
+// updated on the tile grown by (GX_k, GY_k) cells, so no block reads another
+// block's new values.  The new iterate goes to a second buffer.  Per-point
+// arithmetic is gs_apply, as in every other kernel, so the result is
+// bit-identical to theirs.
 //
-// Staged box: rows j0-NPH .. j0+TY+NPH-1 and columns i0-HA .. i0+TX+HA-1
-// of each plane, (i0, j0) the tile's first interior point.  HA >= NPH columns
-// make 16 bytes a whole number of times, which keeps the box's first column
+// Growth.  A point of a later phase reads the points of an earlier phase at
+// offsets (dx, dy) with |dx| = 1 exactly when the two sub-lattices differ in
+// column parity and |dy| = 1 exactly when they differ in row parity, so the
+// earlier phase must be relaxed on the later phase's region grown by those
+// amounts.  Red-black (5-point): (1, 1) then (0, 0).  Four colours in the
+// order (0,0), (0,1), (1,0), (1,1) of (row, column) parities, or its reverse:
+// (3, 1), (2, 1), (1, 0), (0, 0) -- the first two phases differ from the
+// last in column parity, so the growth is mostly along x, and the tile
+// needs two halo rows instead of four.
+//
+// Staged box: rows j0-HY .. j0+TY+HY-1 and columns i0-HA .. i0+TX+HA-1 of
+// each plane, (i0, j0) the tile's first interior point; HY = 2 rows and
+// HA >= NPH columns (old values one cell beyond the widest phase region).
+// HA is a whole number of 16-byte units, which keeps the box's first column
 // on a 16-byte boundary (interior rows start on a 128-byte boundary).  Rows and columns
 // outside the plane read as zero, the Dirichlet ghost value.
 //
@@ -103,16 +114,27 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 
 }  // namespace tma_detail
 
+// Halo rows of every staged box (both colour schemes grow by at most one
+// row before the last phase).
+constexpr int kTmaHaloRows = 2;
+
+// Growth of colour phase k (of nph) along x and y, as derived above.
+__host__ __device__ constexpr int tma_grow_x(int nph, int k) { return nph - 1 - k; }
+__host__ __device__ constexpr int tma_grow_y(int nph, int k) {
+  return nph == 4 ? (k < 2 ? 1 : 0) : nph - 1 - k;
+}
+
 // Shape of the staged tile.  NPH colour phases (2 on 5-point levels, 4 on
-// 9-point levels) need NPH halo rows and at least NPH halo columns; HA
-// columns are staged so that the box start stays 16-byte aligned.
+// 9-point levels) need kTmaHaloRows halo rows and at least NPH halo columns;
+// HA columns are staged so that the box start stays 16-byte aligned.
 template <typename T, bool NINE, int TX, int TY, int NSTAGE = 2, bool PRE = false>
 struct TmaTile {
   static constexpr int NPH = NINE ? 4 : 2;                  // colour phases
   static constexpr int ALIGN = int(16 / sizeof(T));        // elements per 16 bytes
   static constexpr int HA = NPH > ALIGN ? NPH : ALIGN;      // halo columns staged on each side
+  static constexpr int HY = kTmaHaloRows;                   // halo rows staged above and below
   static constexpr int BW = TX + 2 * HA;                    // box width (elements)
-  static constexpr int BH = TY + 2 * NPH;                   // box height
+  static constexpr int BH = TY + 2 * HY;                    // box height
   static constexpr int PLANE = BW * BH;                     // elements of one staged plane
   // x, 1/C, W, S, b (, SW, NW); prescaled: x, b/C, W/C, S/C, E/C, N/C
   static constexpr int NPL = PRE ? 6 : (NINE ? 7 : 5);
@@ -120,7 +142,10 @@ struct TmaTile {
   static constexpr size_t SMEM = NSTAGE * size_t(STAGE_BYTES);
   static_assert(NSTAGE == 1 || NSTAGE == 2, "one or two stages");
   static_assert(TX % 4 == 0 && TY % 2 == 0, "tile sides keep colours and TMA alignment");
-  static_assert(HA % ALIGN == 0 && HA % 2 == 0, "box start aligned, colour parity kept");
+  static_assert(HA % ALIGN == 0 && HA % 2 == 0 && HY % 2 == 0,
+                "box start aligned, colour parity kept");
+  static_assert(tma_grow_x(NPH, 0) + 1 <= HA && tma_grow_y(NPH, 0) + 1 <= HY,
+                "old values staged one cell beyond the widest phase region");
   static_assert(BW <= 256 && BH <= 256, "TMA box sides are at most 256 elements");
   static_assert((BW * sizeof(T)) % 16 == 0, "TMA box rows are multiples of 16 bytes");
   static_assert((PLANE * sizeof(T)) % 128 == 0, "staged planes start 128-byte aligned");
@@ -142,7 +167,7 @@ __global__ void __launch_bounds__(NT, MINB)
   using namespace tma_detail;
   static_assert(!(PRE && NINE), "prescaled levels are 5-point");
   using G = TmaTile<T, NINE, TX, TY, NSTAGE, PRE>;
-  constexpr int BW = G::BW, HA = G::HA, PL = G::PLANE, NPH = G::NPH;
+  constexpr int BW = G::BW, HA = G::HA, HY = G::HY, PL = G::PLANE, NPH = G::NPH;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[2];
   const int nx = L.nx, ny = L.ny, p = L.pitch;
@@ -164,7 +189,7 @@ __global__ void __launch_bounds__(NT, MINB)
   auto issue = [&](int s, int t) {
     const int bx = t % ntx, by = t / ntx;
     const int X = bx * TX + 1 - HA + base_shift<T>();   // tensor column of the box start
-    const int Y = by * TY + 1 - NPH;                    // tensor row (= j) of the box start
+    const int Y = by * TY + 1 - HY;                     // tensor row (= j) of the box start
     T* d = s ? stage1 : stage0;
     uint64_t* b = &bar[s];
     mbar_expect_tx(b, G::STAGE_BYTES);
@@ -212,15 +237,15 @@ __global__ void __launch_bounds__(NT, MINB)
     const T* const snw = sx + TP_NW * PL;
     const int bx = t % ntx, by = t / ntx;
     const int i0 = bx * TX + 1, j0 = by * TY + 1;
-    // Shared cell (r, c) holds domain point (i0 + c - HA, j0 + r - NPH).  With
-    // TX, TY, HA and NPH even, the 0-based domain parities of (r, c) are
-    // (r & 1, c & 1).  Phase k is relaxed on the tile grown by NPH - 1 - k.
+    // Shared cell (r, c) holds domain point (i0 + c - HA, j0 + r - HY).  With
+    // TX, TY, HA and HY even, the 0-based domain parities of (r, c) are
+    // (r & 1, c & 1).  Phase k is relaxed on the tile grown by (gx, gy).
 #pragma unroll
     for (int k = 0; k < NPH; ++k) {
       const unsigned mask = (order >> (4 * k)) & 0xFu;
-      const int ring = NPH - 1 - k;
-      const int r0 = NPH - ring, r1 = NPH + TY + ring;
-      const int c0 = HA - ring, c1 = HA + TX + ring;
+      const int gx = tma_grow_x(NPH, k), gy = tma_grow_y(NPH, k);
+      const int r0 = HY - gy, r1 = HY + TY + gy;
+      const int c0 = HA - gx, c1 = HA + TX + gx;
 #pragma unroll
       for (int sl = 0; sl < 4; ++sl) {
         if (!(mask & (1u << sl))) continue;
@@ -241,9 +266,9 @@ __global__ void __launch_bounds__(NT, MINB)
             cc -= ncol;
             ++rr;
           }
-          // domain point (i, j) = (i0 + c - HA, j0 + r - NPH) inside 1..nx, 1..ny
+          // domain point (i, j) = (i0 + c - HA, j0 + r - HY) inside 1..nx, 1..ny
           if (unsigned(i0 + c - HA - 1) >= unsigned(nx) ||
-              unsigned(j0 + r - NPH - 1) >= unsigned(ny))
+              unsigned(j0 + r - HY - 1) >= unsigned(ny))
             continue;
           const int o = r * BW + c;
           if (PRE) {
@@ -274,7 +299,7 @@ __global__ void __launch_bounds__(NT, MINB)
     for (int e = tid; e < TX * TY; e += NT) {
       const int r = e / TX, c = e - r * TX;
       const int i = i0 + c, j = j0 + r;
-      if (i <= nx && j <= ny) xout[j * p + i] = sx[(r + NPH) * BW + c + HA];
+      if (i <= nx && j <= ny) xout[j * p + i] = sx[(r + HY) * BW + c + HA];
     }
     // this stage is refilled by the copies issued next
     fence_proxy_async();
