@@ -2,14 +2,15 @@
 // single-problem and the batched kernels.
 //
 // A thread block owns a TX x TY tile.  It loads the old iterate on the tile
-// plus a halo of NC cells into shared memory, then relaxes the colours in
-// order: colour k (0-based) is updated on the tile grown by NC-1-k cells, so
-// the last colour's neighbours of earlier colours are all available without
-// reading another block's new values.  The points a block relaxes outside its
-// tile are recomputed by the neighbouring block from the same old values, so
-// every block sees exactly what an in-place sweep would see.  The new iterate
-// goes to a second buffer (old and new never alias); only the tile is
-// written.  Per-point arithmetic is gs_load/gs_apply.
+// plus a halo of NC columns and 2 rows into shared memory, then relaxes the
+// colours in order: colour k (0-based) is updated on the tile grown by
+// (colour_grow_x(NC, k), colour_grow_y(NC, k)) cells, so the last colour's
+// neighbours of earlier colours are all available without reading another
+// block's new values.  The points a block relaxes outside its tile are
+// recomputed by the neighbouring block from the same old values, so every
+// block sees exactly what an in-place sweep would see.  The new iterate goes
+// to a second buffer (old and new never alias); only the tile is written.
+// Per-point arithmetic is gs_load/gs_apply.
 #pragma once
 
 #include "bmg_internal.h"
@@ -23,17 +24,32 @@ __host__ __device__ constexpr unsigned four_order(bool reverse) {
   return reverse ? 0x1248u : 0x8421u;
 }
 
+// Growth of colour phase k of nc (2: rb_order, 4: four_order, either
+// direction) for a sweep that relaxes each tile once.  A later phase reads
+// an earlier phase's points at offsets whose x part is +-1 exactly when the
+// two sub-lattices differ in column parity and whose y part is +-1 exactly
+// when they differ in row parity; the earlier phase must cover the later
+// one's region grown by those amounts.  Red-black: (1, 1), (0, 0).  Four
+// colours (0,0), (0,1), (1,0), (1,1) of (row, column) parities or the
+// reverse: (3, 1), (2, 1), (1, 0), (0, 0).  Every phase needs old values one
+// cell beyond its region: nc halo columns and 2 halo rows.
+__host__ __device__ constexpr int colour_grow_x(int nc, int k) { return nc - 1 - k; }
+__host__ __device__ constexpr int colour_grow_y(int nc, int k) {
+  return nc == 4 ? (k < 2 ? 1 : 0) : nc - 1 - k;
+}
+constexpr int kColourHaloRows = 2;
+
 template <typename T, bool NINE, int TX, int TY, int NT, int UB = (NINE ? 3 : 1)>
 __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restrict__ xin,
                                            T* __restrict__ xout, unsigned order, int bx, int by) {
   constexpr int NC = NINE ? 4 : 2;
-  constexpr int H = NC;
-  constexpr int SX = TX + 2 * H, SY = TY + 2 * H;
+  constexpr int H = NC, HY = kColourHaloRows;   // halo columns, halo rows
+  constexpr int SX = TX + 2 * H, SY = TY + 2 * HY;
   __shared__ T xs[SY * SX];
   const int nx = L.nx, ny = L.ny, p = L.pitch;
   // domain coordinates of shared-memory cell (0, 0)
   const int ib = bx * TX + 1 - H;
-  const int jb = by * TY + 1 - H;
+  const int jb = by * TY + 1 - HY;
 
   for (int e = threadIdx.x; e < SX * SY; e += NT) {
     const int r = e / SX, c = e - r * SX;
@@ -47,9 +63,9 @@ __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restri
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     const unsigned mask = (order >> (4 * k)) & 0xFu;
-    const int ring = NC - 1 - k;
-    const int r0 = H - ring, r1 = H + TY + ring;   // region rows [r0, r1)
-    const int c0 = H - ring, c1 = H + TX + ring;
+    const int gx = colour_grow_x(NC, k), gy = colour_grow_y(NC, k);
+    const int r0 = HY - gy, r1 = HY + TY + gy;   // region rows [r0, r1)
+    const int c0 = H - gx, c1 = H + TX + gx;
 #pragma unroll
     for (int sl = 0; sl < 4; ++sl) {
       if (!(mask & (1u << sl))) continue;
@@ -94,8 +110,8 @@ __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restri
 
   for (int e = threadIdx.x; e < TX * TY; e += NT) {
     const int r = e / TX, c = e - r * TX;
-    const int i = ib + H + c, j = jb + H + r;
-    if (i <= nx && j <= ny) xout[j * p + i] = xs[(r + H) * SX + c + H];
+    const int i = ib + H + c, j = jb + HY + r;
+    if (i <= nx && j <= ny) xout[j * p + i] = xs[(r + HY) * SX + c + H];
   }
 }
 

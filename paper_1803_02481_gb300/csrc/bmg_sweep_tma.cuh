@@ -40,6 +40,7 @@
 #include <cuda.h>
 
 #include "bmg_internal.h"
+#include "bmg_sweep_tile.cuh"
 
 namespace bmg {
 
@@ -115,14 +116,8 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 }  // namespace tma_detail
 
 // Halo rows of every staged box (both colour schemes grow by at most one
-// row before the last phase).
-constexpr int kTmaHaloRows = 2;
-
-// Growth of colour phase k (of nph) along x and y, as derived above.
-__host__ __device__ constexpr int tma_grow_x(int nph, int k) { return nph - 1 - k; }
-__host__ __device__ constexpr int tma_grow_y(int nph, int k) {
-  return nph == 4 ? (k < 2 ? 1 : 0) : nph - 1 - k;
-}
+// row before the last phase; colour_grow_x/y give the growth).
+constexpr int kTmaHaloRows = kColourHaloRows;
 
 // Shape of the staged tile.  NPH colour phases (2 on 5-point levels, 4 on
 // 9-point levels) need kTmaHaloRows halo rows and at least NPH halo columns;
@@ -144,7 +139,7 @@ struct TmaTile {
   static_assert(TX % 4 == 0 && TY % 2 == 0, "tile sides keep colours and TMA alignment");
   static_assert(HA % ALIGN == 0 && HA % 2 == 0 && HY % 2 == 0,
                 "box start aligned, colour parity kept");
-  static_assert(tma_grow_x(NPH, 0) + 1 <= HA && tma_grow_y(NPH, 0) + 1 <= HY,
+  static_assert(colour_grow_x(NPH, 0) + 1 <= HA && colour_grow_y(NPH, 0) + 1 <= HY,
                 "old values staged one cell beyond the widest phase region");
   static_assert(BW <= 256 && BH <= 256, "TMA box sides are at most 256 elements");
   static_assert((BW * sizeof(T)) % 16 == 0, "TMA box rows are multiples of 16 bytes");
@@ -243,7 +238,7 @@ __global__ void __launch_bounds__(NT, MINB)
 #pragma unroll
     for (int k = 0; k < NPH; ++k) {
       const unsigned mask = (order >> (4 * k)) & 0xFu;
-      const int gx = tma_grow_x(NPH, k), gy = tma_grow_y(NPH, k);
+      const int gx = colour_grow_x(NPH, k), gy = colour_grow_y(NPH, k);
       const int r0 = HY - gy, r1 = HY + TY + gy;
       const int c0 = HA - gx, c1 = HA + TX + gx;
 #pragma unroll
