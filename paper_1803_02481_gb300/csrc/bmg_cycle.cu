@@ -16,75 +16,14 @@ constexpr int kTB = 128;
 inline int cdiv(long a, long b) { return int((a + b - 1) / b); }
 
 
-// Two adjacent values of T as one aligned vector access.
-template <typename T>
-struct Pair;
-template <>
-struct Pair<double> {
-  using type = double2;
-};
-template <>
-struct Pair<float> {
-  using type = float2;
-};
-
-// Element 1 of every row starts a 128-byte line and the pitch is a multiple
-// of it, so a pair (i, i + 1) with i odd starts on a multiple of
-// 2 * sizeof(T) bytes.
-template <typename T>
-__device__ __forceinline__ typename Pair<T>::type load_pair(const T* q) {
-  return *reinterpret_cast<const typename Pair<T>::type*>(q);
-}
-
-// r = b - A x at the points (i, j) and (i + 1, j), i odd, of one thread:
-// the rows of x and the coefficient planes are read as aligned pairs plus the
-// single values on either side.  Each point's fused multiply-adds run in
-// resid_value's order, so r is bit-identical to it.
 template <typename T, bool NINE>
 __global__ void k_residual(LevelV<T> L, const T* __restrict__ x, const T* __restrict__ b,
                            T* __restrict__ r) {
-  using V = typename Pair<T>::type;
-  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y + 1;
   if (i > L.nx) return;
-  const int p = L.pitch;
-  const int o = j * p + i;
-  if (i + 1 > L.nx) {
-    r[o] = resid_value<T, NINE>(L, x, b[o], o);
-    return;
-  }
-  const V xc = load_pair(x + o), xs = load_pair(x + o - p), xn = load_pair(x + o + p);
-  const V cv = load_pair(L.C + o), bv = load_pair(b + o), wv = load_pair(L.W + o);
-  const V sv = load_pair(L.S + o), nv = load_pair(L.S + o + p);
-  const T xw = x[o - 1], xe = x[o + 2], we = L.W[o + 2];
-  T r0 = fma(-cv.x, xc.x, bv.x);
-  r0 = fma(wv.x, xw, r0);
-  r0 = fma(wv.y, xc.y, r0);
-  r0 = fma(sv.x, xs.x, r0);
-  r0 = fma(nv.x, xn.x, r0);
-  T r1 = fma(-cv.y, xc.y, bv.y);
-  r1 = fma(wv.y, xc.x, r1);
-  r1 = fma(we, xe, r1);
-  r1 = fma(sv.y, xs.y, r1);
-  r1 = fma(nv.y, xn.y, r1);
-  if (NINE) {
-    const V swv = load_pair(L.SW + o), nwv = load_pair(L.NW + o);
-    const T xsw = x[o - p - 1], xse = x[o - p + 2], xnw = x[o + p - 1], xne = x[o + p + 2];
-    const T se0 = L.NW[o + 1 - p], se1 = L.NW[o + 2 - p];
-    const T ne0 = L.SW[o + 1 + p], ne1 = L.SW[o + 2 + p];
-    r0 = fma(swv.x, xsw, r0);
-    r0 = fma(se0, xs.y, r0);
-    r0 = fma(nwv.x, xnw, r0);
-    r0 = fma(ne0, xn.y, r0);
-    r1 = fma(swv.y, xs.x, r1);
-    r1 = fma(se1, xse, r1);
-    r1 = fma(nwv.y, xn.x, r1);
-    r1 = fma(ne1, xne, r1);
-  }
-  V rv;
-  rv.x = r0;
-  rv.y = r1;
-  *reinterpret_cast<V*>(r + o) = rv;
+  const int o = j * L.pitch + i;
+  r[o] = resid_value<T, NINE>(L, x, b[o], o);
 }
 
 template <typename T>
@@ -97,6 +36,18 @@ __global__ void k_restrict(LevelV<T> F, const T* __restrict__ r, LevelV<T> Cc, i
   Cc.b[c] = restrict_value<T>(F.P, Cc.pitch, r, F.pitch, c, f);
   if (zero_x) Cc.x[c] = T(0);
 }
+
+// Two adjacent values of T as one aligned vector access.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+template <>
+struct Pair<float> {
+  using type = float2;
+};
 
 // One thread per coarse cell (I, J), 0 <= I <= ncx, 0 <= J <= ncy: the four
 // fine points (2I+1..2I+2, 2J+1..2J+2) -- a cell centre, a y-edge, an x-edge
@@ -299,7 +250,7 @@ __global__ void k_refine_update(LevelV<double> L, LevelV<float> F, const Scalars
 template <typename T>
 void launch_residual(const LevelV<T>& L, bool nine, const T* x, const T* b, T* r,
                      cudaStream_t s) {
-  const dim3 grid(cdiv((L.nx + 1) / 2, kTB), L.ny);   // two points per thread
+  const dim3 grid(cdiv(L.nx, kTB), L.ny);
   if (!nine) prof_begin(BMG_PROF_FINE_RESID, s);
   if (nine)
     k_residual<T, true><<<grid, kTB, 0, s>>>(L, x, b, r);
