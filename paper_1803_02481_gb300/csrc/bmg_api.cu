@@ -400,8 +400,12 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
     const bool nine = l != L - 1;
     if (nine) prof_begin(BMG_PROF_LEVELS, s);
     for (int k = 0; k < nu1; ++k) sweep(l, false);
-    launch_residual<T>(lv[l], nine, lv[l].x, lv[l].b, lv[l].r, s);
-    launch_restrict<T>(lv[l], lv[l].r, lv[l - 1], true, s);
+    if (!rc && rr_fused(nine, sizeof(T) == 8)) {
+      launch_resid_restrict<T>(lv[l], nine, lv[l - 1], s);
+    } else {
+      launch_residual<T>(lv[l], nine, lv[l].x, lv[l].b, lv[l].r, s);
+      launch_restrict<T>(lv[l], lv[l].r, lv[l - 1], true, s);
+    }
     if (nine) prof_end(BMG_PROF_LEVELS, s);
   }
   launch_coarse_cycle<T>(h, dlev, thr, s);

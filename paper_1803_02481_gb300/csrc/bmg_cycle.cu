@@ -7,6 +7,7 @@
 #include "bmg_coarse.cuh"
 
 #include <cmath>
+#include <cstdlib>
 
 namespace bmg {
 
@@ -35,6 +36,44 @@ __global__ void k_restrict(LevelV<T> F, const T* __restrict__ r, LevelV<T> Cc, i
   const int f = 2 * J * F.pitch + 2 * I;
   Cc.b[c] = restrict_value<T>(F.P, Cc.pitch, r, F.pitch, c, f);
   if (zero_x) Cc.x[c] = T(0);
+}
+
+// Residual and restriction in one pass (Algorithm 1: b_{l-1} = P^T (b - A x)).
+// A block owns kRRX x kRRY coarse points; it first computes the residual on
+// the (2 kRRX + 1) x (2 kRRY + 1) fine points they gather from (one shared
+// row and column with each neighbouring block) into shared memory, then
+// restricts from there, so r never goes to global memory.  Both steps use
+// resid_value and restrict_value, so b_{l-1} is bit-identical to the two
+// separate kernels'.
+constexpr int kRRX = 32, kRRY = 8, kRRT = 256;
+
+template <typename T, bool NINE>
+__global__ void __launch_bounds__(kRRT) k_resid_restrict(LevelV<T> F, LevelV<T> Cc) {
+  constexpr int RW = 2 * kRRX + 1, RH = 2 * kRRY + 1;
+  __shared__ T rs[RH * RW];
+  const int I0 = blockIdx.x * kRRX + 1, J0 = blockIdx.y * kRRY + 1;
+  // fine point of rs[0]: (2 I0 - 1, 2 J0 - 1)
+  const int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1;
+  for (int e = threadIdx.x; e < RW * RH; e += kRRT) {
+    const int rr = e / RW, cc = e - rr * RW;
+    const int i = fi0 + cc, j = fj0 + rr;
+    T v = T(0);
+    if (i <= F.nx && j <= F.ny) {
+      const int o = j * F.pitch + i;
+      v = resid_value<T, NINE>(F, F.x, F.b[o], o);
+    }
+    rs[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kRRX * kRRY; e += kRRT) {
+    const int dj = e / kRRX, di = e - dj * kRRX;
+    const int I = I0 + di, J = J0 + dj;
+    if (I > Cc.nx || J > Cc.ny) continue;
+    const int c = J * Cc.pitch + I;
+    // coarse (I, J) is fine (2I, 2J): rs cell (2 dj + 1, 2 di + 1)
+    Cc.b[c] = restrict_value<T>(F.P, Cc.pitch, rs, RW, c, (2 * dj + 1) * RW + 2 * di + 1);
+    Cc.x[c] = T(0);
+  }
 }
 
 // Two adjacent values of T as one aligned vector access.
@@ -268,6 +307,34 @@ void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool z
   count_launch();
 }
 
+// Which levels take the fused residual + restriction: BMG_RR_FUSED=0 never,
+// 1 always, unset the measured choice: FP32 levels, which are bound by
+// memory traffic (the 8191^2 FP32-refined solve 99.5 -> 97.3 ms).  FP64
+// levels keep the separate kernels: the FP64 pipe bounds the residual either
+// way, and the fused kernel's per-thread loop over several residuals hid
+// latency worse (4095^2 solve 3924 -> 3961 ms with fused 9-point levels).
+bool rr_fused(bool nine, bool fp64) {
+  (void)nine;
+  static const int v = [] {
+    const char* e = std::getenv("BMG_RR_FUSED");
+    return e && e[0] ? std::atoi(e) : -1;
+  }();
+  if (v >= 0) return v != 0;
+  return !fp64;
+}
+
+template <typename T>
+void launch_resid_restrict(const LevelV<T>& fine, bool nine, LevelV<T> coarse, cudaStream_t s) {
+  const dim3 grid(cdiv(coarse.nx, kRRX), cdiv(coarse.ny, kRRY));
+  if (!nine) prof_begin(BMG_PROF_FINE_RESID, s);
+  if (nine)
+    k_resid_restrict<T, true><<<grid, kRRT, 0, s>>>(fine, coarse);
+  else
+    k_resid_restrict<T, false><<<grid, kRRT, 0, s>>>(fine, coarse);
+  if (!nine) prof_end(BMG_PROF_FINE_RESID, s);
+  count_launch();
+}
+
 template <typename T>
 void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s, T* out) {
   const int ncx = (fine.nx - 1) / 2, ncy = (fine.ny - 1) / 2;
@@ -342,6 +409,10 @@ template void launch_restrict<double>(const LevelV<double>&, const double*, Leve
                                       cudaStream_t);
 template void launch_restrict<float>(const LevelV<float>&, const float*, LevelV<float>, bool,
                                      cudaStream_t);
+template void launch_resid_restrict<double>(const LevelV<double>&, bool, LevelV<double>,
+                                            cudaStream_t);
+template void launch_resid_restrict<float>(const LevelV<float>&, bool, LevelV<float>,
+                                           cudaStream_t);
 template void launch_interp<double>(const LevelV<double>&, const double*, bool, cudaStream_t,
                                     double*);
 template void launch_interp<float>(const LevelV<float>&, const float*, bool, cudaStream_t, float*);

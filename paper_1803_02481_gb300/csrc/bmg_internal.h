@@ -384,6 +384,11 @@ void launch_residual(const LevelV<T>& L, bool nine, const T* x, const T* b, T* r
 template <typename T>
 void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool zero_x,
                      cudaStream_t s);
+// Residual and restriction of `fine` into `coarse` in one pass (coarse x set
+// to zero); rr_fused says whether the V-cycle uses it for a level.
+template <typename T>
+void launch_resid_restrict(const LevelV<T>& fine, bool nine, LevelV<T> coarse, cudaStream_t s);
+bool rr_fused(bool nine, bool fp64);
 template <typename T>
 void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s,
                    T* out = nullptr);

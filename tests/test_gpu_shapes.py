@@ -1,10 +1,12 @@
-"""Every measured sweep shape gives the same bits.
+"""Every measured sweep shape (and the fused or separate residual and
+restriction) gives the same bits.
 
 The TMA-staged sweeps have tables of tile shapes (tile sides, threads,
 blocks per SM, stages) selected once per process by environment variables:
 BMG_TMA9_CFG (9-point levels, FP64 and FP32), BMG_TMA_PRE_CFG (the
 prescaled FP64 finest level), BMG_TMA_CFG (5-point levels: FP32, and FP64
-with BMG_RB_PRESCALE=0).  The defaults are covered by the oracle parity
+with BMG_RB_PRESCALE=0); BMG_RR_FUSED picks the levels whose residual and
+restriction run as one kernel.  The defaults are covered by the oracle parity
 tests; here each other entry runs in a subprocess on a grid that puts every
 level through the full-grid kernels (threshold 1), with ragged tiles on every
 level, and its iterates must equal the default's bit for bit, in FP64 and in
@@ -63,7 +65,9 @@ def run_child(tmp_path, name, env_extra):
 
 SETTINGS = ([("nine%d" % k, {"BMG_TMA9_CFG": str(k)}) for k in range(1, 6)] +
             [("pre%d" % k, {"BMG_TMA_PRE_CFG": str(k)}) for k in range(1, 6)] +
-            [("rb%d" % k, {"BMG_TMA_CFG": str(k)}) for k in range(1, 3)])
+            [("rb%d" % k, {"BMG_TMA_CFG": str(k)}) for k in range(1, 3)] +
+            # residual and restriction fused into one kernel on every level, or on none
+            [("rr%d" % k, {"BMG_RR_FUSED": str(k)}) for k in range(2)])
 
 
 def test_every_sweep_shape_gives_identical_iterates(tmp_path):
