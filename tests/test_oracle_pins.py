@@ -694,6 +694,20 @@ def test_level_shapes_for_general_sides():
     assert O.level_shapes(3, 40) == [(3, 40)]
 
 
+def test_coarsening_reproduces_the_papers_enumeration_example():
+    """The paper's redistribution-enumeration example (Section 4) coarsens a
+    9088 x 568 fine grid to a 1136 x 71 global coarse grid: three halvings
+    of both sides.  Sides that are not of the form 2^m - 1 coarsen to
+    floor(n / 2) here; (n - 1) / 2 would give 1135 x 70."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "coarsening_9088x568.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    (fnx, fny, cnx, cny), = [tuple(int(v) for v in r) for r in rows]
+    shapes = O.level_shapes(fnx, fny)
+    assert shapes[3] == (cnx, cny)
+    assert all(O.valid_size(n) for s in shapes for n in s)
+
+
 @pytest.mark.parametrize("nx, ny", [(20, 13), (32, 32), (10, 6), (4, 4), (37, 18)])
 def test_vcycle_converges_to_direct_solution_general_sides(nx, ny):
     rng = np.random.default_rng(nx * 100 + ny)
