@@ -138,17 +138,68 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _diag_window(pr, w, window):
+    off = (w * window) % (N_SIDE - window)
+    return (np.ascontiguousarray(pr["k"][off:off + window, off:off + window]),
+            np.ascontiguousarray(pr["b"][off:off + window, off:off + window]))
+
+
+def _oracle_window(task):
+    """One oracle setup + solve of a window; runs in a worker process of the
+    all-cores sample."""
+    from oracle import boxmg_oracle as O
+    k, b = task
+    t0 = time.perf_counter()
+    r = O.solve(O.setup(k), b, tol=TOL, max_cycles=1000)
+    return k.size, r.cycles, time.perf_counter() - t0
+
+
+def _oracle_import(_):
+    from oracle import boxmg_oracle  # noqa: F401
+    return os.getpid()
+
+
+def cpu_baseline_all_cores(pr, window=511, rounds=2, timeout_s=120.0):
+    """The same oracle windows solved by one worker process per host core
+    (spawned, one BLAS thread each), `rounds` windows per worker; wall time
+    from the first submission to the last result, after every worker has
+    imported the oracle."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    tasks = [_diag_window(pr, w, window) for w in range(rounds * cores)]
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {key: os.environ.get(key) for key in keys}
+    os.environ.update({key: "1" for key in keys})
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map_async(_oracle_import, range(cores), chunksize=1).get(timeout_s)
+            t0 = time.perf_counter()
+            res = pool.map_async(_oracle_window, tasks, chunksize=1).get(timeout_s)
+            wall = time.perf_counter() - t0
+    except Exception as e:  # a worker that failed or a sample that ran out of time
+        return {"unavailable": f"{type(e).__name__}: {e}"[:200], "cores": cores}
+    finally:
+        for key, v in saved.items():
+            if v is None:
+                os.environ.pop(key, None)
+            else:
+                os.environ[key] = v
+    cyc = [c for _, c, _ in res]
+    return {"value": sum(u for u, _, _ in res) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(tasks)} windows of {window}x{window} cells ({min(cyc)}-{max(cyc)} cycles "
+                      f"each), {cores} worker processes, {wall:.1f} s wall"}
+
+
 def cpu_baseline(window=511, budget_s=10.0, max_windows=16):
     """The oracle, as it stands, on a bounded sample of the same field:
     window x window sub-grids along the field's diagonal, solved one after
-    another until budget_s seconds of CPU work have been spent."""
+    another until budget_s seconds of CPU work have been spent; then the
+    same windows on every host core (all_cores)."""
     from oracle import boxmg_oracle as O
     pr = inputs.block_problem(N_SIDE, seed=1, block=64, lo=-4, hi=4)
     total_t, total_u, cycles, done = 0.0, 0, [], 0
     for w in range(max_windows):
-        off = (w * window) % (N_SIDE - window)
-        k = np.ascontiguousarray(pr["k"][off:off + window, off:off + window])
-        b = np.ascontiguousarray(pr["b"][off:off + window, off:off + window])
+        k, b = _diag_window(pr, w, window)
         t0 = time.perf_counter()
         h = O.setup(k)
         r = O.solve(h, b, tol=TOL, max_cycles=1000)
@@ -161,7 +212,8 @@ def cpu_baseline(window=511, budget_s=10.0, max_windows=16):
     return {"value": total_u / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"oracle setup+solve to {TOL:g} of {done} windows of {window}x{window} cells along "
                       f"the diagonal of the same block field ({min(cycles)}-{max(cycles)} cycles each), "
-                      f"{total_t:.1f} s, numpy single thread"}
+                      f"{total_t:.1f} s, numpy single thread",
+            "all_cores": cpu_baseline_all_cores(pr, window)}
 
 
 def run_reference(args, rank, world):
@@ -376,7 +428,8 @@ def run_ours(args, rank, world, local_rank):
             "setup_ms": info.setup_ms, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
             "calibration": calib, "breakdown": breakdown,
             "clocks": clk.summary(), **extra}
-    if rank == 0 and not args.quick and not args.no_cpu:
+    # the CPU baseline is reported at N = 1 only (rank 0)
+    if rank == 0 and world == 1 and not args.quick and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
