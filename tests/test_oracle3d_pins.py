@@ -206,3 +206,15 @@ def test_bad_input_rejected():
         O3.setup(np.ones((1, 4, 4)))
     with pytest.raises(ValueError):
         O3.setup(-np.ones((4, 4, 4)))
+
+
+def test_level_shapes_3d():
+    """Sides n -> floor(n / 2) in every direction while the smallest side
+    exceeds 3; 2^m - 1 sides keep that form down to 3 (the 255^3 benchmark
+    hierarchy has 7 levels)."""
+    assert O3.level_shapes(255, 255, 255) == [(n, n, n) for n in (255, 127, 63, 31, 15, 7, 3)]
+    assert O3.level_shapes(45, 20, 70) == [(45, 20, 70), (22, 10, 35), (11, 5, 17), (5, 2, 8)]
+    assert O3.level_shapes(12, 9, 7) == [(12, 9, 7), (6, 4, 3)]
+    assert O3.level_shapes(3, 40, 40) == [(3, 40, 40)]
+    with pytest.raises(ValueError):
+        O3.level_shapes(1, 8, 8)
