@@ -323,8 +323,11 @@ void bmg_batch_destroy(bmg_batch *b);
  * per grid row) is a static device array of 2 x 16384 doubles (256 KiB) that
  * every GPU loading the library holds until the process exits, so ny may be
  * at most 16384 (BMG_EINVAL beyond, see bmg_last_error).  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array and
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * keeps it for the rest of the process; make that first call before any
+ * stream capture, and do not use this call on a device after
+ * cudaDeviceReset (the kept address belongs to the context that was torn
+ * down).  All calls share the array and
  * each call overwrites every slot it reads, so nothing carries over between
  * calls; calls that overlap on the GPU (different streams, or different
  * threads) race on the array and must be serialised by the caller. */

@@ -198,10 +198,16 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dev(t, name):
+def _dev(t, name, shape=None):
+    """Device pointer of a contiguous float64 CUDA tensor; with `shape`, the
+    tensor must have exactly that shape (the kernels index it by the sizes
+    passed beside it, so a smaller tensor would be read or written past its
+    end on the device)."""
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise TypeError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -235,8 +241,9 @@ class Hierarchy:
             x = torch.zeros_like(b)
         info = Info()
         ok = (BMG_OK, BMG_ENOCONV) if allow_noconv else (BMG_OK,)
-        _check(lib().bmg_solve(self._h, _dev(b, "b"), _dev(x, "x"), float(tol), ctypes.byref(info),
-                               _stream(stream)), "bmg_solve", ok)
+        shape = (self.ny, self.nx)
+        _check(lib().bmg_solve(self._h, _dev(b, "b", shape), _dev(x, "x", shape), float(tol),
+                               ctypes.byref(info), _stream(stream)), "bmg_solve", ok)
         return x, info
 
     def set_max_cycles(self, max_cycles: int):
@@ -296,29 +303,38 @@ class Hierarchy:
         return out
 
     # -- single operations --------------------------------------------------------
+    def _grid(self, level):
+        nx, ny = self.level_shape(level)
+        return ny, nx
+
     def op_relax(self, level, x, b, nu=1, reverse=False, stream=None):
-        _check(lib().bmg_op_relax(self._h, level, _dev(x, "x"), _dev(b, "b"), int(nu), int(bool(reverse)),
-                                  _stream(stream)), "bmg_op_relax")
+        g = self._grid(level)
+        _check(lib().bmg_op_relax(self._h, level, _dev(x, "x", g), _dev(b, "b", g), int(nu),
+                                  int(bool(reverse)), _stream(stream)), "bmg_op_relax")
         return x
 
     def op_residual(self, level, x, b, r, stream=None):
-        _check(lib().bmg_op_residual(self._h, level, _dev(x, "x"), _dev(b, "b"), _dev(r, "r"),
+        g = self._grid(level)
+        _check(lib().bmg_op_residual(self._h, level, _dev(x, "x", g), _dev(b, "b", g), _dev(r, "r", g),
                                      _stream(stream)), "bmg_op_residual")
         return r
 
     def op_restrict(self, level, r, bc, stream=None):
-        _check(lib().bmg_op_restrict(self._h, level, _dev(r, "r"), _dev(bc, "bc"), _stream(stream)),
+        g, gc = self._grid(level), self._grid(level - 1)
+        _check(lib().bmg_op_restrict(self._h, level, _dev(r, "r", g), _dev(bc, "bc", gc), _stream(stream)),
                "bmg_op_restrict")
         return bc
 
     def op_interp(self, level, xc, x, stream=None):
-        _check(lib().bmg_op_interp(self._h, level, _dev(xc, "xc"), _dev(x, "x"), _stream(stream)),
+        g, gc = self._grid(level), self._grid(level - 1)
+        _check(lib().bmg_op_interp(self._h, level, _dev(xc, "xc", gc), _dev(x, "x", g), _stream(stream)),
                "bmg_op_interp")
         return x
 
     def assemble_backward(self, u, lam, dtheta, stream=None):
-        _check(lib().bmg_assemble_backward(self._h, _dev(u, "u"), _dev(lam, "lam"), _dev(dtheta, "dtheta"),
-                                           _stream(stream)), "bmg_assemble_backward")
+        g = (self.ny, self.nx)
+        _check(lib().bmg_assemble_backward(self._h, _dev(u, "u", g), _dev(lam, "lam", g),
+                                           _dev(dtheta, "dtheta", g), _stream(stream)), "bmg_assemble_backward")
         return dtheta
 
 
@@ -326,6 +342,8 @@ def setup(k, options: Options | None = None, stream=None) -> Hierarchy:
     """BoxMG setup from cell coefficients k ((ny, nx) float64 CUDA tensor)."""
     if options is None:
         options = default_options()
+    if k.dim() != 2:
+        raise TypeError(f"k must be 2-D (ny, nx), got shape {tuple(k.shape)}")
     ny, nx = k.shape
     h = ctypes.c_void_p()
     _check(lib().bmg_setup(_dev(k, "k"), nx, ny, ctypes.byref(options), _stream(stream), ctypes.byref(h)),
@@ -347,8 +365,9 @@ class Hierarchy3:
             x = torch.zeros_like(b)
         info = Info()
         ok = (BMG_OK, BMG_ENOCONV) if allow_noconv else (BMG_OK,)
-        _check(lib().bmg3_solve(self._h, _dev(b, "b"), _dev(x, "x"), float(tol), ctypes.byref(info),
-                                _stream(stream)), "bmg3_solve", ok)
+        shape = (self.nz, self.ny, self.nx)
+        _check(lib().bmg3_solve(self._h, _dev(b, "b", shape), _dev(x, "x", shape), float(tol),
+                                ctypes.byref(info), _stream(stream)), "bmg3_solve", ok)
         return x, info
 
     @property
@@ -397,6 +416,8 @@ def setup3(k, options: Options | None = None, stream=None) -> Hierarchy3:
     tensor)."""
     if options is None:
         options = default_options()
+    if k.dim() != 3:
+        raise TypeError(f"k must be 3-D (nz, ny, nx), got shape {tuple(k.shape)}")
     nz, ny, nx = k.shape
     h = ctypes.c_void_p()
     _check(lib().bmg3_setup(_dev(k, "k"), nx, ny, nz, ctypes.byref(options), _stream(stream),
@@ -412,7 +433,7 @@ class Batch:
             options = default_options()
         self.n = [int(k.shape[0]) for k in ks]
         self._ks = ks
-        kp = (ctypes.c_void_p * len(ks))(*[_dev(k, "k").value for k in ks])
+        kp = (ctypes.c_void_p * len(ks))(*[_dev(k, "k", (n, n)).value for k, n in zip(ks, self.n)])
         ns = (ctypes.c_int * len(ks))(*self.n)
         h = ctypes.c_void_p()
         _check(lib().bmg_batch_setup(len(ks), kp, ns, ctypes.byref(options), _stream(stream), ctypes.byref(h)),
@@ -423,8 +444,10 @@ class Batch:
         """Solve all problems in place (xs: initial guesses, overwritten).
         Returns the per-problem Info list."""
         m = len(self.n)
-        bp = (ctypes.c_void_p * m)(*[_dev(b, "b").value for b in bs])
-        xp = (ctypes.c_void_p * m)(*[_dev(x, "x").value for x in xs])
+        if len(bs) != m or len(xs) != m:
+            raise TypeError(f"expected {m} right-hand sides and iterates, got {len(bs)} and {len(xs)}")
+        bp = (ctypes.c_void_p * m)(*[_dev(b, "b", (n, n)).value for b, n in zip(bs, self.n)])
+        xp = (ctypes.c_void_p * m)(*[_dev(x, "x", (n, n)).value for x, n in zip(xs, self.n)])
         infos = (Info * m)()
         ok = (BMG_OK, BMG_ENOCONV) if allow_noconv else (BMG_OK,)
         _check(lib().bmg_batch_solve(self._h, bp, xp, float(tol), infos, _stream(stream)), "bmg_batch_solve", ok)
@@ -447,10 +470,14 @@ def residual_norm_noalloc(k, x, b, norms=None, stream=None):
     without any device allocation inside the library (see
     bmg_residual_norm_noalloc in include/boxmg.h)."""
     import torch
+    if k.dim() != 2:
+        raise TypeError(f"k must be 2-D (ny, nx), got shape {tuple(k.shape)}")
     ny, nx = k.shape
     if norms is None:
         norms = torch.zeros(2, dtype=torch.float64, device=k.device)
-    _check(lib().bmg_residual_norm_noalloc(_dev(k, "k"), _dev(x, "x"), _dev(b, "b"), nx, ny,
+    if norms.numel() < 2:
+        raise TypeError(f"norms must hold at least 2 float64 values, has {norms.numel()}")
+    _check(lib().bmg_residual_norm_noalloc(_dev(k, "k"), _dev(x, "x", (ny, nx)), _dev(b, "b", (ny, nx)), nx, ny,
                                            _dev(norms, "norms"), _stream(stream)), "bmg_residual_norm_noalloc")
     return norms
 
@@ -464,6 +491,8 @@ def solve_host(k: np.ndarray, b: np.ndarray, x: np.ndarray, options: Options | N
             raise TypeError(f"{n} must be a C-contiguous float64 numpy array")
     if options is None:
         options = default_options()
+    if k.ndim != 2 or b.shape != k.shape or x.shape != k.shape:
+        raise TypeError(f"k, b and x must share one 2-D shape, got {k.shape}, {b.shape}, {x.shape}")
     ny, nx = k.shape
     info = Info()
     ok = (BMG_OK, BMG_ENOCONV) if allow_noconv else (BMG_OK,)

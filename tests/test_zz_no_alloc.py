@@ -52,6 +52,54 @@ def test_noalloc_norm_matches_existing_entry_points_twice():
     h.destroy()
 
 
+def test_noalloc_allocates_no_device_memory():
+    """The point of the entry point: repeated calls leave the device's free
+    memory unchanged.  The first call resolves the scratch array's address
+    (with lazy module loading that may load the library's device code), so
+    it comes before the first reading."""
+    pr = inputs.block_problem(127, seed=1, block=16, lo=-2, hi=2)
+    k = torch.from_numpy(pr["k"]).cuda()
+    b = torch.from_numpy(pr["b"]).cuda()
+    x = torch.zeros_like(b)
+    norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    ny, nx = pr["k"].shape
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert bm.lib().bmg_residual_norm_noalloc(_ptr(k), _ptr(x), _ptr(b), nx, ny, _ptr(norms), stream) == bm.BMG_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(50):
+        assert bm.lib().bmg_residual_norm_noalloc(_ptr(k), _ptr(x), _ptr(b), nx, ny, _ptr(norms),
+                                                  stream) == bm.BMG_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    # with x = 0 the residual is b itself
+    got = norms.cpu().numpy()
+    bnorm = np.linalg.norm(pr["b"])
+    assert abs(got[0] - bnorm) <= 1e-13 * bnorm and abs(got[1] - bnorm) <= 1e-13 * bnorm
+
+
+def test_noalloc_python_wrapper_checks_shapes():
+    """bm.residual_norm_noalloc passes k's sizes to the kernels, so it must
+    refuse x, b or norms that are smaller than those sizes imply."""
+    pr = inputs.block_problem(63, seed=1, block=16, lo=-2, hi=2)
+    k = torch.from_numpy(pr["k"]).cuda()
+    b = torch.from_numpy(pr["b"]).cuda()
+    x = torch.zeros_like(b)
+    norms = bm.residual_norm_noalloc(k, x, b)
+    bnorm = np.linalg.norm(pr["b"])
+    assert abs(norms[0].item() - bnorm) <= 1e-13 * bnorm
+    small = torch.zeros((62, 63), dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        bm.residual_norm_noalloc(k, small, b)
+    with pytest.raises(TypeError):
+        bm.residual_norm_noalloc(k, x, small)
+    with pytest.raises(TypeError):
+        bm.residual_norm_noalloc(k, x, b, norms=torch.zeros(1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(TypeError):
+        bm.residual_norm_noalloc(k.reshape(-1), x, b)
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch():
     t = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
     norms = torch.zeros(2, dtype=torch.float64, device="cuda")
