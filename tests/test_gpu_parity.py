@@ -225,6 +225,40 @@ def test_interp_residual_term_variant_matches_oracle():
     hg.destroy()
 
 
+@pytest.mark.parametrize("name", ["poisson255", "lognormal255", "blocks255"])
+def test_interp_residual_term_on_the_gpu_is_the_post_smoothing_residual_over_c(name):
+    """The property that pins the oracle's r/C term, checked on the GPU's own
+    cycle: with nu2 = 0, one cycle's update minus r_pre/C at non-coarse points
+    (r_pre the residual after pre-smoothing, C the fine diagonal) is P times
+    the coarse correction, i.e. interpolated exactly from its values at the
+    coarse points.  Then the same cycle against the oracle's."""
+    pr = problem(name)
+    ny, nx = pr["k"].shape
+    rng = np.random.default_rng(17)
+    x0 = rng.uniform(-1, 1, (ny, nx))
+    hg = bm.setup(dev(pr["k"]), bm.default_options(nu1=1, nu2=0, interp_residual_term=1, max_cycles=1))
+    x1, info = hg.solve(dev(pr["b"]), dev(x0), tol=1e-300, allow_noconv=True)
+    assert info.cycles == 1
+    x1 = x1.cpu().numpy()
+    hg.destroy()
+    ho = O.setup(pr["k"], nu1=1, nu2=0, interp_residual_term=True)
+    st = ho.levels[-1].st
+    x_pre = x0.copy()
+    O.relax(st, x_pre, pr["b"], 1, O.colour_order(st))
+    r_pre = O.residual(st, x_pre, pr["b"])
+    cm = np.zeros((ny, nx), dtype=bool)
+    cm[1::2, 1::2] = True
+    y = x1 - x_pre - np.where(cm, 0.0, r_pre / st["C"])
+    # P from the oracle (the GPU's weights equal it to 1e-12, tested above)
+    py = (ho.levels[-1].p @ y[1::2, 1::2].ravel()).reshape(ny, nx)
+    scale = np.abs(y).max()
+    assert scale > 1e-3
+    assert np.abs(y - py).max() <= 1e-11 * scale
+    xo = x0.copy()
+    O.vcycle(ho, xo, pr["b"])
+    assert np.abs(x1 - xo).max() <= 1e-10 * np.abs(xo).max()
+
+
 @pytest.mark.parametrize("name", ["poisson255", "blocks255", "lognormal255", "wide2047x127"])
 def test_fp32_refinement_reaches_fp64_tolerance(name):
     pr = problem(name)
@@ -428,6 +462,35 @@ def test_anisotropic_options_are_checked():
     u = dev(np.ones((31, 63)))
     with pytest.raises(bm.BoxMGError):
         h.assemble_backward(u, u, torch.zeros_like(u))
+    h.destroy()
+
+
+def test_binding_rejects_tensors_of_the_wrong_shape():
+    """The kernels index b, x and the level arrays by the hierarchy's sizes,
+    so the binding refuses any tensor whose shape differs from them."""
+    k = dev(np.ones((31, 63)))
+    h = bm.setup(k)
+    good = torch.zeros((31, 63), dtype=torch.float64, device="cuda")
+    small = torch.zeros((30, 63), dtype=torch.float64, device="cuda")
+    for args in ((small, None), (good, small), (small.t().contiguous(), None)):
+        with pytest.raises(TypeError):
+            h.solve(args[0], args[1])
+    L = h.nlevels
+    nxc, nyc = h.level_shape(L - 2)
+    coarse = torch.zeros((nyc, nxc), dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        h.op_relax(L - 1, small, good)
+    with pytest.raises(TypeError):
+        h.op_residual(L - 1, good, good, small)
+    with pytest.raises(TypeError):
+        h.op_restrict(L - 1, good, small)
+    with pytest.raises(TypeError):
+        h.op_interp(L - 1, good, good)      # xc must have the coarse shape
+    with pytest.raises(TypeError):
+        h.assemble_backward(good, good, small)
+    h.op_restrict(L - 1, good, coarse)      # the right shapes still pass
+    x, info = h.solve(good.clone().fill_(1.0))
+    assert info.rel_resid <= 1e-10
     h.destroy()
 
 
