@@ -18,6 +18,7 @@ Conventions
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft as sfft
 
 SIDES_BATCH = (63, 127, 255, 511, 1023)
 SIDE_WEIGHTS_BATCH = (8, 4, 2, 1, 1)
@@ -45,18 +46,19 @@ def block_field(rng: np.random.Generator, nx: int, ny: int, block: int,
 
 def _gauss_filter_axis(a: np.ndarray, ell: float, axis: int) -> np.ndarray:
     """Linear convolution along ``axis`` with exp(-d^2/ell^2), via a
-    zero-padded FFT of twice the length (no wrap-around inside the grid)."""
+    zero-padded FFT of twice the length (no wrap-around inside the grid);
+    the transforms run on every host core."""
     n = a.shape[axis]
     m = 2 * n
     d = np.arange(m, dtype=np.float64)
     d = np.minimum(d, m - d)
     h = np.exp(-(d * d) / (ell * ell))
-    hh = np.fft.rfft(h)
+    hh = sfft.rfft(h)
     shape = [1] * a.ndim
     shape[axis] = hh.shape[0]
-    fa = np.fft.rfft(a, n=m, axis=axis)
+    fa = sfft.rfft(a, n=m, axis=axis, workers=-1)
     fa *= hh.reshape(shape)
-    out = np.fft.irfft(fa, n=m, axis=axis)
+    out = sfft.irfft(fa, n=m, axis=axis, workers=-1)
     sl = [slice(None)] * a.ndim
     sl[axis] = slice(0, n)
     return np.ascontiguousarray(out[tuple(sl)])
@@ -157,31 +159,3 @@ def batch_problems(count: int = 512, seed: int = 4, block: int = 16,
         probs.append({"n": n, "k": k, "b": b})
     return probs
 
-
-def gaussian_random_field_torch(seed: int, nx: int, ny: int, ell: float = 32.0, device="cuda"):
-    """The same spectral synthesis as ``gaussian_random_field`` with torch
-    (on the GPU, for the 8191^2 benchmark field): white noise from a seeded
-    torch generator, two zero-padded FFT filters with exp(-d^2/ell^2),
-    standardised.  The numbers differ from the NumPy generator (another
-    random stream); the statistics are the same."""
-    import torch
-    g = torch.Generator(device=device)
-    g.manual_seed(seed)
-    w = torch.randn((ny, nx), generator=g, device=device, dtype=torch.float64)
-
-    def filt(a, axis):
-        n = a.shape[axis]
-        m = 2 * n
-        d = torch.arange(m, device=device, dtype=torch.float64)
-        d = torch.minimum(d, m - d)
-        hh = torch.fft.rfft(torch.exp(-(d * d) / (ell * ell)))
-        fa = torch.fft.rfft(a, n=m, dim=axis)
-        shape = [1, 1]
-        shape[axis] = hh.shape[0]
-        fa = fa * hh.reshape(shape)
-        out = torch.fft.irfft(fa, n=m, dim=axis)
-        return out.narrow(axis, 0, n).contiguous()
-
-    f = filt(filt(w, 1), 0)
-    f = f - f.mean()
-    return f / f.std(unbiased=False)

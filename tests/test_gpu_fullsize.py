@@ -146,9 +146,20 @@ def test_c2_solve_satisfies_the_stop_test_against_the_oracle_operator(c2):
     the residual the GPU reports."""
     pr, h = c2
     x, info = h.solve(dev(pr["b"]), tol=1e-9)
-    rel = _rel_resid(O.assemble_fv5(pr["k"]), x.cpu().numpy(), pr["b"])
+    st = O.assemble_fv5(pr["k"])
+    xn = x.cpu().numpy()
+    rel = _rel_resid(st, xn, pr["b"])
     assert info.rel_resid <= 1e-9 and rel <= 1.2e-9
     assert abs(rel - info.rel_resid) <= 0.2e-9
+    # Why this workload is solved to 1e-9 and not 1e-10: rounding the
+    # FP64-stored iterate alone moves b - A x by up to eps (|A| |x|) per row,
+    # and for this field eps || |A| |x| ||_2 / ||b||_2 lies above 1e-10
+    # (high-k blocks at large potential).
+    st_abs = dict(st)
+    for d in O.DIRS:
+        st_abs[d] = -st[d]                       # |A| |x| = C |x| + sum_X a_X |x_X|
+    floor = np.finfo(np.float64).eps * np.linalg.norm(O.apply(st_abs, np.abs(xn))) / np.linalg.norm(pr["b"])
+    assert floor > 1e-10, floor
 
 
 @pytest.mark.parametrize("nx,ny", [(16383, 1023), (9088, 568)])
@@ -171,19 +182,15 @@ def test_paper_workload_solves_satisfy_the_stop_test(nx, ny):
 
 
 def test_c3_fp32_refinement_satisfies_the_fp64_stop_test():
-    """8191^2 log-normal field (k = exp(2 g), correlation 32 cells, drawn on
-    the device as in the benchmark): FP32 V-cycles inside FP64 refinement
-    reach 1e-10 for the oracle's FP64 operator."""
-    n = 8191
-    d = torch.device("cuda", 0)
-    g = inputs.gaussian_random_field_torch(2, n, n, 32.0, device=d)
-    k = torch.exp(2.0 * g)
-    del g
-    b = np.random.default_rng(92).uniform(-1, 1, (n, n))
-    h = bm.setup(k, bm.default_options(precision=bm.BMG_FP32_REFINE, max_cycles=500))
+    """8191^2 log-normal field (k = exp(2 g), correlation 32 cells, seed 2,
+    as in the benchmark): FP32 V-cycles inside FP64 refinement reach 1e-10
+    for the oracle's FP64 operator."""
+    pr = inputs.lognormal_problem(8191, seed=2)
+    b = pr["b"]
+    h = bm.setup(dev(pr["k"]), bm.default_options(precision=bm.BMG_FP32_REFINE, max_cycles=500))
     x, info = h.solve(dev(b), tol=1e-10)
     h.destroy()
-    rel = _rel_resid(O.assemble_fv5(k.cpu().numpy()), x.cpu().numpy(), b)
+    rel = _rel_resid(O.assemble_fv5(pr["k"]), x.cpu().numpy(), b)
     assert info.rel_resid <= 1e-10 and rel <= 1.2e-10, (rel, info.rel_resid)
     assert abs(rel - info.rel_resid) <= 0.2e-10, (rel, info.rel_resid)
 

@@ -37,7 +37,7 @@ def _worker(rank, world, port, results):
 
 def test_whole_job_time_is_the_slowest_rank_and_value_counts_all_ranks():
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         results = mgr.dict()
         mp.start_processes(_worker, args=(world, _free_port(), results), nprocs=world,
                            start_method="spawn", join=True)
