@@ -46,12 +46,14 @@ WORKLOAD = {"workload": "diffusion 4095x4095, 64x64-cell blocks k=10^U(-4,4), se
 
 
 # DRAM bytes (read + write) per fine unknown of one fine-level sweep launch,
-# from the ncu capture summarised in profiles/k_sweep_tma_fine_ncu.md; set
-# to None whenever the kernel changes until it is captured again.
+# from ncu captures of that kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum over the unknowns of the captured level); set to None
+# whenever the kernel changes until it is captured again.  Value, and the
+# level the capture ran on.
 SWEEP_DRAM_BYTES_PER_UNKNOWN = {
-    "fp64": (169.342720e6 + 18.732288e6) / 4190209,    # 2047^2 block field
-    "fp64_prescaled": (203.332864e6 + 22.704640e6) / 4190209,   # 2047^2 block field
-    "fp32": (338.814976e6 + 52.656128e6) / 16769025,   # 4095^2 log-normal field
+    "fp64": ((169.342720e6 + 18.732288e6) / 4190209, "2047^2 level of the block field"),
+    "fp64_prescaled": ((203.332864e6 + 22.704640e6) / 4190209, "2047^2 level of the block field"),
+    "fp32": ((338.814976e6 + 52.656128e6) / 16769025, "4095^2 level of the log-normal field"),
 }
 
 
@@ -138,6 +140,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# the window the reference arm (the oracle) solves per step: the top-left
+# REF_WINDOW^2 cells of the block field; the CPU baseline solves CPU_WINDOW^2
+# windows along the field's diagonal
+REF_WINDOW = 255
+CPU_WINDOW = 511
+
+
 def _diag_window(pr, w, window):
     off = (w * window) % (N_SIDE - window)
     return (np.ascontiguousarray(pr["k"][off:off + window, off:off + window]),
@@ -159,7 +168,7 @@ def _oracle_import(_):
     return os.getpid()
 
 
-def cpu_baseline_all_cores(pr, window=511, rounds=2, timeout_s=120.0):
+def cpu_baseline_all_cores(pr, window=CPU_WINDOW, rounds=2, timeout_s=120.0):
     """The same oracle windows solved by one worker process per host core
     (spawned, one BLAS thread each), `rounds` windows per worker; wall time
     from the first submission to the last result, after every worker has
@@ -186,18 +195,20 @@ def cpu_baseline_all_cores(pr, window=511, rounds=2, timeout_s=120.0):
                 os.environ[key] = v
     cyc = [c for _, c, _ in res]
     return {"value": sum(u for u, _, _ in res) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "unknown_cycles_per_s": sum(u * c for u, c, _ in res) / wall, "windows": len(tasks),
+            "window": window,
             "sample": f"{len(tasks)} windows of {window}x{window} cells ({min(cyc)}-{max(cyc)} cycles "
                       f"each), {cores} worker processes, {wall:.1f} s wall"}
 
 
-def cpu_baseline(window=511, budget_s=10.0, max_windows=16):
+def cpu_baseline(window=CPU_WINDOW, budget_s=10.0, max_windows=16):
     """The oracle, as it stands, on a bounded sample of the same field:
     window x window sub-grids along the field's diagonal, solved one after
     another until budget_s seconds of CPU work have been spent; then the
     same windows on every host core (all_cores)."""
     from oracle import boxmg_oracle as O
     pr = inputs.block_problem(N_SIDE, seed=1, block=64, lo=-4, hi=4)
-    total_t, total_u, cycles, done = 0.0, 0, [], 0
+    total_t, total_u, total_uc, cycles, done = 0.0, 0, 0, [], 0
     for w in range(max_windows):
         k, b = _diag_window(pr, w, window)
         t0 = time.perf_counter()
@@ -205,11 +216,14 @@ def cpu_baseline(window=511, budget_s=10.0, max_windows=16):
         r = O.solve(h, b, tol=TOL, max_cycles=1000)
         total_t += time.perf_counter() - t0
         total_u += window * window
+        total_uc += window * window * r.cycles
         cycles.append(r.cycles)
         done += 1
         if total_t >= budget_s:
             break
     return {"value": total_u / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "unknown_cycles_per_s": total_uc / total_t, "windows": done, "window": window,
+            "cycles_per_window": cycles,
             "sample": f"oracle setup+solve to {TOL:g} of {done} windows of {window}x{window} cells along "
                       f"the diagonal of the same block field ({min(cycles)}-{max(cycles)} cycles each), "
                       f"{total_t:.1f} s, numpy single thread",
@@ -219,7 +233,7 @@ def cpu_baseline(window=511, budget_s=10.0, max_windows=16):
 def run_reference(args, rank, world):
     if world > 1 and rank != 0:
         return
-    window = 255
+    window = REF_WINDOW
     from oracle import boxmg_oracle as O
     pr = inputs.block_problem(N_SIDE, seed=1, block=64, lo=-4, hi=4)
     k = np.ascontiguousarray(pr["k"][:window, :window])
@@ -237,10 +251,12 @@ def run_reference(args, rank, world):
     tot = sum(times)
     value = window * window * len(times) / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "unknown_cycles_per_s": value * cycles, "cycles": cycles,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(WORKLOAD, sample_window=window),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "unknown_cycles_per_s": value * cycles,
                              "sample": f"oracle setup+solve of the top-left {window}x{window} window of the "
                                        f"same block field per step, {cycles} cycles, numpy single thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -259,17 +275,13 @@ def run_ours(args, rank, world, local_rank):
     tol = TOL
     workload = dict(WORKLOAD)
     if args.workload == "lognormal":
-        # the log-normal field of the mixed-precision comparison (generated on
-        # the GPU), solved to 1e-10
+        # the log-normal field of the mixed-precision comparison (seed 2),
+        # solved to 1e-10
         n = args.n if args.n is not None else 8191
         args.n = n
-        g = inputs.gaussian_random_field_torch(2, n, n, 32.0, device=dev)
-        k = torch.exp(2.0 * g)
-        del g
-        gen = torch.Generator(device=dev)
-        gen.manual_seed(102)
-        b = torch.rand((n, n), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
-        pr = None
+        pr = inputs.lognormal_problem(n, seed=2)
+        k = torch.from_numpy(pr["k"]).to(dev)
+        b = torch.from_numpy(pr["b"]).to(dev)
         tol = 1e-10
         workload = {"workload": f"log-normal k = exp(2 g), GRF correlation 32 cells, {n}x{n}, tol 1e-10",
                     "nx": n, "ny": n, "seed": 2, "cycle": "V(2,1)", "tol": tol}
@@ -353,6 +365,12 @@ def run_ours(args, rank, world, local_rank):
         extra["paper_workload_9088x568"] = paper_workload_leg(bm, torch, dev, stream, nx=9088, ny=568)
         extra["line_smoother"] = line_smoother_leg(bm, torch, dev, stream, load_peaks()[0])
         extra["three_d"] = three_d_leg(bm, torch, dev, stream, load_peaks()[0])
+        extra["c1_poisson255"] = c1_leg(bm, torch, dev, stream)
+        extra["adjoint_gradient"] = adjoint_leg(bm, torch, dev, stream)
+        if pr is not None and args.n == N_SIDE:
+            extra["gpu_on_reference_window"] = windows_leg(bm, torch, dev, stream, pr, REF_WINDOW, [None] * 5)
+            extra["gpu_on_cpu_baseline_windows"] = windows_leg(bm, torch, dev, stream, pr, CPU_WINDOW,
+                                                               list(range(32)))
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.quick:
@@ -380,38 +398,50 @@ def run_ours(args, rank, world, local_rank):
 
     peaks, peak_kind = load_peaks()
     # fine-level smoothing: one bracket = one full red-black sweep over the
-    # fine level.  Algorithmic bytes per fine unknown: 1/C, W, S, b and x
-    # read, x written = 6 words (48 B FP64); flops: 4 FMA + 1 MUL = 9.  The
-    # prescaled FP64 level: b/C, W/C, E/C, S/C, N/C and x read, x written =
-    # 7 words (56 B); flops: 4 FMA = 8.
+    # fine level.  Algorithmic bytes per fine unknown, the method's: 1/C, W,
+    # S, b and x read, x written = 6 words (48 B FP64); flops 4 FMA + 1 MUL
+    # = 9.  The prescaled FP64 layout moves 7 words (b/C, W/C, E/C, S/C, N/C
+    # and x read, x written: 56 B) for 4 FMA = 8 flops; the achieved rate of
+    # those moved bytes is reported beside the algorithmic one, and the
+    # fraction compared with the 60 % target is the algorithmic one.
     word = 8.0 if args.precision == "fp64" else 4.0
     prescaled = bool(state.get("prescaled"))
-    per_unit_b, per_unit_f = (7 * word, 8.0) if prescaled else (6 * word, 9.0)
+    per_unit_b = 6 * word
+    moved_b, per_unit_f = (7 * word, 8.0) if prescaled else (6 * word, 9.0)
     sweep_ms = prof_ms / max(1, nprof)
     gbs = per_unit_b * n_fine / (sweep_ms / 1e3) / 1e9
+    gbs_moved = moved_b * n_fine / (sweep_ms / 1e3) / 1e9
     gfl = per_unit_f * n_fine / (sweep_ms / 1e3) / 1e9
     f_hbm = gbs / peaks["hbm_gbs"]
     alu_peak, alu_src = alu_peak_gflops(torch, dev, args.precision, clk.summary())
     f_alu = gfl / alu_peak
     kname = "k_sweep_tma<%s, 5-point%s>" % ("double" if args.precision == "fp64" else "float",
                                              ", prescaled" if prescaled else "")
-    # DRAM bytes per launch from the ncu capture of this kernel (a smaller
-    # grid of the same kind, scaled by the units one launch processes)
-    traffic_per_unit = SWEEP_DRAM_BYTES_PER_UNKNOWN.get(args.precision + ("_prescaled" if prescaled else ""))
-    traffic = traffic_per_unit * n_fine if traffic_per_unit else None
+    # DRAM bytes per launch from the ncu capture of this kernel (per unknown
+    # of the captured level, times the units one launch processes)
+    traffic_entry = SWEEP_DRAM_BYTES_PER_UNKNOWN.get(args.precision + ("_prescaled" if prescaled else ""))
+    traffic = traffic_entry[0] * n_fine if traffic_entry and traffic_entry[0] else None
     common = {"kernel": kname + ": fine-level red-black Gauss-Seidel sweep, TMA-staged, one launch per sweep",
               "per_launch_ms": sweep_ms, "launches_timed": nprof,
               "timing": "CUDA events around every fine sweep of one full profiled step on the solve stream",
               "algorithmic_bytes_per_unknown": per_unit_b, "algorithmic_flops_per_unknown": per_unit_f,
               "units_per_launch": n_fine,
-              "traffic_source": ("profiles/k_sweep_tma_fine_prescaled_ncu.md" if prescaled
-                                 else "profiles/k_sweep_tma_fine_ncu.md") + " (dram bytes per unknown x units)",
+              "frac_basis": "achieved = the method's algorithmic bytes (48 B FP64 per unknown: 1/C, W, S, b, "
+                            "x read, x write) / launch time; this is the fraction compared with the 60 % target",
+              "bytes_moved_per_unknown": moved_b, "achieved_gbs_moved": gbs_moved,
+              "frac_moved": gbs_moved / peaks["hbm_gbs"],
+              "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel on the "
+                                 f"{traffic_entry[1]}, per unknown x units per launch") if traffic_entry else None,
               "hbm": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": f_hbm,
                       "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
               "alu": {"achieved_gflops": gfl, "peak_gflops": alu_peak, "frac": f_alu,
                       "peak_source": alu_src,
                       "measured_gflops": calib["gpu_gflops64" if args.precision == "fp64" else "gpu_gflops32"]}}
-    if f_alu > f_hbm:
+    # which roof binds follows from the kernel's own arithmetic intensity
+    # (executed flops per moved byte) against the ridge of the two peaks
+    intensity, ridge = per_unit_f / moved_b, alu_peak / peaks["hbm_gbs"]
+    common["intensity_flop_per_byte"], common["ridge_flop_per_byte"] = intensity, ridge
+    if intensity > ridge:
         roofline = {"bound": "alu", "achieved": gfl, "peak": alu_peak, "unit": "GFLOP/s", "frac": f_alu,
                     "traffic": traffic, **common}
     else:
@@ -425,12 +455,14 @@ def run_ours(args, rank, world, local_rank):
             "config": dict(workload, nx=args.n, ny=args.n, precision=args.precision,
                            l2="inputs and hierarchy larger than L2", parallelism=f"replicas{world}"),
             "cycles": info.cycles, "rel_resid": info.rel_resid, "threshold": info.threshold,
+            "unknown_cycles_per_s": value * info.cycles,
             "setup_ms": info.setup_ms, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
             "calibration": calib, "breakdown": breakdown,
             "clocks": clk.summary(), **extra}
     # the CPU baseline is reported at N = 1 only (rank 0)
     if rank == 0 and world == 1 and not args.quick and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
+        same_windows_ratio(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -440,13 +472,11 @@ def lognormal_leg(bm, torch, dev, stream, args, n=8191):
     1e-10 on the 8191^2 log-normal field (setup + solve timed); beside them
     the r/C interpolation variant and CG preconditioned by a symmetric
     V(1,1) cycle, both FP64."""
-    g = inputs.gaussian_random_field_torch(2, n, n, 32.0, device=dev)
-    k = torch.exp(2.0 * g)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(102)
-    b = torch.rand((n, n), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
-    del g
-    out = {"workload": f"log-normal k = exp(2 g), GRF correlation 32 cells, {n}x{n}, tol 1e-10"}
+    pr = inputs.lognormal_problem(n, seed=2)
+    k = torch.from_numpy(pr["k"]).to(dev)
+    b = torch.from_numpy(pr["b"]).to(dev)
+    del pr
+    out = {"workload": f"log-normal k = exp(2 g), GRF correlation 32 cells (seed 2), {n}x{n}, tol 1e-10"}
     xs = {}
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -475,6 +505,7 @@ def lognormal_leg(bm, torch, dev, stream, args, n=8191):
         ms = sum(times) / len(times)
         xs[name] = x.clone()
         out[name] = {"value": n * n / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms, "cycles": info.cycles,
+                     "unknown_cycles_per_s": n * n * info.cycles / (ms / 1e3),
                      "rel_resid": info.rel_resid, "setup_ms": info.setup_ms}
     out["speedup_fp32_refine_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["fp32_refine"]["ms_per_solve"]
     d = (xs["fp32_refine"] - xs["fp64"]).abs().max() / xs["fp64"].abs().max()
@@ -779,6 +810,179 @@ def batch_leg(bm, torch, dev, stream, count=512):
     return out
 
 
+def windows_leg(bm, torch, dev, stream, pr, window, which):
+    """The GPU on exactly the windows the CPU oracle solves: setup + solve to
+    the bench tolerance of each window (None: the top-left window of the
+    reference arm; an integer w: the w-th diagonal window of the CPU
+    baseline), timed with CUDA events, one warm-up solve first."""
+    def window_of(w):
+        if w is None:
+            return (np.ascontiguousarray(pr["k"][:window, :window]),
+                    np.ascontiguousarray(pr["b"][:window, :window]))
+        return _diag_window(pr, w, window)
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    opts = bm.default_options(max_cycles=1000)
+    per = []
+    for rep, w in enumerate([which[0]] + list(which)):
+        kw, bw = window_of(w)
+        k = torch.from_numpy(kw).to(dev)
+        b = torch.from_numpy(bw).to(dev)
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        h = bm.setup(k, opts, stream=stream)
+        _, info = h.solve(b, x, tol=TOL, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        h.destroy()
+        if rep:                              # the first solve is the warm-up
+            per.append((ev0.elapsed_time(ev1), info.cycles))
+    units = window * window * len(per)
+    ms = sum(t for t, _ in per)
+    return {"window": window, "windows": len(per),
+            "which": (f"top-left, {len(per)} timed solves" if which[0] is None
+                      else f"diagonal windows 0..{len(per) - 1}"),
+            "value": units / (ms / 1e3), "unit": UNIT,
+            "unknown_cycles_per_s": sum(window * window * c for _, c in per) / (ms / 1e3),
+            "ms_per_window": [t for t, _ in per], "cycles_per_window": [c for _, c in per]}
+
+
+def same_windows_ratio(line):
+    """GPU / CPU on the same windows of the same field, per unknown solved
+    and per unknown-cycle: the one-thread oracle against the GPU on its
+    windows, and the all-cores oracle against the GPU on its windows."""
+    cpu = line.get("cpu_baseline") or {}
+    gw = line.get("gpu_on_cpu_baseline_windows")
+    if not gw or "windows" not in cpu:
+        return
+    nwin = cpu["windows"]
+    ms = sum(gw["ms_per_window"][:nwin])
+    uc = sum(CPU_WINDOW * CPU_WINDOW * c for c in gw["cycles_per_window"][:nwin])
+    g1 = {"value": CPU_WINDOW * CPU_WINDOW * nwin / (ms / 1e3), "unknown_cycles_per_s": uc / (ms / 1e3)}
+    out = {"one_thread": {"windows": nwin, "gpu": g1,
+                          "ratio_unknowns_per_s": g1["value"] / cpu["value"],
+                          "ratio_unknown_cycles_per_s": g1["unknown_cycles_per_s"] / cpu["unknown_cycles_per_s"],
+                          "same_cycles": gw["cycles_per_window"][:nwin] == cpu.get("cycles_per_window")}}
+    ac = cpu.get("all_cores") or {}
+    if "windows" in ac and ac["windows"] <= gw["windows"]:
+        ms = sum(gw["ms_per_window"][:ac["windows"]])
+        uc = sum(CPU_WINDOW * CPU_WINDOW * c for c in gw["cycles_per_window"][:ac["windows"]])
+        ga = {"value": CPU_WINDOW * CPU_WINDOW * ac["windows"] / (ms / 1e3), "unknown_cycles_per_s": uc / (ms / 1e3)}
+        out["all_cores"] = {"windows": ac["windows"], "cores": ac.get("cores"), "gpu": ga,
+                            "ratio_unknowns_per_s": ga["value"] / ac["value"],
+                            "ratio_unknown_cycles_per_s": ga["unknown_cycles_per_s"] / ac["unknown_cycles_per_s"]}
+    line["vs_cpu_same_windows"] = out
+
+
+def c1_leg(bm, torch, dev, stream, reps=20):
+    """The 255^2 Poisson problem (k = 1, seed-0 right-hand side), FP64 V(2,1)
+    to 1e-10: its whole hierarchy fits in L2, so it is latency-bound.
+    Latency of setup + solve and of the solve alone (median of `reps`), per
+    cycle, and the threshold sweep of the level schedule."""
+    pr = inputs.constant_problem(255, seed=0)
+    k = torch.from_numpy(pr["k"]).to(dev)
+    b = torch.from_numpy(pr["b"]).to(dev)
+    x = torch.zeros_like(b)
+    opts = bm.default_options()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    both, solve_only = [], []
+    for rep in range(reps + 3):
+        x.zero_()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        h = bm.setup(k, opts, stream=stream)
+        _, info = h.solve(b, x, tol=1e-10, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        h.destroy()
+        if rep >= 3:
+            both.append(ev0.elapsed_time(ev1))
+    h = bm.setup(k, opts, stream=stream)
+    for rep in range(reps + 3):
+        x.zero_()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        _, info = h.solve(b, x, tol=1e-10, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= 3:
+            solve_only.append(ev0.elapsed_time(ev1))
+    h.destroy()
+    ms_both, ms_solve = statistics.median(both), statistics.median(solve_only)
+    return {"workload": "Poisson k = 1, 255x255, seed-0 uniform[-1,1] RHS, FP64 V(2,1), tol 1e-10",
+            "value": 255 * 255 / (ms_both / 1e3), "unit": UNIT,
+            "ms_setup_plus_solve": ms_both, "ms_solve": ms_solve, "cycles": info.cycles,
+            "us_per_cycle": 1e3 * ms_solve / info.cycles, "rel_resid": info.rel_resid,
+            "threshold": info.threshold, "levels": 7,
+            "threshold_sweep": threshold_sweep(bm, torch, k, b, stream)}
+
+
+def adjoint_leg(bm, torch, dev, stream, n=2047, reps=3):
+    """The adjoint gradient on the 2047^2 seed-3 log-normal field: through
+    the autograd wrapper (setup with log-coefficients, forward solve to 1e-10,
+    loss 0.5 ||u - u_obs||^2, adjoint solve on the same hierarchy, the
+    backward assembly kernel), timed against the plain FP64 forward solve
+    (setup + solve) of the same field.  The adjoint right-hand side u - u_obs
+    is about 1e-3 of u, so its FP64 residual floor sits near 2.5e-10
+    relative (200 cycles do not reach 1e-10); it is solved to 1e-9."""
+    from paper_1803_02481_gb300.autograd import solve as diff_solve
+    pr = inputs.adjoint_problem(n, seed=3)
+    theta = torch.from_numpy(pr["theta"]).to(dev)
+    b = torch.from_numpy(pr["b"]).to(dev)
+    ho = bm.setup(torch.from_numpy(pr["theta_obs"]).to(dev), bm.default_options(log_coefficients=1, max_cycles=500),
+                  stream=stream)
+    u_obs, _ = ho.solve(b, tol=1e-11, stream=stream)
+    ho.destroy()
+    u_obs = u_obs + 1e-3 * torch.from_numpy(pr["eps"]).to(dev)
+    del pr
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def gradient():
+        th = theta.clone().requires_grad_(True)
+        u = diff_solve(th, b, tol=1e-10, max_cycles=500, adjoint_tol=1e-9, adjoint_max_cycles=200)
+        loss = 0.5 * ((u - u_obs) ** 2).sum()
+        loss.backward()
+        return th.grad, u.grad_fn
+
+    opts = bm.default_options(log_coefficients=1, max_cycles=500)
+    x = torch.zeros_like(b)
+
+    def forward():
+        x.zero_()
+        h = bm.setup(theta, opts, stream=stream)
+        _, info = h.solve(b, x, tol=1e-10, stream=stream)
+        h.destroy()
+        return info
+
+    out = {"workload": f"log-normal theta = 2 g (seed 3), {n}x{n}, loss 0.5 ||u - u_obs||^2, tol 1e-10"}
+    for name, fn in (("gradient", gradient), ("forward_fp64", forward)):
+        fn()
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            res = fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+        ms = statistics.median(times)
+        out[name] = {"ms": ms, "value": n * n / (ms / 1e3), "unit": UNIT}
+        if name == "gradient":
+            g, node = res
+            out[name].update(forward_cycles=node.info.cycles, forward_rel_resid=node.info.rel_resid,
+                             adjoint_cycles=node.adjoint_info.cycles,
+                             adjoint_rel_resid=node.adjoint_info.rel_resid,
+                             grad_finite=bool(torch.isfinite(g).all().item()))
+        else:
+            out[name].update(cycles=res.cycles, rel_resid=res.rel_resid)
+    out["gradient_over_forward"] = out["gradient"]["ms"] / out["forward_fp64"]["ms"]
+    return out
+
+
 def run_leg(name):
     """One of the extra legs alone, on cuda:0 (profiling and single-feature
     measurements)."""
@@ -793,6 +997,12 @@ def run_leg(name):
         out = three_d_leg(bm, torch, dev, stream, load_peaks()[0])
     elif name == "paper_workload":
         out = paper_workload_leg(bm, torch, dev, stream)
+    elif name == "c1_poisson255":
+        out = c1_leg(bm, torch, dev, stream)
+    elif name == "adjoint_gradient":
+        out = adjoint_leg(bm, torch, dev, stream)
+    elif name == "lognormal":
+        out = lognormal_leg(bm, torch, dev, stream, None)
     else:
         out = paper_workload_leg(bm, torch, dev, stream, nx=9088, ny=568)
     print(json.dumps({"leg": name, **out}))
@@ -816,7 +1026,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the e2e, fp32 and CPU legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--only", default=None,
-                    choices=["line_smoother", "three_d", "paper_workload", "paper_workload_9088x568"],
+                    choices=["line_smoother", "three_d", "paper_workload", "paper_workload_9088x568",
+                             "c1_poisson255", "adjoint_gradient", "lognormal"],
                     help="run one measurement leg alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.only is not None:
