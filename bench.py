@@ -52,7 +52,8 @@ WORKLOAD = {"workload": "diffusion 4095x4095, 64x64-cell blocks k=10^U(-4,4), se
 # level the capture ran on.
 SWEEP_DRAM_BYTES_PER_UNKNOWN = {
     "fp64": ((169.342720e6 + 18.732288e6) / 4190209, "2047^2 level of the block field"),
-    "fp64_prescaled": ((203.332864e6 + 22.704640e6) / 4190209, "2047^2 level of the block field"),
+    "fp64_prescaled": ((811.621376e6 + 122.874880e6 + 813.646080e6 + 119.546112e6) / 2 / 16769025,
+                       "4095^2 level of the block field (the benchmarked size), mean of two launches"),
     "fp32": ((338.814976e6 + 52.656128e6) / 16769025, "4095^2 level of the log-normal field"),
 }
 
@@ -455,7 +456,7 @@ def run_ours(args, rank, world, local_rank):
             "config": dict(workload, nx=args.n, ny=args.n, precision=args.precision,
                            l2="inputs and hierarchy larger than L2", parallelism=f"replicas{world}"),
             "cycles": info.cycles, "rel_resid": info.rel_resid, "threshold": info.threshold,
-            "unknown_cycles_per_s": value * info.cycles,
+            "coarse_ctas": info.coarse_ctas, "unknown_cycles_per_s": value * info.cycles,
             "setup_ms": info.setup_ms, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
             "calibration": calib, "breakdown": breakdown,
             "clocks": clk.summary(), **extra}
@@ -693,39 +694,43 @@ def three_d_leg(bm, torch, dev, stream, peaks, n=255, block=16):
 
 def threshold_sweep(bm, torch, k, b, stream, cycles=20):
     """Measured time of one V-cycle for every schedule threshold (levels below
-    it run inside the persistent coarse kernel) next to the cost model's
-    prediction, on the bench workload (the single-GPU analogue of comparing
-    modelled and measured redistribution paths)."""
+    it run inside the persistent coarse kernel, by one thread block or by a
+    thread-block cluster) next to the cost model's prediction, on the given
+    workload (the single-GPU analogue of comparing modelled and measured
+    redistribution paths)."""
     h0 = bm.setup(k, bm.default_options(), stream=stream)
     nl = h0.nlevels
-    chosen = None
     h0.destroy()
     rows = []
     x = torch.zeros_like(b)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    for thr in range(1, nl + 1):
-        h = bm.setup(k, bm.default_options(coarse_threshold=thr, max_cycles=cycles), stream=stream)
-        pred = h.predict_cycle_us(thr)
-        x.zero_()
-        h.solve(b, x, tol=1e-30, stream=stream, allow_noconv=True)
-        x.zero_()
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        h.solve(b, x, tol=1e-30, stream=stream, allow_noconv=True)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        rows.append({"threshold": thr, "measured_us_per_cycle": 1e3 * ms / cycles, "predicted_us_per_cycle": pred})
-        h.destroy()
+    for ctas in sorted({1, bm.max_coarse_ctas()}):
+        for thr in range(1, nl + 1):
+            h = bm.setup(k, bm.default_options(coarse_threshold=thr, coarse_ctas=ctas, max_cycles=cycles),
+                         stream=stream)
+            pred = h.predict_cycle_us(thr)
+            x.zero_()
+            h.solve(b, x, tol=1e-30, stream=stream, allow_noconv=True)
+            x.zero_()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            h.solve(b, x, tol=1e-30, stream=stream, allow_noconv=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            rows.append({"threshold": thr, "coarse_ctas": ctas, "measured_us_per_cycle": 1e3 * ms / cycles,
+                         "predicted_us_per_cycle": pred})
+            h.destroy()
     hc = bm.setup(k, bm.default_options(), stream=stream)
     x.zero_()
     _, info = hc.solve(b, x, tol=1e-30, stream=stream, allow_noconv=True)
-    chosen = info.threshold
     hc.destroy()
-    best = min(rows, key=lambda r: r["measured_us_per_cycle"])["threshold"]
-    return {"levels": nl, "model_choice": chosen, "measured_best": best, "rows": rows,
-            "note": "per cycle including the convergence norm and one host read of the stop flag"}
+    best = min(rows, key=lambda r: r["measured_us_per_cycle"])
+    return {"levels": nl, "model_choice": [info.threshold, info.coarse_ctas],
+            "measured_best": [best["threshold"], best["coarse_ctas"]], "rows": rows,
+            "note": "[threshold, blocks of the coarse kernel]; per cycle including the convergence norm "
+                    "and one host read of the stop flag"}
 
 
 def pcg_leg(bm, torch, k, b, stream, tol, vcycle_ms, vcycle_cycles, max_iter=2000):
@@ -916,7 +921,7 @@ def c1_leg(bm, torch, dev, stream, reps=20):
             "value": 255 * 255 / (ms_both / 1e3), "unit": UNIT,
             "ms_setup_plus_solve": ms_both, "ms_solve": ms_solve, "cycles": info.cycles,
             "us_per_cycle": 1e3 * ms_solve / info.cycles, "rel_resid": info.rel_resid,
-            "threshold": info.threshold, "levels": 7,
+            "threshold": info.threshold, "coarse_ctas": info.coarse_ctas, "levels": 7,
             "threshold_sweep": threshold_sweep(bm, torch, k, b, stream)}
 
 

@@ -12,9 +12,9 @@
  *     restriction R = P^T and interpolate-and-correct;
  *   - the coarse-grid redistribution of Section 2.2 / Algorithm 2 re-read for
  *     one GPU: every level below a threshold runs inside one persistent
- *     thread block instead of one kernel launch per operation; a cost model in
- *     the spirit of Section 3 (Eq. (Vmodel)) with measured parameters picks
- *     the threshold.
+ *     thread block, or one thread-block cluster, instead of one kernel launch
+ *     per operation; a cost model in the spirit of Section 3 (Eq. (Vmodel))
+ *     with measured parameters picks the threshold and the number of blocks.
  *
  * Conventions (all entry points):
  *   - Grid arrays passed in or out are dense, row-major, shape (ny, nx):
@@ -105,6 +105,14 @@ typedef struct {
   int smoother;             /* BMG_SMOOTH_* (default BMG_SMOOTH_POINT); line
                                smoothers are not available to the batched
                                solver                                         */
+  int coarse_ctas;          /* thread blocks that run the levels below the
+                               threshold: 1 = one block; 2..16 = one
+                               thread-block cluster of that many blocks, the
+                               phases separated by the hardware cluster
+                               barrier (point smoother only; sizes above 8
+                               need the device's non-portable cluster
+                               support); -1 (default) = chosen by the cost
+                               model together with the threshold            */
 } bmg_options;
 
 typedef struct {
@@ -113,6 +121,7 @@ typedef struct {
   double rel_resid;  /* final ||b - A x||_2 / ||b||_2, computed in FP64       */
   double setup_ms;   /* wall time of bmg_setup                                 */
   double solve_ms;   /* wall time of the last bmg_solve                        */
+  int coarse_ctas;   /* thread blocks running the levels below the threshold  */
 } bmg_info;
 
 /* Fill *opt with the defaults above. */
@@ -262,14 +271,25 @@ int bmg_assemble_backward(bmg_hierarchy *h, const double *u_dev,
 /* Measure the cost-model parameters on the current device (the analogue of
  * the Section 3 machine parameters alpha, beta, gamma) and use them for every
  * later threshold choice in this process.  params_out (may be NULL) receives
- * 8 doubles: launch latency [us], in-block barrier phase [us], streaming
+ * 10 doubles: launch latency [us], in-block barrier phase [us], streaming
  * bandwidth [GB/s], FP64 and FP32 FMA rates of the whole GPU [GFLOP/s],
- * one-block L2 bandwidth [GB/s], one-block FP64 and FP32 rates [GFLOP/s].
+ * one-block L2 bandwidth [GB/s], one-block FP64 and FP32 rates [GFLOP/s],
+ * cluster-barrier phase [us] and the cluster size it was measured with (the
+ * largest the coarse kernel can use; 1 and the default phase time when the
+ * device has no thread-block clusters).
  * Allocates and frees 1 GiB of scratch; synchronises the stream. */
 int bmg_calibrate(bmg_stream_t stream, double *params_out);
 
+/* Largest value bmg_options.coarse_ctas may take on the current device for
+ * the given precision (BMG_FP64 or BMG_FP32_REFINE): the largest thread-block
+ * cluster (a power of two <= 16) the cluster coarse kernel can be launched
+ * with, 1 when the device has no thread-block clusters.  No device work
+ * besides attribute queries. */
+int bmg_max_coarse_ctas(int precision, int *out);
+
 /* Model-predicted time [us] of one V-cycle of h with the given threshold
- * (levels l < threshold inside the persistent kernel). */
+ * (levels l < threshold inside the persistent kernel, run by as many blocks
+ * as h uses, see bmg_info.coarse_ctas). */
 int bmg_predict_cycle_us(const bmg_hierarchy *h, int threshold, double *us);
 
 /* ---- Batched solves (many independent problems) -------------------------- */

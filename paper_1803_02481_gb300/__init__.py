@@ -34,12 +34,12 @@ class Options(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("log_coefficients", ctypes.c_int),
                 ("solver", ctypes.c_int), ("aniso_r", ctypes.c_double),
                 ("cell_aspect", ctypes.c_double), ("bc_beta", ctypes.c_double * 4),
-                ("smoother", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("coarse_ctas", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("threshold", ctypes.c_int), ("rel_resid", ctypes.c_double),
-                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("coarse_ctas", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -87,6 +87,7 @@ EXPORTED = {
     "bmg_batch_destroy": (None, [_vp]),
     "bmg_calibrate": (_i, [_vp, _vp]),
     "bmg_predict_cycle_us": (_i, [_vp, _i, ctypes.POINTER(_d)]),
+    "bmg_max_coarse_ctas": (_i, [_i, ctypes.POINTER(_i)]),
     "bmg_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp]),
     "bmg_selftest_bounded_wait": (_i, [_vp]),
     "bmg_kernel_launches": (ctypes.c_longlong, []),
@@ -110,14 +111,22 @@ PROF_CLASSES = {"fine_smooth": 1, "fine_resid": 2, "fine_interp": 3, "coarse_ker
 
 
 CALIBRATION_KEYS = ("launch_us", "sync_us", "gpu_gbs", "gpu_gflops64", "gpu_gflops32", "cta_gbs",
-                    "cta_gflops64", "cta_gflops32")
+                    "cta_gflops64", "cta_gflops32", "cluster_sync_us", "cluster_ctas")
 
 
 def calibrate(stream=None) -> dict:
     """Measure the level-schedule cost-model parameters on this GPU."""
-    out = (ctypes.c_double * 8)()
+    out = (ctypes.c_double * len(CALIBRATION_KEYS))()
     _check(lib().bmg_calibrate(_stream(stream), out), "bmg_calibrate")
     return dict(zip(CALIBRATION_KEYS, list(out)))
+
+
+def max_coarse_ctas(precision: int = BMG_FP64) -> int:
+    """Largest thread-block cluster the coarse kernel can use on this GPU
+    (1: none)."""
+    out = ctypes.c_int()
+    _check(lib().bmg_max_coarse_ctas(int(precision), ctypes.byref(out)), "bmg_max_coarse_ctas")
+    return out.value
 
 
 def kernel_launches() -> int:

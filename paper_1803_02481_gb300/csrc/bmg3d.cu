@@ -832,6 +832,7 @@ int bmg3_solve(bmg3_hierarchy* h, const double* b, double* x, double tol, bmg_in
     info->rel_resid = rel;
     info->setup_ms = h->setup_ms;
     info->solve_ms = now_ms() - t0;
+    info->coarse_ctas = 1;
   }
   return rc;
 }

@@ -253,6 +253,15 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
     delete h;
     return BMG_EINVAL;
   }
+  if (opt.coarse_ctas != -1 &&
+      (opt.coarse_ctas < 1 || opt.coarse_ctas > 16 ||
+       (opt.coarse_ctas > 1 && (opt.smoother != BMG_SMOOTH_POINT ||
+                                opt.coarse_ctas > max_cluster_ctas(opt.precision == BMG_FP32_REFINE))))) {
+    set_last_error("coarse_ctas must be -1 or 1..%d, and 1 with a line smoother",
+                   max_cluster_ctas(opt.precision == BMG_FP32_REFINE));
+    delete h;
+    return BMG_EINVAL;
+  }
   const bool fp32 = opt.precision == BMG_FP32_REFINE;
   for (int l = 0; l < L; ++l) {
     const auto& q = sz[L - 1 - l];
@@ -351,8 +360,9 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
     make_maps(h->f, h->maps32);
   }
 
-  // Level schedule: which levels leave the full-grid launches.
-  h->threshold = opt.coarse_threshold > 0 ? opt.coarse_threshold : choose_threshold(h);
+  // Level schedule: which levels leave the full-grid launches, and how many
+  // blocks run them.
+  choose_schedule(h);
   h->setup_ms = now_ms() - t0;
   *out = h;
   return BMG_OK;
@@ -567,10 +577,10 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
       if (r.bnorm2 == 0.0) {
         BMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * size_t(h->nx) * h->ny, s));
         BMG_CUDA(cudaStreamSynchronize(s));
-        if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0};
+        if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0, h->coarse_ctas};
         return BMG_OK;
       }
-      if (info) *info = bmg_info{r.cycles, h->threshold, r.rel, h->setup_ms, now_ms() - t0};
+      if (info) *info = bmg_info{r.cycles, h->threshold, r.rel, h->setup_ms, now_ms() - t0, h->coarse_ctas};
       if (r.err & DEV_NAN) return BMG_ENAN;
       if (r.err & DEV_TIMEOUT) return BMG_ETIMEOUT;
       if (!(r.rel <= tol)) return BMG_ENOCONV;
@@ -583,7 +593,7 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
     if (h->sc_host->bnorm2 == 0.0) {
       BMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * size_t(h->nx) * h->ny, s));
       BMG_CUDA(cudaStreamSynchronize(s));
-      if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0};
+      if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0, h->coarse_ctas};
       return BMG_OK;
     }
     if (h->sc_host->go) {
@@ -606,7 +616,7 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
     if (h->sc_host->bnorm2 == 0.0) {
       BMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * size_t(h->nx) * h->ny, s));
       BMG_CUDA(cudaStreamSynchronize(s));
-      if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0};
+      if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0, h->coarse_ctas};
       return BMG_OK;
     }
     while (h->sc_host->go) {
@@ -619,7 +629,7 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
     if (h->sc_host->bnorm2 == 0.0) {
       BMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * size_t(h->nx) * h->ny, s));
       BMG_CUDA(cudaStreamSynchronize(s));
-      if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0};
+      if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0, h->coarse_ctas};
       return BMG_OK;
     }
     for (;;) {
@@ -635,7 +645,7 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
   BMG_CUDA(cudaGetLastError());
   BMG_CUDA(cudaStreamSynchronize(s));
   const Scalars& r = *h->sc_host;
-  if (info) *info = bmg_info{r.cycles, h->threshold, r.rel, h->setup_ms, now_ms() - t0};
+  if (info) *info = bmg_info{r.cycles, h->threshold, r.rel, h->setup_ms, now_ms() - t0, h->coarse_ctas};
   if (r.err & DEV_NAN) return BMG_ENAN;
   if (r.err & DEV_TIMEOUT) return BMG_ETIMEOUT;
   if (!(r.rel <= tol)) return BMG_ENOCONV;
@@ -664,6 +674,7 @@ void bmg_default_options(bmg_options* opt) {
   opt->coarse_threshold = -1;
   opt->max_cycles = 200;
   opt->smoother = BMG_SMOOTH_POINT;
+  opt->coarse_ctas = -1;
   opt->log_coefficients = 0;
   opt->solver = BMG_SOLVER_VCYCLE;
   opt->aniso_r = 1.0;

@@ -589,6 +589,7 @@ extern "C" int bmg_batch_setup(int nprob, const double* const* k_dev, const int*
       if (m <= kCoarseSide) ++levels_small;
     bmg_options o = opt;
     o.coarse_threshold = std::max(1, levels_small);
+    o.coarse_ctas = 1;         // the batched coarse kernel runs one block per problem
     Hierarchy* h = nullptr;
     const int rc = setup_impl(k_dev[p], n[p], n[p], &o, s, &h);
     if (rc) {
@@ -753,7 +754,7 @@ extern "C" int bmg_batch_solve(bmg_batch* bp, const double* const* b_dev, double
   int rc = BMG_OK;
   for (int p = 0; p < b->nprob; ++p) {
     const Scalars& r = b->sc_host[p];
-    if (per_prob) per_prob[p] = bmg_info{r.cycles, b->hs[p]->threshold, r.rel, b->setup_ms, ms};
+    if (per_prob) per_prob[p] = bmg_info{r.cycles, b->hs[p]->threshold, r.rel, b->setup_ms, ms, 1};
     if (r.err & DEV_NAN) rc = BMG_ENAN;
     else if (!(r.rel <= tol) && r.bnorm2 > 0.0 && rc == BMG_OK) rc = BMG_ENOCONV;
   }

@@ -145,6 +145,62 @@ __global__ void __launch_bounds__(512, 1) k_coarse_cycle_line(CoarseArgs<T> a) {
   coarse_cycle_body<T, true>(a);
 }
 
+// The point-smoother sub-cycle over every block of one thread-block cluster
+// (launched with a cluster dimension equal to the grid): each phase is spread
+// over the cluster's blocks, one per SM, and phases are separated by the
+// hardware cluster barrier.
+template <typename T>
+__global__ void __launch_bounds__(kCoarseClusterThreads, 1) k_coarse_cycle_cluster(CoarseArgs<T> a) {
+  coarse_cycle_body<T, false, ClusterTeam>(a);
+}
+
+template <typename T>
+static cudaError_t launch_cluster_kernel(int ctas, cudaStream_t s, const CoarseArgs<T>& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(ctas));
+  cfg.blockDim = dim3(kCoarseClusterThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = unsigned(ctas);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_coarse_cycle_cluster<T>, a);
+}
+
+// Largest cluster size (a power of two up to 16) whose blocks of the cluster
+// kernel the device can co-schedule, 1 when clusters are unavailable.
+// Sizes above 8 need the non-portable cluster attribute.
+template <typename T>
+static int max_cluster_ctas_t() {
+  int dev = 0, cc = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  cudaDeviceGetAttribute(&cc, cudaDevAttrClusterLaunch, dev);
+  if (!cc) return 1;
+  cudaFuncSetAttribute(k_coarse_cycle_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int c = 16; c >= 2; c /= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(c));
+    cfg.blockDim = dim3(kCoarseClusterThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(c);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_coarse_cycle_cluster<T>, &cfg) == cudaSuccess && n > 0)
+      return c;
+    cudaGetLastError();
+  }
+  return 1;
+}
+
+
 // ---------------------------------------------------------------------------
 // Norms and the stop test.  Fixed grid, fixed per-thread order and a fixed
 // reduction tree, so the result is deterministic.
@@ -282,6 +338,13 @@ __global__ void k_refine_update(LevelV<double> L, LevelV<float> F, const Scalars
 
 }  // namespace
 
+int max_cluster_ctas(bool fp32) {
+  static int cached[2] = {0, 0};
+  int& c = cached[fp32 ? 1 : 0];
+  if (c == 0) c = fp32 ? max_cluster_ctas_t<float>() : max_cluster_ctas_t<double>();
+  return c;
+}
+
 // ---------------------------------------------------------------------------
 // Launch wrappers
 // ---------------------------------------------------------------------------
@@ -362,6 +425,8 @@ void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* dev_levels, int thr, cud
   prof_begin(BMG_PROF_COARSE, s);
   if (a.smoother != BMG_SMOOTH_POINT)
     k_coarse_cycle_line<T><<<1, 512, 0, s>>>(a);
+  else if (h->coarse_ctas > 1)
+    launch_cluster_kernel<T>(h->coarse_ctas, s, a);
   else
     k_coarse_cycle<T><<<1, 1024, 0, s>>>(a);
   prof_end(BMG_PROF_COARSE, s);

@@ -312,6 +312,7 @@ struct Hierarchy {
   int nx = 0, ny = 0, L = 0;
   bmg_options opt{};
   int threshold = 1;                 // levels l < threshold: persistent kernel
+  int coarse_ctas = 1;               // its thread blocks (1: one block; more: a cluster)
   std::vector<LevelV<double>> d;     // FP64 levels (all for FP64; finest only
                                      // for FP32_REFINE)
   std::vector<LevelV<float>> f;      // FP32 levels (FP32_REFINE)
@@ -393,6 +394,12 @@ template <typename T>
 void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s,
                    T* out = nullptr);
 void prepare_sweep_kernels();
+
+// Threads per block of the cluster coarse kernel, and the largest cluster
+// (blocks, a power of two <= 16) the device can run it with; 1 when thread-
+// block clusters are unavailable.
+constexpr int kCoarseClusterThreads = 512;
+int max_cluster_ctas(bool fp32);
 // Runs the TMA sweeps' bounded mbarrier wait on a phase nothing completes
 // (bmg_selftest_bounded_wait).
 int selftest_bounded_wait(cudaStream_t s);

@@ -13,7 +13,7 @@ namespace bmg {
 CostParams& cost_params() {
   // Defaults: GB300 class figures; bmg_calibrate() replaces them with
   // measured values.
-  static CostParams p{2.5, 0.35, 6000.0, 1100.0, 60000.0, 120.0, 7.0, 450.0};
+  static CostParams p{2.5, 0.35, 6000.0, 1100.0, 60000.0, 120.0, 7.0, 450.0, 1.0};
   return p;
 }
 
@@ -56,11 +56,12 @@ LevelCost level_cost(const Hierarchy* h, int l) {
 
 }  // namespace
 
-double predict_vcycle_us(const Hierarchy* h, int thr) {
+double predict_vcycle_us(const Hierarchy* h, int thr, int ctas) {
   const CostParams& p = cost_params();
   const bool fp32 = h->opt.precision == BMG_FP32_REFINE;
   const double fg = fp32 ? p.gpu_gflops32 : p.gpu_gflops64;
   const double fc = fp32 ? p.cta_gflops32 : p.cta_gflops64;
+  const double sync = ctas > 1 ? p.cluster_sync_us : p.sync_us;
   double t = 0.0;
   for (int l = 1; l < h->L; ++l) {
     const LevelCost c = level_cost(h, l);
@@ -69,9 +70,10 @@ double predict_vcycle_us(const Hierarchy* h, int thr) {
       const double work = std::max(c.bytes / (p.gpu_gbs * 1e3), c.flops / (fg * 1e3));
       t += c.launches * p.launch_us + work;
     } else {
-      // inside one block: barrier latency + work at one SM's rates
-      const double work = std::max(c.bytes / (p.cta_gbs * 1e3), c.flops / (fc * 1e3));
-      t += c.launches * p.sync_us + work;
+      // inside the persistent kernel: barrier latency + work at the rates of
+      // `ctas` SMs
+      const double work = std::max(c.bytes / (ctas * p.cta_gbs * 1e3), c.flops / (ctas * fc * 1e3));
+      t += c.launches * sync + work;
     }
   }
   // the persistent kernel itself and the coarsest solve (n0^2 flops, as the
@@ -81,18 +83,31 @@ double predict_vcycle_us(const Hierarchy* h, int thr) {
   return t;
 }
 
-int choose_threshold(Hierarchy* h) {
-  int best = 1;
+void choose_schedule(Hierarchy* h) {
+  const bool point = h->opt.smoother == BMG_SMOOTH_POINT;
+  int cands[2] = {1, 1};
+  int nc = 1;
+  if (h->opt.coarse_ctas > 0) {
+    cands[0] = h->opt.coarse_ctas;
+  } else if (point) {
+    const int cmax = max_cluster_ctas(h->opt.precision == BMG_FP32_REFINE);
+    if (cmax > 1) cands[nc++] = cmax;
+  }
+  const int t0 = h->opt.coarse_threshold > 0 ? h->opt.coarse_threshold : 1;
+  const int t1 = h->opt.coarse_threshold > 0 ? h->opt.coarse_threshold : h->L;
   double bt = 1e300;
-  for (int thr = 1; thr <= h->L; ++thr) {
-    const double t = predict_vcycle_us(h, thr);
-    if (thr - 1 < 16) h->predicted_us[thr - 1] = t;
-    if (t < bt) {
-      bt = t;
-      best = thr;
+  for (int k = 0; k < nc; ++k) {
+    for (int thr = t0; thr <= t1; ++thr) {
+      const double t = predict_vcycle_us(h, thr, cands[k]);
+      if (t < bt) {
+        bt = t;
+        h->threshold = thr;
+        h->coarse_ctas = cands[k];
+      }
     }
   }
-  return best;
+  for (int thr = 1; thr <= h->L && thr <= 16; ++thr)
+    h->predicted_us[thr - 1] = predict_vcycle_us(h, thr, h->coarse_ctas);
 }
 
 }  // namespace bmg
@@ -120,6 +135,36 @@ __global__ void __launch_bounds__(1024) k_phases(double* buf, int phases) {
     __syncthreads();
   }
   if (v == -1.0) buf[0] = v;
+}
+
+// The same phases over every block of a thread-block cluster, separated by
+// the cluster barrier.
+__global__ void __launch_bounds__(kCoarseClusterThreads) k_phases_cluster(double* buf, int phases) {
+  double v = 0.0;
+  unsigned rank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  for (int p = 0; p < phases; ++p) {
+    v += buf[(threadIdx.x + p + 64 * rank) & 1023];
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+    if (threadIdx.x == 0) buf[(p + 64 * rank) & 1023] = v;
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+  }
+  if (v == -1.0) buf[0] = v;
+}
+
+cudaError_t launch_phases_cluster(int ctas, cudaStream_t s, double* buf, int phases) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(ctas));
+  cfg.blockDim = dim3(kCoarseClusterThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = unsigned(ctas);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_phases_cluster, buf, phases);
 }
 
 template <typename T>
@@ -177,6 +222,16 @@ int calibrate(cudaStream_t s, double* out) {
   k_phases<<<1, 1024, 0, s>>>(buf, ph);
   cudaEventRecord(e1, s);
   p.sync_us = 1e3 * time_ms(s, e0, e1) / (2.0 * ph);
+  // cluster-barrier phase over the largest cluster the coarse kernel can use
+  const int cmax = max_cluster_ctas(false);
+  if (cmax > 1) {
+    cudaFuncSetAttribute(k_phases_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    launch_phases_cluster(cmax, s, buf, 10);
+    cudaEventRecord(e0, s);
+    launch_phases_cluster(cmax, s, buf, ph);
+    cudaEventRecord(e1, s);
+    p.cluster_sync_us = 1e3 * time_ms(s, e0, e1) / (2.0 * ph);
+  }
   // FMA rates, whole GPU and one block
   const int iters = 1 << 14, tb = 256;
   auto rate = [&](auto tag, int blocks) {
@@ -223,6 +278,8 @@ int calibrate(cudaStream_t s, double* out) {
     out[5] = p.cta_gbs;
     out[6] = p.cta_gflops64;
     out[7] = p.cta_gflops32;
+    out[8] = p.cluster_sync_us;
+    out[9] = double(cmax);
   }
   return BMG_OK;
 }
@@ -236,6 +293,12 @@ extern "C" int bmg_calibrate(bmg_stream_t stream, double* params_out) {
 extern "C" int bmg_predict_cycle_us(const bmg_hierarchy* hp, int threshold, double* us) {
   const bmg::Hierarchy* h = reinterpret_cast<const bmg::Hierarchy*>(hp);
   if (!h || !us || threshold < 1 || threshold > h->L) return BMG_EINVAL;
-  *us = bmg::predict_vcycle_us(h, threshold);
+  *us = bmg::predict_vcycle_us(h, threshold, h->coarse_ctas);
+  return BMG_OK;
+}
+
+extern "C" int bmg_max_coarse_ctas(int precision, int* out) {
+  if (!out || (precision != BMG_FP64 && precision != BMG_FP32_REFINE)) return BMG_EINVAL;
+  *out = bmg::max_cluster_ctas(precision == BMG_FP32_REFINE);
   return BMG_OK;
 }

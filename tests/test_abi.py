@@ -40,6 +40,7 @@ def test_host_only_calls_work_without_gpu():
     lib = bm.lib()
     o = bm.default_options()
     assert (o.nu1, o.nu2, o.precision, o.coarse_threshold, o.max_cycles) == (2, 1, 0, -1, 200)
+    assert o.coarse_ctas == -1 and o.smoother == bm.BMG_SMOOTH_POINT
     assert lib.bmg_strerror(bm.BMG_ENOCONV).decode().startswith("no convergence")
     # argument validation happens before any device work
     h = ctypes.c_void_p()

@@ -167,25 +167,68 @@ def test_solve_slow_contrast_case_matches_oracle():
     test_solve_matches_oracle("blocks511_c2")
 
 
+def cluster_sizes(precision=bm.BMG_FP64):
+    cmax = bm.max_coarse_ctas(precision)
+    return sorted({1, min(2, cmax), cmax})
+
+
 @pytest.mark.parametrize("name", ["blocks255", "rect127x31"])
 def test_every_threshold_gives_identical_iterates(name):
     """The level schedule moves levels between full-grid launches and the
-    persistent kernel; per-point arithmetic is shared, so results are
-    bit-identical for every threshold."""
+    persistent kernel, run by one block or by a thread-block cluster;
+    per-point arithmetic is shared and the points of a colour are
+    independent, so results are bit-identical for every threshold and every
+    number of blocks."""
     pr = problem(name)
     L = oracle_hierarchy(name).nlevels
     ref = None
-    for thr in range(1, L + 1):
-        hg = gpu_setup(name, coarse_threshold=thr)
-        x, info = hg.solve(dev(pr["b"]), tol=1e-10)
-        assert info.threshold == thr
-        xn = x.cpu().numpy()
-        if ref is None:
-            ref = (xn, info.cycles, info.rel_resid)
-        else:
-            assert np.array_equal(xn, ref[0]), thr
-            assert info.cycles == ref[1] and info.rel_resid == ref[2]
-        hg.destroy()
+    for ctas in cluster_sizes():
+        for thr in range(1, L + 1):
+            hg = gpu_setup(name, coarse_threshold=thr, coarse_ctas=ctas)
+            x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+            assert info.threshold == thr and info.coarse_ctas == ctas
+            xn = x.cpu().numpy()
+            if ref is None:
+                ref = (xn, info.cycles, info.rel_resid)
+            else:
+                assert np.array_equal(xn, ref[0]), (ctas, thr)
+                assert info.cycles == ref[1] and info.rel_resid == ref[2]
+            hg.destroy()
+
+
+def test_cluster_coarse_kernel_fp32_and_rc_identical_to_one_block():
+    """FP32 refinement and the r/C variant through the cluster kernel: the
+    same bits as the one-block kernel at every threshold."""
+    name = "lognormal255"
+    pr = problem(name)
+    L = oracle_hierarchy(name).nlevels
+    for prec, kw in ((bm.BMG_FP32_REFINE, {}), (bm.BMG_FP64, dict(interp_residual_term=1))):
+        cmax = bm.max_coarse_ctas(prec)
+        for thr in (2, L - 2, L):
+            out = []
+            for ctas in (1, cmax):
+                hg = gpu_setup(name, precision=prec, coarse_threshold=thr, coarse_ctas=ctas, **kw)
+                x, info = hg.solve(dev(pr["b"]), tol=1e-10)
+                hg.destroy()
+                out.append((x.cpu().numpy(), info.cycles, info.rel_resid))
+            assert np.array_equal(out[0][0], out[1][0]), (prec, thr)
+            assert out[0][1:] == out[1][1:]
+
+
+def test_schedule_options_are_checked():
+    k = dev(np.ones((31, 31)))
+    cmax = bm.max_coarse_ctas()
+    for kw in (dict(coarse_ctas=0), dict(coarse_ctas=17), dict(coarse_ctas=cmax + 1),
+               dict(coarse_ctas=2, smoother=bm.BMG_SMOOTH_XLINE), dict(coarse_threshold=0)):
+        if kw.get("coarse_ctas") == 2 and cmax < 2:
+            continue
+        with pytest.raises(bm.BoxMGError) as e:
+            bm.setup(k, bm.default_options(**kw))
+        assert e.value.code == bm.BMG_EINVAL, kw
+    h = bm.setup(k)                     # the model's choice is reported
+    _, info = h.solve(dev(np.ones((31, 31))))
+    assert 1 <= info.coarse_ctas <= cmax and 1 <= info.threshold <= h.nlevels
+    h.destroy()
 
 
 def test_prescaled_fine_level_identical_in_every_kernel():
@@ -197,8 +240,8 @@ def test_prescaled_fine_level_identical_in_every_kernel():
     pr = problem(name)
     L = oracle_hierarchy(name).nlevels
     ref = None
-    for thr in (1, L - 1, L):
-        hg = gpu_setup(name, coarse_threshold=thr)
+    for thr, ctas in ((1, 1), (L - 1, 1), (L, 1), (L, bm.max_coarse_ctas())):
+        hg = gpu_setup(name, coarse_threshold=thr, coarse_ctas=ctas)
         assert hg.level_prescaled(L - 1) and not hg.level_prescaled(L - 2)
         x, info = hg.solve(dev(pr["b"]), tol=1e-10)
         hg.destroy()
@@ -206,7 +249,7 @@ def test_prescaled_fine_level_identical_in_every_kernel():
         if ref is None:
             ref = (xn, info.cycles, info.rel_resid)
         else:
-            assert np.array_equal(xn, ref[0]), thr
+            assert np.array_equal(xn, ref[0]), (thr, ctas)
             assert info.cycles == ref[1] and info.rel_resid == ref[2]
     hf = gpu_setup(name, precision=bm.BMG_FP32_REFINE)
     assert not hf.level_prescaled(L - 1)
