@@ -812,6 +812,30 @@ def batch_leg(bm, torch, dev, stream, count=512):
         ms = ev0.elapsed_time(ev1)
         out[name] = {"value": unknowns / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms}
     out["speedup_batched_vs_sequential_fp64"] = out["sequential_fp64"]["ms_per_solve"] / ms_batch
+    # split by size class: each class solved alone as a batch of its own
+    # (same problems, same solver), so the share of the whole batch's time
+    # that each class's refinement-step count sets is visible
+    classes = {}
+    for n in sorted({p["n"] for p in probs}):
+        idx = [i for i, p in enumerate(probs) if p["n"] == n]
+        bc = bm.Batch([ks[i] for i in idx], bm.default_options(max_cycles=3000), stream=stream)
+        xc = [xs[i] for i in idx]
+        for x in xc:
+            x.zero_()
+        bc.solve([bs[i] for i in idx], xc, tol=1e-8, stream=stream)
+        for x in xc:
+            x.zero_()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        inf = bc.solve([bs[i] for i in idx], xc, tol=1e-8, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        bc.destroy()
+        steps = sorted(i.cycles for i in inf)
+        classes[str(n)] = {"problems": len(idx), "ms_alone": ev0.elapsed_time(ev1),
+                           "steps_max": steps[-1], "steps_median": steps[len(steps) // 2],
+                           "unknowns": len(idx) * n * n}
+    out["by_side_alone"] = classes
     return out
 
 

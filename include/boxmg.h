@@ -326,6 +326,89 @@ int bmg_batch_size(const bmg_batch *b, int *nprob);
 /* Release a batch (NULL is allowed). */
 void bmg_batch_destroy(bmg_batch *b);
 
+/* ---- Domain decomposition (Section 2.1) and redistribution (Algorithm 2) --
+ *
+ * One rank's part of a distributed hierarchy.  The ranks form a px x py
+ * processor grid (Section 2.1); on every distributed level a rank owns one
+ * rectangular block of points, stored with a one-point ring that holds the
+ * neighbours' values (the width-1 halo).  A part holds nlev levels, part
+ * level 0 (the gather level of Algorithm 2, vectors only) up to part level
+ * nlev - 1 (the finest).  The caller moves ring and block data between ranks
+ * (halo exchange, gather_rhs, scatter_sol) with bmg_dd_copy and bmg_dd_block
+ * and runs the coarse levels below the gather level on one rank with
+ * bmg_op_vcycle_from.  Blocks must start at 0-based global indices that are
+ * multiples of 2^(nlev - 1) in both directions, so that local and global
+ * point parities (colours, coarse points) agree on every level.  All device
+ * work is ordered on the given stream. */
+
+typedef struct bmg_dd_part bmg_dd_part;  /* opaque, library-owned */
+
+enum { BMG_DD_X = 0, BMG_DD_B = 1, BMG_DD_R = 2 };              /* vectors      */
+enum { BMG_DD_WEST = 0, BMG_DD_EAST = 1, BMG_DD_SOUTH = 2, BMG_DD_NORTH = 3 };
+
+/* Create one rank's part.  nx[k], ny[k]: owned block size on part level k
+ * (>= 1).  nine[k]: 1 if part level k has a 9-point operator, 0 for the
+ * 5-point finest level.  stencil_host[k] (k >= 1; entry 0 ignored): host
+ * doubles (5, ny[k] + 2, nx[k] + 2), the planes C, W, S, SW, NW (the
+ * negated couplings of bmg_level_stencil) of the block and its ring, zero
+ * outside the domain.  interp_host[k] (k >= 1): host doubles
+ * (8, ny[k-1] + 2, nx[k-1] + 2), the eight interpolation planes of
+ * bmg_level_interp (weights stored at coarse points, Section 3) on the
+ * coarser block with its ring.  Copies everything; vectors start at zero.
+ * Synchronises the stream.  BMG_EINVAL for empty blocks or missing planes. */
+int bmg_dd_part_create(int nlev, const int *nx, const int *ny, const int *nine,
+                       const double *const *stencil_host,
+                       const double *const *interp_host, bmg_stream_t stream,
+                       bmg_dd_part **out);
+
+/* Release a part (NULL is allowed). */
+void bmg_dd_part_destroy(bmg_dd_part *p);
+
+/* One colour of multicolour Gauss-Seidel on the owned points of part level
+ * k >= 1, in place (colour 0..1 red-black on a 5-point level, 0..3 on a
+ * 9-point level, in the forward order of the full-level smoother).  The ring
+ * of x must hold the neighbours' current values (halo exchange per colour,
+ * Algorithm 2). */
+int bmg_dd_relax_colour(bmg_dd_part *p, int k, int colour, bmg_stream_t stream);
+
+/* r = b - A x on the owned points of part level k >= 1 (x ring current). */
+int bmg_dd_residual(bmg_dd_part *p, int k, bmg_stream_t stream);
+
+/* b = P^T r on the owned points of part level k - 1, x there set to zero
+ * (r's ring current; restriction needs no other communication, Section 3). */
+int bmg_dd_restrict(bmg_dd_part *p, int k, bmg_stream_t stream);
+
+/* x_k += P x_{k-1} on the owned points of part level k (the coarse x and
+ * its ring current). */
+int bmg_dd_interp(bmg_dd_part *p, int k, bmg_stream_t stream);
+
+/* out2_host[0] = sum of r^2, out2_host[1] = sum of b^2 over the owned points
+ * of part level k >= 1, in a fixed order; synchronises the stream. */
+int bmg_dd_norms(bmg_dd_part *p, int k, double *out2_host, bmg_stream_t stream);
+
+/* Halo strips of vector `vec` (BMG_DD_X/B/R) of part level k.  dir 0 (get)
+ * copies the owned edge line next to `side` into buf_dev; dir 1 (put) copies
+ * buf_dev into the ring line on that side.  West/east lines are columns of
+ * ny[k] values (rows 1..ny); south/north lines are rows of nx[k] + 2 values
+ * (ring columns included, so a west/east exchange followed by a south/north
+ * exchange fills the ring corners).  buf_dev: caller-owned device memory. */
+int bmg_dd_copy(bmg_dd_part *p, int k, int vec, int side, int dir, double *buf_dev,
+                bmg_stream_t stream);
+
+/* Whole block of `vec` on part level k to (dir 0) or from (dir 1) a dense
+ * row-major device array: ring == 0: the owned (ny, nx) points; ring == 1:
+ * (ny + 2, nx + 2) including the ring. */
+int bmg_dd_block(bmg_dd_part *p, int k, int vec, int dir, int ring, double *dense_dev,
+                 bmg_stream_t stream);
+
+/* x = one V-cycle (Algorithm 1, the hierarchy's nu1, nu2, smoother and level
+ * schedule) on levels 0..level of h for A_level x = b from x = 0: the cycle
+ * the rank holding an agglomerated coarse problem runs (Algorithm 2, after
+ * gather_rhs).  b_dev, x_dev: dense (ny, nx) float64 device arrays of that
+ * level.  FP64 point-smoother hierarchies; 0 <= level < number of levels. */
+int bmg_op_vcycle_from(bmg_hierarchy *h, int level, const double *b_dev, double *x_dev,
+                       bmg_stream_t stream);
+
 /* ---- Allocation-free residual check --------------------------------------- */
 
 /* ||b - A(k) x||_2 and ||b||_2 for the 5-point cell-centred operator of k

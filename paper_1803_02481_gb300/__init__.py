@@ -89,6 +89,16 @@ EXPORTED = {
     "bmg_predict_cycle_us": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "bmg_max_coarse_ctas": (_i, [_i, ctypes.POINTER(_i)]),
     "bmg_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp]),
+    "bmg_dd_part_create": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _HP]),
+    "bmg_dd_part_destroy": (None, [_vp]),
+    "bmg_dd_relax_colour": (_i, [_vp, _i, _i, _vp]),
+    "bmg_dd_residual": (_i, [_vp, _i, _vp]),
+    "bmg_dd_restrict": (_i, [_vp, _i, _vp]),
+    "bmg_dd_interp": (_i, [_vp, _i, _vp]),
+    "bmg_dd_norms": (_i, [_vp, _i, _vp, _vp]),
+    "bmg_dd_copy": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
+    "bmg_dd_block": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
+    "bmg_op_vcycle_from": (_i, [_vp, _i, _vp, _vp, _vp]),
     "bmg_selftest_bounded_wait": (_i, [_vp]),
     "bmg_kernel_launches": (ctypes.c_longlong, []),
     "bmg_profile_set": (_i, [_i]),
@@ -338,6 +348,14 @@ class Hierarchy:
         g, gc = self._grid(level), self._grid(level - 1)
         _check(lib().bmg_op_interp(self._h, level, _dev(xc, "xc", gc), _dev(x, "x", g), _stream(stream)),
                "bmg_op_interp")
+        return x
+
+    def vcycle_from(self, level, b, x, stream=None):
+        """x = one V-cycle on A_level x = b from x = 0 over levels 0..level
+        (the agglomerated coarse cycle of Algorithm 2)."""
+        g = self._grid(level)
+        _check(lib().bmg_op_vcycle_from(self._h, level, _dev(b, "b", g), _dev(x, "x", g), _stream(stream)),
+               "bmg_op_vcycle_from")
         return x
 
     def assemble_backward(self, u, lam, dtheta, stream=None):

@@ -386,8 +386,12 @@ const SweepMaps<float>* level_maps<float>(const Hierarchy* h, int l) {
 
 template <typename T>
 void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* dlev, int thr,
-                    cudaStream_t s) {
+                    cudaStream_t s, int top) {
   const int L = h->L;
+  // a cycle from level `top` down (the finest unless given): the levels
+  // below the schedule's threshold still run in the persistent kernel
+  if (top < 0 || top > L - 1) top = L - 1;
+  thr = std::min(thr, top + 1);
   const int nu1 = h->opt.nu1, nu2 = h->opt.nu2;
   const bool rc = h->opt.interp_residual_term != 0;
   // Sweeps write the other iterate buffer; with nu1 + nu2 odd the
@@ -406,7 +410,7 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
     std::swap(V.x, V.x2);
   };
   prof_begin(BMG_PROF_CYCLE, s);
-  for (int l = L - 1; l >= thr; --l) {
+  for (int l = top; l >= thr; --l) {
     const bool nine = l != L - 1;
     if (nine) prof_begin(BMG_PROF_LEVELS, s);
     for (int k = 0; k < nu1; ++k) sweep(l, false);
@@ -419,7 +423,7 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
     if (nine) prof_end(BMG_PROF_LEVELS, s);
   }
   launch_coarse_cycle<T>(h, dlev, thr, s);
-  for (int l = thr; l < L; ++l) {
+  for (int l = thr; l <= top; ++l) {
     const bool nine = l != L - 1;
     if (nine) prof_begin(BMG_PROF_LEVELS, s);
     if (interp_oop) {
@@ -435,9 +439,9 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
 }
 
 template void enqueue_vcycle<double>(Hierarchy*, std::vector<LevelV<double>>&,
-                                     const LevelV<double>*, int, cudaStream_t);
+                                     const LevelV<double>*, int, cudaStream_t, int);
 template void enqueue_vcycle<float>(Hierarchy*, std::vector<LevelV<float>>&, const LevelV<float>*,
-                                    int, cudaStream_t);
+                                    int, cudaStream_t, int);
 
 static int read_scalars(Hierarchy* h, cudaStream_t s) {
   BMG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
@@ -948,6 +952,27 @@ int bmg_op_interp(bmg_hierarchy* hp, int level, const double* xc, double* x,
   bmg::launch_pack<double>(xc, Lc.x, Lc.nx, Lc.ny, Lc.pitch, s);
   bmg::launch_pack<double>(x, L.x, L.nx, L.ny, L.pitch, s);
   bmg::launch_interp<double>(L, Lc.x, false, s);
+  bmg::launch_unpack<double>(L.x, x, L.nx, L.ny, L.pitch, s);
+  return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;
+}
+
+int bmg_op_vcycle_from(bmg_hierarchy* hp, int level, const double* b, double* x, bmg_stream_t stream) {
+  int rc = op_check(hp, level, 0);
+  if (rc) return rc;
+  if (!b || !x) return BMG_EINVAL;
+  Hierarchy* h = H(hp);
+  if (h->opt.smoother != BMG_SMOOTH_POINT) {
+    bmg::set_last_error("bmg_op_vcycle_from: point smoother hierarchies only");
+    return BMG_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto& L = h->d[level];
+  bmg::launch_pack<double>(b, L.b, L.nx, L.ny, L.pitch, s);
+  if (L.PR[bmg::PR_B]) bmg::launch_prescale_b<double>(L, s);
+  if (cudaMemsetAsync(L.x - bmg::base_shift<double>(), 0, h->geo64[level].elems * sizeof(double), s) !=
+      cudaSuccess)
+    return BMG_ECUDA;
+  bmg::enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s, level);
   bmg::launch_unpack<double>(L.x, x, L.nx, L.ny, L.pitch, s);
   return cudaGetLastError() == cudaSuccess ? BMG_OK : BMG_ECUDA;
 }

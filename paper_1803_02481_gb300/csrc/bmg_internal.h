@@ -466,7 +466,7 @@ void launch_pcg_p(Hierarchy* h, cudaStream_t s);
 // One V-cycle of the FP64 (d) or FP32 (f) hierarchy (bmg_api.cu).
 template <typename T>
 void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* dlev, int thr,
-                    cudaStream_t s);
+                    cudaStream_t s, int top = -1);
 
 void launch_assemble_backward(const double* k, const double* u, const double* lam,
                               double* g, int nx, int ny, cudaStream_t s);
