@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include "bmg_coarse.cuh"
+
 namespace bmg {
 
 CostParams& cost_params() {
@@ -20,8 +22,10 @@ CostParams& cost_params() {
 namespace {
 
 struct LevelCost {
-  int launches;          // kernel launches (grid mode) == phases (block mode)
-  double bytes;          // bytes moved per V-cycle
+  int launches;          // kernel launches (grid mode) == phases (persistent mode)
+  double bytes;          // bytes moved per V-cycle by the full-grid kernels
+  double bytes_resident; // the same inside the persistent kernel, where a colour
+                         // phase touches only its own points' data
   double flops;          // flops per V-cycle
 };
 
@@ -41,17 +45,31 @@ LevelCost level_cost(const Hierarchy* h, int l) {
   c.launches = sweeps * nc + 3;
   // a colour launch streams every coefficient plane, b and x, writes 1/nc of x
   c.bytes = sweeps * nc * ((ncoef + 2) * w * n + w * n / nc);
+  // inside the persistent kernel a sweep reads each point's data once
+  // (neighbour values come from cache) and writes x once
+  c.bytes_resident = sweeps * ((ncoef + 2) * w * n + w * n);
   c.flops = sweeps * 2.0 * ns * n;
-  // residual
-  c.bytes += (ncoef + 3) * w * n;
-  c.flops += 2.0 * ns * n;
-  // restriction: r, 2 weights per fine point, b_c
-  c.bytes += w * n + 2 * w * n + w * n / 4;
-  c.flops += 2.0 * 2.25 * n;
-  // interpolation: x in and out, weights, x_c
-  c.bytes += 2 * w * n + 2 * w * n + w * n / 4;
-  c.flops += 2.0 * 2.25 * n;
+  // residual, restriction (r, 2 weights per fine point, b_c), interpolation
+  // (x in and out, weights, x_c)
+  const double rest = (ncoef + 3) * w * n + (w * n + 2 * w * n + w * n / 4) +
+                      (2 * w * n + 2 * w * n + w * n / 4);
+  c.bytes += rest;
+  c.bytes_resident += rest;
+  c.flops += 2.0 * ns * n + 2.0 * 2.25 * n + 2.0 * 2.25 * n;
   return c;
+}
+
+// Latency units of one level per V-cycle inside the persistent kernel run
+// by `threads` threads: every phase costs one calibrated phase per point a
+// thread updates in it (a thread's points are done one after another, each
+// waiting on its loads).
+double phase_units(const Hierarchy* h, int l, int threads) {
+  const Geom& g = h->geo64[l];
+  const double n = double(g.nx) * g.ny;
+  const int nc = l != h->L - 1 ? 4 : 2;
+  const int sweeps = h->opt.nu1 + h->opt.nu2;
+  auto units = [&](double pts) { return std::max(1.0, std::ceil(pts / threads)); };
+  return sweeps * nc * units(n / nc) + units(n) + units(n / 4) + units(n);
 }
 
 }  // namespace
@@ -72,8 +90,10 @@ double predict_vcycle_us(const Hierarchy* h, int thr, int ctas) {
     } else {
       // inside the persistent kernel: barrier latency + work at the rates of
       // `ctas` SMs
-      const double work = std::max(c.bytes / (ctas * p.cta_gbs * 1e3), c.flops / (ctas * fc * 1e3));
-      t += c.launches * sync + work;
+      const double work =
+          std::max(c.bytes_resident / (ctas * p.cta_gbs * 1e3), c.flops / (ctas * fc * 1e3));
+      const int threads = ctas > 1 ? ctas * kCoarseClusterThreads : 1024;
+      t += phase_units(h, l, threads) * sync + work;
     }
   }
   // the persistent kernel itself and the coarsest solve (n0^2 flops, as the
@@ -124,35 +144,17 @@ namespace {
 
 __global__ void k_empty() {}
 
-// Barrier-separated phases in one block, each touching global memory the way
-// the persistent kernel does.
-__global__ void __launch_bounds__(1024) k_phases(double* buf, int phases) {
-  double v = 0.0;
-  for (int p = 0; p < phases; ++p) {
-    v += buf[(threadIdx.x + p) & 1023];
-    __syncthreads();
-    if (threadIdx.x == 0) buf[p & 1023] = v;
-    __syncthreads();
-  }
-  if (v == -1.0) buf[0] = v;
+// Colour phases of the persistent kernels themselves, timed on a synthetic
+// 15 x 15 nine-point level (values all zero: the timing of a phase does not
+// depend on them): one thread block, or every block of a cluster.  At one
+// point per thread the arithmetic is negligible, so this is the latency of a
+// phase (loads, stores, barrier); the cost model adds the arithmetic.
+template <class Team>
+__global__ void __launch_bounds__(1024) k_phases_real(LevelV<double> L, int phases) {
+  for (int p = 0; p < phases; ++p) blk_colour<double, true, Team>(L, four_mask(p & 3));
 }
 
-// The same phases over every block of a thread-block cluster, separated by
-// the cluster barrier.
-__global__ void __launch_bounds__(kCoarseClusterThreads) k_phases_cluster(double* buf, int phases) {
-  double v = 0.0;
-  unsigned rank;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  for (int p = 0; p < phases; ++p) {
-    v += buf[(threadIdx.x + p + 64 * rank) & 1023];
-    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-    if (threadIdx.x == 0) buf[(p + 64 * rank) & 1023] = v;
-    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-  }
-  if (v == -1.0) buf[0] = v;
-}
-
-cudaError_t launch_phases_cluster(int ctas, cudaStream_t s, double* buf, int phases) {
+cudaError_t launch_phases_cluster(int ctas, cudaStream_t s, const LevelV<double>& L, int phases) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(ctas));
   cfg.blockDim = dim3(kCoarseClusterThreads);
@@ -164,7 +166,33 @@ cudaError_t launch_phases_cluster(int ctas, cudaStream_t s, double* buf, int pha
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_phases_cluster, buf, phases);
+  return cudaLaunchKernelEx(&cfg, k_phases_real<ClusterTeam>, L, phases);
+}
+
+// A 15 x 15 nine-point level carved from scratch memory (planes 256-byte
+// aligned, interior rows 128-byte aligned as in a hierarchy).
+LevelV<double> probe_level(double* scratch) {
+  const Geom g = make_geom<double>(15, 15);
+  LevelV<double> L{};
+  L.nx = g.nx;
+  L.ny = g.ny;
+  L.pitch = g.pitch;
+  size_t off = 0;
+  auto plane = [&]() {
+    off = (off + 31) & ~size_t(31);                    // 256 bytes
+    double* p = scratch + off + base_shift<double>();
+    off += g.elems;
+    return p;
+  };
+  L.C = plane();
+  L.iC = plane();
+  L.W = plane();
+  L.S = plane();
+  L.SW = plane();
+  L.NW = plane();
+  L.x = plane();
+  L.b = plane();
+  return L;
 }
 
 template <typename T>
@@ -215,22 +243,23 @@ int calibrate(cudaStream_t s, double* out) {
   for (int i = 0; i < nl; ++i) k_empty<<<1, 32, 0, s>>>();
   cudaEventRecord(e1, s);
   p.launch_us = 1e3 * time_ms(s, e0, e1) / nl;
-  // barrier phase inside one block
-  const int ph = 4000;
-  k_phases<<<1, 1024, 0, s>>>(buf, 10);
+  // one colour phase of the persistent kernel on a small nine-point level:
+  // in one block, and over the largest cluster the coarse kernel can use
+  const LevelV<double> probe = probe_level(buf);
+  const int ph = 2000;
+  k_phases_real<BlockTeam><<<1, 1024, 0, s>>>(probe, 8);
   cudaEventRecord(e0, s);
-  k_phases<<<1, 1024, 0, s>>>(buf, ph);
+  k_phases_real<BlockTeam><<<1, 1024, 0, s>>>(probe, ph);
   cudaEventRecord(e1, s);
-  p.sync_us = 1e3 * time_ms(s, e0, e1) / (2.0 * ph);
-  // cluster-barrier phase over the largest cluster the coarse kernel can use
+  p.sync_us = 1e3 * time_ms(s, e0, e1) / ph;
   const int cmax = max_cluster_ctas(false);
   if (cmax > 1) {
-    cudaFuncSetAttribute(k_phases_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    launch_phases_cluster(cmax, s, buf, 10);
+    cudaFuncSetAttribute(k_phases_real<ClusterTeam>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    launch_phases_cluster(cmax, s, probe, 8);
     cudaEventRecord(e0, s);
-    launch_phases_cluster(cmax, s, buf, ph);
+    launch_phases_cluster(cmax, s, probe, ph);
     cudaEventRecord(e1, s);
-    p.cluster_sync_us = 1e3 * time_ms(s, e0, e1) / (2.0 * ph);
+    p.cluster_sync_us = 1e3 * time_ms(s, e0, e1) / ph;
   }
   // FMA rates, whole GPU and one block
   const int iters = 1 << 14, tb = 256;
