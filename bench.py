@@ -286,6 +286,16 @@ def run_ours(args, rank, world, local_rank):
         tol = 1e-10
         workload = {"workload": f"log-normal k = exp(2 g), GRF correlation 32 cells, {n}x{n}, tol 1e-10",
                     "nx": n, "ny": n, "seed": 2, "cycle": "V(2,1)", "tol": tol}
+    elif args.workload == "poisson":
+        # the Poisson problem of the latency leg (k = 1, seed-0 RHS), to 1e-10
+        n = args.n if args.n is not None else 255
+        args.n = n
+        pr = inputs.constant_problem(n, seed=0)
+        k = torch.from_numpy(pr["k"]).to(dev)
+        b = torch.from_numpy(pr["b"]).to(dev)
+        tol = 1e-10
+        workload = {"workload": f"Poisson k = 1, {n}x{n}, seed-0 uniform[-1,1] RHS, FP64 V(2,1), tol 1e-10",
+                    "nx": n, "ny": n, "seed": 0, "cycle": "V(2,1)", "tol": tol}
     else:
         if args.n is None:
             args.n = N_SIDE
@@ -298,6 +308,8 @@ def run_ours(args, rank, world, local_rank):
                               max_cycles=args.max_cycles)
     if args.threshold is not None:
         opts.coarse_threshold = args.threshold
+    if args.coarse_ctas is not None:
+        opts.coarse_ctas = args.coarse_ctas
 
     state = {}
 
@@ -409,10 +421,13 @@ def run_ours(args, rank, world, local_rank):
     prescaled = bool(state.get("prescaled"))
     per_unit_b = 6 * word
     moved_b, per_unit_f = (7 * word, 8.0) if prescaled else (6 * word, 9.0)
+    # (under a profiler that serialises kernels the bracketing events can read
+    # zero; the rates are then not defined)
     sweep_ms = prof_ms / max(1, nprof)
-    gbs = per_unit_b * n_fine / (sweep_ms / 1e3) / 1e9
-    gbs_moved = moved_b * n_fine / (sweep_ms / 1e3) / 1e9
-    gfl = per_unit_f * n_fine / (sweep_ms / 1e3) / 1e9
+    rate_s = sweep_ms / 1e3 if sweep_ms > 0 else float("inf")
+    gbs = per_unit_b * n_fine / rate_s / 1e9
+    gbs_moved = moved_b * n_fine / rate_s / 1e9
+    gfl = per_unit_f * n_fine / rate_s / 1e9
     f_hbm = gbs / peaks["hbm_gbs"]
     alu_peak, alu_src = alu_peak_gflops(torch, dev, args.precision, clk.summary())
     f_alu = gfl / alu_peak
@@ -1044,9 +1059,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--workload", default="blocks", choices=["blocks", "lognormal"],
-                    help="blocks: the 4095^2 block field (default); lognormal: the 8191^2 log-normal field")
+    ap.add_argument("--workload", default="blocks", choices=["blocks", "lognormal", "poisson"],
+                    help="blocks: the 4095^2 block field (default); lognormal: the 8191^2 log-normal field; "
+                         "poisson: the 255^2 Poisson problem")
     ap.add_argument("--threshold", type=int, default=None)
+    ap.add_argument("--coarse-ctas", type=int, default=None,
+                    help="blocks of the persistent coarse kernel (1, or a cluster size); default: the cost model")
     ap.add_argument("--max-cycles", type=int, default=4000)
     ap.add_argument("--n", type=int, default=None,
                     help="grid side (default 4095 block field, 8191 log-normal field)")
