@@ -329,6 +329,8 @@ class CudaPart:
         self._h = h
         self._keep = None
 
+    _h = None
+
     def _stream(self):
         return ctypes.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream)
 
@@ -336,6 +338,12 @@ class CudaPart:
         if self._h:
             self._lib().bmg_dd_part_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
     def relax_colour(self, k, c):
         self._check(self._lib().bmg_dd_relax_colour(self._h, k, c, self._stream()), "bmg_dd_relax_colour")
