@@ -63,6 +63,19 @@ def test_dd_on_a_rectangular_grid_with_the_minimum_local_size_rule():
     assert np.array_equal(x, xg.cpu().numpy())
 
 
+def test_dd_at_four_million_unknowns_reproduces_the_single_domain_solve():
+    """1023 x 2047 block field (4.2 M unknowns, 11 levels) on 2 x 2 blocks
+    with the gather level chosen by the minimum-local-size rule: the same
+    bits as the single-domain solve."""
+    pr = inputs.block_problem(seed=8, block=32, lo=-2, hi=2, nx=1023, ny=2047)
+    h = bm.setup(dev(pr["k"]))
+    xg, ig = h.solve(dev(pr["b"]), tol=1e-10)
+    h.destroy()
+    x, infos, gather = _dd_solve(pr, 2, 2, None)
+    assert infos[0].cycles == ig.cycles, (infos[0].cycles, ig.cycles)
+    assert np.array_equal(x, xg.cpu().numpy())
+
+
 def test_vcycle_from_the_top_is_one_solve_cycle():
     """bmg_op_vcycle_from at the finest level from x = 0 is the first cycle
     of bmg_solve."""
