@@ -110,28 +110,32 @@ class CpuPart:
         nxc, nyc = self.dims[k - 1]
         r, P = self.vec[k][VR], self.p[k]
         bc, xc = self.vec[k - 1][VB], self.vec[k - 1][VX]
-        for Jc in range(1, nyc + 1):
-            for Ic in range(1, nxc + 1):
-                f, g = 2 * Jc, 2 * Ic
-                acc = r[f, g]
-                acc += P["XE"][Jc, Ic - 1] * r[f, g - 1] + P["XW"][Jc, Ic] * r[f, g + 1]
-                acc += P["YN"][Jc - 1, Ic] * r[f - 1, g] + P["YS"][Jc, Ic] * r[f + 1, g]
-                acc += P["CNE"][Jc - 1, Ic - 1] * r[f - 1, g - 1] + P["CNW"][Jc - 1, Ic] * r[f - 1, g + 1]
-                acc += P["CSE"][Jc, Ic - 1] * r[f + 1, g - 1] + P["CSW"][Jc, Ic] * r[f + 1, g + 1]
-                bc[Jc, Ic] = acc
+        Jc, Ic = np.meshgrid(np.arange(1, nyc + 1), np.arange(1, nxc + 1), indexing="ij")
+        f, g = 2 * Jc, 2 * Ic
+        acc = r[f, g].copy()
+        acc += P["XE"][Jc, Ic - 1] * r[f, g - 1] + P["XW"][Jc, Ic] * r[f, g + 1]
+        acc += P["YN"][Jc - 1, Ic] * r[f - 1, g] + P["YS"][Jc, Ic] * r[f + 1, g]
+        acc += P["CNE"][Jc - 1, Ic - 1] * r[f - 1, g - 1] + P["CNW"][Jc - 1, Ic] * r[f - 1, g + 1]
+        acc += P["CSE"][Jc, Ic - 1] * r[f + 1, g - 1] + P["CSW"][Jc, Ic] * r[f + 1, g + 1]
+        bc[1:nyc + 1, 1:nxc + 1] = acc
         xc[1:nyc + 1, 1:nxc + 1] = 0.0
 
     def interp(self, k):
         nx, ny = self.dims[k]
         x, xc, P = self.vec[k][VX], self.vec[k - 1][VX], self.p[k]
-        for j in range(1, ny + 1):
-            for i in range(1, nx + 1):
-                I, J = i >> 1, j >> 1
-                if not (i & 1) and not (j & 1):
+        for pj in (0, 1):
+            for pi in (0, 1):
+                jj = np.arange(2 - pj, ny + 1, 2)        # pj = 0: even j, 1: odd j
+                ii = np.arange(2 - pi, nx + 1, 2)
+                if jj.size == 0 or ii.size == 0:
+                    continue
+                j, i = np.meshgrid(jj, ii, indexing="ij")
+                J, I = j >> 1, i >> 1
+                if not pi and not pj:
                     v = xc[J, I]
-                elif not (i & 1):
+                elif not pi:
                     v = P["YS"][J, I] * xc[J, I] + P["YN"][J, I] * xc[J + 1, I]
-                elif not (j & 1):
+                elif not pj:
                     v = P["XW"][J, I] * xc[J, I] + P["XE"][J, I] * xc[J, I + 1]
                 else:
                     v = (P["CSW"][J, I] * xc[J, I] + P["CSE"][J, I] * xc[J, I + 1]

@@ -142,3 +142,131 @@ def test_a_failed_rank_surfaces_instead_of_hanging():
 
     with pytest.raises(RuntimeError, match="rank 1 failed"):
         dd.run_threads(2, body)
+
+
+# ---------------------------------------------------------------------------
+# Multi-stage redistribution plans (Section 2.2, Algorithm 2; Section 4)
+# ---------------------------------------------------------------------------
+
+def _coarsen(r, m):
+    for _ in range(m):
+        r = dd.coarse_range(*r)
+    return r
+
+
+def _check_plan(plan):
+    """Blocks tile every level, start on the stage's alignment, and a coarse
+    task's block is the union of its processor block's blocks; every rank
+    runs a prefix of the stages; the coarse task runs on rank 0."""
+    for s, st in enumerate(plan.stages):
+        for k in range(st.nlev):
+            nx, ny = plan.shapes[st.lo + k]
+            for rng, n in ((st.xr[k], nx), (st.yr[k], ny)):
+                assert rng[0][0] == 1 and rng[-1][1] == n
+                assert all(b[0] == a[1] + 1 for a, b in zip(rng, rng[1:]))
+        for lo, _ in st.xr[-1] + st.yr[-1]:
+            assert (lo - 1) % 2 ** (st.nlev - 1) == 0
+        if s + 1 < plan.nstage:
+            nxt = plan.stages[s + 1]
+            for d, (mine, theirs) in enumerate(((st.xr[0], nxt.xr[-1]), (st.yr[0], nxt.yr[-1]))):
+                for g, members in enumerate(plan.grp[s][d]):
+                    assert (mine[members[0]][0], mine[members[-1]][1]) == theirs[g]
+    for r in range(plan.size):
+        assert [t[0] for t in plan.roles[r]] == list(range(len(plan.roles[r])))
+    assert 0 in plan.coarse_ranks()
+
+
+def test_plan_layouts_tile_nest_and_balance():
+    shapes = [(7, 3), (15, 7), (31, 15), (63, 31), (127, 63), (255, 127)]
+    for path, red in [([((4, 2), 5), ((2, 1), 3), ((1, 1), 1)], False),
+                      ([((4, 2), 5), ((2, 2), 4), ((2, 1), 2), ((1, 1), 0)], False),
+                      ([((3, 2), 5), ((2, 1), 3), ((1, 1), 2)], False),
+                      ([((4, 2), 5), ((2, 1), 3), ((1, 1), 1)], True),
+                      ([((4, 4), 5), ((2, 2), 3), ((1, 1), 2)], True)]:
+        plan = dd.Plan(shapes, path, red)
+        _check_plan(plan)
+        if red:
+            # every fine rank runs the coarse task of one copy
+            assert plan.coarse_ranks() == list(range(plan.size))
+        else:
+            assert plan.coarse_ranks() == [0]
+    # 3 ranks agglomerated into groups of 1 and 2: the coarse split follows the
+    # rank counts, so the finest blocks stay balanced (85 = 255 / 3 points each,
+    # within the coarse stage's alignment of 2 points on level 3, 8 on level 5)
+    plan = dd.Plan(shapes, [((3, 2), 5), ((2, 1), 3), ((1, 1), 2)])
+    widths = [hi - lo + 1 for lo, hi in plan.stages[0].xr[-1]]
+    assert max(widths) - min(widths) <= 8 and sum(widths) == 255
+    assert plan.grp[0][0] == [[0], [1, 2]]
+    with pytest.raises(ValueError):
+        dd.Plan(shapes, [((3, 2), 5), ((2, 1), 3), ((1, 1), 2)], redundant=True)
+    with pytest.raises(ValueError):
+        dd.Plan(shapes, [((4, 2), 5), ((4, 2), 3), ((1, 1), 2)])
+    with pytest.raises(ValueError):
+        dd.Plan(shapes, [((4, 2), 5), ((2, 1), 3)])
+
+
+def test_search_plan_on_the_minimum_local_size_rule():
+    shapes = [(3, 3), (7, 7), (15, 15), (31, 31), (63, 63), (127, 127), (255, 255), (511, 511)]
+    plan, res = dd.search_plan(shapes, (8, 8), min_local=256)
+    _check_plan(plan)
+    assert plan.path == res.path and plan.path[0] == ((8, 8), 7) and plan.path[-1][0] == (1, 1)
+
+
+def _solve_plan(comm, pr, P, path, redundant, cycles, min_local=64):
+    h = O.setup(pr["k"])
+    src = OracleSource(h)
+    shapes = [src.level_shape(l) for l in range(src.nlevels)]
+    plan = dd.make_plan(shapes, P[0], P[1], path=path, redundant=redundant, min_local=min_local)
+    parts = [CpuPart(p) for p in dd.plan_payloads(src, plan, comm.rank)]
+    coarse = src if comm.rank in plan.coarse_ranks() else None
+    solver = dd.DDSolver(comm, plan, parts, coarse=coarse)
+    (i0, i1), (j0, j1) = solver.block()
+    b = torch.from_numpy(np.ascontiguousarray(pr["b"][j0 - 1:j1, i0 - 1:i1]))
+    x, info = solver.solve(b, tol=1e-300, max_cycles=cycles)
+    return (i0, i1, j0, j1), x.numpy().copy(), info
+
+
+def _check_cycles(pr, results, cycles):
+    ref = O.solve(O.setup(pr["k"]), pr["b"], tol=1e-300, max_cycles=cycles)
+    x = np.zeros_like(pr["b"])
+    for (i0, i1, j0, j1), xb, info in results:
+        x[j0 - 1:j1, i0 - 1:i1] = xb
+        assert info.cycles == cycles
+        np.testing.assert_allclose(info.history, ref.history, rtol=1e-9, atol=1e-15)
+    assert np.abs(x - ref.x).max() <= 1e-12 * np.abs(ref.x).max()
+
+
+@pytest.mark.parametrize("P,path,red", [
+    ((4, 2), [(4, 2), (2, 1), (1, 1)], False),
+    ((4, 2), [(4, 2), (2, 1), (1, 1)], True),
+    ((3, 2), [(3, 2), (2, 1), (1, 1)], False),
+    ((4, 2), [((4, 2), 4), ((2, 2), 2), ((2, 1), 1), ((1, 1), 0)], False),
+    ((4, 4), "search", False),
+    ((4, 4), [(4, 4), (2, 2), (1, 1)], True),
+])
+def test_thread_ranks_on_a_redistribution_path_reproduce_the_single_domain_cycles(P, path, red):
+    pr = inputs.block_problem(seed=31, block=8, lo=-2, hi=2, nx=127, ny=63)
+    res = dd.run_threads(P[0] * P[1], lambda comm: _solve_plan(comm, pr, P, path, red, 3), timeout=120.0)
+    _check_cycles(pr, res, 3)
+
+
+def _gloo_plan_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.set_num_threads(1)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        pr = inputs.block_problem(seed=32, block=8, lo=-2, hi=2, nx=127, ny=63)
+        out[rank] = _solve_plan(dd.TorchComm(), pr, (2, 2), [(2, 2), (2, 1), (1, 1)], False, 3)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_ranks_on_a_two_stage_path():
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_gloo_plan_worker, args=(4, _free_port(), out), nprocs=4,
+                           start_method="spawn", join=True)
+        res = [out[r] for r in range(4)]
+    _check_cycles(inputs.block_problem(seed=32, block=8, lo=-2, hi=2, nx=127, ny=63), res, 3)
