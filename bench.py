@@ -380,6 +380,7 @@ def run_ours(args, rank, world, local_rank):
         extra["three_d"] = three_d_leg(bm, torch, dev, stream, load_peaks()[0])
         extra["c1_poisson255"] = c1_leg(bm, torch, dev, stream)
         extra["adjoint_gradient"] = adjoint_leg(bm, torch, dev, stream)
+        extra["redistribution"] = redistribution_leg()
         if pr is not None and args.n == N_SIDE:
             extra["gpu_on_reference_window"] = windows_leg(bm, torch, dev, stream, pr, REF_WINDOW, [None] * 5)
             extra["gpu_on_cpu_baseline_windows"] = windows_leg(bm, torch, dev, stream, pr, CPU_WINDOW,
@@ -920,6 +921,49 @@ def same_windows_ratio(line):
     line["vs_cpu_same_windows"] = out
 
 
+def redistribution_leg(max_brute_np=2 ** 14):
+    """The model-guided redistribution of Sections 3-4 on the paper's
+    configuration (host logic, no GPU): the V-cycle model's time of the nine
+    printed paths for 568 x 71 local problems on 64 x 32 processors with the
+    Blue Waters parameters, the A* choice, and the search cost of A* against
+    brute force as the processor count grows at fixed local size."""
+    from paper_1803_02481_gb300 import redist as R
+    paths = {0: [(64, 32), (1, 1)],
+             1: [(64, 32), (64, 16), (64, 8), (64, 4), (32, 2), (16, 1), (1, 1)],
+             2: [(64, 32), (64, 4), (8, 1), (4, 1), (1, 1)],
+             3: [(64, 32), (16, 2), (1, 1)],
+             4: [(64, 32), (64, 16), (2, 1), (1, 1)],
+             5: [(64, 32), (4, 1), (1, 1)],
+             6: [(64, 32), (64, 16), (4, 1), (1, 1)],
+             7: [(64, 32), (64, 16), (64, 8), (2, 1), (1, 1)],
+             8: [(64, 32), (2, 1), (1, 1)]}
+    sp = R.Space(R.halving_shapes((568 * 64, 71 * 32)), (64, 32), R.BLUE_WATERS, R.Cycle(), 1024)
+    model = {str(k): sp.path_cost(sp.states_of_grids(g)) * 1e3 for k, g in paths.items()}
+    best = R.search_astar(sp)
+    out = {"config": "568 x 71 local problems on 64 x 32 processors, Blue Waters alpha/beta/gamma, "
+                     "minimum local size 1024; path 2 completed by 1 x 1",
+           "model_ms_per_cycle_by_paper_path": model,
+           "cheapest_paper_path": min(model, key=model.get),
+           "path0_over_path1": model["0"] / model["1"],
+           "astar_path": [list(q) for q, _ in best.path], "astar_ms_per_cycle": best.cost * 1e3}
+    scaling = []
+    for e in range(1, 21):
+        P = (2 ** ((e + 1) // 2), 2 ** (e // 2))
+        sp = R.Space(R.halving_shapes((568 * P[0], 71 * P[1])), P, R.BLUE_WATERS, R.Cycle(), 1024)
+        row = {"n_p": P[0] * P[1], "grid": list(P)}
+        t0 = time.perf_counter()
+        a = R.search_astar(sp)
+        row["astar_ms"], row["astar_expanded"] = (time.perf_counter() - t0) * 1e3, a.expanded
+        if P[0] * P[1] <= max_brute_np:
+            t0 = time.perf_counter()
+            bf = R.search_brute_force(sp)
+            row["brute_ms"], row["brute_visited"] = (time.perf_counter() - t0) * 1e3, bf.expanded
+            row["same_cost"] = abs(bf.cost - a.cost) <= 1e-12 * a.cost
+        scaling.append(row)
+    out["search_weak_scaling"] = scaling
+    return out
+
+
 def c1_leg(bm, torch, dev, stream, reps=20):
     """The 255^2 Poisson problem (k = 1, seed-0 right-hand side), FP64 V(2,1)
     to 1e-10: its whole hierarchy fits in L2, so it is latency-bound.
@@ -1074,9 +1118,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--only", default=None,
                     choices=["line_smoother", "three_d", "paper_workload", "paper_workload_9088x568",
-                             "c1_poisson255", "adjoint_gradient", "lognormal"],
+                             "c1_poisson255", "adjoint_gradient", "lognormal", "redistribution"],
                     help="run one measurement leg alone and print its JSON (no headline line)")
     args = ap.parse_args()
+    if args.only == "redistribution":
+        print(json.dumps({"leg": "redistribution", **redistribution_leg()}))
+        return
     if args.only is not None:
         run_leg(args.only)
         return

@@ -27,11 +27,10 @@ def _dd_solve(pr, px, py, m, tol=1e-10):
 
     def body(comm):
         solver, _ = dd.cuda_setup(comm, (px, py, m), k if comm.rank == 0 else None)
-        lay = solver.layout
-        (i0, i1), (j0, j1) = lay.block(comm.rank, lay.nlev - 1)
+        (i0, i1), (j0, j1) = solver.block()
         x, info = solver.solve(dev(pr["b"][j0 - 1:j1, i0 - 1:i1]), tol=tol, max_cycles=300)
-        solver.part.destroy()
-        return (i0, i1, j0, j1), x.cpu().numpy(), info, lay.gather
+        solver.destroy()
+        return (i0, i1, j0, j1), x.cpu().numpy(), info, solver.plan.path[1][1]
 
     res = dd.run_threads(px * py, body, timeout=300.0)
     x = np.zeros_like(pr["b"])
