@@ -1079,6 +1079,7 @@ def run_leg(name):
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
+    bm.calibrate(stream)     # the level schedule's cost model, as in the full run
     if name == "line_smoother":
         out = line_smoother_leg(bm, torch, dev, stream, load_peaks()[0])
     elif name == "three_d":
