@@ -598,7 +598,9 @@ void enqueue_cycle(bmg3_hierarchy* h, cudaStream_t s) {
       if (seven) bmg::prof_end(BMG_PROF_FINE_SMOOTH, s);
     }
   };
+  bmg::NvtxRange cycle_range("vcycle3d", L - 1);
   for (int l = L - 1; l >= 1; --l) {
+    bmg::NvtxRange r("restrict_leg", l);
     const Lev3& V = h->lv[l];
     sweep(l, h->opt.nu1, false);
     if (l == L - 1)
@@ -611,6 +613,7 @@ void enqueue_cycle(bmg3_hierarchy* h, cudaStream_t s) {
   k3_coarse_solve<<<1, 256, 0, s>>>(h->lv[0], h->chol, h->chol_idiag);
   count_launch();
   for (int l = 1; l < L; ++l) {
+    bmg::NvtxRange r("interp_leg", l);
     k3_interp<<<dim3(cdiv((h->lv[l].nx + 1) / 2, kT), h->lv[l].ny, h->lv[l].nz), kT, 0, s>>>(
         h->lv[l], h->lv[l - 1]);
     count_launch();

@@ -410,7 +410,9 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
     std::swap(V.x, V.x2);
   };
   prof_begin(BMG_PROF_CYCLE, s);
+  NvtxRange cycle_range("vcycle", top);
   for (int l = top; l >= thr; --l) {
+    NvtxRange r("restrict_leg", l);
     const bool nine = l != L - 1;
     if (nine) prof_begin(BMG_PROF_LEVELS, s);
     for (int k = 0; k < nu1; ++k) sweep(l, false);
@@ -422,8 +424,12 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
     }
     if (nine) prof_end(BMG_PROF_LEVELS, s);
   }
-  launch_coarse_cycle<T>(h, dlev, thr, s);
+  {
+    NvtxRange r("coarse_cycle", thr - 1);
+    launch_coarse_cycle<T>(h, dlev, thr, s);
+  }
   for (int l = thr; l <= top; ++l) {
+    NvtxRange r("interp_leg", l);
     const bool nine = l != L - 1;
     if (nine) prof_begin(BMG_PROF_LEVELS, s);
     if (interp_oop) {

@@ -353,6 +353,17 @@ struct Hierarchy {
 // class (bmg_profile.cu).
 void count_launch(int n = 1);
 bool prof_active();
+// Host-side NVTX range named after a V-cycle operation, with the level as
+// its payload, for profilers that record NVTX (ncu --nvtx, Nsight Systems).
+// On the stream-launched path it brackets the operation's launches; while a
+// graph is being captured it brackets the recording.
+struct NvtxRange {
+  NvtxRange(const char* op, int level);
+  ~NvtxRange();
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 void prof_begin(int which, cudaStream_t s);
 void prof_end(int which, cudaStream_t s);
 

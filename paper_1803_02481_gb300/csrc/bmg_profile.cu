@@ -2,6 +2,8 @@
 // and CUDA-event bracketing of one kernel class for live per-launch timing.
 #include "bmg_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -35,6 +37,19 @@ Prof& prof() {
 }  // namespace
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+NvtxRange::NvtxRange(const char* op, int level) {
+  nvtxEventAttributes_t a = {};
+  a.version = NVTX_VERSION;
+  a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+  a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+  a.message.ascii = op;
+  a.payloadType = NVTX_PAYLOAD_TYPE_INT32;
+  a.payload.iValue = level;
+  nvtxRangePushEx(&a);
+}
+
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 bool prof_active() { return prof().mask != 0; }
 
