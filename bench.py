@@ -690,6 +690,26 @@ def three_d_leg(bm, torch, dev, stream, peaks, n=255, block=16):
     out["fp64"] = {"value": n ** 3 / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms,
                    "setup_ms": sum(setups) / len(setups), "cycles": info.cycles,
                    "rel_resid": info.rel_resid, "levels": h.nlevels}
+    x64 = x.clone()
+    # FP32 V-cycles inside FP64 refinement on the same field, to the same tolerance
+    opts32 = bm.default_options(precision=bm.BMG_FP32_REFINE)
+    t32 = []
+    for rep in range(3):
+        x.zero_()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        h32 = bm.setup3(k, opts32, stream=stream)
+        _, i32 = h32.solve(b, x, tol=1e-10, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        h32.destroy()
+        if rep:
+            t32.append(ev0.elapsed_time(ev1))
+    m32 = sum(t32) / len(t32)
+    out["fp32_refine"] = {"value": n ** 3 / (m32 / 1e3), "unit": UNIT, "ms_per_solve": m32,
+                          "steps": i32.cycles, "rel_resid": i32.rel_resid,
+                          "max_rel_diff_vs_fp64": float((x - x64).abs().max() / x64.abs().max())}
+    out["speedup_fp32_refine_vs_fp64"] = ms / m32
     # the fine-level sweep alone (stream-launched solve with CUDA events)
     bm.profile_set(("fine_smooth",))
     x.zero_()

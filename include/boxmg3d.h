@@ -41,17 +41,25 @@ typedef struct bmg3_hierarchy bmg3_hierarchy; /* opaque, library-owned */
 
 /* Setup: assemble, build P_l and A_{l-1} level by level, factor the
  * coarsest operator.  k_dev: (nz, ny, nx) float64 cell coefficients > 0,
- * device.  opt: nu1, nu2 and max_cycles are used; precision must be BMG_FP64,
- * smoother BMG_SMOOTH_POINT, solver BMG_SOLVER_VCYCLE, and the anisotropy,
- * aspect and wall options their defaults (BMG_EINVAL otherwise); NULL for the
+ * device.  opt: nu1, nu2, max_cycles and precision are used (BMG_FP64, or
+ * BMG_FP32_REFINE: the hierarchy is built in FP64 and also kept as an FP32
+ * copy, operator, 1/C and interpolation rounded once, on which each solve
+ * step runs one FP32 V-cycle inside FP64 iterative refinement); smoother must
+ * be BMG_SMOOTH_POINT, solver BMG_SOLVER_VCYCLE, and the anisotropy, aspect
+ * and wall options their defaults (BMG_EINVAL otherwise); NULL for the
  * defaults.  BMG_EINVAL for bad sizes or non-positive / non-finite k. */
 int bmg3_setup(const double *k_dev, int nx, int ny, int nz, const bmg_options *opt,
                bmg_stream_t stream, bmg3_hierarchy **out);
 
 /* V-cycles from the initial guess in x_dev (overwritten) until the relative
  * residual is at most tol, on device arrays of (nz, ny, nx) float64.
- * info (may be NULL): cycles run, final relative residual, solve wall time.
- * BMG_ENOCONV after max_cycles, BMG_ENAN if the residual is not finite. */
+ * BMG_FP32_REFINE: each step computes r = b - A x in FP64, runs one FP32
+ * V-cycle on A e = r / s from e = 0 (s the previous residual norm, so the
+ * FP32 right-hand side is of order one) and updates x += s e in FP64; the
+ * stop test is the FP64 relative residual.
+ * info (may be NULL): cycles (refinement steps) run, final relative residual,
+ * solve wall time.  BMG_ENOCONV after max_cycles, BMG_ENAN if the residual is
+ * not finite. */
 int bmg3_solve(bmg3_hierarchy *h, const double *b_dev, double *x_dev, double tol, bmg_info *info,
                bmg_stream_t stream);
 

@@ -37,17 +37,24 @@ constexpr int kT = 128;   // threads along x
 constexpr int kNormBlocks = 4 * 152;
 constexpr int kNormThreads = 256;
 
-struct Lev3 {
+// A level's planes in FP64 (the hierarchy) or FP32 (the V-cycles of
+// FP32 refinement: the FP64 operator and interpolation rounded once).
+template <typename T>
+struct Lev3T {
   int nx, ny, nz, px, py;
-  double *C, *iC, *A[NA];
-  double *x, *b, *r;
-  double *P[NPW3];
+  T *C, *iC, *A[NA];
+  T *x, *b, *r;
+  T *P[NPW3];
 };
+using Lev3 = Lev3T<double>;
+using Lev3f = Lev3T<float>;
 
-__host__ __device__ __forceinline__ int off3(const Lev3& L, int di, int dj, int dk) {
+template <typename T>
+__host__ __device__ __forceinline__ int off3(const Lev3T<T>& L, int di, int dj, int dk) {
   return (dk * L.py + dj) * L.px + di;
 }
-__host__ __device__ __forceinline__ int idx3(const Lev3& L, int i, int j, int k) {
+template <typename T>
+__host__ __device__ __forceinline__ int idx3(const Lev3T<T>& L, int i, int j, int k) {
   return (k * L.py + j) * L.px + i;
 }
 __host__ __device__ __forceinline__ bool is_neg(int di, int dj, int dk) {
@@ -60,7 +67,8 @@ __host__ __device__ __forceinline__ int neg_index(int di, int dj, int dk) {
   return 12;
 }
 // a_d at point o (negated off-diagonal to o + d)
-__device__ __forceinline__ double coupling(const Lev3& L, int o, int di, int dj, int dk) {
+template <typename T>
+__device__ __forceinline__ T coupling(const Lev3T<T>& L, int o, int di, int dj, int dk) {
   if (is_neg(di, dj, dk)) return L.A[neg_index(di, dj, dk)][o];
   return L.A[neg_index(-di, -dj, -dk)][o + off3(L, di, dj, dk)];
 }
@@ -281,9 +289,9 @@ __global__ void k3_rap(Lev3 F, Lev3 Cc, int* err) {
 // Smoothing, residual, restriction, interpolation
 // ---------------------------------------------------------------------------
 
-template <bool SEVEN>
-__device__ __forceinline__ double nb_sum(const Lev3& L, const double* __restrict__ x, int o) {
-  double s = 0.0;
+template <bool SEVEN, typename T>
+__device__ __forceinline__ T nb_sum(const Lev3T<T>& L, const T* __restrict__ x, int o) {
+  T s = T(0);
   if (SEVEN) {
     const int sx = 1, sy = L.px, sz = L.py * L.px;
     s = fma(L.A[12][o], x[o - sx], s);
@@ -309,8 +317,8 @@ __device__ __forceinline__ double nb_sum(const Lev3& L, const double* __restrict
 
 // One colour of a sweep, in place.  SEVEN: red-black, colour (i + j + k)
 // parity (0-based); else colour 4 (k mod 2) + 2 (j mod 2) + (i mod 2).
-template <bool SEVEN>
-__global__ void k3_gs(Lev3 L, int colour) {
+template <bool SEVEN, typename T>
+__global__ void k3_gs(Lev3T<T> L, int colour) {
   const int ih = blockIdx.x * blockDim.x + threadIdx.x;
   int i0, j0, k0;
   if (SEVEN) {
@@ -334,7 +342,8 @@ __global__ void k3_gs(Lev3 L, int colour) {
 // 0 .. 2m - 1 (reverse), untouched by this launch.  One thread block per row:
 // the first colour of the row, a barrier, the second.  Each point update is
 // that of k3_gs<false>, so a sweep gives the same bits as eight launches.
-__global__ void __launch_bounds__(kT) k3_gs27_pair(Lev3 L, int m, int reverse) {
+template <typename T>
+__global__ void __launch_bounds__(kT) k3_gs27_pair(Lev3T<T> L, int m, int reverse) {
   const int j0 = 2 * blockIdx.x + (m & 1), k0 = 2 * blockIdx.y + (m >> 1);   // 0-based
   if (j0 >= L.ny || k0 >= L.nz) return;
   const int base = idx3(L, 0, j0 + 1, k0 + 1);
@@ -348,8 +357,8 @@ __global__ void __launch_bounds__(kT) k3_gs27_pair(Lev3 L, int m, int reverse) {
   }
 }
 
-template <bool SEVEN>
-__global__ void k3_residual(Lev3 L) {
+template <bool SEVEN, typename T>
+__global__ void k3_residual(Lev3T<T> L) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
   if (i > L.nx) return;
   const int o = idx3(L, i, j, k);
@@ -357,10 +366,11 @@ __global__ void k3_residual(Lev3 L) {
 }
 
 // b_c(I) = sum over the fine support of I of P(f, I) r(f); x_c = 0.
-__global__ void k3_restrict(Lev3 F, Lev3 Cc) {
+template <typename T>
+__global__ void k3_restrict(Lev3T<T> F, Lev3T<T> Cc) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x + 1, J = blockIdx.y + 1, K = blockIdx.z + 1;
   if (I > Cc.nx) return;
-  double s = 0.0;
+  T s = T(0);
   for (int ez = -1; ez <= 1; ++ez)
     for (int ey = -1; ey <= 1; ++ey)
       for (int ex = -1; ex <= 1; ++ex) {
@@ -371,16 +381,17 @@ __global__ void k3_restrict(Lev3 F, Lev3 Cc) {
       }
   const int oc = idx3(Cc, I, J, K);
   Cc.b[oc] = s;
-  Cc.x[oc] = 0.0;
+  Cc.x[oc] = T(0);
 }
 
 // x(f) += sum over f's parents of P(f, I) x_c(I).  A point has 1, 2, 4 or 8
 // parents by the parities of i, j, k; each thread takes one point of each
 // parity of i in turn (j and k are fixed per block), so the lanes of a warp
 // always follow the same parents.
-__device__ __forceinline__ void interp_point(const Lev3& F, const Lev3& Cc, int i, int j, int k) {
+template <typename T>
+__device__ __forceinline__ void interp_point(const Lev3T<T>& F, const Lev3T<T>& Cc, int i, int j, int k) {
   const int o = idx3(F, i, j, k);
-  double s = 0.0;
+  T s = T(0);
   for (int m = 0; m < NPW3; ++m) {
     const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
     if ((cx && !(i & 1)) || (cy && !(j & 1)) || (cz && !(k & 1))) continue;
@@ -392,7 +403,8 @@ __device__ __forceinline__ void interp_point(const Lev3& F, const Lev3& Cc, int 
   F.x[o] += s;
 }
 
-__global__ void k3_interp(Lev3 F, Lev3 Cc) {
+template <typename T>
+__global__ void k3_interp(Lev3T<T> F, Lev3T<T> Cc) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y + 1, k = blockIdx.z + 1;
   if (2 * t + 1 <= F.nx) interp_point(F, Cc, 2 * t + 1, j, k);
   if (2 * t + 2 <= F.nx) interp_point(F, Cc, 2 * t + 2, j, k);
@@ -431,6 +443,7 @@ __global__ void k3_norm(Lev3 L, int what, double* __restrict__ partials) {
 
 struct Scal3 {
   double bnorm2, rnorm2;
+  double scale;             // FP32 refinement: the norm the FP32 right-hand side was divided by
   int err;                  // E3_* bits set by setup kernels
 };
 
@@ -444,6 +457,67 @@ __global__ void k3_norm_final(const double* __restrict__ partials, int n, Scal3*
     else
       sc->bnorm2 = acc;
   }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 V-cycles inside FP64 refinement (the mixed-precision extension on the
+// 3D path): each step solves A e = r / ||r|| approximately with one FP32
+// V-cycle from e = 0 and updates x += ||r|| e in FP64; the residual and the
+// stop test stay FP64 on the finest level.
+// ---------------------------------------------------------------------------
+
+// r = b - A x on the FP64 finest level (the arithmetic of k3_norm, whose grid
+// and summation order it shares), r^2 summed into block partials, and the
+// FP32 finest level's right-hand side b32 = r / ||r_prev|| (the latest
+// residual norm, sc->rnorm2) with x32 = 0.
+__global__ void k3_refine_residual(Lev3 L, Lev3f Lf, const Scal3* __restrict__ sc,
+                                   double* __restrict__ partials) {
+  const double inv = sc->rnorm2 > 0.0 ? 1.0 / sqrt(sc->rnorm2) : 0.0;
+  double acc = 0.0;
+  const int n = L.nx * L.ny * L.nz;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int i = t % L.nx + 1, rest = t / L.nx, j = rest % L.ny + 1, k = rest / L.ny + 1;
+    const int o = idx3(L, i, j, k), of = idx3(Lf, i, j, k);
+    const double v = fma(-L.C[o], L.x[o], L.b[o]) + nb_sum<true>(L, L.x, o);
+    Lf.b[of] = float(v * inv);
+    Lf.x[of] = 0.0f;
+    acc = fma(v, v, acc);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// The new residual norm; the previous one becomes the scale the right-hand
+// side just cast was divided by.
+__global__ void k3_refine_norm_final(const double* __restrict__ partials, int n, Scal3* sc) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    sc->scale = sqrt(sc->rnorm2);
+    sc->rnorm2 = acc;
+  }
+}
+
+// x += scale * e on the finest level.
+__global__ void k3_refine_update(Lev3 L, Lev3f Lf, const Scal3* __restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
+  if (i > L.nx) return;
+  const int o = idx3(L, i, j, k);
+  L.x[o] = fma(sc->scale, double(Lf.x[idx3(Lf, i, j, k)]), L.x[o]);
+}
+
+// The FP32 copy of a level: operator, 1/C and interpolation rounded once
+// from FP64, every plane whole (ring included).
+__global__ void k3_downcast(Lev3 V, Lev3f F, int with_p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i > V.nx + 1) return;
+  const int o = idx3(V, i, j, k), of = idx3(F, i, j, k);
+  F.C[of] = float(V.C[o]);
+  F.iC[of] = float(V.iC[o]);
+  for (int m = 0; m < NA; ++m) F.A[m][of] = float(V.A[m][o]);
+  if (with_p)
+    for (int m = 0; m < NPW3; ++m) F.P[m][of] = float(V.P[m][o]);
 }
 
 // ---------------------------------------------------------------------------
@@ -491,12 +565,13 @@ __global__ void k3_coarse_factor(Lev3 L0, double* __restrict__ lo, double* __res
   }
 }
 
-__global__ void k3_coarse_solve(Lev3 L0, const double* __restrict__ lo,
+template <typename T>
+__global__ void k3_coarse_solve(Lev3T<T> L0, const double* __restrict__ lo,
                                 const double* __restrict__ idiag) {
   __shared__ double v[BMG_MAX_COARSEST];
   const int nx = L0.nx, ny = L0.ny, n = nx * ny * L0.nz;
   for (int r = threadIdx.x; r < n; r += blockDim.x)
-    v[r] = L0.b[idx3(L0, r % nx + 1, (r / nx) % ny + 1, r / (nx * ny) + 1)];
+    v[r] = double(L0.b[idx3(L0, r % nx + 1, (r / nx) % ny + 1, r / (nx * ny) + 1)]);
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     const double y = v[j] * idiag[j];
@@ -513,7 +588,7 @@ __global__ void k3_coarse_solve(Lev3 L0, const double* __restrict__ lo,
     __syncthreads();
   }
   for (int r = threadIdx.x; r < n; r += blockDim.x)
-    L0.x[idx3(L0, r % nx + 1, (r / nx) % ny + 1, r / (nx * ny) + 1)] = v[r];
+    L0.x[idx3(L0, r % nx + 1, (r / nx) % ny + 1, r / (nx * ny) + 1)] = T(v[r]);
 }
 
 // dense (nz, ny, nx) <-> plane interior
@@ -529,7 +604,8 @@ __global__ void k3_unpack(const double* __restrict__ src, double* __restrict__ d
 }
 
 inline int cdiv(long a, long b) { return int((a + b - 1) / b); }
-inline dim3 grid_pts(const Lev3& L) { return dim3(cdiv(L.nx, kT), L.ny, L.nz); }
+template <typename T>
+inline dim3 grid_pts(const Lev3T<T>& L) { return dim3(cdiv(L.nx, kT), L.ny, L.nz); }
 
 }  // namespace bmg3
 
@@ -539,6 +615,8 @@ struct bmg3_hierarchy {
   int L = 0;
   bmg_options opt{};
   std::vector<Lev3> lv;           // lv[0] coarsest ... lv[L-1] finest
+  std::vector<Lev3f> lv32;        // FP32 copies (BMG_FP32_REFINE), else empty
+  bool refine = false;            // FP32 V-cycles inside FP64 refinement
   void* arena = nullptr;
   double *chol = nullptr, *chol_idiag = nullptr, *partials = nullptr;
   Scal3* sc = nullptr;
@@ -570,10 +648,13 @@ void free3(bmg3_hierarchy* h) {
 }
 
 // One V(nu1, nu2) cycle (Algorithm 1), then ||b - A x||^2 of the finest level.
-void enqueue_cycle(bmg3_hierarchy* h, cudaStream_t s) {
+// One V(nu1, nu2) cycle (Algorithm 1) on the levels `lv` (FP64, or the FP32
+// copies of FP32 refinement).
+template <typename T>
+void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t s) {
   const int L = h->L;
   auto sweep = [&](int l, int nu, bool reverse) {
-    const Lev3& V = h->lv[l];
+    const Lev3T<T>& V = lv[l];
     const bool seven = l == L - 1;
     const int nc = seven ? 2 : 8;
     for (int it = 0; it < nu; ++it) {
@@ -601,28 +682,53 @@ void enqueue_cycle(bmg3_hierarchy* h, cudaStream_t s) {
   bmg::NvtxRange cycle_range("vcycle3d", L - 1);
   for (int l = L - 1; l >= 1; --l) {
     bmg::NvtxRange r("restrict_leg", l);
-    const Lev3& V = h->lv[l];
+    const Lev3T<T>& V = lv[l];
     sweep(l, h->opt.nu1, false);
     if (l == L - 1)
       k3_residual<true><<<grid_pts(V), kT, 0, s>>>(V);
     else
       k3_residual<false><<<grid_pts(V), kT, 0, s>>>(V);
-    k3_restrict<<<grid_pts(h->lv[l - 1]), kT, 0, s>>>(V, h->lv[l - 1]);
+    k3_restrict<<<grid_pts(lv[l - 1]), kT, 0, s>>>(V, lv[l - 1]);
     count_launch(2);
   }
-  k3_coarse_solve<<<1, 256, 0, s>>>(h->lv[0], h->chol, h->chol_idiag);
+  k3_coarse_solve<<<1, 256, 0, s>>>(lv[0], h->chol, h->chol_idiag);
   count_launch();
   for (int l = 1; l < L; ++l) {
     bmg::NvtxRange r("interp_leg", l);
-    k3_interp<<<dim3(cdiv((h->lv[l].nx + 1) / 2, kT), h->lv[l].ny, h->lv[l].nz), kT, 0, s>>>(
-        h->lv[l], h->lv[l - 1]);
+    k3_interp<<<dim3(cdiv((lv[l].nx + 1) / 2, kT), lv[l].ny, lv[l].nz), kT, 0, s>>>(lv[l], lv[l - 1]);
     count_launch();
     sweep(l, h->opt.nu2, true);
   }
-  k3_norm<<<kNormBlocks, kNormThreads, 0, s>>>(h->lv[L - 1], 1, h->partials);
-  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
-  cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
+}
+
+// FP32 refinement: the residual of the current x as the next FP32
+// right-hand side, and its norm (the stop test).
+void enqueue_refine_residual(bmg3_hierarchy* h, cudaStream_t s) {
+  k3_refine_residual<<<kNormBlocks, kNormThreads, 0, s>>>(h->lv[h->L - 1], h->lv32[h->L - 1], h->sc,
+                                                         h->partials);
+  k3_refine_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc);
   count_launch(2);
+}
+
+// One step of the solve: a V-cycle and the stop test's residual norm, copied
+// to the host.  FP64: the cycle on x, then ||b - A x||^2.  FP32 refinement:
+// the FP32 cycle on the FP32 right-hand side, x += scale e, then the next
+// right-hand side and ||b - A x||^2.
+void enqueue_step(bmg3_hierarchy* h, cudaStream_t s) {
+  const int L = h->L;
+  if (h->refine) {
+    enqueue_vcycle3<float>(h, h->lv32, s);
+    const Lev3& F = h->lv[L - 1];
+    k3_refine_update<<<grid_pts(F), kT, 0, s>>>(F, h->lv32[L - 1], h->sc);
+    count_launch();
+    enqueue_refine_residual(h, s);
+  } else {
+    enqueue_vcycle3<double>(h, h->lv, s);
+    k3_norm<<<kNormBlocks, kNormThreads, 0, s>>>(h->lv[L - 1], 1, h->partials);
+    k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+    count_launch(2);
+  }
+  cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
 }
 
 int check_err(bmg3_hierarchy* h, cudaStream_t s) {
@@ -658,11 +764,11 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
   bmg_default_options(&opt);
   if (opt_in) opt = *opt_in;
   if (opt.nu1 < 0 || opt.nu2 < 0 || opt.nu1 + opt.nu2 < 1 || opt.max_cycles < 0 ||
-      opt.precision != BMG_FP64 || opt.smoother != BMG_SMOOTH_POINT ||
+      (opt.precision != BMG_FP64 && opt.precision != BMG_FP32_REFINE) || opt.smoother != BMG_SMOOTH_POINT ||
       opt.solver != BMG_SOLVER_VCYCLE || opt.interp_residual_term || opt.aniso_r != 1.0 ||
       opt.cell_aspect != 1.0 || opt.bc_beta[0] >= 0.0 || opt.bc_beta[1] >= 0.0 ||
       opt.bc_beta[2] >= 0.0 || opt.bc_beta[3] >= 0.0 || opt.log_coefficients) {
-    set_last_error("3D setup: options other than nu1, nu2 and max_cycles must be the defaults");
+    set_last_error("3D setup: options other than nu1, nu2, max_cycles and precision must be the defaults");
     return BMG_EINVAL;
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -707,6 +813,23 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
     const int nplanes = 2 + NA + 3 + (l >= 1 ? NPW3 : 0);
     for (int p = 0; p < nplanes; ++p) offs.push_back(reserve(pb));
   }
+  h->refine = opt.precision == BMG_FP32_REFINE;
+  std::vector<size_t> offs32;
+  if (h->refine) {
+    h->lv32.assign(L, Lev3f{});
+    for (int l = 0; l < L; ++l) {
+      Lev3f& W = h->lv32[l];
+      const Lev3& V = h->lv[l];
+      W.nx = V.nx;
+      W.ny = V.ny;
+      W.nz = V.nz;
+      W.px = (V.nx + 2 + 31) / 32 * 32;
+      W.py = V.ny + 2;
+      const size_t pb = size_t(W.nz + 2) * W.py * W.px * sizeof(float);
+      const int nplanes = 2 + NA + 3 + (l >= 1 ? NPW3 : 0);
+      for (int p = 0; p < nplanes; ++p) offs32.push_back(reserve(pb));
+    }
+  }
   const size_t o_chol = reserve(sizeof(double) * size_t(h->n0) * h->n0);
   const size_t o_idiag = reserve(sizeof(double) * h->n0);
   const size_t o_part = reserve(sizeof(double) * kNormBlocks);
@@ -733,6 +856,18 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
     V.r = next();
     for (int m = 0; m < NPW3; ++m) V.P[m] = l >= 1 ? next() : nullptr;
   }
+  size_t qi = 0;
+  for (int l = 0; l < int(h->lv32.size()); ++l) {
+    Lev3f& W = h->lv32[l];
+    auto next = [&]() { return reinterpret_cast<float*>(base + offs32[qi++]); };
+    W.C = next();
+    W.iC = next();
+    for (int m = 0; m < NA; ++m) W.A[m] = next();
+    W.x = next();
+    W.b = next();
+    W.r = next();
+    for (int m = 0; m < NPW3; ++m) W.P[m] = l >= 1 ? next() : nullptr;
+  }
   h->chol = reinterpret_cast<double*>(base + o_chol);
   h->chol_idiag = reinterpret_cast<double*>(base + o_idiag);
   h->partials = reinterpret_cast<double*>(base + o_part);
@@ -756,6 +891,11 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
   }
   k3_coarse_factor<<<1, 512, 0, s>>>(h->lv[0], h->chol, h->chol_idiag, h->err);
   count_launch();
+  for (int l = 0; l < int(h->lv32.size()); ++l) {
+    const Lev3& V = h->lv[l];
+    k3_downcast<<<dim3(cdiv(V.nx + 2, kT), V.ny + 2, V.nz + 2), kT, 0, s>>>(V, h->lv32[l], l >= 1 ? 1 : 0);
+    count_launch();
+  }
   if (cudaGetLastError() != cudaSuccess) {
     free3(h);
     return BMG_ECUDA;
@@ -801,7 +941,7 @@ int bmg3_solve(bmg3_hierarchy* h, const double* b, double* x, double tol, bmg_in
       cudaStream_t cs;
       if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return BMG_ECUDA;
       bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-      if (ok) enqueue_cycle(h, cs);
+      if (ok) enqueue_step(h, cs);
       ok = cudaStreamEndCapture(cs, &h->graph) == cudaSuccess && ok;
       ok = ok && cudaGraphInstantiate(&h->gexec, h->graph, 0) == cudaSuccess;
       cudaStreamDestroy(cs);
@@ -810,11 +950,13 @@ int bmg3_solve(bmg3_hierarchy* h, const double* b, double* x, double tol, bmg_in
         return BMG_ECUDA;
       }
     }
+    // FP32 refinement: the first right-hand side is the initial residual
+    if (h->refine && rel > tol && h->opt.max_cycles > 0) enqueue_refine_residual(h, s);
     while (rel > tol && cycles < h->opt.max_cycles) {
       if (use_graph) {
         if (cudaGraphLaunch(h->gexec, s) != cudaSuccess) return BMG_ECUDA;
       } else {
-        enqueue_cycle(h, s);
+        enqueue_step(h, s);
       }
       if (cudaStreamSynchronize(s) != cudaSuccess) return BMG_ECUDA;
       ++cycles;

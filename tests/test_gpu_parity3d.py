@@ -152,6 +152,26 @@ def test_3d_solve_matches_oracle(name):
     assert rel <= 1.0000001e-10
 
 
+@pytest.mark.parametrize("name", ["blocks15", "blocks31_c4", "poisson31", "general45x20x70",
+                                  "general12x9x7", "tiny4", "single3"])
+def test_3d_fp32_refinement_reaches_fp64_tolerance(name):
+    """FP32 V-cycles inside FP64 refinement: the iterate meets the FP64 stop
+    test against the oracle's operator, and its error against the FP64
+    oracle solution is what a 1e-10 relative residual allows."""
+    k, b = case(name)
+    ro = O3.solve(oracle_h(name), b, tol=1e-10)
+    hg = bm.setup3(dev(k), bm.default_options(precision=bm.BMG_FP32_REFINE))
+    x, info = hg.solve(dev(b), tol=1e-10)
+    hg.destroy()
+    xg = x.cpu().numpy()
+    a = oracle_h(name).levels[-1].a
+    rel = np.linalg.norm(b.ravel() - a @ xg.ravel()) / np.linalg.norm(b)
+    assert rel <= 1.0000001e-10 and info.rel_resid <= 1e-10
+    assert np.abs(xg - ro.x).max() <= 1e-7 * np.abs(ro.x).max()
+    # a step contracts the residual about as much as an FP64 cycle
+    assert info.cycles <= 2 * ro.cycles + 4, (info.cycles, ro.cycles)
+
+
 def test_3d_zero_rhs_and_error_codes():
     k = np.ones((7, 7, 7))
     h = bm.setup3(dev(k))
@@ -162,7 +182,7 @@ def test_3d_zero_rhs_and_error_codes():
         with pytest.raises(bm.BoxMGError) as e:
             bm.setup3(dev(bad))
         assert e.value.code == bm.BMG_EINVAL
-    for opts in (dict(smoother=bm.BMG_SMOOTH_ALTLINE), dict(precision=bm.BMG_FP32_REFINE),
+    for opts in (dict(smoother=bm.BMG_SMOOTH_ALTLINE), dict(solver=bm.BMG_SOLVER_PCG),
                  dict(aniso_r=2.0)):
         with pytest.raises(bm.BoxMGError) as e:
             bm.setup3(dev(k), bm.default_options(**opts))
