@@ -221,11 +221,14 @@ __device__ __forceinline__ int support_slot(int ex, int ey, int ez) {
   return (ex == -1 ? 1 : 0) | ((ey == -1 ? 1 : 0) << 1) | ((ez == -1 ? 1 : 0) << 2);
 }
 
+// One thread per coarse point and stored entry (blockIdx.y = 14 (J - 1) + e):
+// a block's threads share the entry, so their loops run in step.
 __global__ void k3_rap(Lev3 F, Lev3 Cc, int* err) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x + 1, J = blockIdx.y + 1, K = blockIdx.z + 1;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x + 1, J = blockIdx.y / 14 + 1, K = blockIdx.z + 1;
   if (I > Cc.nx) return;
   const int oc = idx3(Cc, I, J, K);
-  for (int e = 0; e < 14; ++e) {
+  {
+    const int e = blockIdx.y % 14;
     int di = 0, dj = 0, dk = 0;
     if (e > 0) {
       const int m = e - 1;
@@ -886,7 +889,10 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
       k3_interp_weights<<<dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), kT, 0, s>>>(V, pass, h->err);
       count_launch();
     }
-    k3_rap<<<grid_pts(h->lv[l - 1]), kT, 0, s>>>(V, h->lv[l - 1], h->err);
+    {
+      const Lev3& Cc = h->lv[l - 1];
+      k3_rap<<<dim3(cdiv(Cc.nx, kT), 14 * Cc.ny, Cc.nz), kT, 0, s>>>(V, Cc, h->err);
+    }
     count_launch();
   }
   k3_coarse_factor<<<1, 512, 0, s>>>(h->lv[0], h->chol, h->chol_idiag, h->err);
