@@ -144,6 +144,68 @@ def test_a_failed_rank_surfaces_instead_of_hanging():
         dd.run_threads(2, body)
 
 
+class _DyingComm(dd.TorchComm):
+    """TorchComm whose rank `victim` dies (the process exits at once, as a
+    crashed rank would) at its `after`-th exchange."""
+
+    def __init__(self, victim, after):
+        super().__init__()
+        self.victim, self.after, self.n = victim, after, 0
+
+    def exchange(self, sends, recvs):
+        self.n += 1
+        if self.rank == self.victim and self.n == self.after:
+            os._exit(3)
+        return super().exchange(sends, recvs)
+
+
+def _gloo_dying_worker(rank, world, port, out):
+    import datetime
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.set_num_threads(1)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    pr = _problem(31, seed=25)
+    comm = _DyingComm(victim=1, after=40)
+    t0 = time.monotonic()
+    try:
+        _solve_ranks(comm, pr, 2, 1, 2)
+        out[rank] = ("finished", time.monotonic() - t0)
+    except Exception as e:  # noqa: BLE001 - the error is the result
+        out[rank] = ("error: " + type(e).__name__ + ": " + str(e)[:200], time.monotonic() - t0)
+    os._exit(0)
+
+
+def test_a_dead_gloo_rank_ends_the_others_solve_with_an_error():
+    """Failure detection across processes: rank 1 dies in the middle of a
+    V-cycle (between two halo exchanges); rank 0's next exchange with it
+    fails within the process group's timeout instead of blocking forever."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        pc = mp.start_processes(_gloo_dying_worker, args=(world, _free_port(), out), nprocs=world,
+                                start_method="spawn", join=False)
+        codes = {}
+        deadline = 120.0
+        import time
+        t0 = time.monotonic()
+        while len(codes) < world and time.monotonic() - t0 < deadline:
+            for r, proc in enumerate(pc.processes):
+                if r not in codes and not proc.is_alive():
+                    codes[r] = proc.exitcode
+            time.sleep(0.2)
+        for proc in pc.processes:
+            if proc.is_alive():
+                proc.kill()
+        res = dict(out)
+    assert codes == {0: 0, 1: 3}, codes
+    status, seconds = res[0]
+    assert status.startswith("error"), status
+    assert seconds < 60.0
+
+
 # ---------------------------------------------------------------------------
 # Multi-stage redistribution plans (Section 2.2, Algorithm 2; Section 4)
 # ---------------------------------------------------------------------------
