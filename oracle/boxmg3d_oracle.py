@@ -33,6 +33,9 @@ the 2D oracle's readings to three dimensions:
   (i-1 mod 2) forward for pre-smoothing and reversed for post-smoothing.
 * ``vcycle`` / ``solve`` -- Algorithm 1 with a dense Cholesky solve on the
   coarsest level; stop on ||b - Ax||_2 / ||b||_2 <= tol after each cycle.
+* ``vcycle_precond`` / ``pcg`` -- conjugate gradients on the finest operator
+  preconditioned by one symmetric V(nu, nu) cycle from zero (an extension;
+  the 2D oracle's textbook order).
 
 Sizes: any side >= 2; a side of n points coarsens to floor(n / 2); coarsening
 stops once the smallest side is at most 3.
@@ -352,3 +355,68 @@ def solve(h: Hierarchy3, b: np.ndarray, tol: float = 1e-10, max_cycles: int = 20
         if not np.isfinite(rel):
             break
     return SolveResult3(x.reshape(shape), cyc, rel, hist, bool(rel <= tol))
+
+
+# ---------------------------------------------------------------------------
+# Conjugate gradients preconditioned by one symmetric V-cycle
+# ---------------------------------------------------------------------------
+
+def vcycle_precond(h: Hierarchy3, r: np.ndarray) -> np.ndarray:
+    """z = M^{-1} r (flat vectors): one V(nu, nu) cycle of Algorithm 1 on
+    A z = r from z = 0.  With nu1 = nu2, the post-smoothing colours reversed,
+    R = P^T and an exact coarsest solve, M^{-1} is symmetric and positive
+    definite."""
+    z = np.zeros_like(r)
+    vcycle(h, z, r)
+    return z
+
+
+def pcg(h: Hierarchy3, b: np.ndarray, tol: float = 1e-10, max_iter: int = 500,
+        precond=None) -> SolveResult3:
+    """Preconditioned conjugate gradients on A x = b from x = 0, in the
+    textbook order:
+        r = b - A x, z = M^{-1} r, p = z, rz = r.z; then per iteration
+        q = A p, alpha = rz / p.q, x += alpha p, r -= alpha q, stop test,
+        z = M^{-1} r, rz' = r.z, beta = rz' / rz, p = z + beta p.
+    The stop test ||r||_2 / ||b||_2 <= tol uses the updated r, before the
+    first iteration and after each one.  ``precond``: None for one symmetric
+    V-cycle (nu1 == nu2 required), or "identity" for plain conjugate
+    gradients.  Returns x in b's shape; `cycles` counts iterations."""
+    if precond is None:
+        if h.nu1 != h.nu2:
+            raise ValueError("the V-cycle preconditioner needs nu1 == nu2")
+        precond = lambda r: vcycle_precond(h, r)  # noqa: E731
+    elif precond == "identity":
+        precond = lambda r: r.copy()  # noqa: E731
+    shape = np.shape(b)
+    bf = np.asarray(b, dtype=np.float64).ravel()
+    a = h.levels[-1].a
+    x = np.zeros_like(bf)
+    bn = float(np.linalg.norm(bf))
+    if bn == 0.0:
+        return SolveResult3(x.reshape(shape), 0, 0.0, [0.0], True)
+    r = bf - a @ x
+    rel = float(np.linalg.norm(r)) / bn
+    hist = [rel]
+    it = 0
+    if rel <= tol:
+        return SolveResult3(x.reshape(shape), 0, rel, hist, True)
+    z = precond(r)
+    p = z.copy()
+    rz = float(r @ z)
+    while it < max_iter:
+        q = a @ p
+        alpha = rz / float(p @ q)
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        rel = float(np.linalg.norm(r)) / bn
+        hist.append(rel)
+        if rel <= tol or not np.isfinite(rel):
+            break
+        z = precond(r)
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    return SolveResult3(x.reshape(shape), it, rel, hist, bool(rel <= tol))

@@ -218,3 +218,75 @@ def test_level_shapes_3d():
     assert O3.level_shapes(3, 40, 40) == [(3, 40, 40)]
     with pytest.raises(ValueError):
         O3.level_shapes(1, 8, 8)
+
+
+# ---------------------------------------------------------------------------
+# Conjugate gradients preconditioned by one symmetric V-cycle (3D)
+# ---------------------------------------------------------------------------
+
+def _one_d_operator(n):
+    """1-D cell-centred Dirichlet operator of unit coefficient: 2 on the
+    diagonal, 3 at both ends (a boundary face carries 2k), -1 off it."""
+    t = np.diag(np.full(n, 2.0)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)
+    t[0, 0] = t[-1, -1] = 3.0
+    return t
+
+
+def test_3d_cg_converges_in_as_many_steps_as_distinct_eigenvalues():
+    # k = 1: the 7-point operator is the Kronecker sum T (+) T (+) T with
+    # eigenvectors v_i (x) v_j (x) v_k and eigenvalues mu_i + mu_j + mu_k; CG
+    # from x = 0 on a right-hand side along three eigenvectors of three
+    # distinct eigenvalues is exact after three steps
+    n = 7
+    mu, v = np.linalg.eigh(_one_d_operator(n))
+    triples = [(0, 0, 0), (1, 3, 2), (6, 4, 5)]
+    assert len({round(mu[i] + mu[j] + mu[k], 9) for i, j, k in triples}) == 3
+    b = sum(c * np.einsum("k,j,i->kji", v[:, k], v[:, j], v[:, i])
+            for c, (i, j, k) in zip((1.0, -0.5, 2.0), triples))
+    h = O3.setup(np.ones((n, n, n)), nu1=1, nu2=1)
+    r = O3.pcg(h, b, tol=1e-13, max_iter=10, precond="identity")
+    assert r.cycles == 3
+    assert r.history[2] > 1e-3 and r.history[3] < 1e-12
+    a = h.levels[-1].a
+    assert np.abs(a @ r.x.ravel() - b.ravel()).max() < 1e-12 * np.abs(b).max()
+
+
+def test_3d_symmetric_vcycle_preconditioner_is_symmetric_positive_definite():
+    k = _block_k((15, 15, 15), 41, block=4, lo=-3, hi=3)
+    rng = np.random.default_rng(42)
+    u, w = rng.normal(size=15 ** 3), rng.normal(size=15 ** 3)
+    h = O3.setup(k, nu1=1, nu2=1)
+    mu, mw = O3.vcycle_precond(h, u), O3.vcycle_precond(h, w)
+    scale = np.linalg.norm(u) * np.linalg.norm(mw)
+    assert abs(mu @ w - u @ mw) <= 1e-13 * scale
+    assert mu @ u > 0 and mw @ w > 0
+    # V(2,1) is not symmetric: the same check fails by orders of magnitude
+    h21 = O3.setup(k, nu1=2, nu2=1)
+    z, z2 = np.zeros_like(u), np.zeros_like(w)
+    O3.vcycle(h21, z, u)
+    O3.vcycle(h21, z2, w)
+    assert abs(z @ w - u @ z2) > 1e-6 * np.linalg.norm(u) * np.linalg.norm(z2)
+
+
+@pytest.mark.parametrize("shape", [(7, 7, 7), (15, 12, 9)])
+def test_3d_pcg_converges_to_direct_solution(shape):
+    k = _block_k(shape, 43, block=3, lo=-3, hi=3)
+    b = np.random.default_rng(44).uniform(-1, 1, k.shape)
+    h = O3.setup(k, nu1=1, nu2=1)
+    r = O3.pcg(h, b, tol=1e-12)
+    a = h.levels[-1].a
+    xd = spla.spsolve(a.tocsc(), b.ravel())
+    assert r.converged
+    assert np.abs(r.x.ravel() - xd).max() <= 1e-9 * np.abs(xd).max()
+    # the recursively updated residual tracks the true one
+    assert np.linalg.norm(b.ravel() - a @ r.x.ravel()) / np.linalg.norm(b) <= 1e-11
+
+
+def test_3d_pcg_needs_fewer_iterations_than_vcycles_and_rejects_unsymmetric_cycle():
+    k = _block_k((15, 15, 15), 45, block=4, lo=-4, hi=4)
+    b = np.random.default_rng(46).uniform(-1, 1, k.shape)
+    rp = O3.pcg(O3.setup(k, nu1=1, nu2=1), b, tol=1e-10)
+    rv = O3.solve(O3.setup(k, nu1=1, nu2=1), b, tol=1e-10, max_cycles=2000)
+    assert rp.converged and rv.converged and rp.cycles < rv.cycles
+    with pytest.raises(ValueError):
+        O3.pcg(O3.setup(k, nu1=2, nu2=1), b)
