@@ -710,6 +710,27 @@ def three_d_leg(bm, torch, dev, stream, peaks, n=255, block=16):
                           "steps": i32.cycles, "rel_resid": i32.rel_resid,
                           "max_rel_diff_vs_fp64": float((x - x64).abs().max() / x64.abs().max())}
     out["speedup_fp32_refine_vs_fp64"] = ms / m32
+    # CG preconditioned by one symmetric V(1,1) cycle (FP64 cycle, and the
+    # cycle on the FP32 copies), the same field and tolerance
+    for tag, prec in (("pcg_fp64", bm.BMG_FP64), ("pcg_fp32_cycle", bm.BMG_FP32_REFINE)):
+        optp = bm.default_options(nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG, precision=prec)
+        tp = []
+        for rep in range(3):
+            x.zero_()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            hp = bm.setup3(k, optp, stream=stream)
+            _, ip = hp.solve(b, x, tol=1e-10, stream=stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            hp.destroy()
+            if rep:
+                tp.append(ev0.elapsed_time(ev1))
+        mp_ = sum(tp) / len(tp)
+        out[tag] = {"value": n ** 3 / (mp_ / 1e3), "unit": UNIT, "ms_per_solve": mp_,
+                    "iterations": ip.cycles, "rel_resid": ip.rel_resid,
+                    "max_rel_diff_vs_fp64_vcycles": float((x - x64).abs().max() / x64.abs().max()),
+                    "speedup_vs_fp64_vcycles": ms / mp_}
     # the fine-level sweep alone (stream-launched solve with CUDA events)
     bm.profile_set(("fine_smooth",))
     x.zero_()

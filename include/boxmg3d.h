@@ -44,8 +44,11 @@ typedef struct bmg3_hierarchy bmg3_hierarchy; /* opaque, library-owned */
  * device.  opt: nu1, nu2, max_cycles and precision are used (BMG_FP64, or
  * BMG_FP32_REFINE: the hierarchy is built in FP64 and also kept as an FP32
  * copy, operator, 1/C and interpolation rounded once, on which each solve
- * step runs one FP32 V-cycle inside FP64 iterative refinement); smoother must
- * be BMG_SMOOTH_POINT, solver BMG_SOLVER_VCYCLE, and the anisotropy, aspect
+ * step runs one FP32 V-cycle inside FP64 iterative refinement) and solver
+ * (BMG_SOLVER_VCYCLE, or BMG_SOLVER_PCG: conjugate gradients on the finest
+ * operator in FP64, preconditioned by one symmetric V(nu, nu) cycle from
+ * zero, which needs nu1 == nu2; with BMG_FP32_REFINE that cycle runs on the
+ * FP32 copies); smoother must be BMG_SMOOTH_POINT and the anisotropy, aspect
  * and wall options their defaults (BMG_EINVAL otherwise); NULL for the
  * defaults.  BMG_EINVAL for bad sizes or non-positive / non-finite k. */
 int bmg3_setup(const double *k_dev, int nx, int ny, int nz, const bmg_options *opt,
@@ -57,8 +60,10 @@ int bmg3_setup(const double *k_dev, int nx, int ny, int nz, const bmg_options *o
  * V-cycle on A e = r / s from e = 0 (s the previous residual norm, so the
  * FP32 right-hand side is of order one) and updates x += s e in FP64; the
  * stop test is the FP64 relative residual.
- * info (may be NULL): cycles (refinement steps) run, final relative residual,
- * solve wall time.  BMG_ENOCONV after max_cycles, BMG_ENAN if the residual is
+ * BMG_SOLVER_PCG: CG iterations in the oracle's textbook order; the stop test
+ * uses the recursively updated residual.
+ * info (may be NULL): cycles (refinement steps, or CG iterations) run, final
+ * relative residual, solve wall time.  BMG_ENOCONV after max_cycles, BMG_ENAN if the residual is
  * not finite. */
 int bmg3_solve(bmg3_hierarchy *h, const double *b_dev, double *x_dev, double tol, bmg_info *info,
                bmg_stream_t stream);

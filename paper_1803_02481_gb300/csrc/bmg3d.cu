@@ -447,6 +447,8 @@ __global__ void k3_norm(Lev3 L, int what, double* __restrict__ partials) {
 struct Scal3 {
   double bnorm2, rnorm2;
   double scale;             // FP32 refinement: the norm the FP32 right-hand side was divided by
+  double rz, alpha, beta;   // PCG scalars
+  double rnorm, rinv;       // sqrt(rnorm2) and its inverse (0 for a zero residual)
   int err;                  // E3_* bits set by setup kernels
 };
 
@@ -455,8 +457,11 @@ __global__ void k3_norm_final(const double* __restrict__ partials, int n, Scal3*
   for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
   acc = block_sum(acc);
   if (threadIdx.x == 0) {
-    if (what)
+    if (what) {
       sc->rnorm2 = acc;
+      sc->rnorm = sqrt(acc);
+      sc->rinv = acc > 0.0 ? 1.0 / sc->rnorm : 0.0;
+    }
     else
       sc->bnorm2 = acc;
   }
@@ -521,6 +526,116 @@ __global__ void k3_downcast(Lev3 V, Lev3f F, int with_p) {
   for (int m = 0; m < NA; ++m) F.A[m][of] = float(V.A[m][o]);
   if (with_p)
     for (int m = 0; m < NPW3; ++m) F.P[m][of] = float(V.P[m][o]);
+}
+
+// ---------------------------------------------------------------------------
+// Conjugate gradients on the finest operator preconditioned by one symmetric
+// V(nu, nu) cycle from zero (nu1 = nu2, post-smoothing colours reversed,
+// R = P^T, exact coarsest solve: a symmetric positive definite M), in the
+// textbook order of the oracle.  The finest level's b plane holds the
+// residual r (the V-cycle's right-hand side) and its x plane z = M^{-1} r;
+// the iterate X, the right-hand side B, the direction P and Q = A P are
+// planes of their own.  Every kernel visits the points in k3_norm's grid and
+// order, so the dot products are deterministic.
+// ---------------------------------------------------------------------------
+
+template <class Fn>
+__device__ __forceinline__ double pcg_points(const Lev3& F, Fn f) {
+  double acc = 0.0;
+  const int n = F.nx * F.ny * F.nz;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int i = t % F.nx + 1, rest = t / F.nx, j = rest % F.ny + 1, k = rest / F.ny + 1;
+    acc = f(idx3(F, i, j, k), acc);
+  }
+  return block_sum(acc);
+}
+
+// r = B - A X (in F.b), z = 0 (F.x), partials of r.r
+__global__ void k3_pcg_init(Lev3 F, const double* __restrict__ X, const double* __restrict__ B,
+                            double* __restrict__ partials) {
+  const double sum = pcg_points(F, [&](int o, double acc) {
+    const double r = fma(-F.C[o], X[o], B[o]) + nb_sum<true>(F, X, o);
+    F.b[o] = r;
+    F.x[o] = 0.0;
+    return fma(r, r, acc);
+  });
+  if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
+// Q = A P (the negated residual of P for a zero right-hand side), partials of P.Q
+__global__ void k3_pcg_ap(Lev3 F, const double* __restrict__ P, double* __restrict__ Q,
+                          double* __restrict__ partials) {
+  const double sum = pcg_points(F, [&](int o, double acc) {
+    const double q = -(fma(-F.C[o], P[o], 0.0) + nb_sum<true>(F, P, o));
+    Q[o] = q;
+    return fma(P[o], q, acc);
+  });
+  if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
+// X += alpha P, r -= alpha Q, z = 0, partials of r.r
+__global__ void k3_pcg_xr(Lev3 F, double* __restrict__ X, const double* __restrict__ P,
+                          const double* __restrict__ Q, const Scal3* __restrict__ sc,
+                          double* __restrict__ partials) {
+  const double a = sc->alpha;
+  const double sum = pcg_points(F, [&](int o, double acc) {
+    X[o] = fma(a, P[o], X[o]);
+    const double r = fma(-a, Q[o], F.b[o]);
+    F.b[o] = r;
+    F.x[o] = 0.0;
+    return fma(r, r, acc);
+  });
+  if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
+// partials of r.z
+__global__ void k3_pcg_rz(Lev3 F, double* __restrict__ partials) {
+  const double sum = pcg_points(F, [&](int o, double acc) { return fma(F.b[o], F.x[o], acc); });
+  if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
+// P = z + beta P
+__global__ void k3_pcg_p(Lev3 F, double* __restrict__ P, const Scal3* __restrict__ sc) {
+  const double beta = sc->beta;
+  pcg_points(F, [&](int o, double acc) {
+    P[o] = fma(beta, P[o], F.x[o]);
+    return acc;
+  });
+}
+
+// One block sums the partials; what 0: rz = sum, beta = 0 (first
+// direction); 1: alpha = rz / sum (sum = P.Q); 2: beta = sum / rz, rz = sum
+// (sum = r.z of the new residual).  A zero denominator gives 0.
+__global__ void k3_pcg_scalar(const double* __restrict__ partials, int n, Scal3* sc, int what) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
+  acc = block_sum(acc);
+  if (threadIdx.x != 0) return;
+  if (what == 0) {
+    sc->rz = acc;
+    sc->beta = 0.0;
+  } else if (what == 1) {
+    sc->alpha = acc != 0.0 ? sc->rz / acc : 0.0;
+  } else {
+    sc->beta = sc->rz != 0.0 ? acc / sc->rz : 0.0;
+    sc->rz = acc;
+  }
+}
+
+// FP32 preconditioner: the FP32 finest level's right-hand side r / s and
+// x32 = 0, s = ||r|| of the latest residual (sc->rnorm, sc->rinv, set once by
+// k3_norm_final); then z = s e.
+__global__ void k3_pcg_cast(Lev3 F, Lev3f Ff, const Scal3* __restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
+  if (i > F.nx) return;
+  const int of = idx3(Ff, i, j, k);
+  Ff.b[of] = float(F.b[idx3(F, i, j, k)] * sc->rinv);
+  Ff.x[of] = 0.0f;
+}
+__global__ void k3_pcg_uncast(Lev3 F, Lev3f Ff, const Scal3* __restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
+  if (i > F.nx) return;
+  F.x[idx3(F, i, j, k)] = sc->rnorm * double(Ff.x[idx3(Ff, i, j, k)]);
 }
 
 // ---------------------------------------------------------------------------
@@ -620,6 +735,10 @@ struct bmg3_hierarchy {
   std::vector<Lev3> lv;           // lv[0] coarsest ... lv[L-1] finest
   std::vector<Lev3f> lv32;        // FP32 copies (BMG_FP32_REFINE), else empty
   bool refine = false;            // FP32 V-cycles inside FP64 refinement
+  bool pcg = false;               // BMG_SOLVER_PCG: CG preconditioned by the V-cycle
+  double *pX = nullptr, *pB = nullptr, *pP = nullptr, *pQ = nullptr;   // PCG planes (finest layout)
+  cudaGraph_t pcg_graph[2] = {nullptr, nullptr};          // first iteration, later ones
+  cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};
   void* arena = nullptr;
   double *chol = nullptr, *chol_idiag = nullptr, *partials = nullptr;
   Scal3* sc = nullptr;
@@ -645,6 +764,10 @@ void free3(bmg3_hierarchy* h) {
   if (!h) return;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
+  for (int g = 0; g < 2; ++g) {
+    if (h->pcg_exec[g]) cudaGraphExecDestroy(h->pcg_exec[g]);
+    if (h->pcg_graph[g]) cudaGraphDestroy(h->pcg_graph[g]);
+  }
   if (h->arena) cudaFree(h->arena);
   if (h->sc_host) cudaFreeHost(h->sc_host);
   delete h;
@@ -734,6 +857,108 @@ void enqueue_step(bmg3_hierarchy* h, cudaStream_t s) {
   cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
 }
 
+// z = M^{-1} r: one V-cycle on the residual held in the finest level's b
+// plane, from z = 0 in its x plane; on the FP32 copies (BMG_FP32_REFINE)
+// with r / ||r|| cast down and z = ||r|| e cast back.
+void enqueue_precond(bmg3_hierarchy* h, cudaStream_t s) {
+  const int L = h->L;
+  if (h->refine) {
+    const Lev3& F = h->lv[L - 1];
+    k3_pcg_cast<<<grid_pts(F), kT, 0, s>>>(F, h->lv32[L - 1], h->sc);
+    enqueue_vcycle3<float>(h, h->lv32, s);
+    k3_pcg_uncast<<<grid_pts(F), kT, 0, s>>>(F, h->lv32[L - 1], h->sc);
+    count_launch(2);
+  } else {
+    enqueue_vcycle3<double>(h, h->lv, s);
+  }
+}
+
+// One PCG iteration after a failed stop test: z = M^{-1} r, r.z (the first
+// iteration takes p = z), p = z + beta p, q = A p, alpha, x += alpha p,
+// r -= alpha q, ||r||^2 for the stop test, copied to the host.
+void enqueue_pcg_iter(bmg3_hierarchy* h, bool first, cudaStream_t s) {
+  const Lev3& F = h->lv[h->L - 1];
+  enqueue_precond(h, s);
+  k3_pcg_rz<<<kNormBlocks, kNormThreads, 0, s>>>(F, h->partials);
+  k3_pcg_scalar<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, first ? 0 : 2);
+  k3_pcg_p<<<kNormBlocks, kNormThreads, 0, s>>>(F, h->pP, h->sc);
+  k3_pcg_ap<<<kNormBlocks, kNormThreads, 0, s>>>(F, h->pP, h->pQ, h->partials);
+  k3_pcg_scalar<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+  k3_pcg_xr<<<kNormBlocks, kNormThreads, 0, s>>>(F, h->pX, h->pP, h->pQ, h->sc, h->partials);
+  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+  count_launch(7);
+  cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
+}
+
+// Records fn(stream) as a graph (on a private stream) and instantiates it.
+template <class Fn>
+bool record_graph(cudaGraph_t* g, cudaGraphExec_t* e, Fn fn) {
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) fn(cs);
+  ok = cudaStreamEndCapture(cs, g) == cudaSuccess && ok;
+  ok = ok && cudaGraphInstantiate(e, *g, 0) == cudaSuccess;
+  cudaStreamDestroy(cs);
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
+// The PCG solve of bmg3_solve (BMG_SOLVER_PCG).
+int solve_pcg(bmg3_hierarchy* h, const double* b, double* x, double tol, cudaStream_t s, int* iters,
+              double* rel_out) {
+  const Lev3& F = h->lv[h->L - 1];
+  const dim3 g = dim3(cdiv(F.nx, kT), F.ny, F.nz);
+  k3_pack<<<g, kT, 0, s>>>(b, h->pB, F);
+  k3_pack<<<g, kT, 0, s>>>(b, F.b, F);
+  k3_pack<<<g, kT, 0, s>>>(x, h->pX, F);
+  k3_norm<<<kNormBlocks, kNormThreads, 0, s>>>(F, 0, h->partials);
+  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 0);
+  k3_pcg_init<<<kNormBlocks, kNormThreads, 0, s>>>(F, h->pX, h->pB, h->partials);
+  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+  count_launch(7);
+  if (cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return BMG_ECUDA;
+  const double bn2 = h->sc_host->bnorm2;
+  double rel = bn2 > 0.0 ? std::sqrt(h->sc_host->rnorm2 / bn2) : 0.0;
+  int it = 0, rc = BMG_OK;
+  if (bn2 == 0.0) {
+    cudaMemsetAsync(x, 0, sizeof(double) * size_t(F.nx) * F.ny * F.nz, s);
+    *iters = 0;
+    *rel_out = 0.0;
+    return cudaStreamSynchronize(s) == cudaSuccess ? BMG_OK : BMG_ECUDA;
+  }
+  const bool use_graph = !bmg::prof_active();
+  if (use_graph && !h->pcg_exec[0]) {
+    for (int k = 0; k < 2; ++k)
+      if (!record_graph(&h->pcg_graph[k], &h->pcg_exec[k],
+                        [&](cudaStream_t cs) { enqueue_pcg_iter(h, k == 0, cs); }))
+        return BMG_ECUDA;
+  }
+  while (rel > tol && it < h->opt.max_cycles) {
+    if (use_graph) {
+      if (cudaGraphLaunch(h->pcg_exec[it == 0 ? 0 : 1], s) != cudaSuccess) return BMG_ECUDA;
+    } else {
+      enqueue_pcg_iter(h, it == 0, s);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BMG_ECUDA;
+    ++it;
+    rel = std::sqrt(h->sc_host->rnorm2 / bn2);
+    if (!std::isfinite(rel)) {
+      rc = BMG_ENAN;
+      break;
+    }
+  }
+  if (!rc && rel > tol) rc = BMG_ENOCONV;
+  k3_unpack<<<g, kT, 0, s>>>(h->pX, x, F);
+  count_launch();
+  if (cudaStreamSynchronize(s) != cudaSuccess) return BMG_ECUDA;
+  *iters = it;
+  *rel_out = rel;
+  return rc;
+}
+
 int check_err(bmg3_hierarchy* h, cudaStream_t s) {
   if (cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -768,10 +993,12 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
   if (opt_in) opt = *opt_in;
   if (opt.nu1 < 0 || opt.nu2 < 0 || opt.nu1 + opt.nu2 < 1 || opt.max_cycles < 0 ||
       (opt.precision != BMG_FP64 && opt.precision != BMG_FP32_REFINE) || opt.smoother != BMG_SMOOTH_POINT ||
-      opt.solver != BMG_SOLVER_VCYCLE || opt.interp_residual_term || opt.aniso_r != 1.0 ||
+      (opt.solver != BMG_SOLVER_VCYCLE && !(opt.solver == BMG_SOLVER_PCG && opt.nu1 == opt.nu2)) ||
+      opt.interp_residual_term || opt.aniso_r != 1.0 ||
       opt.cell_aspect != 1.0 || opt.bc_beta[0] >= 0.0 || opt.bc_beta[1] >= 0.0 ||
       opt.bc_beta[2] >= 0.0 || opt.bc_beta[3] >= 0.0 || opt.log_coefficients) {
-    set_last_error("3D setup: options other than nu1, nu2, max_cycles and precision must be the defaults");
+    set_last_error("3D setup: options other than nu1, nu2, max_cycles, precision and solver must be the "
+                   "defaults (BMG_SOLVER_PCG needs nu1 == nu2)");
     return BMG_EINVAL;
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -833,6 +1060,14 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
       for (int p = 0; p < nplanes; ++p) offs32.push_back(reserve(pb));
     }
   }
+  h->pcg = opt.solver == BMG_SOLVER_PCG;
+  size_t o_pcg = 0;
+  if (h->pcg) {
+    const Lev3& Ff = h->lv[L - 1];
+    const size_t pbf = size_t(Ff.nz + 2) * Ff.py * Ff.px * sizeof(double);
+    o_pcg = reserve(pbf);
+    for (int q = 1; q < 4; ++q) reserve(pbf);
+  }
   const size_t o_chol = reserve(sizeof(double) * size_t(h->n0) * h->n0);
   const size_t o_idiag = reserve(sizeof(double) * h->n0);
   const size_t o_part = reserve(sizeof(double) * kNormBlocks);
@@ -870,6 +1105,14 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
     W.b = next();
     W.r = next();
     for (int m = 0; m < NPW3; ++m) W.P[m] = l >= 1 ? next() : nullptr;
+  }
+  if (h->pcg) {
+    const Lev3& Ff = h->lv[L - 1];
+    const size_t pbf = (size_t(Ff.nz + 2) * Ff.py * Ff.px * sizeof(double) + 255) & ~size_t(255);
+    h->pX = reinterpret_cast<double*>(base + o_pcg);
+    h->pB = reinterpret_cast<double*>(base + o_pcg + pbf);
+    h->pP = reinterpret_cast<double*>(base + o_pcg + 2 * pbf);
+    h->pQ = reinterpret_cast<double*>(base + o_pcg + 3 * pbf);
   }
   h->chol = reinterpret_cast<double*>(base + o_chol);
   h->chol_idiag = reinterpret_cast<double*>(base + o_idiag);
@@ -921,6 +1164,20 @@ int bmg3_solve(bmg3_hierarchy* h, const double* b, double* x, double tol, bmg_in
   if (!h || !b || !x || !(tol >= 0.0)) return BMG_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const double t0 = now_ms();
+  if (h->pcg) {
+    int it = 0;
+    double rel = 0.0;
+    const int rc = solve_pcg(h, b, x, tol, s, &it, &rel);
+    if (info) {
+      info->cycles = it;
+      info->threshold = 0;
+      info->rel_resid = rel;
+      info->setup_ms = h->setup_ms;
+      info->solve_ms = now_ms() - t0;
+      info->coarse_ctas = 1;
+    }
+    return rc;
+  }
   const Lev3& F = h->lv[h->L - 1];
   const dim3 g = dim3(cdiv(F.nx, kT), F.ny, F.nz);
   k3_pack<<<g, kT, 0, s>>>(b, F.b, F);

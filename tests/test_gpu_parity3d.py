@@ -172,6 +172,52 @@ def test_3d_fp32_refinement_reaches_fp64_tolerance(name):
     assert info.cycles <= 2 * ro.cycles + 4, (info.cycles, ro.cycles)
 
 
+@functools.lru_cache(maxsize=None)
+def oracle_pcg(name):
+    k, b = case(name)
+    return O3.pcg(O3.setup(k, nu1=1, nu2=1), b, tol=1e-10)
+
+
+PCG_CASES = ["blocks15", "blocks31_c4", "poisson31", "general45x20x70", "general12x9x7", "tiny4"]
+
+
+@pytest.mark.parametrize("name", PCG_CASES)
+def test_3d_pcg_matches_oracle(name):
+    """CG preconditioned by one symmetric V(1,1) cycle: the oracle's
+    iteration count, its final relative residual to rounding (the dot
+    products are summed in another order) and its iterate."""
+    k, b = case(name)
+    ro = oracle_pcg(name)
+    hg = bm.setup3(dev(k), bm.default_options(nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG, max_cycles=400))
+    x, info = hg.solve(dev(b), tol=1e-10)
+    hg.destroy()
+    xg = x.cpu().numpy()
+    assert ro.converged and info.cycles == ro.cycles, (info.cycles, ro.cycles)
+    assert abs(info.rel_resid - ro.rel_resid) <= 1e-7 * ro.rel_resid + 1e-14
+    assert np.abs(xg - ro.x).max() <= 1e-9 * np.abs(ro.x).max()
+    # the true residual of the returned x (the stop test uses the updated one)
+    a = oracle_h(name).levels[-1].a
+    assert np.linalg.norm(b.ravel() - a @ xg.ravel()) / np.linalg.norm(b) <= 2e-10
+
+
+@pytest.mark.parametrize("name", PCG_CASES)
+def test_3d_pcg_with_fp32_cycles_reaches_fp64_tolerance(name):
+    """The same with the V-cycle on the FP32 copies of the levels (r / ||r||
+    cast down, ||r|| e cast back): the FP64 recurrences still reach 1e-10."""
+    k, b = case(name)
+    ro = oracle_pcg(name)
+    hg = bm.setup3(dev(k), bm.default_options(nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG, max_cycles=400,
+                                              precision=bm.BMG_FP32_REFINE))
+    x, info = hg.solve(dev(b), tol=1e-10)
+    hg.destroy()
+    xg = x.cpu().numpy()
+    a = oracle_h(name).levels[-1].a
+    assert info.rel_resid <= 1e-10
+    assert np.linalg.norm(b.ravel() - a @ xg.ravel()) / np.linalg.norm(b) <= 2e-10
+    assert np.abs(xg - ro.x).max() <= 1e-7 * np.abs(ro.x).max()
+    assert info.cycles <= ro.cycles + 3, (info.cycles, ro.cycles)
+
+
 def test_3d_zero_rhs_and_error_codes():
     k = np.ones((7, 7, 7))
     h = bm.setup3(dev(k))
