@@ -179,12 +179,15 @@ __device__ void weights_point(const Lev3& F, int i, int j, int k, int pass, int*
   for (int m = 0; m < NPW3; ++m) {
     const int mc[3] = {m & 1, (m >> 1) & 1, (m >> 2) & 1};
     if ((mc[0] && !fr[0]) || (mc[1] && !fr[1]) || (mc[2] && !fr[2])) continue;
+    // collapsed couplings live only at offsets that vary in the directions
+    // the point lies between coarse points (integer bounds instead of an
+    // FP64 test per neighbour; the skipped terms are exact zeros)
     double w = 0.0;
-    for (int dk = -1; dk <= 1; ++dk)
-      for (int dj = -1; dj <= 1; ++dj)
-        for (int di = -1; di <= 1; ++di) {
+    for (int dk = -fr[2]; dk <= fr[2]; ++dk)
+      for (int dj = -fr[1]; dj <= fr[1]; ++dj)
+        for (int di = -fr[0]; di <= fr[0]; ++di) {
           const int t = (dk + 1) * 9 + (dj + 1) * 3 + (di + 1);
-          if (t == 13 || coll[t] == 0.0) continue;
+          if (t == 13) continue;
           const int dd[3] = {di, dj, dk};
           int gslot = 0;
           bool ok = true;
@@ -259,8 +262,9 @@ __global__ void k3_rap(Lev3 F, Lev3 Cc, int* err) {
             const int fi = 2 * I + ex, fj = 2 * J + ey, fk = 2 * K + ez;
             if (fi > F.nx || fj > F.ny || fk > F.nz) continue;
             const int of = idx3(F, fi, fj, fk);
+            // no test for zero weights: they add exact zeros, and an FP64
+            // compare costs as much as the multiply-add on this part
             const double wf = F.P[support_slot(ex, ey, ez)][of];
-            if (wf == 0.0) continue;
             double s = 0.0;
             for (int hz = lo(ez, dk); hz <= hi(ez, dk); ++hz)
               for (int hy = lo(ey, dj); hy <= hi(ey, dj); ++hy)
@@ -270,7 +274,6 @@ __global__ void k3_rap(Lev3 F, Lev3 Cc, int* err) {
                   if (gi < 1 || gj < 1 || gk < 1 || gi > F.nx || gj > F.ny || gk > F.nz) continue;
                   const int og = idx3(F, gi, gj, gk);
                   const double wg = F.P[support_slot(gx, gy, gz)][og];
-                  if (wg == 0.0) continue;
                   const double afg =
                       (hx | hy | hz) == 0 ? F.C[of] : -coupling(F, of, hx, hy, hz);
                   s = fma(afg, wg, s);
