@@ -58,13 +58,16 @@ def coarse_range(lo: int, hi: int):
 
 def split_weighted(lo: int, hi: int, weights, align: int):
     """Contiguous 0-based half-open ranges covering [lo, hi), one per weight,
-    each starting at a multiple of `align` (lo is one), with unit counts
-    (units of `align` points) proportional to the weights: floors, then the
-    largest remainders (ties to the lower index), at least one unit each."""
-    units = -(-(hi - lo) // align)
+    each starting at a multiple of `align` (lo is one).  The units are the
+    whole `align`-point units of the range (the points a coarser level keeps
+    after log2(align) coarsenings); the last range also takes the remainder,
+    so every range keeps at least one point on that level.  Unit counts
+    follow the weights: floors, then the largest remainders (ties to the
+    lower index), at least one unit each."""
+    units = (hi - lo) // align
     p = len(weights)
     if units < p:
-        raise ValueError(f"{hi - lo} points cannot be split into {p} blocks aligned to {align}")
+        raise ValueError(f"{hi - lo} points cannot be split into {p} blocks of at least {align}")
     W = sum(weights)
     cnt = [units * w // W for w in weights]
     order = sorted(range(p), key=lambda i: (-(units * weights[i] % W), i))
@@ -77,8 +80,9 @@ def split_weighted(lo: int, hi: int, weights, align: int):
             cnt[i] = 1
     out, u = [], 0
     for c in cnt:
-        out.append((lo + u * align, min(lo + (u + c) * align, hi)))
+        out.append((lo + u * align, lo + (u + c) * align))
         u += c
+    out[-1] = (out[-1][0], hi)
     return out
 
 

@@ -89,7 +89,11 @@ def test_layout_alignment_and_rules():
             assert (clo, chi) == ((lo + 1) // 2, hi // 2)
     with pytest.raises(ValueError):
         dd.Layout(shapes, 4, 1, 4)                  # 16-aligned blocks: only 4 units of 63 -> empty
-    assert dd.split(255, 4, 64) == [(1, 64), (65, 128), (129, 192), (193, 255)]
+    # whole 64-point units (the 3 points 255 keeps after six coarsenings);
+    # the last block takes the remainder, and four blocks do not fit
+    assert dd.split(255, 3, 64) == [(1, 64), (65, 128), (129, 255)]
+    with pytest.raises(ValueError):
+        dd.split(255, 4, 64)
     # 255^2 on 2 x 2: the smallest blocks of the 127^2 level hold 63^2 = 3969
     # points, of the 63^2 level 31^2 = 961, of the 31^2 level 15^2 = 225
     big = [(3, 3), (7, 7), (15, 15), (31, 31), (63, 63), (127, 127), (255, 255)]

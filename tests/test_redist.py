@@ -13,7 +13,9 @@ paper's printed examples and by the mathematics of the search.
 * A* with its heuristic returns the brute-force optimum on random spaces and
   expands far fewer states; the heuristic never exceeds the optimal cost to
   the goal;
-* the model's terms agree with their definitions on hand-counted cases.
+* the model's terms agree with their definitions on hand-counted cases, in
+  2D and in 3D (the paper's 3D interpolation count); the 3D search space
+  has the same properties.
 """
 import math
 import os
@@ -174,3 +176,82 @@ def test_model_terms_on_hand_counted_cases():
     want = (2 * 5 * 225 * 3 + 2 * 2 * 5 * 225 + 225 + 20 * 49 + 6 * 14) * 1e-6
     assert R.level_time(shapes, 2, (1, 1), m, R.Cycle()) == pytest.approx(want)
     assert R.t_cgsolve_factor(shapes, m) == pytest.approx(81 * 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# 3D: the paper's 3D interpolation count, and the search over 3D grids
+# ---------------------------------------------------------------------------
+
+def test_3d_model_terms_on_hand_counted_cases():
+    m = R.Machine(alpha=1.0, beta=1e-3, gamma=1e-6)
+    # a 10 x 20 x 30 block split in every dimension: faces 600, 300, 200
+    assert R.t_exchange((10, 20, 30), (2, 2, 2), m) == pytest.approx(6 + 2 * 1100 * 8e-3)
+    assert R.t_exchange((10, 20, 30), (1, 1, 2), m) == pytest.approx(2 + 2 * 200 * 8e-3)
+    # 3D interpolation onto a 5^3 block from a 2^3 coarse block:
+    # 125 + 60 * 8 + 15 * 2 * 2 + 6 * 2 * 2 + 2 flops
+    assert R.interp_flops((5, 5, 5), (2, 2, 2)) == 125 + 480 + 60 + 24 + 2
+    # level 1 (7^3, 27-point, 8 colours) of a 3-level hierarchy on one
+    # processor, V(2,1): smoothing 2*27*343*3, residual and restriction
+    # 2*27*343 each, interpolation 343 + 60*27 + 15*9 + 6*9 + 3
+    shapes = [(3, 3, 3), (7, 7, 7), (15, 15, 15)]
+    want = (2 * 27 * 343 * 3 + 2 * 2 * 27 * 343 + 343 + 60 * 27 + 15 * 9 + 6 * 9 + 3) * 1e-6
+    assert R.level_time(shapes, 1, (1, 1, 1), m, R.Cycle()) == pytest.approx(want)
+    # the finest level: 7-point, red-black
+    want = (2 * 7 * 3375 * 3 + 2 * 2 * 7 * 3375 + 3375 + 60 * 343 + 15 * 49 + 6 * 49 + 7) * 1e-6
+    assert R.level_time(shapes, 2, (1, 1, 1), m, R.Cycle()) == pytest.approx(want)
+    # gather over 2 x 2 x 2 -> 1: three latency steps
+    assert R.t_agglomerate((7, 7, 7), (2, 2, 2), (1, 1, 1), m, redundant=True) == pytest.approx(
+        3 + 343 * 7 / 8 * 8e-3)
+    assert R.t_cgsolve_factor(shapes, m) == pytest.approx(27 ** 2 * 1e-6)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_3d_enumeration_is_a_chain(seed):
+    rng = random.Random(200 + seed)
+    q = tuple(2 ** rng.randint(0, 4) for _ in range(3))
+    if q == (1, 1, 1):
+        q = (2, 2, 1)
+    N = tuple(rng.randint(q[d], 3000) for d in range(3))
+    grids = R.enumerate_grids(N, q)
+    assert grids[0] == (1, 1, 1)
+    assert len(grids) == math.log2(q[0] * q[1] * q[2])
+    for g, g2 in zip(grids, grids[1:] + [q]):
+        changed = [d for d in range(3) if g2[d] != g[d]]
+        assert len(changed) == 1 and g2[changed[0]] == 2 * g[changed[0]]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_3d_astar_returns_the_brute_force_optimum(seed):
+    rng = random.Random(300 + seed)
+    P = tuple(2 ** rng.randint(0, 3) for _ in range(3))
+    if P == (1, 1, 1):
+        P = (2, 2, 2)
+    machine = R.Machine(alpha=10 ** rng.uniform(-7, -4), beta=10 ** rng.uniform(-11, -8),
+                        gamma=10 ** rng.uniform(-11, -9))
+    N = tuple(rng.randint(40, 160) * P[d] for d in range(3))
+    sp = R.Space(R.halving_shapes(N), P, machine, R.Cycle(), min_local=rng.choice([64, 512, 4096]),
+                 redundant=rng.random() < 0.3)
+    a, b = R.search_astar(sp), R.search_brute_force(sp)
+    assert a.cost == pytest.approx(b.cost, rel=1e-12)
+    assert sp.path_cost(a.path) == pytest.approx(a.cost, rel=1e-12)
+    assert a.path[0] == (P, len(sp.shapes) - 1) and a.path[-1][0] == (1, 1, 1)
+
+
+def test_paths_always_end_on_one_processor_and_execute_as_plans():
+    """A grid that keeps the coarsening limit down to level 1 hands level 0
+    to one processor as an explicit last state, so every searched path is a
+    runnable redistribution plan."""
+    from paper_1803_02481_gb300 import dd
+    shapes = [(3, 3), (7, 7), (15, 15), (31, 31), (63, 63)]
+    sp = R.Space(shapes, (2, 2), min_local=4)          # 2 x 2 keeps >= 4 points to level 1
+    res = R.search_astar(sp)
+    assert res.path[-1] == ((1, 1), 0)
+    assert sp.states_of_grids([(2, 2), (1, 1)]) == [((2, 2), 4), ((1, 1), 0)]
+    dd.Plan(shapes, res.path)
+    for seed in range(5):
+        sp = _random_space(random.Random(500 + seed))
+        if sp.redundant:
+            continue
+        path = R.search_astar(sp).path
+        assert path[-1][0] == sp.one
+        dd.Plan(sp.shapes, path)
