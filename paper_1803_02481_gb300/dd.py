@@ -1,21 +1,29 @@
 """Domain-decomposed solve phase (Section 2.1) with coarse-grid
-redistribution by agglomeration (Section 2.2, Algorithm 2).
+redistribution by agglomeration (Section 2.2, Algorithm 2), along a path
+chosen by the performance model (Sections 3-4, ``redist``).
 
-The ranks form a px x py processor grid.  On each of the `dist_levels`
-finest levels every rank owns one rectangular block of points and keeps it,
-with a one-point ring of its neighbours' values (the width-1 halo), in a
-part of the CUDA library (``bmg_dd_*``).  One V-cycle is Algorithm 2 with
-p_l = px * py on the distributed levels and p_l = 1 below them:
+The ranks form a px x py processor grid.  A redistribution plan (`Plan`)
+is a path of states (grid, level): the fine grid runs the finest levels,
+then the problem of the level where the coarsening limit is reached is
+agglomerated onto a coarser grid, which runs the next levels, and so on
+down to one rank, which runs the rest of the cycle with the library's
+single-GPU schedule.  On each level of its stage a rank owns one
+rectangular block of points and keeps it, with a one-point ring of its
+neighbours' values (the width-1 halo), in a part of the CUDA library
+(``bmg_dd_*``).  One V-cycle is Algorithm 2 with p_l decreasing stage by
+stage:
 
 * relax: one halo exchange of x before every colour, then the colour;
 * residual: a halo exchange of x, r = b - A x;
 * restriction: a halo exchange of r, b_{l-1} = P^T r (local otherwise);
-* gather_rhs: every rank sends its block of the restricted right-hand side
-  of the gather level to rank 0, which runs the rest of the cycle on the
-  levels below with the library's single-GPU schedule;
-* scatter_sol: rank 0 sends every rank its block of the coarse solution,
-  ring included; then interpolation and post-smoothing climb back, with a
-  halo exchange of the coarser x before each interpolation;
+* gather_rhs where p_l > p_{l-1}: the processor block of each coarse task
+  sends its blocks of the restricted right-hand side to the block's first
+  member, which runs the coarse task; or, redundant, every member
+  allgathers them and runs it as a replica;
+* scatter_sol: the coarse task sends every member its block of the coarse
+  solution, ring included (none when redundant); then interpolation and
+  post-smoothing climb back, with a halo exchange of the coarser x before
+  each interpolation;
 * the stop test adds the ranks' partial sums of r^2 and b^2 (allreduce).
 
 A halo exchange runs in two phases, west/east (owned rows) and then
@@ -23,10 +31,10 @@ south/north (rows including the ring columns, which carry the corners).
 
 Setup is centralised: rank 0 builds the global hierarchy (assembly,
 operator-induced interpolation, Galerkin operators, coarsest factor) and
-scatters to every rank the planes of its blocks, ring included.  Blocks start
-at 0-based global indices that are multiples of 2^dist_levels, so the
-colours, coarse points and restriction/interpolation offsets of a block are
-those of the full level.
+scatters to every rank the planes of its blocks, ring included.  A stage's
+blocks start at 0-based indices that are multiples of 2^(levels it
+coarsens), so the colours, coarse points and restriction/interpolation
+offsets of a block are those of the full level.
 
 Every numerical step runs in the CUDA library; this module moves blocks
 between ranks (``torch.distributed`` or, for several blocks on one GPU, the
