@@ -793,31 +793,39 @@ def threshold_sweep(bm, torch, k, b, stream, cycles=20):
 def pcg_leg(bm, torch, k, b, stream, tol, vcycle_ms, vcycle_cycles, max_iter=2000):
     """Conjugate gradients preconditioned by one symmetric V(1,1) cycle on the
     bench workload, to the bench tolerance, setup + solve timed like a bench
-    step, against the plain V(2,1) iteration of the headline."""
-    opts = bm.default_options(nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG, max_cycles=max_iter)
+    step, against the plain V(2,1) iteration of the headline; the cycle on
+    the FP64 levels, and on the FP32 hierarchy (fp32_cycle)."""
     x = torch.zeros_like(b)
-
-    def step():
-        x.zero_()
-        h = bm.setup(k, opts, stream=stream)
-        _, info = h.solve(b, x, tol=tol, stream=stream)
-        h.destroy()
-        return info
-
-    step()
-    torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    info = step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
     n = b.numel()
+    out = {}
+    for tag, prec in (("fp64_cycle", bm.BMG_FP64), ("fp32_cycle", bm.BMG_FP32_REFINE)):
+        opts = bm.default_options(nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG, max_cycles=max_iter,
+                                  precision=prec)
+
+        def step():
+            x.zero_()
+            h = bm.setup(k, opts, stream=stream)
+            _, info = h.solve(b, x, tol=tol, stream=stream)
+            h.destroy()
+            return info
+
+        step()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        info = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        out[tag] = {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms, "iterations": info.cycles,
+                    "rel_resid": info.rel_resid, "speedup_vs_vcycle": vcycle_ms / ms}
+    f64 = out["fp64_cycle"]
     return {"solver": "CG preconditioned by one symmetric V(1,1) cycle", "tol": tol,
-            "value": n / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms, "iterations": info.cycles,
-            "rel_resid": info.rel_resid, "vcycle_v21_ms_per_solve": vcycle_ms,
-            "vcycle_v21_cycles": vcycle_cycles, "speedup_vs_vcycle": vcycle_ms / ms}
+            "value": f64["value"], "unit": UNIT, "ms_per_solve": f64["ms_per_solve"],
+            "iterations": f64["iterations"], "rel_resid": f64["rel_resid"],
+            "vcycle_v21_ms_per_solve": vcycle_ms, "vcycle_v21_cycles": vcycle_cycles,
+            "speedup_vs_vcycle": f64["speedup_vs_vcycle"], "fp32_cycle": out["fp32_cycle"]}
 
 
 def batch_leg(bm, torch, dev, stream, count=512):

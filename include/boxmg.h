@@ -61,9 +61,11 @@ enum { BMG_FP64 = 0, BMG_FP32_REFINE = 1 };
 
 /* Solvers: the V-cycle iteration of Algorithm 1, or conjugate gradients
  * preconditioned by one symmetric V(nu, nu) cycle (an extension: the paper
- * iterates V-cycles).  BMG_SOLVER_PCG needs precision BMG_FP64, nu1 == nu2
- * >= 1 and interp_residual_term == 0, which make the cycle a symmetric
- * positive definite preconditioner. */
+ * iterates V-cycles).  BMG_SOLVER_PCG needs nu1 == nu2 >= 1 and
+ * interp_residual_term == 0, which make the cycle a symmetric positive
+ * definite preconditioner.  The CG recurrences are FP64; with precision
+ * BMG_FP32_REFINE the cycle runs on the FP32 hierarchy (r / ||r|| cast down,
+ * ||r|| e cast back), which can cost iterations on high-contrast fields. */
 enum { BMG_SOLVER_VCYCLE = 0, BMG_SOLVER_PCG = 1 };
 
 /* Smoothers: multicolour point Gauss-Seidel (red-black on the 5-point finest

@@ -217,10 +217,9 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
       return BMG_EINVAL;
     }
   }
-  if (opt.solver == BMG_SOLVER_PCG &&
-      (opt.precision != BMG_FP64 || opt.nu1 != opt.nu2 || opt.interp_residual_term)) {
-    set_last_error("BMG_SOLVER_PCG needs precision BMG_FP64, nu1 == nu2 and "
-                   "interp_residual_term == 0 (a symmetric V-cycle)");
+  if (opt.solver == BMG_SOLVER_PCG && (opt.nu1 != opt.nu2 || opt.interp_residual_term)) {
+    set_last_error("BMG_SOLVER_PCG needs nu1 == nu2 and interp_residual_term == 0 "
+                   "(a symmetric V-cycle)");
     return BMG_EINVAL;
   }
   const double t0 = now_ms();
@@ -468,7 +467,7 @@ static int build_solve_graph(Hierarchy* h) {
   auto prologue = [&] {
     if (pcg) {
       launch_pcg_init(h, s, true);
-      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+      launch_pcg_precond(h, s);
       launch_pcg_rz(h, true, s);
       launch_pcg_p(h, s);
     } else if (fp32) {
@@ -483,7 +482,7 @@ static int build_solve_graph(Hierarchy* h) {
       // direction (x no longer changes), so a last pass is harmless
       launch_pcg_ap(h, s);
       launch_pcg_xr(h, s, true);
-      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+      launch_pcg_precond(h, s);
       launch_pcg_rz(h, false, s);
       launch_pcg_p(h, s);
     } else if (fp32) {
@@ -607,7 +606,7 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
       return BMG_OK;
     }
     if (h->sc_host->go) {
-      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+      launch_pcg_precond(h, s);
       launch_pcg_rz(h, true, s);
       launch_pcg_p(h, s);
       for (;;) {
@@ -615,7 +614,7 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
         launch_pcg_xr(h, s, false);
         if ((rc = read_scalars(h, s))) return rc;
         if (!h->sc_host->go) break;
-        enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+        launch_pcg_precond(h, s);
         launch_pcg_rz(h, false, s);
         launch_pcg_p(h, s);
       }

@@ -254,13 +254,15 @@ __global__ void __launch_bounds__(kNormThreads) k_norm_final(const double* parti
   if (what == 0) {
     sc->bnorm2 = acc;
     sc->rnorm2 = acc;
-    sc->inv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+    sc->rnorm = sqrt(acc);
+    sc->inv = acc > 0.0 ? 1.0 / sc->rnorm : 0.0;
     return;
   }
   sc->scale2 = sc->rnorm2;
   sc->scale = sqrt(sc->scale2);
   sc->rnorm2 = acc;
-  sc->inv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+  sc->rnorm = sqrt(acc);
+  sc->inv = acc > 0.0 ? 1.0 / sc->rnorm : 0.0;
   const double rel = sqrt(acc / sc->bnorm2);
   sc->rel = rel;
   if (sc->cycles < BMG_MAX_HISTORY) hist[sc->cycles] = rel;

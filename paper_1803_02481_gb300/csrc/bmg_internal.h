@@ -285,6 +285,7 @@ struct Scalars {            // device-resident solve state
   double tol;               // stop test
   double scale;             // sqrt(scale2), set with scale2 (one thread)
   double inv;               // 1 / sqrt(rnorm2) (0 when rnorm2 == 0), set with rnorm2
+  double rnorm;             // sqrt(rnorm2), set with rnorm2
   double rz;                // BMG_SOLVER_PCG: r.z of the current iteration
   double alpha, beta;       // BMG_SOLVER_PCG: step and direction coefficients
   int cycles;               // cycles / refinement steps run
@@ -473,6 +474,10 @@ void launch_pcg_ap(Hierarchy* h, cudaStream_t s);
 void launch_pcg_xr(Hierarchy* h, cudaStream_t s, bool in_graph);
 void launch_pcg_rz(Hierarchy* h, bool first, cudaStream_t s);
 void launch_pcg_p(Hierarchy* h, cudaStream_t s);
+// z = M^{-1} r for PCG: one V-cycle on the residual in the finest level's b
+// plane (FP64 levels; BMG_FP32_REFINE: r / ||r|| cast to the FP32 finest
+// level, the FP32 cycle, z = ||r|| e cast back).
+void launch_pcg_precond(Hierarchy* h, cudaStream_t s);
 
 // One V-cycle of the FP64 (d) or FP32 (f) hierarchy (bmg_api.cu).
 template <typename T>

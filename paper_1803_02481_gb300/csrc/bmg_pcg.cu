@@ -1,5 +1,6 @@
 // Conjugate gradients on the finest operator, preconditioned by one
-// symmetric V(nu, nu) cycle of Algorithm 1 from a zero initial guess (an
+// symmetric V(nu, nu) cycle of Algorithm 1 from a zero initial guess (on the
+// FP64 levels, or on the FP32 hierarchy of BMG_FP32_REFINE; an
 // extension: the paper iterates V-cycles; with nu1 = nu2, the colours of the
 // post-smoothing reversed, R = P^T and an exact coarsest solve, the cycle is
 // a symmetric positive definite preconditioner).
@@ -129,7 +130,37 @@ __global__ void __launch_bounds__(kThreads) k_pcg_scalar(const double* __restric
   }
 }
 
+// FP32 preconditioner: the FP32 finest level's right-hand side r / ||r||
+// and x32 = 0 (||r|| of the latest residual: sc->inv, sc->rnorm, set once by
+// the norm's final kernel); after the FP32 cycle z = ||r|| e.
+__global__ void k_pcg_cast(LevelV<double> L, LevelV<float> F, const Scalars* __restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1;
+  if (i > L.nx) return;
+  const int of = j * F.pitch + i;
+  F.b[of] = float(L.b[j * L.pitch + i] * sc->inv);
+  F.x[of] = 0.0f;
+}
+
+__global__ void k_pcg_uncast(LevelV<double> L, LevelV<float> F, const Scalars* __restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1;
+  if (i > L.nx) return;
+  L.x[j * L.pitch + i] = sc->rnorm * double(F.x[j * F.pitch + i]);
+}
+
 }  // namespace
+
+void launch_pcg_precond(Hierarchy* h, cudaStream_t s) {
+  if (h->opt.precision != BMG_FP32_REFINE) {
+    enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+    return;
+  }
+  LevelV<double>& F = h->d.back();
+  const dim3 g((F.nx + kThreads - 1) / kThreads, F.ny);
+  k_pcg_cast<<<g, kThreads, 0, s>>>(F, h->f.back(), h->sc);
+  enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s);
+  k_pcg_uncast<<<g, kThreads, 0, s>>>(F, h->f.back(), h->sc);
+  count_launch(2);
+}
 
 void launch_pcg_init(Hierarchy* h, cudaStream_t s, bool in_graph) {
   LevelV<double>& F = h->d.back();
