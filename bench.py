@@ -877,6 +877,26 @@ def batch_leg(bm, torch, dev, stream, count=512):
         ms = ev0.elapsed_time(ev1)
         out[name] = {"value": unknowns / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms}
     out["speedup_batched_vs_sequential_fp64"] = out["sequential_fp64"]["ms_per_solve"] / ms_batch
+    # the same batch with batched CG preconditioned by the symmetric FP32
+    # V(1,1) cycle (one graph launch, FP64 recurrences per problem)
+    bp = bm.Batch(ks, bm.default_options(nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG, max_cycles=500),
+                  stream=stream)
+    for x in xs:
+        x.zero_()
+    bp.solve(bs, xs, tol=1e-8, stream=stream)
+    ev0.record(stream)
+    for _ in range(reps):
+        for x in xs:
+            x.zero_()
+        ip = bp.solve(bs, xs, tol=1e-8, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_pcg = ev0.elapsed_time(ev1) / reps
+    bp.destroy()
+    out["batched_pcg_fp32_cycle"] = {"value": unknowns / (ms_pcg / 1e3), "unit": UNIT, "ms_per_solve": ms_pcg,
+                                     "max_iterations": max(i.cycles for i in ip),
+                                     "max_rel_resid": max(i.rel_resid for i in ip),
+                                     "speedup_vs_batched_fp32_refine": ms_batch / ms_pcg}
     # split by size class: each class solved alone as a batch of its own
     # (same problems, same solver), so the share of the whole batch's time
     # that each class's refinement-step count sets is visible
@@ -1141,6 +1161,8 @@ def run_leg(name):
         out = adjoint_leg(bm, torch, dev, stream)
     elif name == "lognormal":
         out = lognormal_leg(bm, torch, dev, stream, None)
+    elif name == "batched":
+        out = batch_leg(bm, torch, dev, stream)
     else:
         out = paper_workload_leg(bm, torch, dev, stream, nx=9088, ny=568)
     print(json.dumps({"leg": name, **out}))
@@ -1168,7 +1190,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--only", default=None,
                     choices=["line_smoother", "three_d", "paper_workload", "paper_workload_9088x568",
-                             "c1_poisson255", "adjoint_gradient", "lognormal", "redistribution"],
+                             "c1_poisson255", "adjoint_gradient", "lognormal", "redistribution", "batched"],
                     help="run one measurement leg alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.only == "redistribution":

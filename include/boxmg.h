@@ -301,9 +301,12 @@ typedef struct bmg_batch bmg_batch; /* opaque, library-owned */
 /* Set up nprob independent square problems at once: problem p has side n[p]
  * (2^m - 1) and coefficients k_dev[p] (dense n[p] x n[p] float64, device).
  * k_dev and n are host arrays.  Each problem is solved with FP32 V-cycles
- * (Algorithm 1) inside FP64 iterative refinement (opt->precision is ignored);
- * levels of side <= 31 run in the persistent coarse kernel, one thread block
- * per problem.  Setup also picks the tile shape of the batched sweeps for
+ * (Algorithm 1) inside FP64 iterative refinement (opt->precision is ignored),
+ * or, with opt->solver BMG_SOLVER_PCG (nu1 == nu2, no r/C term), with FP64
+ * conjugate gradients preconditioned by one symmetric FP32 V(nu, nu) cycle
+ * (r / ||r|| cast down, ||r|| e cast back), all problems' iterations
+ * advanced together; levels of side <= 31 run in the persistent coarse
+ * kernel, one thread block per problem.  Setup also picks the tile shape of the batched sweeps for
  * every level side by timing the candidates on this batch (cached per
  * process, and in the file named by the environment variable BMG_TUNE_CACHE
  * if set) and records the refinement loop as one CUDA graph.  Errors as

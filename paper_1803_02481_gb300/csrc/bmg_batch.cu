@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(kNT) k_bnorm_final(const double* __restrict__ 
   if (what == 0) {
     s->bnorm2 = acc;
     s->rnorm2 = acc;
-    s->inv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+    s->rnorm = sqrt(acc);
+    s->inv = acc > 0.0 ? 1.0 / s->rnorm : 0.0;
     s->go = acc > 0.0 ? 1 : 0;     // a zero right-hand side needs no cycle
     s->rel = 0.0;
     return;
@@ -198,7 +199,8 @@ __global__ void __launch_bounds__(kNT) k_bnorm_final(const double* __restrict__ 
   s->scale2 = s->rnorm2;
   s->scale = sqrt(s->scale2);
   s->rnorm2 = acc;
-  s->inv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+  s->rnorm = sqrt(acc);
+  s->inv = acc > 0.0 ? 1.0 / s->rnorm : 0.0;
   const double rel = sqrt(acc / s->bnorm2);
   s->rel = rel;
   const bool finite = isfinite(rel);
@@ -237,37 +239,143 @@ __global__ void k_bupdate(const LevelV<double>* __restrict__ f64,
   L.x[o] = fma(s, double(e[j * f32[z].pitch + i]), L.x[o]);
 }
 
+// ---------------------------------------------------------------------------
+// Batched conjugate gradients (BMG_SOLVER_PCG): per problem, CG on its finest
+// operator in FP64, preconditioned by one symmetric FP32 V(nu, nu) cycle of
+// the batched V-cycle (r / ||r|| cast to the FP32 finest level, z = ||r|| e
+// cast back), in the single-problem solver's order.  The FP64 finest level's
+// b plane holds r and its x plane z; X, B, P, Q are the problem's CG planes.
+// ---------------------------------------------------------------------------
+
+struct BPcg {
+  double *x, *b, *p, *q;
+};
+
+enum { BPCG_INIT = 0, BPCG_AP = 1, BPCG_XR = 2, BPCG_RZ = 3, BPCG_P = 4 };
+
+// One problem per blockIdx.y, kPB blocks each, active problems only:
+// INIT r = B - A X, z = 0, partials of r.r; AP Q = A P, partials of P.Q;
+// XR X += alpha P, r -= alpha Q, z = 0, partials of r.r; RZ partials of r.z;
+// P P = z + beta P.
+__global__ void __launch_bounds__(kNT) k_bpcg(const LevelV<double>* __restrict__ f64,
+                                              const BPcg* __restrict__ vec,
+                                              const int* __restrict__ pids,
+                                              const Scalars* __restrict__ sc,
+                                              double* __restrict__ partials, int what) {
+  const int z = blockIdx.y;
+  const int pr = pids[z];
+  if (!sc[pr].go) return;
+  const LevelV<double> L = f64[z];
+  const BPcg v = vec[z];
+  const double alpha = sc[pr].alpha, beta = sc[pr].beta;
+  double acc = 0.0;
+  for (int j = blockIdx.x + 1; j <= L.ny; j += gridDim.x) {
+    for (int i = threadIdx.x + 1; i <= L.nx; i += blockDim.x) {
+      const int o = j * L.pitch + i;
+      if (what == BPCG_INIT) {
+        const double r = resid_value<double, false>(L, v.x, v.b[o], o);
+        L.b[o] = r;
+        L.x[o] = 0.0;
+        acc = fma(r, r, acc);
+      } else if (what == BPCG_AP) {
+        const double q = -resid_value<double, false>(L, v.p, 0.0, o);
+        v.q[o] = q;
+        acc = fma(v.p[o], q, acc);
+      } else if (what == BPCG_XR) {
+        v.x[o] = fma(alpha, v.p[o], v.x[o]);
+        const double r = fma(-alpha, v.q[o], L.b[o]);
+        L.b[o] = r;
+        L.x[o] = 0.0;
+        acc = fma(r, r, acc);
+      } else if (what == BPCG_RZ) {
+        acc = fma(L.b[o], L.x[o], acc);
+      } else {
+        v.p[o] = fma(beta, v.p[o], L.x[o]);
+      }
+    }
+  }
+  if (what == BPCG_P) return;
+  acc = bsum(acc);
+  if (threadIdx.x == 0) partials[size_t(pr) * kPB + blockIdx.x] = acc;
+}
+
+// One block per problem: AP alpha = rz / sum (0 for a zero denominator); RZ
+// beta = sum / rz (0 while rz is 0: the first direction is z), rz = sum.
+__global__ void __launch_bounds__(kNT) k_bpcg_scalar(const double* __restrict__ partials,
+                                                     Scalars* __restrict__ sc, int what) {
+  const int pr = blockIdx.x;
+  Scalars* s = sc + pr;
+  if (!s->go) return;
+  double acc = threadIdx.x < kPB ? partials[size_t(pr) * kPB + threadIdx.x] : 0.0;
+  acc = bsum(acc);
+  if (threadIdx.x != 0) return;
+  if (what == BPCG_AP) {
+    s->alpha = acc != 0.0 ? s->rz / acc : 0.0;
+  } else {
+    s->beta = s->rz != 0.0 ? acc / s->rz : 0.0;
+    s->rz = acc;
+  }
+}
+
+// The preconditioner's casts: dir 0, FP32 finest b = r / ||r|| and x = 0;
+// dir 1, z = ||r|| e (||r|| of the latest residual, set once per problem by
+// k_bnorm_final).
+__global__ void k_bpcg_cast(const LevelV<double>* __restrict__ f64,
+                            const LevelV<float>* __restrict__ f32, const int* __restrict__ pids,
+                            const Scalars* __restrict__ sc, int dir) {
+  const int z = blockIdx.z;
+  const int pr = pids[z];
+  if (!sc[pr].go) return;
+  const LevelV<double> L = f64[z];
+  const LevelV<float> F = f32[z];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int j = blockIdx.y + 1;
+  if (i > L.nx) return;
+  const int o = j * L.pitch + i, of = j * F.pitch + i;
+  if (dir == 0) {
+    F.b[of] = float(L.b[o] * sc[pr].inv);
+    F.x[of] = 0.0f;
+  } else {
+    L.x[o] = sc[pr].rnorm * double(F.x[of]);
+  }
+}
+
 // Dense user arrays <-> FP64 finest planes, batched over one finest side.
+// which: 0 the finest b plane, 1 its x plane, 2 the CG right-hand side B,
+// 3 the CG iterate X.
 __global__ void k_bpack(const LevelV<double>* __restrict__ f64, double* const* __restrict__ src,
-                        int which) {
+                        int which, const BPcg* __restrict__ vec) {
   const int z = blockIdx.z;
   const LevelV<double> L = f64[z];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i >= L.nx) return;
   const double v = src[z][size_t(j) * L.nx + i];
-  (which ? L.x : L.b)[(j + 1) * L.pitch + i + 1] = v;
+  double* dst = which == 0 ? L.b : which == 1 ? L.x : which == 2 ? vec[z].b : vec[z].x;
+  dst[(j + 1) * L.pitch + i + 1] = v;
 }
 
 // x = 0 for problems whose right-hand side is zero (they run no cycle).
+// The iterate (the finest x plane, or the CG iterate X when vec is given).
 __global__ void k_bzero_x(const LevelV<double>* __restrict__ f64, const int* __restrict__ pids,
-                          const Scalars* __restrict__ sc) {
+                          const Scalars* __restrict__ sc, const BPcg* __restrict__ vec) {
   const int z = blockIdx.z;
   if (sc[pids[z]].bnorm2 != 0.0) return;
   const LevelV<double> L = f64[z];
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y + 1;
   if (i > L.nx) return;
-  L.x[j * L.pitch + i] = 0.0;
+  (vec ? vec[z].x : L.x)[j * L.pitch + i] = 0.0;
 }
 
-__global__ void k_bunpack(const LevelV<double>* __restrict__ f64, double* const* __restrict__ dst) {
+__global__ void k_bunpack(const LevelV<double>* __restrict__ f64, double* const* __restrict__ dst,
+                          const BPcg* __restrict__ vec) {
   const int z = blockIdx.z;
   const LevelV<double> L = f64[z];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (i >= L.nx) return;
-  dst[z][size_t(j) * L.nx + i] = L.x[(j + 1) * L.pitch + i + 1];
+  dst[z][size_t(j) * L.nx + i] = (vec ? vec[z].x : L.x)[(j + 1) * L.pitch + i + 1];
 }
 
 // ---------------------------------------------------------------------------
@@ -359,6 +467,7 @@ struct BFine {                   // FP64 finest levels of the problems of one si
   LevelV<double>* f64 = nullptr;
   LevelV<float>* f32 = nullptr;
   double** user = nullptr;       // device array of user pointers (b, x)
+  BPcg* pcg = nullptr;           // the problems' CG planes (BMG_SOLVER_PCG), else null
 };
 
 struct Batch {
@@ -455,6 +564,44 @@ void enqueue_update(Batch* b, cudaStream_t s) {
   count_launch(int(b->fines.size()));
 }
 
+void enqueue_pcg_vec(Batch* b, int what, cudaStream_t s) {
+  for (BFine& f : b->fines)
+    k_bpcg<<<dim3(kPB, f.count), kNT, 0, s>>>(f.f64, f.pcg, f.pids, b->sc, b->partials, what);
+  count_launch(int(b->fines.size()));
+}
+
+void enqueue_pcg_cast(Batch* b, int dir, cudaStream_t s) {
+  for (BFine& f : b->fines)
+    k_bpcg_cast<<<dim3(cdiv(f.n, 128), f.n, f.count), 128, 0, s>>>(f.f64, f.f32, f.pids, b->sc, dir);
+  count_launch(int(b->fines.size()));
+}
+
+// The first residual of PCG (r = B - A X, z = 0) and its stop test.
+void enqueue_pcg_init(Batch* b, cudaStream_t s) {
+  enqueue_pcg_vec(b, BPCG_INIT, s);
+  k_bnorm_final<<<b->nprob, kNT, 0, s>>>(b->partials, b->sc, 1);
+  k_bany<<<1, kNT, 0, s>>>(b->sc, b->nprob, b->handle, 0, b->any);
+  count_launch(2);
+}
+
+// One batched PCG iteration of the active problems: z = M^{-1} r (the FP32
+// batched V-cycle between the casts), r.z and beta, p = z + beta p,
+// q = A p and alpha, x += alpha p and r -= alpha q, the stop test, any.
+void enqueue_pcg_iter(Batch* b, bool use_handle, cudaStream_t s) {
+  enqueue_pcg_cast(b, 0, s);
+  enqueue_bvcycle(b, s);
+  enqueue_pcg_cast(b, 1, s);
+  enqueue_pcg_vec(b, BPCG_RZ, s);
+  k_bpcg_scalar<<<b->nprob, kNT, 0, s>>>(b->partials, b->sc, BPCG_RZ);
+  enqueue_pcg_vec(b, BPCG_P, s);
+  enqueue_pcg_vec(b, BPCG_AP, s);
+  k_bpcg_scalar<<<b->nprob, kNT, 0, s>>>(b->partials, b->sc, BPCG_AP);
+  enqueue_pcg_vec(b, BPCG_XR, s);
+  k_bnorm_final<<<b->nprob, kNT, 0, s>>>(b->partials, b->sc, 1);
+  k_bany<<<1, kNT, 0, s>>>(b->sc, b->nprob, b->handle, use_handle ? 1 : 0, b->any);
+  count_launch(4);
+}
+
 // Pick the fastest tile variant of every class by timing sweeps on the batch
 // (x = 0 and b = 0 after setup, so the timing sweeps change nothing).
 int autotune(Batch* b, cudaStream_t s) {
@@ -502,7 +649,8 @@ int autotune(Batch* b, cudaStream_t s) {
 int build_graph_on(Batch* b, cudaStream_t s);
 
 // The refinement loop as one graph: WHILE(any active) { V-cycle; update;
-// residuals + stop tests + any }.  Recorded on a private stream (the
+// residuals + stop tests + any }, or (BMG_SOLVER_PCG) WHILE(any active) {
+// one PCG iteration }.  Recorded on a private stream (the
 // caller's stream may be the legacy default stream, which cannot capture);
 // recording executes nothing.
 int build_graph(Batch* b) {
@@ -532,9 +680,13 @@ int build_graph_on(Batch* b, cudaStream_t s) {
   if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
       cudaSuccess)
     return BMG_ECUDA;
-  enqueue_bvcycle(b, s);
-  enqueue_update(b, s);
-  enqueue_residuals(b, 1, true, s);
+  if (b->opt.solver == BMG_SOLVER_PCG) {
+    enqueue_pcg_iter(b, true, s);
+  } else {
+    enqueue_bvcycle(b, s);
+    enqueue_update(b, s);
+    enqueue_residuals(b, 1, true, s);
+  }
   cudaGraph_t out = nullptr;
   if (cudaStreamEndCapture(s, &out) != cudaSuccess) return BMG_ECUDA;
   if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return BMG_ECUDA;
@@ -572,6 +724,11 @@ extern "C" int bmg_batch_setup(int nprob, const double* const* k_dev, const int*
     set_last_error("batch setup: only the point smoother is batched");
     return BMG_EINVAL;
   }
+  if (opt.solver == BMG_SOLVER_PCG && (opt.nu1 != opt.nu2 || opt.interp_residual_term)) {
+    set_last_error("batch setup: BMG_SOLVER_PCG needs nu1 == nu2 and interp_residual_term == 0");
+    return BMG_EINVAL;
+  }
+  if (opt.solver != BMG_SOLVER_VCYCLE && opt.solver != BMG_SOLVER_PCG) return BMG_EINVAL;
   opt.precision = BMG_FP32_REFINE;
   Batch* b = new Batch();
   b->nprob = nprob;
@@ -642,7 +799,8 @@ extern "C" int bmg_batch_setup(int nprob, const double* const* k_dev, const int*
   for (auto& x : hc) bytes += al(sizeof(int) * x.c.count) + 3 * al(sizeof(LevelV<float>) * x.c.count);
   for (auto& kv : by_side)
     bytes += al(sizeof(int) * kv.second.size()) + al(sizeof(LevelV<double>) * kv.second.size()) +
-             al(sizeof(LevelV<float>) * kv.second.size()) + al(sizeof(double*) * kv.second.size());
+             al(sizeof(LevelV<float>) * kv.second.size()) + al(sizeof(double*) * kv.second.size()) +
+             al(sizeof(BPcg) * kv.second.size());
   bytes += al(sizeof(Scalars) * nprob) + al(sizeof(double) * kPB * nprob) +
            al(sizeof(BCoarse) * nprob) + al(sizeof(int));
   if (cudaMalloc(&b->arena, bytes) != cudaSuccess) {
@@ -669,14 +827,22 @@ extern "C" int bmg_batch_setup(int nprob, const double* const* k_dev, const int*
     f.count = int(kv.second.size());
     std::vector<LevelV<double>> v64;
     std::vector<LevelV<float>> v32;
+    std::vector<BPcg> vp;
     for (int p : kv.second) {
-      v64.push_back(b->hs[p]->d.back());
-      v32.push_back(b->hs[p]->f.back());
+      const Hierarchy* h = b->hs[p];
+      v64.push_back(h->d.back());
+      v32.push_back(h->f.back());
+      vp.push_back(BPcg{h->pcg_x, h->pcg_b, h->pcg_p, h->pcg_q});
     }
     f.pids = carve<int>(cur, f.count);
     f.f64 = carve<LevelV<double>>(cur, f.count);
     f.f32 = carve<LevelV<float>>(cur, f.count);
     f.user = carve<double*>(cur, f.count);
+    BPcg* pcg_dev = carve<BPcg>(cur, f.count);
+    if (opt.solver == BMG_SOLVER_PCG) {
+      f.pcg = pcg_dev;
+      cudaMemcpyAsync(f.pcg, vp.data(), sizeof(BPcg) * f.count, cudaMemcpyHostToDevice, s);
+    }
     cudaMemcpyAsync(f.pids, kv.second.data(), sizeof(int) * f.count, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(f.f64, v64.data(), sizeof(LevelV<double>) * f.count, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(f.f32, v32.data(), sizeof(LevelV<float>) * f.count, cudaMemcpyHostToDevice, s);
@@ -716,13 +882,17 @@ extern "C" int bmg_batch_solve(bmg_batch* bp, const double* const* b_dev, double
   // pack b and x (batched per finest side)
   std::map<int, std::vector<int>> by_side;
   for (int p = 0; p < b->nprob; ++p) by_side[b->side[p]].push_back(p);
+  const bool pcg = b->opt.solver == BMG_SOLVER_PCG;
   for (int pass = 0; pass < 2; ++pass) {
     for (BFine& f : b->fines) {
       std::vector<double*> ptr;
       for (int p : by_side[f.n]) ptr.push_back(pass == 0 ? const_cast<double*>(b_dev[p]) : x_dev[p]);
       cudaMemcpyAsync(f.user, ptr.data(), sizeof(double*) * ptr.size(), cudaMemcpyHostToDevice, s);
-      k_bpack<<<dim3(cdiv(f.n, 128), f.n, f.count), 128, 0, s>>>(f.f64, f.user, pass);
-      count_launch();
+      const dim3 g(cdiv(f.n, 128), f.n, f.count);
+      // V-cycles: b and x into the finest planes; PCG: b also into B, x into X
+      if (pass == 0 || !pcg) k_bpack<<<g, 128, 0, s>>>(f.f64, f.user, pass, f.pcg);
+      if (pcg) k_bpack<<<g, 128, 0, s>>>(f.f64, f.user, pass == 0 ? 2 : 3, f.pcg);
+      count_launch(pcg && pass == 0 ? 2 : 1);
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return BMG_ECUDA;
   }
@@ -734,15 +904,18 @@ extern "C" int bmg_batch_solve(bmg_batch* bp, const double* const* b_dev, double
   }
   cudaMemcpyAsync(b->sc, b->sc_host, sizeof(Scalars) * b->nprob, cudaMemcpyHostToDevice, s);
   enqueue_residuals(b, 0, false, s);       // ||b||, go = (b != 0)
-  enqueue_residuals(b, 1, false, s);       // first residual and stop test
+  if (pcg)
+    enqueue_pcg_init(b, s);                // r = B - A X and the stop test
+  else
+    enqueue_residuals(b, 1, false, s);     // first residual and stop test
   if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return BMG_ECUDA;
   for (BFine& f : b->fines) {
-    k_bzero_x<<<dim3(cdiv(f.n, 128), f.n, f.count), 128, 0, s>>>(f.f64, f.pids, b->sc);
+    k_bzero_x<<<dim3(cdiv(f.n, 128), f.n, f.count), 128, 0, s>>>(f.f64, f.pids, b->sc, f.pcg);
     count_launch();
     std::vector<double*> ptr;
     for (int p : by_side[f.n]) ptr.push_back(x_dev[p]);
     cudaMemcpyAsync(f.user, ptr.data(), sizeof(double*) * ptr.size(), cudaMemcpyHostToDevice, s);
-    k_bunpack<<<dim3(cdiv(f.n, 128), f.n, f.count), 128, 0, s>>>(f.f64, f.user);
+    k_bunpack<<<dim3(cdiv(f.n, 128), f.n, f.count), 128, 0, s>>>(f.f64, f.user, f.pcg);
     count_launch();
     if (cudaStreamSynchronize(s) != cudaSuccess) return BMG_ECUDA;
   }
