@@ -487,8 +487,8 @@ def run_ours(args, rank, world, local_rank):
 def lognormal_leg(bm, torch, dev, stream, args, n=8191):
     """FP64 V-cycles against FP32 V-cycles inside FP64 refinement, both to
     1e-10 on the 8191^2 log-normal field (setup + solve timed); beside them
-    the r/C interpolation variant and CG preconditioned by a symmetric
-    V(1,1) cycle, both FP64."""
+    the r/C interpolation variant (FP64) and CG preconditioned by a
+    symmetric V(1,1) cycle (FP64 cycle, and FP32 cycle)."""
     pr = inputs.lognormal_problem(n, seed=2)
     k = torch.from_numpy(pr["k"]).to(dev)
     b = torch.from_numpy(pr["b"]).to(dev)
@@ -501,9 +501,12 @@ def lognormal_leg(bm, torch, dev, stream, args, n=8191):
                 ("fp32_refine", dict(precision=bm.BMG_FP32_REFINE)),
                 # the Section 3 interpolation with the r/C term, FP64
                 ("fp64_interp_rc", dict(precision=bm.BMG_FP64, interp_residual_term=1)),
-                # CG preconditioned by one symmetric V(1,1) cycle, FP64
+                # CG preconditioned by one symmetric V(1,1) cycle, FP64, and
+                # with the cycle on the FP32 hierarchy
                 ("fp64_pcg_v11", dict(precision=bm.BMG_FP64, nu1=1, nu2=1,
-                                      solver=bm.BMG_SOLVER_PCG)))
+                                      solver=bm.BMG_SOLVER_PCG)),
+                ("pcg_v11_fp32_cycle", dict(precision=bm.BMG_FP32_REFINE, nu1=1, nu2=1,
+                                            solver=bm.BMG_SOLVER_PCG)))
     for name, kw in variants:
         opts = bm.default_options(max_cycles=500, **kw)
         x = torch.zeros_like(b)
