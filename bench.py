@@ -551,7 +551,9 @@ def paper_workload_leg(bm, torch, dev, stream, nx=16383, ny=1023, r=16.0):
     for name, kw in (("fp64", dict(precision=bm.BMG_FP64)),
                      ("fp32_refine", dict(precision=bm.BMG_FP32_REFINE)),
                      ("fp64_pcg_v11", dict(precision=bm.BMG_FP64, nu1=1, nu2=1,
-                                           solver=bm.BMG_SOLVER_PCG))):
+                                           solver=bm.BMG_SOLVER_PCG)),
+                     ("pcg_v11_fp32_cycle", dict(precision=bm.BMG_FP32_REFINE, nu1=1, nu2=1,
+                                                 solver=bm.BMG_SOLVER_PCG))):
         opts = bm.default_options(**base, **kw)
         x = torch.zeros_like(b)
         times = []
