@@ -1103,12 +1103,16 @@ def adjoint_leg(bm, torch, dev, stream, n=2047, reps=3):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
 
-    def gradient():
+    def gradient(solver="vcycle"):
         th = theta.clone().requires_grad_(True)
-        u = diff_solve(th, b, tol=1e-10, max_cycles=500, adjoint_tol=1e-9, adjoint_max_cycles=200)
+        u = diff_solve(th, b, tol=1e-10, max_cycles=500, adjoint_tol=1e-9, adjoint_max_cycles=200,
+                       solver=solver)
         loss = 0.5 * ((u - u_obs) ** 2).sum()
         loss.backward()
         return th.grad, u.grad_fn
+
+    def gradient_pcg():
+        return gradient("pcg")
 
     opts = bm.default_options(log_coefficients=1, max_cycles=500)
     x = torch.zeros_like(b)
@@ -1121,7 +1125,8 @@ def adjoint_leg(bm, torch, dev, stream, n=2047, reps=3):
         return info
 
     out = {"workload": f"log-normal theta = 2 g (seed 3), {n}x{n}, loss 0.5 ||u - u_obs||^2, tol 1e-10"}
-    for name, fn in (("gradient", gradient), ("forward_fp64", forward)):
+    grads = {}
+    for name, fn in (("gradient", gradient), ("gradient_pcg", gradient_pcg), ("forward_fp64", forward)):
         fn()
         times = []
         for _ in range(reps):
@@ -1133,8 +1138,9 @@ def adjoint_leg(bm, torch, dev, stream, n=2047, reps=3):
             times.append(ev0.elapsed_time(ev1))
         ms = statistics.median(times)
         out[name] = {"ms": ms, "value": n * n / (ms / 1e3), "unit": UNIT}
-        if name == "gradient":
+        if name.startswith("gradient"):
             g, node = res
+            grads[name] = g
             out[name].update(forward_cycles=node.info.cycles, forward_rel_resid=node.info.rel_resid,
                              adjoint_cycles=node.adjoint_info.cycles,
                              adjoint_rel_resid=node.adjoint_info.rel_resid,
@@ -1142,6 +1148,9 @@ def adjoint_leg(bm, torch, dev, stream, n=2047, reps=3):
         else:
             out[name].update(cycles=res.cycles, rel_resid=res.rel_resid)
     out["gradient_over_forward"] = out["gradient"]["ms"] / out["forward_fp64"]["ms"]
+    out["gradient_pcg_over_forward"] = out["gradient_pcg"]["ms"] / out["forward_fp64"]["ms"]
+    gv, gp = grads["gradient"], grads["gradient_pcg"]
+    out["gradient_pcg_max_rel_diff"] = float((gp - gv).abs().max() / gv.abs().max())
     return out
 
 

@@ -16,18 +16,32 @@ smooth vector by up to ~n^2: its FP64 residual floor can sit above the
 forward tolerance (about 1e-10 relative on a 2047^2 log-normal field).  The
 adjoint solve therefore stops at ``adjoint_tol`` or after
 ``adjoint_max_cycles`` cycles, whichever comes first, and uses that iterate.
+
+``solver``: "vcycle" (V(2,1) cycles, Algorithm 1) or "pcg" (CG
+preconditioned by one symmetric V(1,1) cycle) for both solves; A is
+symmetric, so the adjoint solve can use either on the same hierarchy.
 """
 from __future__ import annotations
 
 import torch
 
-from . import BMG_FP64, default_options, setup
+from . import BMG_FP64, BMG_SOLVER_PCG, default_options, setup
+
+
+def _options(solver, max_cycles):
+    if solver == "vcycle":
+        return default_options(precision=BMG_FP64, log_coefficients=1, max_cycles=max_cycles)
+    if solver == "pcg":
+        return default_options(precision=BMG_FP64, log_coefficients=1, max_cycles=max_cycles,
+                               nu1=1, nu2=1, solver=BMG_SOLVER_PCG)
+    raise ValueError(f"solver must be 'vcycle' or 'pcg', got {solver!r}")
 
 
 class BoxMGSolve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, theta, b, tol=1e-12, max_cycles=500, adjoint_tol=1e-12, adjoint_max_cycles=200):
-        opts = default_options(precision=BMG_FP64, log_coefficients=1, max_cycles=max_cycles)
+    def forward(ctx, theta, b, tol=1e-12, max_cycles=500, adjoint_tol=1e-12, adjoint_max_cycles=200,
+                solver="vcycle"):
+        opts = _options(solver, max_cycles)
         h = setup(theta.detach().contiguous(), opts)
         u, info = h.solve(b.detach().contiguous(), tol=tol)
         ctx.h = h
@@ -48,9 +62,11 @@ class BoxMGSolve(torch.autograd.Function):
         h.assemble_backward(u, lam, dtheta)
         h.destroy()
         ctx.h = None
-        return dtheta, lam, None, None, None, None
+        return dtheta, lam, None, None, None, None, None
 
 
-def solve(theta, b, tol=1e-12, max_cycles=500, adjoint_tol=1e-12, adjoint_max_cycles=200):
-    """u = A(exp(theta))^{-1} b, differentiable in theta and b."""
-    return BoxMGSolve.apply(theta, b, tol, max_cycles, adjoint_tol, adjoint_max_cycles)
+def solve(theta, b, tol=1e-12, max_cycles=500, adjoint_tol=1e-12, adjoint_max_cycles=200,
+          solver="vcycle"):
+    """u = A(exp(theta))^{-1} b, differentiable in theta and b; `solver`
+    "vcycle" or "pcg" for the forward and the adjoint solve."""
+    return BoxMGSolve.apply(theta, b, tol, max_cycles, adjoint_tol, adjoint_max_cycles, solver)

@@ -31,14 +31,16 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
 
 
-@pytest.mark.parametrize("n", [127, 255])
-def test_adjoint_gradient_matches_oracle(n):
+@pytest.mark.parametrize("n,solver", [(127, "vcycle"), (255, "vcycle"), (127, "pcg"), (255, "pcg")])
+def test_adjoint_gradient_matches_oracle(n, solver):
+    """Forward and adjoint solves by V(2,1) cycles or by CG with the
+    symmetric V(1,1) preconditioner: the same oracle gradient."""
     pr = inputs.adjoint_problem(n, seed=3)
     u_obs = O.direct_solve(np.exp(pr["theta_obs"]), pr["b"]) + 1e-3 * pr["eps"]
     g_o, u_o, lam_o = O.adjoint_gradient(pr["theta"], pr["b"], u_obs)
     theta = dev(pr["theta"]).requires_grad_(True)
     b = dev(pr["b"]).requires_grad_(True)
-    u = diff_solve(theta, b, tol=1e-12)
+    u = diff_solve(theta, b, tol=1e-12, solver=solver)
     loss = 0.5 * ((u - dev(u_obs)) ** 2).sum()
     loss.backward()
     g = theta.grad.cpu().numpy()
