@@ -164,6 +164,13 @@ int bmg_setup(const double *k_dev, int nx, int ny, const bmg_options *opt,
  * test on the updated r, z = M^{-1} r, beta = r.z' / r.z, p = z + beta p;
  * M^{-1} is one V(nu, nu) cycle from zero), max_cycles capping the
  * iterations and info->cycles counting them.
+ * FP64 V-cycles with point smoothing on a prescaled finest level (nx >= 1024)
+ * take the residual after a cycle inside the next cycle's first fine sweep:
+ * after the cycle's last sweep one colour satisfies its equation exactly, so
+ * that sweep's second colour phase sees the whole residual, evaluated as
+ * C (b/C + sum (a/C) x_nb - x) with the level's prescaled coefficients.  The
+ * output of that sweep is dropped when the loop stops (one extra sweep per
+ * solve); the iterate is the same bits as without it.
  * b_dev: dense (ny, nx) float64, device.  x_dev: dense (ny, nx) float64,
  * device; on entry the initial guess, on exit the solution.  info may be
  * NULL.  Synchronises the stream (the cycle count and residual return to the
@@ -471,7 +478,10 @@ enum { BMG_PROF_FINE_SMOOTH = 1, BMG_PROF_FINE_RESID = 2, BMG_PROF_FINE_INTERP =
  * records; mask 0 stops recording.  Classes: fine-level sweeps (one bracket
  * per full sweep), fine-level residual, fine-level interpolation, the
  * persistent coarse kernel, all other levels' full-grid work of one V-cycle,
- * the convergence norm, one whole V-cycle, and the conjugate-gradient vector
+ * the convergence norm (where the stop test is taken inside the next
+ * cycle's first fine sweep: that sweep and the stop test, which the
+ * fine-sweep class then leaves out), one whole V-cycle, and the
+ * conjugate-gradient vector
  * kernels of BMG_SOLVER_PCG (A p with p.q, the x/r update with r.r, r.z with
  * the scalars, and p = z + beta p; one bracket per iteration). */
 int bmg_profile_set(int mask);

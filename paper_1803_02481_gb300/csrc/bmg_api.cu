@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <tuple>
 #include <utility>
 #include <cstdarg>
 #include <cstdio>
@@ -227,6 +228,7 @@ int setup_impl(const double* k, int nx, int ny, const bmg_options* opt_in, cudaS
 
   Hierarchy* h = new (std::nothrow) Hierarchy();
   if (!h) return BMG_ENOMEM;
+  if (const char* e = std::getenv("BMG_FUSED_NORM")) h->fused_norm_allowed = e[0] != '0';
   h->nx = nx;
   h->ny = ny;
   h->opt = opt;
@@ -385,7 +387,7 @@ const SweepMaps<float>* level_maps<float>(const Hierarchy* h, int l) {
 
 template <typename T>
 void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* dlev, int thr,
-                    cudaStream_t s, int top) {
+                    cudaStream_t s, int top, bool skip_first) {
   const int L = h->L;
   // a cycle from level `top` down (the finest unless given): the levels
   // below the schedule's threshold still run in the persistent kernel
@@ -414,7 +416,7 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
     NvtxRange r("restrict_leg", l);
     const bool nine = l != L - 1;
     if (nine) prof_begin(BMG_PROF_LEVELS, s);
-    for (int k = 0; k < nu1; ++k) sweep(l, false);
+    for (int k = skip_first && l == top ? 1 : 0; k < nu1; ++k) sweep(l, false);
     if (!rc && rr_fused(nine, sizeof(T) == 8)) {
       launch_resid_restrict<T>(lv[l], nine, lv[l - 1], s);
     } else {
@@ -444,9 +446,47 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
 }
 
 template void enqueue_vcycle<double>(Hierarchy*, std::vector<LevelV<double>>&,
-                                     const LevelV<double>*, int, cudaStream_t, int);
+                                     const LevelV<double>*, int, cudaStream_t, int, bool);
 template void enqueue_vcycle<float>(Hierarchy*, std::vector<LevelV<float>>&, const LevelV<float>*,
-                                    int, cudaStream_t, int);
+                                    int, cudaStream_t, int, bool);
+
+// Stop test inside the next cycle's first fine sweep.  The V(nu1, nu2)
+// cycle's last fine sweep is a post-smoothing sweep (reverse colour order),
+// and the next cycle starts with a pre-smoothing sweep of the same level, so
+// that sweep can sum the residual of the iterate it reads
+// (launch_sweep_pre_norm).  The solve loop then runs as: stop test of x0
+// (separate norm pass), first pre-sweep; WHILE(go) { rest of the cycle, the
+// next cycle's first pre-sweep with the residual of the cycle's result, stop
+// test }.  On exit the result is the iterate that sweep read; its output is
+// dropped.  Applies to FP64 V-cycles with point smoothing whose finest level
+// is prescaled and swept outside the persistent coarse kernel, with nu1 and
+// nu2 >= 1 (environment BMG_FUSED_NORM=0 at setup turns it off).
+static bool fused_norm_on(const Hierarchy* h) {
+  const int L = h->L;
+  const SweepMaps<double>* m = level_maps<double>(h, L - 1);
+  return h->fused_norm_allowed && h->opt.solver == BMG_SOLVER_VCYCLE && h->opt.precision == BMG_FP64 &&
+         h->opt.smoother == BMG_SMOOTH_POINT && h->opt.nu1 >= 1 && h->opt.nu2 >= 1 &&
+         h->threshold < L && m && m->pre;
+}
+
+// The finest level's first pre-smoothing sweep of a cycle: plain, or with
+// the stop test (the sweep summing the residual, then the stop test on its
+// partials; timed as the norm class, not as a fine sweep).
+static void fine_presweep(Hierarchy* h, cudaStream_t s, bool with_norm, bool in_graph) {
+  LevelV<double>& F = h->d.back();
+  const SweepMaps<double>* m = level_maps<double>(h, h->L - 1);
+  if (with_norm) {
+    prof_begin(BMG_PROF_NORM, s);
+    const int n = launch_sweep_pre_norm(F, m, F.x, F.x2, h->partials, h->npartials, s);
+    launch_norm_final(h, s, in_graph, n);
+    prof_end(BMG_PROF_NORM, s);
+  } else {
+    prof_begin(BMG_PROF_FINE_SMOOTH, s);
+    launch_sweep<double>(F, false, false, F.x, F.x2, s, m);
+    prof_end(BMG_PROF_FINE_SMOOTH, s);
+  }
+  std::swap(F.x, F.x2);
+}
 
 static int read_scalars(Hierarchy* h, cudaStream_t s) {
   BMG_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
@@ -462,7 +502,15 @@ static int build_solve_graph(Hierarchy* h) {
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return BMG_ECUDA;
   const bool fp32 = h->opt.precision == BMG_FP32_REFINE;
   const bool pcg = h->opt.solver == BMG_SOLVER_PCG;
+  const bool fused = !pcg && !fp32 && fused_norm_on(h);
   LevelV<double>& F = h->d.back();
+  // recording swaps the levels' iterate buffers as the launches would; the
+  // roles are put back afterwards (with the fused stop test the solve's
+  // result is in the buffer its input was packed into)
+  std::vector<std::pair<double*, double*>> roles64;
+  std::vector<std::pair<float*, float*>> roles32;
+  for (auto& V : h->d) roles64.emplace_back(V.x, V.x2);
+  for (auto& V : h->f) roles32.emplace_back(V.x, V.x2);
   // [prologue: first residual and stop test] WHILE(go) { body }
   auto prologue = [&] {
     if (pcg) {
@@ -474,6 +522,7 @@ static int build_solve_graph(Hierarchy* h) {
       launch_refine_residual(h, 0.0, s, true);
     } else {
       launch_fine_norm(h, F.x, F.b, 1, 0.0, s, true);
+      if (fused) fine_presweep(h, s, false, true);
     }
   };
   auto body = [&] {
@@ -489,6 +538,9 @@ static int build_solve_graph(Hierarchy* h) {
       enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s);
       launch_refine_update(h, s);
       launch_refine_residual(h, 0.0, s, true);
+    } else if (fused) {
+      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s, -1, true);
+      fine_presweep(h, s, true, true);
     } else {
       enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
       launch_fine_norm(h, F.x, F.b, 1, 0.0, s, true);
@@ -532,6 +584,8 @@ static int build_solve_graph(Hierarchy* h) {
     if (cudaGraphInstantiate(&h->gexec, h->graph, 0) != cudaSuccess) break;
     rc = BMG_OK;
   } while (0);
+  for (size_t l = 0; l < h->d.size(); ++l) std::tie(h->d[l].x, h->d[l].x2) = roles64[l];
+  for (size_t l = 0; l < h->f.size(); ++l) std::tie(h->f[l].x, h->f[l].x2) = roles32[l];
   cudaStreamDestroy(s);
   if (rc != BMG_OK) {
     cudaGetLastError();
@@ -628,10 +682,25 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
       if (info) *info = bmg_info{0, h->threshold, 0.0, h->setup_ms, now_ms() - t0, h->coarse_ctas};
       return BMG_OK;
     }
-    while (h->sc_host->go) {
-      enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
-      launch_fine_norm(h, F.x, F.b, 1, tol, s);
-      if ((rc = read_scalars(h, s))) return rc;
+    if (fused_norm_on(h)) {
+      // the loop of build_solve_graph, step by step
+      if (h->sc_host->go) {
+        fine_presweep(h, s, false, false);
+        while (h->sc_host->go) {
+          enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s, -1, true);
+          fine_presweep(h, s, true, false);
+          if ((rc = read_scalars(h, s))) break;
+        }
+        // the result is the input of the last sweep
+        std::swap(F.x, F.x2);
+        if (rc) return rc;
+      }
+    } else {
+      while (h->sc_host->go) {
+        enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+        launch_fine_norm(h, F.x, F.b, 1, tol, s);
+        if ((rc = read_scalars(h, s))) return rc;
+      }
     }
   } else {
     if ((rc = read_scalars(h, s))) return rc;

@@ -456,9 +456,9 @@ void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s, bool in_gr
   count_launch(2);
 }
 
-void launch_norm_final(Hierarchy* h, cudaStream_t s, bool in_graph) {
-  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, 1, h->hist, h->cond,
-                                          in_graph ? 1 : 0);
+void launch_norm_final(Hierarchy* h, cudaStream_t s, bool in_graph, int n) {
+  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, n > 0 ? n : h->npartials, h->sc, 1, h->hist,
+                                          h->cond, in_graph ? 1 : 0);
   count_launch();
 }
 

@@ -336,6 +336,8 @@ struct Hierarchy {
   cudaGraphExec_t gexec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   int graph_state = 0;               // 0 not built, 1 ready, -1 unavailable
+  bool fused_norm_allowed = true;    // stop test inside the next fine sweep
+                                     // where it applies (BMG_FUSED_NORM at setup)
   void* arena = nullptr;
   size_t arena_bytes = 0;
   double setup_ms = 0.0;
@@ -427,6 +429,15 @@ bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m);
 template <typename T>
 void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* xout,
                   cudaStream_t s, const SweepMaps<T>* maps = nullptr);
+// The prescaled level's red-black sweep in the pre-smoothing colour order
+// that also sums the stop test's squared residual of its input iterate into
+// partials[0 .. grid) (grid <= nmax, returned).  Valid only when the sweep
+// before it on this level was a post-smoothing sweep (reverse colour order)
+// and nothing changed the iterate since; returns 0 and launches nothing when
+// the level has no prescaled TMA maps for xin.
+int launch_sweep_pre_norm(const LevelV<double>& L, const SweepMaps<double>* maps,
+                          const double* xin, double* xout, double* partials, int nmax,
+                          cudaStream_t s);
 template <typename T>
 void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* levels, int threshold,
                          cudaStream_t s);
@@ -460,10 +471,10 @@ void launch_fine_norm(Hierarchy* h, const double* x, const double* b, int what,
 // into the FP32 fine RHS; zero the FP32 fine x.
 void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s, bool in_graph = false);
 void launch_refine_update(Hierarchy* h, cudaStream_t s);
-// Sums h->partials (npartials squared-residual partials) into the stop test:
+// Sums h->partials (the first n, else npartials, squared-residual partials) into the stop test:
 // rnorm2, rel, history, go, cycles; in a graph it also sets the WHILE
 // condition.
-void launch_norm_final(Hierarchy* h, cudaStream_t s, bool in_graph);
+void launch_norm_final(Hierarchy* h, cudaStream_t s, bool in_graph, int n = 0);
 
 // Preconditioned conjugate gradients (bmg_pcg.cu).  init: r = b - A x, z = 0,
 // ||r||^2 and the stop test; ap: q = A p, p.q, alpha; xr: x += alpha p,
@@ -479,10 +490,11 @@ void launch_pcg_p(Hierarchy* h, cudaStream_t s);
 // level, the FP32 cycle, z = ||r|| e cast back).
 void launch_pcg_precond(Hierarchy* h, cudaStream_t s);
 
-// One V-cycle of the FP64 (d) or FP32 (f) hierarchy (bmg_api.cu).
+// One V-cycle of the FP64 (d) or FP32 (f) hierarchy (bmg_api.cu);
+// skip_first: the top level's first pre-smoothing sweep was already issued.
 template <typename T>
 void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* dlev, int thr,
-                    cudaStream_t s, int top = -1);
+                    cudaStream_t s, int top = -1, bool skip_first = false);
 
 void launch_assemble_backward(const double* k, const double* u, const double* lam,
                               double* g, int nx, int ny, cudaStream_t s);

@@ -243,12 +243,13 @@ bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m) {
 // Blocks of a TMA sweep shape resident per SM (at most MINB), measured once;
 // first called from prepare_sweep_kernels, after the shared-memory opt-in and
 // before any graph capture.
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false>
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false,
+          bool NRM = false>
 static int tma_resident() {
   static const int r = [] {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE>, NT,
+            &n, k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE, NRM>, NT,
             TmaTile<T, NINE, TX, TY, NSTAGE, PRE>::SMEM) != cudaSuccess ||
         n < 1)
       n = 1;
@@ -270,15 +271,16 @@ static void launch_tma_shape(const LevelV<T>& L, const SweepMaps<T>& m, const CU
   const CUtensorMap& msw = NINE ? m.sw : m.b;
   const CUtensorMap& mnw = NINE ? m.nw : m.b;
   k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE><<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(
-      mx, m.ic, m.w, m.s, m.b, msw, mnw, L, xout, order, m.err);
+      mx, m.ic, m.w, m.s, m.b, msw, mnw, L, xout, order, m.err, nullptr, nullptr);
 }
 
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false>
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false,
+          bool NRM = false>
 static void allow_tma_smem() {
-  cudaFuncSetAttribute(k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE>,
+  cudaFuncSetAttribute(k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE, NRM>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                        int(TmaTile<T, NINE, TX, TY, NSTAGE, PRE>::SMEM));
-  tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE>();
+  tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE, NRM>();
 }
 
 // The prescaled red-black sweep (FP64, 5-point): x, b/C, W/C, S/C, E/C, N/C.
@@ -290,7 +292,22 @@ static void launch_tma_pre(const LevelV<double>& L, const SweepMaps<double>& m,
   const int cap = sm_count() * tma_resident<double, false, TX, TY, NT, MINB, NSTAGE, true>();
   k_sweep_tma<double, false, TX, TY, NT, MINB, NSTAGE, true>
       <<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(mx, m.pb, m.pw, m.ps, m.pe, m.pn, m.pn, L,
-                                                        xout, order, m.err);
+                                                        xout, order, m.err, nullptr, nullptr);
+}
+
+// The same sweep in the pre-smoothing colour order with the fused residual
+// (NRM); returns its grid, the number of partials written.
+template <int TX, int TY, int NT, int MINB, int NSTAGE>
+static int launch_tma_pre_norm(const LevelV<double>& L, const SweepMaps<double>& m,
+                               const CUtensorMap& mx, double* xout, double* partials, int nmax,
+                               cudaStream_t s) {
+  using G = TmaTile<double, false, TX, TY, NSTAGE, true>;
+  const int ntiles = ((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
+  const int cap = sm_count() * tma_resident<double, false, TX, TY, NT, MINB, NSTAGE, true, true>();
+  const int grid = std::min(std::min(ntiles, cap), nmax);
+  k_sweep_tma<double, false, TX, TY, NT, MINB, NSTAGE, true, true><<<grid, NT, G::SMEM, s>>>(
+      mx, m.pb, m.pw, m.ps, m.pe, m.pn, m.pn, L, xout, rb_order(false), m.err, L.C, partials);
+  return grid;
 }
 
 #define BMG_TMA_PRE_DISPATCH(K, BODY)      \
@@ -365,6 +382,20 @@ static void launch_sweep_tma(const LevelV<T>& L, const SweepMaps<T>& m, bool rev
 }
 
 
+int launch_sweep_pre_norm(const LevelV<double>& L, const SweepMaps<double>* maps,
+                          const double* xin, double* xout, double* partials, int nmax,
+                          cudaStream_t s) {
+  if (!maps || !maps->pre || nmax < 1 || (xin != maps->xp && xin != maps->x2p)) return 0;
+  const CUtensorMap& mx = xin == maps->xp ? maps->x : maps->x2;
+  int grid = 0;
+#define BMG_TMA_PRE_NORM_LAUNCH(TX, TY, NT, MB, NS) \
+  grid = launch_tma_pre_norm<TX, TY, NT, MB, NS>(L, *maps, mx, xout, partials, nmax, s)
+  BMG_TMA_PRE_DISPATCH(pre_cfg_index(), BMG_TMA_PRE_NORM_LAUNCH);
+#undef BMG_TMA_PRE_NORM_LAUNCH
+  count_launch();
+  return grid;
+}
+
 template <typename T>
 void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* xout,
                   cudaStream_t s, const SweepMaps<T>* maps) {
@@ -430,6 +461,10 @@ void prepare_sweep_kernels() {
 #define BMG_TMA_PRE_ALLOW(TX, TY, NT, MB, NS) allow_tma_smem<double, false, TX, TY, NT, MB, NS, true>()
     BMG_TMA_PRE_DISPATCH(pre_cfg_index(), BMG_TMA_PRE_ALLOW);
 #undef BMG_TMA_PRE_ALLOW
+#define BMG_TMA_PRE_NORM_ALLOW(TX, TY, NT, MB, NS) \
+  allow_tma_smem<double, false, TX, TY, NT, MB, NS, true, true>()
+    BMG_TMA_PRE_DISPATCH(pre_cfg_index(), BMG_TMA_PRE_NORM_ALLOW);
+#undef BMG_TMA_PRE_NORM_ALLOW
     sm_count();
     encode_tiled();
     return true;

@@ -35,6 +35,18 @@
 // Every wait on an mbarrier gives up after one second: the block then sets
 // DEV_TIMEOUT in the error word, waits (again bounded) for its copies in
 // flight and returns.
+//
+// Stop-test residual inside a sweep (NRM, prescaled red-black levels).  Let
+// the previous sweep of the level end with colour c, and nothing change the
+// iterate since.  Then every point of c satisfies its prescaled equation
+// exactly: recomputing its update from the same neighbours gives the same
+// bits, so C (x_new - x_old) = 0 there.  A sweep whose phases are
+// (c, other colour) therefore leaves c unchanged in its first phase, and in
+// its second phase C (x_new - x_old) at each point is that point's residual
+// b - A x of the iterate before the sweep, evaluated in the prescaled form
+// C (b/C + sum_X (a_X/C) x_X - x).  The sweep sums its square over the
+// tile interiors (every point once) into one partial per block; C is read
+// from global memory before the tile's copies are waited for.
 #pragma once
 
 #include <cuda.h>
@@ -151,18 +163,28 @@ struct TmaTile {
 enum TmaPlane { TP_X = 0, TP_IC, TP_W, TP_S, TP_B, TP_SW, TP_NW };
 
 // PRE: the level is prescaled (5-point only); the seven map parameters then
-// carry x, b/C, W/C, S/C, E/C, N/C and an unused one.
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false>
+// carry x, b/C, W/C, S/C, E/C, N/C and an unused one.  NRM (with PRE): the
+// second colour phase also sums (C (x_new - x_old))^2, C read from `cdiag`,
+// into nrm[blockIdx.x].
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false,
+          bool NRM = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_sweep_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mic,
                 const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap ms,
                 const __grid_constant__ CUtensorMap mb, const __grid_constant__ CUtensorMap msw,
                 const __grid_constant__ CUtensorMap mnw, LevelV<T> L, T* __restrict__ xout,
-                unsigned order, int* __restrict__ err) {
+                unsigned order, int* __restrict__ err, const T* __restrict__ cdiag,
+                double* __restrict__ nrm) {
   using namespace tma_detail;
   static_assert(!(PRE && NINE), "prescaled levels are 5-point");
+  static_assert(!NRM || PRE, "the fused residual is taken on prescaled levels");
   using G = TmaTile<T, NINE, TX, TY, NSTAGE, PRE>;
   constexpr int BW = G::BW, HA = G::HA, HY = G::HY, PL = G::PLANE, NPH = G::NPH;
+  // NRM: the last phase relaxes the tile interior; each of its two
+  // sub-lattices has (TY / 2) x (TX / 2) points, at most KU per thread
+  constexpr int QX = TX / 2, NQ = QX * (TY / 2), KU = (NQ + NT - 1) / NT;
+  const unsigned last_mask = (order >> (4 * (NPH - 1))) & 0xFu;
+  double nacc = 0.0;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[2];
   const int nx = L.nx, ny = L.ny, p = L.pitch;
@@ -211,6 +233,23 @@ __global__ void __launch_bounds__(NT, MINB)
     const unsigned parity = unsigned(it / NSTAGE) & 1u;
     const int tn = t + gridDim.x;
     if (NSTAGE == 2 && tid == 0 && tn < ntiles) issue(s ^ 1, tn);
+    const int bx = t % ntx, by = t / ntx;
+    const int i0 = bx * TX + 1, j0 = by * TY + 1;
+    // NRM: C at this thread's points of the last phase (sub-lattice sl,
+    // u-th point), zero outside the plane
+    T cpre[NRM ? 4 * KU : 1];
+    if (NRM) {
+#pragma unroll
+      for (int sl = 0; sl < 4; ++sl) {
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+          const int q = tid + u * NT;
+          const int i = i0 + (sl & 1) + 2 * (q % QX), j = j0 + (sl >> 1) + 2 * (q / QX);
+          const bool in = (last_mask & (1u << sl)) && q < NQ && i <= nx && j <= ny;
+          cpre[sl * KU + u] = in ? __ldg(cdiag + size_t(j) * p + i) : T(0);
+        }
+      }
+    }
     const bool ok = mbar_wait_bounded(&bar[s], parity);
     if (!__syncthreads_and(ok)) {
       if (tid == 0) {
@@ -230,13 +269,36 @@ __global__ void __launch_bounds__(NT, MINB)
     const T* const sb = sx + TP_B * PL;
     const T* const ssw = sx + TP_SW * PL;
     const T* const snw = sx + TP_NW * PL;
-    const int bx = t % ntx, by = t / ntx;
-    const int i0 = bx * TX + 1, j0 = by * TY + 1;
     // Shared cell (r, c) holds domain point (i0 + c - HA, j0 + r - HY).  With
     // TX, TY, HA and HY even, the 0-based domain parities of (r, c) are
     // (r & 1, c & 1).  Phase k is relaxed on the tile grown by (gx, gy).
 #pragma unroll
     for (int k = 0; k < NPH; ++k) {
+      if (NRM && k == NPH - 1) {
+        // the last phase with the residual of the points it updates
+#pragma unroll
+        for (int sl = 0; sl < 4; ++sl) {
+          if (!(last_mask & (1u << sl))) continue;
+#pragma unroll
+          for (int u = 0; u < KU; ++u) {
+            const int q = tid + u * NT;
+            const int c = HA + (sl & 1) + 2 * (q % QX), r = HY + (sl >> 1) + 2 * (q / QX);
+            if (q >= NQ || unsigned(i0 + c - HA - 1) >= unsigned(nx) ||
+                unsigned(j0 + r - HY - 1) >= unsigned(ny))
+              continue;
+            const int o = r * BW + c;
+            T* xp = sx + o;
+            const T xo = *xp;
+            const T xn = gs_pre_apply<T>(sic[o], sw[o], sb[o], ss[o], ssw[o],
+                                         [&](int dx, int dy) { return xp[dx + dy * BW]; });
+            const double rv = double(cpre[sl * KU + u]) * double(xn - xo);
+            nacc = fma(rv, rv, nacc);
+            *xp = xn;
+          }
+        }
+        __syncthreads();
+        continue;
+      }
       const unsigned mask = (order >> (4 * k)) & 0xFu;
       const int gx = colour_grow_x(NPH, k), gy = colour_grow_y(NPH, k);
       const int r0 = HY - gy, r1 = HY + TY + gy;
@@ -300,6 +362,19 @@ __global__ void __launch_bounds__(NT, MINB)
     fence_proxy_async();
     __syncthreads();
     if (NSTAGE == 1 && tid == 0 && tn < ntiles) issue(0, tn);
+  }
+  if (NRM) {
+    // fixed reduction tree: warps, then warp sums in order
+    __shared__ double wsum[NT / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, off);
+    if ((tid & 31) == 0) wsum[tid >> 5] = nacc;
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0;
+      for (int w = 0; w < NT / 32; ++w) a += wsum[w];
+      nrm[blockIdx.x] = a;
+    }
   }
 }
 

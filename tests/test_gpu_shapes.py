@@ -10,7 +10,8 @@ restriction run as one kernel.  The defaults are covered by the oracle parity
 tests; here each other entry runs in a subprocess on a grid that puts every
 level through the full-grid kernels (threshold 1), with ragged tiles on every
 level, and its iterates must equal the default's bit for bit, in FP64 and in
-FP32 refinement.
+FP32 refinement (and its stop-test residuals too, except where the prescaled
+sweep sums them: there another tile shape changes only the order of the sum).
 """
 import json
 import os
@@ -80,7 +81,14 @@ def test_every_sweep_shape_gives_identical_iterates(tmp_path):
     for name, env in SETTINGS:
         got, meta = run_child(tmp_path, name, env)
         for tag in ("fp64", "fp32"):
-            assert meta[tag] == ref_meta[tag], (name, tag, meta[tag], ref_meta[tag])
+            if name.startswith("pre") and tag == "fp64":
+                # the stop test is summed inside the prescaled sweep, per tile
+                # and block: another tile shape adds the same squares in
+                # another order
+                assert meta[tag][0] == ref_meta[tag][0], (name, meta[tag], ref_meta[tag])
+                assert abs(meta[tag][1] - ref_meta[tag][1]) <= 1e-13 * ref_meta[tag][1]
+            else:
+                assert meta[tag] == ref_meta[tag], (name, tag, meta[tag], ref_meta[tag])
             assert np.array_equal(got[tag], ref[tag]), (name, tag)
     # the standard FP64 operator through the other 5-point shapes
     for k in (1, 2):
