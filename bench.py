@@ -58,6 +58,21 @@ SWEEP_DRAM_BYTES_PER_UNKNOWN = {
 }
 
 
+def extended_residual(st, x, b):
+    """||b - A x|| / ||b|| of a 5-point level (planes C, W, S as the library
+    stores them: A x = C x - W x_w - W(i+1) x_e - S x_s - S(j+1) x_n) with
+    every FP64 value taken as exact and the arithmetic in long double."""
+    ld = np.longdouble
+    c, w, s = (st[n].astype(ld) for n in ("C", "W", "S"))
+    xl = x.astype(ld)
+    r = b.astype(ld) - c * xl
+    r[:, 1:] += w[:, 1:] * xl[:, :-1]
+    r[:, :-1] += w[:, 1:] * xl[:, 1:]
+    r[1:, :] += s[1:, :] * xl[:-1, :]
+    r[:-1, :] += s[1:, :] * xl[1:, :]
+    return float(np.sqrt(np.sum(r * r)) / np.sqrt(np.sum(b.astype(ld) ** 2)))
+
+
 def aggregate(torch, ms, units, world, device):
     """Whole-job timing across ranks: the slowest rank's time (MAX over
     ranks) and the units all ranks processed divided by it.  Each rank runs
@@ -364,9 +379,18 @@ def run_ours(args, rank, world, local_rank):
     ms, value = aggregate(torch, ms, n_fine * args.steps, world, dev)
     info = infos[-1]
     # the returned iterate's residual by a separate pass over the unscaled
-    # operator (the stop test itself may be summed inside the prescaled sweep)
+    # operator (the stop test itself may be summed inside the prescaled
+    # sweep), and in extended precision on the host with the library's own
+    # fine operator (FP64 values taken as exact)
     nrm = bm.residual_norm_noalloc(k, x, b, stream=stream).cpu().numpy()
     rel_check = float(nrm[0] / nrm[1]) if nrm[1] > 0 else 0.0
+    rel_ext = None
+    if rank == 0 and not args.quick:
+        hh = bm.setup(k, opts, stream=stream)
+        stc = hh.level_stencil(hh.nlevels - 1)
+        hh.destroy()
+        rel_ext = extended_residual(stc, x.cpu().numpy(), b.cpu().numpy())
+        del stc
 
     # FP64 vs FP32 + refinement on the log-normal 8191^2 field (its own
     # workload: smooth k = exp(2 g), correlation 32 cells), solved to 1e-10;
@@ -476,6 +500,7 @@ def run_ours(args, rank, world, local_rank):
             "config": dict(workload, nx=args.n, ny=args.n, precision=args.precision,
                            l2="inputs and hierarchy larger than L2", parallelism=f"replicas{world}"),
             "cycles": info.cycles, "rel_resid": info.rel_resid, "rel_resid_separate_pass": rel_check,
+            "rel_resid_extended_precision": rel_ext,
             "threshold": info.threshold,
             "coarse_ctas": info.coarse_ctas, "unknown_cycles_per_s": value * info.cycles,
             "setup_ms": info.setup_ms, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,

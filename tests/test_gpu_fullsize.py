@@ -16,7 +16,9 @@ evaluation of ||b - A x|| / ||b|| and the GPU's (with fused multiply-adds)
 are two roundings of the same quantity, apart by about eps ||(|A| |x|)|| /
 ||b||, which on these grids reaches ~1e-10 (the C2 field's residual floor is
 6e-10): the oracle's value may exceed tol, and differ from the reported
-one, by at most 0.2 tol.
+one, by at most 0.2 tol.  For the C2 solve the residual is also evaluated in
+extended precision (long double), which decides whether the iterate meets
+the tolerance.
 """
 import numpy as np
 import pytest
@@ -160,6 +162,16 @@ def test_c2_solve_satisfies_the_stop_test_against_the_oracle_operator(c2):
         st_abs[d] = -st[d]                       # |A| |x| = C |x| + sum_X a_X |x_X|
     floor = np.finfo(np.float64).eps * np.linalg.norm(O.apply(st_abs, np.abs(xn))) / np.linalg.norm(pr["b"])
     assert floor > 1e-10, floor
+    # The same residual in extended precision (the FP64 iterate and FP64
+    # operator taken as exact): the solve meets the tolerance exactly, and
+    # the stop test's value (summed inside the prescaled fine sweep) is within
+    # the FP64 evaluation noise of it
+    ld = np.longdouble
+    assert np.finfo(ld).eps < 1e-18
+    rl = O.residual({d: v.astype(ld) for d, v in st.items()}, xn.astype(ld), pr["b"].astype(ld))
+    exact = float(np.sqrt(np.sum(rl * rl)) / ld(np.linalg.norm(pr["b"])))
+    assert exact <= 1e-9, exact
+    assert abs(info.rel_resid - exact) <= 0.1 * exact, (info.rel_resid, exact, rel)
 
 
 @pytest.mark.parametrize("nx,ny", [(16383, 1023), (9088, 568)])
