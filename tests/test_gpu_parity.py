@@ -841,33 +841,38 @@ def test_smoother_option_is_checked():
     assert e.value.code == bm.BMG_EINVAL
 
 
-@pytest.mark.parametrize("stream_launched", [False, True])
-def test_stop_test_fused_into_the_next_fine_sweep(monkeypatch, stream_launched):
+@pytest.mark.parametrize("stream_launched,nu", [(False, (2, 1)), (True, (2, 1)), (False, (1, 1)),
+                                                (True, (3, 2)), (False, (0, 1)), (False, (1, 0))])
+def test_stop_test_fused_into_the_next_fine_sweep(monkeypatch, stream_launched, nu):
     """On a prescaled finest level (nx >= 1024) the residual after a cycle is
     summed inside the next cycle's first fine sweep (after the reverse-order
     post-smoothing sweep one colour satisfies its equation exactly), and that
     sweep's output is dropped when the loop stops.  The iterate must be the
     same bits as with the separate norm pass, cycle count and residual
     history equal to rounding, and the reported residual that of the
-    oracle's operator on the returned iterate."""
+    oracle's operator on the returned iterate.  Cycles V(nu1, nu2) with
+    nu1 = 1 (the sweep with the residual is the only pre-sweep), more sweeps,
+    and nu1 or nu2 = 0 (no fusion: the separate pass)."""
     name = "wide2047x127"
     pr = problem(name)
     b = dev(pr["b"])
+    fused = nu[0] >= 1 and nu[1] >= 1
     out = {}
     for mode in ("0", "1"):
         monkeypatch.setenv("BMG_FUSED_NORM", mode)
         for cap, tol in ((5, 1e-300), (400, 1e-10)):
-            hg = gpu_setup(name, max_cycles=cap)
+            hg = gpu_setup(name, max_cycles=cap, nu1=nu[0], nu2=nu[1])
             if stream_launched:
                 bm.profile_set(("norm", "fine_smooth"))
             try:
                 x, info = hg.solve(b, tol=tol, allow_noconv=True)
                 if stream_launched:
-                    # fused: the prologue's sweep and nu1 - 1 + nu2 = 2 sweeps
-                    # per cycle are plain; the norm class holds the fused
-                    # sweeps (one per cycle) and the passes for ||b|| and r(x0)
-                    c = info.cycles
-                    assert bm.profile_read("fine_smooth")[0] == (1 + 2 * c if mode == "1" else 3 * c)
+                    # fused: the prologue's sweep and nu1 - 1 + nu2 sweeps per
+                    # cycle are plain; the norm class holds the fused sweeps
+                    # (one per cycle) and the passes for ||b|| and r(x0)
+                    c, per = info.cycles, nu[0] + nu[1]
+                    want = 1 + (per - 1) * c if mode == "1" and fused else per * c
+                    assert bm.profile_read("fine_smooth")[0] == want
                     assert bm.profile_read("norm")[0] == c + 2
             finally:
                 bm.profile_set(())
@@ -884,4 +889,4 @@ def test_stop_test_fused_into_the_next_fine_sweep(monkeypatch, stream_launched):
         rel = np.linalg.norm(O.residual(st, x1.cpu().numpy(), pr["b"])) / np.linalg.norm(pr["b"])
         assert abs(i1.rel_resid - rel) <= 1e-6 * rel + 2e-15, (i1.rel_resid, rel)
     assert out["1", 5][1].cycles == 5
-    assert out["1", 400][1].rel_resid <= 1e-10
+    assert out["1", 400][1].rel_resid <= 1e-10 or nu == (1, 0)
