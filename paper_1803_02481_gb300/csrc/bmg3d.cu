@@ -447,6 +447,46 @@ __global__ void k3_norm(Lev3 L, int what, double* __restrict__ partials) {
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// The first sweep of a cycle on the finest (7-point) level, carrying the
+// stop test of the cycle before it.  That cycle ended with a post-smoothing
+// sweep in reverse colour order, whose last colour is colour 0; nothing has
+// changed x since, so recomputing a colour-0 point gives the same bits and
+// the sweep's first colour is a copy.  Its second colour updates each
+// colour-1 point from its (unchanged) colour-0 neighbours, and
+// C (x_new - x_old) there is the residual b - A x of the iterate the sweep
+// reads (zero at colour 0 in the same evaluation).  Out of place: x is left
+// as it was (the previous cycle's result, returned if the test stops the
+// loop) and the swept iterate goes to `out`; the squared residual is summed
+// per block into partials.  One thread per pair of points of a row (one of
+// each colour), in k3_norm's fixed grid and order.
+__global__ void __launch_bounds__(kNormThreads) k3_gs_norm(Lev3 L, double* __restrict__ out,
+                                                           double* __restrict__ partials) {
+  const int hx = (L.nx + 1) / 2;
+  const long n = long(hx) * L.ny * L.nz;
+  double acc = 0.0;
+  for (long t = long(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += long(gridDim.x) * blockDim.x) {
+    const int ih = int(t % hx);
+    const long rest = t / hx;
+    const int j = int(rest % L.ny) + 1, k = int(rest / L.ny) + 1;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int i = 2 * ih + 1 + e;
+      if (i > L.nx) continue;
+      const int o = idx3(L, i, j, k);
+      if (((i + j + k - 3) & 1) == 0) {
+        out[o] = L.x[o];
+        continue;
+      }
+      const double xn = (L.b[o] + nb_sum<true>(L, L.x, o)) * L.iC[o];
+      out[o] = xn;
+      const double r = L.C[o] * (xn - L.x[o]);
+      acc = fma(r, r, acc);
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
 struct Scal3 {
   double bnorm2, rnorm2;
   double scale;             // FP32 refinement: the norm the FP32 right-hand side was divided by
@@ -753,6 +793,14 @@ struct bmg3_hierarchy {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t gstream = nullptr;   // stream the graph was built for
+  // FP64 V-cycles with the stop test in the next cycle's first fine sweep
+  // (k3_gs_norm; environment BMG3_FUSED_NORM=0 at setup turns it off): the
+  // finest iterate alternates between lv[L-1].x and x2, one step graph per
+  // direction
+  bool fused = false;
+  double* x2 = nullptr;
+  cudaGraph_t fgraph[2] = {nullptr, nullptr};
+  cudaGraphExec_t fexec[2] = {nullptr, nullptr};
   double setup_ms = 0.0;
 };
 
@@ -768,6 +816,8 @@ void free3(bmg3_hierarchy* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   for (int g = 0; g < 2; ++g) {
+    if (h->fexec[g]) cudaGraphExecDestroy(h->fexec[g]);
+    if (h->fgraph[g]) cudaGraphDestroy(h->fgraph[g]);
     if (h->pcg_exec[g]) cudaGraphExecDestroy(h->pcg_exec[g]);
     if (h->pcg_graph[g]) cudaGraphDestroy(h->pcg_graph[g]);
   }
@@ -779,8 +829,11 @@ void free3(bmg3_hierarchy* h) {
 // One V(nu1, nu2) cycle (Algorithm 1), then ||b - A x||^2 of the finest level.
 // One V(nu1, nu2) cycle (Algorithm 1) on the levels `lv` (FP64, or the FP32
 // copies of FP32 refinement).
+// skip_first: the finest level's first pre-smoothing sweep was already
+// issued (k3_gs_norm).
 template <typename T>
-void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t s) {
+void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t s,
+                     bool skip_first = false) {
   const int L = h->L;
   auto sweep = [&](int l, int nu, bool reverse) {
     const Lev3T<T>& V = lv[l];
@@ -812,7 +865,7 @@ void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t 
   for (int l = L - 1; l >= 1; --l) {
     bmg::NvtxRange r("restrict_leg", l);
     const Lev3T<T>& V = lv[l];
-    sweep(l, h->opt.nu1, false);
+    sweep(l, h->opt.nu1 - (skip_first && l == L - 1 ? 1 : 0), false);
     if (l == L - 1)
       k3_residual<true><<<grid_pts(V), kT, 0, s>>>(V);
     else
@@ -857,6 +910,33 @@ void enqueue_step(bmg3_hierarchy* h, cudaStream_t s) {
     k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
     count_launch(2);
   }
+  cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
+}
+
+// The finest level's first pre-smoothing sweep (two colour launches, in
+// place): the start of the first cycle of a fused solve.
+void enqueue_first_sweep3(bmg3_hierarchy* h, cudaStream_t s) {
+  const Lev3& V = h->lv[h->L - 1];
+  bmg::prof_begin(BMG_PROF_FINE_SMOOTH, s);
+  for (int c = 0; c < 2; ++c)
+    k3_gs<true><<<dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), kT, 0, s>>>(V, c);
+  bmg::prof_end(BMG_PROF_FINE_SMOOTH, s);
+  count_launch(2);
+}
+
+// One step of a fused solve (h->fused): the rest of a cycle on the finest
+// iterate in `in` (its first pre-sweep done), then the next cycle's first
+// sweep from `in` into `out` with the stop test of `in`, copied to the host.
+void enqueue_fused_step(bmg3_hierarchy* h, double* in, double* out, cudaStream_t s) {
+  const int L = h->L;
+  std::vector<Lev3> lv = h->lv;
+  lv[L - 1].x = in;
+  enqueue_vcycle3<double>(h, lv, s, true);
+  bmg::prof_begin(BMG_PROF_NORM, s);
+  k3_gs_norm<<<kNormBlocks, kNormThreads, 0, s>>>(lv[L - 1], out, h->partials);
+  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+  bmg::prof_end(BMG_PROF_NORM, s);
+  count_launch(2);
   cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
 }
 
@@ -1071,6 +1151,15 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
     o_pcg = reserve(pbf);
     for (int q = 1; q < 4; ++q) reserve(pbf);
   }
+  {
+    const char* e = std::getenv("BMG3_FUSED_NORM");
+    h->fused = !h->pcg && !h->refine && opt.nu1 >= 1 && opt.nu2 >= 1 && !(e && e[0] == '0');
+  }
+  size_t o_x2 = 0;
+  if (h->fused) {
+    const Lev3& Ff = h->lv[L - 1];
+    o_x2 = reserve(size_t(Ff.nz + 2) * Ff.py * Ff.px * sizeof(double));
+  }
   const size_t o_chol = reserve(sizeof(double) * size_t(h->n0) * h->n0);
   const size_t o_idiag = reserve(sizeof(double) * h->n0);
   const size_t o_part = reserve(sizeof(double) * kNormBlocks);
@@ -1117,6 +1206,7 @@ int bmg3_setup(const double* k, int nx, int ny, int nz, const bmg_options* opt_i
     h->pP = reinterpret_cast<double*>(base + o_pcg + 2 * pbf);
     h->pQ = reinterpret_cast<double*>(base + o_pcg + 3 * pbf);
   }
+  if (h->fused) h->x2 = reinterpret_cast<double*>(base + o_x2);
   h->chol = reinterpret_cast<double*>(base + o_chol);
   h->chol_idiag = reinterpret_cast<double*>(base + o_idiag);
   h->partials = reinterpret_cast<double*>(base + o_part);
@@ -1199,6 +1289,37 @@ int bmg3_solve(bmg3_hierarchy* h, const double* b, double* x, double tol, bmg_in
   int rc = BMG_OK;
   if (bn2 == 0.0) {
     cudaMemsetAsync(x, 0, sizeof(double) * size_t(F.nx) * F.ny * F.nz, s);
+  } else if (h->fused) {
+    // step k (1, 2, ...) works on the iterate in x (k odd) or x2 (k even)
+    // and sweeps it into the other; after K steps the result is step K's
+    // input (x for K = 0)
+    double* buf[2] = {F.x, h->x2};
+    const bool use_graph = !bmg::prof_active();
+    if (use_graph && !h->fexec[0]) {
+      for (int p = 0; p < 2; ++p)
+        if (!record_graph(&h->fgraph[p], &h->fexec[p],
+                          [&](cudaStream_t cs) { enqueue_fused_step(h, buf[p], buf[1 - p], cs); }))
+          return BMG_ECUDA;
+    }
+    if (rel > tol && h->opt.max_cycles > 0) enqueue_first_sweep3(h, s);
+    while (rel > tol && cycles < h->opt.max_cycles) {
+      const int p = cycles & 1;
+      if (use_graph) {
+        if (cudaGraphLaunch(h->fexec[p], s) != cudaSuccess) return BMG_ECUDA;
+      } else {
+        enqueue_fused_step(h, buf[p], buf[1 - p], s);
+      }
+      if (cudaStreamSynchronize(s) != cudaSuccess) return BMG_ECUDA;
+      ++cycles;
+      rel = std::sqrt(h->sc_host->rnorm2 / bn2);
+      if (!std::isfinite(rel)) {
+        rc = BMG_ENAN;
+        break;
+      }
+    }
+    if (!rc && rel > tol) rc = BMG_ENOCONV;
+    k3_unpack<<<g, kT, 0, s>>>(cycles == 0 ? F.x : buf[(cycles - 1) & 1], x, F);
+    count_launch();
   } else {
     // one cycle as a graph, recorded on a private stream (stream launches
     // while kernel classes are being timed)

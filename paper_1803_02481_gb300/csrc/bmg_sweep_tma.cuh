@@ -41,9 +41,11 @@
 // iterate since.  Then every point of c satisfies its prescaled equation
 // exactly: recomputing its update from the same neighbours gives the same
 // bits, so C (x_new - x_old) = 0 there.  A sweep whose phases are
-// (c, other colour) therefore leaves c unchanged in its first phase, and in
-// its second phase C (x_new - x_old) at each point is that point's residual
-// b - A x of the iterate before the sweep, evaluated in the prescaled form
+// (c, other colour) therefore leaves c unchanged in its first phase, which it
+// skips (the staged values of c, ring included, are already the phase's
+// result), and in its second phase C (x_new - x_old) at each point is that
+// point's residual b - A x of the iterate before the sweep, evaluated in the
+// prescaled form
 // C (b/C + sum_X (a_X/C) x_X - x).  The sweep sums its square over the
 // tile interiors (every point once) into one partial per block; C is read
 // from global memory before the tile's copies are waited for.
@@ -274,6 +276,9 @@ __global__ void __launch_bounds__(NT, MINB)
     // (r & 1, c & 1).  Phase k is relaxed on the tile grown by (gx, gy).
 #pragma unroll
     for (int k = 0; k < NPH; ++k) {
+      // NRM: the first phase would recompute every value of its colour from
+      // unchanged neighbours, giving the same bits (see above): skipped
+      if (NRM && k == 0) continue;
       if (NRM && k == NPH - 1) {
         // the last phase with the residual of the points it updates
 #pragma unroll

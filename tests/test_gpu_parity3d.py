@@ -263,3 +263,38 @@ def test_3d_paired_colour_sweeps_are_bit_identical(name, nu, monkeypatch):
         out.append((x.cpu().numpy(), info.cycles, info.rel_resid))
     assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("name", ["blocks31_c4", "general45x20x70", "tiny4"])
+@pytest.mark.parametrize("nu,stream_launched", [((2, 1), False), ((2, 1), True), ((1, 1), False),
+                                                ((1, 0), False)])
+def test_3d_stop_test_in_the_next_sweep_is_bit_identical(name, nu, stream_launched, monkeypatch):
+    """FP64 V-cycles take the stop test inside the next cycle's first fine
+    sweep (its first colour a copy, its second colour's updates giving the
+    residual), out of place, so the loop returns the iterate that sweep read.
+    Against the separate norm pass: the same iterates bit for bit after an
+    odd and an even number of cycles and at convergence, the same cycle
+    counts, residuals equal to rounding.  V(1,0) has no fusion."""
+    k, b = case(name)
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("BMG3_FUSED_NORM", mode)
+        for cap, tol in ((5, 1e-300), (6, 1e-300), (400, 1e-10)):
+            h = bm.setup3(dev(k), bm.default_options(nu1=nu[0], nu2=nu[1], max_cycles=cap))
+            if stream_launched:
+                bm.profile_set(("norm",))
+            try:
+                x, info = h.solve(dev(b), tol=tol, allow_noconv=True)
+            finally:
+                bm.profile_set(())
+            h.destroy()
+            out[mode, cap] = (x.cpu().numpy(), info.cycles, info.rel_resid)
+    a = oracle_h(name).levels[-1].a
+    for cap in (5, 6, 400):
+        (x0, c0, r0), (x1, c1, r1) = out["0", cap], out["1", cap]
+        assert c0 == c1, (cap, c0, c1)
+        assert np.array_equal(x0, x1), cap
+        assert abs(r1 - r0) <= 1e-6 * r0 + 1e-15, (cap, r0, r1)
+        rel = np.linalg.norm(b.ravel() - a @ x1.ravel()) / np.linalg.norm(b)
+        assert abs(r1 - rel) <= 1e-6 * rel + 1e-15, (cap, r1, rel)
+    assert out["1", 5][1] == 5 and out["1", 6][1] == 6
