@@ -62,6 +62,11 @@ int bmg3_setup(const double *k_dev, int nx, int ny, int nz, const bmg_options *o
  * stop test is the FP64 relative residual.
  * BMG_SOLVER_PCG: CG iterations in the oracle's textbook order; the stop test
  * uses the recursively updated residual.
+ * FP64 V-cycles with nu1, nu2 >= 1 take the residual after a cycle inside the
+ * next cycle's first fine sweep (the cycle's last colour is unchanged by it;
+ * C (x_new - x_old) at the other colour is the residual), which writes out of
+ * place, so the iterate returned is the one the residual belongs to: the same
+ * bits as with a separate residual pass (one extra half sweep per solve).
  * info (may be NULL): cycles (refinement steps, or CG iterations) run, final
  * relative residual, solve wall time.  BMG_ENOCONV after max_cycles, BMG_ENAN if the residual is
  * not finite. */
