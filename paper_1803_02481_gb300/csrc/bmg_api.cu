@@ -387,7 +387,7 @@ const SweepMaps<float>* level_maps<float>(const Hierarchy* h, int l) {
 
 template <typename T>
 void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* dlev, int thr,
-                    cudaStream_t s, int top, bool skip_first) {
+                    cudaStream_t s, int top, bool skip_first, bool top_zero) {
   const int L = h->L;
   // a cycle from level `top` down (the finest unless given): the levels
   // below the schedule's threshold still run in the persistent kernel
@@ -399,14 +399,22 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
   // interpolation also writes out of place, so every level's iterate is back
   // in lv[l].x when the cycle ends and every cycle issues the same launches.
   const bool interp_oop = ((nu1 + nu2) & 1) != 0;
-  auto sweep = [&](int l, bool reverse) {
+  // zero: the level's iterate is zero (its first pre-sweep: every level below
+  // the top was zeroed by its restriction); the sweep may then take the
+  // zero-start form (environment BMG_ZERO_START=0 turns it off)
+  static const bool zero_start = [] {
+    const char* e = std::getenv("BMG_ZERO_START");
+    return !(e && e[0] == '0');
+  }();
+  auto sweep = [&](int l, bool reverse, bool zero) {
+    zero = zero && zero_start;
     LevelV<T>& V = lv[l];
     const bool nine = l != L - 1;
     if (!nine) prof_begin(BMG_PROF_FINE_SMOOTH, s);
     if (h->opt.smoother != BMG_SMOOTH_POINT)
       launch_line_sweep<T>(V, nine, h->opt.smoother, reverse, V.x, V.x2, s);
     else
-      launch_sweep<T>(V, nine, reverse, V.x, V.x2, s, level_maps<T>(h, l));
+      launch_sweep<T>(V, nine, reverse, V.x, V.x2, s, level_maps<T>(h, l), zero);
     if (!nine) prof_end(BMG_PROF_FINE_SMOOTH, s);
     std::swap(V.x, V.x2);
   };
@@ -416,7 +424,8 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
     NvtxRange r("restrict_leg", l);
     const bool nine = l != L - 1;
     if (nine) prof_begin(BMG_PROF_LEVELS, s);
-    for (int k = skip_first && l == top ? 1 : 0; k < nu1; ++k) sweep(l, false);
+    for (int k = skip_first && l == top ? 1 : 0; k < nu1; ++k)
+      sweep(l, false, k == 0 && (l < top || top_zero));
     if (!rc && rr_fused(nine, sizeof(T) == 8)) {
       launch_resid_restrict<T>(lv[l], nine, lv[l - 1], s);
     } else {
@@ -439,16 +448,16 @@ void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* d
     } else {
       launch_interp<T>(lv[l], lv[l - 1].x, rc, s);
     }
-    for (int k = 0; k < nu2; ++k) sweep(l, true);
+    for (int k = 0; k < nu2; ++k) sweep(l, true, false);
     if (nine) prof_end(BMG_PROF_LEVELS, s);
   }
   prof_end(BMG_PROF_CYCLE, s);
 }
 
 template void enqueue_vcycle<double>(Hierarchy*, std::vector<LevelV<double>>&,
-                                     const LevelV<double>*, int, cudaStream_t, int, bool);
+                                     const LevelV<double>*, int, cudaStream_t, int, bool, bool);
 template void enqueue_vcycle<float>(Hierarchy*, std::vector<LevelV<float>>&, const LevelV<float>*,
-                                    int, cudaStream_t, int, bool);
+                                    int, cudaStream_t, int, bool, bool);
 
 // Stop test inside the next cycle's first fine sweep.  The V(nu1, nu2)
 // cycle's last fine sweep is a post-smoothing sweep (reverse colour order),
@@ -535,7 +544,8 @@ static int build_solve_graph(Hierarchy* h) {
       launch_pcg_rz(h, false, s);
       launch_pcg_p(h, s);
     } else if (fp32) {
-      enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s);
+      // the refinement residual zeroed the FP32 fine iterate
+      enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s, -1, false, true);
       launch_refine_update(h, s);
       launch_refine_residual(h, 0.0, s, true);
     } else if (fused) {
@@ -714,7 +724,7 @@ static int solve_impl(Hierarchy* h, const double* b, double* x, double tol, bmg_
       launch_refine_residual(h, tol, s);
       if ((rc = read_scalars(h, s))) return rc;
       if (!h->sc_host->go) break;
-      enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s);
+      enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s, -1, false, true);
       launch_refine_update(h, s);
     }
   }

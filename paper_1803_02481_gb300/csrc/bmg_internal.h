@@ -144,6 +144,27 @@ __device__ __forceinline__ GsCoef<T, NINE> gs_load(const LevelV<T>& L, int o, T 
   return c;
 }
 
+// gs_apply with only the neighbour terms whose bit is set in `mask` (bits in
+// the order W, E, S, N, SW, SE, NW, NE): the caller knows the others' x to
+// be zero, and fma(a, 0, acc) = acc, so the value is gs_apply's (a zero
+// result may differ in sign).  `mask` is a compile-time constant at every
+// call after unrolling, so the skipped terms cost nothing.
+template <typename T, bool NINE, class XA>
+__device__ __forceinline__ T gs_apply_masked(const GsCoef<T, NINE>& c, XA xa, unsigned mask) {
+  T acc = c.b;
+  if (mask & 0x01u) acc = fma(c.w, xa(-1, 0), acc);
+  if (mask & 0x02u) acc = fma(c.e, xa(1, 0), acc);
+  if (mask & 0x04u) acc = fma(c.s, xa(0, -1), acc);
+  if (mask & 0x08u) acc = fma(c.n, xa(0, 1), acc);
+  if (NINE) {
+    if (mask & 0x10u) acc = fma(c.sw, xa(-1, -1), acc);
+    if (mask & 0x20u) acc = fma(c.se, xa(1, -1), acc);
+    if (mask & 0x40u) acc = fma(c.nw, xa(-1, 1), acc);
+    if (mask & 0x80u) acc = fma(c.ne, xa(1, 1), acc);
+  }
+  return acc * c.ic;
+}
+
 template <typename T, bool NINE, class XA>
 __device__ __forceinline__ T gs_apply(const GsCoef<T, NINE>& c, XA xa) {
   T acc = c.b;
@@ -425,10 +446,11 @@ bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m);
 // One multicolour Gauss-Seidel sweep of a level as a single kernel: reads
 // the iterate from xin and writes the swept iterate to xout (xin != xout).
 // `maps` (the level's descriptors, may be null) selects the TMA-staged
-// kernel.
+// kernel.  `zero`: xin is known to be zero (a forward sweep may then use the
+// zero-start form: the same values, less work).
 template <typename T>
 void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* xout,
-                  cudaStream_t s, const SweepMaps<T>* maps = nullptr);
+                  cudaStream_t s, const SweepMaps<T>* maps = nullptr, bool zero = false);
 // The prescaled level's red-black sweep in the pre-smoothing colour order
 // that also sums the stop test's squared residual of its input iterate into
 // partials[0 .. grid) (grid <= nmax, returned).  Valid only when the sweep
@@ -491,10 +513,12 @@ void launch_pcg_p(Hierarchy* h, cudaStream_t s);
 void launch_pcg_precond(Hierarchy* h, cudaStream_t s);
 
 // One V-cycle of the FP64 (d) or FP32 (f) hierarchy (bmg_api.cu);
-// skip_first: the top level's first pre-smoothing sweep was already issued.
+// skip_first: the top level's first pre-smoothing sweep was already issued;
+// top_zero: the top level's iterate is zero on entry (as every coarser
+// level's is after its restriction).
 template <typename T>
 void enqueue_vcycle(Hierarchy* h, std::vector<LevelV<T>>& lv, const LevelV<T>* dlev, int thr,
-                    cudaStream_t s, int top = -1, bool skip_first = false);
+                    cudaStream_t s, int top = -1, bool skip_first = false, bool top_zero = false);
 
 void launch_assemble_backward(const double* k, const double* u, const double* lam,
                               double* g, int nx, int ny, cudaStream_t s);

@@ -157,7 +157,8 @@ void launch_pcg_precond(Hierarchy* h, cudaStream_t s) {
   LevelV<double>& F = h->d.back();
   const dim3 g((F.nx + kThreads - 1) / kThreads, F.ny);
   k_pcg_cast<<<g, kThreads, 0, s>>>(F, h->f.back(), h->sc);
-  enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s);
+  // (the cast zeroed the FP32 fine iterate)
+  enqueue_vcycle<float>(h, h->f, h->dlev32, h->threshold, s, -1, false, true);
   k_pcg_uncast<<<g, kThreads, 0, s>>>(F, h->f.back(), h->sc);
   count_launch(2);
 }

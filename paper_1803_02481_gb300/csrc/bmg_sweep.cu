@@ -244,12 +244,12 @@ bool make_sweep_maps(const LevelV<T>& L, int* err, SweepMaps<T>* m) {
 // first called from prepare_sweep_kernels, after the shared-memory opt-in and
 // before any graph capture.
 template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false,
-          bool NRM = false>
+          bool NRM = false, bool ZERO = false>
 static int tma_resident() {
   static const int r = [] {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE, NRM>, NT,
+            &n, k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE, NRM, ZERO>, NT,
             TmaTile<T, NINE, TX, TY, NSTAGE, PRE>::SMEM) != cudaSuccess ||
         n < 1)
       n = 1;
@@ -260,27 +260,29 @@ static int tma_resident() {
 }
 
 // `order`: 4 bits per colour phase (sub-lattice masks, see rb_order).
-template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE>
+// ZERO: a forward sweep of a zero iterate (order must be the forward one).
+template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool ZERO = false>
 static void launch_tma_shape(const LevelV<T>& L, const SweepMaps<T>& m, const CUtensorMap& mx,
                              unsigned order, T* xout, cudaStream_t s) {
   using G = TmaTile<T, NINE, TX, TY, NSTAGE>;
   const int ntiles = ((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
   // persistent blocks: no more than fit on the GPU at once
-  const int cap = sm_count() * tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE>();
+  const int cap = sm_count() * tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE, false, false, ZERO>();
   // 5-point levels have no SW/NW planes: their maps are passed unused
   const CUtensorMap& msw = NINE ? m.sw : m.b;
   const CUtensorMap& mnw = NINE ? m.nw : m.b;
-  k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE><<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(
-      mx, m.ic, m.w, m.s, m.b, msw, mnw, L, xout, order, m.err, nullptr, nullptr);
+  k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, false, false, ZERO>
+      <<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(mx, m.ic, m.w, m.s, m.b, msw, mnw, L, xout,
+                                                        order, m.err, nullptr, nullptr);
 }
 
 template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false,
-          bool NRM = false>
+          bool NRM = false, bool ZERO = false>
 static void allow_tma_smem() {
-  cudaFuncSetAttribute(k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE, NRM>,
+  cudaFuncSetAttribute(k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE, NRM, ZERO>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                        int(TmaTile<T, NINE, TX, TY, NSTAGE, PRE>::SMEM));
-  tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE, NRM>();
+  tma_resident<T, NINE, TX, TY, NT, MINB, NSTAGE, PRE, NRM, ZERO>();
 }
 
 // The prescaled red-black sweep (FP64, 5-point): x, b/C, W/C, S/C, E/C, N/C.
@@ -361,9 +363,19 @@ static int launch_tma_pre_norm(const LevelV<double>& L, const SweepMaps<double>&
 
 template <typename T>
 static void launch_sweep_tma(const LevelV<T>& L, const SweepMaps<T>& m, bool reverse,
-                             const T* xin, T* xout, cudaStream_t s) {
+                             const T* xin, T* xout, cudaStream_t s, bool zero) {
   const CUtensorMap& mx = xin == m.xp ? m.x : m.x2;
   const unsigned order = m.nine ? four_order(reverse) : rb_order(reverse);
+  if (zero && !reverse && !m.pre) {
+#define BMG_TMA_LAUNCH_Z(TT, NN, TX, TY, NT, MB, NS) \
+  launch_tma_shape<TT, NN, TX, TY, NT, MB, NS, true>(L, m, mx, order, xout, s)
+    if (m.nine)
+      BMG_TMA_DISPATCH(T, true, nine_cfg_index(), BMG_TMA_LAUNCH_Z);
+    else
+      BMG_TMA_DISPATCH(T, false, rb_cfg_index(), BMG_TMA_LAUNCH_Z);
+#undef BMG_TMA_LAUNCH_Z
+    return;
+  }
   if constexpr (sizeof(T) == 8) {
     if (m.pre) {
 #define BMG_TMA_PRE_LAUNCH(TX, TY, NT, MB, NS) launch_tma_pre<TX, TY, NT, MB, NS>(L, m, mx, order, xout, s)
@@ -398,14 +410,14 @@ int launch_sweep_pre_norm(const LevelV<double>& L, const SweepMaps<double>* maps
 
 template <typename T>
 void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* xout,
-                  cudaStream_t s, const SweepMaps<T>* maps) {
+                  cudaStream_t s, const SweepMaps<T>* maps, bool zero) {
   // Large tiles keep the redundant halo work small (4% red-black, 12% four
   // colours); levels narrower than 1024 use small tiles so that they still
   // spread over all SMs.
   const bool small = L.nx < 1024;
   const bool tma = maps && maps->nine == nine && (xin == maps->xp || xin == maps->x2p);
   if (tma) {
-    launch_sweep_tma<T>(L, *maps, reverse, xin, xout, s);
+    launch_sweep_tma<T>(L, *maps, reverse, xin, xout, s, zero);
   } else if (nine) {
     if (small) {
       constexpr int TX = 32, TY = 16;
@@ -453,10 +465,17 @@ void prepare_sweep_kernels() {
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(S32::Row) * S32::NSLOT));
 #define BMG_TMA_ALLOW(TT, NN, TX, TY, NT, MB, NS) allow_tma_smem<TT, NN, TX, TY, NT, MB, NS>()
+#define BMG_TMA_ALLOW_Z(TT, NN, TX, TY, NT, MB, NS) \
+  allow_tma_smem<TT, NN, TX, TY, NT, MB, NS, false, false, true>()
     BMG_TMA_DISPATCH(double, false, rb_cfg_index(), BMG_TMA_ALLOW);
     BMG_TMA_DISPATCH(float, false, rb_cfg_index(), BMG_TMA_ALLOW);
     BMG_TMA_DISPATCH(double, true, nine_cfg_index(), BMG_TMA_ALLOW);
     BMG_TMA_DISPATCH(float, true, nine_cfg_index(), BMG_TMA_ALLOW);
+    BMG_TMA_DISPATCH(double, false, rb_cfg_index(), BMG_TMA_ALLOW_Z);
+    BMG_TMA_DISPATCH(float, false, rb_cfg_index(), BMG_TMA_ALLOW_Z);
+    BMG_TMA_DISPATCH(double, true, nine_cfg_index(), BMG_TMA_ALLOW_Z);
+    BMG_TMA_DISPATCH(float, true, nine_cfg_index(), BMG_TMA_ALLOW_Z);
+#undef BMG_TMA_ALLOW_Z
 #undef BMG_TMA_ALLOW
 #define BMG_TMA_PRE_ALLOW(TX, TY, NT, MB, NS) allow_tma_smem<double, false, TX, TY, NT, MB, NS, true>()
     BMG_TMA_PRE_DISPATCH(pre_cfg_index(), BMG_TMA_PRE_ALLOW);
@@ -501,9 +520,9 @@ int selftest_bounded_wait(cudaStream_t s) {
 }
 
 template void launch_sweep<double>(const LevelV<double>&, bool, bool, const double*, double*,
-                                   cudaStream_t, const SweepMaps<double>*);
+                                   cudaStream_t, const SweepMaps<double>*, bool);
 template void launch_sweep<float>(const LevelV<float>&, bool, bool, const float*, float*,
-                                  cudaStream_t, const SweepMaps<float>*);
+                                  cudaStream_t, const SweepMaps<float>*, bool);
 template bool make_sweep_maps<double>(const LevelV<double>&, int*, SweepMaps<double>*);
 template void launch_prescale_coeffs<double>(const LevelV<double>&, cudaStream_t);
 template void launch_prescale_b<double>(const LevelV<double>&, cudaStream_t);

@@ -39,6 +39,23 @@ __host__ __device__ constexpr int colour_grow_y(int nc, int k) {
 }
 constexpr int kColourHaloRows = 2;
 
+// A forward sweep (rb_order(false), four_order(false)) from x = 0: phase k
+// sees nonzero x only at points of the colours updated before it in the same
+// sweep.  Neighbour-term mask of phase k (the bits of gs_apply_masked): the
+// point's (row, column) parities are (k >> 1, k & 1) with four colours; a
+// neighbour differing in (row, column) parity by (dr, dc) has colour
+// 2 (pr ^ dr) + (pc ^ dc), and counts if that colour comes before k.  With
+// two colours the second phase's neighbours are all of the first.
+__host__ __device__ constexpr unsigned zero_start_mask(bool nine, int k) {
+  if (!nine) return k == 0 ? 0u : 0x0Fu;
+  return ((2 * (k >> 1) + ((k & 1) ^ 1) < k) ? 0x03u : 0u) |
+         ((2 * ((k >> 1) ^ 1) + (k & 1) < k) ? 0x0Cu : 0u) |
+         ((2 * ((k >> 1) ^ 1) + ((k & 1) ^ 1) < k) ? 0xF0u : 0u);
+}
+static_assert(zero_start_mask(true, 0) == 0u && zero_start_mask(true, 1) == 0x03u &&
+                  zero_start_mask(true, 2) == 0xFCu && zero_start_mask(true, 3) == 0xFFu,
+              "four-colour zero-start masks");
+
 template <typename T, bool NINE, int TX, int TY, int NT, int UB = (NINE ? 3 : 1)>
 __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restrict__ xin,
                                            T* __restrict__ xout, unsigned order, int bx, int by) {

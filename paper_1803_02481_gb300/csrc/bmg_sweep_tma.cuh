@@ -168,8 +168,15 @@ enum TmaPlane { TP_X = 0, TP_IC, TP_W, TP_S, TP_B, TP_SW, TP_NW };
 // carry x, b/C, W/C, S/C, E/C, N/C and an unused one.  NRM (with PRE): the
 // second colour phase also sums (C (x_new - x_old))^2, C read from `cdiag`,
 // into nrm[blockIdx.x].
+// ZERO (not with PRE): a forward sweep whose input iterate is zero (a coarse
+// level after the restriction, an FP32 finest level after the refinement
+// residual): x is not staged, each phase applies only the neighbour terms of
+// the colours updated before it (zero_start_mask), and the phases write zero
+// at the points of their regions outside the grid (the Dirichlet values the
+// staged ghosts would hold) -- the same values as the plain sweep of a zero
+// iterate.
 template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false,
-          bool NRM = false>
+          bool NRM = false, bool ZERO = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_sweep_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mic,
                 const __grid_constant__ CUtensorMap mw, const __grid_constant__ CUtensorMap ms,
@@ -180,6 +187,7 @@ __global__ void __launch_bounds__(NT, MINB)
   using namespace tma_detail;
   static_assert(!(PRE && NINE), "prescaled levels are 5-point");
   static_assert(!NRM || PRE, "the fused residual is taken on prescaled levels");
+  static_assert(!ZERO || !PRE, "zero-start sweeps are standard-operator sweeps");
   using G = TmaTile<T, NINE, TX, TY, NSTAGE, PRE>;
   constexpr int BW = G::BW, HA = G::HA, HY = G::HY, PL = G::PLANE, NPH = G::NPH;
   // NRM: the last phase relaxes the tile interior; each of its two
@@ -211,8 +219,8 @@ __global__ void __launch_bounds__(NT, MINB)
     const int Y = by * TY + 1 - HY;                     // tensor row (= j) of the box start
     T* d = s ? stage1 : stage0;
     uint64_t* b = &bar[s];
-    mbar_expect_tx(b, G::STAGE_BYTES);
-    tma_load_2d(d + TP_X * PL, &mx, X, Y, b);
+    mbar_expect_tx(b, G::STAGE_BYTES - (ZERO ? unsigned(PL * sizeof(T)) : 0u));
+    if (!ZERO) tma_load_2d(d + TP_X * PL, &mx, X, Y, b);
     tma_load_2d(d + TP_IC * PL, &mic, X, Y, b);
     tma_load_2d(d + TP_W * PL, &mw, X, Y, b);
     tma_load_2d(d + TP_S * PL, &ms, X, Y, b);
@@ -330,8 +338,10 @@ __global__ void __launch_bounds__(NT, MINB)
           }
           // domain point (i, j) = (i0 + c - HA, j0 + r - HY) inside 1..nx, 1..ny
           if (unsigned(i0 + c - HA - 1) >= unsigned(nx) ||
-              unsigned(j0 + r - HY - 1) >= unsigned(ny))
+              unsigned(j0 + r - HY - 1) >= unsigned(ny)) {
+            if (ZERO) sx[r * BW + c] = T(0);
             continue;
+          }
           const int o = r * BW + c;
           if (PRE) {
             T* xp = sx + o;
@@ -353,7 +363,11 @@ __global__ void __launch_bounds__(NT, MINB)
             cf_.ne = ssw[o + 1 + BW];
           }
           T* xp = sx + o;
-          *xp = gs_apply<T, NINE>(cf_, [&](int dx, int dy) { return xp[dx + dy * BW]; });
+          if (ZERO)
+            *xp = gs_apply_masked<T, NINE>(cf_, [&](int dx, int dy) { return xp[dx + dy * BW]; },
+                                           zero_start_mask(NINE, k));
+          else
+            *xp = gs_apply<T, NINE>(cf_, [&](int dx, int dy) { return xp[dx + dy * BW]; });
         }
       }
       __syncthreads();

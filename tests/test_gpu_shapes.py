@@ -6,7 +6,8 @@ blocks per SM, stages) selected once per process by environment variables:
 BMG_TMA9_CFG (9-point levels, FP64 and FP32), BMG_TMA_PRE_CFG (the
 prescaled FP64 finest level), BMG_TMA_CFG (5-point levels: FP32, and FP64
 with BMG_RB_PRESCALE=0); BMG_RR_FUSED picks the levels whose residual and
-restriction run as one kernel.  The defaults are covered by the oracle parity
+restriction run as one kernel; BMG_ZERO_START=0 sweeps zero iterates (each
+coarse level's, the FP32 finest level's in refinement) in the plain form.  The defaults are covered by the oracle parity
 tests; here each other entry runs in a subprocess on a grid that puts every
 level through the full-grid kernels (threshold 1), with ragged tiles on every
 level, and its iterates must equal the default's bit for bit, in FP64 and in
@@ -68,7 +69,9 @@ SETTINGS = ([("nine%d" % k, {"BMG_TMA9_CFG": str(k)}) for k in range(1, 6)] +
             [("pre%d" % k, {"BMG_TMA_PRE_CFG": str(k)}) for k in range(1, 6)] +
             [("rb%d" % k, {"BMG_TMA_CFG": str(k)}) for k in range(1, 3)] +
             # residual and restriction fused into one kernel on every level, or on none
-            [("rr%d" % k, {"BMG_RR_FUSED": str(k)}) for k in range(2)])
+            [("rr%d" % k, {"BMG_RR_FUSED": str(k)}) for k in range(2)] +
+            # first pre-sweeps of zero iterates in the plain form
+            [("zero_start_off", {"BMG_ZERO_START": "0"})])
 
 
 def test_every_sweep_shape_gives_identical_iterates(tmp_path):
