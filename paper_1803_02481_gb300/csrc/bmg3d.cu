@@ -321,9 +321,41 @@ __device__ __forceinline__ T nb_sum(const Lev3T<T>& L, const T* __restrict__ x, 
   return s;
 }
 
+// A forward sweep from x = 0 (a coarse level after its restriction, the
+// finest level of FP32 refinement or of a PCG preconditioner cycle): a point
+// of colour c sees nonzero x only at neighbours of colours updated before c
+// in the same sweep.  A neighbour at (di, dj, dk) differs from the point in
+// colour by the parity flips f = 4|dk| + 2|dj| + |di| (eight colours), so
+// its colour c ^ f precedes c exactly when the highest bit of f is set in
+// c; with two colours (parity of i + j + k) every neighbour of colour 1 is
+// of colour 0 and colour 0 has none.  nb_sum_zero skips the other terms:
+// fma(a, 0, s) = s, so the sum equals nb_sum's (up to the sign of a zero).
+__host__ __device__ constexpr bool zero_term3(int c, int di, int dj, int dk) {
+  return (dk ? (c & 4) != 0 : dj ? (c & 2) != 0 : (c & 1) != 0);
+}
+
+template <int C, typename T>
+__device__ __forceinline__ T nb_sum27_zero(const Lev3T<T>& L, const T* __restrict__ x, int o) {
+  T s = T(0);
+#pragma unroll
+  for (int dk = -1; dk <= 1; ++dk)
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        if (di == 0 && dj == 0 && dk == 0) continue;
+        if (!zero_term3(C, di, dj, dk)) continue;
+        const int d = off3(L, di, dj, dk);
+        s = fma(coupling(L, o, di, dj, dk), x[o + d], s);
+      }
+  return s;
+}
+
 // One colour of a sweep, in place.  SEVEN: red-black, colour (i + j + k)
 // parity (0-based); else colour 4 (k mod 2) + 2 (j mod 2) + (i mod 2).
-template <bool SEVEN, typename T>
+// ZERO (SEVEN, forward sweep of a zero iterate): colour 0 has no nonzero
+// neighbour, x = (b + 0) / C.
+template <bool SEVEN, typename T, bool ZERO = false>
 __global__ void k3_gs(Lev3T<T> L, int colour) {
   const int ih = blockIdx.x * blockDim.x + threadIdx.x;
   int i0, j0, k0;
@@ -338,7 +370,10 @@ __global__ void k3_gs(Lev3T<T> L, int colour) {
   }
   if (i0 >= L.nx || j0 >= L.ny || k0 >= L.nz) return;
   const int o = idx3(L, i0 + 1, j0 + 1, k0 + 1);
-  L.x[o] = (L.b[o] + nb_sum<SEVEN>(L, L.x, o)) * L.iC[o];
+  if (ZERO && colour == 0)
+    L.x[o] = (L.b[o] + T(0)) * L.iC[o];
+  else
+    L.x[o] = (L.b[o] + nb_sum<SEVEN>(L, L.x, o)) * L.iC[o];
 }
 
 // Two colours of an eight-colour sweep in one launch: colours 2m and 2m + 1
@@ -361,6 +396,28 @@ __global__ void __launch_bounds__(kT) k3_gs27_pair(Lev3T<T> L, int m, int revers
     }
     __syncthreads();
   }
+}
+
+// The colour pair 2M, 2M + 1 of a forward 27-point sweep of a zero iterate
+// (k3_gs27_pair's layout; each colour with only the terms nb_sum27_zero
+// keeps).
+template <int C, typename T>
+__device__ __forceinline__ void gs27_row_zero(const Lev3T<T>& L, int base) {
+  for (int i0 = 2 * threadIdx.x + (C & 1); i0 < L.nx; i0 += 2 * kT) {
+    const int o = base + i0 + 1;
+    L.x[o] = (L.b[o] + nb_sum27_zero<C>(L, L.x, o)) * L.iC[o];
+  }
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kT) k3_gs27_pair_zero(Lev3T<T> L) {
+  const int j0 = 2 * blockIdx.x + (M & 1), k0 = 2 * blockIdx.y + (M >> 1);   // 0-based
+  if (j0 >= L.ny || k0 >= L.nz) return;
+  const int base = idx3(L, 0, j0 + 1, k0 + 1);
+  gs27_row_zero<2 * M>(L, base);
+  __syncthreads();
+  gs27_row_zero<2 * M + 1>(L, base);
+  __syncthreads();
 }
 
 template <bool SEVEN, typename T>
@@ -831,16 +888,34 @@ void free3(bmg3_hierarchy* h) {
 // copies of FP32 refinement).
 // skip_first: the finest level's first pre-smoothing sweep was already
 // issued (k3_gs_norm).
+// top_zero: the finest iterate is zero on entry (every coarser level's is
+// after its restriction); the first forward sweep of a zero iterate takes
+// the zero-start kernels (environment BMG_ZERO_START=0 turns them off).
 template <typename T>
 void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t s,
-                     bool skip_first = false) {
+                     bool skip_first = false, bool top_zero = false) {
   const int L = h->L;
-  auto sweep = [&](int l, int nu, bool reverse) {
+  static const bool zero_start = [] {
+    const char* e = std::getenv("BMG_ZERO_START");
+    return !(e && e[0] == '0');
+  }();
+  auto sweep = [&](int l, int nu, bool reverse, bool zero) {
     const Lev3T<T>& V = lv[l];
     const bool seven = l == L - 1;
     const int nc = seven ? 2 : 8;
     for (int it = 0; it < nu; ++it) {
+      const bool z = zero && zero_start && it == 0 && !reverse;
       if (seven) bmg::prof_begin(BMG_PROF_FINE_SMOOTH, s);
+      if (!seven && h->gs27_pairs && z) {
+        const dim3 g0((V.ny + 1) / 2, (V.nz + 1) / 2), g1(V.ny / 2, (V.nz + 1) / 2),
+            g2((V.ny + 1) / 2, V.nz / 2), g3(V.ny / 2, V.nz / 2);
+        k3_gs27_pair_zero<T, 0><<<g0, kT, 0, s>>>(V);
+        k3_gs27_pair_zero<T, 1><<<g1, kT, 0, s>>>(V);
+        k3_gs27_pair_zero<T, 2><<<g2, kT, 0, s>>>(V);
+        k3_gs27_pair_zero<T, 3><<<g3, kT, 0, s>>>(V);
+        count_launch(4);
+        continue;
+      }
       if (!seven && h->gs27_pairs) {
         for (int p0 = 0; p0 < 4; ++p0) {
           const int m = reverse ? 3 - p0 : p0;
@@ -852,7 +927,9 @@ void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t 
       }
       for (int c0 = 0; c0 < nc; ++c0) {
         const int c = reverse ? nc - 1 - c0 : c0;
-        if (seven)
+        if (seven && z)
+          k3_gs<true, T, true><<<dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), kT, 0, s>>>(V, c);
+        else if (seven)
           k3_gs<true><<<dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), kT, 0, s>>>(V, c);
         else
           k3_gs<false><<<dim3(cdiv((V.nx + 1) / 2, kT), (V.ny + 1) / 2, (V.nz + 1) / 2), kT, 0, s>>>(V, c);
@@ -865,7 +942,8 @@ void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t 
   for (int l = L - 1; l >= 1; --l) {
     bmg::NvtxRange r("restrict_leg", l);
     const Lev3T<T>& V = lv[l];
-    sweep(l, h->opt.nu1 - (skip_first && l == L - 1 ? 1 : 0), false);
+    sweep(l, h->opt.nu1 - (skip_first && l == L - 1 ? 1 : 0), false,
+          !(skip_first && l == L - 1) && (l < L - 1 || top_zero));
     if (l == L - 1)
       k3_residual<true><<<grid_pts(V), kT, 0, s>>>(V);
     else
@@ -879,7 +957,7 @@ void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t 
     bmg::NvtxRange r("interp_leg", l);
     k3_interp<<<dim3(cdiv((lv[l].nx + 1) / 2, kT), lv[l].ny, lv[l].nz), kT, 0, s>>>(lv[l], lv[l - 1]);
     count_launch();
-    sweep(l, h->opt.nu2, true);
+    sweep(l, h->opt.nu2, true, false);
   }
 }
 
@@ -899,7 +977,8 @@ void enqueue_refine_residual(bmg3_hierarchy* h, cudaStream_t s) {
 void enqueue_step(bmg3_hierarchy* h, cudaStream_t s) {
   const int L = h->L;
   if (h->refine) {
-    enqueue_vcycle3<float>(h, h->lv32, s);
+    // the refinement residual zeroed the FP32 finest iterate
+    enqueue_vcycle3<float>(h, h->lv32, s, false, true);
     const Lev3& F = h->lv[L - 1];
     k3_refine_update<<<grid_pts(F), kT, 0, s>>>(F, h->lv32[L - 1], h->sc);
     count_launch();
@@ -948,11 +1027,11 @@ void enqueue_precond(bmg3_hierarchy* h, cudaStream_t s) {
   if (h->refine) {
     const Lev3& F = h->lv[L - 1];
     k3_pcg_cast<<<grid_pts(F), kT, 0, s>>>(F, h->lv32[L - 1], h->sc);
-    enqueue_vcycle3<float>(h, h->lv32, s);
+    enqueue_vcycle3<float>(h, h->lv32, s, false, true);   // the cast zeroed z
     k3_pcg_uncast<<<grid_pts(F), kT, 0, s>>>(F, h->lv32[L - 1], h->sc);
     count_launch(2);
   } else {
-    enqueue_vcycle3<double>(h, h->lv, s);
+    enqueue_vcycle3<double>(h, h->lv, s, false, true);    // z = 0 from the update
   }
 }
 
