@@ -151,7 +151,8 @@ __global__ void k_pcg_uncast(LevelV<double> L, LevelV<float> F, const Scalars* _
 
 void launch_pcg_precond(Hierarchy* h, cudaStream_t s) {
   if (h->opt.precision != BMG_FP32_REFINE) {
-    enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s);
+    // the PCG kernels left z = 0 in the finest x plane
+    enqueue_vcycle<double>(h, h->d, h->dlev64, h->threshold, s, -1, false, true);
     return;
   }
   LevelV<double>& F = h->d.back();

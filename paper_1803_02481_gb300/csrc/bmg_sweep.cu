@@ -286,13 +286,15 @@ static void allow_tma_smem() {
 }
 
 // The prescaled red-black sweep (FP64, 5-point): x, b/C, W/C, S/C, E/C, N/C.
-template <int TX, int TY, int NT, int MINB, int NSTAGE>
+// ZERO: a forward sweep of a zero iterate.
+template <int TX, int TY, int NT, int MINB, int NSTAGE, bool ZERO = false>
 static void launch_tma_pre(const LevelV<double>& L, const SweepMaps<double>& m,
                            const CUtensorMap& mx, unsigned order, double* xout, cudaStream_t s) {
   using G = TmaTile<double, false, TX, TY, NSTAGE, true>;
   const int ntiles = ((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
-  const int cap = sm_count() * tma_resident<double, false, TX, TY, NT, MINB, NSTAGE, true>();
-  k_sweep_tma<double, false, TX, TY, NT, MINB, NSTAGE, true>
+  const int cap =
+      sm_count() * tma_resident<double, false, TX, TY, NT, MINB, NSTAGE, true, false, ZERO>();
+  k_sweep_tma<double, false, TX, TY, NT, MINB, NSTAGE, true, false, ZERO>
       <<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(mx, m.pb, m.pw, m.ps, m.pe, m.pn, m.pn, L,
                                                         xout, order, m.err, nullptr, nullptr);
 }
@@ -366,6 +368,15 @@ static void launch_sweep_tma(const LevelV<T>& L, const SweepMaps<T>& m, bool rev
                              const T* xin, T* xout, cudaStream_t s, bool zero) {
   const CUtensorMap& mx = xin == m.xp ? m.x : m.x2;
   const unsigned order = m.nine ? four_order(reverse) : rb_order(reverse);
+  if constexpr (sizeof(T) == 8) {
+    if (zero && !reverse && m.pre) {
+#define BMG_TMA_PRE_LAUNCH_Z(TX, TY, NT, MB, NS) \
+  launch_tma_pre<TX, TY, NT, MB, NS, true>(L, m, mx, order, xout, s)
+      BMG_TMA_PRE_DISPATCH(pre_cfg_index(), BMG_TMA_PRE_LAUNCH_Z);
+#undef BMG_TMA_PRE_LAUNCH_Z
+      return;
+    }
+  }
   if (zero && !reverse && !m.pre) {
 #define BMG_TMA_LAUNCH_Z(TT, NN, TX, TY, NT, MB, NS) \
   launch_tma_shape<TT, NN, TX, TY, NT, MB, NS, true>(L, m, mx, order, xout, s)
@@ -484,6 +495,10 @@ void prepare_sweep_kernels() {
   allow_tma_smem<double, false, TX, TY, NT, MB, NS, true, true>()
     BMG_TMA_PRE_DISPATCH(pre_cfg_index(), BMG_TMA_PRE_NORM_ALLOW);
 #undef BMG_TMA_PRE_NORM_ALLOW
+#define BMG_TMA_PRE_ZERO_ALLOW(TX, TY, NT, MB, NS) \
+  allow_tma_smem<double, false, TX, TY, NT, MB, NS, true, false, true>()
+    BMG_TMA_PRE_DISPATCH(pre_cfg_index(), BMG_TMA_PRE_ZERO_ALLOW);
+#undef BMG_TMA_PRE_ZERO_ALLOW
     sm_count();
     encode_tiled();
     return true;

@@ -168,13 +168,14 @@ enum TmaPlane { TP_X = 0, TP_IC, TP_W, TP_S, TP_B, TP_SW, TP_NW };
 // carry x, b/C, W/C, S/C, E/C, N/C and an unused one.  NRM (with PRE): the
 // second colour phase also sums (C (x_new - x_old))^2, C read from `cdiag`,
 // into nrm[blockIdx.x].
-// ZERO (not with PRE): a forward sweep whose input iterate is zero (a coarse
-// level after the restriction, an FP32 finest level after the refinement
-// residual): x is not staged, each phase applies only the neighbour terms of
-// the colours updated before it (zero_start_mask), and the phases write zero
-// at the points of their regions outside the grid (the Dirichlet values the
-// staged ghosts would hold) -- the same values as the plain sweep of a zero
-// iterate.
+// ZERO: a forward sweep whose input iterate is zero (a coarse level after the
+// restriction, an FP32 finest level after the refinement residual, the
+// finest level of a PCG preconditioner cycle): x is not staged, each phase
+// applies only the neighbour terms of the colours updated before it
+// (zero_start_mask; on a prescaled level the first phase's value is b/C),
+// and the phases write zero at the points of their regions outside the grid
+// (the Dirichlet values the staged ghosts would hold) -- the same values as
+// the plain sweep of a zero iterate.
 template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false,
           bool NRM = false, bool ZERO = false>
 __global__ void __launch_bounds__(NT, MINB)
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(NT, MINB)
   using namespace tma_detail;
   static_assert(!(PRE && NINE), "prescaled levels are 5-point");
   static_assert(!NRM || PRE, "the fused residual is taken on prescaled levels");
-  static_assert(!ZERO || !PRE, "zero-start sweeps are standard-operator sweeps");
+  static_assert(!(ZERO && NRM), "the stop-test sweep reads a converging iterate");
   using G = TmaTile<T, NINE, TX, TY, NSTAGE, PRE>;
   constexpr int BW = G::BW, HA = G::HA, HY = G::HY, PL = G::PLANE, NPH = G::NPH;
   // NRM: the last phase relaxes the tile interior; each of its two
@@ -345,8 +346,13 @@ __global__ void __launch_bounds__(NT, MINB)
           const int o = r * BW + c;
           if (PRE) {
             T* xp = sx + o;
-            *xp = gs_pre_apply<T>(sic[o], sw[o], sb[o], ss[o], ssw[o],
-                                  [&](int dx, int dy) { return xp[dx + dy * BW]; });
+            // zero start: the first phase's neighbours are all zero, and
+            // fma(a, 0, b/C) = b/C
+            if (ZERO && zero_start_mask(false, k) == 0u)
+              *xp = sic[o];
+            else
+              *xp = gs_pre_apply<T>(sic[o], sw[o], sb[o], ss[o], ssw[o],
+                                    [&](int dx, int dy) { return xp[dx + dy * BW]; });
             continue;
           }
           GsCoef<T, NINE> cf_;

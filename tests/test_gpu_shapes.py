@@ -10,8 +10,8 @@ restriction run as one kernel; BMG_ZERO_START=0 sweeps zero iterates (each
 coarse level's, the FP32 finest level's in refinement) in the plain form.  The defaults are covered by the oracle parity
 tests; here each other entry runs in a subprocess on a grid that puts every
 level through the full-grid kernels (threshold 1), with ragged tiles on every
-level, and its iterates must equal the default's bit for bit, in FP64 and in
-FP32 refinement (and its stop-test residuals too, except where the prescaled
+level, and its iterates must equal the default's bit for bit, in FP64, in
+FP32 refinement and in PCG with the V(1,1) cycle (and its stop-test residuals too, except where the prescaled
 sweep sums them: there another tile shape changes only the order of the sum).
 """
 import json
@@ -37,8 +37,9 @@ src, dst = sys.argv[1], sys.argv[2]
 d = np.load(src)
 dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
 out, meta = {}, {}
-for tag, prec in (("fp64", bm.BMG_FP64), ("fp32", bm.BMG_FP32_REFINE)):
-    h = bm.setup(dev(d["k"]), bm.default_options(coarse_threshold=1, precision=prec))
+for tag, prec, kw in (("fp64", bm.BMG_FP64, {}), ("fp32", bm.BMG_FP32_REFINE, {}),
+                      ("pcg", bm.BMG_FP64, dict(nu1=1, nu2=1, solver=bm.BMG_SOLVER_PCG))):
+    h = bm.setup(dev(d["k"]), bm.default_options(coarse_threshold=1, precision=prec, **kw))
     x, info = h.solve(dev(d["b"]), tol=1e-10)
     out[tag] = x.cpu().numpy()
     meta[tag] = [info.cycles, info.rel_resid]
@@ -83,7 +84,7 @@ def test_every_sweep_shape_gives_identical_iterates(tmp_path):
     assert np.array_equal(std["fp32"], ref["fp32"])
     for name, env in SETTINGS:
         got, meta = run_child(tmp_path, name, env)
-        for tag in ("fp64", "fp32"):
+        for tag in ("fp64", "fp32", "pcg"):
             if name.startswith("pre") and tag == "fp64":
                 # the stop test is summed inside the prescaled sweep, per tile
                 # and block: another tile shape adds the same squares in
