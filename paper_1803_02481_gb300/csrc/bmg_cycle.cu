@@ -377,7 +377,9 @@ void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool z
 // memory traffic (the 8191^2 FP32-refined solve 99.5 -> 97.3 ms).  FP64
 // levels keep the separate kernels: the FP64 pipe bounds the residual either
 // way, and the fused kernel's per-thread loop over several residuals hid
-// latency worse (4095^2 solve 3924 -> 3961 ms with fused 9-point levels).
+// latency worse (4095^2 solve 3924 -> 3961 ms with fused 9-point levels; on
+// the launch-latency-bound small levels too: fused below 512 points wide,
+// the 255^2 Poisson cycle took 137.9 instead of 130.3 us).
 bool rr_fused(bool nine, bool fp64) {
   (void)nine;
   static const int v = [] {
@@ -411,6 +413,21 @@ void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaSt
   count_launch();
 }
 
+// Threads of the one-block persistent kernel (environment BMG_COARSE_THREADS,
+// a multiple of 32 up to 1024).  Measured on the 255^2 Poisson cycle with
+// the coarse kernel on levels 15^2 and below: 127.3 us at 1024 threads,
+// 124.9 at 512, 124.7 at 256, 136.3 at 128 (another box: 129.8 and 127.3 at
+// 1024 and 512); 512 also keeps wider levels inside the kernel near the
+// 1024-thread cost.  The model's calibration probes use the same count.
+int coarse_block_threads() {
+  static const int n = [] {
+    const char* e = std::getenv("BMG_COARSE_THREADS");
+    const int v = e && e[0] ? std::atoi(e) : 512;
+    return v >= 32 && v <= 1024 && v % 32 == 0 ? v : 512;
+  }();
+  return n;
+}
+
 template <typename T>
 void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* dev_levels, int thr, cudaStream_t s) {
   CoarseArgs<T> a;
@@ -430,7 +447,7 @@ void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* dev_levels, int thr, cud
   else if (h->coarse_ctas > 1)
     launch_cluster_kernel<T>(h->coarse_ctas, s, a);
   else
-    k_coarse_cycle<T><<<1, 1024, 0, s>>>(a);
+    k_coarse_cycle<T><<<1, coarse_block_threads(), 0, s>>>(a);
   prof_end(BMG_PROF_COARSE, s);
   count_launch();
 }

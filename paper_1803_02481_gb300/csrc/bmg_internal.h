@@ -425,6 +425,8 @@ void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool z
 template <typename T>
 void launch_resid_restrict(const LevelV<T>& fine, bool nine, LevelV<T> coarse, cudaStream_t s);
 bool rr_fused(bool nine, bool fp64);
+// Threads of the one-block persistent coarse kernel.
+int coarse_block_threads();
 template <typename T>
 void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaStream_t s,
                    T* out = nullptr);

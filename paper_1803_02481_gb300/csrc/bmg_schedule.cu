@@ -247,9 +247,9 @@ int calibrate(cudaStream_t s, double* out) {
   // in one block, and over the largest cluster the coarse kernel can use
   const LevelV<double> probe = probe_level(buf);
   const int ph = 2000;
-  k_phases_real<BlockTeam><<<1, 1024, 0, s>>>(probe, 8);
+  k_phases_real<BlockTeam><<<1, coarse_block_threads(), 0, s>>>(probe, 8);
   cudaEventRecord(e0, s);
-  k_phases_real<BlockTeam><<<1, 1024, 0, s>>>(probe, ph);
+  k_phases_real<BlockTeam><<<1, coarse_block_threads(), 0, s>>>(probe, ph);
   cudaEventRecord(e1, s);
   p.sync_us = 1e3 * time_ms(s, e0, e1) / ph;
   const int cmax = max_cluster_ctas(false);
@@ -287,9 +287,9 @@ int calibrate(cudaStream_t s, double* out) {
   p.gpu_gbs = 2.0 * sizeof(double) * stream_elems / (time_ms(s, e0, e1) * 1e6);
   // one block on an L2-resident 4 MiB buffer
   const size_t small2 = (size_t(1) << 19) / 2;
-  k_stream<<<1, 1024, 0, s>>>(src, dst, small2);
+  k_stream<<<1, coarse_block_threads(), 0, s>>>(src, dst, small2);
   cudaEventRecord(e0, s);
-  for (int r = 0; r < 4; ++r) k_stream<<<1, 1024, 0, s>>>(src, dst, small2);
+  for (int r = 0; r < 4; ++r) k_stream<<<1, coarse_block_threads(), 0, s>>>(src, dst, small2);
   cudaEventRecord(e1, s);
   p.cta_gbs = 4 * 2.0 * sizeof(double) * (size_t(1) << 19) / (time_ms(s, e0, e1) * 1e6);
   const bool ok = cudaGetLastError() == cudaSuccess;
