@@ -20,6 +20,7 @@ inline int cdiv(long a, long b) { return int((a + b - 1) / b); }
 template <typename T, bool NINE>
 __global__ void k_residual(LevelV<T> L, const T* __restrict__ x, const T* __restrict__ b,
                            T* __restrict__ r) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int j = blockIdx.y + 1;
   if (i > L.nx) return;
@@ -29,6 +30,7 @@ __global__ void k_residual(LevelV<T> L, const T* __restrict__ x, const T* __rest
 
 template <typename T>
 __global__ void k_restrict(LevelV<T> F, const T* __restrict__ r, LevelV<T> Cc, int zero_x) {
+  griddep_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int J = blockIdx.y + 1;
   if (I > Cc.nx) return;
@@ -49,6 +51,7 @@ constexpr int kRRX = 32, kRRY = 8, kRRT = 256;
 
 template <typename T, bool NINE>
 __global__ void __launch_bounds__(kRRT) k_resid_restrict(LevelV<T> F, LevelV<T> Cc) {
+  griddep_wait();
   constexpr int RW = 2 * kRRX + 1, RH = 2 * kRRY + 1;
   __shared__ T rs[RH * RW];
   const int I0 = blockIdx.x * kRRX + 1, J0 = blockIdx.y * kRRY + 1;
@@ -98,6 +101,7 @@ struct Pair<float> {
 // reach the ghost column nx + 1 is done point by point.
 template <typename T>
 __global__ void k_interp(LevelV<T> F, const T* __restrict__ xc, int add_rc, T* __restrict__ out) {
+  griddep_wait();
   using V = typename Pair<T>::type;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y;
@@ -135,6 +139,7 @@ __global__ void k_interp(LevelV<T> F, const T* __restrict__ xc, int add_rc, T* _
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
+  griddep_wait();
   coarse_cycle_body<T>(a);
 }
 
@@ -142,6 +147,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseArgs<T> a) {
 // a block's substitution.
 template <typename T>
 __global__ void __launch_bounds__(512, 1) k_coarse_cycle_line(CoarseArgs<T> a) {
+  griddep_wait();
   coarse_cycle_body<T, true>(a);
 }
 
@@ -151,6 +157,7 @@ __global__ void __launch_bounds__(512, 1) k_coarse_cycle_line(CoarseArgs<T> a) {
 // hardware cluster barrier.
 template <typename T>
 __global__ void __launch_bounds__(kCoarseClusterThreads, 1) k_coarse_cycle_cluster(CoarseArgs<T> a) {
+  griddep_wait();
   coarse_cycle_body<T, false, ClusterTeam>(a);
 }
 
@@ -161,13 +168,15 @@ static cudaError_t launch_cluster_kernel(int ctas, cudaStream_t s, const CoarseA
   cfg.blockDim = dim3(kCoarseClusterThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = unsigned(ctas);
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl_enabled() ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, k_coarse_cycle_cluster<T>, a);
 }
 
@@ -229,6 +238,7 @@ template <bool NINE>
 __global__ void __launch_bounds__(kNormThreads) k_fine_norm(LevelV<double> L, const double* x,
                                                             const double* b, int what,
                                                             double* partials) {
+  griddep_wait();
   double acc = 0.0;
   for (int j = blockIdx.x + 1; j <= L.ny; j += gridDim.x) {
     for (int i = threadIdx.x + 1; i <= L.nx; i += blockDim.x) {
@@ -247,6 +257,7 @@ __global__ void __launch_bounds__(kNormThreads) k_norm_final(const double* parti
                                                              Scalars* sc, int what, double* hist,
                                                              cudaGraphConditionalHandle cond,
                                                              int use_cond) {
+  griddep_wait();
   double acc = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
   acc = block_sum(acc);
@@ -309,6 +320,7 @@ template <bool NINE>
 __global__ void __launch_bounds__(kNormThreads) k_refine_residual(LevelV<double> L, LevelV<float> F,
                                                                   const Scalars* sc,
                                                                   double* partials) {
+  griddep_wait();
   const double inv = sc->inv;
   double acc = (inv > 1e-28 && inv < 1e28) ? refine_rows<NINE, true>(L, F, inv)
                                            : refine_rows<NINE, false>(L, F, inv);
@@ -321,6 +333,7 @@ __global__ void __launch_bounds__(kNormThreads) k_refine_residual(LevelV<double>
 // 128-byte boundaries, so the pair is one 16-byte FP64 and one 8-byte FP32
 // access; a last unpaired point (i = nx, nx odd) is done alone.
 __global__ void k_refine_update(LevelV<double> L, LevelV<float> F, const Scalars* sc) {
+  griddep_wait();
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + 1;
   const int j = blockIdx.y + 1;
   if (i > L.nx) return;
@@ -340,6 +353,14 @@ __global__ void k_refine_update(LevelV<double> L, LevelV<float> F, const Scalars
 
 }  // namespace
 
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("BMG_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 int max_cluster_ctas(bool fp32) {
   static int cached[2] = {0, 0};
   int& c = cached[fp32 ? 1 : 0];
@@ -357,9 +378,9 @@ void launch_residual(const LevelV<T>& L, bool nine, const T* x, const T* b, T* r
   const dim3 grid(cdiv(L.nx, kTB), L.ny);
   if (!nine) prof_begin(BMG_PROF_FINE_RESID, s);
   if (nine)
-    k_residual<T, true><<<grid, kTB, 0, s>>>(L, x, b, r);
+    launch_pdl(k_residual<T, true>, grid, dim3(kTB), 0, s, L, x, b, r);
   else
-    k_residual<T, false><<<grid, kTB, 0, s>>>(L, x, b, r);
+    launch_pdl(k_residual<T, false>, grid, dim3(kTB), 0, s, L, x, b, r);
   if (!nine) prof_end(BMG_PROF_FINE_RESID, s);
   count_launch();
 }
@@ -368,7 +389,7 @@ template <typename T>
 void launch_restrict(const LevelV<T>& fine, const T* r, LevelV<T> coarse, bool zero_x,
                      cudaStream_t s) {
   const dim3 grid(cdiv(coarse.nx, kTB), coarse.ny);
-  k_restrict<T><<<grid, kTB, 0, s>>>(fine, r, coarse, zero_x ? 1 : 0);
+  launch_pdl(k_restrict<T>, grid, dim3(kTB), 0, s, fine, r, coarse, zero_x ? 1 : 0);
   count_launch();
 }
 
@@ -395,9 +416,9 @@ void launch_resid_restrict(const LevelV<T>& fine, bool nine, LevelV<T> coarse, c
   const dim3 grid(cdiv(coarse.nx, kRRX), cdiv(coarse.ny, kRRY));
   if (!nine) prof_begin(BMG_PROF_FINE_RESID, s);
   if (nine)
-    k_resid_restrict<T, true><<<grid, kRRT, 0, s>>>(fine, coarse);
+    launch_pdl(k_resid_restrict<T, true>, grid, dim3(kRRT), 0, s, fine, coarse);
   else
-    k_resid_restrict<T, false><<<grid, kRRT, 0, s>>>(fine, coarse);
+    launch_pdl(k_resid_restrict<T, false>, grid, dim3(kRRT), 0, s, fine, coarse);
   if (!nine) prof_end(BMG_PROF_FINE_RESID, s);
   count_launch();
 }
@@ -408,7 +429,7 @@ void launch_interp(const LevelV<T>& fine, const T* xc, bool add_r_over_c, cudaSt
   const dim3 grid(cdiv(ncx + 1, kTB), ncy + 1);
   const bool finest = fine.SW == nullptr;
   if (finest) prof_begin(BMG_PROF_FINE_INTERP, s);
-  k_interp<T><<<grid, kTB, 0, s>>>(fine, xc, add_r_over_c ? 1 : 0, out ? out : fine.x);
+  launch_pdl(k_interp<T>, grid, dim3(kTB), 0, s, fine, xc, add_r_over_c ? 1 : 0, out ? out : fine.x);
   if (finest) prof_end(BMG_PROF_FINE_INTERP, s);
   count_launch();
 }
@@ -443,11 +464,11 @@ void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* dev_levels, int thr, cud
   a.n0 = h->n0;
   prof_begin(BMG_PROF_COARSE, s);
   if (a.smoother != BMG_SMOOTH_POINT)
-    k_coarse_cycle_line<T><<<1, 512, 0, s>>>(a);
+    launch_pdl(k_coarse_cycle_line<T>, dim3(1), dim3(512), 0, s, a);
   else if (h->coarse_ctas > 1)
     launch_cluster_kernel<T>(h->coarse_ctas, s, a);
   else
-    k_coarse_cycle<T><<<1, coarse_block_threads(), 0, s>>>(a);
+    launch_pdl(k_coarse_cycle<T>, dim3(1), dim3(coarse_block_threads()), 0, s, a);
   prof_end(BMG_PROF_COARSE, s);
   count_launch();
 }
@@ -457,31 +478,33 @@ void launch_fine_norm(Hierarchy* h, const double* x, const double* b, int what, 
   (void)tol;
   const LevelV<double>& L = h->d.back();
   prof_begin(BMG_PROF_NORM, s);
-  k_fine_norm<false><<<h->npartials, kNormThreads, 0, s>>>(L, x, b, what, h->partials);
-  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, what, h->hist, h->cond,
-                                          in_graph ? 1 : 0);
+  launch_pdl(k_fine_norm<false>, dim3(h->npartials), dim3(kNormThreads), 0, s, L, x, b, what,
+             h->partials);
+  launch_pdl(k_norm_final, dim3(1), dim3(kNormThreads), 0, s, (const double*)h->partials,
+             h->npartials, h->sc, what, h->hist, h->cond, in_graph ? 1 : 0);
   prof_end(BMG_PROF_NORM, s);
   count_launch(2);
 }
 
 void launch_refine_residual(Hierarchy* h, double tol, cudaStream_t s, bool in_graph) {
   (void)tol;
-  k_refine_residual<false><<<h->npartials, kNormThreads, 0, s>>>(h->d.back(), h->f.back(), h->sc,
-                                                                 h->partials);
-  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, h->npartials, h->sc, 1, h->hist, h->cond,
-                                          in_graph ? 1 : 0);
+  launch_pdl(k_refine_residual<false>, dim3(h->npartials), dim3(kNormThreads), 0, s, h->d.back(),
+             h->f.back(), (const Scalars*)h->sc, h->partials);
+  launch_pdl(k_norm_final, dim3(1), dim3(kNormThreads), 0, s, (const double*)h->partials,
+             h->npartials, h->sc, 1, h->hist, h->cond, in_graph ? 1 : 0);
   count_launch(2);
 }
 
 void launch_norm_final(Hierarchy* h, cudaStream_t s, bool in_graph, int n) {
-  k_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, n > 0 ? n : h->npartials, h->sc, 1, h->hist,
-                                          h->cond, in_graph ? 1 : 0);
+  launch_pdl(k_norm_final, dim3(1), dim3(kNormThreads), 0, s, (const double*)h->partials,
+             n > 0 ? n : h->npartials, h->sc, 1, h->hist, h->cond, in_graph ? 1 : 0);
   count_launch();
 }
 
 void launch_refine_update(Hierarchy* h, cudaStream_t s) {
   const LevelV<double>& L = h->d.back();
-  k_refine_update<<<dim3(cdiv((L.nx + 1) / 2, kTB), L.ny), kTB, 0, s>>>(L, h->f.back(), h->sc);
+  launch_pdl(k_refine_update, dim3(cdiv((L.nx + 1) / 2, kTB), L.ny), dim3(kTB), 0, s, L, h->f.back(),
+             (const Scalars*)h->sc);
   count_launch();
 }
 

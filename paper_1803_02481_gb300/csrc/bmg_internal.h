@@ -109,6 +109,37 @@ struct LevelV {
   int cpitch;          // pitch of the coarse grid the P planes live on
 };
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be
+// scheduled while the kernel before it in the stream (or graph) is still
+// finishing; its first statement is griddep_wait(), which returns once that
+// kernel has completed and its memory operations are visible, so nothing it
+// reads or writes can race with it -- only the launch itself overlaps.  No
+// kernel triggers its dependents early (they launch as its blocks exit):
+// triggering right after the wait let waiting blocks of the next kernel hold
+// SM resources and cost the 4095^2 solve 10 % (measured), while the overlap
+// at exit gains 3 % on the launch-bound 255^2 cycle.  (griddepcontrol.wait is
+// a no-op in a kernel launched without the attribute.)  Environment
+// BMG_PDL=0 launches without it.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---------------------------------------------------------------------------
 // Per-point arithmetic.  Every kernel (full-grid or persistent) uses these,
 // so a level gives bit-identical results whichever kernel processes it.

@@ -17,6 +17,7 @@ inline int cdiv(long a, long b) { return int((a + b - 1) / b); }
 template <typename T, bool NINE, int TX, int TY, int NT, int U = (NINE ? 3 : 1)>
 __global__ void __launch_bounds__(NT) k_sweep(LevelV<T> L, const T* __restrict__ xin,
                                               T* __restrict__ xout, unsigned order) {
+  griddep_wait();
   sweep_tile<T, NINE, TX, TY, NT, U>(L, xin, xout, order, blockIdx.x, blockIdx.y);
 }
 
@@ -271,9 +272,9 @@ static void launch_tma_shape(const LevelV<T>& L, const SweepMaps<T>& m, const CU
   // 5-point levels have no SW/NW planes: their maps are passed unused
   const CUtensorMap& msw = NINE ? m.sw : m.b;
   const CUtensorMap& mnw = NINE ? m.nw : m.b;
-  k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, false, false, ZERO>
-      <<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(mx, m.ic, m.w, m.s, m.b, msw, mnw, L, xout,
-                                                        order, m.err, nullptr, nullptr);
+  launch_pdl(k_sweep_tma<T, NINE, TX, TY, NT, MINB, NSTAGE, false, false, ZERO>,
+             dim3(ntiles < cap ? ntiles : cap), dim3(NT), G::SMEM, s, mx, m.ic, m.w, m.s, m.b, msw,
+             mnw, L, xout, order, m.err, (const T*)nullptr, (double*)nullptr);
 }
 
 template <typename T, bool NINE, int TX, int TY, int NT, int MINB, int NSTAGE, bool PRE = false,
@@ -294,9 +295,9 @@ static void launch_tma_pre(const LevelV<double>& L, const SweepMaps<double>& m,
   const int ntiles = ((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
   const int cap =
       sm_count() * tma_resident<double, false, TX, TY, NT, MINB, NSTAGE, true, false, ZERO>();
-  k_sweep_tma<double, false, TX, TY, NT, MINB, NSTAGE, true, false, ZERO>
-      <<<ntiles < cap ? ntiles : cap, NT, G::SMEM, s>>>(mx, m.pb, m.pw, m.ps, m.pe, m.pn, m.pn, L,
-                                                        xout, order, m.err, nullptr, nullptr);
+  launch_pdl(k_sweep_tma<double, false, TX, TY, NT, MINB, NSTAGE, true, false, ZERO>,
+             dim3(ntiles < cap ? ntiles : cap), dim3(NT), G::SMEM, s, mx, m.pb, m.pw, m.ps, m.pe,
+             m.pn, m.pn, L, xout, order, m.err, (const double*)nullptr, (double*)nullptr);
 }
 
 // The same sweep in the pre-smoothing colour order with the fused residual
@@ -309,8 +310,9 @@ static int launch_tma_pre_norm(const LevelV<double>& L, const SweepMaps<double>&
   const int ntiles = ((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
   const int cap = sm_count() * tma_resident<double, false, TX, TY, NT, MINB, NSTAGE, true, true>();
   const int grid = std::min(std::min(ntiles, cap), nmax);
-  k_sweep_tma<double, false, TX, TY, NT, MINB, NSTAGE, true, true><<<grid, NT, G::SMEM, s>>>(
-      mx, m.pb, m.pw, m.ps, m.pe, m.pn, m.pn, L, xout, rb_order(false), m.err, L.C, partials);
+  launch_pdl(k_sweep_tma<double, false, TX, TY, NT, MINB, NSTAGE, true, true>, dim3(grid), dim3(NT),
+             G::SMEM, s, mx, m.pb, m.pw, m.ps, m.pe, m.pn, m.pn, L, xout, rb_order(false), m.err,
+             (const double*)L.C, partials);
   return grid;
 }
 
@@ -432,18 +434,18 @@ void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* 
   } else if (nine) {
     if (small) {
       constexpr int TX = 32, TY = 16;
-      k_sweep<T, true, TX, TY, 128><<<dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), 128, 0, s>>>(
-          L, xin, xout, four_order(reverse));
+      launch_pdl(k_sweep<T, true, TX, TY, 128>, dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), dim3(128), 0, s, L, xin, xout,
+                 four_order(reverse));
     } else {
       constexpr int TX = 128, TY = 32;
-      k_sweep<T, true, TX, TY, 256><<<dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), 256, 0, s>>>(
-          L, xin, xout, four_order(reverse));
+      launch_pdl(k_sweep<T, true, TX, TY, 256>, dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), dim3(256), 0, s, L, xin, xout,
+                 four_order(reverse));
     }
   } else {
     if (small) {
       constexpr int TX = 32, TY = 16;
-      k_sweep<T, false, TX, TY, 128><<<dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), 128, 0, s>>>(
-          L, xin, xout, rb_order(reverse));
+      launch_pdl(k_sweep<T, false, TX, TY, 128>, dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), dim3(128), 0, s, L, xin, xout,
+                 rb_order(reverse));
     } else if (stream_rb_enabled()) {
       constexpr int NT = kStreamNT, R = kStreamR;
       using S = StreamRB<T, NT, R>;
@@ -452,12 +454,12 @@ void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* 
           L, xin, xout, reverse ? 1 : 0);
     } else if (rb_kernel_choice() == 2) {
       constexpr int TX = 128, TY = 32;
-      k_sweep<T, false, TX, TY, 256, 2><<<dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), 256, 0, s>>>(
-          L, xin, xout, rb_order(reverse));
+      launch_pdl(k_sweep<T, false, TX, TY, 256, 2>, dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), dim3(256), 0, s, L, xin, xout,
+                 rb_order(reverse));
     } else {
       constexpr int TX = 128, TY = 32;
-      k_sweep<T, false, TX, TY, 256><<<dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), 256, 0, s>>>(
-          L, xin, xout, rb_order(reverse));
+      launch_pdl(k_sweep<T, false, TX, TY, 256>, dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), dim3(256), 0, s, L, xin, xout,
+                 rb_order(reverse));
     }
   }
   count_launch();

@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(NT, MINB)
                 const __grid_constant__ CUtensorMap mnw, LevelV<T> L, T* __restrict__ xout,
                 unsigned order, int* __restrict__ err, const T* __restrict__ cdiag,
                 double* __restrict__ nrm) {
+  griddep_wait();
   using namespace tma_detail;
   static_assert(!(PRE && NINE), "prescaled levels are 5-point");
   static_assert(!NRM || PRE, "the fused residual is taken on prescaled levels");
