@@ -29,6 +29,7 @@
 namespace bmg3 {
 
 using bmg::count_launch;
+using bmg::griddep_wait;
 using bmg::set_last_error;
 
 constexpr int NA = 13;    // stored couplings per point
@@ -357,6 +358,7 @@ __device__ __forceinline__ T nb_sum27_zero(const Lev3T<T>& L, const T* __restric
 // neighbour, x = (b + 0) / C.
 template <bool SEVEN, typename T, bool ZERO = false>
 __global__ void k3_gs(Lev3T<T> L, int colour) {
+  griddep_wait();
   const int ih = blockIdx.x * blockDim.x + threadIdx.x;
   int i0, j0, k0;
   if (SEVEN) {
@@ -385,6 +387,7 @@ __global__ void k3_gs(Lev3T<T> L, int colour) {
 // that of k3_gs<false>, so a sweep gives the same bits as eight launches.
 template <typename T>
 __global__ void __launch_bounds__(kT) k3_gs27_pair(Lev3T<T> L, int m, int reverse) {
+  griddep_wait();
   const int j0 = 2 * blockIdx.x + (m & 1), k0 = 2 * blockIdx.y + (m >> 1);   // 0-based
   if (j0 >= L.ny || k0 >= L.nz) return;
   const int base = idx3(L, 0, j0 + 1, k0 + 1);
@@ -411,6 +414,7 @@ __device__ __forceinline__ void gs27_row_zero(const Lev3T<T>& L, int base) {
 
 template <typename T, int M>
 __global__ void __launch_bounds__(kT) k3_gs27_pair_zero(Lev3T<T> L) {
+  griddep_wait();
   const int j0 = 2 * blockIdx.x + (M & 1), k0 = 2 * blockIdx.y + (M >> 1);   // 0-based
   if (j0 >= L.ny || k0 >= L.nz) return;
   const int base = idx3(L, 0, j0 + 1, k0 + 1);
@@ -422,6 +426,7 @@ __global__ void __launch_bounds__(kT) k3_gs27_pair_zero(Lev3T<T> L) {
 
 template <bool SEVEN, typename T>
 __global__ void k3_residual(Lev3T<T> L) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
   if (i > L.nx) return;
   const int o = idx3(L, i, j, k);
@@ -431,6 +436,7 @@ __global__ void k3_residual(Lev3T<T> L) {
 // b_c(I) = sum over the fine support of I of P(f, I) r(f); x_c = 0.
 template <typename T>
 __global__ void k3_restrict(Lev3T<T> F, Lev3T<T> Cc) {
+  griddep_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x + 1, J = blockIdx.y + 1, K = blockIdx.z + 1;
   if (I > Cc.nx) return;
   T s = T(0);
@@ -468,6 +474,7 @@ __device__ __forceinline__ void interp_point(const Lev3T<T>& F, const Lev3T<T>& 
 
 template <typename T>
 __global__ void k3_interp(Lev3T<T> F, Lev3T<T> Cc) {
+  griddep_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y + 1, k = blockIdx.z + 1;
   if (2 * t + 1 <= F.nx) interp_point(F, Cc, 2 * t + 1, j, k);
   if (2 * t + 2 <= F.nx) interp_point(F, Cc, 2 * t + 2, j, k);
@@ -491,6 +498,7 @@ __device__ __forceinline__ double block_sum(double v) {
 
 // what 0: ||b||^2; 1: ||b - A x||^2 (7-point finest level)
 __global__ void k3_norm(Lev3 L, int what, double* __restrict__ partials) {
+  griddep_wait();
   double acc = 0.0;
   const int n = L.nx * L.ny * L.nz;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -518,6 +526,7 @@ __global__ void k3_norm(Lev3 L, int what, double* __restrict__ partials) {
 // each colour), in k3_norm's fixed grid and order.
 __global__ void __launch_bounds__(kNormThreads) k3_gs_norm(Lev3 L, double* __restrict__ out,
                                                            double* __restrict__ partials) {
+  griddep_wait();
   const int hx = (L.nx + 1) / 2;
   const long n = long(hx) * L.ny * L.nz;
   double acc = 0.0;
@@ -553,6 +562,7 @@ struct Scal3 {
 };
 
 __global__ void k3_norm_final(const double* __restrict__ partials, int n, Scal3* sc, int what) {
+  griddep_wait();
   double acc = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
   acc = block_sum(acc);
@@ -580,6 +590,7 @@ __global__ void k3_norm_final(const double* __restrict__ partials, int n, Scal3*
 // residual norm, sc->rnorm2) with x32 = 0.
 __global__ void k3_refine_residual(Lev3 L, Lev3f Lf, const Scal3* __restrict__ sc,
                                    double* __restrict__ partials) {
+  griddep_wait();
   const double inv = sc->rnorm2 > 0.0 ? 1.0 / sqrt(sc->rnorm2) : 0.0;
   double acc = 0.0;
   const int n = L.nx * L.ny * L.nz;
@@ -598,6 +609,7 @@ __global__ void k3_refine_residual(Lev3 L, Lev3f Lf, const Scal3* __restrict__ s
 // The new residual norm; the previous one becomes the scale the right-hand
 // side just cast was divided by.
 __global__ void k3_refine_norm_final(const double* __restrict__ partials, int n, Scal3* sc) {
+  griddep_wait();
   double acc = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
   acc = block_sum(acc);
@@ -609,6 +621,7 @@ __global__ void k3_refine_norm_final(const double* __restrict__ partials, int n,
 
 // x += scale * e on the finest level.
 __global__ void k3_refine_update(Lev3 L, Lev3f Lf, const Scal3* __restrict__ sc) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
   if (i > L.nx) return;
   const int o = idx3(L, i, j, k);
@@ -665,6 +678,7 @@ __global__ void k3_pcg_init(Lev3 F, const double* __restrict__ X, const double* 
 // Q = A P (the negated residual of P for a zero right-hand side), partials of P.Q
 __global__ void k3_pcg_ap(Lev3 F, const double* __restrict__ P, double* __restrict__ Q,
                           double* __restrict__ partials) {
+  griddep_wait();
   const double sum = pcg_points(F, [&](int o, double acc) {
     const double q = -(fma(-F.C[o], P[o], 0.0) + nb_sum<true>(F, P, o));
     Q[o] = q;
@@ -677,6 +691,7 @@ __global__ void k3_pcg_ap(Lev3 F, const double* __restrict__ P, double* __restri
 __global__ void k3_pcg_xr(Lev3 F, double* __restrict__ X, const double* __restrict__ P,
                           const double* __restrict__ Q, const Scal3* __restrict__ sc,
                           double* __restrict__ partials) {
+  griddep_wait();
   const double a = sc->alpha;
   const double sum = pcg_points(F, [&](int o, double acc) {
     X[o] = fma(a, P[o], X[o]);
@@ -690,12 +705,14 @@ __global__ void k3_pcg_xr(Lev3 F, double* __restrict__ X, const double* __restri
 
 // partials of r.z
 __global__ void k3_pcg_rz(Lev3 F, double* __restrict__ partials) {
+  griddep_wait();
   const double sum = pcg_points(F, [&](int o, double acc) { return fma(F.b[o], F.x[o], acc); });
   if (threadIdx.x == 0) partials[blockIdx.x] = sum;
 }
 
 // P = z + beta P
 __global__ void k3_pcg_p(Lev3 F, double* __restrict__ P, const Scal3* __restrict__ sc) {
+  griddep_wait();
   const double beta = sc->beta;
   pcg_points(F, [&](int o, double acc) {
     P[o] = fma(beta, P[o], F.x[o]);
@@ -707,6 +724,7 @@ __global__ void k3_pcg_p(Lev3 F, double* __restrict__ P, const Scal3* __restrict
 // direction); 1: alpha = rz / sum (sum = P.Q); 2: beta = sum / rz, rz = sum
 // (sum = r.z of the new residual).  A zero denominator gives 0.
 __global__ void k3_pcg_scalar(const double* __restrict__ partials, int n, Scal3* sc, int what) {
+  griddep_wait();
   double acc = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
   acc = block_sum(acc);
@@ -726,6 +744,7 @@ __global__ void k3_pcg_scalar(const double* __restrict__ partials, int n, Scal3*
 // x32 = 0, s = ||r|| of the latest residual (sc->rnorm, sc->rinv, set once by
 // k3_norm_final); then z = s e.
 __global__ void k3_pcg_cast(Lev3 F, Lev3f Ff, const Scal3* __restrict__ sc) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
   if (i > F.nx) return;
   const int of = idx3(Ff, i, j, k);
@@ -733,6 +752,7 @@ __global__ void k3_pcg_cast(Lev3 F, Lev3f Ff, const Scal3* __restrict__ sc) {
   Ff.x[of] = 0.0f;
 }
 __global__ void k3_pcg_uncast(Lev3 F, Lev3f Ff, const Scal3* __restrict__ sc) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1, k = blockIdx.z + 1;
   if (i > F.nx) return;
   F.x[idx3(F, i, j, k)] = sc->rnorm * double(Ff.x[idx3(Ff, i, j, k)]);
@@ -786,6 +806,7 @@ __global__ void k3_coarse_factor(Lev3 L0, double* __restrict__ lo, double* __res
 template <typename T>
 __global__ void k3_coarse_solve(Lev3T<T> L0, const double* __restrict__ lo,
                                 const double* __restrict__ idiag) {
+  griddep_wait();
   __shared__ double v[BMG_MAX_COARSEST];
   const int nx = L0.nx, ny = L0.ny, n = nx * ny * L0.nz;
   for (int r = threadIdx.x; r < n; r += blockDim.x)
@@ -909,18 +930,17 @@ void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t 
       if (!seven && h->gs27_pairs && z) {
         const dim3 g0((V.ny + 1) / 2, (V.nz + 1) / 2), g1(V.ny / 2, (V.nz + 1) / 2),
             g2((V.ny + 1) / 2, V.nz / 2), g3(V.ny / 2, V.nz / 2);
-        k3_gs27_pair_zero<T, 0><<<g0, kT, 0, s>>>(V);
-        k3_gs27_pair_zero<T, 1><<<g1, kT, 0, s>>>(V);
-        k3_gs27_pair_zero<T, 2><<<g2, kT, 0, s>>>(V);
-        k3_gs27_pair_zero<T, 3><<<g3, kT, 0, s>>>(V);
+        bmg::launch_pdl(k3_gs27_pair_zero<T, 0>, g0, dim3(kT), 0, s, V);
+        bmg::launch_pdl(k3_gs27_pair_zero<T, 1>, g1, dim3(kT), 0, s, V);
+        bmg::launch_pdl(k3_gs27_pair_zero<T, 2>, g2, dim3(kT), 0, s, V);
+        bmg::launch_pdl(k3_gs27_pair_zero<T, 3>, g3, dim3(kT), 0, s, V);
         count_launch(4);
         continue;
       }
       if (!seven && h->gs27_pairs) {
         for (int p0 = 0; p0 < 4; ++p0) {
           const int m = reverse ? 3 - p0 : p0;
-          k3_gs27_pair<<<dim3((V.ny + 1 - (m & 1)) / 2, (V.nz + 1 - (m >> 1)) / 2), kT, 0, s>>>(
-              V, m, reverse ? 1 : 0);
+          bmg::launch_pdl(k3_gs27_pair<T>, dim3((V.ny + 1 - (m & 1)) / 2, (V.nz + 1 - (m >> 1)) / 2), dim3(kT), 0, s, V, m, reverse ? 1 : 0);
           count_launch();
         }
         continue;
@@ -928,11 +948,11 @@ void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t 
       for (int c0 = 0; c0 < nc; ++c0) {
         const int c = reverse ? nc - 1 - c0 : c0;
         if (seven && z)
-          k3_gs<true, T, true><<<dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), kT, 0, s>>>(V, c);
+          bmg::launch_pdl(k3_gs<true, T, true>, dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), dim3(kT), 0, s, V, c);
         else if (seven)
-          k3_gs<true><<<dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), kT, 0, s>>>(V, c);
+          bmg::launch_pdl(k3_gs<true, T>, dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), dim3(kT), 0, s, V, c);
         else
-          k3_gs<false><<<dim3(cdiv((V.nx + 1) / 2, kT), (V.ny + 1) / 2, (V.nz + 1) / 2), kT, 0, s>>>(V, c);
+          bmg::launch_pdl(k3_gs<false, T>, dim3(cdiv((V.nx + 1) / 2, kT), (V.ny + 1) / 2, (V.nz + 1) / 2), dim3(kT), 0, s, V, c);
         count_launch();
       }
       if (seven) bmg::prof_end(BMG_PROF_FINE_SMOOTH, s);
@@ -945,17 +965,17 @@ void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t 
     sweep(l, h->opt.nu1 - (skip_first && l == L - 1 ? 1 : 0), false,
           !(skip_first && l == L - 1) && (l < L - 1 || top_zero));
     if (l == L - 1)
-      k3_residual<true><<<grid_pts(V), kT, 0, s>>>(V);
+      bmg::launch_pdl(k3_residual<true, T>, dim3(grid_pts(V)), dim3(kT), 0, s, V);
     else
-      k3_residual<false><<<grid_pts(V), kT, 0, s>>>(V);
-    k3_restrict<<<grid_pts(lv[l - 1]), kT, 0, s>>>(V, lv[l - 1]);
+      bmg::launch_pdl(k3_residual<false, T>, dim3(grid_pts(V)), dim3(kT), 0, s, V);
+    bmg::launch_pdl(k3_restrict<T>, dim3(grid_pts(lv[l - 1])), dim3(kT), 0, s, V, lv[l - 1]);
     count_launch(2);
   }
-  k3_coarse_solve<<<1, 256, 0, s>>>(lv[0], h->chol, h->chol_idiag);
+  bmg::launch_pdl(k3_coarse_solve<T>, dim3(1), dim3(256), 0, s, lv[0], h->chol, h->chol_idiag);
   count_launch();
   for (int l = 1; l < L; ++l) {
     bmg::NvtxRange r("interp_leg", l);
-    k3_interp<<<dim3(cdiv((lv[l].nx + 1) / 2, kT), lv[l].ny, lv[l].nz), kT, 0, s>>>(lv[l], lv[l - 1]);
+    bmg::launch_pdl(k3_interp<T>, dim3(cdiv((lv[l].nx + 1) / 2, kT), lv[l].ny, lv[l].nz), dim3(kT), 0, s, lv[l], lv[l - 1]);
     count_launch();
     sweep(l, h->opt.nu2, true, false);
   }
@@ -964,9 +984,8 @@ void enqueue_vcycle3(bmg3_hierarchy* h, std::vector<Lev3T<T>>& lv, cudaStream_t 
 // FP32 refinement: the residual of the current x as the next FP32
 // right-hand side, and its norm (the stop test).
 void enqueue_refine_residual(bmg3_hierarchy* h, cudaStream_t s) {
-  k3_refine_residual<<<kNormBlocks, kNormThreads, 0, s>>>(h->lv[h->L - 1], h->lv32[h->L - 1], h->sc,
-                                                         h->partials);
-  k3_refine_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc);
+  bmg::launch_pdl(k3_refine_residual, dim3(kNormBlocks), dim3(kNormThreads), 0, s, h->lv[h->L - 1], h->lv32[h->L - 1], h->sc, h->partials);
+  bmg::launch_pdl(k3_refine_norm_final, dim3(1), dim3(kNormThreads), 0, s, h->partials, kNormBlocks, h->sc);
   count_launch(2);
 }
 
@@ -980,13 +999,13 @@ void enqueue_step(bmg3_hierarchy* h, cudaStream_t s) {
     // the refinement residual zeroed the FP32 finest iterate
     enqueue_vcycle3<float>(h, h->lv32, s, false, true);
     const Lev3& F = h->lv[L - 1];
-    k3_refine_update<<<grid_pts(F), kT, 0, s>>>(F, h->lv32[L - 1], h->sc);
+    bmg::launch_pdl(k3_refine_update, dim3(grid_pts(F)), dim3(kT), 0, s, F, h->lv32[L - 1], h->sc);
     count_launch();
     enqueue_refine_residual(h, s);
   } else {
     enqueue_vcycle3<double>(h, h->lv, s);
-    k3_norm<<<kNormBlocks, kNormThreads, 0, s>>>(h->lv[L - 1], 1, h->partials);
-    k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+    bmg::launch_pdl(k3_norm, dim3(kNormBlocks), dim3(kNormThreads), 0, s, h->lv[L - 1], 1, h->partials);
+    bmg::launch_pdl(k3_norm_final, dim3(1), dim3(kNormThreads), 0, s, h->partials, kNormBlocks, h->sc, 1);
     count_launch(2);
   }
   cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
@@ -998,7 +1017,7 @@ void enqueue_first_sweep3(bmg3_hierarchy* h, cudaStream_t s) {
   const Lev3& V = h->lv[h->L - 1];
   bmg::prof_begin(BMG_PROF_FINE_SMOOTH, s);
   for (int c = 0; c < 2; ++c)
-    k3_gs<true><<<dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), kT, 0, s>>>(V, c);
+    bmg::launch_pdl(k3_gs<true, double>, dim3(cdiv((V.nx + 1) / 2, kT), V.ny, V.nz), dim3(kT), 0, s, V, c);
   bmg::prof_end(BMG_PROF_FINE_SMOOTH, s);
   count_launch(2);
 }
@@ -1012,8 +1031,8 @@ void enqueue_fused_step(bmg3_hierarchy* h, double* in, double* out, cudaStream_t
   lv[L - 1].x = in;
   enqueue_vcycle3<double>(h, lv, s, true);
   bmg::prof_begin(BMG_PROF_NORM, s);
-  k3_gs_norm<<<kNormBlocks, kNormThreads, 0, s>>>(lv[L - 1], out, h->partials);
-  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+  bmg::launch_pdl(k3_gs_norm, dim3(kNormBlocks), dim3(kNormThreads), 0, s, lv[L - 1], out, h->partials);
+  bmg::launch_pdl(k3_norm_final, dim3(1), dim3(kNormThreads), 0, s, h->partials, kNormBlocks, h->sc, 1);
   bmg::prof_end(BMG_PROF_NORM, s);
   count_launch(2);
   cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
@@ -1026,9 +1045,9 @@ void enqueue_precond(bmg3_hierarchy* h, cudaStream_t s) {
   const int L = h->L;
   if (h->refine) {
     const Lev3& F = h->lv[L - 1];
-    k3_pcg_cast<<<grid_pts(F), kT, 0, s>>>(F, h->lv32[L - 1], h->sc);
+    bmg::launch_pdl(k3_pcg_cast, dim3(grid_pts(F)), dim3(kT), 0, s, F, h->lv32[L - 1], h->sc);
     enqueue_vcycle3<float>(h, h->lv32, s, false, true);   // the cast zeroed z
-    k3_pcg_uncast<<<grid_pts(F), kT, 0, s>>>(F, h->lv32[L - 1], h->sc);
+    bmg::launch_pdl(k3_pcg_uncast, dim3(grid_pts(F)), dim3(kT), 0, s, F, h->lv32[L - 1], h->sc);
     count_launch(2);
   } else {
     enqueue_vcycle3<double>(h, h->lv, s, false, true);    // z = 0 from the update
@@ -1041,13 +1060,13 @@ void enqueue_precond(bmg3_hierarchy* h, cudaStream_t s) {
 void enqueue_pcg_iter(bmg3_hierarchy* h, bool first, cudaStream_t s) {
   const Lev3& F = h->lv[h->L - 1];
   enqueue_precond(h, s);
-  k3_pcg_rz<<<kNormBlocks, kNormThreads, 0, s>>>(F, h->partials);
-  k3_pcg_scalar<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, first ? 0 : 2);
-  k3_pcg_p<<<kNormBlocks, kNormThreads, 0, s>>>(F, h->pP, h->sc);
-  k3_pcg_ap<<<kNormBlocks, kNormThreads, 0, s>>>(F, h->pP, h->pQ, h->partials);
-  k3_pcg_scalar<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
-  k3_pcg_xr<<<kNormBlocks, kNormThreads, 0, s>>>(F, h->pX, h->pP, h->pQ, h->sc, h->partials);
-  k3_norm_final<<<1, kNormThreads, 0, s>>>(h->partials, kNormBlocks, h->sc, 1);
+  bmg::launch_pdl(k3_pcg_rz, dim3(kNormBlocks), dim3(kNormThreads), 0, s, F, h->partials);
+  bmg::launch_pdl(k3_pcg_scalar, dim3(1), dim3(kNormThreads), 0, s, h->partials, kNormBlocks, h->sc, first ? 0 : 2);
+  bmg::launch_pdl(k3_pcg_p, dim3(kNormBlocks), dim3(kNormThreads), 0, s, F, h->pP, h->sc);
+  bmg::launch_pdl(k3_pcg_ap, dim3(kNormBlocks), dim3(kNormThreads), 0, s, F, h->pP, h->pQ, h->partials);
+  bmg::launch_pdl(k3_pcg_scalar, dim3(1), dim3(kNormThreads), 0, s, h->partials, kNormBlocks, h->sc, 1);
+  bmg::launch_pdl(k3_pcg_xr, dim3(kNormBlocks), dim3(kNormThreads), 0, s, F, h->pX, h->pP, h->pQ, h->sc, h->partials);
+  bmg::launch_pdl(k3_norm_final, dim3(1), dim3(kNormThreads), 0, s, h->partials, kNormBlocks, h->sc, 1);
   count_launch(7);
   cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scal3), cudaMemcpyDeviceToHost, s);
 }
