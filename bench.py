@@ -375,6 +375,7 @@ def run_ours(args, rank, world, local_rank):
         cnt, cms = bm.profile_read(cname)
         breakdown[cname] = {"brackets": cnt, "ms_per_step": cms}
     nprof, prof_ms = bm.profile_read("fine_smooth")
+    nres, res_ms = bm.profile_read("fine_resid")
     bm.profile_set(())
     ms, value = aggregate(torch, ms, n_fine * args.steps, world, dev)
     info = infos[-1]
@@ -493,6 +494,19 @@ def run_ours(args, rank, world, local_rank):
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
                     "traffic": traffic, **common}
 
+    # the fine-level residual kernel (r = b - A x before the restriction):
+    # 48 algorithmic B per unknown (C, W, S, x, b read, r written) per launch
+    # (FP64 only: FP32 levels take the residual and the restriction as one kernel)
+    res_per_ms = res_ms / max(1, nres)
+    res_gbs = 6 * word * n_fine / (res_per_ms / 1e3) / 1e9 if res_per_ms > 0 else None
+    roofline_residual = None if args.precision != "fp64" else {
+                         "kernel": "k_residual<double, 5-point>: fine-level residual",
+                         "per_launch_ms": res_per_ms, "launches_timed": nres,
+                         "algorithmic_bytes_per_unknown": 6 * word, "units_per_launch": n_fine,
+                         "achieved": res_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": res_gbs / peaks["hbm_gbs"] if res_gbs else None,
+                         "timing": "CUDA events around every fine residual of one full profiled step"}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
@@ -505,7 +519,7 @@ def run_ours(args, rank, world, local_rank):
             "coarse_ctas": info.coarse_ctas, "unknown_cycles_per_s": value * info.cycles,
             "setup_ms": info.setup_ms, "gpu_launches": int(launches), "roofline": roofline, "e2e": e2e,
             "calibration": calib, "breakdown": breakdown,
-            "clocks": clk.summary(), **extra}
+            "roofline_fine_residual": roofline_residual, "clocks": clk.summary(), **extra}
     # the CPU baseline is reported at N = 1 only (rank 0)
     if rank == 0 and world == 1 and not args.quick and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
