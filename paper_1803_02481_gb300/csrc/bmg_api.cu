@@ -487,7 +487,13 @@ static void fine_presweep(Hierarchy* h, cudaStream_t s, bool with_norm, bool in_
   if (with_norm) {
     prof_begin(BMG_PROF_NORM, s);
     const int n = launch_sweep_pre_norm(F, m, F.x, F.x2, h->partials, h->npartials, s);
-    launch_norm_final(h, s, in_graph, n);
+    if (n > 0) {
+      launch_norm_final(h, s, in_graph, n);
+    } else {
+      // (not reached while fused_norm_on holds) the same result in two passes
+      launch_fine_norm(h, F.x, F.b, 1, 0.0, s, in_graph);
+      launch_sweep<double>(F, false, false, F.x, F.x2, s, m);
+    }
     prof_end(BMG_PROF_NORM, s);
   } else {
     prof_begin(BMG_PROF_FINE_SMOOTH, s);
