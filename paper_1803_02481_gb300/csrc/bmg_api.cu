@@ -484,16 +484,16 @@ static bool fused_norm_on(const Hierarchy* h) {
 static void fine_presweep(Hierarchy* h, cudaStream_t s, bool with_norm, bool in_graph) {
   LevelV<double>& F = h->d.back();
   const SweepMaps<double>* m = level_maps<double>(h, h->L - 1);
+  const bool fusable = m && m->pre && (F.x == m->xp || F.x == m->x2p);
+  if (with_norm && !fusable) {
+    // (not reached while fused_norm_on holds) the same result in two passes
+    launch_fine_norm(h, F.x, F.b, 1, 0.0, s, in_graph);
+    with_norm = false;
+  }
   if (with_norm) {
     prof_begin(BMG_PROF_NORM, s);
     const int n = launch_sweep_pre_norm(F, m, F.x, F.x2, h->partials, h->npartials, s);
-    if (n > 0) {
-      launch_norm_final(h, s, in_graph, n);
-    } else {
-      // (not reached while fused_norm_on holds) the same result in two passes
-      launch_fine_norm(h, F.x, F.b, 1, 0.0, s, in_graph);
-      launch_sweep<double>(F, false, false, F.x, F.x2, s, m);
-    }
+    launch_norm_final(h, s, in_graph, n);
     prof_end(BMG_PROF_NORM, s);
   } else {
     prof_begin(BMG_PROF_FINE_SMOOTH, s);
