@@ -334,6 +334,26 @@ __device__ __forceinline__ T nb_sum(const Lev3T<T>& L, const T* __restrict__ x, 
 __host__ __device__ constexpr bool zero_term3(int c, int di, int dj, int dk) {
   return (dk ? (c & 4) != 0 : dj ? (c & 2) != 0 : (c & 1) != 0);
 }
+// Checked by brute force over every colour and offset: the rule above keeps
+// exactly the neighbours whose colour (c with the offset's parities flipped)
+// precedes c, 0, 2, 6, 8, 18, 20, 24, 26 of them for colours 0..7.
+constexpr bool zero_terms3_ok() {
+  const int want[8] = {0, 2, 6, 8, 18, 20, 24, 26};
+  for (int c = 0; c < 8; ++c) {
+    int n = 0;
+    for (int dk = -1; dk <= 1; ++dk)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          if (!di && !dj && !dk) continue;
+          const int nb = c ^ ((dk ? 4 : 0) | (dj ? 2 : 0) | (di ? 1 : 0));
+          if (zero_term3(c, di, dj, dk) != (nb < c)) return false;
+          n += zero_term3(c, di, dj, dk) ? 1 : 0;
+        }
+    if (n != want[c]) return false;
+  }
+  return true;
+}
+static_assert(zero_terms3_ok(), "zero-start neighbour rule");
 
 template <int C, typename T>
 __device__ __forceinline__ T nb_sum27_zero(const Lev3T<T>& L, const T* __restrict__ x, int o) {
