@@ -468,14 +468,15 @@ template void enqueue_vcycle<float>(Hierarchy*, std::vector<LevelV<float>>&, con
 // next cycle's first pre-sweep with the residual of the cycle's result, stop
 // test }.  On exit the result is the iterate that sweep read; its output is
 // dropped.  Applies to FP64 V-cycles with point smoothing whose finest level
-// is prescaled and swept outside the persistent coarse kernel, with nu1 and
-// nu2 >= 1 (environment BMG_FUSED_NORM=0 at setup turns it off).
+// is swept outside the persistent coarse kernel by the prescaled TMA kernel
+// or the small tiled one, with nu1 and nu2 >= 1 (environment
+// BMG_FUSED_NORM=0 at setup turns it off).
 static bool fused_norm_on(const Hierarchy* h) {
   const int L = h->L;
   const SweepMaps<double>* m = level_maps<double>(h, L - 1);
   return h->fused_norm_allowed && h->opt.solver == BMG_SOLVER_VCYCLE && h->opt.precision == BMG_FP64 &&
          h->opt.smoother == BMG_SMOOTH_POINT && h->opt.nu1 >= 1 && h->opt.nu2 >= 1 &&
-         h->threshold < L && m && m->pre;
+         h->threshold < L && sweep_norm_partials(h->d.back(), m, h->npartials) > 0;
 }
 
 // The finest level's first pre-smoothing sweep of a cycle: plain, or with
@@ -484,7 +485,8 @@ static bool fused_norm_on(const Hierarchy* h) {
 static void fine_presweep(Hierarchy* h, cudaStream_t s, bool with_norm, bool in_graph) {
   LevelV<double>& F = h->d.back();
   const SweepMaps<double>* m = level_maps<double>(h, h->L - 1);
-  const bool fusable = m && m->pre && (F.x == m->xp || F.x == m->x2p);
+  const bool fusable = sweep_norm_partials(F, m, h->npartials) > 0 &&
+                       (!(m && m->pre) || F.x == m->xp || F.x == m->x2p);
   if (with_norm && !fusable) {
     // (not reached while fused_norm_on holds) the same result in two passes
     launch_fine_norm(h, F.x, F.b, 1, 0.0, s, in_graph);

@@ -489,10 +489,14 @@ void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* 
 // partials[0 .. grid) (grid <= nmax, returned).  Valid only when the sweep
 // before it on this level was a post-smoothing sweep (reverse colour order)
 // and nothing changed the iterate since; returns 0 and launches nothing when
-// the level has no prescaled TMA maps for xin.
+// the level cannot take it (see sweep_norm_partials).
 int launch_sweep_pre_norm(const LevelV<double>& L, const SweepMaps<double>* maps,
                           const double* xin, double* xout, double* partials, int nmax,
                           cudaStream_t s);
+// Partials that sweep writes on this level (at most nmax), 0 where it cannot
+// run: prescaled TMA levels, and 5-point levels narrower than 1024 (swept by
+// the small tiled kernel) with at most nmax tiles.
+int sweep_norm_partials(const LevelV<double>& L, const SweepMaps<double>* maps, int nmax);
 template <typename T>
 void launch_coarse_cycle(Hierarchy* h, const LevelV<T>* levels, int threshold,
                          cudaStream_t s);

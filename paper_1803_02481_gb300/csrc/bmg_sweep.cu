@@ -21,6 +21,16 @@ __global__ void __launch_bounds__(NT) k_sweep(LevelV<T> L, const T* __restrict__
   sweep_tile<T, NINE, TX, TY, NT, U>(L, xin, xout, order, blockIdx.x, blockIdx.y);
 }
 
+// The small-level red-black sweep carrying the stop test (sweep_tile's NRM):
+// pre-smoothing order, one partial of the squared residual per block.
+template <int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_sweep_nrm(LevelV<double> L, const double* __restrict__ xin,
+                                                  double* __restrict__ xout, double* __restrict__ nrm) {
+  griddep_wait();
+  sweep_tile<double, false, TX, TY, NT, 1, true>(L, xin, xout, rb_order(false), blockIdx.x,
+                                                 blockIdx.y, nrm);
+}
+
 }  // namespace
 
 // Streaming kernel shape: 64 threads own a 126-column strip, 32 rows per
@@ -407,10 +417,29 @@ static void launch_sweep_tma(const LevelV<T>& L, const SweepMaps<T>& m, bool rev
 }
 
 
+// Tiles of the small-level red-black sweep (launch_sweep's `small` shape).
+constexpr int kSmallTX = 32, kSmallTY = 16;
+
+int sweep_norm_partials(const LevelV<double>& L, const SweepMaps<double>* maps, int nmax) {
+  if (maps && maps->pre) return std::min(nmax, 4 * sm_count());
+  if (L.SW != nullptr || L.nx >= 1024) return 0;
+  const int tiles = cdiv(L.nx, kSmallTX) * cdiv(L.ny, kSmallTY);
+  return tiles <= nmax ? tiles : 0;
+}
+
 int launch_sweep_pre_norm(const LevelV<double>& L, const SweepMaps<double>* maps,
                           const double* xin, double* xout, double* partials, int nmax,
                           cudaStream_t s) {
-  if (!maps || !maps->pre || nmax < 1 || (xin != maps->xp && xin != maps->x2p)) return 0;
+  if (!(maps && maps->pre)) {
+    // a level swept by the small tiled kernel: one partial per tile
+    const int tiles = sweep_norm_partials(L, maps, nmax);
+    if (tiles < 1) return 0;
+    launch_pdl(k_sweep_nrm<kSmallTX, kSmallTY, 128>, dim3(cdiv(L.nx, kSmallTX), cdiv(L.ny, kSmallTY)),
+               dim3(128), 0, s, L, xin, xout, partials);
+    count_launch();
+    return tiles;
+  }
+  if (nmax < 1 || (xin != maps->xp && xin != maps->x2p)) return 0;
   const CUtensorMap& mx = xin == maps->xp ? maps->x : maps->x2;
   int grid = 0;
 #define BMG_TMA_PRE_NORM_LAUNCH(TX, TY, NT, MB, NS) \
@@ -443,7 +472,7 @@ void launch_sweep(const LevelV<T>& L, bool nine, bool reverse, const T* xin, T* 
     }
   } else {
     if (small) {
-      constexpr int TX = 32, TY = 16;
+      constexpr int TX = kSmallTX, TY = kSmallTY;
       launch_pdl(k_sweep<T, false, TX, TY, 128>, dim3(cdiv(L.nx, TX), cdiv(L.ny, TY)), dim3(128), 0, s, L, xin, xout,
                  rb_order(reverse));
     } else if (stream_rb_enabled()) {

@@ -56,9 +56,17 @@ static_assert(zero_start_mask(true, 0) == 0u && zero_start_mask(true, 1) == 0x03
                   zero_start_mask(true, 2) == 0xFCu && zero_start_mask(true, 3) == 0xFFu,
               "four-colour zero-start masks");
 
-template <typename T, bool NINE, int TX, int TY, int NT, int UB = (NINE ? 3 : 1)>
+// NRM (5-point, forward order, double): the sweep that carries the stop test
+// (the same argument as the TMA sweep's: after a reverse-order sweep the
+// first colour's update is a no-op, so that phase is skipped, and the second
+// phase's C (x_new - x_old) is the residual of the iterate read); the squared
+// residual is summed per block into nrm[by * gridDim.x + bx].
+template <typename T, bool NINE, int TX, int TY, int NT, int UB = (NINE ? 3 : 1), bool NRM = false>
 __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restrict__ xin,
-                                           T* __restrict__ xout, unsigned order, int bx, int by) {
+                                           T* __restrict__ xout, unsigned order, int bx, int by,
+                                           double* __restrict__ nrm = nullptr) {
+  static_assert(!NRM || (!NINE && UB == 1), "the fused stop test is a red-black sweep");
+  double nacc = 0.0;
   constexpr int NC = NINE ? 4 : 2;
   constexpr int H = NC, HY = kColourHaloRows;   // halo columns, halo rows
   constexpr int SX = TX + 2 * H, SY = TY + 2 * HY;
@@ -79,6 +87,7 @@ __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restri
 
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
+    if (NRM && k == 0) continue;
     const unsigned mask = (order >> (4 * k)) & 0xFu;
     const int gx = colour_grow_x(NC, k), gy = colour_grow_y(NC, k);
     const int r0 = HY - gy, r1 = HY + TY + gy;   // region rows [r0, r1)
@@ -99,6 +108,7 @@ __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restri
       constexpr int U = UB;
       for (int t0 = threadIdx.x; t0 < npts; t0 += NT * U) {
         GsCoef<T, NINE> cf_[U];
+        T cc[U];
         int sp[U];
         bool ok[U];
 #pragma unroll
@@ -112,13 +122,19 @@ __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restri
           if (ok[u]) {
             const int o = j * p + i;
             cf_[u] = gs_load<T, NINE>(L, o, __ldg(L.b + o));
+            if (NRM) cc[u] = __ldg(L.C + o);
           }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (!ok[u]) continue;
           T* xp = xs + sp[u];
-          *xp = gs_apply<T, NINE>(cf_[u], [&](int dx, int dy) { return xp[dx + dy * SX]; });
+          const T xn = gs_apply<T, NINE>(cf_[u], [&](int dx, int dy) { return xp[dx + dy * SX]; });
+          if (NRM && k == NC - 1) {
+            const double rv = double(cc[u]) * double(xn - *xp);
+            nacc = fma(rv, rv, nacc);
+          }
+          *xp = xn;
         }
       }
     }
@@ -129,6 +145,19 @@ __device__ __forceinline__ void sweep_tile(const LevelV<T>& L, const T* __restri
     const int r = e / TX, c = e - r * TX;
     const int i = ib + H + c, j = jb + HY + r;
     if (i <= nx && j <= ny) xout[j * p + i] = xs[(r + HY) * SX + c + H];
+  }
+  if (NRM) {
+    // fixed reduction tree: warps, then warp sums in order
+    __shared__ double wsum[NT / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, off);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = nacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0;
+      for (int w = 0; w < NT / 32; ++w) a += wsum[w];
+      nrm[by * gridDim.x + bx] = a;
+    }
   }
 }
 

@@ -178,7 +178,10 @@ def test_every_threshold_gives_identical_iterates(name):
     persistent kernel, run by one block or by a thread-block cluster;
     per-point arithmetic is shared and the points of a colour are
     independent, so results are bit-identical for every threshold and every
-    number of blocks."""
+    number of blocks.  While the finest level is swept outside the
+    persistent kernel the stop test runs inside its next sweep (the same bits
+    for every such threshold); with the finest level inside the kernel it is
+    the separate norm pass, equal to rounding."""
     pr = problem(name)
     L = oracle_hierarchy(name).nlevels
     ref = None
@@ -192,7 +195,11 @@ def test_every_threshold_gives_identical_iterates(name):
                 ref = (xn, info.cycles, info.rel_resid)
             else:
                 assert np.array_equal(xn, ref[0]), (ctas, thr)
-                assert info.cycles == ref[1] and info.rel_resid == ref[2]
+                assert info.cycles == ref[1]
+                if thr < L:
+                    assert info.rel_resid == ref[2]
+                else:
+                    assert abs(info.rel_resid - ref[2]) <= 1e-6 * ref[2] + 2e-15
             hg.destroy()
 
 
@@ -841,10 +848,12 @@ def test_smoother_option_is_checked():
     assert e.value.code == bm.BMG_EINVAL
 
 
+@pytest.mark.parametrize("name", ["wide2047x127", "blocks255"])
 @pytest.mark.parametrize("stream_launched,nu", [(False, (2, 1)), (True, (2, 1)), (False, (1, 1)),
                                                 (True, (3, 2)), (False, (0, 1)), (False, (1, 0))])
-def test_stop_test_fused_into_the_next_fine_sweep(monkeypatch, stream_launched, nu):
-    """On a prescaled finest level (nx >= 1024) the residual after a cycle is
+def test_stop_test_fused_into_the_next_fine_sweep(monkeypatch, name, stream_launched, nu):
+    """On a prescaled finest level (nx >= 1024: the TMA sweep) and on a
+    narrower one (the small tiled sweep) the residual after a cycle is
     summed inside the next cycle's first fine sweep (after the reverse-order
     post-smoothing sweep one colour satisfies its equation exactly), and that
     sweep's output is dropped when the loop stops.  The iterate must be the
@@ -853,7 +862,6 @@ def test_stop_test_fused_into_the_next_fine_sweep(monkeypatch, stream_launched, 
     oracle's operator on the returned iterate.  Cycles V(nu1, nu2) with
     nu1 = 1 (the sweep with the residual is the only pre-sweep), more sweeps,
     and nu1 or nu2 = 0 (no fusion: the separate pass)."""
-    name = "wide2047x127"
     pr = problem(name)
     b = dev(pr["b"])
     fused = nu[0] >= 1 and nu[1] >= 1
@@ -879,14 +887,19 @@ def test_stop_test_fused_into_the_next_fine_sweep(monkeypatch, stream_launched, 
             out[mode, cap] = (x, info, hg.residual_history())
             hg.destroy()
     st = oracle_hierarchy(name).levels[-1].st
+    st_abs = dict(st)
+    for d in O.DIRS:
+        st_abs[d] = -st[d]                       # |A| |x| = C |x| + sum_X a_X |x_X|
     for cap in (5, 400):
         (x0, i0, h0), (x1, i1, h1) = out["0", cap], out["1", cap]
         assert i0.cycles == i1.cycles and len(h0) == len(h1) == i1.cycles + 1
         assert torch.equal(x0, x1)
         # two evaluations of ||b - A x|| / ||b|| of the same iterate differ by
-        # rounding: about eps ||A| |x|| / ||b|| (1.7e-16 measured here)
-        assert np.all(np.abs(h1 - h0) <= 1e-6 * h0 + 2e-15), np.abs(h1 - h0).max()
-        rel = np.linalg.norm(O.residual(st, x1.cpu().numpy(), pr["b"])) / np.linalg.norm(pr["b"])
-        assert abs(i1.rel_resid - rel) <= 1e-6 * rel + 2e-15, (i1.rel_resid, rel)
+        # rounding: a few eps ||A| |x|| / ||b|| (x: the final iterate)
+        xn = x1.cpu().numpy()
+        floor = np.finfo(np.float64).eps * np.linalg.norm(O.apply(st_abs, np.abs(xn))) / np.linalg.norm(pr["b"])
+        assert np.all(np.abs(h1 - h0) <= 1e-6 * h0 + 10 * floor), (np.abs(h1 - h0).max(), floor)
+        rel = np.linalg.norm(O.residual(st, xn, pr["b"])) / np.linalg.norm(pr["b"])
+        assert abs(i1.rel_resid - rel) <= 1e-6 * rel + 10 * floor, (i1.rel_resid, rel, floor)
     assert out["1", 5][1].cycles == 5
     assert out["1", 400][1].rel_resid <= 1e-10 or nu == (1, 0)
