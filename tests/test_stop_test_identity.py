@@ -1,5 +1,6 @@
-"""The exactness argument behind the stop test taken inside the next sweep,
-checked with the oracle's own Gauss-Seidel arithmetic on CPU.
+"""The exactness arguments behind two shortcuts of the GPU cycle -- the stop
+test taken inside the next sweep, and the zero-start form of a sweep from
+x = 0 -- checked with the oracle's own Gauss-Seidel arithmetic on CPU.
 
 After a sweep in reverse colour order, nothing else touching x:
 * the colour updated last satisfies its update exactly: recomputing that
@@ -63,3 +64,40 @@ def test_second_colour_update_carries_the_residual():
     for (pj, pi) in order[0]:
         mask[pj::2, pi::2] = True
     assert np.abs(r[mask]).max() <= 1e-12 * np.abs(r).max()
+
+
+def _colour_of(order, pj, pi):
+    for k, colour in enumerate(order):
+        if (pj, pi) in colour:
+            return k
+    raise AssertionError((pj, pi))
+
+
+@pytest.mark.parametrize("name", ["five", "nine"])
+def test_zero_start_sweep_needs_only_the_colours_before(name):
+    """A forward sweep from x = 0 (each coarse level's first pre-sweep) gives
+    the same values when colour k applies only the neighbour terms of the
+    colours updated before it: the zero-start form of the GPU sweeps (four
+    colours: 0, 2, 6 and 8 of the 8 terms; two colours: 0 and 4)."""
+    st, b = _level(name)
+    order = O.colour_order(st)
+    x = np.zeros_like(b)
+    O.relax(st, x, b, 1, order)
+    y = np.zeros_like(b)
+    ny, nx = b.shape
+    counts = []
+    for k, colour in enumerate(order):
+        yp = np.pad(y, 1)
+        for (pj, pi) in colour:
+            rows, cols = slice(pj, None, 2), slice(pi, None, 2)
+            s = b[rows, cols].copy()
+            used = 0
+            for d in O.DIRS:
+                di, dj = O.OFFSETS[d]
+                if _colour_of(order, (pj + dj) % 2, (pi + di) % 2) < k:
+                    s += st[d][rows, cols] * O.shifted(yp, d, ny, nx, rows, cols)
+                    used += 1 if np.any(st[d]) else 0
+            y[rows, cols] = s / st["C"][rows, cols]
+        counts.append(used)
+    assert np.array_equal(x, y)
+    assert counts == ([0, 2, 6, 8] if name == "nine" else [0, 4])
