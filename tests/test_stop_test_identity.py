@@ -101,3 +101,65 @@ def test_zero_start_sweep_needs_only_the_colours_before(name):
         counts.append(used)
     assert np.array_equal(x, y)
     assert counts == ([0, 2, 6, 8] if name == "nine" else [0, 4])
+
+
+def _three_d():
+    from oracle import boxmg3d_oracle as O3
+    rng = np.random.default_rng(21)
+    nx, ny, nz = 11, 9, 7
+    kb = 10.0 ** rng.uniform(-2, 2, (3, 3, 3))
+    k = np.repeat(np.repeat(np.repeat(kb, 4, 0), 4, 1), 4, 2)[:nz, :ny, :nx]
+    h = O3.setup(k)
+    return O3, h, rng
+
+
+def test_3d_stop_test_identities():
+    """The 3D V-cycle's stop test inside the next fine sweep (k3_gs_norm):
+    after a reverse red-black sweep colour 0 is unchanged by its update, and
+    C (x_new - x_old) over colour 1 has the norm of b - A x."""
+    O3, h, rng = _three_d()
+    lv = h.levels[-1]
+    a, shape = lv.a, lv.shape
+    n = a.shape[0]
+    b = rng.uniform(-1, 1, n)
+    x = rng.uniform(-1, 1, n)
+    O3.relax(a, shape, x, b, 2)
+    O3.relax(a, shape, x, b, 1, reverse=True)
+    col, nc = O3.colours(shape, True)
+    diag = a.diagonal()
+    off = (a - O3.sp.diags(diag)).tocsr()
+    s0, s1 = np.nonzero(col == 0)[0], np.nonzero(col == 1)[0]
+    assert np.array_equal(x[s0], (b[s0] - off[s0] @ x) / diag[s0])
+    y1 = (b[s1] - off[s1] @ x) / diag[s1]
+    r = b - a @ x
+    fused = np.linalg.norm(diag[s1] * (y1 - x[s1]))
+    assert abs(fused - np.linalg.norm(r)) <= 1e-12 * np.linalg.norm(r)
+
+
+def test_3d_zero_start_terms_per_colour():
+    """A forward eight-colour sweep of a 27-point (Galerkin) level from
+    x = 0 equals the sweep in which colour c uses only the neighbours of
+    colours before it -- 0, 2, 6, 8, 18, 20, 24, 26 of the 26 for c = 0..7,
+    the kernel's zero_term3 rule."""
+    O3, h, rng = _three_d()
+    lv = h.levels[-2]
+    a, shape = lv.a, lv.shape
+    n = a.shape[0]
+    b = rng.uniform(-1, 1, n)
+    x = np.zeros(n)
+    O3.relax(a, shape, x, b, 1)
+    col, nc = O3.colours(shape, False)
+    assert nc == 8
+    diag = a.diagonal()
+    off = (a - O3.sp.diags(diag)).tocoo()
+    y = np.zeros(n)
+    counts = []
+    for c in range(8):
+        s = np.nonzero(col == c)[0]
+        keep = (col[off.row] == c) & (col[off.col] < c)
+        part = O3.sp.csr_matrix((off.data[keep], (off.row[keep], off.col[keep])), shape=off.shape)
+        y[s] = (b[s] - part[s] @ y) / diag[s]
+        # the largest number of terms one point of colour c keeps
+        counts.append(int(np.diff(part.tocsr().indptr)[s].max()) if s.size else 0)
+    assert np.allclose(x, y, rtol=0, atol=0)
+    assert counts == [0, 2, 6, 8, 18, 20, 24, 26]
